@@ -1,0 +1,238 @@
+/*
+ * ctq.h -- C ABI of the GB300 local-trace library (libctq.so).
+ *
+ * The library evaluates the CT-HYB local trace of arXiv 2010.08482,
+ * Eq. pweight1 in the sector form of Sec. 3.3.1 ("Computing the local
+ * impurity trace"):
+ *
+ *   w(C) = sum_{q0} Tr P_{beta - tau_n}(q_n) F_{alpha_n}(q_{n-1}) ...
+ *                      F_{alpha_1}(q0) P_{tau_1}(q0),
+ *
+ * for batches of already time-ordered operator sequences, on one GPU, with
+ * the lazy-trace norm bounds (Sec. 3.3.1, lazy-trace paragraph) for early
+ * rejection.  The time-ordering permutation sign is the caller's
+ * (Sec. 3.3.1 states the product after T_tau has been applied).
+ *
+ * Conventions for every entry point:
+ *   - return 0 (CTQ_OK) on success, a negative CTQ_ERR_* code otherwise;
+ *     no C++ exception crosses the ABI; ctq_strerror() names the code.
+ *   - the library never frees caller buffers; objects it creates are freed
+ *     by the matching ctq_free_* call.
+ *   - "device" pointers are CUDA global-memory pointers on the impurity's
+ *     device; "host" pointers are ordinary CPU memory.
+ *   - operator code alpha = 2*f + dag (dag = 1: c^dagger), flavour f in the
+ *     paper's order: all spin-down orbitals, then all spin-up (App. A,
+ *     Eqs. enumProduct / enumCoupled).
+ */
+#ifndef CTQ_H
+#define CTQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes returned by the entry points ---------------------------- */
+#define CTQ_OK 0
+#define CTQ_ERR_ARG (-1)         /* invalid argument (null, size, value)        */
+#define CTQ_ERR_NOMEM (-2)       /* host or device allocation failed            */
+#define CTQ_ERR_CUDA (-3)        /* a CUDA runtime call failed                  */
+#define CTQ_ERR_TIMEOUT (-4)     /* a bounded device wait expired               */
+#define CTQ_ERR_UNSUPPORTED (-5) /* combination not built (e.g. precision)      */
+#define CTQ_ERR_NUMERIC (-6)     /* eigensolver did not converge                */
+#define CTQ_ERR_WORKSPACE (-7)   /* workspace smaller than ctq_workspace_size() */
+
+/* ---- per-chain status written by ctq_eval_traces -------------------------- */
+#define CTQ_CHAIN_OK 0             /* trace computed; no decision requested    */
+#define CTQ_CHAIN_ZERO 1           /* no surviving q0, or the trace is exactly 0 */
+#define CTQ_CHAIN_REJECTED_EARLY 2 /* bound below threshold: trace not finished */
+#define CTQ_CHAIN_ACCEPTED 3       /* full trace, log|w| >= threshold           */
+#define CTQ_CHAIN_REJECTED 4       /* full trace, log|w| <  threshold           */
+#define CTQ_CHAIN_ERR_ARG (-1)     /* malformed sequence (see ctq_batch)        */
+
+/* ---- enums ------------------------------------------------------------------ */
+#define CTQ_KANAMORI 0 /* U, U' = U - 2J, J (rotationally invariant Kanamori)    */
+#define CTQ_SLATER 1   /* Slater-Condon, F0 = U, J fixes F2, F4 (, F6)            */
+
+#define CTQ_MU_GIVEN 0        /* mu as given                                      */
+#define CTQ_MU_PH_SYMMETRIC 1 /* mu such that E_gs(n0 - 1) = E_gs(n0 + 1)         */
+
+#define CTQ_SECTORS_N_SZ 0 /* sectors labelled by (N_down, N_up)                 */
+#define CTQ_SECTORS_N 1    /* sectors labelled by N                               */
+
+#define CTQ_FP64 0   /* all products in float64                                  */
+#define CTQ_TF32 1   /* tensor-core TF32 products, FP32 accumulation             */
+#define CTQ_BF16X3 2 /* three-term bf16 split products, FP32 accumulation        */
+#define CTQ_TF32X3 3 /* three-term tf32 split products, FP32 accumulation        */
+
+/*
+ * Local-Hamiltonian parameters (Eq. ImpurityHamiltonian, Sec. 2.1):
+ *   H = sum_ij c+_i (t_ij - mu delta_ij) c_j + 1/2 sum_ijkl U_ijkl c+_i c+_j c_k c_l.
+ * n_orb orbitals, n_f = 2 n_orb flavours.  interaction = CTQ_KANAMORI uses a
+ * generic orbital basis; CTQ_SLATER uses the real-harmonic product basis of
+ * App. A with l = 2 (d) or 3 (f).  soc_xi adds xi l.s (Slater shells).  cf_re /
+ * cf_im (host, n_f x n_f row-major, nullable) add an Hermitian one-body term
+ * t_ij in the flavour basis.  n_min / n_max (-1: none) truncate the Hilbert
+ * space to N in [n_min, n_max]; an operator leaving the window maps to the
+ * zero sector.  device: CUDA ordinal that receives the blocks (-1: host only,
+ * ctq_eval_traces then fails with CTQ_ERR_ARG).
+ */
+typedef struct {
+  int n_orb;
+  int l;
+  int interaction;
+  double U, J;
+  int mu_mode;
+  double mu;
+  int n0;
+  double soc_xi;
+  const double* cf_re;
+  const double* cf_im;
+  int sector_mode;
+  int n_min, n_max;
+  int device;
+} ctq_model_params;
+
+typedef struct ctq_impurity ctq_impurity;
+
+typedef struct {
+  int n_flav;      /* flavours (spin-orbitals)                              */
+  int n_sec;       /* sectors                                               */
+  int max_dim;     /* largest sector dimension                              */
+  int is_complex;  /* 1 if the blocks are complex                           */
+  double mu;       /* chemical potential used                               */
+  double E_gs;     /* ground-state energy (mu included)                     */
+  int64_t n_block_elems; /* total elements over all nonzero blocks          */
+} ctq_info;
+
+/*
+ * Build the sector-decomposed impurity (Sec. 3.2 "Structure", phase (1):
+ * decompose the Hilbert space into invariant spaces, diagonalise each, build
+ * the operator matrices in the eigenbasis; Sec. 3.3.1 sector map s_alpha(q)).
+ * Host work, then an upload of the blocks to p->device.  *out is owned by the
+ * library (free with ctq_free_impurity).  Errors: CTQ_ERR_ARG (bad params),
+ * CTQ_ERR_NUMERIC, CTQ_ERR_NOMEM, CTQ_ERR_CUDA.
+ */
+int ctq_build_impurity(const ctq_model_params* p, ctq_impurity** out);
+
+/*
+ * Load an impurity given directly in its eigenbasis (all host arrays, copied):
+ *   dims[n_sec], N[n_sec] (particle number per sector),
+ *   energies: sum(dims) float64, sector by sector, ascending within a sector,
+ *   s_table[(2 n_flav) x n_sec] int32: target sector of alpha on q, or -1,
+ *   blocks_re / blocks_im: every nonzero block F_alpha(q) (d_{s(q)} x d_q,
+ *     row-major, <m(q')|c_alpha|n(q)>) concatenated in (alpha, q) order;
+ *     blocks_im may be NULL for a real impurity,
+ *   opnorm (nullable): ||F_alpha(q)||_2 per (alpha, q) in the same order;
+ *     NULL: estimated by power iteration and inflated by 1e-9 relative.
+ * Same ownership and errors as ctq_build_impurity.
+ */
+int ctq_load_impurity(int n_flav, int n_sec, const int* dims, const int* N, const double* energies,
+                      const int* s_table, const double* blocks_re, const double* blocks_im,
+                      const double* opnorm, double mu, int device, ctq_impurity** out);
+
+int ctq_impurity_info(const ctq_impurity* imp, ctq_info* out);
+
+/*
+ * Copy sector data to host arrays (each nullable): dims[n_sec], N[n_sec],
+ * E_min[n_sec], s_table[(2 n_flav) x n_sec].
+ */
+int ctq_get_sectors(const ctq_impurity* imp, int* dims, int* N, double* E_min, int* s_table);
+
+/* Energies of sector q (host, dims[q] float64, ascending, mu included). */
+int ctq_get_energies(const ctq_impurity* imp, int q, double* E);
+
+/*
+ * Copy block F_alpha(q) to host arrays re / im (d_{s(q)} x d_q row-major; im
+ * nullable, zero-filled for real impurities when given).  CTQ_ERR_ARG if the
+ * block is zero (s_alpha(q) = -1).
+ */
+int ctq_get_block(const ctq_impurity* imp, int alpha, int q, double* re, double* im);
+
+/*
+ * A batch of time-ordered operator sequences (device pointers, caller-owned):
+ *   offsets[n_chains + 1] int32, nondecreasing; chain c owns entries
+ *     offsets[c] .. offsets[c+1]-1 of tau and op,
+ *   tau   float64, strictly increasing within a chain, in [0, beta),
+ *   op    int32 alpha codes in [0, 2 n_flav),
+ *   log_threshold[n_chains] float64 (nullable): Metropolis threshold
+ *     T = log r + log|w_old| - log(other ratios), the random number r drawn
+ *     first (App. B, Eq. decide); accept iff log|w| >= T.
+ * A chain that breaks these rules gets status CTQ_CHAIN_ERR_ARG.
+ */
+typedef struct {
+  int n_chains;
+  double beta;
+  const int32_t* offsets;
+  const double* tau;
+  const int32_t* op;
+  const double* log_threshold;
+} ctq_batch;
+
+/*
+ * precision: CTQ_FP64 (others return CTQ_ERR_UNSUPPORTED where not built).
+ * lazy: 1 = stop a chain as soon as its upper bound falls below its threshold
+ *   (needs log_threshold).  segment: operators per bound refinement (>= 1).
+ * max_ops: largest 2k in the batch (sizes the bounds output).
+ * timeout_ns: limit for bounded device waits (0: library default).
+ */
+typedef struct {
+  int precision;
+  int lazy;
+  int segment;
+  int max_ops;
+  int64_t timeout_ns;
+} ctq_eval_opts;
+
+/*
+ * Results (device pointers, caller-owned):
+ *   log_abs[n_chains]  log|w| with every energy shift undone (-inf if w = 0,
+ *                      NaN if not evaluated),
+ *   phase[2 n_chains]  (re, im) of w/|w| (real impurities: (+-1, 0)),
+ *   status[n_chains]   CTQ_CHAIN_*,
+ *   bounds (nullable)  [n_chains x (n_seg + 1)], n_seg = ceil(max_ops/segment):
+ *                      column 0 the level-0 bound log B, column s >= 1 the
+ *                      refined bound after min(s*segment, 2k) operators (the
+ *                      last is log sum_q0 |w_q0|); NaN where not evaluated.
+ */
+typedef struct {
+  double* log_abs;
+  double* phase;
+  int32_t* status;
+  double* bounds;
+} ctq_result;
+
+/* Bytes of device workspace ctq_eval_traces needs for this batch shape. */
+size_t ctq_workspace_size(const ctq_impurity* imp, int n_chains, const ctq_eval_opts* opts);
+
+/*
+ * Evaluate the local traces of a batch.  Asynchronous on `stream` (a
+ * cudaStream_t; NULL = legacy default stream): only kernel launches and
+ * memsets are enqueued, nothing is allocated and nothing synchronises, so the
+ * call may be captured in a CUDA graph.  workspace: device memory of at least
+ * ctq_workspace_size() bytes, 256-byte aligned, used only for the duration of
+ * the enqueued work (calls that overlap on the GPU must not share it).
+ * Errors: CTQ_ERR_ARG, CTQ_ERR_WORKSPACE, CTQ_ERR_UNSUPPORTED, CTQ_ERR_CUDA.
+ */
+int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_eval_opts* opts,
+                    const ctq_result* result, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Number of kernels one ctq_eval_traces call enqueues (for launch accounting).
+ */
+int ctq_launches_per_eval(const ctq_impurity* imp, const ctq_eval_opts* opts);
+
+void ctq_free_impurity(ctq_impurity* imp);
+
+const char* ctq_strerror(int code);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* ctq_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CTQ_H */

@@ -1,0 +1,372 @@
+// extern "C" entry points of libctq (declared in include/ctq.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ctq_internal.h"
+
+struct ctq_impurity {
+  ctq::HostModel host;
+  int device = -1;
+  int num_sms = 0;
+  ctq::DevModel dev{};
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev_);
+    ok_ = (dev == prev_) || cudaSetDevice(dev) == cudaSuccess;
+    switched_ = dev != prev_;
+  }
+  ~DeviceGuard() {
+    if (switched_) cudaSetDevice(prev_);
+  }
+  bool ok() const { return ok_; }
+
+ private:
+  int prev_ = 0;
+  bool ok_ = false, switched_ = false;
+};
+
+template <typename T>
+int upload_vec(ctq_impurity* imp, const std::vector<T>& v, const T** dst) {
+  void* p = nullptr;
+  const size_t bytes = std::max<size_t>(v.size() * sizeof(T), 16);
+  if (cudaMalloc(&p, bytes) != cudaSuccess) return CTQ_ERR_NOMEM;
+  imp->allocs.push_back(p);
+  if (!v.empty() && cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+    return CTQ_ERR_CUDA;
+  *dst = static_cast<const T*>(p);
+  return CTQ_OK;
+}
+
+void free_device(ctq_impurity* imp) {
+  if (imp->device < 0) return;
+  DeviceGuard g(imp->device);
+  for (void* p : imp->allocs) cudaFree(p);
+  imp->allocs.clear();
+}
+
+// Copies the host model to its device: energies relative to each sector's
+// minimum, sector map, block offsets, blocks (complex interleaved) and
+// log spectral norms.
+int upload_model(ctq_impurity* imp) {
+  const ctq::HostModel& h = imp->host;
+  if (imp->device < 0) return CTQ_OK;
+  DeviceGuard g(imp->device);
+  if (!g.ok()) return fail(CTQ_ERR_CUDA, "cudaSetDevice failed");
+  if (cudaDeviceGetAttribute(&imp->num_sms, cudaDevAttrMultiProcessorCount, imp->device) != cudaSuccess)
+    return fail(CTQ_ERR_CUDA, "cannot query the device");
+  ctq::DevModel& d = imp->dev;
+  d.n_flav = h.n_flav;
+  d.n_alpha = h.n_alpha();
+  d.n_sec = h.n_sec;
+  d.max_dim = h.max_dim;
+  d.is_complex = h.is_complex;
+  std::vector<double> e_rel(h.E.size());
+  for (int q = 0; q < h.n_sec; ++q)
+    for (int j = h.E_off[q]; j < h.E_off[q + 1]; ++j) e_rel[j] = h.E[j] - h.E_min[q];
+  std::vector<double> blk;
+  if (h.is_complex) {
+    blk.resize(2 * h.blk_re.size());
+    for (size_t i = 0; i < h.blk_re.size(); ++i) {
+      blk[2 * i] = h.blk_re[i];
+      blk[2 * i + 1] = h.blk_im[i];
+    }
+  } else {
+    blk = h.blk_re;
+  }
+  std::vector<double> lognorm(h.opnorm.size());
+  for (size_t i = 0; i < lognorm.size(); ++i) lognorm[i] = h.opnorm[i] > 0 ? std::log(h.opnorm[i]) : -INFINITY;
+  int st = CTQ_OK;
+  if ((st = upload_vec(imp, h.dims, &d.dims)) || (st = upload_vec(imp, h.E_off, &d.E_off)) ||
+      (st = upload_vec(imp, e_rel, &d.E_rel)) || (st = upload_vec(imp, h.E_min, &d.E_min)) ||
+      (st = upload_vec(imp, h.s, &d.s)) || (st = upload_vec(imp, h.blk_off, &d.blk_off)) ||
+      (st = upload_vec(imp, blk, &d.blk)) || (st = upload_vec(imp, lognorm, &d.log_norm))) {
+    free_device(imp);
+    return fail(st, "device upload failed");
+  }
+  return CTQ_OK;
+}
+
+// Power iteration on F^H F for ||F||_2 (user-supplied blocks).
+double spectral_norm(int rows, int cols, const double* re, const double* im) {
+  std::vector<double> xr(cols, 1.0 / std::sqrt(double(cols))), xi(cols, 0.0), yr(rows), yi(rows);
+  double lam = 0.0;
+  for (int it = 0; it < 200; ++it) {
+    for (int r = 0; r < rows; ++r) {
+      double ar = 0, ai = 0;
+      for (int c = 0; c < cols; ++c) {
+        const double fr = re[size_t(r) * cols + c], fi = im ? im[size_t(r) * cols + c] : 0.0;
+        ar += fr * xr[c] - fi * xi[c];
+        ai += fr * xi[c] + fi * xr[c];
+      }
+      yr[r] = ar;
+      yi[r] = ai;
+    }
+    double nrm = 0;
+    for (int c = 0; c < cols; ++c) {
+      double ar = 0, ai = 0;
+      for (int r = 0; r < rows; ++r) {
+        const double fr = re[size_t(r) * cols + c], fi = im ? -im[size_t(r) * cols + c] : 0.0;
+        ar += fr * yr[r] - fi * yi[r];
+        ai += fr * yi[r] + fi * yr[r];
+      }
+      xr[c] = ar;
+      xi[c] = ai;
+      nrm += ar * ar + ai * ai;
+    }
+    nrm = std::sqrt(nrm);
+    if (nrm == 0.0) return 0.0;
+    const double prev = lam;
+    lam = nrm;
+    for (int c = 0; c < cols; ++c) {
+      xr[c] /= nrm;
+      xi[c] /= nrm;
+    }
+    if (it > 5 && std::fabs(lam - prev) <= 1e-15 * lam) break;
+  }
+  return std::sqrt(lam) * (1.0 + 1e-9);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ctq_strerror(int code) {
+  switch (code) {
+    case CTQ_OK: return "ok";
+    case CTQ_ERR_ARG: return "invalid argument";
+    case CTQ_ERR_NOMEM: return "out of memory";
+    case CTQ_ERR_CUDA: return "CUDA runtime error";
+    case CTQ_ERR_TIMEOUT: return "device wait timed out";
+    case CTQ_ERR_UNSUPPORTED: return "unsupported configuration";
+    case CTQ_ERR_NUMERIC: return "eigensolver did not converge";
+    case CTQ_ERR_WORKSPACE: return "workspace too small";
+    default: return "unknown error";
+  }
+}
+
+const char* ctq_last_error_message(void) { return g_last_error.c_str(); }
+
+int ctq_build_impurity(const ctq_model_params* p, ctq_impurity** out) {
+  if (!p || !out) return fail(CTQ_ERR_ARG, "null argument");
+  *out = nullptr;
+  try {
+    ctq_impurity* imp = new ctq_impurity();
+    std::string err;
+    int st = ctq::build_host_model(p, imp->host, err);
+    if (st != CTQ_OK) {
+      delete imp;
+      return fail(st, err);
+    }
+    imp->device = p->device;
+    st = upload_model(imp);
+    if (st != CTQ_OK) {
+      delete imp;
+      return st;
+    }
+    *out = imp;
+    return CTQ_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(CTQ_ERR_NOMEM, "host allocation failed");
+  } catch (...) {
+    return fail(CTQ_ERR_ARG, "unexpected exception");
+  }
+}
+
+int ctq_load_impurity(int n_flav, int n_sec, const int* dims, const int* N, const double* energies,
+                      const int* s_table, const double* blocks_re, const double* blocks_im,
+                      const double* opnorm, double mu, int device, ctq_impurity** out) {
+  if (!out || !dims || !energies || !s_table || !blocks_re || n_flav < 1 || n_sec < 1)
+    return fail(CTQ_ERR_ARG, "null or empty argument");
+  *out = nullptr;
+  try {
+    ctq_impurity* imp = new ctq_impurity();
+    ctq::HostModel& h = imp->host;
+    h.n_flav = n_flav;
+    h.n_sec = n_sec;
+    h.is_complex = blocks_im ? 1 : 0;
+    h.mu = mu;
+    h.dims.assign(dims, dims + n_sec);
+    h.N.assign(n_sec, 0);
+    if (N) h.N.assign(N, N + n_sec);
+    h.E_off.assign(n_sec + 1, 0);
+    h.E_min.resize(n_sec);
+    h.E_gs = INFINITY;
+    for (int q = 0; q < n_sec; ++q) {
+      if (dims[q] < 1) { delete imp; return fail(CTQ_ERR_ARG, "sector dimension < 1"); }
+      h.E_off[q + 1] = h.E_off[q] + dims[q];
+      h.max_dim = std::max(h.max_dim, dims[q]);
+    }
+    h.E.assign(energies, energies + h.E_off[n_sec]);
+    for (int q = 0; q < n_sec; ++q) {
+      for (int j = h.E_off[q] + 1; j < h.E_off[q + 1]; ++j)
+        if (!(h.E[j] >= h.E[j - 1])) { delete imp; return fail(CTQ_ERR_ARG, "energies not ascending"); }
+      h.E_min[q] = h.E[h.E_off[q]];
+      h.E_gs = std::min(h.E_gs, h.E_min[q]);
+    }
+    const int na = 2 * n_flav;
+    h.s.assign(s_table, s_table + size_t(na) * n_sec);
+    h.blk_off.assign(size_t(na) * n_sec, -1);
+    h.opnorm.assign(size_t(na) * n_sec, 0.0);
+    int64_t total = 0;
+    for (int a = 0; a < na; ++a)
+      for (int q = 0; q < n_sec; ++q) {
+        const int qp = h.s[size_t(a) * n_sec + q];
+        if (qp < -1 || qp >= n_sec) { delete imp; return fail(CTQ_ERR_ARG, "sector table out of range"); }
+        if (qp < 0) continue;
+        h.blk_off[size_t(a) * n_sec + q] = total;
+        total += int64_t(dims[qp]) * dims[q];
+      }
+    h.blk_re.assign(blocks_re, blocks_re + total);
+    if (blocks_im) h.blk_im.assign(blocks_im, blocks_im + total);
+    int k = 0;
+    for (int a = 0; a < na; ++a)
+      for (int q = 0; q < n_sec; ++q) {
+        const size_t i = size_t(a) * n_sec + q;
+        const int qp = h.s[i];
+        if (qp < 0) continue;
+        h.opnorm[i] = opnorm ? opnorm[k]
+                             : spectral_norm(dims[qp], dims[q], &h.blk_re[h.blk_off[i]],
+                                             blocks_im ? &h.blk_im[h.blk_off[i]] : nullptr);
+        ++k;
+      }
+    imp->device = device;
+    int st = upload_model(imp);
+    if (st != CTQ_OK) {
+      delete imp;
+      return st;
+    }
+    *out = imp;
+    return CTQ_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(CTQ_ERR_NOMEM, "host allocation failed");
+  } catch (...) {
+    return fail(CTQ_ERR_ARG, "unexpected exception");
+  }
+}
+
+int ctq_impurity_info(const ctq_impurity* imp, ctq_info* out) {
+  if (!imp || !out) return fail(CTQ_ERR_ARG, "null argument");
+  const ctq::HostModel& h = imp->host;
+  out->n_flav = h.n_flav;
+  out->n_sec = h.n_sec;
+  out->max_dim = h.max_dim;
+  out->is_complex = h.is_complex;
+  out->mu = h.mu;
+  out->E_gs = h.E_gs;
+  out->n_block_elems = int64_t(h.blk_re.size());
+  return CTQ_OK;
+}
+
+int ctq_get_sectors(const ctq_impurity* imp, int* dims, int* N, double* E_min, int* s_table) {
+  if (!imp) return fail(CTQ_ERR_ARG, "null impurity");
+  const ctq::HostModel& h = imp->host;
+  if (dims) std::copy(h.dims.begin(), h.dims.end(), dims);
+  if (N) std::copy(h.N.begin(), h.N.end(), N);
+  if (E_min) std::copy(h.E_min.begin(), h.E_min.end(), E_min);
+  if (s_table) std::copy(h.s.begin(), h.s.end(), s_table);
+  return CTQ_OK;
+}
+
+int ctq_get_energies(const ctq_impurity* imp, int q, double* E) {
+  if (!imp || !E || q < 0 || q >= imp->host.n_sec) return fail(CTQ_ERR_ARG, "bad sector");
+  const ctq::HostModel& h = imp->host;
+  std::copy(h.E.begin() + h.E_off[q], h.E.begin() + h.E_off[q + 1], E);
+  return CTQ_OK;
+}
+
+int ctq_get_block(const ctq_impurity* imp, int alpha, int q, double* re, double* im) {
+  if (!imp || !re) return fail(CTQ_ERR_ARG, "null argument");
+  const ctq::HostModel& h = imp->host;
+  if (alpha < 0 || alpha >= h.n_alpha() || q < 0 || q >= h.n_sec) return fail(CTQ_ERR_ARG, "bad index");
+  const size_t i = size_t(alpha) * h.n_sec + q;
+  const int qp = h.s[i];
+  if (qp < 0) return fail(CTQ_ERR_ARG, "zero block");
+  const size_t cnt = size_t(h.dims[qp]) * h.dims[q];
+  const int64_t off = h.blk_off[i];
+  std::copy(h.blk_re.begin() + off, h.blk_re.begin() + off + cnt, re);
+  if (im) {
+    if (h.is_complex)
+      std::copy(h.blk_im.begin() + off, h.blk_im.begin() + off + cnt, im);
+    else
+      std::fill(im, im + cnt, 0.0);
+  }
+  return CTQ_OK;
+}
+
+static int n_seg_of(const ctq_eval_opts* o) {
+  const int S = std::max(1, o->segment);
+  return (std::max(0, o->max_ops) + S - 1) / S;
+}
+
+size_t ctq_workspace_size(const ctq_impurity* imp, int n_chains, const ctq_eval_opts* opts) {
+  if (!imp || !opts || n_chains < 0) return 0;
+  return ctq::workspace_layout(n_chains, imp->host.n_sec, n_seg_of(opts), nullptr, nullptr);
+}
+
+int ctq_launches_per_eval(const ctq_impurity* imp, const ctq_eval_opts* opts) {
+  if (!imp || !opts) return 0;
+  return 3;  // plan, trace, combine
+}
+
+int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_eval_opts* opts,
+                    const ctq_result* result, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!imp || !batch || !opts || !result) return fail(CTQ_ERR_ARG, "null argument");
+  if (imp->device < 0) return fail(CTQ_ERR_ARG, "impurity has no device copy");
+  if (batch->n_chains < 0) return fail(CTQ_ERR_ARG, "n_chains < 0");
+  if (batch->n_chains == 0) return CTQ_OK;
+  if (!batch->offsets || !batch->tau || !batch->op) return fail(CTQ_ERR_ARG, "null batch array");
+  if (!(batch->beta > 0.0)) return fail(CTQ_ERR_ARG, "beta <= 0");
+  if (!result->log_abs || !result->phase || !result->status) return fail(CTQ_ERR_ARG, "null result array");
+  if (opts->segment < 1 || opts->max_ops < 0) return fail(CTQ_ERR_ARG, "segment < 1 or max_ops < 0");
+  if (opts->lazy && !batch->log_threshold) return fail(CTQ_ERR_ARG, "lazy evaluation needs thresholds");
+  if (opts->precision != CTQ_FP64) return fail(CTQ_ERR_UNSUPPORTED, "precision not built");
+  if (!workspace) return fail(CTQ_ERR_ARG, "null workspace");
+  if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return fail(CTQ_ERR_ARG, "workspace not 256-byte aligned");
+  const int n_seg = n_seg_of(opts);
+  const size_t need = ctq::workspace_layout(batch->n_chains, imp->host.n_sec, n_seg, nullptr, nullptr);
+  if (workspace_bytes < need) return fail(CTQ_ERR_WORKSPACE, "workspace smaller than ctq_workspace_size()");
+  DeviceGuard g(imp->device);
+  if (!g.ok()) return fail(CTQ_ERR_CUDA, "cudaSetDevice failed");
+
+  ctq::Work W;
+  ctq::workspace_layout(batch->n_chains, imp->host.n_sec, n_seg, workspace, &W);
+  ctq::BatchView B{batch->n_chains, batch->beta, batch->offsets, batch->tau, batch->op, batch->log_threshold};
+  ctq::EvalCfg cfg;
+  cfg.lazy = opts->lazy ? 1 : 0;
+  cfg.has_thr = batch->log_threshold ? 1 : 0;
+  cfg.S = opts->segment;
+  cfg.n_seg_max = n_seg;
+  cfg.max_ops = opts->max_ops;
+  cfg.margin = 1e-9;
+  cfg.bounds = result->bounds;
+  const int st = ctq::launch_eval_fp64(imp->dev, B, cfg, W, result, imp->num_sms, stream);
+  if (st != CTQ_OK) return fail(st, st == CTQ_ERR_CUDA ? cudaGetErrorString(cudaGetLastError()) : "launch failed");
+  return CTQ_OK;
+}
+
+void ctq_free_impurity(ctq_impurity* imp) {
+  if (!imp) return;
+  free_device(imp);
+  delete imp;
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// Internal declarations shared by the translation units of libctq.
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "ctq.h"
+
+namespace ctq {
+
+using cplx = std::complex<double>;
+
+// Sector-decomposed impurity in its eigenbasis, host copy.
+//   E is concatenated per sector (E_off[q] .. E_off[q+1]), ascending, mu included.
+//   s[alpha * n_sec + q]: target sector of operator alpha on q, or -1.
+//   blk_off[alpha * n_sec + q]: element offset of block F_alpha(q)
+//     (d_{s(q)} x d_q, row-major) in blk_re / blk_im, or -1.
+//   opnorm: spectral norm of each block (0 for absent blocks).
+struct HostModel {
+  int n_flav = 0, n_sec = 0, max_dim = 0, is_complex = 0;
+  double mu = 0.0, E_gs = 0.0;
+  std::vector<int> dims, N, E_off;
+  std::vector<double> E, E_min;
+  std::vector<int> s;
+  std::vector<int64_t> blk_off;
+  std::vector<double> blk_re, blk_im;
+  std::vector<double> opnorm;
+  int n_alpha() const { return 2 * n_flav; }
+};
+
+// Builds the model from physics parameters on the host (Fock space, H_loc,
+// sectors, eigensolver, blocks).  Returns a CTQ_* status.
+int build_host_model(const ctq_model_params* p, HostModel& m, std::string& err);
+
+// Hermitian eigensolver (cyclic Jacobi): A (n x n, row-major) is destroyed;
+// E ascending, V[row * n + col] = component row of eigenvector col.
+int jacobi_eigh_real(int n, std::vector<double>& A, std::vector<double>& E, std::vector<double>& V);
+int jacobi_eigh_cplx(int n, std::vector<cplx>& A, std::vector<double>& E, std::vector<cplx>& V);
+
+// Device-side view of a model (all pointers on the model's device).
+struct DevModel {
+  int n_flav, n_alpha, n_sec, max_dim, is_complex;
+  const int* dims;      // [n_sec]
+  const int* E_off;     // [n_sec + 1]
+  const double* E_rel;  // [sum dims]  E_q,j - E_min(q)  (>= 0)
+  const double* E_min;  // [n_sec]
+  const int* s;         // [n_alpha * n_sec]
+  const int64_t* blk_off;  // [n_alpha * n_sec]  element offsets, -1 absent
+  const double* blk;    // real: re; complex: interleaved (re, im)
+  const double* log_norm;  // [n_alpha * n_sec]  log ||F||_2 (-inf absent)
+};
+
+struct BatchView {
+  int n_chains;
+  double beta;
+  const int32_t* offsets;
+  const double* tau;
+  const int32_t* op;
+  const double* log_threshold;
+};
+
+struct EvalCfg {
+  int lazy;         // early reject enabled (and thresholds present)
+  int has_thr;      // thresholds present
+  int S;            // segment length
+  int n_seg_max;    // ceil(max_ops / S)
+  int max_ops;      // longest chain allowed (longer chains are flagged invalid)
+  double margin;    // safety margin (log units) applied to bounds before rejecting
+  double* bounds;   // result bounds [C x (n_seg_max + 1)] or nullptr
+};
+
+// A work item: one surviving (chain, q0) string.
+struct Item {
+  int c;
+  int q0;
+  int r;         // min over the string of the sector dimension (rank bound)
+  int n_seg;     // ceil(n / S)
+  double t_all;  // sum of log ||F_i||_2 and -dtau E_min over the string (see plan kernel)
+};
+
+// Views of the caller's workspace.
+struct Work {
+  int* counters;   // [0] n_items, [1] next item, [2] device error bits
+  Item* items;     // [C * n_sec]
+  double* res_val; // [C * n_sec * 2]  scaled trace value (re, im)
+  double* res_log; // [C * n_sec]      log scale of res_val (-inf: zero)
+  double* live;    // [C * n_sec]      live log upper bound per (c, q0)
+  double* lvl0;    // [C * n_sec]      level-0 log bound per (c, q0)
+  double* seg;     // [C * n_sec * (n_seg_max + 1)] per-segment log bounds
+  int* chain_flag; // [C]  bit 0 invalid, bit 1 rejected early
+};
+
+enum : int { FLAG_INVALID = 1, FLAG_REJECTED = 2 };
+
+size_t workspace_layout(int n_chains, int n_sec, int n_seg_max, void* base, Work* w);
+
+// Launchers (trace_fp64.cu).  Return a CTQ_* status.
+int launch_eval_fp64(const DevModel& M, const BatchView& B, const EvalCfg& cfg, const Work& W,
+                     const ctq_result* R, int num_sms, void* stream);
+
+}  // namespace ctq

@@ -1,0 +1,324 @@
+"""Python binding of libctq (include/ctq.h): argument marshalling only.
+
+Every step of the local-trace evaluation runs in the library's CUDA kernels.
+PyTorch supplies device memory and the current stream; nothing here computes
+a trace.  If libctq.so is missing the import fails loudly (build it with
+``python -c "import __graft_entry__ as g; g.build()"``); there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int, c_int32, c_int64, c_size_t, c_void_p
+from typing import Optional
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libctq.so")
+
+CTQ_OK = 0
+CTQ_ERR_ARG, CTQ_ERR_NOMEM, CTQ_ERR_CUDA, CTQ_ERR_TIMEOUT = -1, -2, -3, -4
+CTQ_ERR_UNSUPPORTED, CTQ_ERR_NUMERIC, CTQ_ERR_WORKSPACE = -5, -6, -7
+
+CHAIN_OK, CHAIN_ZERO, CHAIN_REJECTED_EARLY, CHAIN_ACCEPTED, CHAIN_REJECTED = 0, 1, 2, 3, 4
+CHAIN_ERR_ARG = -1
+
+KANAMORI, SLATER = 0, 1
+MU_GIVEN, MU_PH_SYMMETRIC = 0, 1
+SECTORS_N_SZ, SECTORS_N = 0, 1
+FP64, TF32, BF16X3, TF32X3 = 0, 1, 2, 3
+
+
+class CtqError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib.ctq_strerror(code).decode()
+        detail = _lib.ctq_last_error_message().decode()
+        super().__init__(f"{where}: {msg} ({code}){': ' + detail if detail else ''}")
+        self.code = code
+
+
+class ModelParamsC(ctypes.Structure):
+    _fields_ = [("n_orb", c_int), ("l", c_int), ("interaction", c_int), ("U", c_double), ("J", c_double),
+                ("mu_mode", c_int), ("mu", c_double), ("n0", c_int), ("soc_xi", c_double),
+                ("cf_re", POINTER(c_double)), ("cf_im", POINTER(c_double)), ("sector_mode", c_int),
+                ("n_min", c_int), ("n_max", c_int), ("device", c_int)]
+
+
+class InfoC(ctypes.Structure):
+    _fields_ = [("n_flav", c_int), ("n_sec", c_int), ("max_dim", c_int), ("is_complex", c_int),
+                ("mu", c_double), ("E_gs", c_double), ("n_block_elems", c_int64)]
+
+
+class BatchC(ctypes.Structure):
+    _fields_ = [("n_chains", c_int), ("beta", c_double), ("offsets", c_void_p), ("tau", c_void_p),
+                ("op", c_void_p), ("log_threshold", c_void_p)]
+
+
+class EvalOptsC(ctypes.Structure):
+    _fields_ = [("precision", c_int), ("lazy", c_int), ("segment", c_int), ("max_ops", c_int),
+                ("timeout_ns", c_int64)]
+
+
+class ResultC(ctypes.Structure):
+    _fields_ = [("log_abs", c_void_p), ("phase", c_void_p), ("status", c_void_p), ("bounds", c_void_p)]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libctq.so is not built ({_LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(_LIB_PATH)
+    P = c_void_p
+    sig = {
+        "ctq_build_impurity": (c_int, [POINTER(ModelParamsC), POINTER(P)]),
+        "ctq_load_impurity": (c_int, [c_int, c_int, P, P, P, P, P, P, P, c_double, c_int, POINTER(P)]),
+        "ctq_impurity_info": (c_int, [P, POINTER(InfoC)]),
+        "ctq_get_sectors": (c_int, [P, P, P, P, P]),
+        "ctq_get_energies": (c_int, [P, c_int, P]),
+        "ctq_get_block": (c_int, [P, c_int, c_int, P, P]),
+        "ctq_workspace_size": (c_size_t, [P, c_int, POINTER(EvalOptsC)]),
+        "ctq_eval_traces": (c_int, [P, POINTER(BatchC), POINTER(EvalOptsC), POINTER(ResultC), P, c_size_t, P]),
+        "ctq_launches_per_eval": (c_int, [P, POINTER(EvalOptsC)]),
+        "ctq_free_impurity": (None, [P]),
+        "ctq_strerror": (c_char_p, [c_int]),
+        "ctq_last_error_message": (c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+EXPORTED = ("ctq_build_impurity", "ctq_load_impurity", "ctq_impurity_info", "ctq_get_sectors",
+            "ctq_get_energies", "ctq_get_block", "ctq_workspace_size", "ctq_eval_traces",
+            "ctq_launches_per_eval", "ctq_free_impurity", "ctq_strerror", "ctq_last_error_message")
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def strerror(code: int) -> str:
+    return _lib.ctq_strerror(code).decode()
+
+
+def _check(code: int, where: str):
+    if code != CTQ_OK:
+        raise CtqError(code, where)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(c_void_p) if a is not None else None
+
+
+class Impurity:
+    """Owner of a ctq_impurity handle (freed with ctq_free_impurity)."""
+
+    def __init__(self, handle: c_void_p):
+        self.handle = handle
+        info = InfoC()
+        _check(_lib.ctq_impurity_info(handle, ctypes.byref(info)), "ctq_impurity_info")
+        self.n_flav = info.n_flav
+        self.n_sec = info.n_sec
+        self.max_dim = info.max_dim
+        self.is_complex = bool(info.is_complex)
+        self.mu = info.mu
+        self.E_gs = info.E_gs
+        self.n_block_elems = info.n_block_elems
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.ctq_free_impurity(h)
+            self.handle = None
+
+    def sectors(self):
+        dims = np.zeros(self.n_sec, np.int32)
+        N = np.zeros(self.n_sec, np.int32)
+        Emin = np.zeros(self.n_sec)
+        s = np.zeros((2 * self.n_flav, self.n_sec), np.int32)
+        _check(_lib.ctq_get_sectors(self.handle, _ptr(dims), _ptr(N), _ptr(Emin), _ptr(s)), "ctq_get_sectors")
+        return dims, N, Emin, s
+
+    def energies(self, q: int) -> np.ndarray:
+        dims = self.sectors()[0]
+        E = np.zeros(int(dims[q]))
+        _check(_lib.ctq_get_energies(self.handle, q, _ptr(E)), "ctq_get_energies")
+        return E
+
+    def block(self, alpha: int, q: int) -> np.ndarray:
+        dims, _, _, s = self.sectors()
+        qp = int(s[alpha, q])
+        if qp < 0:
+            raise CtqError(CTQ_ERR_ARG, "zero block")
+        re = np.zeros((int(dims[qp]), int(dims[q])))
+        im = np.zeros_like(re)
+        _check(_lib.ctq_get_block(self.handle, alpha, q, _ptr(re), _ptr(im)), "ctq_get_block")
+        return re + 1j * im if self.is_complex else re
+
+
+def build_impurity(p, device: int = 0) -> Impurity:
+    """ctq_build_impurity from a workloads.ModelParams-like object."""
+    nf = 2 * p.n_orb
+    cf_re = cf_im = None
+    if p.cf is not None:
+        cf = np.asarray(p.cf, dtype=np.complex128).reshape(nf, nf)
+        cf_re = np.ascontiguousarray(cf.real)
+        cf_im = np.ascontiguousarray(cf.imag)
+    c = ModelParamsC()
+    c.n_orb = p.n_orb
+    c.l = p.l
+    c.interaction = KANAMORI if p.interaction == "kanamori" else SLATER
+    c.U, c.J = p.U, p.J
+    c.mu_mode = MU_PH_SYMMETRIC if p.mu is None else MU_GIVEN
+    c.mu = 0.0 if p.mu is None else float(p.mu)
+    c.n0 = p.n0
+    c.soc_xi = p.soc_xi
+    c.cf_re = cf_re.ctypes.data_as(POINTER(c_double)) if cf_re is not None else None
+    c.cf_im = cf_im.ctypes.data_as(POINTER(c_double)) if cf_im is not None else None
+    c.sector_mode = SECTORS_N_SZ if p.sector_mode == "n_sz" else SECTORS_N
+    c.n_min, c.n_max = p.n_min, p.n_max
+    c.device = device
+    h = c_void_p()
+    _check(_lib.ctq_build_impurity(ctypes.byref(c), ctypes.byref(h)), "ctq_build_impurity")
+    return Impurity(h)
+
+
+def load_impurity(n_flav: int, dims, N, energies, s_table, blocks, mu: float = 0.0,
+                  opnorm=None, device: int = 0) -> Impurity:
+    """ctq_load_impurity: blocks is a dict {(alpha, q): matrix} (every nonzero block)."""
+    dims = np.ascontiguousarray(dims, dtype=np.int32)
+    n_sec = len(dims)
+    N = np.ascontiguousarray(N, dtype=np.int32)
+    E = np.ascontiguousarray(np.concatenate([np.asarray(e, np.float64) for e in energies]))
+    s = np.ascontiguousarray(s_table, dtype=np.int32).reshape(2 * n_flav, n_sec)
+    parts, norms = [], []
+    is_c = any(np.iscomplexobj(b) for b in blocks.values())
+    for a in range(2 * n_flav):
+        for q in range(n_sec):
+            if s[a, q] < 0:
+                continue
+            parts.append(np.asarray(blocks[(a, q)]).reshape(-1))
+            if opnorm is not None:
+                norms.append(opnorm[(a, q)])
+    flat = np.concatenate(parts) if parts else np.zeros(0)
+    re = np.ascontiguousarray(flat.real, dtype=np.float64)
+    im = np.ascontiguousarray(flat.imag, dtype=np.float64) if is_c else None
+    nrm = np.ascontiguousarray(norms, dtype=np.float64) if opnorm is not None else None
+    h = c_void_p()
+    _check(_lib.ctq_load_impurity(n_flav, n_sec, _ptr(dims), _ptr(N), _ptr(E), _ptr(s), _ptr(re), _ptr(im),
+                                  _ptr(nrm), float(mu), device, ctypes.byref(h)), "ctq_load_impurity")
+    return Impurity(h)
+
+
+def _opts(precision=FP64, lazy=False, segment=8, max_ops=0, timeout_ns=0) -> EvalOptsC:
+    o = EvalOptsC()
+    o.precision, o.lazy, o.segment, o.max_ops, o.timeout_ns = precision, int(lazy), segment, max_ops, timeout_ns
+    return o
+
+
+def workspace_size(imp: Impurity, n_chains: int, precision=FP64, lazy=False, segment=8, max_ops=0) -> int:
+    o = _opts(precision, lazy, segment, max_ops)
+    return int(_lib.ctq_workspace_size(imp.handle, n_chains, ctypes.byref(o)))
+
+
+def launches_per_eval(imp: Impurity, precision=FP64) -> int:
+    o = _opts(precision)
+    return int(_lib.ctq_launches_per_eval(imp.handle, ctypes.byref(o)))
+
+
+def eval_traces(imp: Impurity, n_chains: int, beta: float, offsets, tau, op, log_threshold,
+                log_abs, phase, status, bounds, workspace, workspace_bytes: int, stream,
+                precision=FP64, lazy=False, segment=8, max_ops=0, timeout_ns=0):
+    """ctq_eval_traces with raw device pointers (ints) and a cudaStream_t (int)."""
+    b = BatchC()
+    b.n_chains, b.beta = n_chains, beta
+    b.offsets, b.tau, b.op, b.log_threshold = offsets, tau, op, log_threshold
+    r = ResultC()
+    r.log_abs, r.phase, r.status, r.bounds = log_abs, phase, status, bounds
+    o = _opts(precision, lazy, segment, max_ops, timeout_ns)
+    _check(_lib.ctq_eval_traces(imp.handle, ctypes.byref(b), ctypes.byref(o), ctypes.byref(r),
+                                workspace, workspace_bytes, stream), "ctq_eval_traces")
+
+
+free_impurity = Impurity.__del__
+
+
+# --------------------------------------------------------------------------- torch helpers
+
+class DeviceBatch:
+    """A workloads.Batch copied to device tensors (int32 offsets/op, float64 tau)."""
+
+    def __init__(self, batch, device="cuda", log_threshold: Optional[np.ndarray] = None):
+        import torch
+        self.n_chains = batch.n_chains
+        self.beta = float(batch.beta)
+        self.max_ops = int(np.max(np.diff(batch.offsets))) if batch.n_chains else 0
+        self.offsets = torch.as_tensor(np.asarray(batch.offsets, np.int32), device=device)
+        n = max(1, len(batch.tau))
+        self.tau = torch.zeros(n, dtype=torch.float64, device=device)
+        self.op = torch.zeros(n, dtype=torch.int32, device=device)
+        if len(batch.tau):
+            self.tau[: len(batch.tau)] = torch.as_tensor(np.asarray(batch.tau, np.float64), device=device)
+            self.op[: len(batch.op)] = torch.as_tensor(np.asarray(batch.op, np.int32), device=device)
+        self.log_threshold = None
+        if log_threshold is not None:
+            self.log_threshold = torch.as_tensor(np.asarray(log_threshold, np.float64), device=device)
+
+
+class TraceEvaluator:
+    """Pre-allocates the workspace and result tensors for batches of up to
+    n_chains chains with at most max_ops operators, then evaluates batches on
+    the current torch stream (no allocation per call)."""
+
+    def __init__(self, imp: Impurity, n_chains: int, max_ops: int, precision=FP64, segment=8,
+                 with_bounds=True, device="cuda"):
+        import torch
+        self.imp = imp
+        self.n_chains = n_chains
+        self.max_ops = max_ops
+        self.precision = precision
+        self.segment = segment
+        self.n_seg = (max_ops + segment - 1) // segment
+        self.ws_bytes = workspace_size(imp, n_chains, precision, False, segment, max_ops)
+        # 256-byte aligned workspace
+        self._ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=device)
+        base = self._ws.data_ptr()
+        self.ws_ptr = (base + 255) // 256 * 256
+        self.log_abs = torch.empty(n_chains, dtype=torch.float64, device=device)
+        self.phase = torch.empty(2 * n_chains, dtype=torch.float64, device=device)
+        self.status = torch.empty(n_chains, dtype=torch.int32, device=device)
+        self.bounds = (torch.empty(n_chains * (self.n_seg + 1), dtype=torch.float64, device=device)
+                       if with_bounds else None)
+
+    def __call__(self, db: DeviceBatch, lazy=False, stream=None):
+        import torch
+        if db.n_chains > self.n_chains or db.max_ops > self.max_ops:
+            raise ValueError("batch larger than the evaluator was sized for")
+        s = torch.cuda.current_stream() if stream is None else stream
+        thr = db.log_threshold.data_ptr() if db.log_threshold is not None else None
+        eval_traces(self.imp, db.n_chains, db.beta, db.offsets.data_ptr(), db.tau.data_ptr(), db.op.data_ptr(),
+                    thr, self.log_abs.data_ptr(), self.phase.data_ptr(), self.status.data_ptr(),
+                    self.bounds.data_ptr() if self.bounds is not None else None,
+                    self.ws_ptr, self.ws_bytes, s.cuda_stream, self.precision, lazy, self.segment, self.max_ops)
+
+    def results(self, n_chains: Optional[int] = None):
+        n = self.n_chains if n_chains is None else n_chains
+        out = {
+            "log_abs": self.log_abs[:n].cpu().numpy(),
+            "phase": self.phase[: 2 * n].cpu().numpy().reshape(n, 2),
+            "status": self.status[:n].cpu().numpy(),
+        }
+        if self.bounds is not None:
+            out["bounds"] = self.bounds[: n * (self.n_seg + 1)].cpu().numpy().reshape(n, self.n_seg + 1)
+        return out
+
+
+def log_value(log_abs: float, phase) -> complex:
+    """w as a complex number (may overflow for large log|w|)."""
+    if log_abs == -math.inf:
+        return 0j
+    return complex(phase[0], phase[1]) * math.exp(log_abs)
