@@ -1,0 +1,381 @@
+"""Benchmark of the GB300 local-trace path (one JSON line on rank 0).
+
+One step = one ctq_eval_traces call over the whole batch: sector walk and
+level-0 bounds, the chain products with fused propagators, renormalisation,
+per-segment refined bounds, final traces and the per-chain combine.
+
+Default workload: the 3-orbital t2g Kanamori impurity (U=5, J=0.7, beta=50,
+16 sectors by (N_dn, N_up), blocks <= 9), 4096 seeded chains with orders
+~ Poisson(40), FP64.  `value` is evaluations/s with inputs resident in HBM;
+L2 is flushed (a 256 MiB write) between timed steps, outside the timed
+kernels.  `e2e` repeats the measurement through the same C-ABI call with the
+batch copied from pinned host memory and the results copied back inside the
+timed region.  Multi-GPU (torchrun): every rank evaluates its own batch (no
+collective on the data path; weak scaling); timing is max over ranks.
+
+--impl reference times the FP64 CPU oracle (the reference arm here) on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "local-trace evals/s and TFLOP/s vs peak, FP64 vs mixed at stated error, 1×GB300"
+WORKLOAD_TEXT = {
+    "t2g": "3-orbital t2g Kanamori (6 spin-orbitals, Fock dim 64, 16 (N_dn,N_up) sectors, blocks<=9), "
+           "U=5, J=0.7, beta=50, real FP64; 4096 chains, order ~Poisson(40), tau uniform",
+    "hubbard2": "2-orbital Kanamori (4 spin-orbitals, 9 sectors), U=4, J=0.5, mu=U/2, beta=10; 64 chains, k in 8..20",
+    "d5": "5-orbital d-shell Slater-Condon (10 spin-orbitals, 36 sectors, largest block 100), U=8, J=1, "
+          "real CF sigma=0.1, beta=40; 1024 chains, order ~Poisson(60)",
+}
+CPU_SAMPLE = {"t2g": 4096, "hubbard2": 64, "d5": 24}       # cpu_baseline leg (~5-30 s)
+CPU_SAMPLE_REF = {"t2g": 64, "hubbard2": 64, "d5": 2}      # per step of --impl reference
+FLUSH_BYTES = 256 << 20
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def algorithmic_flops(imp, batch):
+    """Real FP64-equivalent flops of the surviving strings (complex x4):
+    for each surviving (c, q0): sum_{i=1}^{n-2} 2 d_{q_{i+1}} d_{q_i} d_{q0}
+    + 2 d_{q0} d_{q_{n-1}} (the first operator only scales; the last needs only
+    a diagonal).  Host accounting from the library's sector table."""
+    dims, _, _, s = imp.sectors()
+    C = batch.n_chains
+    lens = np.diff(batch.offsets)
+    nmax = int(lens.max()) if C else 0
+    ops = np.full((C, max(nmax, 1)), -1, np.int64)
+    for c in range(C):
+        a, b = batch.offsets[c], batch.offsets[c + 1]
+        ops[c, : b - a] = batch.op[a:b]
+    total = 0.0
+    n_items = 0
+    for q0 in range(len(dims)):
+        q = np.full(C, q0, np.int64)
+        alive = np.ones(C, bool)
+        fl = np.zeros(C)
+        d0 = dims[q0]
+        for i in range(nmax):
+            act = alive & (i < lens)
+            a = np.where(act, ops[:, i], 0)
+            qn = np.where(act, s[a, np.maximum(q, 0)], q)
+            alive &= ~(act & (qn < 0))
+            qn = np.where(alive, qn, 0)
+            mid = act & alive & (i >= 1) & (i <= lens - 2)
+            fl += np.where(mid, 2.0 * dims[qn] * dims[q] * d0, 0.0)
+            last = act & alive & (i == lens - 1) & (lens >= 2)
+            fl += np.where(last, 2.0 * d0 * dims[q], 0.0)
+            q = np.where(act & alive, qn, q)
+        surv = alive & (q == q0)
+        total += float(fl[surv].sum())
+        n_items += int(surv.sum())
+    return total * (4.0 if imp.is_complex else 1.0), n_items
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def start(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def stop(self):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+        sm = [float(x[1]) for x in self.samples if x[1].replace(".", "").isdigit()]
+        mx = [float(x[2]) for x in self.samples if x[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for x in self.samples for i in range(4) if len(x) > 5 + i and "Active" in x[5 + i]
+                          and "Not" not in x[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def profile_traffic(kernel: str, workload: str, src_hash: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for line in open(p):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().split()[0] if v.strip() else ""
+    if vals.get("source_sha256", "")[:16] != src_hash[:16]:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for fn in ("trace_fp64.cu", "ctq_internal.h"):
+        with open(os.path.join(ROOT, "paper_2010_08482_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+_ORACLE_CACHE = {}
+
+
+def cpu_oracle_rate(workload: str, n_chains: int):
+    """The FP64 oracle, as it stands, on the first n_chains of the workload."""
+    from oracle import atom
+    from oracle import trace as OT
+    from paper_2010_08482_gb300 import workloads as w
+    if workload not in _ORACLE_CACHE:
+        mf, bf = w.WORKLOADS[workload]
+        _ORACLE_CACHE[workload] = (atom.Model(mf()), bf())
+    m, b = _ORACLE_CACHE[workload]
+    n = min(n_chains, b.n_chains)
+    t0 = time.perf_counter()
+    for c in range(n):
+        OT.trace_chain(m, *b.chain(c), beta=b.beta)
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float, device) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    per_step = CPU_SAMPLE_REF.get(args.workload, 8)
+    rates = []
+    for i in range(args.warmup + args.steps):
+        r, n, dt = cpu_oracle_rate(args.workload, per_step)
+        if i >= args.warmup:
+            rates.append(r)
+    value = statistics.mean(rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_step / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[args.workload], "parallelism": "host cores, 1 process"},
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {per_step} chains of the workload per step, NumPy FP64, 1 thread"},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="t2g", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    from paper_2010_08482_gb300 import ctq
+    from paper_2010_08482_gb300 import workloads as w
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mf, bf = w.WORKLOADS[args.workload]
+    params = mf()
+    batch = bf()
+    imp = ctq.build_impurity(params, device=local)
+    db = ctq.DeviceBatch(batch, device=dev)
+    ev = ctq.TraceEvaluator(imp, batch.n_chains, db.max_ops, device=dev)
+    flops, n_items = algorithmic_flops(imp, batch)
+    launches = ctq.launches_per_eval(imp)
+    stream = torch.cuda.current_stream()
+    events = [torch.cuda.Event(enable_timing=True) for _ in range(launches + 1)]
+    for e in events:
+        e.record(stream)  # materialise the cudaEvent_t handles
+    ev_handles = (ctypes_void_array(len(events)))(*[e.cuda_event for e in events])
+    import ctypes
+    ev_ptr = ctypes.cast(ev_handles, ctypes.c_void_p).value
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    for _ in range(args.warmup):
+        ev(db, events=ev_ptr)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    step_ms, kern_ms = [], [[] for _ in range(launches)]
+    for _ in range(args.steps):
+        flush.zero_()
+        ev(db, events=ev_ptr)
+        events[-1].synchronize()
+        step_ms.append(events[0].elapsed_time(events[-1]))
+        for k in range(launches):
+            kern_ms[k].append(events[k].elapsed_time(events[k + 1]))
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - t0
+
+    # end to end: pinned host batch in, results out, inside the timed region
+    h_off = torch.as_tensor(np.asarray(batch.offsets, np.int32)).pin_memory()
+    h_tau = torch.as_tensor(np.asarray(batch.tau, np.float64)).pin_memory()
+    h_op = torch.as_tensor(np.asarray(batch.op, np.int32)).pin_memory()
+    h_la = torch.empty(batch.n_chains, dtype=torch.float64).pin_memory()
+    h_ph = torch.empty(2 * batch.n_chains, dtype=torch.float64).pin_memory()
+    h_st = torch.empty(batch.n_chains, dtype=torch.int32).pin_memory()
+    e_start = torch.cuda.Event(enable_timing=True)
+    e_end = torch.cuda.Event(enable_timing=True)
+    e2e_ms = []
+    n_ops = len(batch.tau)
+    for i in range(args.warmup + max(10, args.steps // 4)):
+        flush.zero_()
+        e_start.record(stream)
+        db.offsets.copy_(h_off, non_blocking=True)
+        db.tau[:n_ops].copy_(h_tau, non_blocking=True)
+        db.op[:n_ops].copy_(h_op, non_blocking=True)
+        ev(db)
+        h_la.copy_(ev.log_abs, non_blocking=True)
+        h_ph.copy_(ev.phase, non_blocking=True)
+        h_st.copy_(ev.status, non_blocking=True)
+        e_end.record(stream)
+        e_end.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(e_start.elapsed_time(e_end))
+    clocks.stop()
+    h2d = h_off.numel() * 4 + h_tau.numel() * 8 + h_op.numel() * 4
+    d2h = h_la.numel() * 8 + h_ph.numel() * 8 + h_st.numel() * 4
+
+    ms = statistics.mean(step_ms)
+    ms = max_over_ranks(world, ms, dev)
+    e2e = max_over_ranks(world, statistics.mean(e2e_ms), dev)
+    trace_ms = statistics.mean(kern_ms[1])
+    value = world * batch.n_chains / (ms * 1e-3)
+    fp64_peak = ctq.probe_fma_rate(local, 0)
+    achieved_tf = flops / (trace_ms * 1e-3) / 1e12
+    traffic = profile_traffic("k_trace", args.workload, source_hash())
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "evals/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[args.workload], "n_chains": batch.n_chains,
+                   "surviving_strings": n_items, "precision": "fp64", "l2": "flushed (256 MiB write) between steps",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "tflops": flops / (ms * 1e-3) / 1e12,
+        "algorithmic_flops_per_step": flops,
+        "kernel_ms": {"plan": statistics.mean(kern_ms[0]), "trace": trace_ms, "combine": statistics.mean(kern_ms[2])},
+        "roofline": {"kernel": "k_trace<fp64>", "bound": "alu", "achieved": achieved_tf,
+                     "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": achieved_tf / (fp64_peak / 1e12),
+                     "peak_source": "measured FP64 FMA rate (ctq_probe_fma_rate, this run)",
+                     "traffic": traffic},
+        "e2e": {"value": world * batch.n_chains / (e2e * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps * launches,
+        "clocks": clocks.summary(),
+        "wall_s_timed_region": wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, n, dt = cpu_oracle_rate(args.workload, CPU_SAMPLE.get(args.workload, 64))
+        line["cpu_baseline"] = {"value": r, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                                "sample": f"first {n} chains of the same workload ({dt:.1f} s), NumPy FP64, 1 thread"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def ctypes_void_array(n):
+    import ctypes
+    return ctypes.c_void_p * n
+
+
+if __name__ == "__main__":
+    main()

@@ -177,6 +177,9 @@ typedef struct {
  *   (needs log_threshold).  segment: operators per bound refinement (>= 1).
  * max_ops: largest 2k in the batch (sizes the bounds output).
  * timeout_ns: limit for bounded device waits (0: library default).
+ * timing_events (nullable): ctq_launches_per_eval() + 1 cudaEvent_t handles,
+ *   recorded on `stream` before the first kernel and after each kernel, so a
+ *   caller can time every kernel of the evaluation on its launching stream.
  */
 typedef struct {
   int precision;
@@ -184,6 +187,7 @@ typedef struct {
   int segment;
   int max_ops;
   int64_t timeout_ns;
+  void* const* timing_events;
 } ctq_eval_opts;
 
 /*
@@ -225,6 +229,16 @@ int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_e
 int ctq_launches_per_eval(const ctq_impurity* imp, const ctq_eval_opts* opts);
 
 void ctq_free_impurity(ctq_impurity* imp);
+
+/*
+ * Measures the sustained fused-multiply-add rate of one arithmetic pipe on
+ * `device` (kind 0: float64, 1: float32), 8 independent FMA chains per thread,
+ * 8 CTAs of 256 threads per SM.  *flops_per_s receives 2 x FMAs / second.
+ * Allocates and frees a small device buffer; synchronises the device.
+ * No counterpart in the paper: it states the arithmetic roofline of the
+ * small-block trace.  Errors: CTQ_ERR_ARG, CTQ_ERR_NOMEM, CTQ_ERR_CUDA.
+ */
+int ctq_probe_fma_rate(int device, int kind, int iters, double* flops_per_s);
 
 const char* ctq_strerror(int code);
 

@@ -15,6 +15,7 @@ struct ctq_impurity {
   int device = -1;
   int num_sms = 0;
   ctq::DevModel dev{};
+  ctq::LaunchCfg launch{};
   std::vector<void*> allocs;
 };
 
@@ -101,6 +102,10 @@ int upload_model(ctq_impurity* imp) {
       (st = upload_vec(imp, blk, &d.blk)) || (st = upload_vec(imp, lognorm, &d.log_norm))) {
     free_device(imp);
     return fail(st, "device upload failed");
+  }
+  if ((st = ctq::prepare_eval_fp64(d, imp->num_sms, &imp->launch)) != CTQ_OK) {
+    free_device(imp);
+    return fail(st, "cannot configure the trace kernel");
   }
   return CTQ_OK;
 }
@@ -358,7 +363,7 @@ int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_e
   cfg.max_ops = opts->max_ops;
   cfg.margin = 1e-9;
   cfg.bounds = result->bounds;
-  const int st = ctq::launch_eval_fp64(imp->dev, B, cfg, W, result, imp->num_sms, stream);
+  const int st = ctq::launch_eval_fp64(imp->dev, imp->launch, B, cfg, W, result, stream, opts->timing_events);
   if (st != CTQ_OK) return fail(st, st == CTQ_ERR_CUDA ? cudaGetErrorString(cudaGetLastError()) : "launch failed");
   return CTQ_OK;
 }

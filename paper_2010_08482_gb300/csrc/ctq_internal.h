@@ -96,8 +96,19 @@ enum : int { FLAG_INVALID = 1, FLAG_REJECTED = 2 };
 
 size_t workspace_layout(int n_chains, int n_sec, int n_seg_max, void* base, Work* w);
 
+// Launch shape of the trace kernel, fixed per impurity when it is uploaded
+// (so that evaluation makes no attribute or occupancy query, e.g. while a
+// CUDA graph is being captured).
+struct LaunchCfg {
+  int threads = 0;
+  size_t smem = 0;
+  int per_sm = 0;   // resident CTAs per SM (0: shape not supported)
+  int num_sms = 0;
+};
+
 // Launchers (trace_fp64.cu).  Return a CTQ_* status.
-int launch_eval_fp64(const DevModel& M, const BatchView& B, const EvalCfg& cfg, const Work& W,
-                     const ctq_result* R, int num_sms, void* stream);
+int prepare_eval_fp64(const DevModel& M, int num_sms, LaunchCfg* lc);
+int launch_eval_fp64(const DevModel& M, const LaunchCfg& lc, const BatchView& B, const EvalCfg& cfg,
+                     const Work& W, const ctq_result* R, void* stream, void* const* events);
 
 }  // namespace ctq

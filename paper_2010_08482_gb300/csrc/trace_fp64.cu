@@ -567,43 +567,57 @@ static size_t trace_smem(int max_dim, bool cplx) {
   return 2 * size_t(max_dim) * max_dim * el + 2 * size_t(max_dim) * 8 + 64 * 8;
 }
 
-int launch_eval_fp64(const DevModel& M, const BatchView& B, const EvalCfg& cfg, const Work& W,
-                     const ctq_result* R, int num_sms, void* stream) {
+int prepare_eval_fp64(const DevModel& M, int num_sms, LaunchCfg* lc) {
+  lc->threads = trace_threads(M.max_dim);
+  lc->smem = trace_smem(M.max_dim, M.is_complex != 0);
+  lc->num_sms = num_sms;
+  lc->per_sm = 0;
+  if (lc->smem > 227 * 1024) return CTQ_OK;  // needs the large-block path
+  int per_sm = 0;
+  if (M.is_complex) {
+    if (cudaFuncSetAttribute(k_trace<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lc->smem)) !=
+        cudaSuccess)
+      return CTQ_ERR_CUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<true>, lc->threads, lc->smem) != cudaSuccess)
+      return CTQ_ERR_CUDA;
+  } else {
+    if (cudaFuncSetAttribute(k_trace<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lc->smem)) !=
+        cudaSuccess)
+      return CTQ_ERR_CUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<false>, lc->threads, lc->smem) != cudaSuccess)
+      return CTQ_ERR_CUDA;
+  }
+  lc->per_sm = per_sm;
+  return CTQ_OK;
+}
+
+int launch_eval_fp64(const DevModel& M, const LaunchCfg& lc, const BatchView& B, const EvalCfg& cfg,
+                     const Work& W, const ctq_result* R, void* stream, void* const* events) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (B.n_chains == 0) return CTQ_OK;
+  if (lc.per_sm < 1) return CTQ_ERR_UNSUPPORTED;
+  auto mark = [&](int i) {
+    if (events) cudaEventRecord(static_cast<cudaEvent_t>(events[i]), st);
+  };
   if (cudaMemsetAsync(W.counters, 0, 256, st) != cudaSuccess) return CTQ_ERR_CUDA;
+  mark(0);
   const int warps_per_block = 4;
   const int grid_c = (B.n_chains + warps_per_block - 1) / warps_per_block;
   k_plan<<<grid_c, 32 * warps_per_block, 0, st>>>(M, B, cfg, W);
   if (cudaGetLastError() != cudaSuccess) return CTQ_ERR_CUDA;
-
-  const int threads = trace_threads(M.max_dim);
-  const size_t smem = trace_smem(M.max_dim, M.is_complex != 0);
-  if (smem > 227 * 1024) return CTQ_ERR_UNSUPPORTED;
-  int per_sm = 0;
-  if (M.is_complex) {
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(k_trace<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
-      return CTQ_ERR_CUDA;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<true>, threads, smem);
-  } else {
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(k_trace<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
-      return CTQ_ERR_CUDA;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<false>, threads, smem);
-  }
-  if (per_sm < 1) return CTQ_ERR_UNSUPPORTED;
+  mark(1);
   long long max_items = (long long)B.n_chains * M.n_sec;
-  long long grid = (long long)num_sms * per_sm;
+  long long grid = (long long)lc.num_sms * lc.per_sm;
   if (grid > max_items) grid = max_items;
   if (M.is_complex)
-    k_trace<true><<<int(grid), threads, smem, st>>>(M, B, cfg, W);
+    k_trace<true><<<int(grid), lc.threads, lc.smem, st>>>(M, B, cfg, W);
   else
-    k_trace<false><<<int(grid), threads, smem, st>>>(M, B, cfg, W);
+    k_trace<false><<<int(grid), lc.threads, lc.smem, st>>>(M, B, cfg, W);
   if (cudaGetLastError() != cudaSuccess) return CTQ_ERR_CUDA;
-
+  mark(2);
   k_combine<<<grid_c, 32 * warps_per_block, 0, st>>>(M, B, cfg, W, *R);
   if (cudaGetLastError() != cudaSuccess) return CTQ_ERR_CUDA;
+  mark(3);
   return CTQ_OK;
 }
 

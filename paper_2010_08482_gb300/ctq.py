@@ -58,7 +58,7 @@ class BatchC(ctypes.Structure):
 
 class EvalOptsC(ctypes.Structure):
     _fields_ = [("precision", c_int), ("lazy", c_int), ("segment", c_int), ("max_ops", c_int),
-                ("timeout_ns", c_int64)]
+                ("timeout_ns", c_int64), ("timing_events", c_void_p)]
 
 
 class ResultC(ctypes.Structure):
@@ -83,6 +83,7 @@ def _load():
         "ctq_free_impurity": (None, [P]),
         "ctq_strerror": (c_char_p, [c_int]),
         "ctq_last_error_message": (c_char_p, []),
+        "ctq_probe_fma_rate": (c_int, [c_int, c_int, c_int, POINTER(c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -94,7 +95,15 @@ def _load():
 _lib = _load()
 EXPORTED = ("ctq_build_impurity", "ctq_load_impurity", "ctq_impurity_info", "ctq_get_sectors",
             "ctq_get_energies", "ctq_get_block", "ctq_workspace_size", "ctq_eval_traces",
-            "ctq_launches_per_eval", "ctq_free_impurity", "ctq_strerror", "ctq_last_error_message")
+            "ctq_launches_per_eval", "ctq_free_impurity", "ctq_strerror", "ctq_last_error_message",
+            "ctq_probe_fma_rate")
+
+
+def probe_fma_rate(device: int = 0, kind: int = 0, iters: int = 20000) -> float:
+    """Measured FMA throughput (flop/s) of the FP64 (kind 0) or FP32 (kind 1) pipe."""
+    out = c_double()
+    _check(_lib.ctq_probe_fma_rate(device, kind, iters, ctypes.byref(out)), "ctq_probe_fma_rate")
+    return out.value
 
 
 def lib_path() -> str:
@@ -214,9 +223,10 @@ def load_impurity(n_flav: int, dims, N, energies, s_table, blocks, mu: float = 0
     return Impurity(h)
 
 
-def _opts(precision=FP64, lazy=False, segment=8, max_ops=0, timeout_ns=0) -> EvalOptsC:
+def _opts(precision=FP64, lazy=False, segment=8, max_ops=0, timeout_ns=0, events=None) -> EvalOptsC:
     o = EvalOptsC()
     o.precision, o.lazy, o.segment, o.max_ops, o.timeout_ns = precision, int(lazy), segment, max_ops, timeout_ns
+    o.timing_events = events
     return o
 
 
@@ -232,14 +242,15 @@ def launches_per_eval(imp: Impurity, precision=FP64) -> int:
 
 def eval_traces(imp: Impurity, n_chains: int, beta: float, offsets, tau, op, log_threshold,
                 log_abs, phase, status, bounds, workspace, workspace_bytes: int, stream,
-                precision=FP64, lazy=False, segment=8, max_ops=0, timeout_ns=0):
-    """ctq_eval_traces with raw device pointers (ints) and a cudaStream_t (int)."""
+                precision=FP64, lazy=False, segment=8, max_ops=0, timeout_ns=0, events=None):
+    """ctq_eval_traces with raw device pointers (ints) and a cudaStream_t (int);
+    events: optional address of an array of cudaEvent_t handles (see ctq.h)."""
     b = BatchC()
     b.n_chains, b.beta = n_chains, beta
     b.offsets, b.tau, b.op, b.log_threshold = offsets, tau, op, log_threshold
     r = ResultC()
     r.log_abs, r.phase, r.status, r.bounds = log_abs, phase, status, bounds
-    o = _opts(precision, lazy, segment, max_ops, timeout_ns)
+    o = _opts(precision, lazy, segment, max_ops, timeout_ns, events)
     _check(_lib.ctq_eval_traces(imp.handle, ctypes.byref(b), ctypes.byref(o), ctypes.byref(r),
                                 workspace, workspace_bytes, stream), "ctq_eval_traces")
 
@@ -294,7 +305,7 @@ class TraceEvaluator:
         self.bounds = (torch.empty(n_chains * (self.n_seg + 1), dtype=torch.float64, device=device)
                        if with_bounds else None)
 
-    def __call__(self, db: DeviceBatch, lazy=False, stream=None):
+    def __call__(self, db: DeviceBatch, lazy=False, stream=None, events=None):
         import torch
         if db.n_chains > self.n_chains or db.max_ops > self.max_ops:
             raise ValueError("batch larger than the evaluator was sized for")
@@ -303,7 +314,8 @@ class TraceEvaluator:
         eval_traces(self.imp, db.n_chains, db.beta, db.offsets.data_ptr(), db.tau.data_ptr(), db.op.data_ptr(),
                     thr, self.log_abs.data_ptr(), self.phase.data_ptr(), self.status.data_ptr(),
                     self.bounds.data_ptr() if self.bounds is not None else None,
-                    self.ws_ptr, self.ws_bytes, s.cuda_stream, self.precision, lazy, self.segment, self.max_ops)
+                    self.ws_ptr, self.ws_bytes, s.cuda_stream, self.precision, lazy, self.segment, self.max_ops,
+                    0, events)
 
     def results(self, n_chains: Optional[int] = None):
         n = self.n_chains if n_chains is None else n_chains
