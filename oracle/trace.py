@@ -13,8 +13,11 @@ Definitions followed, all in float64:
   To keep e^{-tau E} representable, each propagator is applied as
   e^{-tau E_min(q)} * diag(e^{-tau (E_q,j - E_min(q))}) with the scalar factor
   kept as a float64 logarithm, and the running product is rescaled by an exact
-  power of two after every factor (the logarithm absorbs it).  Both steps are
-  exact identities; nothing else is reordered.
+  power of two after every factor (the logarithm absorbs it).  Because the
+  propagation times sum to beta, the scalar factors are accumulated relative
+  to the ground-state energy, sum dtau (E_min(q) - E_gs), with an exactly
+  rounded sum, and -beta E_gs is added once at the end.  These steps are exact
+  identities; nothing else is reordered.
 * Full-space brute force (Eq. pweight1 with Sec. 3.3.1's naive form):
   Tr[e^{-(beta - tau_n) H} O_n ... O_1 e^{-tau_1 H}] over the whole Fock space,
   with scipy.linalg.expm.
@@ -68,22 +71,30 @@ def walk(model, ops, q0: int):
 
 
 def trace_q0(model, tau, ops, q0: int, beta: float):
-    """One initial sector: returns (value, logscale, abs_value, abs_logscale)
-    with w_q0 = value * e^{logscale}; the abs_* pair is the same product taken
-    with |F| entrywise (the scale of float rounding errors)."""
+    """One initial sector: returns (value, log_rel, log_abs_product) with
+    w_q0 = value * e^{log_rel} * e^{-beta E_gs}.
+
+    The scalar factors e^{-dtau E_min(q)} are written as
+    e^{-dtau E_gs} e^{-dtau (E_min(q) - E_gs)}; the propagation times tile
+    [0, beta) (they sum to beta), so the first factors multiply to
+    e^{-beta E_gs} and only the second ones are accumulated, with math.fsum
+    (exactly rounded).  log_abs_product is the same product taken with |F|
+    entrywise (the scale of float rounding errors), in the same relative
+    convention."""
     path = walk(model, ops, q0)
     if path is None:
         return None
     n = len(ops)
-    E, Emin = model.E, model.E_min
+    E, Emin, Egs = model.E, model.E_min, model.E_gs
 
     def prop(q, dt):
-        return np.exp(-dt * (E[q] - Emin[q])), -dt * Emin[q]
+        return np.exp(-dt * (E[q] - Emin[q])), -dt * (Emin[q] - Egs)
 
-    p, L = prop(q0, tau[0] if n else beta)
+    p, l0 = prop(q0, tau[0] if n else beta)
     M = np.diag(p).astype(model_dtype(model))
     A = np.diag(p)
-    LA = L
+    logs = [l0]
+    e_sum, ea_sum = 0, 0
     for i in range(n):
         qa, qb = path[i], path[i + 1]
         Fb = model.F[(int(ops[i]), qa)]
@@ -93,20 +104,29 @@ def trace_q0(model, tau, ops, q0: int, beta: float):
         p, l = prop(qb, dt)
         M = p[:, None] * M
         A = p[:, None] * A
-        L += l
-        LA += l
-        M, e = _rescale(M)
+        logs.append(l)
+        M, e = _rescale_exp(M)
+        A, ea = _rescale_exp(A)
         if M is None:
-            return 0.0, -math.inf, _finish_abs(A, LA)
-        L += e
-        A, ea = _rescale(A)
-        LA += ea
+            return 0.0, -math.inf, _finish_abs(A, math.fsum(logs) + ea_sum * LN2)
+        e_sum += e
+        ea_sum += ea
+    L = math.fsum(logs)
     val = np.trace(M)
-    return val, L, _finish_abs(A, LA)
+    return val, L + e_sum * LN2, _finish_abs(A, L + ea_sum * LN2)
+
+
+def _rescale_exp(M: np.ndarray):
+    """Scale M by 2^-e with e = floor(log2 max|M|); return (M', e) or (None, 0)."""
+    s = float(np.max(np.abs(M))) if M.size else 0.0
+    if s == 0.0:
+        return None, 0
+    e = math.floor(math.log2(s))
+    return M * (2.0 ** -e), e
 
 
 def _finish_abs(A, LA):
-    if A is None:
+    if A is None or LA == -math.inf:
         return -math.inf
     t = float(np.trace(A))
     return math.log(t) + LA if t > 0 else -math.inf
@@ -131,10 +151,12 @@ def logsumexp_signed(terms):
 def trace_chain(model, tau, ops, beta: float | None = None):
     """w for one chain.  Returns dict(log_abs, phase, per_q0, log_cond) where
     per_q0 = {q0: (log|w_q0|, phase_q0)} over surviving q0 and log_cond is the
-    log of sum_q0 of the |F|-product traces."""
+    log of sum_q0 of the |F|-product traces.  The sum over q0 is taken in the
+    E_gs-relative log convention of trace_q0; -beta E_gs is added last."""
     beta = model.beta if beta is None else beta
     tau = np.asarray(tau, dtype=np.float64)
     ops = np.asarray(ops, dtype=np.int64)
+    shift = -beta * model.E_gs
     terms, per_q0, conds = [], {}, []
     for q0 in range(model.n_sec):
         r = trace_q0(model, tau, ops, q0, beta)
@@ -142,17 +164,17 @@ def trace_chain(model, tau, ops, beta: float | None = None):
             continue
         val, L, lc = r
         terms.append((val, L))
-        per_q0[q0] = ((math.log(abs(val)) + L) if val != 0 else -math.inf,
+        per_q0[q0] = ((math.log(abs(val)) + L + shift) if val != 0 else -math.inf,
                       (val / abs(val)) if val != 0 else 0.0)
         conds.append(lc)
     la, ph = logsumexp_signed(terms)
     finite = [c for c in conds if c != -math.inf]
     if finite:
         m = max(finite)
-        lcond = m + math.log(sum(math.exp(c - m) for c in finite))
+        lcond = m + math.log(sum(math.exp(c - m) for c in finite)) + shift
     else:
         lcond = -math.inf
-    return {"log_abs": la, "phase": ph, "per_q0": per_q0, "log_cond": lcond}
+    return {"log_abs": la + shift, "phase": ph, "per_q0": per_q0, "log_cond": lcond}
 
 
 def trace_batch(model, batch, chains=None):

@@ -80,6 +80,7 @@ int upload_model(ctq_impurity* imp) {
   d.n_sec = h.n_sec;
   d.max_dim = h.max_dim;
   d.is_complex = h.is_complex;
+  d.E_ref = h.E_gs;
   std::vector<double> e_rel(h.E.size());
   for (int q = 0; q < h.n_sec; ++q)
     for (int j = h.E_off[q]; j < h.E_off[q + 1]; ++j) e_rel[j] = h.E[j] - h.E_min[q];

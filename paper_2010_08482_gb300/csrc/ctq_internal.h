@@ -42,6 +42,7 @@ int jacobi_eigh_cplx(int n, std::vector<cplx>& A, std::vector<double>& E, std::v
 // Device-side view of a model (all pointers on the model's device).
 struct DevModel {
   int n_flav, n_alpha, n_sec, max_dim, is_complex;
+  double E_ref;         // reference energy (E_gs); logs are kept relative to -beta E_ref
   const int* dims;      // [n_sec]
   const int* E_off;     // [n_sec + 1]
   const double* E_rel;  // [sum dims]  E_q,j - E_min(q)  (>= 0)
@@ -77,7 +78,7 @@ struct Item {
   int q0;
   int r;         // min over the string of the sector dimension (rank bound)
   int n_seg;     // ceil(n / S)
-  double t_all;  // sum of log ||F_i||_2 and -dtau E_min over the string (see plan kernel)
+  double t_all;  // sum of log ||F_i||_2 and -dtau (E_min - E_ref) over the string (plan kernel)
 };
 
 // Views of the caller's workspace.
@@ -85,6 +86,7 @@ struct Work {
   int* counters;   // [0] n_items, [1] next item, [2] device error bits
   Item* items;     // [C * n_sec]
   double* res_val; // [C * n_sec * 2]  scaled trace value (re, im)
+  // All logs below are relative: the true value carries an extra e^{-beta E_ref}.
   double* res_log; // [C * n_sec]      log scale of res_val (-inf: zero)
   double* live;    // [C * n_sec]      live log upper bound per (c, q0)
   double* lvl0;    // [C * n_sec]      level-0 log bound per (c, q0)

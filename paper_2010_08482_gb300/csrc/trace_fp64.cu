@@ -20,7 +20,10 @@
 //              tau_1 scales the columns of the first block (trace cyclicity).
 //              After every product the max |Y| is reduced across the CTA and
 //              the next product absorbs the exact power-of-two rescale; the
-//              log scale (energy shifts and exponents) stays in float64.  Every
+//              log scale (energy shifts and exponents) stays in float64,
+//              relative to e^{-beta E_gs} (the propagation times sum to beta)
+//              and summed with compensation, so that log|w| ~ 10^3 loses no
+//              accuracy before the final -beta E_gs is added.  Every
 //              `segment` operators the refined bound
 //                ub = sqrt(r) ||Y||_F prod_{rest} ||F||_2 e^{-dtau E_min}
 //              is recorded and, with lazy evaluation, the chain's live bound
@@ -58,6 +61,17 @@ __device__ __forceinline__ double warp_logsumexp(double m, double s) {
   t = warp_sum(t);
   return (gm == -INFINITY || t == 0.0) ? -INFINITY : gm + log(t);
 }
+
+// Compensated (Neumaier) sum of float64 terms.
+struct KSum {
+  double s = 0.0, c = 0.0;
+  __device__ __forceinline__ void add(double x) {
+    const double t = s + x;
+    c += (fabs(s) >= fabs(x)) ? ((s - t) + x) : ((x - t) + s);
+    s = t;
+  }
+  __device__ __forceinline__ double val() const { return s + c; }
+};
 
 // ----------------------------------------------------------------------- plan
 
@@ -101,14 +115,14 @@ __global__ void k_plan(DevModel M, BatchView B, EvalCfg cfg, Work W) {
       q = M.s[idx];
       if (q < 0) { alive = false; break; }
       r = min(r, M.dims[q]);
-      if (i + 1 < n) lb -= (B.tau[a0 + i + 1] - B.tau[a0 + i]) * M.E_min[q];
+      if (i + 1 < n) lb -= (B.tau[a0 + i + 1] - B.tau[a0 + i]) * (M.E_min[q] - M.E_ref);
     }
     alive = alive && (q == q0);
     const size_t slot = size_t(c) * ns + q0;
     double b = -INFINITY;
     if (alive) {
-      b = (n == 0) ? (log(double(M.dims[q0])) - B.beta * M.E_min[q0])
-                   : (log(double(r)) - t_wrap * M.E_min[q0] + lb);
+      b = (n == 0) ? (log(double(M.dims[q0])) - B.beta * (M.E_min[q0] - M.E_ref))
+                   : (log(double(r)) - t_wrap * (M.E_min[q0] - M.E_ref) + lb);
       Item it;
       it.c = c;
       it.q0 = q0;
@@ -130,10 +144,11 @@ __global__ void k_plan(DevModel M, BatchView B, EvalCfg cfg, Work W) {
       ls += exp(b - lm);
     }
   }
-  const double logB = warp_logsumexp(lm, ls);
-  if (cfg.bounds && lane == 0) cfg.bounds[size_t(c) * (cfg.n_seg_max + 1)] = logB;
+  const double logB = warp_logsumexp(lm, ls);  // relative to -beta E_ref
+  const double shift = -B.beta * M.E_ref;
+  if (cfg.bounds && lane == 0) cfg.bounds[size_t(c) * (cfg.n_seg_max + 1)] = logB + shift;
   bool reject = false;
-  if (cfg.lazy && logB != -INFINITY) reject = (logB + cfg.margin < B.log_threshold[c]);
+  if (cfg.lazy && logB != -INFINITY) reject = (logB + cfg.margin < B.log_threshold[c] - shift);
   if (lane == 0) W.chain_flag[c] = reject ? FLAG_REJECTED : 0;
   if (reject) return;
   // append the surviving strings (warp-aggregated atomic)
@@ -244,16 +259,18 @@ __global__ void __launch_bounds__(256) k_trace(DevModel M, BatchView B, EvalCfg 
       for (int j = tid; j < d0; j += nt) sm += exp(-B.beta * E0[j]);
       block_max_sum(mx, sm, red);
       if (tid == 0) {
+        const double l = -B.beta * (M.E_min[q0] - M.E_ref);
         W.res_val[2 * slot] = sm;
         W.res_val[2 * slot + 1] = 0.0;
-        W.res_log[slot] = -B.beta * M.E_min[q0];
-        if (track) segp[0] = log(sm) - B.beta * M.E_min[q0];
+        W.res_log[slot] = l;
+        if (track) segp[0] = log(sm) + l;
       }
       continue;
     }
 
     const double t_wrap = B.beta - B.tau[a0 + n - 1] + B.tau[a0];
-    double L = -t_wrap * M.E_min[q0];  // log scale (energy shifts)
+    KSum L;                            // log scale (energy shifts, relative to E_ref)
+    L.add(-t_wrap * (M.E_min[q0] - M.E_ref));
     long long Eacc = 0;                // power-of-two exponent: true = stored * 2^Eacc
     for (int j = tid; j < d0; j += nt) p0[j] = exp(-t_wrap * E0[j]);
 
@@ -278,8 +295,8 @@ __global__ void __launch_bounds__(256) k_trace(DevModel M, BatchView B, EvalCfg 
         const bool zero_v = (vr == 0.0 && vi == 0.0);
         W.res_val[2 * slot] = vr;
         W.res_val[2 * slot + 1] = vi;
-        W.res_log[slot] = zero_v ? -INFINITY : L;
-        if (track) segp[it.n_seg] = zero_v ? -INFINITY : log(sqrt(vr * vr + vi * vi)) + L;
+        W.res_log[slot] = zero_v ? -INFINITY : L.val();
+        if (track) segp[it.n_seg] = zero_v ? -INFINITY : log(sqrt(vr * vr + vi * vi)) + L.val();
       }
       continue;
     }
@@ -294,8 +311,8 @@ __global__ void __launch_bounds__(256) k_trace(DevModel M, BatchView B, EvalCfg 
       const double* Eb = M.E_rel + M.E_off[qb];
       const int db = M.dims[qb];
       for (int m = tid; m < db; m += nt) p[m] = exp(-dt * Eb[m]);
-      L -= dt * M.E_min[qb];
-      prefix -= dt * M.E_min[qb];
+      L.add(-dt * (M.E_min[qb] - M.E_ref));
+      prefix -= dt * (M.E_min[qb] - M.E_ref);
     }
     __syncthreads();
     T* Y = Ybuf0;
@@ -326,7 +343,7 @@ __global__ void __launch_bounds__(256) k_trace(DevModel M, BatchView B, EvalCfg 
       if (mx == 0.0) { dead = true; break; }
       int e = ilogb(mx);
       if (track && applied % cfg.S == 0 && applied < n) {
-        const double ub = 0.5 * log(double(it.r)) + 0.5 * log(fr) + double(Eacc) * LN2 + L +
+        const double ub = 0.5 * log(double(it.r)) + 0.5 * log(fr) + double(Eacc) * LN2 + L.val() +
                           (it.t_all - prefix);
         if (tid == 0) {
           segp[applied / cfg.S] = ub;
@@ -347,7 +364,7 @@ __global__ void __launch_bounds__(256) k_trace(DevModel M, BatchView B, EvalCfg 
             const double lub = warp_logsumexp(lm, lsum);
             if (tid == 0) {
               int flag = atomicAdd(&W.chain_flag[c], 0);
-              if (!(flag & FLAG_REJECTED) && lub + cfg.margin < B.log_threshold[c]) {
+              if (!(flag & FLAG_REJECTED) && lub + cfg.margin < B.log_threshold[c] + B.beta * M.E_ref) {
                 atomicOr(&W.chain_flag[c], FLAG_REJECTED);
                 flag |= FLAG_REJECTED;
               }
@@ -391,10 +408,10 @@ __global__ void __launch_bounds__(256) k_trace(DevModel M, BatchView B, EvalCfg 
           W.res_val[2 * slot] = vr * scale;
           W.res_val[2 * slot + 1] = vi * scale;
           const bool zero_v = (vr == 0.0 && vi == 0.0);
-          W.res_log[slot] = zero_v ? -INFINITY : L + double(Eacc) * LN2;
+          W.res_log[slot] = zero_v ? -INFINITY : L.val() + double(Eacc) * LN2;
           if (track) {
             const double a = sqrt(vr * vr + vi * vi) * scale;
-            segp[it.n_seg] = zero_v ? -INFINITY : log(a) + L + double(Eacc) * LN2;
+            segp[it.n_seg] = zero_v ? -INFINITY : log(a) + L.val() + double(Eacc) * LN2;
           }
         }
         applied = n;
@@ -405,8 +422,8 @@ __global__ void __launch_bounds__(256) k_trace(DevModel M, BatchView B, EvalCfg 
       const double* Eb = M.E_rel + M.E_off[qb];
       const int db = M.dims[qb];
       for (int m = tid; m < db; m += nt) p[m] = exp(-dt * Eb[m]) * scale;
-      L -= dt * M.E_min[qb];
-      prefix -= dt * M.E_min[qb];
+      L.add(-dt * (M.E_min[qb] - M.E_ref));
+      prefix -= dt * (M.E_min[qb] - M.E_ref);
       __syncthreads();
       // Yn[m][j] = p[m] * sum_k F[m][k] Y[k][j]
       mx = 0.0;
@@ -488,6 +505,7 @@ __global__ void k_combine(DevModel M, BatchView B, EvalCfg cfg, Work W, ctq_resu
   sr = warp_sum(sr);
   si = warp_sum(si);
   const double a = hypot(sr, si);
+  const double shift = -B.beta * M.E_ref;  // logs above are relative to e^{-beta E_ref}
   if (lane == 0) {
     int st = CTQ_CHAIN_OK;
     if (lm == -INFINITY || a == 0.0) {
@@ -496,7 +514,7 @@ __global__ void k_combine(DevModel M, BatchView B, EvalCfg cfg, Work W, ctq_resu
       R.phase[2 * c + 1] = 0.0;
       st = CTQ_CHAIN_ZERO;
     } else {
-      const double la = lm + log(a);
+      const double la = (lm + log(a)) + shift;
       R.log_abs[c] = la;
       R.phase[2 * c] = sr / a;
       R.phase[2 * c + 1] = si / a;
@@ -518,7 +536,7 @@ __global__ void k_combine(DevModel M, BatchView B, EvalCfg cfg, Work W, ctq_resu
         else if (v != -INFINITY) s2 += exp(v - m2);
       }
       const double lb = warp_logsumexp(m2, s2);
-      if (lane == 0) cfg.bounds[size_t(c) * nb + s] = lb;
+      if (lane == 0) cfg.bounds[size_t(c) * nb + s] = lb + shift;
     }
   }
 }

@@ -96,6 +96,7 @@ class _LibModel:
         self.dims = [int(d) for d in dims]
         self.E = [imp.energies(q) for q in range(self.n_sec)]
         self.E_min = np.asarray([e[0] for e in self.E])
+        self.E_gs = float(self.E_min.min())
         self.s = s.astype(np.int64)
         self.is_complex = imp.is_complex
         self.beta = beta
