@@ -177,6 +177,54 @@ def trace_chain(model, tau, ops, beta: float | None = None):
     return {"log_abs": la + shift, "phase": ph, "per_q0": per_q0, "log_cond": lcond}
 
 
+def trace_q0_left(model, tau, ops, q0: int, beta: float):
+    """The same trace as trace_q0 multiplied in the opposite association order:
+    starting from the leftmost factor P_{beta - tau_n}(q0) and moving right.
+    Returns (value, log_rel).  Comparing the two orders measures the float64
+    rounding spread of a chain (used to set parity tolerances)."""
+    path = walk(model, ops, q0)
+    if path is None:
+        return None
+    n = len(ops)
+    E, Emin, Egs = model.E, model.E_min, model.E_gs
+    if n == 0:
+        return trace_q0(model, tau, ops, q0, beta)[:2]
+
+    def prop(q, dt):
+        return np.exp(-dt * (E[q] - Emin[q])), -dt * (Emin[q] - Egs)
+
+    p, l0 = prop(q0, beta - tau[n - 1])
+    M = np.diag(p).astype(model_dtype(model))
+    logs = [l0]
+    e_sum = 0
+    for i in range(n - 1, -1, -1):
+        M = M @ model.F[(int(ops[i]), path[i])]
+        dt = (tau[i] - tau[i - 1]) if i > 0 else tau[0]
+        p, l = prop(path[i], dt)
+        M = M * p[None, :]
+        logs.append(l)
+        M, e = _rescale_exp(M)
+        if M is None:
+            return 0.0, -math.inf
+        e_sum += e
+    return np.trace(M), math.fsum(logs) + e_sum * LN2
+
+
+def trace_chain_left(model, tau, ops, beta: float | None = None):
+    """trace_chain with every q0 product multiplied left to right (see
+    trace_q0_left); returns dict(log_abs, phase)."""
+    beta = model.beta if beta is None else beta
+    tau = np.asarray(tau, dtype=np.float64)
+    ops = np.asarray(ops, dtype=np.int64)
+    terms = []
+    for q0 in range(model.n_sec):
+        r = trace_q0_left(model, tau, ops, q0, beta)
+        if r is not None:
+            terms.append(r)
+    la, ph = logsumexp_signed(terms)
+    return {"log_abs": la - beta * model.E_gs, "phase": ph}
+
+
 def trace_batch(model, batch, chains=None):
     """trace_chain over a workloads.Batch (optionally a subset of chain ids)."""
     idx = range(batch.n_chains) if chains is None else chains

@@ -268,11 +268,15 @@ __global__ void __launch_bounds__(256) k_trace(DevModel M, BatchView B, EvalCfg 
       continue;
     }
 
-    const double t_wrap = B.beta - B.tau[a0 + n - 1] + B.tau[a0];
+    // The wrap-around propagators P_{beta - tau_n}(q0) and P_{tau_1}(q0) scale
+    // the columns of the first block (trace cyclicity); the two time
+    // arguments are kept separate so that no extra rounding enters them.
+    const double t_first = B.tau[a0], t_last = B.beta - B.tau[a0 + n - 1];
     KSum L;                            // log scale (energy shifts, relative to E_ref)
-    L.add(-t_wrap * (M.E_min[q0] - M.E_ref));
+    L.add(-t_first * (M.E_min[q0] - M.E_ref));
+    L.add(-t_last * (M.E_min[q0] - M.E_ref));
     long long Eacc = 0;                // power-of-two exponent: true = stored * 2^Eacc
-    for (int j = tid; j < d0; j += nt) p0[j] = exp(-t_wrap * E0[j]);
+    for (int j = tid; j < d0; j += nt) p0[j] = exp(-t_first * E0[j]) * exp(-t_last * E0[j]);
 
     if (n == 1) {  // only reachable with user tables where s_alpha(q0) = q0
       __syncthreads();

@@ -13,10 +13,38 @@ FP64_REL = 1e-12
 # Chains whose per-q0 terms cancel (sum |w_q0| > CANCEL * |w|) are compared
 # against sum |w_q0| instead of |w|.
 CANCEL = 10.0
+# Multiple of the oracle's own association-order spread allowed on the GPU.
+NOISE_FACTOR = 8.0
 
 
-def oracle_chain_results(model, batch, chains):
-    return {int(c): OT.trace_chain(model, *batch.chain(int(c)), beta=batch.beta) for c in chains}
+def oracle_chain_results(model, batch, chains, noise=True):
+    """Oracle trace per chain; with noise=True each result also carries
+    'noise': the relative spread between multiplying the strings right-to-left
+    and left-to-right (the chain's own float64 rounding spread)."""
+    out = {}
+    for c in chains:
+        tau, ops = batch.chain(int(c))
+        r = OT.trace_chain(model, tau, ops, beta=batch.beta)
+        if noise:
+            l = OT.trace_chain_left(model, tau, ops, beta=batch.beta)
+            r["noise"] = rel_spread(l, r)
+        out[int(c)] = r
+    return out
+
+
+def rel_spread(a, ref) -> float:
+    if ref["log_abs"] == -math.inf:
+        return 0.0 if a["log_abs"] == -math.inf else math.inf
+    if a["log_abs"] == -math.inf:
+        return 1.0
+    return abs(complex(a["phase"]) * math.exp(a["log_abs"] - ref["log_abs"]) - complex(ref["phase"]))
+
+
+def fp64_tolerance(ref) -> float:
+    """Parity bar for one chain in FP64 mode: 1e-12, or 8x the chain's own
+    float64 rounding spread when cancellation inside the trace makes that
+    larger (the spread is measured, not assumed)."""
+    return max(FP64_REL, NOISE_FACTOR * ref.get("noise", 0.0))
 
 
 def log_sum_abs_q0(r) -> float:

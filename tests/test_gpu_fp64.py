@@ -3,8 +3,11 @@
 Bar (FP64 mode): |w_gpu - w_oracle| / |w_oracle| <= 1e-12 with the sign
 identical, on the oracle's own eigenbasis (ctq_load_impurity), so that only
 the GPU arithmetic is compared.  Chains whose q0 terms cancel by more than
-10x are measured against sum_q0 |w_q0|.  The impurity built by the library's
-own eigensolver (ctq_build_impurity) is compared at the tolerance its
+10x are measured against sum_q0 |w_q0|; chains whose trace cancels
+internally (e.g. exact zeros by symmetry computed as rounding noise) are
+held to 8x the oracle's own rounding spread, measured per chain by
+multiplying the same string in the opposite association order.  The
+impurity built by the library's own eigensolver (ctq_build_impurity) is compared at the tolerance its
 eigenvalue differences allow: |d log w| <= beta * max|dE| (the trace's
 sensitivity to energies) plus the 1e-12 arithmetic bar.
 """
@@ -42,17 +45,20 @@ def full_batch(name):
 
 
 def assert_parity(res, ref, chains, tol=parity.FP64_REL, is_complex=False):
+    """Per chain: error <= max(tol, 8 x the oracle's own association spread)."""
     worst = 0.0
     for i, c in enumerate(chains):
         r = ref[int(c)]
         err, kind = parity.chain_error(res["log_abs"][i], res["phase"][i], r)
         worst = max(worst, err)
-        assert err <= tol, (int(c), err, kind)
+        t = max(tol, parity.fp64_tolerance(r))
+        assert err <= t, (int(c), err, kind, r.get("noise"))
         if r["log_abs"] == -math.inf:
             assert res["status"][i] == ctq.CHAIN_ZERO
             continue
         assert res["status"][i] == ctq.CHAIN_OK
-        if kind == "abs" and not is_complex:
+        if kind == "abs" and not is_complex and r.get("noise", 0.0) <= parity.FP64_REL:
+            # well-conditioned chain: the sign must agree exactly
             assert res["phase"][i][0] == np.sign(np.real(r["phase"])) and res["phase"][i][1] == 0.0
     return worst
 
@@ -156,7 +162,7 @@ def test_lazy_decisions_equal_exact_decisions(name, n, models):
         elif st[c] == ctq.CHAIN_ACCEPTED:
             assert exact_accept
             err, _ = parity.chain_error(res["log_abs"][c], res["phase"][c], ref[c])
-            assert err <= parity.FP64_REL
+            assert err <= parity.fp64_tolerance(ref[c])
         else:
             assert st[c] == ctq.CHAIN_REJECTED and not exact_accept
         if kind[c] == 0:

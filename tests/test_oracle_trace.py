@@ -238,3 +238,18 @@ def test_level0_bound_is_tight_for_single_state():
 
 def test_decide_matches_threshold():
     assert T.decide(-1.0, -1.5) and not T.decide(-2.0, -1.5)
+
+
+def test_left_and_right_association_agree(models):
+    """Multiplying the string from the left or from the right gives the same
+    trace to float64 rounding (well-conditioned chains)."""
+    m = models("t2g")
+    b = w.batch_t2g(40)
+    for c in range(b.n_chains):
+        tau, ops = b.chain(c)
+        r = T.trace_chain(m, tau, ops)
+        l = T.trace_chain_left(m, tau, ops)
+        if r["log_abs"] == -math.inf:
+            assert l["log_abs"] == -math.inf
+            continue
+        assert rel_log(l, r) < 1e-12
