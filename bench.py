@@ -258,7 +258,7 @@ def main():
     dev = torch.device("cuda", local)
     mf, bf = w.WORKLOADS[args.workload]
     params = mf()
-    batch = bf()
+    batch = bf(rank=rank)  # each rank evaluates its own independent batch (weak scaling)
     imp = ctq.build_impurity(params, device=local)
     db = ctq.DeviceBatch(batch, device=dev)
     ev = ctq.TraceEvaluator(imp, batch.n_chains, db.max_ops, device=dev)

@@ -14,7 +14,8 @@ Plain float64 construction of
 * spin-orbit coupling xi l.s and a crystal field as extra one-body terms;
 * the sector decomposition H = (+)_q H(q) by abelian quantum numbers
   (Sec. 3.3.1), an optional window on N (basis truncation), numpy.linalg.eigh
-  per sector, the sector map s_alpha(q) and the operator blocks
+  per sector (per connected component of the sector's nonzero pattern, so
+  that exact zeros stay exact), the sector map s_alpha(q) and the operator blocks
   [F_alpha(q)]_{mn} = <m(q')| c_alpha |n(q)> in the eigenbasis.
 
 Matrix-element reading: the paper prints (F_i)_{nm} = <m|c_i|n>; the oracle
@@ -328,6 +329,44 @@ def sector_hamiltonian(states: np.ndarray, terms) -> np.ndarray:
     return H
 
 
+def eigh_by_components(h: np.ndarray):
+    """Eigen-decomposition of a Hermitian sector Hamiltonian.
+
+    H restricted to a sector is still block-diagonal over the connected
+    components of its nonzero pattern (states that no chain of nonzero matrix
+    elements links are never mixed by H).  numpy.linalg.eigh is applied to each
+    component on its own, so eigenvectors have exact zeros outside their
+    component and strings that such a hidden symmetry forbids give exactly 0
+    instead of rounding noise.  Returns (E ascending, V columns)."""
+    d = h.shape[0]
+    adj = h != 0
+    comp = -np.ones(d, dtype=np.int64)
+    n_comp = 0
+    for start in range(d):
+        if comp[start] >= 0:
+            continue
+        stack = [start]
+        comp[start] = n_comp
+        while stack:
+            i = stack.pop()
+            for j in np.nonzero(adj[i])[0]:
+                if comp[j] < 0:
+                    comp[j] = n_comp
+                    stack.append(j)
+        n_comp += 1
+    E = np.zeros(d)
+    V = np.zeros((d, d), dtype=h.dtype)
+    col = 0
+    for k in range(n_comp):
+        idx = np.nonzero(comp == k)[0]
+        e, v = np.linalg.eigh(h[np.ix_(idx, idx)])
+        E[col:col + len(idx)] = e
+        V[idx, col:col + len(idx)] = v
+        col += len(idx)
+    order = np.argsort(E, kind="stable")
+    return E[order], V[:, order]
+
+
 class Model:
     """Sector-decomposed impurity in its eigenbasis.
 
@@ -348,10 +387,7 @@ class Model:
         self.is_complex = any(np.abs(h.imag).max() > 0.0 for h in H0)
         E0, self.V = [], []
         for h in H0:
-            if self.is_complex:
-                e, v = np.linalg.eigh(h)
-            else:
-                e, v = np.linalg.eigh(h.real)
+            e, v = eigh_by_components(h if self.is_complex else h.real)
             E0.append(e)
             self.V.append(v)
         if p.mu is None:

@@ -1,0 +1,231 @@
+// Plan and combine kernels of the local-trace evaluation (every precision).
+//
+//   k_plan     one warp per chain.  Validates the sequence, follows the sector
+//              map s_alpha(q) for every q0 without any matrix work (Sec. 3.3.1,
+//              the string q0 -> q1 -> ... must return to q0 and never visit the
+//              zero sector), computes the level-0 lazy bound per surviving q0
+//                b(q0) = r * prod ||F_i||_2 * prod e^{-dtau E_min(q)}
+//              (Sec. 3.3.1, lazy-trace paragraph: submultiplicative norms, the
+//              spectral norm of a propagator is e^{-dtau E_min}), decides an
+//              early reject when log sum_q0 b < T, and appends the surviving
+//              (chain, q0) strings to the work list.
+//   k_combine  one warp per chain: w = sum_q0 w_q0 in log space with sign or
+//              phase (Sec. 3.1.4, Eqs. PSignRewrite / Sign: the sampled weight is
+//              |w| with phase w/|w|), the Metropolis decision (App. B, Eq.
+//              decide) and the per-segment chain bounds.
+#include "device_common.cuh"
+
+namespace ctq {
+
+using namespace dev;
+
+// ----------------------------------------------------------------------- plan
+
+__global__ void k_plan(DevModel M, BatchView B, EvalCfg cfg, Work W) {
+  const int lane = threadIdx.x & 31;
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (c >= B.n_chains) return;
+  const int a0 = B.offsets[c];
+  const int n = B.offsets[c + 1] - a0;
+  const int ns = M.n_sec;
+
+  bool bad = n < 0 || n > cfg.max_ops;
+  for (int i = lane; !bad && i < n; i += 32) {
+    const int alpha = B.op[a0 + i];
+    const double t = B.tau[a0 + i];
+    if (alpha < 0 || alpha >= M.n_alpha || !(t >= 0.0) || !(t < B.beta)) bad = true;
+    if (i > 0 && !(t > B.tau[a0 + i - 1])) bad = true;
+  }
+  bad = __any_sync(FULL, bad);
+  if (bad) {
+    for (int q0 = lane; q0 < ns; q0 += 32) {
+      W.lvl0[size_t(c) * ns + q0] = -INFINITY;
+      W.live[size_t(c) * ns + q0] = -INFINITY;
+      W.res_log[size_t(c) * ns + q0] = -INFINITY;
+    }
+    if (lane == 0) W.chain_flag[c] = FLAG_INVALID;
+    return;
+  }
+  const double t_wrap = (n > 0) ? (B.beta - B.tau[a0 + n - 1] + B.tau[a0]) : B.beta;
+
+  // walk every q0 (lanes stride over sectors)
+  double lm = -INFINITY, ls = 0.0;  // running logsumexp of b over this lane's q0
+  for (int q0 = lane; q0 < ns; q0 += 32) {
+    int q = q0, r = M.dims[q0];
+    double lb = 0.0;
+    bool alive = true;
+    for (int i = 0; i < n; ++i) {
+      const int alpha = B.op[a0 + i];
+      const int idx = alpha * ns + q;
+      lb += M.log_norm[idx];
+      q = M.s[idx];
+      if (q < 0) { alive = false; break; }
+      r = min(r, M.dims[q]);
+      if (i + 1 < n) lb -= (B.tau[a0 + i + 1] - B.tau[a0 + i]) * (M.E_min[q] - M.E_ref);
+    }
+    alive = alive && (q == q0);
+    const size_t slot = size_t(c) * ns + q0;
+    double b = -INFINITY;
+    if (alive) {
+      b = (n == 0) ? (log(double(M.dims[q0])) - B.beta * (M.E_min[q0] - M.E_ref))
+                   : (log(double(r)) - t_wrap * (M.E_min[q0] - M.E_ref) + lb);
+      Item it;
+      it.c = c;
+      it.q0 = q0;
+      it.r = r;
+      it.n_seg = (n + cfg.S - 1) / cfg.S;
+      it.t_all = lb;
+      // the item is appended below unless the chain is rejected at level 0
+      W.items[slot] = it;  // staging copy in the (c, q0) slot
+    }
+    W.lvl0[slot] = b;
+    W.live[slot] = b;
+    W.res_log[slot] = -INFINITY;
+    W.res_val[2 * slot] = 0.0;
+    W.res_val[2 * slot + 1] = 0.0;
+    if (b > lm) {
+      ls = ls * exp(lm - b) + 1.0;
+      lm = b;
+    } else if (b != -INFINITY) {
+      ls += exp(b - lm);
+    }
+  }
+  const double logB = warp_logsumexp(lm, ls);  // relative to -beta E_ref
+  const double shift = -B.beta * M.E_ref;
+  if (cfg.bounds && lane == 0) cfg.bounds[size_t(c) * (cfg.n_seg_max + 1)] = logB + shift;
+  bool reject = false;
+  if (cfg.lazy && logB != -INFINITY) reject = (logB + cfg.margin < B.log_threshold[c] - shift);
+  if (lane == 0) W.chain_flag[c] = reject ? FLAG_REJECTED : 0;
+  if (reject) return;
+  // append the surviving strings (warp-aggregated atomic)
+  for (int base = 0; base < ns; base += 32) {
+    const int q0 = base + lane;
+    const bool alive = q0 < ns && W.lvl0[size_t(c) * ns + q0] != -INFINITY;
+    const unsigned mask = __ballot_sync(FULL, alive);
+    if (!mask) continue;
+    int first = 0;
+    if (lane == 0) first = atomicAdd(&W.counters[0], __popc(mask));
+    first = __shfl_sync(FULL, first, 0);
+    if (alive) {
+      const int pos = first + __popc(mask & ((1u << lane) - 1u));
+      // items[pos] may alias a staging slot of another chain that is already
+      // consumed: staging copies live in a separate region (see Work).
+      W.items[size_t(B.n_chains) * ns + pos] = W.items[size_t(c) * ns + q0];
+    }
+  }
+}
+
+// ----------------------------------------------------------------------- combine
+
+__global__ void k_combine(DevModel M, BatchView B, EvalCfg cfg, Work W, ctq_result R) {
+  const int lane = threadIdx.x & 31;
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (c >= B.n_chains) return;
+  const int ns = M.n_sec;
+  const int flag = W.chain_flag[c];
+  const int nb = cfg.n_seg_max + 1;
+  if (flag & (FLAG_INVALID | FLAG_REJECTED)) {
+    if (lane == 0) {
+      R.log_abs[c] = NAN;
+      R.phase[2 * c] = 0.0;
+      R.phase[2 * c + 1] = 0.0;
+      R.status[c] = (flag & FLAG_INVALID) ? CTQ_CHAIN_ERR_ARG : CTQ_CHAIN_REJECTED_EARLY;
+    }
+    if (cfg.bounds)
+      for (int s = lane; s < nb; s += 32)
+        if (s > 0 || (flag & FLAG_INVALID)) cfg.bounds[size_t(c) * nb + s] = NAN;
+    return;
+  }
+  // sum_q0 w_q0 = sum val * e^{log}, with a common max log
+  double lm = -INFINITY;
+  for (int q = lane; q < ns; q += 32) {
+    const size_t slot = size_t(c) * ns + q;
+    const double lg = W.res_log[slot];
+    if (lg == -INFINITY) continue;
+    const double a = hypot(W.res_val[2 * slot], W.res_val[2 * slot + 1]);
+    if (a > 0.0) lm = fmax(lm, lg + log(a));
+  }
+  lm = warp_max(lm);
+  double sr = 0.0, si = 0.0;
+  if (lm != -INFINITY) {
+    for (int q = lane; q < ns; q += 32) {
+      const size_t slot = size_t(c) * ns + q;
+      const double lg = W.res_log[slot];
+      if (lg == -INFINITY) continue;
+      const double f = exp(lg - lm);
+      sr += W.res_val[2 * slot] * f;
+      si += W.res_val[2 * slot + 1] * f;
+    }
+  }
+  sr = warp_sum(sr);
+  si = warp_sum(si);
+  const double a = hypot(sr, si);
+  const double shift = -B.beta * M.E_ref;  // logs above are relative to e^{-beta E_ref}
+  if (lane == 0) {
+    int st = CTQ_CHAIN_OK;
+    if (lm == -INFINITY || a == 0.0) {
+      R.log_abs[c] = -INFINITY;
+      R.phase[2 * c] = 0.0;
+      R.phase[2 * c + 1] = 0.0;
+      st = CTQ_CHAIN_ZERO;
+    } else {
+      const double la = (lm + log(a)) + shift;
+      R.log_abs[c] = la;
+      R.phase[2 * c] = sr / a;
+      R.phase[2 * c + 1] = si / a;
+      if (cfg.has_thr) st = (la >= B.log_threshold[c]) ? CTQ_CHAIN_ACCEPTED : CTQ_CHAIN_REJECTED;
+    }
+    R.status[c] = st;
+  }
+  if (cfg.bounds) {
+    for (int s = 1; s < nb; ++s) {
+      double m2 = -INFINITY, s2 = 0.0;
+      for (int q = lane; q < ns; q += 32) {
+        const size_t slot = size_t(c) * ns + q;
+        if (W.lvl0[slot] == -INFINITY) continue;
+        // items finish at their own last segment; later columns repeat the exact value
+        const int n = B.offsets[c + 1] - B.offsets[c];
+        const int nseg = (n + cfg.S - 1) / cfg.S;
+        const double v = W.seg[slot * size_t(nb) + min(s, nseg)];
+        if (v > m2) { s2 = s2 * exp(m2 - v) + 1.0; m2 = v; }
+        else if (v != -INFINITY) s2 += exp(v - m2);
+      }
+      const double lb = warp_logsumexp(m2, s2);
+      if (lane == 0) cfg.bounds[size_t(c) * nb + s] = lb + shift;
+    }
+  }
+}
+
+
+size_t workspace_layout(int n_chains, int n_sec, int n_seg_max, void* base, Work* w) {
+  auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t cs = size_t(n_chains) * n_sec;
+  size_t off = 0;
+  char* b = static_cast<char*>(base);
+  auto take = [&](size_t bytes) {
+    char* p = b ? b + off : nullptr;
+    off += align(bytes);
+    return p;
+  };
+  char* counters = take(256);
+  char* items = take(2 * cs * sizeof(Item));  // staging slots + compacted list
+  char* res_val = take(2 * cs * sizeof(double));
+  char* res_log = take(cs * sizeof(double));
+  char* live = take(cs * sizeof(double));
+  char* lvl0 = take(cs * sizeof(double));
+  char* seg = take(cs * size_t(n_seg_max + 1) * sizeof(double));
+  char* flags = take(size_t(n_chains) * sizeof(int));
+  if (w) {
+    w->counters = reinterpret_cast<int*>(counters);
+    w->items = reinterpret_cast<Item*>(items);
+    w->res_val = reinterpret_cast<double*>(res_val);
+    w->res_log = reinterpret_cast<double*>(res_log);
+    w->live = reinterpret_cast<double*>(live);
+    w->lvl0 = reinterpret_cast<double*>(lvl0);
+    w->seg = reinterpret_cast<double*>(seg);
+    w->chain_flag = reinterpret_cast<int*>(flags);
+  }
+  return off;
+}
+
+}  // namespace ctq

@@ -262,33 +262,34 @@ def _pack(chains, beta, model=None) -> Batch:
                  op=op, model=None if model is None else np.asarray(model, dtype=np.int32))
 
 
-def batch_hubbard2(n_chains: int = 64) -> Batch:
-    """64 chains, k ~ U{8..20}, G1."""
-    rng = np.random.default_rng(SEED_BASE + 1)
+def batch_hubbard2(n_chains: int = 64, rank: int = 0) -> Batch:
+    """64 chains, k ~ U{8..20}, G1.  rank > 0 draws an independent batch of the
+    same shape (one per process in multi-GPU runs)."""
+    rng = np.random.default_rng(SEED_BASE + 1 + 1000 * rank)
     m = model_hubbard2()
     chains = [g1_chain(rng, m.n_flav, int(rng.integers(8, 21)), m.beta) for _ in range(n_chains)]
     return _pack(chains, m.beta)
 
 
-def batch_t2g(n_chains: int = 4096) -> Batch:
-    """4096 chains, k ~ Poisson(40), G1."""
-    rng = np.random.default_rng(SEED_BASE + 2)
+def batch_t2g(n_chains: int = 4096, rank: int = 0) -> Batch:
+    """4096 chains, k ~ Poisson(40), G1 (rank: see batch_hubbard2)."""
+    rng = np.random.default_rng(SEED_BASE + 2 + 1000 * rank)
     m = model_t2g()
     chains = [g1_chain(rng, m.n_flav, int(rng.poisson(40)), m.beta) for _ in range(n_chains)]
     return _pack(chains, m.beta)
 
 
-def batch_d5(n_chains: int = 1024) -> Batch:
-    """1024 chains, k ~ Poisson(60), G1."""
-    rng = np.random.default_rng(SEED_BASE + 3)
+def batch_d5(n_chains: int = 1024, rank: int = 0) -> Batch:
+    """1024 chains, k ~ Poisson(60), G1 (rank: see batch_hubbard2)."""
+    rng = np.random.default_rng(SEED_BASE + 3 + 1000 * rank)
     m = model_d5()
     chains = [g1_chain(rng, m.n_flav, int(rng.poisson(60)), m.beta) for _ in range(n_chains)]
     return _pack(chains, m.beta)
 
 
-def batch_f7(n_chains: int = 256) -> Batch:
-    """256 chains, k ~ Poisson(80), G2 (width-2 N walk)."""
-    rng = np.random.default_rng(SEED_BASE + 4)
+def batch_f7(n_chains: int = 256, rank: int = 0) -> Batch:
+    """256 chains, k ~ Poisson(80), G2 (width-2 N walk; rank: see batch_hubbard2)."""
+    rng = np.random.default_rng(SEED_BASE + 4 + 1000 * rank)
     m = model_f7()
     chains = [g2_chain(rng, m.n_flav, int(rng.poisson(80)), m.beta) for _ in range(n_chains)]
     return _pack(chains, m.beta)

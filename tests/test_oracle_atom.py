@@ -252,3 +252,33 @@ def test_sector_map_unique_and_charge_conserving(models):
             qp = m.s[alpha, q]
             if qp >= 0:
                 assert m.N[qp] == m.N[q] + (1 if dag else -1)
+
+
+def test_eigh_by_components_is_an_eigendecomposition():
+    """Block-diagonal input (hidden components permuted together): the result
+    diagonalises H, is orthonormal, and keeps exact zeros across components."""
+    rng = np.random.default_rng(3)
+    a = rng.normal(size=(3, 3))
+    b = rng.normal(size=(4, 4))
+    H = np.zeros((7, 7))
+    H[:3, :3] = a + a.T
+    H[3:, 3:] = b + b.T
+    perm = rng.permutation(7)
+    H = H[np.ix_(perm, perm)]
+    E, V = atom.eigh_by_components(H)
+    assert np.allclose(V.T @ V, np.eye(7), atol=1e-14)
+    assert np.allclose(H @ V, V * E[None, :], atol=1e-13)
+    assert np.allclose(E, np.linalg.eigvalsh(H), atol=1e-13)
+    for j in range(7):
+        orig = perm[np.nonzero(V[:, j])[0]]  # row i of the permuted H is original index perm[i]
+        assert np.all(orig < 3) or np.all(orig >= 3)
+
+
+def test_symmetry_forbidden_string_is_exactly_zero(models):
+    """t2g Kanamori conserves every orbital's occupation parity; moving one
+    electron between orbitals (c_2 ... c+_0) must give exactly 0."""
+    from oracle import trace as OT
+    m = models("t2g")
+    tau = [0.5, 1.0, 2.0, 3.0, 4.0, 5.0]
+    r = OT.trace_chain(m, tau, [11, 10, 8, 4, 1, 9])
+    assert r["log_abs"] == -math.inf
