@@ -172,7 +172,9 @@ typedef struct {
 } ctq_batch;
 
 /*
- * precision: CTQ_FP64 (others return CTQ_ERR_UNSUPPORTED where not built).
+ * precision: CTQ_FP64 (any impurity); CTQ_TF32 and CTQ_TF32X3 (tensor cores,
+ *   real impurities with sector blocks <= 112; CTQ_ERR_UNSUPPORTED otherwise);
+ *   CTQ_BF16X3 is not built (CTQ_ERR_UNSUPPORTED).
  * lazy: 1 = stop a chain as soon as its upper bound falls below its threshold
  *   (needs log_threshold).  segment: operators per bound refinement (>= 1).
  * max_ops: largest 2k in the batch (sizes the bounds output).
@@ -239,6 +241,18 @@ void ctq_free_impurity(ctq_impurity* imp);
  * small-block trace.  Errors: CTQ_ERR_ARG, CTQ_ERR_NOMEM, CTQ_ERR_CUDA.
  */
 int ctq_probe_fma_rate(int device, int kind, int iters, double* flops_per_s);
+
+/*
+ * Diagnostic of the tensor-core operand conventions used by CTQ_TF32 /
+ * CTQ_TF32X3: computes D = A B^T on `device` with one tcgen05 MMA sequence
+ * (A: host 128 x K row-major floats, placed in tensor memory; B: host N x K
+ * row-major floats, staged in shared memory as K-major core matrices; D: host
+ * 128 x N row-major floats), split = 1 (TF32) or 3 (hi*hi + hi*lo + lo*hi).
+ * N in [16, 112] and K in [16, 112], both multiples of 16.  Allocates and frees
+ * device buffers and synchronises.  No counterpart in the paper.
+ * Errors: CTQ_ERR_ARG, CTQ_ERR_NOMEM, CTQ_ERR_CUDA, CTQ_ERR_TIMEOUT.
+ */
+int ctq_tc_gemm_check(int device, const float* A, const float* B, float* D, int N, int K, int split);
 
 const char* ctq_strerror(int code);
 

@@ -16,6 +16,9 @@ struct ctq_impurity {
   int num_sms = 0;
   ctq::DevModel dev{};
   ctq::LaunchCfg launch{};
+  // tensor-core path (real impurities with blocks <= 112): TF32 and 3xTF32
+  ctq::TcParams tc1{}, tc3{};
+  ctq::LaunchCfg launch_tc1{}, launch_tc3{};
   std::vector<void*> allocs;
 };
 
@@ -107,6 +110,28 @@ int upload_model(ctq_impurity* imp) {
   if ((st = ctq::prepare_eval_fp64(d, imp->num_sms, &imp->launch)) != CTQ_OK) {
     free_device(imp);
     return fail(st, "cannot configure the trace kernel");
+  }
+  if (!h.is_complex && h.max_dim <= 112) {
+    std::vector<float> tcb;
+    std::vector<int64_t> tco;
+    int stage3 = 0;
+    if ((st = ctq::build_tc_blocks(h, 3, tcb, tco, &stage3)) != CTQ_OK ||
+        (st = upload_vec(imp, tcb, &imp->tc3.blk)) != CTQ_OK || (st = upload_vec(imp, tco, &imp->tc3.off)) != CTQ_OK) {
+      free_device(imp);
+      return fail(st, "tensor-core block upload failed");
+    }
+    imp->tc3.split = 3;
+    imp->tc3.stage_floats = stage3;
+    imp->tc3.tmem_cols = 512;
+    imp->tc1 = imp->tc3;  // same blocks; TF32 fetches only the hi half
+    imp->tc1.split = 1;
+    imp->tc1.stage_floats = stage3 / 2;
+    imp->tc1.tmem_cols = 256;
+    if ((st = ctq::prepare_eval_tc(d, 3, imp->tc3.stage_floats, imp->num_sms, &imp->launch_tc3)) != CTQ_OK ||
+        (st = ctq::prepare_eval_tc(d, 1, imp->tc1.stage_floats, imp->num_sms, &imp->launch_tc1)) != CTQ_OK) {
+      free_device(imp);
+      return fail(st, "cannot configure the tensor-core kernel");
+    }
   }
   return CTQ_OK;
 }
@@ -344,7 +369,11 @@ int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_e
   if (!result->log_abs || !result->phase || !result->status) return fail(CTQ_ERR_ARG, "null result array");
   if (opts->segment < 1 || opts->max_ops < 0) return fail(CTQ_ERR_ARG, "segment < 1 or max_ops < 0");
   if (opts->lazy && !batch->log_threshold) return fail(CTQ_ERR_ARG, "lazy evaluation needs thresholds");
-  if (opts->precision != CTQ_FP64) return fail(CTQ_ERR_UNSUPPORTED, "precision not built");
+  if (opts->precision != CTQ_FP64 && opts->precision != CTQ_TF32 && opts->precision != CTQ_TF32X3)
+    return fail(CTQ_ERR_UNSUPPORTED, "precision not built");
+  if (opts->precision != CTQ_FP64 &&
+      (opts->precision == CTQ_TF32 ? imp->launch_tc1.per_sm : imp->launch_tc3.per_sm) < 1)
+    return fail(CTQ_ERR_UNSUPPORTED, "tensor-core path needs a real impurity with blocks <= 112");
   if (!workspace) return fail(CTQ_ERR_ARG, "null workspace");
   if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return fail(CTQ_ERR_ARG, "workspace not 256-byte aligned");
   const int n_seg = n_seg_of(opts);
@@ -362,9 +391,19 @@ int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_e
   cfg.S = opts->segment;
   cfg.n_seg_max = n_seg;
   cfg.max_ops = opts->max_ops;
-  cfg.margin = 1e-9;
+  // Safety margin (log units) before an early reject: float64 rounding, or the
+  // relative error of reduced-precision products over a chain.
+  cfg.margin = opts->precision == CTQ_FP64 ? 1e-9 : (opts->precision == CTQ_TF32 ? 0.25 : 1e-3);
   cfg.bounds = result->bounds;
-  const int st = ctq::launch_eval_fp64(imp->dev, imp->launch, B, cfg, W, result, stream, opts->timing_events);
+  int st;
+  if (opts->precision == CTQ_FP64) {
+    st = ctq::launch_eval_fp64(imp->dev, imp->launch, B, cfg, W, result, stream, opts->timing_events);
+  } else {
+    ctq::TcParams P = opts->precision == CTQ_TF32 ? imp->tc1 : imp->tc3;
+    P.timeout_ns = opts->timeout_ns > 0 ? uint64_t(opts->timeout_ns) : uint64_t(2000000000ull);
+    st = ctq::launch_eval_tc(imp->dev, opts->precision == CTQ_TF32 ? imp->launch_tc1 : imp->launch_tc3, P, B, cfg,
+                             W, result, stream, opts->timing_events);
+  }
   if (st != CTQ_OK) return fail(st, st == CTQ_ERR_CUDA ? cudaGetErrorString(cudaGetLastError()) : "launch failed");
   return CTQ_OK;
 }

