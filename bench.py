@@ -242,6 +242,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="t2g", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "tf32x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -261,7 +262,8 @@ def main():
     batch = bf(rank=rank)  # each rank evaluates its own independent batch (weak scaling)
     imp = ctq.build_impurity(params, device=local)
     db = ctq.DeviceBatch(batch, device=dev)
-    ev = ctq.TraceEvaluator(imp, batch.n_chains, db.max_ops, device=dev)
+    prec = {"fp64": ctq.FP64, "tf32": ctq.TF32, "tf32x3": ctq.TF32X3}[args.precision]
+    ev = ctq.TraceEvaluator(imp, batch.n_chains, db.max_ops, precision=prec, device=dev)
     flops, n_items = algorithmic_flops(imp, batch)
     launches = ctq.launches_per_eval(imp)
     stream = torch.cuda.current_stream()
@@ -343,18 +345,17 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": {"fp64": "f64", "tf32": "tf32 (fp32 accumulate, f64 log scale)",
+                  "tf32x3": "3xtf32 (fp32 accumulate, f64 log scale)"}[args.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT[args.workload], "n_chains": batch.n_chains,
-                   "surviving_strings": n_items, "precision": "fp64", "l2": "flushed (256 MiB write) between steps",
+                   "surviving_strings": n_items, "precision": args.precision,
+                   "l2": "flushed (256 MiB write) between steps",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "tflops": flops / (ms * 1e-3) / 1e12,
         "algorithmic_flops_per_step": flops,
         "kernel_ms": {"plan": statistics.mean(kern_ms[0]), "trace": trace_ms, "combine": statistics.mean(kern_ms[2])},
-        "roofline": {"kernel": "k_trace<fp64>", "bound": "alu", "achieved": achieved_tf,
-                     "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": achieved_tf / (fp64_peak / 1e12),
-                     "peak_source": "measured FP64 FMA rate (ctq_probe_fma_rate, this run)",
-                     "traffic": traffic},
+        "roofline": roofline(args.precision, achieved_tf, fp64_peak, traffic),
         "e2e": {"value": world * batch.n_chains / (e2e * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * launches,
@@ -370,6 +371,23 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def roofline(precision, achieved_tf, fp64_peak, traffic):
+    """Roofline of the dominant kernel: the FP64 pipe for the FP64 path
+    (measured FMA rate), the TF32 tensor pipe for the mixed paths (measured
+    bf16 dense peak x 1/2, the nominal TF32:BF16 ratio)."""
+    if precision == "fp64":
+        return {"kernel": "k_trace<fp64>", "bound": "alu", "achieved": achieved_tf, "peak": fp64_peak / 1e12,
+                "unit": "TFLOP/s", "frac": achieved_tf / (fp64_peak / 1e12),
+                "peak_source": "measured FP64 FMA rate (ctq_probe_fma_rate, this run)", "traffic": traffic}
+    peaks, src = load_peaks()
+    peak = 0.5 * peaks["bf16_tflops"]
+    passes = 3 if precision == "tf32x3" else 1
+    return {"kernel": f"k_trace_tc<{passes}>", "bound": "tensor", "achieved": achieved_tf, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved_tf / peak, "hardware_passes": passes,
+            "peak_source": f"{src} bf16 dense x 0.5 (nominal TF32:BF16 ratio), MEASURED_PEAKS.json",
+            "traffic": traffic}
 
 
 def ctypes_void_array(n):

@@ -1,11 +1,13 @@
 """Tensor-core (tcgen05) path: operand conventions and parity of the TF32 and
 three-term split TF32 chain products against the FP64 oracle.
 
-Mixed-precision bar (no number in the paper; stated per configuration):
-TF32 relative error of w <= 3e-2 and 3xTF32 <= 3e-5 on well-conditioned
-chains (a chain of n products accumulates about n * 2^-11 resp. n * 2^-22
-relative error, times the chain's own conditioning, measured by the oracle's
-association spread).  Signs must agree on well-conditioned chains."""
+Mixed-precision bar (the paper gives no number; stated per configuration):
+a chain of n products accumulates at most about n * u relative error, with
+u = 2^-11 (TF32 operands) or 2^-21 (three-term split: the dropped lo*lo term
+and FP32 accumulation), times the chain's own conditioning (the oracle's
+association spread relative to float64 rounding).  The test holds every
+chain to 4 n u times that conditioning and prints the measured distribution.
+Signs must agree on well-conditioned chains."""
 import math
 
 import numpy as np
@@ -19,7 +21,12 @@ from paper_2010_08482_gb300 import workloads as w  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-TOL = {ctq.TF32: 3e-2, ctq.TF32X3: 3e-5}
+U_EFF = {ctq.TF32: 2.0 ** -11, ctq.TF32X3: 2.0 ** -21}
+
+
+def mixed_tolerance(precision, n_ops, ref):
+    cond = max(1.0, ref.get("noise", 0.0) / 1e-15)
+    return 4.0 * max(n_ops, 1) * U_EFF[precision] * cond
 
 
 @pytest.mark.parametrize("split", [1, 3])
@@ -55,11 +62,10 @@ def test_mixed_precision_parity(precision, name, n, models):
     for c in range(n):
         r = ref[c]
         if r["log_abs"] == -math.inf:
-            assert res["status"][c] == ctq.CHAIN_ZERO or abs(res["log_abs"][c] - 0) >= 0
             continue
         err, kind = parity.chain_error(res["log_abs"][c], res["phase"][c], r)
-        cond = max(1.0, r.get("noise", 0.0) / 1e-15)
-        assert err <= TOL[precision] * cond, (c, err, kind)
+        n_ops = int(sub.offsets[c + 1] - sub.offsets[c])
+        assert err <= mixed_tolerance(precision, n_ops, r), (c, err, kind, n_ops)
         errs.append(err)
         if r.get("noise", 0.0) <= 1e-12 and kind == "abs":
             assert res["phase"][c][0] == np.sign(np.real(r["phase"]))
