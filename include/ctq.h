@@ -226,6 +226,29 @@ int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_e
                     const ctq_result* result, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * Allocation-free variant of ctq_eval_traces, for callers that cannot provide
+ * a workspace: a C or Fortran Monte Carlo driver that owns no device
+ * allocator, code whose device memory belongs to another runtime's pool, or
+ * code that must not call cudaMalloc on a latency-critical path (it can
+ * synchronise the device).  No counterpart in the paper.
+ *
+ * The scratch is a file-scope device array of CTQ_STATIC_SCRATCH_BYTES inside
+ * the library; every GPU that loads the library holds it until the process
+ * exits.  The call allocates nothing and makes no allocating library call.
+ * Batches whose ctq_workspace_size() exceeds CTQ_STATIC_SCRATCH_BYTES are
+ * rejected with CTQ_ERR_WORKSPACE (ctq_last_error_message() gives the sizes).
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array: calls whose work overlaps on the
+ * GPU (other streams, other threads) race on it and must be serialised by the
+ * caller.  Every call re-initialises the parts of the scratch it reads.
+ * Arguments, results and the other errors are those of ctq_eval_traces.
+ */
+#define CTQ_STATIC_SCRATCH_BYTES (32u << 20)
+int ctq_eval_traces_static(const ctq_impurity* imp, const ctq_batch* batch, const ctq_eval_opts* opts,
+                           const ctq_result* result, void* stream);
+
+/*
  * Number of kernels one ctq_eval_traces call enqueues (for launch accounting).
  */
 int ctq_launches_per_eval(const ctq_impurity* imp, const ctq_eval_opts* opts);

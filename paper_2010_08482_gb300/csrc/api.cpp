@@ -178,6 +178,15 @@ double spectral_norm(int rows, int cols, const double* re, const double* im) {
 
 }  // namespace
 
+namespace ctq {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+int impurity_device(const ctq_impurity* imp, int* device) {
+  if (!imp || !device) return CTQ_ERR_ARG;
+  *device = imp->device;
+  return CTQ_OK;
+}
+}  // namespace ctq
+
 extern "C" {
 
 const char* ctq_strerror(int code) {

@@ -98,6 +98,10 @@ enum : int { FLAG_INVALID = 1, FLAG_REJECTED = 2 };
 
 size_t workspace_layout(int n_chains, int n_sec, int n_seg_max, void* base, Work* w);
 
+// Helpers for entry points defined outside api.cpp.
+void set_last_error(const std::string& msg);
+int impurity_device(const ctq_impurity* imp, int* device);
+
 // Launch shape of the trace kernel, fixed per impurity when it is uploaded
 // (so that evaluation makes no attribute or occupancy query, e.g. while a
 // CUDA graph is being captured).

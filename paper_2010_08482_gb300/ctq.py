@@ -85,6 +85,7 @@ def _load():
         "ctq_last_error_message": (c_char_p, []),
         "ctq_probe_fma_rate": (c_int, [c_int, c_int, c_int, POINTER(c_double)]),
         "ctq_tc_gemm_check": (c_int, [c_int, P, P, P, c_int, c_int, c_int]),
+        "ctq_eval_traces_static": (c_int, [P, POINTER(BatchC), POINTER(EvalOptsC), POINTER(ResultC), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -97,7 +98,10 @@ _lib = _load()
 EXPORTED = ("ctq_build_impurity", "ctq_load_impurity", "ctq_impurity_info", "ctq_get_sectors",
             "ctq_get_energies", "ctq_get_block", "ctq_workspace_size", "ctq_eval_traces",
             "ctq_launches_per_eval", "ctq_free_impurity", "ctq_strerror", "ctq_last_error_message",
-            "ctq_probe_fma_rate", "ctq_tc_gemm_check")
+            "ctq_probe_fma_rate", "ctq_tc_gemm_check", "ctq_eval_traces_static")
+
+# Size of the library-owned scratch used by eval_traces_static (ctq.h).
+STATIC_SCRATCH_BYTES = 32 << 20
 
 
 def tc_gemm_check(A: np.ndarray, Bm: np.ndarray, split: int = 3, device: int = 0) -> np.ndarray:
@@ -264,6 +268,22 @@ def eval_traces(imp: Impurity, n_chains: int, beta: float, offsets, tau, op, log
     o = _opts(precision, lazy, segment, max_ops, timeout_ns, events)
     _check(_lib.ctq_eval_traces(imp.handle, ctypes.byref(b), ctypes.byref(o), ctypes.byref(r),
                                 workspace, workspace_bytes, stream), "ctq_eval_traces")
+
+
+def eval_traces_static(imp: Impurity, n_chains: int, beta: float, offsets, tau, op, log_threshold,
+                       log_abs, phase, status, bounds, stream, precision=FP64, lazy=False, segment=8,
+                       max_ops=0, timeout_ns=0):
+    """ctq_eval_traces_static: as eval_traces, with the scratch in the library's
+    fixed device array instead of a caller workspace (for callers that cannot
+    allocate device memory; see ctq.h for the size limit and the sharing rule)."""
+    b = BatchC()
+    b.n_chains, b.beta = n_chains, beta
+    b.offsets, b.tau, b.op, b.log_threshold = offsets, tau, op, log_threshold
+    r = ResultC()
+    r.log_abs, r.phase, r.status, r.bounds = log_abs, phase, status, bounds
+    o = _opts(precision, lazy, segment, max_ops, timeout_ns, None)
+    _check(_lib.ctq_eval_traces_static(imp.handle, ctypes.byref(b), ctypes.byref(o), ctypes.byref(r), stream),
+           "ctq_eval_traces_static")
 
 
 free_impurity = Impurity.__del__
