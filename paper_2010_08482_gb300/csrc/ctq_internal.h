@@ -110,6 +110,7 @@ struct LaunchCfg {
   size_t smem = 0;
   int per_sm = 0;   // resident CTAs per SM (0: shape not supported)
   int num_sms = 0;
+  int regs = 0;     // registers per thread of the kernel
 };
 
 // Kernel parameters specific to the tensor-core path (trace_tc.cu).

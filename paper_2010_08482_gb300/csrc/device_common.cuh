@@ -67,7 +67,9 @@ __device__ __forceinline__ void block_max_sum(double& mx, double& sm, double* re
 }  // namespace dev
 
 // Kernels shared by every precision (plan_combine.cu).
-__global__ void k_plan(DevModel M, BatchView B, EvalCfg cfg, Work W);
-__global__ void k_combine(DevModel M, BatchView B, EvalCfg cfg, Work W, ctq_result R);
+int prepare_plan();
+int launch_plan(const DevModel& M, const BatchView& B, const EvalCfg& cfg, const Work& W, cudaStream_t st);
+int launch_combine(const DevModel& M, const BatchView& B, const EvalCfg& cfg, const Work& W, const ctq_result* R,
+                   cudaStream_t st);
 
 }  // namespace ctq

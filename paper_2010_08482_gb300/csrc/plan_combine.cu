@@ -21,13 +21,20 @@ using namespace dev;
 
 // ----------------------------------------------------------------------- plan
 
-__global__ void k_plan(DevModel M, BatchView B, EvalCfg cfg, Work W) {
+// One warp per chain; the lanes walk different q0 with integer table lookups
+// only and keep the visited sectors in shared memory (one byte per operator,
+// PLAN_MAX_OPS per lane), so that the float64 sums of a surviving string are
+// then taken by the whole warp with lanes over operators.
+__global__ void __launch_bounds__(128) k_plan(DevModel M, BatchView B, EvalCfg cfg, Work W) {
+  extern __shared__ unsigned char plan_paths[];
   const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
   const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (c >= B.n_chains) return;
   const int a0 = B.offsets[c];
   const int n = B.offsets[c + 1] - a0;
   const int ns = M.n_sec;
+  const int MO = max(cfg.max_ops, 1);
 
   bool bad = n < 0 || n > cfg.max_ops;
   for (int i = lane; !bad && i < n; i += 32) {
@@ -47,47 +54,64 @@ __global__ void k_plan(DevModel M, BatchView B, EvalCfg cfg, Work W) {
     return;
   }
   const double t_wrap = (n > 0) ? (B.beta - B.tau[a0 + n - 1] + B.tau[a0]) : B.beta;
+  unsigned char* mine = plan_paths + size_t(wib * 32 + lane) * MO;
 
-  // walk every q0 (lanes stride over sectors)
   double lm = -INFINITY, ls = 0.0;  // running logsumexp of b over this lane's q0
-  for (int q0 = lane; q0 < ns; q0 += 32) {
-    int q = q0, r = M.dims[q0];
-    double lb = 0.0;
-    bool alive = true;
-    for (int i = 0; i < n; ++i) {
-      const int alpha = B.op[a0 + i];
-      const int idx = alpha * ns + q;
-      lb += M.log_norm[idx];
-      q = M.s[idx];
-      if (q < 0) { alive = false; break; }
-      r = min(r, M.dims[q]);
-      if (i + 1 < n) lb -= (B.tau[a0 + i + 1] - B.tau[a0 + i]) * (M.E_min[q] - M.E_ref);
-    }
-    alive = alive && (q == q0);
-    const size_t slot = size_t(c) * ns + q0;
-    double b = -INFINITY;
+  for (int base = 0; base < ns; base += 32) {
+    const int q0 = base + lane;
+    bool alive = q0 < ns;
+    int q = q0, r = alive ? M.dims[q0] : 0;
     if (alive) {
-      b = (n == 0) ? (log(double(M.dims[q0])) - B.beta * (M.E_min[q0] - M.E_ref))
-                   : (log(double(r)) - t_wrap * (M.E_min[q0] - M.E_ref) + lb);
-      Item it;
-      it.c = c;
-      it.q0 = q0;
-      it.r = r;
-      it.n_seg = (n + cfg.S - 1) / cfg.S;
-      it.t_all = lb;
-      // the item is appended below unless the chain is rejected at level 0
-      W.items[slot] = it;  // staging copy in the (c, q0) slot
+      for (int i = 0; i < n; ++i) {
+        q = M.s[B.op[a0 + i] * ns + q];
+        if (q < 0) { alive = false; break; }
+        r = min(r, M.dims[q]);
+        mine[i] = static_cast<unsigned char>(q);
+      }
+      alive = alive && (q == q0);
     }
-    W.lvl0[slot] = b;
-    W.live[slot] = b;
-    W.res_log[slot] = -INFINITY;
-    W.res_val[2 * slot] = 0.0;
-    W.res_val[2 * slot + 1] = 0.0;
-    if (b > lm) {
-      ls = ls * exp(lm - b) + 1.0;
-      lm = b;
-    } else if (b != -INFINITY) {
-      ls += exp(b - lm);
+    if (q0 < ns) {
+      const size_t slot = size_t(c) * ns + q0;
+      W.lvl0[slot] = -INFINITY;
+      W.live[slot] = -INFINITY;
+      W.res_log[slot] = -INFINITY;
+      W.res_val[2 * slot] = 0.0;
+      W.res_val[2 * slot + 1] = 0.0;
+    }
+    unsigned mask = __ballot_sync(FULL, alive);
+    while (mask) {
+      const int src = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const int qs = base + src;
+      const unsigned char* path = plan_paths + size_t(wib * 32 + src) * MO;
+      double acc = 0.0;  // sum of log ||F_i|| - dtau_i (E_min(q_{i+1}) - E_ref)
+      for (int i = lane; i < n; i += 32) {
+        const int qi = (i == 0) ? qs : path[i - 1];
+        acc += M.log_norm[B.op[a0 + i] * ns + qi];
+        if (i + 1 < n) acc -= (B.tau[a0 + i + 1] - B.tau[a0 + i]) * (M.E_min[path[i]] - M.E_ref);
+      }
+      acc = warp_sum(acc);
+      const int rs = __shfl_sync(FULL, r, src);
+      if (lane == src) {
+        const double b = (n == 0) ? (log(double(M.dims[qs])) - B.beta * (M.E_min[qs] - M.E_ref))
+                                  : (log(double(rs)) - t_wrap * (M.E_min[qs] - M.E_ref) + acc);
+        const size_t slot = size_t(c) * ns + qs;
+        Item it;
+        it.c = c;
+        it.q0 = qs;
+        it.r = rs;
+        it.n_seg = (n + cfg.S - 1) / cfg.S;
+        it.t_all = acc;
+        W.items[slot] = it;  // staging copy in the (c, q0) slot
+        W.lvl0[slot] = b;
+        W.live[slot] = b;
+        if (b > lm) {
+          ls = ls * exp(lm - b) + 1.0;
+          lm = b;
+        } else {
+          ls += exp(b - lm);
+        }
+      }
     }
   }
   const double logB = warp_logsumexp(lm, ls);  // relative to -beta E_ref
@@ -108,8 +132,6 @@ __global__ void k_plan(DevModel M, BatchView B, EvalCfg cfg, Work W) {
     first = __shfl_sync(FULL, first, 0);
     if (alive) {
       const int pos = first + __popc(mask & ((1u << lane) - 1u));
-      // items[pos] may alias a staging slot of another chain that is already
-      // consumed: staging copies live in a separate region (see Work).
       W.items[size_t(B.n_chains) * ns + pos] = W.items[size_t(c) * ns + q0];
     }
   }
@@ -136,13 +158,13 @@ __global__ void k_combine(DevModel M, BatchView B, EvalCfg cfg, Work W, ctq_resu
         if (s > 0 || (flag & FLAG_INVALID)) cfg.bounds[size_t(c) * nb + s] = NAN;
     return;
   }
-  // sum_q0 w_q0 = sum val * e^{log}, with a common max log
+  // w = sum_q0 val * e^{log}, with a common max log (lanes over q0)
   double lm = -INFINITY;
   for (int q = lane; q < ns; q += 32) {
     const size_t slot = size_t(c) * ns + q;
     const double lg = W.res_log[slot];
     if (lg == -INFINITY) continue;
-    const double a = hypot(W.res_val[2 * slot], W.res_val[2 * slot + 1]);
+    const double a = fabs(W.res_val[2 * slot]) + fabs(W.res_val[2 * slot + 1]);
     if (a > 0.0) lm = fmax(lm, lg + log(a));
   }
   lm = warp_max(lm);
@@ -159,9 +181,9 @@ __global__ void k_combine(DevModel M, BatchView B, EvalCfg cfg, Work W, ctq_resu
   }
   sr = warp_sum(sr);
   si = warp_sum(si);
-  const double a = hypot(sr, si);
   const double shift = -B.beta * M.E_ref;  // logs above are relative to e^{-beta E_ref}
   if (lane == 0) {
+    const double a = hypot(sr, si);
     int st = CTQ_CHAIN_OK;
     if (lm == -INFINITY || a == 0.0) {
       R.log_abs[c] = -INFINITY;
@@ -178,24 +200,50 @@ __global__ void k_combine(DevModel M, BatchView B, EvalCfg cfg, Work W, ctq_resu
     R.status[c] = st;
   }
   if (cfg.bounds) {
-    for (int s = 1; s < nb; ++s) {
+    // lanes over segments; each lane sums over the surviving q0 serially
+    const int n = B.offsets[c + 1] - B.offsets[c];
+    const int nseg = (n + cfg.S - 1) / cfg.S;
+    for (int s = 1 + lane; s < nb; s += 32) {
+      const int ss = min(s, nseg);
       double m2 = -INFINITY, s2 = 0.0;
-      for (int q = lane; q < ns; q += 32) {
+      int cnt = 0;
+      for (int q = 0; q < ns; ++q) {
         const size_t slot = size_t(c) * ns + q;
         if (W.lvl0[slot] == -INFINITY) continue;
-        // items finish at their own last segment; later columns repeat the exact value
-        const int n = B.offsets[c + 1] - B.offsets[c];
-        const int nseg = (n + cfg.S - 1) / cfg.S;
-        const double v = W.seg[slot * size_t(nb) + min(s, nseg)];
-        if (v > m2) { s2 = s2 * exp(m2 - v) + 1.0; m2 = v; }
-        else if (v != -INFINITY) s2 += exp(v - m2);
+        const double v = W.seg[slot * size_t(nb) + ss];
+        if (v == -INFINITY) continue;
+        ++cnt;
+        if (v > m2) { s2 = (cnt == 1) ? 1.0 : s2 * exp(m2 - v) + 1.0; m2 = v; }
+        else s2 += exp(v - m2);
       }
-      const double lb = warp_logsumexp(m2, s2);
-      if (lane == 0) cfg.bounds[size_t(c) * nb + s] = lb + shift;
+      const double lb = (cnt == 0) ? -INFINITY : (cnt == 1 ? m2 : m2 + log(s2));
+      cfg.bounds[size_t(c) * nb + s] = lb + shift;
     }
   }
 }
 
+int prepare_plan() {
+  return cudaFuncSetAttribute(k_plan, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) == cudaSuccess
+             ? CTQ_OK
+             : CTQ_ERR_CUDA;
+}
+
+// k_plan keeps one byte per operator per lane (4 warps of 32 lanes per CTA).
+int launch_plan(const DevModel& M, const BatchView& B, const EvalCfg& cfg, const Work& W, cudaStream_t st) {
+  if (M.n_sec > 255) return CTQ_ERR_UNSUPPORTED;
+  const size_t smem = size_t(128) * size_t(cfg.max_ops > 0 ? cfg.max_ops : 1);
+  if (smem > 227 * 1024) return CTQ_ERR_UNSUPPORTED;
+  const int grid = (B.n_chains + 3) / 4;
+  k_plan<<<grid, 128, smem, st>>>(M, B, cfg, W);
+  return cudaGetLastError() == cudaSuccess ? CTQ_OK : CTQ_ERR_CUDA;
+}
+
+int launch_combine(const DevModel& M, const BatchView& B, const EvalCfg& cfg, const Work& W, const ctq_result* R,
+                   cudaStream_t st) {
+  const int grid = (B.n_chains + 3) / 4;
+  k_combine<<<grid, 128, 0, st>>>(M, B, cfg, W, *R);
+  return cudaGetLastError() == cudaSuccess ? CTQ_OK : CTQ_ERR_CUDA;
+}
 
 size_t workspace_layout(int n_chains, int n_sec, int n_seg_max, void* base, Work* w) {
   auto align = [](size_t x) { return (x + 255) & ~size_t(255); };

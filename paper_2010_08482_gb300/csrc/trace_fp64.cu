@@ -20,6 +20,8 @@
 //                ub = sqrt(r) ||Y||_F prod_{rest} ||F||_2 e^{-dtau E_min}
 //              is recorded and, with lazy evaluation, the chain's live bound
 //              sum is compared with its threshold (stop early if below).
+#include <algorithm>
+
 #include "device_common.cuh"
 
 namespace ctq {
@@ -40,8 +42,6 @@ struct Scalar<true> {
   using T = double2;
 };
 
-__device__ __forceinline__ double mag(double v) { return fabs(v); }
-__device__ __forceinline__ double mag(double2 v) { return fmax(fabs(v.x), fabs(v.y)); }
 __device__ __forceinline__ double sq(double v) { return v * v; }
 __device__ __forceinline__ double sq(double2 v) { return v.x * v.x + v.y * v.y; }
 __device__ __forceinline__ double2 operator*(double a, double2 b) { return make_double2(a * b.x, a * b.y); }
@@ -60,18 +60,54 @@ __device__ __forceinline__ void fma_acc(double2& acc, double2 f, double2 y) {
 __device__ __forceinline__ void zero(double& v) { v = 0.0; }
 __device__ __forceinline__ void zero(double2& v) { v = make_double2(0.0, 0.0); }
 
-template <bool CPLX>
+// Largest exponent field of |v| (integer; 0 for +-0 and subnormals).
+__device__ __forceinline__ int exp_key(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
+__device__ __forceinline__ int exp_key(double2 v) { return max(exp_key(v.x), exp_key(v.y)); }
+
+// Block-wide max of an int; every thread gets the result.  redi: 32 ints.
+__device__ __forceinline__ int block_max_int(int v, int* redi) {
+  v = __reduce_max_sync(0xffffffffu, v);
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (nw == 1) return v;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) redi[w] = v;
+  __syncthreads();
+  v = redi[0];
+  for (int i = 1; i < nw; ++i) v = max(v, redi[i]);
+  return v;
+}
+
+// Shared-memory layout of k_trace (dynamic part), see trace_smem().
+struct TraceSmem {
+  size_t y_bytes;  // one Y buffer
+  size_t pall;     // float64 propagators of the whole chain (PRE only)
+};
+
+// PRE: every propagator value of the chain is computed in one dense pass at
+// the start of an item (lanes over all (operator, state) pairs), which keeps
+// the FP64 pipe busy with full warps; used when max_ops * max_dim fits.
+template <bool CPLX, bool PRE>
 __global__ void __launch_bounds__(256) k_trace(DevModel M, BatchView B, EvalCfg cfg, Work W) {
   using T = typename Scalar<CPLX>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int D = M.max_dim;
+  const int MO = max(cfg.max_ops, 1);
+  const int NS = cfg.n_seg_max + 1;
   T* Ybuf0 = reinterpret_cast<T*>(smem_raw);
   T* Ybuf1 = Ybuf0 + size_t(D) * D;
-  double* p = reinterpret_cast<double*>(Ybuf1 + size_t(D) * D);  // [D] row propagators
-  double* p0 = p + D;                                            // [D] wrap propagator (columns)
+  double* p = reinterpret_cast<double*>(Ybuf1 + size_t(D) * D);  // [D] propagator of the current step
+  double* p0 = p + D;                                            // [D] wrap-around propagator (columns)
   double* red = p0 + D;                                          // [64] reductions
+  double* segL = red + 64;                                       // [NS] log scale at segment ends
+  double* segP = segL + NS;                                      // [NS] applied log-norm sums
+  double* pall = segP + NS;                                      // [MO * D] (PRE)
+  int* poff = reinterpret_cast<int*>(pall + (PRE ? size_t(MO) * D : 0));  // [MO + 1] (PRE)
+  short* path = reinterpret_cast<short*>(poff + (PRE ? MO + 1 : 0));     // [MO + 1] sectors q_0..q_n
+  short* opsm = path + (MO + 1);                                          // [MO] operator codes
   __shared__ int s_item;
   __shared__ int s_abort;
+  __shared__ int redi[32];
+  __shared__ double s_L;  // total log scale of the chain (thread 0 writes)
   const int tid = threadIdx.x, nt = blockDim.x;
   const int ns = M.n_sec;
   const int n_items = W.counters[0];
@@ -107,88 +143,135 @@ __global__ void __launch_bounds__(256) k_trace(DevModel M, BatchView B, EvalCfg 
       continue;
     }
 
-    // The wrap-around propagators P_{beta - tau_n}(q0) and P_{tau_1}(q0) scale
-    // the columns of the first block (trace cyclicity); the two time
-    // arguments are kept separate so that no extra rounding enters them.
-    const double t_first = B.tau[a0], t_last = B.beta - B.tau[a0 + n - 1];
-    KSum L;                            // log scale (energy shifts, relative to E_ref)
-    L.add(-t_first * (M.E_min[q0] - M.E_ref));
-    L.add(-t_last * (M.E_min[q0] - M.E_ref));
-    long long Eacc = 0;                // power-of-two exponent: true = stored * 2^Eacc
-    for (int j = tid; j < d0; j += nt) p0[j] = exp(-t_first * E0[j]) * exp(-t_last * E0[j]);
-
     if (n == 1) {  // only reachable with user tables where s_alpha(q0) = q0
-      __syncthreads();
-      const int alpha = B.op[a0];
-      const int64_t off = M.blk_off[alpha * ns + q0];
+      const double t1 = B.tau[a0], t2 = B.beta - B.tau[a0];
+      const int64_t off = M.blk_off[B.op[a0] * ns + q0];
       double vr = 0.0, vi = 0.0, mx = 0.0;
       for (int j = tid; j < d0; j += nt) {
+        const double pj = exp(-t1 * E0[j]) * exp(-t2 * E0[j]);
         const T f = load_blk(M.blk, off + int64_t(j) * d0 + j, T());
         if constexpr (CPLX) {
-          vr += f.x * p0[j];
-          vi += f.y * p0[j];
+          vr += f.x * pj;
+          vi += f.y * pj;
         } else {
-          vr += f * p0[j];
+          vr += f * pj;
         }
       }
       block_max_sum(mx, vr, red);
       mx = 0.0;
       block_max_sum(mx, vi, red);
       if (tid == 0) {
+        const double l = -B.beta * (M.E_min[q0] - M.E_ref);
         const bool zero_v = (vr == 0.0 && vi == 0.0);
         W.res_val[2 * slot] = vr;
         W.res_val[2 * slot + 1] = vi;
-        W.res_log[slot] = zero_v ? -INFINITY : L.val();
-        if (track) segp[it.n_seg] = zero_v ? -INFINITY : log(sqrt(vr * vr + vi * vi)) + L.val();
+        W.res_log[slot] = zero_v ? -INFINITY : l;
+        if (track) segp[it.n_seg] = zero_v ? -INFINITY : log(sqrt(vr * vr + vi * vi)) + l;
       }
       continue;
     }
 
+    // ---- walk the string once: sectors, operator codes, log scale and the
+    // applied log-norm sums at every segment end.  The wrap-around
+    // propagators P_{beta - tau_n}(q0) and P_{tau_1}(q0) scale the columns of
+    // the first block (trace cyclicity); their two time arguments are kept
+    // separate so that no extra rounding enters them.
+    const double t_first = B.tau[a0], t_last = B.beta - B.tau[a0 + n - 1];
+    if (tid == 0) {
+      KSum L;
+      L.add(-t_first * (M.E_min[q0] - M.E_ref));
+      L.add(-t_last * (M.E_min[q0] - M.E_ref));
+      double prefix = 0.0;
+      int q = q0;
+      path[0] = short(q0);
+      if (PRE) poff[0] = 0;
+      for (int i = 0; i < n; ++i) {
+        const int alpha = B.op[a0 + i];
+        const int idx = alpha * ns + q;
+        opsm[i] = short(alpha);
+        prefix += M.log_norm[idx];
+        q = M.s[idx];
+        path[i + 1] = short(q);
+        if (i + 1 < n) {
+          const double dt = B.tau[a0 + i + 1] - B.tau[a0 + i];
+          L.add(-dt * (M.E_min[q] - M.E_ref));
+          prefix -= dt * (M.E_min[q] - M.E_ref);
+          if (PRE) poff[i + 1] = poff[i] + M.dims[q];
+          if ((i + 1) % cfg.S == 0) {
+            segL[(i + 1) / cfg.S] = L.val();
+            segP[(i + 1) / cfg.S] = prefix;
+          }
+        }
+      }
+      s_L = L.val();
+    }
+    __syncthreads();
+    for (int j = tid; j < d0; j += nt) p0[j] = exp(-t_first * E0[j]) * exp(-t_last * E0[j]);
+    if (PRE) {
+      // all propagators of the chain: flat index j -> (operator i, state m)
+      const int total = poff[n - 1];
+      for (int j = tid; j < total; j += nt) {
+        int lo = 0, hi = n - 2;  // largest i with poff[i] <= j
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (poff[mid] <= j) lo = mid; else hi = mid - 1;
+        }
+        const int q = path[lo + 1];
+        const double dt = B.tau[a0 + lo + 1] - B.tau[a0 + lo];
+        pall[j] = exp(-dt * M.E_rel[M.E_off[q] + (j - poff[lo])]);
+      }
+    }
+
     // ---- operator 1: Y1[m][j] = p1[m] F1[m][j] p0[j]
     int qa = q0;
-    int alpha = B.op[a0];
-    int qb = M.s[alpha * ns + qa];
-    double prefix = M.log_norm[alpha * ns + qa];  // log-norm + propagator sums of applied ops
-    {
+    int alpha = opsm[0];
+    int qb = path[1];
+    const double* p1 = p;
+    if (!PRE) {
       const double dt = B.tau[a0 + 1] - B.tau[a0];
       const double* Eb = M.E_rel + M.E_off[qb];
-      const int db = M.dims[qb];
-      for (int m = tid; m < db; m += nt) p[m] = exp(-dt * Eb[m]);
-      L.add(-dt * (M.E_min[qb] - M.E_ref));
-      prefix -= dt * (M.E_min[qb] - M.E_ref);
+      for (int m = tid; m < M.dims[qb]; m += nt) p[m] = exp(-dt * Eb[m]);
+    } else {
+      p1 = pall;  // poff[0] = 0
     }
     __syncthreads();
     T* Y = Ybuf0;
     T* Yn = Ybuf1;
     int dcur = M.dims[qb];
-    double mx = 0.0, fr = 0.0;
+    int ekey = 0;
     {
       const int64_t off = M.blk_off[alpha * ns + qa];
       const int tot = dcur * d0;
       for (int idx = tid; idx < tot; idx += nt) {
         const int m = idx / d0, j = idx - m * d0;
-        const T f = load_blk(M.blk, off + idx, T());
-        const T v = (p[m] * p0[j]) * f;
+        const T v = (p1[m] * p0[j]) * load_blk(M.blk, off + idx, T());
         Y[idx] = v;
-        mx = fmax(mx, mag(v));
-        fr += sq(v);
+        ekey = max(ekey, exp_key(v));
       }
     }
-    block_max_sum(mx, fr, red);
+    ekey = block_max_int(ekey, redi);
     qa = qb;
     int applied = 1;
+    long long Eacc = 0;  // power-of-two exponent: true = stored * 2^Eacc
     bool dead = false;
     bool aborted = false;
+    double fr = 0.0;     // ||Y||^2 of the stored product (segment steps only)
+    bool have_fr = false;
 
-    // ---- operators 2 .. n-1: Y <- P F Y, previous rescale folded into P
+    // ---- operators 2 .. n: Y <- P F Y, the previous rescale folded into P
     for (int i = 1; i < n; ++i) {
-      // bookkeeping for the product that has just been stored in Y (after `applied` operators)
-      if (mx == 0.0) { dead = true; break; }
-      int e = ilogb(mx);
+      if (ekey == 0) { dead = true; break; }
+      const int e = ekey - 1023;  // floor(log2 max|Y|) for normal values
       if (track && applied % cfg.S == 0 && applied < n) {
-        const double ub = 0.5 * log(double(it.r)) + 0.5 * log(fr) + double(Eacc) * LN2 + L.val() +
-                          (it.t_all - prefix);
+        if (!have_fr) {  // only after the first operator (segment length 1)
+          double f = 0.0, dmx = 0.0;
+          for (int idx = tid; idx < dcur * d0; idx += nt) f += sq(Y[idx]);
+          block_max_sum(dmx, f, red);
+          fr = f;
+        }
         if (tid == 0) {
+          const double ub = 0.5 * log(double(it.r)) + 0.5 * log(fr) + double(Eacc) * LN2 +
+                            segL[applied / cfg.S] + (it.t_all - segP[applied / cfg.S]);
           segp[applied / cfg.S] = ub;
           if (cfg.lazy) {
             W.live[slot] = fmin(W.live[slot], ub);
@@ -196,7 +279,6 @@ __global__ void __launch_bounds__(256) k_trace(DevModel M, BatchView B, EvalCfg 
           }
         }
         if (cfg.lazy) {
-          // chain bound from the live slots of every q0 (warp 0)
           if (tid < 32) {
             double lm = -INFINITY, lsum = 0.0;
             for (int q = tid; q < ns; q += 32) {
@@ -218,16 +300,14 @@ __global__ void __launch_bounds__(256) k_trace(DevModel M, BatchView B, EvalCfg 
           if (s_abort) { aborted = true; break; }
         }
       }
-      alpha = B.op[a0 + i];
+      alpha = opsm[i];
       const int idx_a = alpha * ns + qa;
-      qb = M.s[idx_a];
+      qb = path[i + 1];
       const int64_t off = M.blk_off[idx_a];
-      prefix += M.log_norm[idx_a];
       const double scale = ldexp(1.0, -e);
       Eacc += e;
 
       if (i == n - 1) {  // final operator: only the diagonal of F_n Y is needed
-        // qb == q0; F_n is d0 x dcur
         double vr = 0.0, vi = 0.0;
         const int tot = d0 * dcur;
         for (int idx = tid; idx < tot; idx += nt) {
@@ -248,29 +328,34 @@ __global__ void __launch_bounds__(256) k_trace(DevModel M, BatchView B, EvalCfg 
           block_max_sum(dm, vi, red);
         }
         if (tid == 0) {
+          const double Lv = s_L;
           W.res_val[2 * slot] = vr * scale;
           W.res_val[2 * slot + 1] = vi * scale;
           const bool zero_v = (vr == 0.0 && vi == 0.0);
-          W.res_log[slot] = zero_v ? -INFINITY : L.val() + double(Eacc) * LN2;
+          W.res_log[slot] = zero_v ? -INFINITY : Lv + double(Eacc) * LN2;
           if (track) {
             const double a = sqrt(vr * vr + vi * vi) * scale;
-            segp[it.n_seg] = zero_v ? -INFINITY : log(a) + L.val() + double(Eacc) * LN2;
+            segp[it.n_seg] = zero_v ? -INFINITY : log(a) + Lv + double(Eacc) * LN2;
           }
         }
         applied = n;
         break;
       }
 
-      const double dt = B.tau[a0 + i + 1] - B.tau[a0 + i];
-      const double* Eb = M.E_rel + M.E_off[qb];
       const int db = M.dims[qb];
-      for (int m = tid; m < db; m += nt) p[m] = exp(-dt * Eb[m]) * scale;
-      L.add(-dt * (M.E_min[qb] - M.E_ref));
-      prefix -= dt * (M.E_min[qb] - M.E_ref);
+      if (PRE) {
+        const double* pi = pall + poff[i];
+        for (int m = tid; m < db; m += nt) p[m] = pi[m] * scale;
+      } else {
+        const double dt = B.tau[a0 + i + 1] - B.tau[a0 + i];
+        const double* Eb = M.E_rel + M.E_off[qb];
+        for (int m = tid; m < db; m += nt) p[m] = exp(-dt * Eb[m]) * scale;
+      }
       __syncthreads();
       // Yn[m][j] = p[m] * sum_k F[m][k] Y[k][j]
-      mx = 0.0;
-      fr = 0.0;
+      const bool seg_next = track && (applied + 1) % cfg.S == 0 && (applied + 1) < n;
+      ekey = 0;
+      double f2 = 0.0;
       const int tot = db * d0;
       for (int idx = tid; idx < tot; idx += nt) {
         const int m = idx / d0, j = idx - m * d0;
@@ -280,10 +365,16 @@ __global__ void __launch_bounds__(256) k_trace(DevModel M, BatchView B, EvalCfg 
         for (int k = 0; k < dcur; ++k) fma_acc(acc, load_blk(M.blk, frow + k, T()), Y[k * d0 + j]);
         const T v = p[m] * acc;
         Yn[idx] = v;
-        mx = fmax(mx, mag(v));
-        fr += sq(v);
+        ekey = max(ekey, exp_key(v));
+        if (seg_next) f2 += sq(v);
       }
-      block_max_sum(mx, fr, red);
+      ekey = block_max_int(ekey, redi);
+      if (seg_next) {
+        double dmx = 0.0;
+        block_max_sum(dmx, f2, red);
+        fr = f2;
+      }
+      have_fr = seg_next;
       T* tmp = Y;
       Y = Yn;
       Yn = tmp;
@@ -311,32 +402,42 @@ static int trace_threads(int max_dim) {
   return 256;
 }
 
-static size_t trace_smem(int max_dim, bool cplx) {
+// Dynamic shared memory of k_trace: two Y buffers, p, p0, reductions, the
+// segment bookkeeping, and (PRE) the chain's propagators and offsets, then
+// the path and operator codes.
+static size_t trace_smem(int max_dim, bool cplx, int max_ops, int n_seg_max, bool pre) {
   const size_t el = cplx ? 16 : 8;
-  return 2 * size_t(max_dim) * max_dim * el + 2 * size_t(max_dim) * 8 + 64 * 8;
+  const size_t mo = size_t(std::max(max_ops, 1));
+  size_t b = 2 * size_t(max_dim) * max_dim * el + 2 * size_t(max_dim) * 8 + 64 * 8 + 2 * size_t(n_seg_max + 1) * 8;
+  if (pre) b += mo * max_dim * 8 + (mo + 1) * 4;
+  b += (mo + 1) * 2 + mo * 2;
+  return (b + 15) & ~size_t(15);
+}
+
+// Whole-chain propagator precompute when it fits comfortably.
+static bool use_pre(int max_dim, int max_ops) { return size_t(std::max(max_ops, 1)) * max_dim * 8 <= 48 * 1024; }
+
+template <bool CPLX, bool PRE>
+static int set_attr() {
+  return cudaFuncSetAttribute(k_trace<CPLX, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) ==
+                 cudaSuccess
+             ? CTQ_OK
+             : CTQ_ERR_CUDA;
 }
 
 int prepare_eval_fp64(const DevModel& M, int num_sms, LaunchCfg* lc) {
   lc->threads = trace_threads(M.max_dim);
-  lc->smem = trace_smem(M.max_dim, M.is_complex != 0);
   lc->num_sms = num_sms;
-  lc->per_sm = 0;
-  if (lc->smem > 227 * 1024) return CTQ_OK;  // needs the large-block path
-  int per_sm = 0;
-  if (M.is_complex) {
-    if (cudaFuncSetAttribute(k_trace<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lc->smem)) !=
-        cudaSuccess)
-      return CTQ_ERR_CUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<true>, lc->threads, lc->smem) != cudaSuccess)
-      return CTQ_ERR_CUDA;
-  } else {
-    if (cudaFuncSetAttribute(k_trace<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lc->smem)) !=
-        cudaSuccess)
-      return CTQ_ERR_CUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<false>, lc->threads, lc->smem) != cudaSuccess)
-      return CTQ_ERR_CUDA;
-  }
-  lc->per_sm = per_sm;
+  lc->smem = trace_smem(M.max_dim, M.is_complex != 0, 1, 1, false);
+  lc->per_sm = (lc->smem > 200 * 1024) ? 0 : 1;  // feasibility at the smallest max_ops
+  int st;
+  if ((st = prepare_plan()) != CTQ_OK) return st;
+  if ((st = set_attr<false, false>()) || (st = set_attr<false, true>()) || (st = set_attr<true, false>()) ||
+      (st = set_attr<true, true>()))
+    return st;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, k_trace<true, true>) != cudaSuccess) return CTQ_ERR_CUDA;
+  lc->regs = fa.numRegs;
   return CTQ_OK;
 }
 
@@ -345,27 +446,40 @@ int launch_eval_fp64(const DevModel& M, const LaunchCfg& lc, const BatchView& B,
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (B.n_chains == 0) return CTQ_OK;
   if (lc.per_sm < 1) return CTQ_ERR_UNSUPPORTED;
+  const bool pre = use_pre(M.max_dim, cfg.max_ops);
+  const size_t smem = trace_smem(M.max_dim, M.is_complex != 0, cfg.max_ops, cfg.n_seg_max, pre);
+  if (smem > 227 * 1024) return CTQ_ERR_UNSUPPORTED;
+  // resident CTAs per SM from shared memory, registers and the 32-CTA limit
+  int per_sm = int((228 * 1024) / (smem + 1024));
+  per_sm = std::min(per_sm, 65536 / std::max(1, lc.regs * lc.threads));
+  per_sm = std::min(per_sm, std::min(32, 2048 / lc.threads));
+  if (per_sm < 1) return CTQ_ERR_UNSUPPORTED;
   auto mark = [&](int i) {
     if (events) cudaEventRecord(static_cast<cudaEvent_t>(events[i]), st);
   };
   if (cudaMemsetAsync(W.counters, 0, 256, st) != cudaSuccess) return CTQ_ERR_CUDA;
   mark(0);
-  const int warps_per_block = 4;
-  const int grid_c = (B.n_chains + warps_per_block - 1) / warps_per_block;
-  k_plan<<<grid_c, 32 * warps_per_block, 0, st>>>(M, B, cfg, W);
-  if (cudaGetLastError() != cudaSuccess) return CTQ_ERR_CUDA;
+  {
+    const int ps = launch_plan(M, B, cfg, W, st);
+    if (ps != CTQ_OK) return ps;
+  }
   mark(1);
   long long max_items = (long long)B.n_chains * M.n_sec;
-  long long grid = (long long)lc.num_sms * lc.per_sm;
+  long long grid = (long long)lc.num_sms * per_sm;
   if (grid > max_items) grid = max_items;
-  if (M.is_complex)
-    k_trace<true><<<int(grid), lc.threads, lc.smem, st>>>(M, B, cfg, W);
-  else
-    k_trace<false><<<int(grid), lc.threads, lc.smem, st>>>(M, B, cfg, W);
+  if (M.is_complex) {
+    if (pre) k_trace<true, true><<<int(grid), lc.threads, smem, st>>>(M, B, cfg, W);
+    else k_trace<true, false><<<int(grid), lc.threads, smem, st>>>(M, B, cfg, W);
+  } else {
+    if (pre) k_trace<false, true><<<int(grid), lc.threads, smem, st>>>(M, B, cfg, W);
+    else k_trace<false, false><<<int(grid), lc.threads, smem, st>>>(M, B, cfg, W);
+  }
   if (cudaGetLastError() != cudaSuccess) return CTQ_ERR_CUDA;
   mark(2);
-  k_combine<<<grid_c, 32 * warps_per_block, 0, st>>>(M, B, cfg, W, *R);
-  if (cudaGetLastError() != cudaSuccess) return CTQ_ERR_CUDA;
+  {
+    const int cs = launch_combine(M, B, cfg, W, R, st);
+    if (cs != CTQ_OK) return cs;
+  }
   mark(3);
   return CTQ_OK;
 }

@@ -709,10 +709,10 @@ int launch_eval_tc(const DevModel& M, const LaunchCfg& lc, const TcParams& P, co
   };
   if (cudaMemsetAsync(W.counters, 0, 256, st) != cudaSuccess) return CTQ_ERR_CUDA;
   mark(0);
-  const int wpb = 4;
-  const int grid_c = (B.n_chains + wpb - 1) / wpb;
-  k_plan<<<grid_c, 32 * wpb, 0, st>>>(M, B, cfg, W);
-  if (cudaGetLastError() != cudaSuccess) return CTQ_ERR_CUDA;
+  {
+    const int ps = launch_plan(M, B, cfg, W, st);
+    if (ps != CTQ_OK) return ps;
+  }
   mark(1);
   long long max_items = (long long)B.n_chains * M.n_sec;
   long long grid = (long long)lc.num_sms * lc.per_sm;
@@ -723,8 +723,10 @@ int launch_eval_tc(const DevModel& M, const LaunchCfg& lc, const TcParams& P, co
     k_trace_tc<1><<<int(grid), TC_THREADS, lc.smem, st>>>(M, B, cfg, W, P);
   if (cudaGetLastError() != cudaSuccess) return CTQ_ERR_CUDA;
   mark(2);
-  k_combine<<<grid_c, 32 * wpb, 0, st>>>(M, B, cfg, W, *R);
-  if (cudaGetLastError() != cudaSuccess) return CTQ_ERR_CUDA;
+  {
+    const int cs = launch_combine(M, B, cfg, W, R, st);
+    if (cs != CTQ_OK) return cs;
+  }
   mark(3);
   return CTQ_OK;
 }
