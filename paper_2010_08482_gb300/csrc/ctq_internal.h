@@ -111,6 +111,7 @@ struct LaunchCfg {
   int per_sm = 0;   // resident CTAs per SM (0: shape not supported)
   int num_sms = 0;
   int regs = 0;     // registers per thread of the kernel
+  int smem_optin = 0;  // opt-in shared memory per block of the device
 };
 
 // Kernel parameters specific to the tensor-core path (trace_tc.cu).

@@ -67,7 +67,7 @@ __device__ __forceinline__ void block_max_sum(double& mx, double& sm, double* re
 }  // namespace dev
 
 // Kernels shared by every precision (plan_combine.cu).
-int prepare_plan();
+int prepare_plan(int optin);
 int launch_plan(const DevModel& M, const BatchView& B, const EvalCfg& cfg, const Work& W, cudaStream_t st);
 int launch_combine(const DevModel& M, const BatchView& B, const EvalCfg& cfg, const Work& W, const ctq_result* R,
                    cudaStream_t st);

@@ -222,8 +222,11 @@ __global__ void k_combine(DevModel M, BatchView B, EvalCfg cfg, Work W, ctq_resu
   }
 }
 
-int prepare_plan() {
-  return cudaFuncSetAttribute(k_plan, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) == cudaSuccess
+int prepare_plan(int optin) {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, k_plan) != cudaSuccess) return CTQ_ERR_CUDA;
+  return cudaFuncSetAttribute(k_plan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - int(fa.sharedSizeBytes)) == cudaSuccess
              ? CTQ_OK
              : CTQ_ERR_CUDA;
 }
@@ -232,7 +235,7 @@ int prepare_plan() {
 int launch_plan(const DevModel& M, const BatchView& B, const EvalCfg& cfg, const Work& W, cudaStream_t st) {
   if (M.n_sec > 255) return CTQ_ERR_UNSUPPORTED;
   const size_t smem = size_t(128) * size_t(cfg.max_ops > 0 ? cfg.max_ops : 1);
-  if (smem > 227 * 1024) return CTQ_ERR_UNSUPPORTED;
+  if (smem > 200 * 1024) return CTQ_ERR_UNSUPPORTED;  // max_ops <= 1600
   const int grid = (B.n_chains + 3) / 4;
   k_plan<<<grid, 128, smem, st>>>(M, B, cfg, W);
   return cudaGetLastError() == cudaSuccess ? CTQ_OK : CTQ_ERR_CUDA;

@@ -417,10 +417,14 @@ static size_t trace_smem(int max_dim, bool cplx, int max_ops, int n_seg_max, boo
 // Whole-chain propagator precompute when it fits comfortably.
 static bool use_pre(int max_dim, int max_ops) { return size_t(std::max(max_ops, 1)) * max_dim * 8 <= 48 * 1024; }
 
+// Raise the dynamic shared-memory cap to the opt-in maximum minus the
+// kernel's static shared memory.
 template <bool CPLX, bool PRE>
-static int set_attr() {
-  return cudaFuncSetAttribute(k_trace<CPLX, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) ==
-                 cudaSuccess
+static int set_attr(int optin) {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, k_trace<CPLX, PRE>) != cudaSuccess) return CTQ_ERR_CUDA;
+  const int cap = optin - int(fa.sharedSizeBytes);
+  return cudaFuncSetAttribute(k_trace<CPLX, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) == cudaSuccess
              ? CTQ_OK
              : CTQ_ERR_CUDA;
 }
@@ -430,10 +434,14 @@ int prepare_eval_fp64(const DevModel& M, int num_sms, LaunchCfg* lc) {
   lc->num_sms = num_sms;
   lc->smem = trace_smem(M.max_dim, M.is_complex != 0, 1, 1, false);
   lc->per_sm = (lc->smem > 200 * 1024) ? 0 : 1;  // feasibility at the smallest max_ops
-  int st;
-  if ((st = prepare_plan()) != CTQ_OK) return st;
-  if ((st = set_attr<false, false>()) || (st = set_attr<false, true>()) || (st = set_attr<true, false>()) ||
-      (st = set_attr<true, true>()))
+  int st, dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return CTQ_ERR_CUDA;
+  lc->smem_optin = optin;
+  if ((st = prepare_plan(optin)) != CTQ_OK) return st;
+  if ((st = set_attr<false, false>(optin)) || (st = set_attr<false, true>(optin)) ||
+      (st = set_attr<true, false>(optin)) || (st = set_attr<true, true>(optin)))
     return st;
   cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, k_trace<true, true>) != cudaSuccess) return CTQ_ERR_CUDA;
@@ -448,7 +456,7 @@ int launch_eval_fp64(const DevModel& M, const LaunchCfg& lc, const BatchView& B,
   if (lc.per_sm < 1) return CTQ_ERR_UNSUPPORTED;
   const bool pre = use_pre(M.max_dim, cfg.max_ops);
   const size_t smem = trace_smem(M.max_dim, M.is_complex != 0, cfg.max_ops, cfg.n_seg_max, pre);
-  if (smem > 227 * 1024) return CTQ_ERR_UNSUPPORTED;
+  if (smem + 1024 > size_t(lc.smem_optin)) return CTQ_ERR_UNSUPPORTED;
   // resident CTAs per SM from shared memory, registers and the 32-CTA limit
   int per_sm = int((228 * 1024) / (smem + 1024));
   per_sm = std::min(per_sm, 65536 / std::max(1, lc.regs * lc.threads));
