@@ -19,6 +19,10 @@ struct ctq_impurity {
   // tensor-core path (real impurities with blocks <= 112): TF32 and 3xTF32
   ctq::TcParams tc1{}, tc3{};
   ctq::LaunchCfg launch_tc1{}, launch_tc3{};
+  // large-block tensor-core path (complex impurities or blocks > 112)
+  bool big = false;
+  ctq::BigParams big1{}, big3{};
+  ctq::LaunchCfg launch_big1{}, launch_big3{};
   std::vector<void*> allocs;
 };
 
@@ -132,6 +136,38 @@ int upload_model(ctq_impurity* imp) {
       free_device(imp);
       return fail(st, "cannot configure the tensor-core kernel");
     }
+  } else if (h.max_dim <= 3072) {
+    // large blocks: embedded, tiled, tf32-split copies formatted on the device
+    std::vector<int64_t> off(h.s.size(), -1);
+    size_t total = 0;
+    for (int a = 0; a < h.n_alpha(); ++a)
+      for (int q = 0; q < h.n_sec; ++q) {
+        const size_t i = size_t(a) * h.n_sec + q;
+        if (h.s[i] < 0) continue;
+        off[i] = int64_t(total);
+        total += ctq::big_block_floats(h.dims[h.s[i]], h.dims[q]);
+      }
+    void* bt = nullptr;
+    if (cudaMalloc(&bt, std::max<size_t>(total, 1) * sizeof(float)) != cudaSuccess) {
+      free_device(imp);
+      return fail(CTQ_ERR_NOMEM, "cannot allocate the large-block operands");
+    }
+    imp->allocs.push_back(bt);
+    if ((st = ctq::format_big_blocks(h, d.blk, static_cast<float*>(bt), off)) != CTQ_OK ||
+        (st = upload_vec(imp, off, &imp->big3.bt_off)) != CTQ_OK) {
+      free_device(imp);
+      return fail(st, "large-block formatting failed");
+    }
+    imp->big3.bt = static_cast<const float*>(bt);
+    imp->big3.split = 3;
+    imp->big1 = imp->big3;
+    imp->big1.split = 1;
+    if ((st = ctq::prepare_eval_big(3, imp->num_sms, &imp->launch_big3)) != CTQ_OK ||
+        (st = ctq::prepare_eval_big(1, imp->num_sms, &imp->launch_big1)) != CTQ_OK) {
+      free_device(imp);
+      return fail(st, "cannot configure the large-block kernel");
+    }
+    imp->big = true;
   }
   return CTQ_OK;
 }
@@ -357,9 +393,14 @@ static int n_seg_of(const ctq_eval_opts* o) {
   return (std::max(0, o->max_ops) + S - 1) / S;
 }
 
+static size_t big_extra(const ctq_impurity* imp, const ctq_eval_opts* opts) {
+  if (!imp->big || opts->precision == CTQ_FP64) return 0;
+  return ctq::big_scratch_bytes(imp->host, std::max(0, opts->max_ops), imp->num_sms) + 256;
+}
+
 size_t ctq_workspace_size(const ctq_impurity* imp, int n_chains, const ctq_eval_opts* opts) {
   if (!imp || !opts || n_chains < 0) return 0;
-  return ctq::workspace_layout(n_chains, imp->host.n_sec, n_seg_of(opts), nullptr, nullptr);
+  return ctq::workspace_layout(n_chains, imp->host.n_sec, n_seg_of(opts), nullptr, nullptr) + big_extra(imp, opts);
 }
 
 int ctq_launches_per_eval(const ctq_impurity* imp, const ctq_eval_opts* opts) {
@@ -380,13 +421,14 @@ int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_e
   if (opts->lazy && !batch->log_threshold) return fail(CTQ_ERR_ARG, "lazy evaluation needs thresholds");
   if (opts->precision != CTQ_FP64 && opts->precision != CTQ_TF32 && opts->precision != CTQ_TF32X3)
     return fail(CTQ_ERR_UNSUPPORTED, "precision not built");
-  if (opts->precision != CTQ_FP64 &&
+  if (opts->precision != CTQ_FP64 && !imp->big &&
       (opts->precision == CTQ_TF32 ? imp->launch_tc1.per_sm : imp->launch_tc3.per_sm) < 1)
-    return fail(CTQ_ERR_UNSUPPORTED, "tensor-core path needs a real impurity with blocks <= 112");
+    return fail(CTQ_ERR_UNSUPPORTED, "no tensor-core path for this impurity");
   if (!workspace) return fail(CTQ_ERR_ARG, "null workspace");
   if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return fail(CTQ_ERR_ARG, "workspace not 256-byte aligned");
   const int n_seg = n_seg_of(opts);
-  const size_t need = ctq::workspace_layout(batch->n_chains, imp->host.n_sec, n_seg, nullptr, nullptr);
+  const size_t base = ctq::workspace_layout(batch->n_chains, imp->host.n_sec, n_seg, nullptr, nullptr);
+  const size_t need = base + big_extra(imp, opts);
   if (workspace_bytes < need) return fail(CTQ_ERR_WORKSPACE, "workspace smaller than ctq_workspace_size()");
   DeviceGuard g(imp->device);
   if (!g.ok()) return fail(CTQ_ERR_CUDA, "cudaSetDevice failed");
@@ -409,6 +451,12 @@ int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_e
   int st;
   if (opts->precision == CTQ_FP64) {
     st = ctq::launch_eval_fp64(imp->dev, imp->launch, B, cfg, W, result, stream, opts->timing_events);
+  } else if (imp->big) {
+    ctq::BigParams P = opts->precision == CTQ_TF32 ? imp->big1 : imp->big3;
+    P.timeout_ns = opts->timeout_ns > 0 ? uint64_t(opts->timeout_ns) : uint64_t(2000000000ull);
+    char* scratch = static_cast<char*>(workspace) + ((base + 255) & ~size_t(255));
+    st = ctq::launch_eval_big(imp->dev, opts->precision == CTQ_TF32 ? imp->launch_big1 : imp->launch_big3, P, B,
+                              cfg, W, result, scratch, stream, opts->timing_events);
   } else {
     ctq::TcParams P = opts->precision == CTQ_TF32 ? imp->tc1 : imp->tc3;
     P.timeout_ns = opts->timeout_ns > 0 ? uint64_t(opts->timeout_ns) : uint64_t(2000000000ull);

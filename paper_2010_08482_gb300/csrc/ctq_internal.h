@@ -124,6 +124,29 @@ struct TcParams {
   uint64_t timeout_ns = 0;
 };
 
+// Per-impurity parameters and scratch of the large-block path (trace_big.cu).
+struct BigParams {
+  const float* bt = nullptr;      // embedded blocks: tiles (hi, then lo), per (alpha, q)
+  const int64_t* bt_off = nullptr;  // [n_alpha * n_sec] float offsets, -1 absent
+  int split = 3;                  // 1 or 3
+  int nst = 3;                    // pipeline stages
+  uint64_t timeout_ns = 0;
+  float* zbuf = nullptr;          // scratch: 2 x (hi, lo) Z buffers
+  size_t zfloats = 0;             // floats of one Z plane
+  unsigned* bar = nullptr;        // grid barrier: count, generation
+  int* ekey = nullptr;            // [max_ops + 2] max exponent field per operator
+  double* fr = nullptr;           // [max_ops + 2] ||Z||^2 per operator
+  double* part = nullptr;         // [2 * grid] final-trace partial sums
+  int* abort_flag = nullptr;
+};
+
+size_t big_block_floats(int dn, int dk);
+int format_big_blocks(const HostModel& h, const double* d_blk, float* out, const std::vector<int64_t>& off);
+size_t big_scratch_bytes(const HostModel& h, int max_ops, int grid);
+int prepare_eval_big(int split, int num_sms, LaunchCfg* lc);
+int launch_eval_big(const DevModel& M, const LaunchCfg& lc, BigParams P, const BatchView& B, const EvalCfg& cfg,
+                    const Work& W, const ctq_result* R, void* scratch, void* stream, void* const* events);
+
 // Launchers (trace_fp64.cu, trace_tc.cu).  Return a CTQ_* status.
 int build_tc_blocks(const HostModel& h, int split, std::vector<float>& out, std::vector<int64_t>& off,
                     int* stage_floats);
