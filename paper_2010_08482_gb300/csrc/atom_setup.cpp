@@ -326,21 +326,34 @@ int build_host_model(const ctq_model_params* p, HostModel& m, std::string& err) 
   // Real-harmonic rotations leave ~1e-16 imaginary residue in a real problem.
   m.is_complex = (max_im > 1e-13 * std::max(1.0, max_abs)) ? 1 : 0;
 
-  // eigenbasis
+  // eigenbasis: host Jacobi, or the device solver when any sector is large
   std::vector<std::vector<double>> Vr(m.n_sec);
   std::vector<std::vector<cplx>> Vc(m.n_sec);
   std::vector<std::vector<double>> E0(m.n_sec);
+  const bool on_device = m.max_dim > kJacobiMaxDim;
+  DeviceSectorLA dla;
+  if (on_device) {
+    const int st = dla.init(p->device, m.is_complex != 0, m.n_sec, err);
+    if (st != CTQ_OK) return st;
+  }
   for (int q = 0; q < m.n_sec; ++q) {
     const int d = m.dims[q];
     int st;
-    if (m.is_complex) {
+    if (on_device) {
+      if (m.is_complex) Vc[q].resize(size_t(d) * d);
+      else Vr[q].resize(size_t(d) * d);
+      st = dla.eigh(q, d, H[q], E0[q], &Vc[q], &Vr[q], err);
+    } else if (m.is_complex) {
       st = jacobi_eigh_cplx(d, H[q], E0[q], Vc[q]);
     } else {
       std::vector<double> A(size_t(d) * d);
       for (size_t i = 0; i < A.size(); ++i) A[i] = H[q][i].real();
       st = jacobi_eigh_real(d, A, E0[q], Vr[q]);
     }
-    if (st != CTQ_OK) { err = "eigensolver did not converge"; return st; }
+    if (st != CTQ_OK) {
+      if (err.empty()) err = "eigensolver did not converge";
+      return st;
+    }
     std::vector<cplx>().swap(H[q]);
   }
 
@@ -400,6 +413,18 @@ int build_host_model(const ctq_model_params* p, HostModel& m, std::string& err) 
       total += int64_t(dp) * dq;
       m.blk_re.resize(size_t(total), 0.0);
       if (m.is_complex) m.blk_im.resize(size_t(total), 0.0);
+      if (on_device) {
+        std::vector<int> src, dst;
+        std::vector<double> sg;
+        for (const auto& pr : pairs) {
+          src.push_back(pr.first);
+          dst.push_back(pr.second.first);
+          sg.push_back(pr.second.second);
+        }
+        const int st = dla.block(q, qp, src, dst, sg, &m.blk_re[base], m.is_complex ? &m.blk_im[base] : nullptr, err);
+        if (st != CTQ_OK) return st;
+        continue;
+      }
       for (const auto& pr : pairs) {
         const int j = pr.first, k = pr.second.first;
         const double sg = pr.second.second;

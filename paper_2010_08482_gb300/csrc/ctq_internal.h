@@ -39,6 +39,28 @@ int build_host_model(const ctq_model_params* p, HostModel& m, std::string& err);
 int jacobi_eigh_real(int n, std::vector<double>& A, std::vector<double>& E, std::vector<double>& V);
 int jacobi_eigh_cplx(int n, std::vector<cplx>& A, std::vector<double>& E, std::vector<cplx>& V);
 
+// Set-up linear algebra for sectors too large for the host Jacobi solver
+// (eigen_device.cu): cuSOLVER eigensolver and cuBLAS block transforms on the
+// impurity's device, libraries loaded on first use.
+class DeviceSectorLA {
+ public:
+  DeviceSectorLA();
+  ~DeviceSectorLA();
+  int init(int device, bool cplx, int n_sec, std::string& err);
+  int eigh(int q, int n, const std::vector<cplx>& H, std::vector<double>& E, std::vector<cplx>* Vc,
+           std::vector<double>* Vr, std::string& err);
+  bool has(int q) const;
+  int block(int q, int qp, const std::vector<int>& src, const std::vector<int>& dst, const std::vector<double>& sg,
+            double* re, double* im, std::string& err);
+
+ private:
+  struct Impl;
+  Impl* impl_;
+};
+
+// Sectors above this dimension are diagonalised on the device.
+constexpr int kJacobiMaxDim = 160;
+
 // Device-side view of a model (all pointers on the model's device).
 struct DevModel {
   int n_flav, n_alpha, n_sec, max_dim, is_complex;
