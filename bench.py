@@ -41,9 +41,11 @@ WORKLOAD_TEXT = {
     "hubbard2": "2-orbital Kanamori (4 spin-orbitals, 9 sectors), U=4, J=0.5, mu=U/2, beta=10; 64 chains, k in 8..20",
     "d5": "5-orbital d-shell Slater-Condon (10 spin-orbitals, 36 sectors, largest block 100), U=8, J=1, "
           "real CF sigma=0.1, beta=40; 1024 chains, order ~Poisson(60)",
+    "f7": "7-orbital f-shell Slater-Condon with SOC 0.3 and complex CF sigma=0.05 (14 spin-orbitals, N in {4,5,6}, "
+          "sectors 1001/2002/3003, complex), U=4.5, J=0.5, beta=40; 256 chains, order ~Poisson(80)",
 }
-CPU_SAMPLE = {"t2g": 4096, "hubbard2": 64, "d5": 24}       # cpu_baseline leg (~5-30 s)
-CPU_SAMPLE_REF = {"t2g": 64, "hubbard2": 64, "d5": 2}      # per step of --impl reference
+CPU_SAMPLE = {"t2g": 4096, "hubbard2": 64, "d5": 24, "f7": 1}  # cpu_baseline leg (~5-120 s)
+CPU_SAMPLE_REF = {"t2g": 64, "hubbard2": 64, "d5": 2, "f7": 1}  # per step of --impl reference
 FLUSH_BYTES = 256 << 20
 
 
@@ -244,6 +246,7 @@ def main():
     ap.add_argument("--workload", default="t2g", choices=sorted(WORKLOAD_TEXT))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "tf32x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--chains", type=int, default=0, help="evaluate only the first N chains of the workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -260,6 +263,8 @@ def main():
     mf, bf = w.WORKLOADS[args.workload]
     params = mf()
     batch = bf(rank=rank)  # each rank evaluates its own independent batch (weak scaling)
+    if args.chains:
+        batch = batch.subset(range(min(args.chains, batch.n_chains)))
     imp = ctq.build_impurity(params, device=local)
     db = ctq.DeviceBatch(batch, device=dev)
     prec = {"fp64": ctq.FP64, "tf32": ctq.TF32, "tf32x3": ctq.TF32X3}[args.precision]
@@ -308,7 +313,8 @@ def main():
     e_end = torch.cuda.Event(enable_timing=True)
     e2e_ms = []
     n_ops = len(batch.tau)
-    for i in range(args.warmup + max(10, args.steps // 4)):
+    e2e_warm = min(args.warmup, 2)
+    for i in range(e2e_warm + args.steps):
         flush.zero_()
         e_start.record(stream)
         db.offsets.copy_(h_off, non_blocking=True)
@@ -320,7 +326,7 @@ def main():
         h_st.copy_(ev.status, non_blocking=True)
         e_end.record(stream)
         e_end.synchronize()
-        if i >= args.warmup:
+        if i >= e2e_warm:
             e2e_ms.append(e_start.elapsed_time(e_end))
     clocks.stop()
     h2d = h_off.numel() * 4 + h_tau.numel() * 8 + h_op.numel() * 4
@@ -348,7 +354,8 @@ def main():
         "dtype": {"fp64": "f64", "tf32": "tf32 (fp32 accumulate, f64 log scale)",
                   "tf32x3": "3xtf32 (fp32 accumulate, f64 log scale)"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_TEXT[args.workload], "n_chains": batch.n_chains,
+        "config": {"workload": WORKLOAD_TEXT[args.workload] + (f" (first {batch.n_chains} chains)" if args.chains else ""),
+                   "n_chains": batch.n_chains,
                    "surviving_strings": n_items, "precision": args.precision,
                    "l2": "flushed (256 MiB write) between steps",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},

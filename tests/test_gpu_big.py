@@ -91,3 +91,44 @@ def test_big_engine_bounds_bracket(small_models):
         bd = res["bounds"][c]
         fin = bd[np.isfinite(bd)]
         assert np.all(fin >= ref[c]["log_abs"] - 1e-3)
+
+
+def _f7_golden():
+    path = os.path.join(HERE, "golden", "f7_oracle.json")
+    if not os.path.exists(path):
+        pytest.skip("tests/golden/f7_oracle.json not generated")
+    with open(path) as f:
+        return json.load(f)
+
+
+@pytest.fixture(scope="module")
+def f7_impurity():
+    return ctq.build_impurity(w.model_f7(), device=0)
+
+
+def test_f7_build_matches_stored_oracle_spectrum(f7_impurity):
+    """Library-built f shell (device eigensolver for the 1001 / 2002 / 3003
+    sectors): sector sizes, chemical potential and ground-state energy agree
+    with the oracle's stored values."""
+    g = _f7_golden()
+    dims, N, Emin, s = f7_impurity.sectors()
+    assert list(dims) == g["dims"]
+    assert f7_impurity.mu == pytest.approx(g["mu"], abs=1e-9)
+    assert f7_impurity.E_gs == pytest.approx(g["E_gs"], abs=1e-9)
+    assert f7_impurity.is_complex
+
+
+@pytest.mark.parametrize("precision", [ctq.TF32X3, ctq.TF32])
+def test_f7_traces_against_stored_oracle(precision, f7_impurity):
+    g = _f7_golden()
+    n = len(g["chains"])
+    b = w.batch_f7().subset(range(n))
+    res = run(f7_impurity, b, precision)
+    errs = []
+    for c, ref in enumerate(g["chains"]):
+        r = {"log_abs": ref["log_abs"], "phase": complex(*ref["phase"]), "per_q0": {}}
+        err = abs(complex(*res["phase"][c]) * math.exp(res["log_abs"][c] - r["log_abs"]) - r["phase"])
+        errs.append(err)
+        assert err <= STATED[("f7", precision)], (c, err)
+        assert res["status"][c] == ctq.CHAIN_OK
+    print(f"f7 precision={precision}: n={len(errs)} max rel err {max(errs):.3e}, median {np.median(errs):.3e}")
