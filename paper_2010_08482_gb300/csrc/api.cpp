@@ -91,6 +91,7 @@ int upload_model(ctq_impurity* imp) {
   std::vector<double> e_rel(h.E.size());
   for (int q = 0; q < h.n_sec; ++q)
     for (int j = h.E_off[q]; j < h.E_off[q + 1]; ++j) e_rel[j] = h.E[j] - h.E_min[q];
+  std::vector<float> e_relf(e_rel.begin(), e_rel.end());
   std::vector<double> blk;
   if (h.is_complex) {
     blk.resize(2 * h.blk_re.size());
@@ -105,7 +106,8 @@ int upload_model(ctq_impurity* imp) {
   for (size_t i = 0; i < lognorm.size(); ++i) lognorm[i] = h.opnorm[i] > 0 ? std::log(h.opnorm[i]) : -INFINITY;
   int st = CTQ_OK;
   if ((st = upload_vec(imp, h.dims, &d.dims)) || (st = upload_vec(imp, h.E_off, &d.E_off)) ||
-      (st = upload_vec(imp, e_rel, &d.E_rel)) || (st = upload_vec(imp, h.E_min, &d.E_min)) ||
+      (st = upload_vec(imp, e_rel, &d.E_rel)) || (st = upload_vec(imp, e_relf, &d.E_relf)) ||
+      (st = upload_vec(imp, h.E_min, &d.E_min)) ||
       (st = upload_vec(imp, h.s, &d.s)) || (st = upload_vec(imp, h.blk_off, &d.blk_off)) ||
       (st = upload_vec(imp, blk, &d.blk)) || (st = upload_vec(imp, lognorm, &d.log_norm))) {
     free_device(imp);

@@ -68,6 +68,7 @@ struct DevModel {
   const int* dims;      // [n_sec]
   const int* E_off;     // [n_sec + 1]
   const double* E_rel;  // [sum dims]  E_q,j - E_min(q)  (>= 0)
+  const float* E_relf;  // [sum dims]  the same in float32 (mixed-precision propagators)
   const double* E_min;  // [n_sec]
   const int* s;         // [n_alpha * n_sec]
   const int64_t* blk_off;  // [n_alpha * n_sec]  element offsets, -1 absent

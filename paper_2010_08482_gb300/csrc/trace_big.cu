@@ -85,6 +85,11 @@ __device__ __forceinline__ bool grid_sync(unsigned* count, volatile unsigned* ge
 }
 
 constexpr int MAX_NST = 6;
+// The K loop of a product is spread over NACC tensor-memory accumulators
+// (chunk kc into accumulator kc % NACC) that the epilogue adds in FP32: each
+// accumulator then sums 1/NACC of the K' terms, which divides the
+// accumulation error of long products (K' up to ~6000) by about NACC.
+constexpr int NACC = 4;
 constexpr int PVEC = 3072;    // largest sector dimension of this path
 
 struct BigShared {
@@ -124,7 +129,7 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
     S.fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) tmem_alloc(&S.tmem_base, 256);
+  if (warp == 0) tmem_alloc(&S.tmem_base, NACC * BN);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -393,10 +398,11 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
             for (int kk = 0; kk < BK / 8; ++kk) {
               const uint64_t da = sdesc(sa + kk * 2 * 2048, 2048, 128);
               const uint64_t dbh = sdesc(sbh + kk * 2 * 2048, 2048, 128);
-              mma_tf32_ss(tD, da, dbh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+              const uint32_t tacc = tD + uint32_t(kc % NACC) * BN;
+              mma_tf32_ss(tacc, da, dbh, idesc, (kc >= NACC || kk > 0) ? 1u : 0u);
               if (SPLIT == 3) {
-                mma_tf32_ss(tD, da, sdesc(sbl + kk * 2 * 2048, 2048, 128), idesc, 1u);
-                mma_tf32_ss(tD, sdesc(sal + kk * 2 * 2048, 2048, 128), dbh, idesc, 1u);
+                mma_tf32_ss(tacc, da, sdesc(sbl + kk * 2 * 2048, 2048, 128), idesc, 1u);
+                mma_tf32_ss(tacc, sdesc(sal + kk * 2 * 2048, 2048, 128), dbh, idesc, 1u);
               }
             }
             mma_commit(&S.empty[st]);
@@ -423,16 +429,29 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
         tc_fence_after();
         // epilogue: thread = row of the tile
         const int row = mt * BM + tid;
+        const int nacc = min(NACC, nkc);
         for (int c0 = 0; c0 < ncols; c0 += 16) {
-          uint32_t v[16];
-          tmem_ld16(tD + lane_off + c0, v);
-          tmem_wait_ld();
+          float acc[16];
+          {
+            uint32_t v[16];
+            tmem_ld16(tD + lane_off + c0, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int t2 = 0; t2 < 16; ++t2) acc[t2] = __uint_as_float(v[t2]);
+          }
+          for (int a = 1; a < nacc; ++a) {
+            uint32_t v[16];
+            tmem_ld16(tD + uint32_t(a * BN) + lane_off + c0, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int t2 = 0; t2 < 16; ++t2) acc[t2] += __uint_as_float(v[t2]);
+          }
           float hi[16], lo[16];
 #pragma unroll
           for (int t2 = 0; t2 < 16; ++t2) {
             const int col = nt * BN + c0 + t2;  // embedded column
             const int j = (col < dpn) ? col : col - dpn;
-            const float x = __uint_as_float(v[t2]) * p_s[j];
+            const float x = acc[t2] * p_s[j];
             ek = max(ek, (__float_as_int(x) >> 23) & 0xff);
             f2 += x * x;
             const uint32_t h = to_tf32(x);
@@ -481,7 +500,7 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tD, 256);
+    tmem_dealloc(tD, NACC * BN);
   }
 }
 

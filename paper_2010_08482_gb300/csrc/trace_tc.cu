@@ -180,11 +180,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     {
       const double dt = B.tau[a0 + 1] - B.tau[a0];
-      const double* Eb = M.E_rel + M.E_off[qb];
+      const float* Eb = M.E_relf + M.E_off[qb];
+      const float* E0f = M.E_relf + M.E_off[q0];
       const int db = M.dims[qb];
       for (int j = tid; j < TC_M; j += TC_THREADS) {
-        p_s[j] = (j < db) ? float(exp(-dt * Eb[j])) : 0.0f;
-        p0_s[j] = (j < d0) ? float(exp(-t_first * E0[j]) * exp(-t_last * E0[j])) : 0.0f;
+        // FP32 exponentials: an absolute argument error of ~1e-7 x changes
+        // e^{-x} by at most max(x e^{-x}) 1e-7 < 4e-8 relative to the largest
+        // entry, below the resolution of the products.
+        p_s[j] = (j < db) ? __expf(-float(dt) * Eb[j]) : 0.0f;
+        p0_s[j] = (j < d0) ? __expf(-float(t_first) * E0f[j]) * __expf(-float(t_last) * E0f[j]) : 0.0f;
       }
       if (tid == 0) {
         L.add(-dt * (M.E_min[qb] - M.E_ref));
@@ -349,8 +353,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       // column scales of this step (overlaps the MMA)
       {
         const double dt = B.tau[a0 + i + 1] - B.tau[a0 + i];
-        const double* Eb = M.E_rel + M.E_off[qb];
-        for (int j = tid; j < TC_M; j += TC_THREADS) p_s[j] = (j < db) ? float(exp(-dt * Eb[j])) * scale : 0.0f;
+        const float* Eb = M.E_relf + M.E_off[qb];
+        const float dtf = float(dt);
+        for (int j = tid; j < TC_M; j += TC_THREADS) p_s[j] = (j < db) ? __expf(-dtf * Eb[j]) * scale : 0.0f;
         if (tid == 0) {
           L.add(-dt * (M.E_min[qb] - M.E_ref));
           prefix -= dt * (M.E_min[qb] - M.E_ref);

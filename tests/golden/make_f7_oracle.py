@@ -28,10 +28,9 @@ def main():
     for c in range(n):
         tau, ops = b.chain(c)
         r = OT.trace_chain(m, tau, ops, beta=b.beta)
-        B, ub = OT.chain_bounds(m, tau, ops, b.beta, 8)
         out["chains"].append({"chain": c, "n_ops": len(ops), "log_abs": r["log_abs"],
                               "phase": [float(complex(r["phase"]).real), float(complex(r["phase"]).imag)],
-                              "q0": sorted(int(q) for q in r["per_q0"]), "level0_bound": B})
+                              "q0": sorted(int(q) for q in r["per_q0"])})
         print(c, len(ops), r["log_abs"], time.time() - t0, flush=True)
     with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "f7_oracle.json"), "w") as f:
         json.dump(out, f, indent=1)
