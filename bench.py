@@ -41,6 +41,8 @@ WORKLOAD_TEXT = {
     "hubbard2": "2-orbital Kanamori (4 spin-orbitals, 9 sectors), U=4, J=0.5, mu=U/2, beta=10; 64 chains, k in 8..20",
     "d5": "5-orbital d-shell Slater-Condon (10 spin-orbitals, 36 sectors, largest block 100), U=8, J=1, "
           "real CF sigma=0.1, beta=40; 1024 chains, order ~Poisson(60)",
+    "mixed": "uneven mixed batch: 2048 chains over the t2g, d5 and f7 models (uniform), orders uniform in 10-200, "
+             "lazy bounds on, fair coin per chain: threshold +inf (reject at level 0) or -inf (full trace, accepted)",
     "f7": "7-orbital f-shell Slater-Condon with SOC 0.3 and complex CF sigma=0.05 (14 spin-orbitals, N in {4,5,6}, "
           "sectors 1001/2002/3003, complex), U=4.5, J=0.5, beta=40; 256 chains, order ~Poisson(80)",
 }
@@ -237,6 +239,75 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_mixed(args, world, rank, local):
+    """The uneven mixed batch: chains of three impurities evaluated on one
+    stream (one ctq_eval_traces per impurity), lazy bounds on.  The coin of
+    each chain sets its threshold to +inf (every bound falls below it: level-0
+    reject) or -inf (never rejected: full trace, accepted), which reproduces
+    the intended 50 % early rejects without an oracle pass."""
+    import torch
+    from paper_2010_08482_gb300 import ctq
+    from paper_2010_08482_gb300 import workloads as w
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    batch, coin = w.batch_mixed()
+    if args.chains:
+        keep = np.arange(min(args.chains, batch.n_chains))
+        batch, coin = batch.subset(keep), coin[keep]
+    models = [w.model_t2g(), w.model_d5(), w.model_f7()]
+    prec = {"fp64": ctq.FP64, "tf32": ctq.TF32, "tf32x3": ctq.TF32X3}[args.precision]
+    groups, flops = [], 0.0
+    for mi, p in enumerate(models):
+        idx = np.nonzero(batch.model == mi)[0]
+        if idx.size == 0:
+            continue
+        if prec == ctq.FP64 and p.name == "f7":
+            continue  # no FP64 large-block path
+        sub = batch.subset(idx)
+        sub.beta = p.beta  # the mixed batch draws each chain's times in [0, beta) of its own model
+        thr = np.where(coin[idx] == 1, np.inf, -np.inf)
+        imp = ctq.build_impurity(p, device=local)
+        db = ctq.DeviceBatch(sub, device=dev, log_threshold=thr)
+        ev = ctq.TraceEvaluator(imp, sub.n_chains, db.max_ops, precision=prec, device=dev)
+        f, _ = algorithmic_flops(imp, sub.subset(np.nonzero(coin[idx] == 0)[0]))
+        flops += f
+        groups.append((p.name, imp, db, ev, sub.n_chains))
+    n_chains = sum(g[4] for g in groups)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def step():
+        for _, _, db, ev, _ in groups:
+            ev(db, lazy=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = []
+    for _ in range(args.steps):
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clocks.stop()
+    status = {g[0]: np.bincount(g[3].results(g[4])["status"] + 1, minlength=6)[1:].tolist() for g in groups}
+    mean = statistics.mean(ms)
+    line = {"metric": METRIC, "value": n_chains / (mean * 1e-3), "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT["mixed"], "n_chains": n_chains,
+                       "groups": {g[0]: g[4] for g in groups}, "precision": args.precision},
+            "tflops": flops / (mean * 1e-3) / 1e12, "algorithmic_flops_per_step": flops,
+            "status_counts [ok, zero, rejected_early, accepted, rejected]": status,
+            "gpu_launches": args.steps * sum(ctq.launches_per_eval(g[1]) for g in groups),
+            "clocks": clocks.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -254,6 +325,9 @@ def main():
         run_reference(args, world, rank)
         return
 
+    if args.workload == "mixed":
+        run_mixed(args, world, rank, local)
+        return
     import torch
     from paper_2010_08482_gb300 import ctq
     from paper_2010_08482_gb300 import workloads as w
