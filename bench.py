@@ -436,7 +436,7 @@ def main():
         "tflops": flops / (ms * 1e-3) / 1e12,
         "algorithmic_flops_per_step": flops,
         "kernel_ms": {"plan": statistics.mean(kern_ms[0]), "trace": trace_ms, "combine": statistics.mean(kern_ms[2])},
-        "roofline": roofline(args.precision, achieved_tf, fp64_peak, traffic),
+        "roofline": roofline(args.precision, achieved_tf, fp64_peak, traffic, big=imp.is_complex or imp.max_dim > 112),
         "e2e": {"value": world * batch.n_chains / (e2e * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * launches,
@@ -454,7 +454,7 @@ def main():
         dist.destroy_process_group()
 
 
-def roofline(precision, achieved_tf, fp64_peak, traffic):
+def roofline(precision, achieved_tf, fp64_peak, traffic, big=False):
     """Roofline of the dominant kernel: the FP64 pipe for the FP64 path
     (measured FMA rate), the TF32 tensor pipe for the mixed paths (measured
     bf16 dense peak x 1/2, the nominal TF32:BF16 ratio)."""
@@ -465,7 +465,7 @@ def roofline(precision, achieved_tf, fp64_peak, traffic):
     peaks, src = load_peaks()
     peak = 0.5 * peaks["bf16_tflops"]
     passes = 3 if precision == "tf32x3" else 1
-    return {"kernel": f"k_trace_tc<{passes}>", "bound": "tensor", "achieved": achieved_tf, "peak": peak,
+    return {"kernel": f"k_trace_big<{passes}>" if big else f"k_trace_tc<{passes}>", "bound": "tensor", "achieved": achieved_tf, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved_tf / peak, "hardware_passes": passes,
             "peak_source": f"{src} bf16 dense x 0.5 (nominal TF32:BF16 ratio), MEASURED_PEAKS.json",
             "traffic": traffic}
