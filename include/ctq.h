@@ -51,6 +51,13 @@ extern "C" {
 #define CTQ_CHAIN_ACCEPTED 3       /* full trace, log|w| >= threshold           */
 #define CTQ_CHAIN_REJECTED 4       /* full trace, log|w| <  threshold           */
 #define CTQ_CHAIN_ERR_ARG (-1)     /* malformed sequence (see ctq_batch)        */
+#define CTQ_CHAIN_ERR_TIMEOUT (-4) /* a bounded device wait expired: no result  */
+
+/* ---- ctq_eval_opts.debug_flags ------------------------------------------- */
+#define CTQ_DEBUG_STALL_WAIT 1 /* tensor-core kernels first wait on an event that
+                                  never happens (bounded by timeout_ns), to test
+                                  the timeout path; every chain then reports
+                                  CTQ_CHAIN_ERR_TIMEOUT */
 
 /* ---- enums ------------------------------------------------------------------ */
 #define CTQ_KANAMORI 0 /* U, U' = U - 2J, J (rotationally invariant Kanamori)    */
@@ -182,6 +189,9 @@ typedef struct {
  * timing_events (nullable): ctq_launches_per_eval() + 1 cudaEvent_t handles,
  *   recorded on `stream` before the first kernel and after each kernel, so a
  *   caller can time every kernel of the evaluation on its launching stream.
+ * debug_flags: 0, or CTQ_DEBUG_STALL_WAIT (test of the timeout path).
+ * When a bounded wait expires, every chain of the call gets
+ * CTQ_CHAIN_ERR_TIMEOUT (log_abs NaN); the context stays usable.
  */
 typedef struct {
   int precision;
@@ -190,6 +200,7 @@ typedef struct {
   int max_ops;
   int64_t timeout_ns;
   void* const* timing_events;
+  int32_t debug_flags;
 } ctq_eval_opts;
 
 /*

@@ -450,6 +450,7 @@ int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_e
   // n u for n products: TF32 (u = 2^-11, n <= 400) and 3xTF32 (u ~ 2^-22).
   cfg.margin = opts->precision == CTQ_FP64 ? 1e-9 : (opts->precision == CTQ_TF32 ? 0.5 : 1e-2);
   cfg.bounds = result->bounds;
+  cfg.debug = opts->debug_flags;
   int st;
   if (opts->precision == CTQ_FP64) {
     st = ctq::launch_eval_fp64(imp->dev, imp->launch, B, cfg, W, result, stream, opts->timing_events);

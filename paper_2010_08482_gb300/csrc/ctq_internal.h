@@ -93,6 +93,7 @@ struct EvalCfg {
   int max_ops;      // longest chain allowed (longer chains are flagged invalid)
   double margin;    // safety margin (log units) applied to bounds before rejecting
   double* bounds;   // result bounds [C x (n_seg_max + 1)] or nullptr
+  int debug;        // ctq_eval_opts.debug_flags
 };
 
 // A work item: one surviving (chain, q0) string.

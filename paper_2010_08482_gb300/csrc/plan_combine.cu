@@ -146,6 +146,17 @@ __global__ void k_combine(DevModel M, BatchView B, EvalCfg cfg, Work W, ctq_resu
   const int ns = M.n_sec;
   const int flag = W.chain_flag[c];
   const int nb = cfg.n_seg_max + 1;
+  if (W.counters[2] != 0) {  // a bounded wait expired in the trace kernel
+    if (lane == 0) {
+      R.log_abs[c] = NAN;
+      R.phase[2 * c] = 0.0;
+      R.phase[2 * c + 1] = 0.0;
+      R.status[c] = (flag & FLAG_INVALID) ? CTQ_CHAIN_ERR_ARG : CTQ_CHAIN_ERR_TIMEOUT;
+    }
+    if (cfg.bounds)
+      for (int s = lane; s < nb; s += 32) cfg.bounds[size_t(c) * nb + s] = NAN;
+    return;
+  }
   if (flag & (FLAG_INVALID | FLAG_REJECTED)) {
     if (lane == 0) {
       R.log_abs[c] = NAN;

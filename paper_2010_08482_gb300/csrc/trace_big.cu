@@ -96,6 +96,7 @@ struct BigShared {
   uint64_t full[MAX_NST];
   uint64_t empty[MAX_NST];
   uint64_t done;
+  uint64_t never;  // never arrived on: CTQ_DEBUG_STALL_WAIT waits on it
   uint32_t tmem_base;
   int fail;
   float red[8];
@@ -126,6 +127,7 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
       mbar_init(&S.empty[i], 1);
     }
     mbar_init(&S.done, 1);
+    mbar_init(&S.never, 1);
     S.fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -138,6 +140,13 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
   uint32_t ph_full[MAX_NST] = {0, 0, 0, 0, 0, 0}, ph_empty[MAX_NST] = {0, 0, 0, 0, 0, 0};
   uint32_t ph_done = 0;
   bool alive = true;
+  if (cfg.debug & CTQ_DEBUG_STALL_WAIT) {
+    // CTA 0 waits on an event that never happens; the others then time out
+    // in the first grid barrier.
+    if (blockIdx.x == 0 && tid == 0 && !mbar_wait(&S.never, 0, P.timeout_ns)) S.fail = 1;
+    __syncthreads();
+    if (S.fail) alive = false;
+  }
 
   const int n_items = W.counters[0];
   const Item* items = W.items + size_t(B.n_chains) * ns;

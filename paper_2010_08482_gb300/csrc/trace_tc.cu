@@ -62,6 +62,7 @@ __device__ __forceinline__ int round_up(int x, int m) { return (x + m - 1) / m *
 struct TcShared {
   uint64_t bar_load[2];
   uint64_t bar_mma;
+  uint64_t bar_never;  // never arrived on: CTQ_DEBUG_STALL_WAIT waits on it
   uint32_t tmem_base;
   int item;
   int abort_flag;
@@ -94,6 +95,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     mbar_init(&S.bar_load[0], 1);
     mbar_init(&S.bar_load[1], 1);
     mbar_init(&S.bar_mma, 1);
+    mbar_init(&S.bar_never, 1);
     S.fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -105,6 +107,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  if ((cfg.debug & CTQ_DEBUG_STALL_WAIT) && tid == 0 && !mbar_wait(&S.bar_never, 0, P.timeout_ns)) {
+    S.fail = 1;  // expected: nothing arrives on bar_never
+    atomicOr(&W.counters[2], 1);
+  }
+  __syncthreads();
   const uint32_t tbase = S.tmem_base;
   const uint32_t lane_off = uint32_t(32 * warp) << 16;
   const uint32_t tD = tbase;          // D: columns [0, 128)

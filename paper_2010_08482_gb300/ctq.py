@@ -23,7 +23,8 @@ CTQ_ERR_ARG, CTQ_ERR_NOMEM, CTQ_ERR_CUDA, CTQ_ERR_TIMEOUT = -1, -2, -3, -4
 CTQ_ERR_UNSUPPORTED, CTQ_ERR_NUMERIC, CTQ_ERR_WORKSPACE = -5, -6, -7
 
 CHAIN_OK, CHAIN_ZERO, CHAIN_REJECTED_EARLY, CHAIN_ACCEPTED, CHAIN_REJECTED = 0, 1, 2, 3, 4
-CHAIN_ERR_ARG = -1
+CHAIN_ERR_ARG, CHAIN_ERR_TIMEOUT = -1, -4
+DEBUG_STALL_WAIT = 1
 
 KANAMORI, SLATER = 0, 1
 MU_GIVEN, MU_PH_SYMMETRIC = 0, 1
@@ -58,7 +59,7 @@ class BatchC(ctypes.Structure):
 
 class EvalOptsC(ctypes.Structure):
     _fields_ = [("precision", c_int), ("lazy", c_int), ("segment", c_int), ("max_ops", c_int),
-                ("timeout_ns", c_int64), ("timing_events", c_void_p)]
+                ("timeout_ns", c_int64), ("timing_events", c_void_p), ("debug_flags", c_int32)]
 
 
 class ResultC(ctypes.Structure):
@@ -238,10 +239,11 @@ def load_impurity(n_flav: int, dims, N, energies, s_table, blocks, mu: float = 0
     return Impurity(h)
 
 
-def _opts(precision=FP64, lazy=False, segment=8, max_ops=0, timeout_ns=0, events=None) -> EvalOptsC:
+def _opts(precision=FP64, lazy=False, segment=8, max_ops=0, timeout_ns=0, events=None, debug_flags=0) -> EvalOptsC:
     o = EvalOptsC()
     o.precision, o.lazy, o.segment, o.max_ops, o.timeout_ns = precision, int(lazy), segment, max_ops, timeout_ns
     o.timing_events = events
+    o.debug_flags = debug_flags
     return o
 
 
@@ -257,7 +259,7 @@ def launches_per_eval(imp: Impurity, precision=FP64) -> int:
 
 def eval_traces(imp: Impurity, n_chains: int, beta: float, offsets, tau, op, log_threshold,
                 log_abs, phase, status, bounds, workspace, workspace_bytes: int, stream,
-                precision=FP64, lazy=False, segment=8, max_ops=0, timeout_ns=0, events=None):
+                precision=FP64, lazy=False, segment=8, max_ops=0, timeout_ns=0, events=None, debug_flags=0):
     """ctq_eval_traces with raw device pointers (ints) and a cudaStream_t (int);
     events: optional address of an array of cudaEvent_t handles (see ctq.h)."""
     b = BatchC()
@@ -265,7 +267,7 @@ def eval_traces(imp: Impurity, n_chains: int, beta: float, offsets, tau, op, log
     b.offsets, b.tau, b.op, b.log_threshold = offsets, tau, op, log_threshold
     r = ResultC()
     r.log_abs, r.phase, r.status, r.bounds = log_abs, phase, status, bounds
-    o = _opts(precision, lazy, segment, max_ops, timeout_ns, events)
+    o = _opts(precision, lazy, segment, max_ops, timeout_ns, events, debug_flags)
     _check(_lib.ctq_eval_traces(imp.handle, ctypes.byref(b), ctypes.byref(o), ctypes.byref(r),
                                 workspace, workspace_bytes, stream), "ctq_eval_traces")
 
@@ -336,7 +338,7 @@ class TraceEvaluator:
         self.bounds = (torch.empty(n_chains * (self.n_seg + 1), dtype=torch.float64, device=device)
                        if with_bounds else None)
 
-    def __call__(self, db: DeviceBatch, lazy=False, stream=None, events=None):
+    def __call__(self, db: DeviceBatch, lazy=False, stream=None, events=None, timeout_ns=0, debug_flags=0):
         import torch
         if db.n_chains > self.n_chains or db.max_ops > self.max_ops:
             raise ValueError("batch larger than the evaluator was sized for")
@@ -346,7 +348,7 @@ class TraceEvaluator:
                     thr, self.log_abs.data_ptr(), self.phase.data_ptr(), self.status.data_ptr(),
                     self.bounds.data_ptr() if self.bounds is not None else None,
                     self.ws_ptr, self.ws_bytes, s.cuda_stream, self.precision, lazy, self.segment, self.max_ops,
-                    0, events)
+                    timeout_ns, events, debug_flags)
 
     def results(self, n_chains: Optional[int] = None):
         n = self.n_chains if n_chains is None else n_chains
