@@ -34,6 +34,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# --precision names and their ctq precision codes (ctq.FP64 = 0, TF32 = 1, BF16X3 = 2, TF32X3 = 3).
+PRECISIONS = {"fp64": 0, "tf32": 1, "bf16x3": 2, "tf32x3": 3}
 METRIC = "local-trace evals/s and TFLOP/s vs peak, FP64 vs mixed at stated error, 1×GB300"
 WORKLOAD_TEXT = {
     "t2g": "3-orbital t2g Kanamori (6 spin-orbitals, Fock dim 64, 16 (N_dn,N_up) sectors, blocks<=9), "
@@ -257,7 +259,7 @@ def run_mixed(args, world, rank, local):
         keep = np.arange(min(args.chains, batch.n_chains))
         batch, coin = batch.subset(keep), coin[keep]
     models = [w.model_t2g(), w.model_d5(), w.model_f7()]
-    prec = {"fp64": ctq.FP64, "tf32": ctq.TF32, "tf32x3": ctq.TF32X3}[args.precision]
+    prec = PRECISIONS[args.precision]
     groups, flops = [], 0.0
     for mi, p in enumerate(models):
         idx = np.nonzero(batch.model == mi)[0]
@@ -270,7 +272,9 @@ def run_mixed(args, world, rank, local):
         thr = np.where(coin[idx] == 1, np.inf, -np.inf)
         imp = ctq.build_impurity(p, device=local)
         db = ctq.DeviceBatch(sub, device=dev, log_threshold=thr)
-        ev = ctq.TraceEvaluator(imp, sub.n_chains, db.max_ops, precision=prec, device=dev)
+        big = imp.is_complex or imp.max_dim > 112
+        gprec = ctq.TF32X3 if (prec == ctq.BF16X3 and not big) else prec  # bf16x3: large-block engine only
+        ev = ctq.TraceEvaluator(imp, sub.n_chains, db.max_ops, precision=gprec, device=dev)
         f, _ = algorithmic_flops(imp, sub.subset(np.nonzero(coin[idx] == 0)[0]))
         flops += f
         groups.append((p.name, imp, db, ev, sub.n_chains))
@@ -285,12 +289,32 @@ def run_mixed(args, world, rank, local):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    # The whole mixed evaluation (every impurity's plan / trace / combine
+    # launches) is captured once as a CUDA graph and replayed per step.
+    graph, graph_note = None, "captured"
+    try:
+        cap_stream = torch.cuda.Stream(device=dev)
+        cap_stream.wait_stream(stream)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cap_stream):
+            step()
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        graph = g
+    except Exception as exc:  # capture is refused: run the same launches eagerly
+        torch.cuda.synchronize()
+        graph_note = f"eager ({type(exc).__name__}: {str(exc)[:80]})"
+    run = graph.replay if graph is not None else step
+    for _ in range(2):
+        run()
+    torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     ms = []
     for _ in range(args.steps):
         e0.record(stream)
-        step()
+        run()
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
@@ -301,7 +325,8 @@ def run_mixed(args, world, rank, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT["mixed"], "n_chains": n_chains,
-                       "groups": {g[0]: g[4] for g in groups}, "precision": args.precision},
+                       "groups": {g[0]: g[4] for g in groups}, "precision": args.precision,
+                       "cuda_graph": graph_note},
             "tflops": flops / (mean * 1e-3) / 1e12, "algorithmic_flops_per_step": flops,
             "status_counts [ok, zero, rejected_early, accepted, rejected]": status,
             "gpu_launches": args.steps * sum(ctq.launches_per_eval(g[1]) for g in groups),
@@ -317,7 +342,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="t2g", choices=sorted(WORKLOAD_TEXT))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "tf32x3"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "tf32x3", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--chains", type=int, default=0, help="evaluate only the first N chains of the workload")
     args = ap.parse_args()
@@ -343,7 +368,7 @@ def main():
         batch = batch.subset(range(min(args.chains, batch.n_chains)))
     imp = ctq.build_impurity(params, device=local)
     db = ctq.DeviceBatch(batch, device=dev)
-    prec = {"fp64": ctq.FP64, "tf32": ctq.TF32, "tf32x3": ctq.TF32X3}[args.precision]
+    prec = PRECISIONS[args.precision]
     ev = ctq.TraceEvaluator(imp, batch.n_chains, db.max_ops, precision=prec, device=dev)
     flops, n_items = algorithmic_flops(imp, batch)
     launches = ctq.launches_per_eval(imp)
@@ -428,7 +453,8 @@ def main():
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": {"fp64": "f64", "tf32": "tf32 (fp32 accumulate, f64 log scale)",
-                  "tf32x3": "3xtf32 (fp32 accumulate, f64 log scale)"}[args.precision],
+                  "tf32x3": "3xtf32 (fp32 accumulate, f64 log scale)",
+                  "bf16x3": "3xbf16 (fp32 accumulate, f64 log scale)"}[args.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT[args.workload] + (f" (first {batch.n_chains} chains)" if args.chains else ""),
                    "n_chains": batch.n_chains,
@@ -458,18 +484,22 @@ def main():
 
 def roofline(precision, achieved_tf, fp64_peak, traffic, big=False):
     """Roofline of the dominant kernel: the FP64 pipe for the FP64 path
-    (measured FMA rate), the TF32 tensor pipe for the mixed paths (measured
-    bf16 dense peak x 1/2, the nominal TF32:BF16 ratio)."""
+    (measured FMA rate), the tensor pipe of the operand type for the mixed
+    paths: measured bf16 dense peak for bf16 operands, x 1/2 (the nominal
+    TF32:BF16 ratio) for tf32 operands."""
     if precision == "fp64":
         return {"kernel": "k_trace<fp64>", "bound": "alu", "achieved": achieved_tf, "peak": fp64_peak / 1e12,
                 "unit": "TFLOP/s", "frac": achieved_tf / (fp64_peak / 1e12),
                 "peak_source": "measured FP64 FMA rate (ctq_probe_fma_rate, this run)", "traffic": traffic}
     peaks, src = load_peaks()
-    peak = 0.5 * peaks["bf16_tflops"]
-    passes = 3 if precision == "tf32x3" else 1
-    return {"kernel": f"k_trace_big<{passes}>" if big else f"k_trace_tc<{passes}>", "bound": "tensor", "achieved": achieved_tf, "peak": peak,
+    bf16 = precision == "bf16x3"
+    peak = peaks["bf16_tflops"] * (1.0 if bf16 else 0.5)
+    passes = 1 if precision == "tf32" else 3
+    kernel = (f"k_trace_big<{precision}>" if big else f"k_trace_tc<{passes}>")
+    return {"kernel": kernel, "bound": "tensor", "achieved": achieved_tf, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved_tf / peak, "hardware_passes": passes,
-            "peak_source": f"{src} bf16 dense x 0.5 (nominal TF32:BF16 ratio), MEASURED_PEAKS.json",
+            "peak_source": (f"{src} bf16 dense, MEASURED_PEAKS.json" if bf16 else
+                            f"{src} bf16 dense x 0.5 (nominal TF32:BF16 ratio), MEASURED_PEAKS.json"),
             "traffic": traffic}
 
 

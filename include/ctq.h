@@ -179,9 +179,12 @@ typedef struct {
 } ctq_batch;
 
 /*
- * precision: CTQ_FP64 (any impurity); CTQ_TF32 and CTQ_TF32X3 (tensor cores,
- *   real impurities with sector blocks <= 112; CTQ_ERR_UNSUPPORTED otherwise);
- *   CTQ_BF16X3 is not built (CTQ_ERR_UNSUPPORTED).
+ * precision: CTQ_FP64 (any impurity).  CTQ_TF32 and CTQ_TF32X3 run on the
+ *   tensor cores: real impurities with sector blocks <= 112 states use the
+ *   small-block kernel, any other impurity with blocks <= 3072 states the
+ *   large-block kernel (complex blocks in their real embedding).  CTQ_BF16X3
+ *   (bf16 hi / lo operands, hi*hi + hi*lo + lo*hi) is built for the
+ *   large-block kernel only.  Other combinations: CTQ_ERR_UNSUPPORTED.
  * lazy: 1 = stop a chain as soon as its upper bound falls below its threshold
  *   (needs log_threshold).  segment: operators per bound refinement (>= 1).
  * max_ops: largest 2k in the batch (sizes the bounds output).
@@ -287,6 +290,19 @@ int ctq_probe_fma_rate(int device, int kind, int iters, double* flops_per_s);
  * Errors: CTQ_ERR_ARG, CTQ_ERR_NOMEM, CTQ_ERR_CUDA, CTQ_ERR_TIMEOUT.
  */
 int ctq_tc_gemm_check(int device, const float* A, const float* B, float* D, int N, int K, int split);
+
+/*
+ * Diagnostic of the large-block kernel's operand conventions: D = A B^T with
+ * A (host 128 x K row-major floats) and B (host N x K row-major floats) split
+ * and tiled on the device like the running product and the embedded blocks,
+ * staged chunk by chunk with bulk copies, and multiplied with the same
+ * descriptors and MMA kinds (precision CTQ_TF32, CTQ_TF32X3 or CTQ_BF16X3);
+ * D: host 128 x N row-major floats.  N in [16, 128], multiple of 16; K in
+ * [64, 4096], multiple of 64.  Allocates and frees device buffers and
+ * synchronises.  No counterpart in the paper.
+ * Errors: CTQ_ERR_ARG, CTQ_ERR_NOMEM, CTQ_ERR_CUDA, CTQ_ERR_TIMEOUT.
+ */
+int ctq_big_gemm_check(int device, const float* A, const float* B, float* D, int N, int K, int precision);
 
 const char* ctq_strerror(int code);
 

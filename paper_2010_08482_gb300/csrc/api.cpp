@@ -21,8 +21,8 @@ struct ctq_impurity {
   ctq::LaunchCfg launch_tc1{}, launch_tc3{};
   // large-block tensor-core path (complex impurities or blocks > 112)
   bool big = false;
-  ctq::BigParams big1{}, big3{};
-  ctq::LaunchCfg launch_big1{}, launch_big3{};
+  ctq::BigParams big1{}, big2{}, big3{};  // CTQ_TF32, CTQ_BF16X3, CTQ_TF32X3
+  ctq::LaunchCfg launch_big1{}, launch_big2{}, launch_big3{};
   std::vector<void*> allocs;
 };
 
@@ -139,7 +139,8 @@ int upload_model(ctq_impurity* imp) {
       return fail(st, "cannot configure the tensor-core kernel");
     }
   } else if (h.max_dim <= 3072) {
-    // large blocks: embedded, tiled, tf32-split copies formatted on the device
+    // large blocks: embedded, tiled, split copies formatted on the device,
+    // tf32 hi / lo (CTQ_TF32X3; CTQ_TF32 reads the hi planes) and bf16 hi / lo
     std::vector<int64_t> off(h.s.size(), -1);
     size_t total = 0;
     for (int a = 0; a < h.n_alpha(); ++a)
@@ -147,25 +148,35 @@ int upload_model(ctq_impurity* imp) {
         const size_t i = size_t(a) * h.n_sec + q;
         if (h.s[i] < 0) continue;
         off[i] = int64_t(total);
-        total += ctq::big_block_floats(h.dims[h.s[i]], h.dims[q]);
+        total += ctq::big_block_elems(h.dims[h.s[i]], h.dims[q]);
       }
-    void* bt = nullptr;
+    void *bt = nullptr, *bt16 = nullptr;
     if (cudaMalloc(&bt, std::max<size_t>(total, 1) * sizeof(float)) != cudaSuccess) {
       free_device(imp);
       return fail(CTQ_ERR_NOMEM, "cannot allocate the large-block operands");
     }
     imp->allocs.push_back(bt);
-    if ((st = ctq::format_big_blocks(h, d.blk, static_cast<float*>(bt), off)) != CTQ_OK ||
+    if (cudaMalloc(&bt16, std::max<size_t>(total, 1) * sizeof(uint16_t)) != cudaSuccess) {
+      free_device(imp);
+      return fail(CTQ_ERR_NOMEM, "cannot allocate the large-block operands");
+    }
+    imp->allocs.push_back(bt16);
+    if ((st = ctq::format_big_blocks(h, d.blk, bt, off, CTQ_TF32X3)) != CTQ_OK ||
+        (st = ctq::format_big_blocks(h, d.blk, bt16, off, CTQ_BF16X3)) != CTQ_OK ||
         (st = upload_vec(imp, off, &imp->big3.bt_off)) != CTQ_OK) {
       free_device(imp);
       return fail(st, "large-block formatting failed");
     }
-    imp->big3.bt = static_cast<const float*>(bt);
-    imp->big3.split = 3;
+    imp->big3.bt = bt;
+    imp->big3.prec = CTQ_TF32X3;
     imp->big1 = imp->big3;
-    imp->big1.split = 1;
-    if ((st = ctq::prepare_eval_big(3, imp->num_sms, &imp->launch_big3)) != CTQ_OK ||
-        (st = ctq::prepare_eval_big(1, imp->num_sms, &imp->launch_big1)) != CTQ_OK) {
+    imp->big1.prec = CTQ_TF32;
+    imp->big2 = imp->big3;
+    imp->big2.bt = bt16;
+    imp->big2.prec = CTQ_BF16X3;
+    if ((st = ctq::prepare_eval_big(CTQ_TF32X3, imp->num_sms, &imp->launch_big3)) != CTQ_OK ||
+        (st = ctq::prepare_eval_big(CTQ_TF32, imp->num_sms, &imp->launch_big1)) != CTQ_OK ||
+        (st = ctq::prepare_eval_big(CTQ_BF16X3, imp->num_sms, &imp->launch_big2)) != CTQ_OK) {
       free_device(imp);
       return fail(st, "cannot configure the large-block kernel");
     }
@@ -421,8 +432,11 @@ int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_e
   if (!result->log_abs || !result->phase || !result->status) return fail(CTQ_ERR_ARG, "null result array");
   if (opts->segment < 1 || opts->max_ops < 0) return fail(CTQ_ERR_ARG, "segment < 1 or max_ops < 0");
   if (opts->lazy && !batch->log_threshold) return fail(CTQ_ERR_ARG, "lazy evaluation needs thresholds");
-  if (opts->precision != CTQ_FP64 && opts->precision != CTQ_TF32 && opts->precision != CTQ_TF32X3)
-    return fail(CTQ_ERR_UNSUPPORTED, "precision not built");
+  if (opts->precision != CTQ_FP64 && opts->precision != CTQ_TF32 && opts->precision != CTQ_TF32X3 &&
+      opts->precision != CTQ_BF16X3)
+    return fail(CTQ_ERR_UNSUPPORTED, "unknown precision");
+  if (opts->precision == CTQ_BF16X3 && !imp->big)
+    return fail(CTQ_ERR_UNSUPPORTED, "CTQ_BF16X3 is built for the large-block path only");
   if (opts->precision != CTQ_FP64 && !imp->big &&
       (opts->precision == CTQ_TF32 ? imp->launch_tc1.per_sm : imp->launch_tc3.per_sm) < 1)
     return fail(CTQ_ERR_UNSUPPORTED, "no tensor-core path for this impurity");
@@ -448,18 +462,23 @@ int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_e
   // relative error of reduced-precision products over a chain.
   // Bounds are norms (no cancellation), so their relative error is about
   // n u for n products: TF32 (u = 2^-11, n <= 400) and 3xTF32 (u ~ 2^-22).
-  cfg.margin = opts->precision == CTQ_FP64 ? 1e-9 : (opts->precision == CTQ_TF32 ? 0.5 : 1e-2);
+  // BF16X3 keeps 16 significant bits (u ~ 2^-16).
+  cfg.margin = opts->precision == CTQ_FP64     ? 1e-9
+               : opts->precision == CTQ_TF32   ? 0.5
+               : opts->precision == CTQ_BF16X3 ? 5e-2
+                                               : 1e-2;
   cfg.bounds = result->bounds;
   cfg.debug = opts->debug_flags;
   int st;
   if (opts->precision == CTQ_FP64) {
     st = ctq::launch_eval_fp64(imp->dev, imp->launch, B, cfg, W, result, stream, opts->timing_events);
   } else if (imp->big) {
-    ctq::BigParams P = opts->precision == CTQ_TF32 ? imp->big1 : imp->big3;
+    const int pr = opts->precision;
+    ctq::BigParams P = pr == CTQ_TF32 ? imp->big1 : pr == CTQ_BF16X3 ? imp->big2 : imp->big3;
+    const ctq::LaunchCfg& lc = pr == CTQ_TF32 ? imp->launch_big1 : pr == CTQ_BF16X3 ? imp->launch_big2 : imp->launch_big3;
     P.timeout_ns = opts->timeout_ns > 0 ? uint64_t(opts->timeout_ns) : uint64_t(2000000000ull);
     char* scratch = static_cast<char*>(workspace) + ((base + 255) & ~size_t(255));
-    st = ctq::launch_eval_big(imp->dev, opts->precision == CTQ_TF32 ? imp->launch_big1 : imp->launch_big3, P, B,
-                              cfg, W, result, scratch, stream, opts->timing_events);
+    st = ctq::launch_eval_big(imp->dev, lc, P, B, cfg, W, result, scratch, stream, opts->timing_events);
   } else {
     ctq::TcParams P = opts->precision == CTQ_TF32 ? imp->tc1 : imp->tc3;
     P.timeout_ns = opts->timeout_ns > 0 ? uint64_t(opts->timeout_ns) : uint64_t(2000000000ull);

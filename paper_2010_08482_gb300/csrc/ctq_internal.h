@@ -150,9 +150,9 @@ struct TcParams {
 
 // Per-impurity parameters and scratch of the large-block path (trace_big.cu).
 struct BigParams {
-  const float* bt = nullptr;      // embedded blocks: tiles (hi, then lo), per (alpha, q)
-  const int64_t* bt_off = nullptr;  // [n_alpha * n_sec] float offsets, -1 absent
-  int split = 3;                  // 1 or 3
+  const void* bt = nullptr;       // embedded blocks: tiles (hi, then lo), per (alpha, q)
+  const int64_t* bt_off = nullptr;  // [n_alpha * n_sec] element offsets, -1 absent
+  int prec = CTQ_TF32X3;          // CTQ_TF32, CTQ_TF32X3 or CTQ_BF16X3
   int nst = 3;                    // pipeline stages
   uint64_t timeout_ns = 0;
   float* zbuf = nullptr;          // scratch: 2 x (hi, lo) Z buffers
@@ -164,10 +164,10 @@ struct BigParams {
   int* abort_flag = nullptr;
 };
 
-size_t big_block_floats(int dn, int dk);
-int format_big_blocks(const HostModel& h, const double* d_blk, float* out, const std::vector<int64_t>& off);
+size_t big_block_elems(int dn, int dk);
+int format_big_blocks(const HostModel& h, const double* d_blk, void* out, const std::vector<int64_t>& off, int prec);
 size_t big_scratch_bytes(const HostModel& h, int max_ops, int grid);
-int prepare_eval_big(int split, int num_sms, LaunchCfg* lc);
+int prepare_eval_big(int prec, int num_sms, LaunchCfg* lc);
 int launch_eval_big(const DevModel& M, const LaunchCfg& lc, BigParams P, const BatchView& B, const EvalCfg& cfg,
                     const Work& W, const ctq_result* R, void* scratch, void* stream, void* const* events);
 

@@ -64,6 +64,19 @@ __device__ __forceinline__ void block_max_sum(double& mx, double& sm, double* re
   }
 }
 
+// Block-wide sum; every thread gets the result.  red: 32 doubles of shared memory.
+__device__ __forceinline__ double block_sum(double sm, double* red) {
+  sm = warp_sum(sm);
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (nw == 1) return sm;
+  __syncthreads();  // red[] may still be read from the previous reduction
+  if ((threadIdx.x & 31) == 0) red[w] = sm;
+  __syncthreads();
+  sm = red[0];
+  for (int i = 1; i < nw; ++i) sm += red[i];
+  return sm;
+}
+
 }  // namespace dev
 
 // Kernels shared by every precision (plan_combine.cu).

@@ -40,21 +40,82 @@ using namespace ptx;
 constexpr int BG_THREADS = 128;
 constexpr int BM = 128;       // rows of a C tile (rows of Z)
 constexpr int BN = 128;       // columns of a C tile (embedded output states)
-constexpr int BK = 32;        // K elements (floats) per staged chunk
-constexpr int A_TILE = BM * BK;  // floats
-constexpr int B_TILE = BN * BK;  // floats
+constexpr int BK = 32;        // sector dimensions are padded to multiples of BK
+constexpr int ROWB = 128;     // bytes of one tile row in a staged K chunk
+constexpr uint32_t A_BYTES = BM * ROWB;  // one staged A tile (16 KB)
+constexpr uint32_t B_BYTES = BN * ROWB;  // one staged B tile (16 KB)
 constexpr uint32_t BAR_TIMEOUT_FLAG = 1u;
+
+// Operand elements: TF32 and 3xTF32 stage float tiles (tf32-rounded), BF16X3
+// stages bf16 hi / lo tiles.  A staged chunk row is always 128 bytes (32
+// floats or 64 bf16), so tile geometry and descriptors in bytes are shared.
+template <int PREC>
+struct Elt {
+  using T = float;
+};
+template <>
+struct Elt<CTQ_BF16X3> {
+  using T = uint16_t;
+};
 
 __device__ __forceinline__ int rup(int x, int m) { return (x + m - 1) / m * m; }
 
-// Offset (floats) of element (row r, column k) of a matrix stored as tiles
-// of `rows_per_tile` x BK, tile (rt, kc) at ((rt * n_kc) + kc) * tile size,
-// core matrix (nb, kb) at (kb * rows_per_tile/8 + nb) * 32 floats.
-__device__ __forceinline__ size_t tiled_off(int r, int k, int rows_per_tile, int n_kc) {
+// Offset (elements of EB bytes) of element (row r, column k) of a matrix
+// stored as tiles of `rows_per_tile` rows x 128 bytes of K, tile (rt, kc) at
+// ((rt * n_kc) + kc) * tile size, core matrix (nb, kb) of 8 rows x 16 bytes at
+// (kb * rows_per_tile/8 + nb) * 128 bytes.
+template <int EB>
+__host__ __device__ __forceinline__ size_t tiled_off(int r, int k, int rows_per_tile, int n_kc) {
+  constexpr int EPC = 16 / EB;    // elements per core-matrix row
+  constexpr int BKE = ROWB / EB;  // elements per chunk row
   const int rt = r / rows_per_tile, rr = r - rt * rows_per_tile;
-  const int kc = k / BK, kk = k - kc * BK;
-  return (size_t(rt) * n_kc + kc) * size_t(rows_per_tile) * BK +
-         size_t((kk >> 2) * (rows_per_tile >> 3) + (rr >> 3)) * 32 + (rr & 7) * 4 + (kk & 3);
+  const int kc = k / BKE, kk = k - kc * BKE;
+  return (size_t(rt) * n_kc + kc) * size_t(rows_per_tile) * BKE +
+         size_t((kk / EPC) * (rows_per_tile >> 3) + (rr >> 3)) * (8 * EPC) + (rr & 7) * EPC + (kk % EPC);
+}
+
+// bf16 bits of x rounded to nearest even (finite x), and the value they hold.
+__device__ __forceinline__ uint32_t bf16_bits(float x) {
+  const uint32_t u = __float_as_uint(x);
+  return (u + 0x7fffu + ((u >> 16) & 1u)) >> 16;
+}
+__device__ __forceinline__ float bf16_val(uint32_t b) { return __uint_as_float(b << 16); }
+
+// hi / lo split of x in the operand format of PREC.
+template <int PREC>
+__device__ __forceinline__ void split_store(float x, typename Elt<PREC>::T& hi, typename Elt<PREC>::T& lo) {
+  if constexpr (PREC == CTQ_BF16X3) {
+    const uint32_t h = bf16_bits(x);
+    hi = uint16_t(h);
+    lo = uint16_t(bf16_bits(x - bf16_val(h)));
+  } else {
+    const uint32_t h = to_tf32(x);
+    hi = __uint_as_float(h);
+    lo = __uint_as_float(to_tf32(x - __uint_as_float(h)));
+  }
+}
+template <int PREC>
+__device__ __forceinline__ float elt_val(typename Elt<PREC>::T v) {
+  if constexpr (PREC == CTQ_BF16X3) return bf16_val(v);
+  else return v;
+}
+
+// 16 bytes of consecutive operand elements as one vector.
+template <int PREC>
+__device__ __forceinline__ uint4 pack16(const typename Elt<PREC>::T* v) {
+  if constexpr (PREC == CTQ_BF16X3) {
+    return make_uint4(uint32_t(v[0]) | (uint32_t(v[1]) << 16), uint32_t(v[2]) | (uint32_t(v[3]) << 16),
+                      uint32_t(v[4]) | (uint32_t(v[5]) << 16), uint32_t(v[6]) | (uint32_t(v[7]) << 16));
+  } else {
+    return make_uint4(__float_as_uint(v[0]), __float_as_uint(v[1]), __float_as_uint(v[2]), __float_as_uint(v[3]));
+  }
+}
+
+// D[tmem] (+)= A[smem] * B[smem] in the operand format of PREC.
+template <int PREC>
+__device__ __forceinline__ void mma_big(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if constexpr (PREC == CTQ_BF16X3) mma_bf16_ss(d, a, b, idesc, acc);
+  else mma_tf32_ss(d, a, b, idesc, acc);
 }
 
 // Grid barrier with a bounded wait (sense reversal on a generation word).
@@ -107,15 +168,19 @@ struct BigShared {
 
 namespace {
 
-template <int SPLIT>
+template <int PREC>
 __global__ void __launch_bounds__(BG_THREADS, 1)
     k_trace_big(DevModel M, BatchView B, EvalCfg cfg, Work W, BigParams P) {
+  using T = typename Elt<PREC>::T;
+  constexpr bool SPLIT = PREC != CTQ_TF32;   // hi and lo operand planes
+  constexpr int EB = int(sizeof(T));
+  constexpr int BKE = ROWB / EB;             // K elements per staged chunk
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ BigShared S;
   const int NST = P.nst;
-  const int stage_floats = (SPLIT == 3 ? 2 : 1) * (A_TILE + B_TILE);
-  float* stage0 = reinterpret_cast<float*>(smem_raw);
-  float* p_s = stage0 + size_t(NST) * stage_floats;  // [PVEC] column scales of the current product
+  const uint32_t stage_bytes = (SPLIT ? 2u : 1u) * (A_BYTES + B_BYTES);
+  unsigned char* stage0 = smem_raw;
+  float* p_s = reinterpret_cast<float*>(stage0 + size_t(NST) * stage_bytes);  // [PVEC] column scales
   float* q_s = p_s + PVEC;                            // [PVEC] wrap-around propagator of q0 (first product)
   const int tid = threadIdx.x, warp = tid >> 5;
   const int ns = M.n_sec;
@@ -150,8 +215,9 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
 
   const int n_items = W.counters[0];
   const Item* items = W.items + size_t(B.n_chains) * ns;
-  float* Zh[2] = {P.zbuf, P.zbuf + 2 * P.zfloats};
-  float* Zl[2] = {P.zbuf + P.zfloats, P.zbuf + 3 * P.zfloats};
+  T* zb = reinterpret_cast<T*>(P.zbuf);
+  T* Zh[2] = {zb, zb + 2 * P.zfloats};
+  T* Zl[2] = {zb + P.zfloats, zb + 3 * P.zfloats};
 
   for (int it_idx = 0; it_idx < n_items && alive; ++it_idx) {
     const Item it = items[it_idx];
@@ -218,7 +284,7 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
       prefix -= dt * (M.E_min[qb] - M.E_ref);
       const int d1 = M.dims[qb];
       const int dpk = rup(d1, BK);
-      const int nkc = 2 * dpk / BK;
+      const int nkc = 2 * dpk / BKE;
       const double* Eb = M.E_rel + M.E_off[qb];
       for (int j = tid; j < d0; j += BG_THREADS)
         q_s[j] = expf(float(-t_first * E0[j])) * expf(float(-t_last * E0[j]));
@@ -239,13 +305,15 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
         }
         ek = max(ek, max((__float_as_int(xr) >> 23) & 0xff, (__float_as_int(xi) >> 23) & 0xff));
         f2 += xr * xr + xi * xi;
-        const size_t o_r = tiled_off(j, m, BM, nkc), o_i = tiled_off(j, dpk + m, BM, nkc);
-        const uint32_t hr = to_tf32(xr), hi_ = to_tf32(xi);
-        Zh[0][o_r] = __uint_as_float(hr);
-        Zh[0][o_i] = __uint_as_float(hi_);
-        if (SPLIT == 3) {
-          Zl[0][o_r] = __uint_as_float(to_tf32(xr - __uint_as_float(hr)));
-          Zl[0][o_i] = __uint_as_float(to_tf32(xi - __uint_as_float(hi_)));
+        const size_t o_r = tiled_off<EB>(j, m, BM, nkc), o_i = tiled_off<EB>(j, dpk + m, BM, nkc);
+        T hr, lr, hi_, li;
+        split_store<PREC>(xr, hr, lr);
+        split_store<PREC>(xi, hi_, li);
+        Zh[0][o_r] = hr;
+        Zh[0][o_i] = hi_;
+        if (SPLIT) {
+          Zl[0][o_r] = lr;
+          Zl[0][o_i] = li;
         }
       }
       ek = __reduce_max_sync(0xffffffffu, ek);
@@ -304,17 +372,17 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
 
       if (i == n - 1) {  // final operator: sum_{j,k} F_n[j][k] Z[j][k]
         const int64_t off = M.blk_off[idx_a];
-        const int dpk = rup(dcur, BK), nkc = 2 * dpk / BK;
+        const int dpk = rup(dcur, BK), nkc = 2 * dpk / BKE;
         double vr = 0.0, vi = 0.0;
         const long long total = (long long)d0 * dcur;
         for (long long e2 = (long long)blockIdx.x * BG_THREADS + tid; e2 < total;
              e2 += (long long)gridDim.x * BG_THREADS) {
           const int j = int(e2 / dcur), k = int(e2 - (long long)j * dcur);
-          const size_t o_r = tiled_off(j, k, BM, nkc), o_i = tiled_off(j, dpk + k, BM, nkc);
-          float zr = Zh[cur][o_r], zi = Zh[cur][o_i];
-          if (SPLIT == 3) {
-            zr += Zl[cur][o_r];
-            zi += Zl[cur][o_i];
+          const size_t o_r = tiled_off<EB>(j, k, BM, nkc), o_i = tiled_off<EB>(j, dpk + k, BM, nkc);
+          float zr = elt_val<PREC>(Zh[cur][o_r]), zi = elt_val<PREC>(Zh[cur][o_i]);
+          if (SPLIT) {
+            zr += elt_val<PREC>(Zl[cur][o_r]);
+            zi += elt_val<PREC>(Zl[cur][o_i]);
           }
           const int64_t fe = off + int64_t(j) * dcur + k;
           const float fr_ = float(cplx ? M.blk[2 * fe] : M.blk[fe]);
@@ -351,8 +419,8 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
 
       // ---- tensor-core product: Z_next = Z F^T, columns scaled by p * 2^-e
       const int db = M.dims[qb];
-      const int dpk = rup(dcur, BK), nkc = 2 * dpk / BK;   // K of this product
-      const int dpn = rup(db, BK), nkc_n = 2 * dpn / BK;   // K of the next one
+      const int dpk = rup(dcur, BK), nkc = 2 * dpk / BKE;   // K chunks of this product
+      const int dpn = rup(db, BK), nkc_n = 2 * dpn / BKE;   // K chunks of the next one
       {
         const double dt = B.tau[a0 + i + 1] - B.tau[a0 + i];
         const double* Eb = M.E_rel + M.E_off[qb];
@@ -362,8 +430,9 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
         prefix -= dt * (M.E_min[qb] - M.E_ref);
       }
       __syncthreads();
-      const float* Bt = P.bt + P.bt_off[idx_a];
-      const size_t b_plane = size_t(rup(2 * dpn, BN) / BN) * nkc * B_TILE;  // floats of one B plane
+      const T* Bt = reinterpret_cast<const T*>(P.bt) + P.bt_off[idx_a];
+      const size_t b_tile = B_BYTES / EB, a_tile = A_BYTES / EB;      // elements per staged tile
+      const size_t b_plane = size_t(rup(2 * dpn, BN) / BN) * nkc * b_tile;  // elements of one B plane
       const int n_mt = dp0 / BM, n_nt = (2 * dpn + BN - 1) / BN;
       const int n_tiles = n_mt * n_nt;
       const int nxt = cur ^ 1;
@@ -372,23 +441,21 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
       for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const int mt = t % n_mt, nt = t / n_mt;  // column-major: B tiles reused across rows
         const int ncols = min(BN, 2 * dpn - nt * BN);
-        const uint32_t idesc = idesc_tf32(BM, ncols);
-        const float* Asrc = Zh[cur] + size_t(mt) * nkc * A_TILE;
-        const float* Alo = Zl[cur] + size_t(mt) * nkc * A_TILE;
-        const float* Bsrc = Bt + size_t(nt) * nkc * B_TILE;
-        const float* Blo = Bsrc + b_plane;
-        const uint32_t a_bytes = A_TILE * 4, b_bytes = B_TILE * 4;
-        const uint32_t st_bytes = (SPLIT == 3 ? 2 : 1) * (a_bytes + b_bytes);
+        const uint32_t idesc = (PREC == CTQ_BF16X3) ? idesc_bf16(BM, ncols) : idesc_tf32(BM, ncols);
+        const T* Asrc = Zh[cur] + size_t(mt) * nkc * a_tile;
+        const T* Alo = Zl[cur] + size_t(mt) * nkc * a_tile;
+        const T* Bsrc = Bt + size_t(nt) * nkc * b_tile;
+        const T* Blo = Bsrc + b_plane;
         if (tid == 0) {
           auto issue = [&](int kc) {
             const int st = kc % NST;
-            float* sb = stage0 + size_t(st) * stage_floats;
-            mbar_arrive_expect_tx(&S.full[st], st_bytes);
-            bulk_g2s(sb, Asrc + size_t(kc) * A_TILE, a_bytes, &S.full[st]);
-            bulk_g2s(sb + A_TILE, Bsrc + size_t(kc) * B_TILE, b_bytes, &S.full[st]);
-            if (SPLIT == 3) {
-              bulk_g2s(sb + A_TILE + B_TILE, Alo + size_t(kc) * A_TILE, a_bytes, &S.full[st]);
-              bulk_g2s(sb + 2 * A_TILE + B_TILE, Blo + size_t(kc) * B_TILE, b_bytes, &S.full[st]);
+            unsigned char* sb = stage0 + size_t(st) * stage_bytes;
+            mbar_arrive_expect_tx(&S.full[st], stage_bytes);
+            bulk_g2s(sb, Asrc + size_t(kc) * a_tile, A_BYTES, &S.full[st]);
+            bulk_g2s(sb + A_BYTES, Bsrc + size_t(kc) * b_tile, B_BYTES, &S.full[st]);
+            if (SPLIT) {
+              bulk_g2s(sb + A_BYTES + B_BYTES, Alo + size_t(kc) * a_tile, A_BYTES, &S.full[st]);
+              bulk_g2s(sb + 2 * A_BYTES + B_BYTES, Blo + size_t(kc) * b_tile, B_BYTES, &S.full[st]);
             }
           };
           // Chunk kc lives in stage kc % NST.  After the products of chunk kc
@@ -402,16 +469,17 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
             if (!mbar_wait(&S.full[st], ph_full[st], P.timeout_ns)) { S.fail = 1; break; }
             ph_full[st] ^= 1u;
             tc_fence_after();
-            const uint32_t sa = smem_u32(stage0 + size_t(st) * stage_floats);
-            const uint32_t sbh = sa + a_bytes, sal = sbh + b_bytes, sbl = sal + a_bytes;
-            for (int kk = 0; kk < BK / 8; ++kk) {
+            const uint32_t sa = smem_u32(stage0 + size_t(st) * stage_bytes);
+            const uint32_t sbh = sa + A_BYTES, sal = sbh + B_BYTES, sbl = sal + A_BYTES;
+            // one MMA covers 32 bytes of K (8 tf32 or 16 bf16): two core matrices
+            for (int kk = 0; kk < ROWB / 32; ++kk) {
               const uint64_t da = sdesc(sa + kk * 2 * 2048, 2048, 128);
               const uint64_t dbh = sdesc(sbh + kk * 2 * 2048, 2048, 128);
               const uint32_t tacc = tD + uint32_t(kc % NACC) * BN;
-              mma_tf32_ss(tacc, da, dbh, idesc, (kc >= NACC || kk > 0) ? 1u : 0u);
-              if (SPLIT == 3) {
-                mma_tf32_ss(tacc, da, sdesc(sbl + kk * 2 * 2048, 2048, 128), idesc, 1u);
-                mma_tf32_ss(tacc, sdesc(sal + kk * 2 * 2048, 2048, 128), dbh, idesc, 1u);
+              mma_big<PREC>(tacc, da, dbh, idesc, (kc >= NACC || kk > 0) ? 1u : 0u);
+              if (SPLIT) {
+                mma_big<PREC>(tacc, da, sdesc(sbl + kk * 2 * 2048, 2048, 128), idesc, 1u);
+                mma_big<PREC>(tacc, sdesc(sal + kk * 2 * 2048, 2048, 128), dbh, idesc, 1u);
               }
             }
             mma_commit(&S.empty[st]);
@@ -455,7 +523,7 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
 #pragma unroll
             for (int t2 = 0; t2 < 16; ++t2) acc[t2] += __uint_as_float(v[t2]);
           }
-          float hi[16], lo[16];
+          T hi[16], lo[16];
 #pragma unroll
           for (int t2 = 0; t2 < 16; ++t2) {
             const int col = nt * BN + c0 + t2;  // embedded column
@@ -463,16 +531,15 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
             const float x = acc[t2] * p_s[j];
             ek = max(ek, (__float_as_int(x) >> 23) & 0xff);
             f2 += x * x;
-            const uint32_t h = to_tf32(x);
-            hi[t2] = __uint_as_float(h);
-            lo[t2] = __uint_as_float(to_tf32(x - hi[t2]));
+            split_store<PREC>(x, hi[t2], lo[t2]);
           }
+          // 16 consecutive K elements of the next product: 16-byte stores
+          constexpr int PER16 = 16 / EB;
 #pragma unroll
-          for (int g = 0; g < 4; ++g) {
-            const size_t o = tiled_off(row, nt * BN + c0 + 4 * g, BM, nkc_n);
-            *reinterpret_cast<float4*>(Zh[nxt] + o) = make_float4(hi[4 * g], hi[4 * g + 1], hi[4 * g + 2], hi[4 * g + 3]);
-            if (SPLIT == 3)
-              *reinterpret_cast<float4*>(Zl[nxt] + o) = make_float4(lo[4 * g], lo[4 * g + 1], lo[4 * g + 2], lo[4 * g + 3]);
+          for (int g = 0; g < 16 / PER16; ++g) {
+            const size_t o = tiled_off<EB>(row, nt * BN + c0 + PER16 * g, BM, nkc_n);
+            *reinterpret_cast<uint4*>(Zh[nxt] + o) = pack16<PREC>(hi + PER16 * g);
+            if (SPLIT) *reinterpret_cast<uint4*>(Zl[nxt] + o) = pack16<PREC>(lo + PER16 * g);
           }
         }
         tc_fence_before();
@@ -513,13 +580,17 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
   }
 }
 
-// Embedded, tiled, tf32-split copy of every block (one CTA per output tile row
-// chunk): B'[n][k] for n < 2 dpn, k < 2 dpk with
+// Embedded, tiled, split copy of every block (grid-stride over elements):
+// B'[n][k] for n < 2 dpn, k < 2 dpk with
 //   n < dpn:  [Re F[n][k],  -Im F[n][k - dpk]]
-//   n >= dpn: [Im F[n - dpn][k], Re F[n - dpn][k - dpk]].
-__global__ void k_format_big(const double* blk, int cplx, int dn, int dk, float* out, int split) {
+//   n >= dpn: [Im F[n - dpn][k], Re F[n - dpn][k - dpk]],
+// hi plane then lo plane in the operand format of PREC.
+template <int PREC>
+__global__ void k_format_big(const double* blk, int cplx, int dn, int dk, typename Elt<PREC>::T* out) {
+  using T = typename Elt<PREC>::T;
+  constexpr int EB = int(sizeof(T));
   const int dpn = rup(dn, BK), dpk = rup(dk, BK);
-  const int N2 = rup(2 * dpn, BN), K2 = 2 * dpk, nkc = K2 / BK;
+  const int N2 = rup(2 * dpn, BN), K2 = 2 * dpk, nkc = K2 / (ROWB / EB);
   const size_t plane = size_t(N2) * K2;
   const long long total = (long long)N2 * K2;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
@@ -534,23 +605,127 @@ __global__ void k_format_big(const double* blk, int cplx, int dn, int dk, float*
       if (n < dpn) v = (k < dpk) ? re : -im;
       else v = (k < dpk) ? im : re;
     }
-    const size_t o = tiled_off(n, k, BN, nkc);
-    const uint32_t h = to_tf32(float(v));
-    out[o] = __uint_as_float(h);
-    if (split == 3) out[plane + o] = __uint_as_float(to_tf32(float(v - double(__uint_as_float(h)))));
+    const size_t o = tiled_off<EB>(n, k, BN, nkc);
+    if constexpr (PREC == CTQ_BF16X3) {
+      const uint32_t h = bf16_bits(float(v));
+      out[o] = uint16_t(h);
+      out[plane + o] = uint16_t(bf16_bits(float(v - double(bf16_val(h)))));
+    } else {
+      const uint32_t h = to_tf32(float(v));
+      out[o] = __uint_as_float(h);
+      out[plane + o] = __uint_as_float(to_tf32(float(v - double(__uint_as_float(h)))));
+    }
+  }
+}
+
+// Diagnostic GEMM with the operand conventions of k_trace_big: D = A B^T for
+// one 128 x N tile, A (128 x K) and B (N x K) split and tiled on the device
+// exactly like Z and the embedded blocks, staged chunk by chunk with bulk
+// copies and multiplied with the same descriptors and instruction kinds.
+template <int PREC>
+__global__ void __launch_bounds__(BG_THREADS, 1)
+    k_big_gemm_check(const float* A, const float* Bm, typename Elt<PREC>::T* ws, float* D, int N, int K,
+                     uint64_t timeout_ns, int* status) {
+  using T = typename Elt<PREC>::T;
+  constexpr bool SPLIT = PREC != CTQ_TF32;
+  constexpr int EB = int(sizeof(T));
+  constexpr int BKE = ROWB / EB;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t bar_full, bar_done;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int nkc = K / BKE;
+  const size_t a_tile = A_BYTES / EB, b_tile = B_BYTES / EB;
+  T* Ah = ws;
+  T* Al = Ah + size_t(nkc) * a_tile;
+  T* Bh = Al + size_t(nkc) * a_tile;
+  T* Bl = Bh + size_t(nkc) * b_tile;
+  for (int e = tid; e < 128 * K; e += BG_THREADS) {
+    const int r = e / K, k = e - r * K;
+    T h, l;
+    split_store<PREC>(A[e], h, l);
+    Ah[tiled_off<EB>(r, k, BM, nkc)] = h;
+    Al[tiled_off<EB>(r, k, BM, nkc)] = l;
+  }
+  for (int e = tid; e < BN * K; e += BG_THREADS) {
+    const int r = e / K, k = e - r * K;
+    T h, l;
+    split_store<PREC>(r < N ? Bm[size_t(r) * K + k] : 0.f, h, l);
+    Bh[tiled_off<EB>(r, k, BN, nkc)] = h;
+    Bl[tiled_off<EB>(r, k, BN, nkc)] = l;
+  }
+  __threadfence();
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  if (tid == 0) {
+    mbar_init(&bar_full, 1);
+    mbar_init(&bar_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, BN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tD = tmem_base;
+  bool ok = true;
+  if (tid == 0) {
+    const uint32_t idesc = (PREC == CTQ_BF16X3) ? idesc_bf16(BM, N) : idesc_tf32(BM, N);
+    const uint32_t bytes = (SPLIT ? 2u : 1u) * (A_BYTES + B_BYTES);
+    for (int kc = 0; kc < nkc && ok; ++kc) {
+      mbar_arrive_expect_tx(&bar_full, bytes);
+      bulk_g2s(smem_raw, Ah + size_t(kc) * a_tile, A_BYTES, &bar_full);
+      bulk_g2s(smem_raw + A_BYTES, Bh + size_t(kc) * b_tile, B_BYTES, &bar_full);
+      if (SPLIT) {
+        bulk_g2s(smem_raw + A_BYTES + B_BYTES, Al + size_t(kc) * a_tile, A_BYTES, &bar_full);
+        bulk_g2s(smem_raw + 2 * A_BYTES + B_BYTES, Bl + size_t(kc) * b_tile, B_BYTES, &bar_full);
+      }
+      ok = mbar_wait(&bar_full, uint32_t(kc & 1), timeout_ns);
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t sa = smem_u32(smem_raw), sbh = sa + A_BYTES, sal = sbh + B_BYTES, sbl = sal + A_BYTES;
+      for (int kk = 0; kk < ROWB / 32; ++kk) {
+        const uint64_t da = sdesc(sa + kk * 2 * 2048, 2048, 128);
+        const uint64_t dbh = sdesc(sbh + kk * 2 * 2048, 2048, 128);
+        mma_big<PREC>(tD, da, dbh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+        if (SPLIT) {
+          mma_big<PREC>(tD, da, sdesc(sbl + kk * 2 * 2048, 2048, 128), idesc, 1u);
+          mma_big<PREC>(tD, sdesc(sal + kk * 2 * 2048, 2048, 128), dbh, idesc, 1u);
+        }
+      }
+      mma_commit(&bar_done);
+      ok = mbar_wait(&bar_done, uint32_t(kc & 1), timeout_ns);  // the stage is reused by the next chunk
+    }
+    if (!ok) *status = CTQ_ERR_TIMEOUT;
+  }
+  __syncthreads();
+  if (*status == 0) {
+    tc_fence_after();
+    const uint32_t lane_off = uint32_t(32 * warp) << 16;
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      uint32_t v[16];
+      tmem_ld16(tD + lane_off + c0, v);
+      tmem_wait_ld();
+      for (int t = 0; t < 16; ++t) D[size_t(tid) * N + c0 + t] = __uint_as_float(v[t]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tD, BN);
   }
 }
 
 }  // namespace
 
-size_t big_block_floats(int dn, int dk) {
+size_t big_block_elems(int dn, int dk) {
   const int dpn = (dn + BK - 1) / BK * BK, dpk = (dk + BK - 1) / BK * BK;
   return size_t((2 * dpn + BN - 1) / BN * BN) * size_t(2 * dpk) * 2;  // hi and lo planes
 }
 
 // Lays out and fills the embedded blocks on the device (d_blk: the float64
-// blocks already on the device).  out/off: device buffer and host offsets.
-int format_big_blocks(const HostModel& h, const double* d_blk, float* out, const std::vector<int64_t>& off) {
+// blocks already on the device) in the operand format of prec (CTQ_TF32X3
+// planes also serve CTQ_TF32).  out/off: device buffer and element offsets.
+int format_big_blocks(const HostModel& h, const double* d_blk, void* out, const std::vector<int64_t>& off, int prec) {
   const int na = h.n_alpha();
   for (int a = 0; a < na; ++a)
     for (int q = 0; q < h.n_sec; ++q) {
@@ -558,7 +733,12 @@ int format_big_blocks(const HostModel& h, const double* d_blk, float* out, const
       const int qp = h.s[i];
       if (qp < 0) continue;
       const double* src = d_blk + (h.is_complex ? 2 : 1) * h.blk_off[i];
-      k_format_big<<<1024, 256>>>(src, h.is_complex, h.dims[qp], h.dims[q], out + off[i], 3);
+      if (prec == CTQ_BF16X3)
+        k_format_big<CTQ_BF16X3><<<1024, 256>>>(src, h.is_complex, h.dims[qp], h.dims[q],
+                                                static_cast<uint16_t*>(out) + off[i]);
+      else
+        k_format_big<CTQ_TF32X3><<<1024, 256>>>(src, h.is_complex, h.dims[qp], h.dims[q],
+                                                static_cast<float*>(out) + off[i]);
       if (cudaGetLastError() != cudaSuccess) return CTQ_ERR_CUDA;
     }
   return cudaDeviceSynchronize() == cudaSuccess ? CTQ_OK : CTQ_ERR_CUDA;
@@ -570,14 +750,24 @@ size_t big_scratch_bytes(const HostModel& h, int max_ops, int grid) {
   return 4 * zf * 4 + 256 + size_t(max_ops + 2) * (4 + 8) + size_t(2 * grid) * 8 + 1024;
 }
 
-int prepare_eval_big(int split, int num_sms, LaunchCfg* lc) {
+static int big_stages(int prec) { return prec == CTQ_TF32 ? 6 : 3; }
+
+static size_t big_smem(int prec) {
+  return size_t(big_stages(prec)) * (prec == CTQ_TF32 ? 1 : 2) * (A_BYTES + B_BYTES) + 2 * PVEC * 4;
+}
+
+template <int PREC>
+static cudaError_t big_attr(size_t smem) {
+  return cudaFuncSetAttribute(k_trace_big<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+}
+
+int prepare_eval_big(int prec, int num_sms, LaunchCfg* lc) {
   lc->threads = BG_THREADS;
   lc->num_sms = num_sms;
-  const int nst = split == 3 ? 3 : 6;
-  lc->smem = size_t(nst) * (split == 3 ? 2 : 1) * (A_TILE + B_TILE) * 4 + 2 * PVEC * 4;
-  const cudaError_t e = (split == 3)
-                            ? cudaFuncSetAttribute(k_trace_big<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lc->smem))
-                            : cudaFuncSetAttribute(k_trace_big<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lc->smem));
+  lc->smem = big_smem(prec);
+  const cudaError_t e = prec == CTQ_TF32     ? big_attr<CTQ_TF32>(lc->smem)
+                        : prec == CTQ_BF16X3 ? big_attr<CTQ_BF16X3>(lc->smem)
+                                             : big_attr<CTQ_TF32X3>(lc->smem);
   if (e != cudaSuccess) return CTQ_ERR_CUDA;
   lc->per_sm = 1;
   return CTQ_OK;
@@ -608,7 +798,7 @@ int launch_eval_big(const DevModel& M, const LaunchCfg& lc, BigParams P, const B
   P.part = reinterpret_cast<double*>(s);
   s += size_t(2 * grid) * 8;
   P.abort_flag = reinterpret_cast<int*>(s);
-  P.nst = P.split == 3 ? 3 : 6;
+  P.nst = big_stages(P.prec);
   if (cudaMemsetAsync(W.counters, 0, 256, st) != cudaSuccess) return CTQ_ERR_CUDA;
   if (cudaMemsetAsync(P.bar, 0, 256, st) != cudaSuccess) return CTQ_ERR_CUDA;
   if (cudaMemsetAsync(P.zbuf, 0, 4 * P.zfloats * 4, st) != cudaSuccess) return CTQ_ERR_CUDA;
@@ -620,9 +810,10 @@ int launch_eval_big(const DevModel& M, const LaunchCfg& lc, BigParams P, const B
   mark(1);
   void* args[] = {const_cast<DevModel*>(&M), const_cast<BatchView*>(&B), const_cast<EvalCfg*>(&cfg),
                   const_cast<Work*>(&W), &P};
-  const cudaError_t e = (P.split == 3)
-                            ? cudaLaunchCooperativeKernel((void*)k_trace_big<3>, grid, BG_THREADS, args, lc.smem, st)
-                            : cudaLaunchCooperativeKernel((void*)k_trace_big<1>, grid, BG_THREADS, args, lc.smem, st);
+  void* fn = P.prec == CTQ_TF32     ? (void*)k_trace_big<CTQ_TF32>
+             : P.prec == CTQ_BF16X3 ? (void*)k_trace_big<CTQ_BF16X3>
+                                    : (void*)k_trace_big<CTQ_TF32X3>;
+  const cudaError_t e = cudaLaunchCooperativeKernel(fn, grid, BG_THREADS, args, lc.smem, st);
   if (e != cudaSuccess) return CTQ_ERR_CUDA;
   mark(2);
   {
@@ -634,3 +825,58 @@ int launch_eval_big(const DevModel& M, const LaunchCfg& lc, BigParams P, const B
 }
 
 }  // namespace ctq
+
+extern "C" int ctq_big_gemm_check(int device, const float* A, const float* Bm, float* D, int N, int K, int precision) {
+  using namespace ctq;
+  auto fail = [](int code, const char* msg) {
+    set_last_error(msg);
+    return code;
+  };
+  if (!A || !Bm || !D) return fail(CTQ_ERR_ARG, "null argument");
+  if (precision != CTQ_TF32 && precision != CTQ_TF32X3 && precision != CTQ_BF16X3)
+    return fail(CTQ_ERR_ARG, "precision must be CTQ_TF32, CTQ_TF32X3 or CTQ_BF16X3");
+  if (N < 16 || N > BN || N % 16 != 0) return fail(CTQ_ERR_ARG, "N must be a multiple of 16 in [16, 128]");
+  if (K < 64 || K > 4096 || K % 64 != 0) return fail(CTQ_ERR_ARG, "K must be a multiple of 64 in [64, 4096]");
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess)
+    return fail(CTQ_ERR_CUDA, "cudaSetDevice failed");
+  float *dA = nullptr, *dB = nullptr, *dD = nullptr;
+  void* ws = nullptr;
+  int* dS = nullptr;
+  int st = CTQ_OK;
+  const size_t ws_bytes = size_t(2) * (128 + BN) * K * 4;
+  if (cudaMalloc(&dA, size_t(128) * K * 4) || cudaMalloc(&dB, size_t(N) * K * 4) ||
+      cudaMalloc(&dD, size_t(128) * N * 4) || cudaMalloc(&ws, ws_bytes) || cudaMalloc(&dS, 4)) {
+    st = CTQ_ERR_NOMEM;
+  } else {
+    cudaMemcpy(dA, A, size_t(128) * K * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(dB, Bm, size_t(N) * K * 4, cudaMemcpyHostToDevice);
+    cudaMemset(dS, 0, 4);
+    const size_t smem = 2 * size_t(A_BYTES + B_BYTES);
+    const uint64_t tmo = 2000000000ull;
+    if (precision == CTQ_BF16X3) {
+      cudaFuncSetAttribute(k_big_gemm_check<CTQ_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      k_big_gemm_check<CTQ_BF16X3><<<1, BG_THREADS, smem>>>(dA, dB, static_cast<uint16_t*>(ws), dD, N, K, tmo, dS);
+    } else if (precision == CTQ_TF32X3) {
+      cudaFuncSetAttribute(k_big_gemm_check<CTQ_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      k_big_gemm_check<CTQ_TF32X3><<<1, BG_THREADS, smem>>>(dA, dB, static_cast<float*>(ws), dD, N, K, tmo, dS);
+    } else {
+      cudaFuncSetAttribute(k_big_gemm_check<CTQ_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      k_big_gemm_check<CTQ_TF32><<<1, BG_THREADS, smem>>>(dA, dB, static_cast<float*>(ws), dD, N, K, tmo, dS);
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) st = CTQ_ERR_CUDA;
+    if (st == CTQ_OK) {
+      int hs = 0;
+      cudaMemcpy(D, dD, size_t(128) * N * 4, cudaMemcpyDeviceToHost);
+      cudaMemcpy(&hs, dS, 4, cudaMemcpyDeviceToHost);
+      st = hs;
+    }
+  }
+  cudaFree(dA);
+  cudaFree(dB);
+  cudaFree(dD);
+  cudaFree(ws);
+  cudaFree(dS);
+  if (prev != device) cudaSetDevice(prev);
+  return st == CTQ_OK ? CTQ_OK : fail(st, "big-path GEMM check failed");
+}

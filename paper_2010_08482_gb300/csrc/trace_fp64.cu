@@ -77,6 +77,69 @@ __device__ __forceinline__ int block_max_int(int v, int* redi) {
   return v;
 }
 
+// 2^e as a float64 built from its exponent field, -1022 <= e <= 1023.
+__device__ __forceinline__ double pow2i(int e) { return __hiloint2double((e + 1023) << 20, 0); }
+
+// h + l += x with the rounding error of h + x kept in l (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum_acc(double& h, double& l, double x) {
+  const double s = h + x;
+  const double bp = s - h;
+  l += (h - (s - bp)) + (x - bp);
+  h = s;
+}
+
+// Log scale of one sector string, computed by one warp with lanes over
+// chunks of operators (Sec. 3.3.1 propagators: every time step dtau_j in
+// sector q_j contributes -dtau_j (E_min(q_j) - E_ref) to the log of the
+// product).  The chunk sums are compensated and combined by a compensated
+// inclusive scan over lanes, so the total keeps the accuracy of a
+// compensated sequential sum.  With tracking, the chunks are the segments of
+// S operators and the scan also yields the log scale segL and the applied
+// log-norm prefix segP at every segment end.
+__device__ __forceinline__ void chain_log_scale(const DevModel& M, const BatchView& B, const EvalCfg& cfg, int a0, int n, int q0,
+                                double t_first, double t_last, bool track, const short* path, const short* opsm,
+                                double* segL, double* segP, double* out_L) {
+  const int lane = threadIdx.x & 31;
+  const int ns = M.n_sec;
+  const double emr0 = M.E_min[q0] - M.E_ref;
+  const int CH = track ? cfg.S : max(1, (n + 30) / 32);  // chunk length over j = 1 .. n-1
+  const int nch = (n - 1 + CH - 1) / CH;
+  double ch = -t_first * emr0, cl = 0.0, cp = 0.0;  // running carry (compensated) and log-norm prefix
+  two_sum_acc(ch, cl, -t_last * emr0);
+  for (int base = 0; base < nch; base += 32) {
+    const int t = base + lane;
+    double h = 0.0, l = 0.0, ps = 0.0;
+    if (t < nch) {
+      const int j2 = min((t + 1) * CH, n - 1);
+      for (int j = t * CH + 1; j <= j2; ++j) {
+        const double term = -(B.tau[a0 + j] - B.tau[a0 + j - 1]) * (M.E_min[path[j]] - M.E_ref);
+        two_sum_acc(h, l, term);
+        if (track) ps += term + M.log_norm[opsm[j - 1] * ns + path[j - 1]];
+      }
+    }
+    for (int o = 1; o < 32; o <<= 1) {  // inclusive scan over the lanes
+      const double oh = __shfl_up_sync(FULL, h, o), ol = __shfl_up_sync(FULL, l, o);
+      const double op = __shfl_up_sync(FULL, ps, o);
+      if (lane >= o) {
+        two_sum_acc(h, l, oh);
+        l += ol;
+        ps += op;
+      }
+    }
+    double H = ch, Lo = cl + l;
+    two_sum_acc(H, Lo, h);
+    const double P = cp + ps;
+    if (track && t < nch && (t + 1) * CH < n) {
+      segL[t + 1] = H + Lo;
+      segP[t + 1] = P;
+    }
+    ch = __shfl_sync(FULL, H, 31);
+    cl = __shfl_sync(FULL, Lo, 31);
+    cp = __shfl_sync(FULL, P, 31);
+  }
+  if (lane == 0) *out_L = ch + cl;
+}
+
 // Shared-memory layout of k_trace (dynamic part), see trace_smem().
 struct TraceSmem {
   size_t y_bytes;  // one Y buffer
@@ -87,7 +150,7 @@ struct TraceSmem {
 // the start of an item (lanes over all (operator, state) pairs), which keeps
 // the FP64 pipe busy with full warps; used when max_ops * max_dim fits.
 template <bool CPLX, bool PRE>
-__global__ void __launch_bounds__(256) k_trace(DevModel M, BatchView B, EvalCfg cfg, Work W) {
+__global__ void __launch_bounds__(256, 1) k_trace(DevModel M, BatchView B, EvalCfg cfg, Work W) {
   using T = typename Scalar<CPLX>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int D = M.max_dim;
@@ -128,6 +191,7 @@ __global__ void __launch_bounds__(256) k_trace(DevModel M, BatchView B, EvalCfg 
     const double* E0 = M.E_rel + M.E_off[q0];
     const bool track = cfg.lazy || cfg.bounds != nullptr;
     double* segp = W.seg + slot * size_t(cfg.n_seg_max + 1);
+    const double ub_const = (track && n > 1) ? 0.5 * log(double(it.r)) : 0.0;  // sqrt(r) of the refined bound
 
     if (n == 0) {  // empty sequence: Tr e^{-beta H(q0)}
       double sm = 0.0, mx = 0.0;
@@ -177,34 +241,20 @@ __global__ void __launch_bounds__(256) k_trace(DevModel M, BatchView B, EvalCfg 
     // the first block (trace cyclicity); their two time arguments are kept
     // separate so that no extra rounding enters them.
     const double t_first = B.tau[a0], t_last = B.beta - B.tau[a0 + n - 1];
-    if (tid == 0) {
-      KSum L;
-      L.add(-t_first * (M.E_min[q0] - M.E_ref));
-      L.add(-t_last * (M.E_min[q0] - M.E_ref));
-      double prefix = 0.0;
+    for (int i = tid; i < n; i += nt) opsm[i] = short(B.op[a0 + i]);
+    __syncthreads();
+    if (tid == 0) {  // integer walk only
       int q = q0;
       path[0] = short(q0);
       if (PRE) poff[0] = 0;
       for (int i = 0; i < n; ++i) {
-        const int alpha = B.op[a0 + i];
-        const int idx = alpha * ns + q;
-        opsm[i] = short(alpha);
-        prefix += M.log_norm[idx];
-        q = M.s[idx];
+        q = M.s[opsm[i] * ns + q];
         path[i + 1] = short(q);
-        if (i + 1 < n) {
-          const double dt = B.tau[a0 + i + 1] - B.tau[a0 + i];
-          L.add(-dt * (M.E_min[q] - M.E_ref));
-          prefix -= dt * (M.E_min[q] - M.E_ref);
-          if (PRE) poff[i + 1] = poff[i] + M.dims[q];
-          if ((i + 1) % cfg.S == 0) {
-            segL[(i + 1) / cfg.S] = L.val();
-            segP[(i + 1) / cfg.S] = prefix;
-          }
-        }
+        if (PRE && i + 1 < n) poff[i + 1] = poff[i] + M.dims[q];
       }
-      s_L = L.val();
     }
+    __syncthreads();
+    if (tid < 32) chain_log_scale(M, B, cfg, a0, n, q0, t_first, t_last, track, path, opsm, segL, segP, &s_L);
     __syncthreads();
     for (int j = tid; j < d0; j += nt) p0[j] = exp(-t_first * E0[j]) * exp(-t_last * E0[j]);
     if (PRE) {
@@ -261,16 +311,15 @@ __global__ void __launch_bounds__(256) k_trace(DevModel M, BatchView B, EvalCfg 
     // ---- operators 2 .. n: Y <- P F Y, the previous rescale folded into P
     for (int i = 1; i < n; ++i) {
       if (ekey == 0) { dead = true; break; }
-      const int e = ekey - 1023;  // floor(log2 max|Y|) for normal values
+      const int e = min(ekey - 1023, 1022);  // floor(log2 max|Y|) for normal values
       if (track && applied % cfg.S == 0 && applied < n) {
         if (!have_fr) {  // only after the first operator (segment length 1)
-          double f = 0.0, dmx = 0.0;
+          double f = 0.0;
           for (int idx = tid; idx < dcur * d0; idx += nt) f += sq(Y[idx]);
-          block_max_sum(dmx, f, red);
-          fr = f;
+          fr = block_sum(f, red);
         }
         if (tid == 0) {
-          const double ub = 0.5 * log(double(it.r)) + 0.5 * log(fr) + double(Eacc) * LN2 +
+          const double ub = ub_const + 0.5 * log(fr) + double(Eacc) * LN2 +
                             segL[applied / cfg.S] + (it.t_all - segP[applied / cfg.S]);
           segp[applied / cfg.S] = ub;
           if (cfg.lazy) {
@@ -304,7 +353,7 @@ __global__ void __launch_bounds__(256) k_trace(DevModel M, BatchView B, EvalCfg 
       const int idx_a = alpha * ns + qa;
       qb = path[i + 1];
       const int64_t off = M.blk_off[idx_a];
-      const double scale = ldexp(1.0, -e);
+      const double scale = pow2i(-e);
       Eacc += e;
 
       if (i == n - 1) {  // final operator: only the diagonal of F_n Y is needed
@@ -369,11 +418,7 @@ __global__ void __launch_bounds__(256) k_trace(DevModel M, BatchView B, EvalCfg 
         if (seg_next) f2 += sq(v);
       }
       ekey = block_max_int(ekey, redi);
-      if (seg_next) {
-        double dmx = 0.0;
-        block_max_sum(dmx, f2, red);
-        fr = f2;
-      }
+      if (seg_next) fr = block_sum(f2, red);
       have_fr = seg_next;
       T* tmp = Y;
       Y = Yn;

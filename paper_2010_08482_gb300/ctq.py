@@ -86,6 +86,7 @@ def _load():
         "ctq_last_error_message": (c_char_p, []),
         "ctq_probe_fma_rate": (c_int, [c_int, c_int, c_int, POINTER(c_double)]),
         "ctq_tc_gemm_check": (c_int, [c_int, P, P, P, c_int, c_int, c_int]),
+        "ctq_big_gemm_check": (c_int, [c_int, P, P, P, c_int, c_int, c_int]),
         "ctq_eval_traces_static": (c_int, [P, POINTER(BatchC), POINTER(EvalOptsC), POINTER(ResultC), P]),
     }
     for name, (res, args) in sig.items():
@@ -99,7 +100,7 @@ _lib = _load()
 EXPORTED = ("ctq_build_impurity", "ctq_load_impurity", "ctq_impurity_info", "ctq_get_sectors",
             "ctq_get_energies", "ctq_get_block", "ctq_workspace_size", "ctq_eval_traces",
             "ctq_launches_per_eval", "ctq_free_impurity", "ctq_strerror", "ctq_last_error_message",
-            "ctq_probe_fma_rate", "ctq_tc_gemm_check", "ctq_eval_traces_static")
+            "ctq_probe_fma_rate", "ctq_tc_gemm_check", "ctq_big_gemm_check", "ctq_eval_traces_static")
 
 # Size of the library-owned scratch used by eval_traces_static (ctq.h).
 STATIC_SCRATCH_BYTES = 32 << 20
@@ -112,6 +113,16 @@ def tc_gemm_check(A: np.ndarray, Bm: np.ndarray, split: int = 3, device: int = 0
     N, K = Bm.shape
     D = np.zeros((128, N), np.float32)
     _check(_lib.ctq_tc_gemm_check(device, _ptr(A), _ptr(Bm), _ptr(D), N, K, split), "ctq_tc_gemm_check")
+    return D
+
+
+def big_gemm_check(A: np.ndarray, Bm: np.ndarray, precision: int = TF32X3, device: int = 0) -> np.ndarray:
+    """D = A B^T with the large-block kernel's operand conventions (diagnostic, see ctq.h)."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    Bm = np.ascontiguousarray(Bm, dtype=np.float32)
+    N, K = Bm.shape
+    D = np.zeros((128, N), np.float32)
+    _check(_lib.ctq_big_gemm_check(device, _ptr(A), _ptr(Bm), _ptr(D), N, K, precision), "ctq_big_gemm_check")
     return D
 
 

@@ -39,7 +39,8 @@ def real_d_window_model(beta=10.0):
 
 
 STATED = {("dc", ctq.TF32X3): 1e-4, ("dc", ctq.TF32): 5e-2, ("dn", ctq.TF32X3): 1e-4, ("dn", ctq.TF32): 5e-2,
-          ("f7", ctq.TF32X3): 2e-3, ("f7", ctq.TF32): 0.5}
+          ("f7", ctq.TF32X3): 2e-3, ("f7", ctq.TF32): 0.5,
+          ("dc", ctq.BF16X3): 2e-3, ("dn", ctq.BF16X3): 2e-3, ("f7", ctq.BF16X3): 5e-3}
 
 
 def run(imp, batch, precision, S=8):
@@ -55,7 +56,7 @@ def small_models():
     return {"dc": atom.Model(complex_d_model()), "dn": atom.Model(real_d_window_model())}
 
 
-@pytest.mark.parametrize("precision", [ctq.TF32X3, ctq.TF32])
+@pytest.mark.parametrize("precision", [ctq.TF32X3, ctq.TF32, ctq.BF16X3])
 @pytest.mark.parametrize("name", ["dc", "dn"])
 def test_big_engine_parity(name, precision, small_models):
     m = small_models[name]
@@ -75,6 +76,30 @@ def test_big_engine_parity(name, precision, small_models):
         errs.append(err)
     assert errs
     print(f"{name} precision={precision}: n={len(errs)} max rel err {max(errs):.3e}, median {np.median(errs):.3e}")
+
+
+# Bound on |D - A B^T| / (|A| |B|^T) elementwise: operand rounding of one
+# pass (TF32: 2^-11 per operand), of the dropped lo*lo term and lo rounding
+# (3xTF32: ~2^-21; bf16 hi / lo: ~2^-16), plus FP32 accumulation over K.
+GEMM_TOL = {ctq.TF32: 3e-3, ctq.TF32X3: 2e-5, ctq.BF16X3: 1e-4}
+
+
+@pytest.mark.parametrize("precision", [ctq.TF32, ctq.TF32X3, ctq.BF16X3])
+@pytest.mark.parametrize("N,K", [(128, 64), (64, 256), (16, 1024), (96, 192)])
+def test_big_gemm_conventions(precision, N, K):
+    """Operand split, tiled layout, descriptors and MMA kind of the
+    large-block engine on one tile: any transposed, shifted or mis-typed
+    operand gives O(1) errors, rounding gives GEMM_TOL."""
+    rng = np.random.default_rng(N * 7919 + K)
+    A = rng.standard_normal((128, K)).astype(np.float32)
+    Bm = rng.standard_normal((N, K)).astype(np.float32)
+    D = ctq.big_gemm_check(A, Bm, precision)
+    A64, B64 = A.astype(np.float64), Bm.astype(np.float64)
+    ref = A64 @ B64.T
+    scale = np.abs(A64) @ np.abs(B64).T
+    err = float(np.max(np.abs(D - ref) / scale))
+    print(f"precision={precision} N={N} K={K}: max err {err:.3e}")
+    assert err < GEMM_TOL[precision]
 
 
 def test_big_engine_bounds_bracket(small_models):
@@ -118,7 +143,7 @@ def test_f7_build_matches_stored_oracle_spectrum(f7_impurity):
     assert f7_impurity.is_complex
 
 
-@pytest.mark.parametrize("precision", [ctq.TF32X3, ctq.TF32])
+@pytest.mark.parametrize("precision", [ctq.TF32X3, ctq.TF32, ctq.BF16X3])
 def test_f7_traces_against_stored_oracle(precision, f7_impurity):
     g = _f7_golden()
     n = len(g["chains"])
