@@ -47,7 +47,7 @@ constexpr uint32_t B_BYTES = BN * ROWB;  // one staged B tile (16 KB)
 constexpr uint32_t BAR_TIMEOUT_FLAG = 1u;
 
 // Operand elements: TF32 and 3xTF32 stage float tiles (tf32-rounded), BF16X3
-// stages bf16 hi / lo tiles.  A staged chunk row is always 128 bytes (32
+// stages bf16 hi / lo tiles.  A staged chunk row is always ROWB bytes (32
 // floats or 64 bf16), so tile geometry and descriptors in bytes are shared.
 template <int PREC>
 struct Elt {
@@ -145,7 +145,7 @@ __device__ __forceinline__ bool grid_sync(unsigned* count, volatile unsigned* ge
   return ok_s != 0;
 }
 
-constexpr int MAX_NST = 6;
+constexpr int MAX_NST = 12;
 // The K loop of a product is spread over NACC tensor-memory accumulators
 // (chunk kc into accumulator kc % NACC) that the epilogue adds in FP32: each
 // accumulator then sums 1/NACC of the K' terms, which divides the
@@ -158,6 +158,8 @@ struct BigShared {
   uint64_t empty[MAX_NST];
   uint64_t done;
   uint64_t never;  // never arrived on: CTQ_DEBUG_STALL_WAIT waits on it
+  uint32_t issued;    // chunks issued by the producer (sequence numbers [0, issued))
+  uint32_t consumed;  // chunks whose data the MMA issuer has waited for
   uint32_t tmem_base;
   int fail;
   float red[8];
@@ -194,6 +196,8 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
     mbar_init(&S.done, 1);
     mbar_init(&S.never, 1);
     S.fail = 0;
+    S.issued = 0;
+    S.consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(&S.tmem_base, NACC * BN);
@@ -202,7 +206,7 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
   tc_fence_after();
   const uint32_t tD = S.tmem_base;
   const uint32_t lane_off = uint32_t(32 * warp) << 16;
-  uint32_t ph_full[MAX_NST] = {0, 0, 0, 0, 0, 0}, ph_empty[MAX_NST] = {0, 0, 0, 0, 0, 0};
+  uint32_t seq_base = 0;  // sequence number of chunk 0 of the current tile (all threads)
   uint32_t ph_done = 0;
   bool alive = true;
   if (cfg.debug & CTQ_DEBUG_STALL_WAIT) {
@@ -438,36 +442,56 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
       const int nxt = cur ^ 1;
       int ek = 0;
       float f2 = 0.f;
+      // Warp-specialised pipeline.  Chunks carry a per-CTA sequence number q
+      // (q = seq_base + kc within a tile), live in stage q % NST and complete
+      // phase q / NST of that stage's full / empty barriers.  Thread 32 (the
+      // producer) refills a stage as soon as the products reading it have
+      // completed and, at the end of a tile, issues the first chunks of the
+      // CTA's next tile of the same product; thread 0 (the MMA issuer) only
+      // waits for data, so the tensor core can have up to NST chunks queued.
+      // Both then join the epilogue.
+      volatile int* fail_v = &S.fail;
+      auto produce = [&](uint32_t q, int tt, int kc) -> bool {
+        const int mt_ = tt % n_mt, nt_ = tt / n_mt;
+        const int st = int(q % uint32_t(NST));
+        if (q >= uint32_t(NST) && !mbar_wait(&S.empty[st], ((q / NST) - 1u) & 1u, P.timeout_ns)) return false;
+        unsigned char* sb = stage0 + size_t(st) * stage_bytes;
+        const size_t ao = (size_t(mt_) * nkc + kc) * a_tile, bo = (size_t(nt_) * nkc + kc) * b_tile;
+        mbar_arrive_expect_tx(&S.full[st], stage_bytes);
+        bulk_g2s(sb, Zh[cur] + ao, A_BYTES, &S.full[st]);
+        bulk_g2s(sb + A_BYTES, Bt + bo, B_BYTES, &S.full[st]);
+        if (SPLIT) {
+          bulk_g2s(sb + A_BYTES + B_BYTES, Zl[cur] + ao, A_BYTES, &S.full[st]);
+          bulk_g2s(sb + 2 * A_BYTES + B_BYTES, Bt + b_plane + bo, B_BYTES, &S.full[st]);
+        }
+        S.issued = q + 1;
+        return true;
+      };
+      int pre = 0;  // (producer) chunks of the current tile already issued
       for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const int mt = t % n_mt, nt = t / n_mt;  // column-major: B tiles reused across rows
         const int ncols = min(BN, 2 * dpn - nt * BN);
         const uint32_t idesc = (PREC == CTQ_BF16X3) ? idesc_bf16(BM, ncols) : idesc_tf32(BM, ncols);
-        const T* Asrc = Zh[cur] + size_t(mt) * nkc * a_tile;
-        const T* Alo = Zl[cur] + size_t(mt) * nkc * a_tile;
-        const T* Bsrc = Bt + size_t(nt) * nkc * b_tile;
-        const T* Blo = Bsrc + b_plane;
-        if (tid == 0) {
-          auto issue = [&](int kc) {
-            const int st = kc % NST;
-            unsigned char* sb = stage0 + size_t(st) * stage_bytes;
-            mbar_arrive_expect_tx(&S.full[st], stage_bytes);
-            bulk_g2s(sb, Asrc + size_t(kc) * a_tile, A_BYTES, &S.full[st]);
-            bulk_g2s(sb + A_BYTES, Bsrc + size_t(kc) * b_tile, B_BYTES, &S.full[st]);
-            if (SPLIT) {
-              bulk_g2s(sb + A_BYTES + B_BYTES, Alo + size_t(kc) * a_tile, A_BYTES, &S.full[st]);
-              bulk_g2s(sb + 2 * A_BYTES + B_BYTES, Blo + size_t(kc) * b_tile, B_BYTES, &S.full[st]);
+        if (tid == 32) {
+          bool okp = true;
+          for (int kc = pre; kc < nkc && okp && !*fail_v; ++kc) okp = produce(seq_base + kc, t, kc);
+          pre = 0;
+          const int tn = t + int(gridDim.x);
+          if (okp && tn < n_tiles) {
+            const int np = min(NST, nkc);
+            for (int j = 0; j < np && okp && !*fail_v; ++j) okp = produce(seq_base + nkc + j, tn, j);
+            pre = np;
+          }
+          if (!okp) *fail_v = 1;
+        } else if (tid == 0) {
+          for (int kc = 0; kc < nkc; ++kc) {
+            const uint32_t q = seq_base + kc;
+            const int st = int(q % uint32_t(NST));
+            if (*fail_v || !mbar_wait(&S.full[st], (q / NST) & 1u, P.timeout_ns)) {
+              *fail_v = 1;
+              break;
             }
-          };
-          // Chunk kc lives in stage kc % NST.  After the products of chunk kc
-          // are queued, the stage of chunk kc - 1 is refilled with chunk
-          // kc - 1 + NST as soon as its products have completed, so loads run
-          // NST - 1 chunks ahead of the tensor core.
-          for (int kc = 0; kc < min(NST, nkc); ++kc) issue(kc);
-          int waited_upto = 0;  // chunks [0, waited_upto) have had their empty barrier waited
-          for (int kc = 0; kc < nkc && !S.fail; ++kc) {
-            const int st = kc % NST;
-            if (!mbar_wait(&S.full[st], ph_full[st], P.timeout_ns)) { S.fail = 1; break; }
-            ph_full[st] ^= 1u;
+            S.consumed = q + 1;
             tc_fence_after();
             const uint32_t sa = smem_u32(stage0 + size_t(st) * stage_bytes);
             const uint32_t sbh = sa + A_BYTES, sal = sbh + B_BYTES, sbl = sal + A_BYTES;
@@ -483,26 +507,20 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
               }
             }
             mma_commit(&S.empty[st]);
-            if (kc >= 1) {
-              const int pk = kc - 1, ps = pk % NST;
-              if (!mbar_wait(&S.empty[ps], ph_empty[ps], P.timeout_ns)) { S.fail = 1; break; }
-              ph_empty[ps] ^= 1u;
-              waited_upto = kc;
-              if (pk + NST < nkc) issue(pk + NST);
-            }
-          }
-          // keep the empty-barrier phases in step for the next tile
-          for (int kc = waited_upto; kc < nkc && !S.fail; ++kc) {
-            const int st = kc % NST;
-            if (!mbar_wait(&S.empty[st], ph_empty[st], P.timeout_ns)) { S.fail = 1; break; }
-            ph_empty[st] ^= 1u;
           }
           mma_commit(&S.done);
         }
+        seq_base += uint32_t(nkc);
         __syncthreads();
         const bool ok = (S.fail == 0) && mbar_wait(&S.done, ph_done, P.timeout_ns);
         ph_done ^= 1u;
-        if (__syncthreads_or(!ok)) { alive = false; break; }
+        if (__syncthreads_or(!ok)) {
+          if (tid == 32)  // let issued copies that were never consumed land before leaving
+            for (uint32_t q = S.consumed; q < S.issued; ++q)
+              mbar_wait(&S.full[q % uint32_t(NST)], (q / NST) & 1u, P.timeout_ns);
+          alive = false;
+          break;
+        }
         tc_fence_after();
         // epilogue: thread = row of the tile
         const int row = mt * BM + tid;
