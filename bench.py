@@ -272,9 +272,7 @@ def run_mixed(args, world, rank, local):
         thr = np.where(coin[idx] == 1, np.inf, -np.inf)
         imp = ctq.build_impurity(p, device=local)
         db = ctq.DeviceBatch(sub, device=dev, log_threshold=thr)
-        big = imp.is_complex or imp.max_dim > 112
-        gprec = ctq.TF32X3 if (prec == ctq.BF16X3 and not big) else prec  # bf16x3: large-block engine only
-        ev = ctq.TraceEvaluator(imp, sub.n_chains, db.max_ops, precision=gprec, device=dev)
+        ev = ctq.TraceEvaluator(imp, sub.n_chains, db.max_ops, precision=prec, device=dev)
         f, _ = algorithmic_flops(imp, sub.subset(np.nonzero(coin[idx] == 0)[0]))
         flops += f
         groups.append((p.name, imp, db, ev, sub.n_chains))
@@ -495,7 +493,7 @@ def roofline(precision, achieved_tf, fp64_peak, traffic, big=False):
     bf16 = precision == "bf16x3"
     peak = peaks["bf16_tflops"] * (1.0 if bf16 else 0.5)
     passes = 1 if precision == "tf32" else 3
-    kernel = (f"k_trace_big<{precision}>" if big else f"k_trace_tc<{passes}>")
+    kernel = f"k_trace_big<{precision}>" if big else f"k_trace_tc<{precision}>"
     return {"kernel": kernel, "bound": "tensor", "achieved": achieved_tf, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved_tf / peak, "hardware_passes": passes,
             "peak_source": (f"{src} bf16 dense, MEASURED_PEAKS.json" if bf16 else

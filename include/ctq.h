@@ -183,8 +183,8 @@ typedef struct {
  *   tensor cores: real impurities with sector blocks <= 112 states use the
  *   small-block kernel, any other impurity with blocks <= 3072 states the
  *   large-block kernel (complex blocks in their real embedding).  CTQ_BF16X3
- *   (bf16 hi / lo operands, hi*hi + hi*lo + lo*hi) is built for the
- *   large-block kernel only.  Other combinations: CTQ_ERR_UNSUPPORTED.
+ *   (bf16 hi / lo operands, hi*hi + hi*lo + lo*hi) runs on both kernels.
+ *   Other combinations: CTQ_ERR_UNSUPPORTED.
  * lazy: 1 = stop a chain as soon as its upper bound falls below its threshold
  *   (needs log_threshold).  segment: operators per bound refinement (>= 1).
  * max_ops: largest 2k in the batch (sizes the bounds output).
@@ -280,11 +280,12 @@ void ctq_free_impurity(ctq_impurity* imp);
 int ctq_probe_fma_rate(int device, int kind, int iters, double* flops_per_s);
 
 /*
- * Diagnostic of the tensor-core operand conventions used by CTQ_TF32 /
- * CTQ_TF32X3: computes D = A B^T on `device` with one tcgen05 MMA sequence
+ * Diagnostic of the small-block kernel's tensor-core operand conventions
+ * (every precision): computes D = A B^T on `device` with one tcgen05 MMA sequence
  * (A: host 128 x K row-major floats, placed in tensor memory; B: host N x K
  * row-major floats, staged in shared memory as K-major core matrices; D: host
- * 128 x N row-major floats), split = 1 (TF32) or 3 (hi*hi + hi*lo + lo*hi).
+ * 128 x N row-major floats), split = CTQ_TF32, CTQ_TF32X3 or CTQ_BF16X3
+ * (the split modes: hi*hi + hi*lo + lo*hi).
  * N in [16, 112] and K in [16, 112], both multiples of 16.  Allocates and frees
  * device buffers and synchronises.  No counterpart in the paper.
  * Errors: CTQ_ERR_ARG, CTQ_ERR_NOMEM, CTQ_ERR_CUDA, CTQ_ERR_TIMEOUT.

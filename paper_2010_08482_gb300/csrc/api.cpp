@@ -17,8 +17,8 @@ struct ctq_impurity {
   ctq::DevModel dev{};
   ctq::LaunchCfg launch{};
   // tensor-core path (real impurities with blocks <= 112): TF32 and 3xTF32
-  ctq::TcParams tc1{}, tc3{};
-  ctq::LaunchCfg launch_tc1{}, launch_tc3{};
+  ctq::TcParams tc1{}, tc2{}, tc3{};  // CTQ_TF32, CTQ_BF16X3, CTQ_TF32X3
+  ctq::LaunchCfg launch_tc1{}, launch_tc2{}, launch_tc3{};
   // large-block tensor-core path (complex impurities or blocks > 112)
   bool big = false;
   ctq::BigParams big1{}, big2{}, big3{};  // CTQ_TF32, CTQ_BF16X3, CTQ_TF32X3
@@ -118,23 +118,32 @@ int upload_model(ctq_impurity* imp) {
     return fail(st, "cannot configure the trace kernel");
   }
   if (!h.is_complex && h.max_dim <= 112) {
-    std::vector<float> tcb;
-    std::vector<int64_t> tco;
-    int stage3 = 0;
-    if ((st = ctq::build_tc_blocks(h, 3, tcb, tco, &stage3)) != CTQ_OK ||
-        (st = upload_vec(imp, tcb, &imp->tc3.blk)) != CTQ_OK || (st = upload_vec(imp, tco, &imp->tc3.off)) != CTQ_OK) {
+    std::vector<unsigned char> tcb, tcb16;
+    std::vector<int64_t> tco, tco16;
+    int stage3 = 0, stage2 = 0;
+    const unsigned char *b3 = nullptr, *b2 = nullptr;
+    if ((st = ctq::build_tc_blocks(h, CTQ_TF32X3, tcb, tco, &stage3)) != CTQ_OK ||
+        (st = ctq::build_tc_blocks(h, CTQ_BF16X3, tcb16, tco16, &stage2)) != CTQ_OK ||
+        (st = upload_vec(imp, tcb, &b3)) != CTQ_OK || (st = upload_vec(imp, tco, &imp->tc3.off)) != CTQ_OK ||
+        (st = upload_vec(imp, tcb16, &b2)) != CTQ_OK || (st = upload_vec(imp, tco16, &imp->tc2.off)) != CTQ_OK) {
       free_device(imp);
       return fail(st, "tensor-core block upload failed");
     }
-    imp->tc3.split = 3;
-    imp->tc3.stage_floats = stage3;
+    imp->tc3.blk = b3;
+    imp->tc2.blk = b2;
+    imp->tc3.prec = CTQ_TF32X3;
+    imp->tc3.stage_bytes = stage3;
     imp->tc3.tmem_cols = 512;
-    imp->tc1 = imp->tc3;  // same blocks; TF32 fetches only the hi half
-    imp->tc1.split = 1;
-    imp->tc1.stage_floats = stage3 / 2;
+    imp->tc1 = imp->tc3;  // same blocks; TF32 fetches only the hi plane
+    imp->tc1.prec = CTQ_TF32;
+    imp->tc1.stage_bytes = stage3 / 2;
     imp->tc1.tmem_cols = 256;
-    if ((st = ctq::prepare_eval_tc(d, 3, imp->tc3.stage_floats, imp->num_sms, &imp->launch_tc3)) != CTQ_OK ||
-        (st = ctq::prepare_eval_tc(d, 1, imp->tc1.stage_floats, imp->num_sms, &imp->launch_tc1)) != CTQ_OK) {
+    imp->tc2.prec = CTQ_BF16X3;
+    imp->tc2.stage_bytes = stage2;
+    imp->tc2.tmem_cols = 256;
+    if ((st = ctq::prepare_eval_tc(d, CTQ_TF32X3, imp->tc3.stage_bytes, imp->num_sms, &imp->launch_tc3)) != CTQ_OK ||
+        (st = ctq::prepare_eval_tc(d, CTQ_TF32, imp->tc1.stage_bytes, imp->num_sms, &imp->launch_tc1)) != CTQ_OK ||
+        (st = ctq::prepare_eval_tc(d, CTQ_BF16X3, imp->tc2.stage_bytes, imp->num_sms, &imp->launch_tc2)) != CTQ_OK) {
       free_device(imp);
       return fail(st, "cannot configure the tensor-core kernel");
     }
@@ -435,10 +444,10 @@ int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_e
   if (opts->precision != CTQ_FP64 && opts->precision != CTQ_TF32 && opts->precision != CTQ_TF32X3 &&
       opts->precision != CTQ_BF16X3)
     return fail(CTQ_ERR_UNSUPPORTED, "unknown precision");
-  if (opts->precision == CTQ_BF16X3 && !imp->big)
-    return fail(CTQ_ERR_UNSUPPORTED, "CTQ_BF16X3 is built for the large-block path only");
-  if (opts->precision != CTQ_FP64 && !imp->big &&
-      (opts->precision == CTQ_TF32 ? imp->launch_tc1.per_sm : imp->launch_tc3.per_sm) < 1)
+  const int pr = opts->precision;
+  const ctq::TcParams& tcp = pr == CTQ_TF32 ? imp->tc1 : pr == CTQ_BF16X3 ? imp->tc2 : imp->tc3;
+  const ctq::LaunchCfg& tcl = pr == CTQ_TF32 ? imp->launch_tc1 : pr == CTQ_BF16X3 ? imp->launch_tc2 : imp->launch_tc3;
+  if (pr != CTQ_FP64 && !imp->big && tcl.per_sm < 1)
     return fail(CTQ_ERR_UNSUPPORTED, "no tensor-core path for this impurity");
   if (!workspace) return fail(CTQ_ERR_ARG, "null workspace");
   if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return fail(CTQ_ERR_ARG, "workspace not 256-byte aligned");
@@ -473,17 +482,15 @@ int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_e
   if (opts->precision == CTQ_FP64) {
     st = ctq::launch_eval_fp64(imp->dev, imp->launch, B, cfg, W, result, stream, opts->timing_events);
   } else if (imp->big) {
-    const int pr = opts->precision;
     ctq::BigParams P = pr == CTQ_TF32 ? imp->big1 : pr == CTQ_BF16X3 ? imp->big2 : imp->big3;
     const ctq::LaunchCfg& lc = pr == CTQ_TF32 ? imp->launch_big1 : pr == CTQ_BF16X3 ? imp->launch_big2 : imp->launch_big3;
     P.timeout_ns = opts->timeout_ns > 0 ? uint64_t(opts->timeout_ns) : uint64_t(2000000000ull);
     char* scratch = static_cast<char*>(workspace) + ((base + 255) & ~size_t(255));
     st = ctq::launch_eval_big(imp->dev, lc, P, B, cfg, W, result, scratch, stream, opts->timing_events);
   } else {
-    ctq::TcParams P = opts->precision == CTQ_TF32 ? imp->tc1 : imp->tc3;
+    ctq::TcParams P = tcp;
     P.timeout_ns = opts->timeout_ns > 0 ? uint64_t(opts->timeout_ns) : uint64_t(2000000000ull);
-    st = ctq::launch_eval_tc(imp->dev, opts->precision == CTQ_TF32 ? imp->launch_tc1 : imp->launch_tc3, P, B, cfg,
-                             W, result, stream, opts->timing_events);
+    st = ctq::launch_eval_tc(imp->dev, tcl, P, B, cfg, W, result, stream, opts->timing_events);
   }
   if (st != CTQ_OK) return fail(st, st == CTQ_ERR_CUDA ? cudaGetErrorString(cudaGetLastError()) : "launch failed");
   return CTQ_OK;

@@ -140,10 +140,10 @@ struct LaunchCfg {
 
 // Kernel parameters specific to the tensor-core path (trace_tc.cu).
 struct TcParams {
-  const float* blk = nullptr;    // pre-formatted blocks (hi, lo) in core-matrix order
-  const int64_t* off = nullptr;  // [n_alpha * n_sec] float offsets into blk, -1 absent
-  int split = 1;                 // 1: TF32, 3: three-term TF32
-  int stage_floats = 0;          // floats per shared-memory stage
+  const void* blk = nullptr;     // pre-formatted blocks (hi, lo) in core-matrix order
+  const int64_t* off = nullptr;  // [n_alpha * n_sec] byte offsets into blk, -1 absent
+  int prec = CTQ_TF32;           // CTQ_TF32, CTQ_TF32X3 or CTQ_BF16X3
+  int stage_bytes = 0;           // bytes per shared-memory stage
   int tmem_cols = 256;           // TMEM columns allocated per CTA
   uint64_t timeout_ns = 0;
 };
@@ -172,9 +172,9 @@ int launch_eval_big(const DevModel& M, const LaunchCfg& lc, BigParams P, const B
                     const Work& W, const ctq_result* R, void* scratch, void* stream, void* const* events);
 
 // Launchers (trace_fp64.cu, trace_tc.cu).  Return a CTQ_* status.
-int build_tc_blocks(const HostModel& h, int split, std::vector<float>& out, std::vector<int64_t>& off,
-                    int* stage_floats);
-int prepare_eval_tc(const DevModel& M, int split, int stage_floats, int num_sms, LaunchCfg* lc);
+int build_tc_blocks(const HostModel& h, int prec, std::vector<unsigned char>& out, std::vector<int64_t>& off,
+                    int* stage_bytes);
+int prepare_eval_tc(const DevModel& M, int prec, int stage_bytes, int num_sms, LaunchCfg* lc);
 int launch_eval_tc(const DevModel& M, const LaunchCfg& lc, const TcParams& P, const BatchView& B,
                    const EvalCfg& cfg, const Work& W, const ctq_result* R, void* stream, void* const* events);
 int prepare_eval_fp64(const DevModel& M, int num_sms, LaunchCfg* lc);

@@ -74,13 +74,6 @@ __host__ __device__ __forceinline__ size_t tiled_off(int r, int k, int rows_per_
          size_t((kk / EPC) * (rows_per_tile >> 3) + (rr >> 3)) * (8 * EPC) + (rr & 7) * EPC + (kk % EPC);
 }
 
-// bf16 bits of x rounded to nearest even (finite x), and the value they hold.
-__device__ __forceinline__ uint32_t bf16_bits(float x) {
-  const uint32_t u = __float_as_uint(x);
-  return (u + 0x7fffu + ((u >> 16) & 1u)) >> 16;
-}
-__device__ __forceinline__ float bf16_val(uint32_t b) { return __uint_as_float(b << 16); }
-
 // hi / lo split of x in the operand format of PREC.
 template <int PREC>
 __device__ __forceinline__ void split_store(float x, typename Elt<PREC>::T& hi, typename Elt<PREC>::T& lo) {

@@ -1,7 +1,8 @@
 // Sector-string local trace on the 5th-generation tensor cores (tcgen05).
 //
 // Same mathematics as k_trace (trace_fp64.cu), with the block products in
-// TF32 or in three-term split TF32 (hi*hi + hi*lo + lo*hi) with FP32
+// TF32, in three-term split TF32 (hi*hi + hi*lo + lo*hi) or in three-term
+// split bf16 (bf16 hi / lo operands, kind::f16 MMAs), all with FP32
 // accumulation; the log scale, the renormalisation exponents, the segment
 // bounds and the final trace sum stay in float64 (mixed-precision reading of
 // Sec. 3.3.2, which anticipates mixed-precision products).
@@ -11,7 +12,8 @@
 //       Z_{i+1} = Z_i F_{i+1}^T P_{i+1}
 //   so that the running product is the MMA's A operand and stays in tensor
 //   memory (TMEM) for the whole chain: A = Z_i (128 lanes = rows of Z, one
-//   32-bit column per K element), B = F_{i+1}^T, whose K-major form is F's own
+//   32-bit column per tf32 K element, or two bf16 K elements packed per
+//   column), B = F_{i+1}^T, whose K-major form is F's own
 //   row-major layout, staged from a pre-formatted global copy into shared
 //   memory by cp.async.bulk (double-buffered: the next block is prefetched
 //   while the current MMA runs), D accumulates in TMEM.  The epilogue reads
@@ -38,6 +40,7 @@ using namespace ptx;
 
 constexpr int TC_THREADS = 128;
 constexpr int TC_M = 128;
+constexpr int TC_MAX_DIM = 112;  // largest sector of the small-block kernel (A, D <= 128 columns)
 
 // Block-wide (max, sum) of floats; all threads get the result.  red: 8 floats.
 __device__ __forceinline__ void block_max_sum_f(float& mx, float& sm, float* red) {
@@ -58,6 +61,84 @@ __device__ __forceinline__ void block_max_sum_f(float& mx, float& sm, float* red
 
 __device__ __forceinline__ int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+// K padding of a block: one MMA takes 8 tf32 or 16 bf16 K elements.
+__host__ __device__ constexpr int tc_kstep(int prec) { return prec == CTQ_BF16X3 ? 16 : 8; }
+
+// Writes 16 consecutive K elements (from column element c0) of this
+// thread's row of the A operand into tensor memory, split as PREC needs.
+template <int PREC>
+__device__ __forceinline__ void store_a16(uint32_t tAh, uint32_t tAl, int c0, const float (&x)[16]) {
+  if constexpr (PREC == CTQ_BF16X3) {
+    uint32_t hi[8], lo[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const uint32_t h0 = bf16_bits(x[2 * t]), h1 = bf16_bits(x[2 * t + 1]);
+      const uint32_t l0 = bf16_bits(x[2 * t] - bf16_val(h0)), l1 = bf16_bits(x[2 * t + 1] - bf16_val(h1));
+      hi[t] = h0 | (h1 << 16);
+      lo[t] = l0 | (l1 << 16);
+    }
+    tmem_st8(tAh + uint32_t(c0 / 2), hi);
+    tmem_st8(tAl + uint32_t(c0 / 2), lo);
+  } else {
+    uint32_t hi[16], lo[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      hi[t] = to_tf32(x[t]);
+      lo[t] = to_tf32(x[t] - __uint_as_float(hi[t]));
+    }
+    tmem_st16(tAh + uint32_t(c0), hi);
+    if (PREC == CTQ_TF32X3) tmem_st16(tAl + uint32_t(c0), lo);
+  }
+}
+
+// Reads back 16 K elements of this thread's row of A (hi + lo).
+template <int PREC>
+__device__ __forceinline__ void load_a16(uint32_t tAh, uint32_t tAl, int c0, float (&z)[16]) {
+  if constexpr (PREC == CTQ_BF16X3) {
+    uint32_t hi[8], lo[8];
+    tmem_ld8(tAh + uint32_t(c0 / 2), hi);
+    tmem_ld8(tAl + uint32_t(c0 / 2), lo);
+    tmem_wait_ld();
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      z[2 * t] = bf16_val(hi[t] & 0xffffu) + bf16_val(lo[t] & 0xffffu);
+      z[2 * t + 1] = bf16_val(hi[t] >> 16) + bf16_val(lo[t] >> 16);
+    }
+  } else {
+    uint32_t hi[16], lo[16];
+    tmem_ld16(tAh + uint32_t(c0), hi);
+    if (PREC == CTQ_TF32X3) tmem_ld16(tAl + uint32_t(c0), lo);
+    tmem_wait_ld();
+#pragma unroll
+    for (int t = 0; t < 16; ++t) z[t] = __uint_as_float(hi[t]) + (PREC == CTQ_TF32X3 ? __uint_as_float(lo[t]) : 0.f);
+  }
+}
+
+// D = A B^T for one block: A in tensor memory (hi at tAh, lo at tAl), B in
+// shared memory at sb (hi plane, then lo plane at lo_off bytes), np x kp.
+template <int PREC>
+__device__ __forceinline__ void mma_block(uint32_t tD, uint32_t tAh, uint32_t tAl, uint32_t sb, int np, int kp,
+                                          uint32_t lo_off) {
+  const uint32_t lbo = uint32_t(np / 8) * 128u, sbo = 128u;
+  const uint32_t id = (PREC == CTQ_BF16X3) ? idesc_bf16(TC_M, np) : idesc_tf32(TC_M, np);
+  // one MMA: 32 bytes of K (two core matrices of B, 8 tensor-memory columns of A)
+  for (int kk = 0; kk < kp / tc_kstep(PREC); ++kk) {
+    const uint32_t kb = uint32_t(2 * kk) * lbo;
+    const uint32_t ah = tAh + 8u * kk, al = tAl + 8u * kk;
+    if constexpr (PREC == CTQ_BF16X3) {
+      mma_bf16_ts(tD, ah, sdesc(sb + kb, lbo, sbo), id, kk > 0 ? 1u : 0u);
+      mma_bf16_ts(tD, ah, sdesc(sb + lo_off + kb, lbo, sbo), id, 1u);
+      mma_bf16_ts(tD, al, sdesc(sb + kb, lbo, sbo), id, 1u);
+    } else {
+      mma_tf32_ts(tD, ah, sdesc(sb + kb, lbo, sbo), id, kk > 0 ? 1u : 0u);
+      if (PREC == CTQ_TF32X3) {
+        mma_tf32_ts(tD, ah, sdesc(sb + lo_off + kb, lbo, sbo), id, 1u);
+        mma_tf32_ts(tD, al, sdesc(sb + kb, lbo, sbo), id, 1u);
+      }
+    }
+  }
+}
+
 // Shared state of one CTA.
 struct TcShared {
   uint64_t bar_load[2];
@@ -76,14 +157,16 @@ struct TcShared {
 
 namespace {
 
-template <int SPLIT>
+template <int PREC>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_trace_tc(DevModel M, BatchView B, EvalCfg cfg, Work W, TcParams P) {
+  constexpr int EB = PREC == CTQ_BF16X3 ? 2 : 4;  // bytes per staged B element
+  constexpr bool SPLIT = PREC != CTQ_TF32;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  float* stage[2];
-  stage[0] = reinterpret_cast<float*>(smem_raw);
-  stage[1] = stage[0] + P.stage_floats;
-  float* p_s = stage[1] + P.stage_floats;  // [128] column scales of the current step
+  unsigned char* stage[2];
+  stage[0] = smem_raw;
+  stage[1] = stage[0] + P.stage_bytes;
+  float* p_s = reinterpret_cast<float*>(stage[1] + P.stage_bytes);  // [128] column scales of the current step
   float* p0_s = p_s + TC_M;                // [128] wrap-around propagator of q0
   __shared__ TcShared S;
 
@@ -114,9 +197,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   const uint32_t tbase = S.tmem_base;
   const uint32_t lane_off = uint32_t(32 * warp) << 16;
-  const uint32_t tD = tbase;          // D: columns [0, 128)
-  const uint32_t tAh = tbase + 128;   // A hi: [128, 256)
-  const uint32_t tAl = tbase + 256;   // A lo: [256, 384) (split mode)
+  // D: columns [0, 128); A hi from 128; A lo from 256 (3xTF32) or 192 (bf16,
+  // two K elements per column).  Addresses include this warp's lane quarter.
+  const uint32_t tD = tbase;
+  const uint32_t tAh = tbase + 128 + lane_off;
+  const uint32_t tAl = tbase + (PREC == CTQ_BF16X3 ? 192 : 256) + lane_off;
 
   uint32_t ph_load[2] = {0, 0};   // next parity to wait for, per stage (thread 0)
   int pending[2] = {0, 0};        // loads issued and not yet waited for (thread 0)
@@ -206,10 +291,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (tid == 0 && n > 2) {
       const int alpha2 = B.op[a0 + 1];
       const int qn = M.s[alpha2 * ns + qb];
-      const int np = round_up(M.dims[qn], 16), kp = round_up(M.dims[qb], 8);
-      const uint32_t bytes = uint32_t(SPLIT == 3 ? 2 : 1) * np * kp * 4;
+      const int np = round_up(M.dims[qn], 16), kp = round_up(M.dims[qb], tc_kstep(PREC));
+      const uint32_t bytes = uint32_t(SPLIT ? 2 : 1) * np * kp * EB;
       mbar_arrive_expect_tx(&S.bar_load[0], bytes);
-      bulk_g2s(stage[0], P.blk + P.off[alpha2 * ns + qb], bytes, &S.bar_load[0]);
+      bulk_g2s(stage[0], static_cast<const unsigned char*>(P.blk) + P.off[alpha2 * ns + qb], bytes, &S.bar_load[0]);
       pending[0] = 1;
     }
     __syncthreads();
@@ -220,19 +305,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int kp = round_up(dcur, 16);
       const float p0r = p0_s[row];
       for (int c0 = 0; c0 < kp; c0 += 16) {
-        uint32_t hi[16], lo[16];
+        float x[16];
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
           const int m = c0 + t;
-          float x = 0.f;
-          if (row < d0 && m < dcur) x = float(M.blk[off + int64_t(m) * d0 + row]) * p0r * p_s[m];
-          mx = fmaxf(mx, fabsf(x));
-          fr += x * x;
-          hi[t] = to_tf32(x);
-          lo[t] = to_tf32(x - __uint_as_float(hi[t]));
+          x[t] = 0.f;
+          if (row < d0 && m < dcur) x[t] = float(M.blk[off + int64_t(m) * d0 + row]) * p0r * p_s[m];
+          mx = fmaxf(mx, fabsf(x[t]));
+          fr += x[t] * x[t];
         }
-        tmem_st16(tAh + lane_off + c0, hi);
-        if (SPLIT == 3) tmem_st16(tAl + lane_off + c0, lo);
+        store_a16<PREC>(tAh, tAl, c0, x);
       }
       tmem_wait_st();
     }
@@ -291,18 +373,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         float acc = 0.f;
         tc_fence_after();
         for (int c0 = 0; c0 < round_up(dcur, 16); c0 += 16) {
-          uint32_t hi[16], lo[16];
-          tmem_ld16(tAh + lane_off + c0, hi);
-          if (SPLIT == 3) tmem_ld16(tAl + lane_off + c0, lo);
-          tmem_wait_ld();
+          float z[16];
+          load_a16<PREC>(tAh, tAl, c0, z);
 #pragma unroll
           for (int t = 0; t < 16; ++t) {
             const int k = c0 + t;
-            if (row < d0 && k < dcur) {
-              float z = __uint_as_float(hi[t]);
-              if (SPLIT == 3) z += __uint_as_float(lo[t]);
-              acc = fmaf(float(M.blk[off + int64_t(row) * dcur + k]), z, acc);
-            }
+            if (row < d0 && k < dcur) acc = fmaf(float(M.blk[off + int64_t(row) * dcur + k]), z[t], acc);
           }
         }
         vr = double(acc) * double(scale);
@@ -321,17 +397,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
       // ---- tensor-core product Z <- Z F^T, then column scale
       const int db = M.dims[qb];
-      const int np = round_up(db, 16), kp = round_up(dcur, 8);
+      const int np = round_up(db, 16), kp = round_up(dcur, tc_kstep(PREC));
       if (tid == 0) {
         // prefetch the next block into the other stage (its last reader has completed)
         if (i + 1 < n - 1) {
           const int alpha_n = B.op[a0 + i + 1];
           const int qn = M.s[alpha_n * ns + qb];
-          const int np2 = round_up(M.dims[qn], 16), kp2 = round_up(db, 8);
-          const uint32_t bytes = uint32_t(SPLIT == 3 ? 2 : 1) * np2 * kp2 * 4;
+          const int np2 = round_up(M.dims[qn], 16), kp2 = round_up(db, tc_kstep(PREC));
+          const uint32_t bytes = uint32_t(SPLIT ? 2 : 1) * np2 * kp2 * EB;
           const int st2 = cur_stage ^ 1;
           mbar_arrive_expect_tx(&S.bar_load[st2], bytes);
-          bulk_g2s(stage[st2], P.blk + P.off[alpha_n * ns + qb], bytes, &S.bar_load[st2]);
+          bulk_g2s(stage[st2], static_cast<const unsigned char*>(P.blk) + P.off[alpha_n * ns + qb], bytes,
+                   &S.bar_load[st2]);
           pending[st2] = 1;
         }
         // operand of this product
@@ -340,18 +417,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           ph_load[cur_stage] ^= 1u;
           pending[cur_stage] = 0;
           tc_fence_after();
-          const uint32_t sb = smem_u32(stage[cur_stage]);
-          const uint32_t lbo = uint32_t(np / 8) * 128u, sbo = 128u;
-          const uint32_t lo_off = uint32_t(np) * kp * 4u;
-          const uint32_t id = idesc_tf32(TC_M, np);
-          for (int kk = 0; kk < kp / 8; ++kk) {
-            const uint32_t kb = uint32_t(2 * kk) * lbo;
-            mma_tf32_ts(tD, tAh + 8 * kk, sdesc(sb + kb, lbo, sbo), id, kk > 0 ? 1u : 0u);
-            if (SPLIT == 3) {
-              mma_tf32_ts(tD, tAh + 8 * kk, sdesc(sb + lo_off + kb, lbo, sbo), id, 1u);
-              mma_tf32_ts(tD, tAl + 8 * kk, sdesc(sb + kb, lbo, sbo), id, 1u);
-            }
-          }
+          // thread 0 is lane 0 of warp 0: its A addresses are the operand's base
+          mma_block<PREC>(tD, tAh, tAl, smem_u32(stage[cur_stage]), np, kp, uint32_t(np) * kp * EB);
           mma_commit(&S.bar_mma);
         } else {
           S.fail = 1;
@@ -380,19 +447,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mx = 0.f;
       fr = 0.f;
       for (int c0 = 0; c0 < np; c0 += 16) {
-        uint32_t v[16], hi[16], lo[16];
+        uint32_t v[16];
+        float x[16];
         tmem_ld16(tD + lane_off + c0, v);
         tmem_wait_ld();
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
-          const float x = __uint_as_float(v[t]) * p_s[c0 + t];
-          mx = fmaxf(mx, fabsf(x));
-          fr += x * x;
-          hi[t] = to_tf32(x);
-          lo[t] = to_tf32(x - __uint_as_float(hi[t]));
+          x[t] = __uint_as_float(v[t]) * p_s[c0 + t];
+          mx = fmaxf(mx, fabsf(x[t]));
+          fr += x[t] * x[t];
         }
-        tmem_st16(tAh + lane_off + c0, hi);
-        if (SPLIT == 3) tmem_st16(tAl + lane_off + c0, lo);
+        store_a16<PREC>(tAh, tAl, c0, x);
       }
       tmem_wait_st();
       tc_fence_before();
@@ -439,12 +504,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // A (128 x K, row-major floats) written to TMEM with tcgen05.st, B (N x K,
 // row-major) formatted by the threads into K-major core matrices in shared
 // memory, D read back with tcgen05.ld.  Diagnostic for the descriptor and
-// layout conventions.
-template <int SPLIT>
+// layout conventions of each precision.
+template <int PREC>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm_check(const float* A, const float* Bm, float* D, int N,
                                                                  int K, uint64_t timeout_ns, int* status) {
+  constexpr int EB = PREC == CTQ_BF16X3 ? 2 : 4;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  float* sb = reinterpret_cast<float*>(smem_raw);
   __shared__ TcShared S;
   const int tid = threadIdx.x, warp = tid >> 5;
   if (tid == 0) {
@@ -456,15 +521,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm_check(const float* A,
                  "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  // B: hi at 0, lo at N*K (core matrix (nb, kb) at ((kb * N/8) + nb) * 32 floats)
+  // B: hi plane at 0, lo plane at N*K elements; core matrix (nb, kb) of 8 rows
+  // x 16 bytes at ((kb * N/8) + nb) * 128 bytes
   const int cnt = N * K;
+  constexpr int EPC = 16 / EB;
   for (int idx = tid; idx < cnt; idx += TC_THREADS) {
     const int nn = idx / K, k = idx - nn * K;
-    const int pos = ((k / 4) * (N / 8) + nn / 8) * 32 + (nn % 8) * 4 + (k % 4);
+    const int pos = ((k / EPC) * (N / 8) + nn / 8) * (8 * EPC) + (nn % 8) * EPC + (k % EPC);
     const float f = Bm[idx];
-    const uint32_t hi = to_tf32(f);
-    sb[pos] = __uint_as_float(hi);
-    sb[cnt + pos] = __uint_as_float(to_tf32(f - __uint_as_float(hi)));
+    if constexpr (PREC == CTQ_BF16X3) {
+      uint16_t* sb = reinterpret_cast<uint16_t*>(smem_raw);
+      const uint32_t h = bf16_bits(f);
+      sb[pos] = uint16_t(h);
+      sb[cnt + pos] = uint16_t(bf16_bits(f - bf16_val(h)));
+    } else {
+      float* sb = reinterpret_cast<float*>(smem_raw);
+      const uint32_t h = to_tf32(f);
+      sb[pos] = __uint_as_float(h);
+      sb[cnt + pos] = __uint_as_float(to_tf32(f - __uint_as_float(h)));
+    }
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   tc_fence_before();
@@ -472,34 +547,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm_check(const float* A,
   tc_fence_after();
   const uint32_t tbase = S.tmem_base;
   const uint32_t lane_off = uint32_t(32 * warp) << 16;
-  const uint32_t tD = tbase, tAh = tbase + 128, tAl = tbase + 256;
+  const uint32_t tD = tbase;
+  const uint32_t tAh = tbase + 128 + lane_off;
+  const uint32_t tAl = tbase + (PREC == CTQ_BF16X3 ? 192 : 256) + lane_off;
   for (int c0 = 0; c0 < K; c0 += 16) {
-    uint32_t hi[16], lo[16];
+    float x[16];
 #pragma unroll
-    for (int t = 0; t < 16; ++t) {
-      const float x = (c0 + t < K) ? A[tid * K + c0 + t] : 0.f;
-      hi[t] = to_tf32(x);
-      lo[t] = to_tf32(x - __uint_as_float(hi[t]));
-    }
-    tmem_st16(tAh + lane_off + c0, hi);
-    tmem_st16(tAl + lane_off + c0, lo);
+    for (int t = 0; t < 16; ++t) x[t] = (c0 + t < K) ? A[tid * K + c0 + t] : 0.f;
+    store_a16<PREC>(tAh, tAl, c0, x);
   }
   tmem_wait_st();
   tc_fence_before();
   __syncthreads();
   if (tid == 0) {
     tc_fence_after();
-    const uint32_t base = smem_u32(sb);
-    const uint32_t lbo = uint32_t(N / 8) * 128u, sbo = 128u;
-    const uint32_t id = idesc_tf32(TC_M, N);
-    for (int kk = 0; kk < K / 8; ++kk) {
-      const uint32_t kb = uint32_t(2 * kk) * lbo;
-      mma_tf32_ts(tD, tAh + 8 * kk, sdesc(base + kb, lbo, sbo), id, kk > 0 ? 1u : 0u);
-      if (SPLIT == 3) {
-        mma_tf32_ts(tD, tAh + 8 * kk, sdesc(base + uint32_t(cnt) * 4u + kb, lbo, sbo), id, 1u);
-        mma_tf32_ts(tD, tAl + 8 * kk, sdesc(base + kb, lbo, sbo), id, 1u);
-      }
-    }
+    mma_block<PREC>(tD, tAh, tAl, smem_u32(smem_raw), N, K, uint32_t(cnt) * EB);
     mma_commit(&S.bar_mma);
   }
   const bool ok = mbar_wait(&S.bar_mma, 0, timeout_ns);
@@ -529,12 +591,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm_check(const float* A,
 // ----------------------------------------------------------------- host side
 
 // Pre-formats every real block F_alpha(q) (d_{q'} x d_q) as the B operand of
-// Z F^T: N = d_{q'} rows padded to 16, K = d_q padded to 8, K-major core
-// matrices of 8 rows x 4 floats, core (nb, kb) at ((kb * N/8) + nb) * 32
-// floats; hi = tf32(F) and, for split mode, lo = tf32(F - hi) after it.
-int build_tc_blocks(const HostModel& h, int split, std::vector<float>& out, std::vector<int64_t>& off,
-                    int* stage_floats) {
+// Z F^T: N = d_{q'} rows padded to 16, K = d_q padded to 8 (tf32) or 16
+// (bf16), K-major core matrices of 8 rows x 16 bytes, core (nb, kb) at
+// ((kb * N/8) + nb) * 128 bytes; the hi plane (tf32(F) or bf16(F)) and, for
+// the split precisions, the lo plane (of F - hi) after it.  Offsets and
+// stage sizes in bytes; every block starts on a 128-byte boundary.
+int build_tc_blocks(const HostModel& h, int prec, std::vector<unsigned char>& out, std::vector<int64_t>& off,
+                    int* stage_bytes) {
   if (h.is_complex) return CTQ_ERR_UNSUPPORTED;
+  const bool bf = prec == CTQ_BF16X3;
+  const bool split = prec != CTQ_TF32;
+  const int eb = bf ? 2 : 4, epc = 16 / eb, kstep = tc_kstep(prec);
   const int na = h.n_alpha();
   off.assign(size_t(na) * h.n_sec, -1);
   out.clear();
@@ -550,50 +617,93 @@ int build_tc_blocks(const HostModel& h, int split, std::vector<float>& out, std:
     std::memcpy(&r, &u, 4);
     return r;
   };
+  auto bf16 = [](float x) -> uint16_t {  // round to nearest even (finite x)
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    return uint16_t((u + 0x7fffu + ((u >> 16) & 1u)) >> 16);
+  };
+  auto bf16_value = [](uint16_t b) {
+    const uint32_t u = uint32_t(b) << 16;
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+  };
   for (int a = 0; a < na; ++a)
     for (int q = 0; q < h.n_sec; ++q) {
       const size_t i = size_t(a) * h.n_sec + q;
       const int qp = h.s[i];
       if (qp < 0) continue;
       const int dn = h.dims[qp], dk = h.dims[q];
-      const int np = (dn + 15) / 16 * 16, kp = (dk + 7) / 8 * 8;
-      const size_t base = (out.size() + 31) / 32 * 32;  // 128-byte aligned
-      const size_t cnt = size_t(np) * kp;
-      out.resize(base + (split == 3 ? 2 : 1) * cnt, 0.0f);
+      const int np = (dn + 15) / 16 * 16, kp = (dk + kstep - 1) / kstep * kstep;
+      const size_t base = (out.size() + 127) / 128 * 128;
+      const size_t cnt = size_t(np) * kp;  // elements of one plane
+      const size_t bytes = (split ? 2 : 1) * cnt * eb;
+      out.resize(base + bytes, 0);
       off[i] = int64_t(base);
-      max_stage = std::max(max_stage, int((split == 3 ? 2 : 1) * cnt));
+      max_stage = std::max(max_stage, int(bytes));
       const double* F = &h.blk_re[h.blk_off[i]];
       for (int nn = 0; nn < dn; ++nn)
         for (int k = 0; k < dk; ++k) {
-          const size_t pos = (size_t(k / 4) * (np / 8) + nn / 8) * 32 + (nn % 8) * 4 + (k % 4);
+          const size_t pos = (size_t(k / epc) * (np / 8) + nn / 8) * (8 * epc) + (nn % 8) * epc + (k % epc);
           const double f = F[size_t(nn) * dk + k];
-          const float hi = tf32(float(f));
-          out[base + pos] = hi;
-          if (split == 3) out[base + cnt + pos] = tf32(float(f - double(hi)));
+          if (bf) {
+            const uint16_t hi = bf16(float(f));
+            const uint16_t lo = bf16(float(f - double(bf16_value(hi))));
+            std::memcpy(&out[base + pos * 2], &hi, 2);
+            std::memcpy(&out[base + (cnt + pos) * 2], &lo, 2);
+          } else {
+            const float hi = tf32(float(f));
+            std::memcpy(&out[base + pos * 4], &hi, 4);
+            if (split) {
+              const float lo = tf32(float(f - double(hi)));
+              std::memcpy(&out[base + (cnt + pos) * 4], &lo, 4);
+            }
+          }
         }
     }
-  *stage_floats = max_stage;
+  *stage_bytes = max_stage;
   return CTQ_OK;
 }
 
-int prepare_eval_tc(const DevModel& M, int split, int stage_floats, int num_sms, LaunchCfg* lc) {
+template <int PREC>
+static cudaError_t tc_attr(size_t smem) {
+  const cudaError_t e = cudaFuncSetAttribute(k_trace_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  // all of the SM's unified L1 / shared storage as shared memory, so that two
+  // CTAs of the 256-column precisions can be resident together
+  return cudaFuncSetAttribute(k_trace_tc<PREC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              int(cudaSharedmemCarveoutMaxShared));
+}
+
+int prepare_eval_tc(const DevModel& M, int prec, int stage_bytes, int num_sms, LaunchCfg* lc) {
   lc->threads = TC_THREADS;
-  lc->smem = size_t(2) * stage_floats * 4 + 2 * TC_M * 4;
+  lc->smem = size_t(2) * stage_bytes + 2 * TC_M * 4;
   // At most 512 / tmem_cols CTAs may share an SM (each holds its TMEM for the
   // whole kernel): request enough shared memory to enforce that.
-  lc->smem = std::max(lc->smem, size_t(split == 3 ? 116 * 1024 : 76 * 1024));
+  lc->smem = std::max(lc->smem, size_t(prec == CTQ_TF32X3 ? 116 * 1024 : 76 * 1024));
   lc->num_sms = num_sms;
   lc->per_sm = 0;
-  if (M.is_complex || M.max_dim > TC_M || lc->smem > 227 * 1024) return CTQ_OK;  // not supported
-  cudaError_t e = (split == 3)
-                      ? cudaFuncSetAttribute(k_trace_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lc->smem))
-                      : cudaFuncSetAttribute(k_trace_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lc->smem));
+  if (M.is_complex || M.max_dim > TC_MAX_DIM || lc->smem > 227 * 1024) return CTQ_OK;  // not supported
+  cudaError_t e = prec == CTQ_TF32     ? tc_attr<CTQ_TF32>(lc->smem)
+                  : prec == CTQ_BF16X3 ? tc_attr<CTQ_BF16X3>(lc->smem)
+                                       : tc_attr<CTQ_TF32X3>(lc->smem);
   if (e != cudaSuccess) return CTQ_ERR_CUDA;
-  int per_sm = 0;
-  e = (split == 3) ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_tc<3>, TC_THREADS, lc->smem)
-                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_tc<1>, TC_THREADS, lc->smem);
-  if (e != cudaSuccess) return CTQ_ERR_CUDA;
-  lc->per_sm = std::min(per_sm, split == 3 ? 1 : 2);  // TMEM: 512 or 256 columns per CTA
+  // resident CTAs per SM: shared memory (with the driver's 1 KB per CTA),
+  // registers, and tensor memory (512 or 256 of the SM's 512 columns)
+  cudaFuncAttributes fa;
+  e = prec == CTQ_TF32     ? cudaFuncGetAttributes(&fa, k_trace_tc<CTQ_TF32>)
+      : prec == CTQ_BF16X3 ? cudaFuncGetAttributes(&fa, k_trace_tc<CTQ_BF16X3>)
+                           : cudaFuncGetAttributes(&fa, k_trace_tc<CTQ_TF32X3>);
+  int dev = 0, sm_smem = 0;
+  if (e != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
+    return CTQ_ERR_CUDA;
+  const int by_smem = int(size_t(sm_smem) / (lc->smem + fa.sharedSizeBytes + 1024));
+  const int regs = (fa.numRegs + 7) / 8 * 8;
+  const int by_regs = 65536 / std::max(1, regs * TC_THREADS);
+  const int by_tmem = prec == CTQ_TF32X3 ? 1 : 2;
+  lc->regs = fa.numRegs;
+  lc->per_sm = std::max(0, std::min(by_smem, std::min(by_regs, by_tmem)));
   return CTQ_OK;
 }
 
@@ -615,10 +725,12 @@ int launch_eval_tc(const DevModel& M, const LaunchCfg& lc, const TcParams& P, co
   long long max_items = (long long)B.n_chains * M.n_sec;
   long long grid = (long long)lc.num_sms * lc.per_sm;
   if (grid > max_items) grid = max_items;
-  if (P.split == 3)
-    k_trace_tc<3><<<int(grid), TC_THREADS, lc.smem, st>>>(M, B, cfg, W, P);
+  if (P.prec == CTQ_TF32)
+    k_trace_tc<CTQ_TF32><<<int(grid), TC_THREADS, lc.smem, st>>>(M, B, cfg, W, P);
+  else if (P.prec == CTQ_BF16X3)
+    k_trace_tc<CTQ_BF16X3><<<int(grid), TC_THREADS, lc.smem, st>>>(M, B, cfg, W, P);
   else
-    k_trace_tc<1><<<int(grid), TC_THREADS, lc.smem, st>>>(M, B, cfg, W, P);
+    k_trace_tc<CTQ_TF32X3><<<int(grid), TC_THREADS, lc.smem, st>>>(M, B, cfg, W, P);
   if (cudaGetLastError() != cudaSuccess) return CTQ_ERR_CUDA;
   mark(2);
   {
@@ -633,7 +745,8 @@ int launch_eval_tc(const DevModel& M, const LaunchCfg& lc, const TcParams& P, co
 
 extern "C" int ctq_tc_gemm_check(int device, const float* A, const float* Bm, float* D, int N, int K, int split) {
   using namespace ctq;
-  if (!A || !Bm || !D || N < 16 || N > 112 || N % 16 || K < 16 || K > 112 || K % 16 || (split != 1 && split != 3))
+  if (!A || !Bm || !D || N < 16 || N > 112 || N % 16 || K < 16 || K > 112 || K % 16 ||
+      (split != CTQ_TF32 && split != CTQ_TF32X3 && split != CTQ_BF16X3))
     return CTQ_ERR_ARG;
   int prev = 0;
   cudaGetDevice(&prev);
@@ -650,12 +763,15 @@ extern "C" int ctq_tc_gemm_check(int device, const float* A, const float* Bm, fl
     cudaMemcpy(dA, A, size_t(128) * K * 4, cudaMemcpyHostToDevice);
     cudaMemcpy(dB, Bm, size_t(N) * K * 4, cudaMemcpyHostToDevice);
     cudaMemset(dS, 0xff, 4);
-    if (split == 3) {
-      cudaFuncSetAttribute(k_tc_gemm_check<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-      k_tc_gemm_check<3><<<1, TC_THREADS, smem>>>(dA, dB, dD, N, K, 2000000000ull, dS);
+    if (split == CTQ_TF32X3) {
+      cudaFuncSetAttribute(k_tc_gemm_check<CTQ_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      k_tc_gemm_check<CTQ_TF32X3><<<1, TC_THREADS, smem>>>(dA, dB, dD, N, K, 2000000000ull, dS);
+    } else if (split == CTQ_BF16X3) {
+      cudaFuncSetAttribute(k_tc_gemm_check<CTQ_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      k_tc_gemm_check<CTQ_BF16X3><<<1, TC_THREADS, smem>>>(dA, dB, dD, N, K, 2000000000ull, dS);
     } else {
-      cudaFuncSetAttribute(k_tc_gemm_check<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-      k_tc_gemm_check<1><<<1, TC_THREADS, smem>>>(dA, dB, dD, N, K, 2000000000ull, dS);
+      cudaFuncSetAttribute(k_tc_gemm_check<CTQ_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      k_tc_gemm_check<CTQ_TF32><<<1, TC_THREADS, smem>>>(dA, dB, dD, N, K, 2000000000ull, dS);
     }
     if (cudaDeviceSynchronize() != cudaSuccess) st = CTQ_ERR_CUDA;
     if (st == CTQ_OK) {
