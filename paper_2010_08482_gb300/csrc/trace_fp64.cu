@@ -77,69 +77,6 @@ __device__ __forceinline__ int block_max_int(int v, int* redi) {
   return v;
 }
 
-// 2^e as a float64 built from its exponent field, -1022 <= e <= 1023.
-__device__ __forceinline__ double pow2i(int e) { return __hiloint2double((e + 1023) << 20, 0); }
-
-// h + l += x with the rounding error of h + x kept in l (Knuth's TwoSum).
-__device__ __forceinline__ void two_sum_acc(double& h, double& l, double x) {
-  const double s = h + x;
-  const double bp = s - h;
-  l += (h - (s - bp)) + (x - bp);
-  h = s;
-}
-
-// Log scale of one sector string, computed by one warp with lanes over
-// chunks of operators (Sec. 3.3.1 propagators: every time step dtau_j in
-// sector q_j contributes -dtau_j (E_min(q_j) - E_ref) to the log of the
-// product).  The chunk sums are compensated and combined by a compensated
-// inclusive scan over lanes, so the total keeps the accuracy of a
-// compensated sequential sum.  With tracking, the chunks are the segments of
-// S operators and the scan also yields the log scale segL and the applied
-// log-norm prefix segP at every segment end.
-__device__ __forceinline__ void chain_log_scale(const DevModel& M, const BatchView& B, const EvalCfg& cfg, int a0, int n, int q0,
-                                double t_first, double t_last, bool track, const short* path, const short* opsm,
-                                double* segL, double* segP, double* out_L) {
-  const int lane = threadIdx.x & 31;
-  const int ns = M.n_sec;
-  const double emr0 = M.E_min[q0] - M.E_ref;
-  const int CH = track ? cfg.S : max(1, (n + 30) / 32);  // chunk length over j = 1 .. n-1
-  const int nch = (n - 1 + CH - 1) / CH;
-  double ch = -t_first * emr0, cl = 0.0, cp = 0.0;  // running carry (compensated) and log-norm prefix
-  two_sum_acc(ch, cl, -t_last * emr0);
-  for (int base = 0; base < nch; base += 32) {
-    const int t = base + lane;
-    double h = 0.0, l = 0.0, ps = 0.0;
-    if (t < nch) {
-      const int j2 = min((t + 1) * CH, n - 1);
-      for (int j = t * CH + 1; j <= j2; ++j) {
-        const double term = -(B.tau[a0 + j] - B.tau[a0 + j - 1]) * (M.E_min[path[j]] - M.E_ref);
-        two_sum_acc(h, l, term);
-        if (track) ps += term + M.log_norm[opsm[j - 1] * ns + path[j - 1]];
-      }
-    }
-    for (int o = 1; o < 32; o <<= 1) {  // inclusive scan over the lanes
-      const double oh = __shfl_up_sync(FULL, h, o), ol = __shfl_up_sync(FULL, l, o);
-      const double op = __shfl_up_sync(FULL, ps, o);
-      if (lane >= o) {
-        two_sum_acc(h, l, oh);
-        l += ol;
-        ps += op;
-      }
-    }
-    double H = ch, Lo = cl + l;
-    two_sum_acc(H, Lo, h);
-    const double P = cp + ps;
-    if (track && t < nch && (t + 1) * CH < n) {
-      segL[t + 1] = H + Lo;
-      segP[t + 1] = P;
-    }
-    ch = __shfl_sync(FULL, H, 31);
-    cl = __shfl_sync(FULL, Lo, 31);
-    cp = __shfl_sync(FULL, P, 31);
-  }
-  if (lane == 0) *out_L = ch + cl;
-}
-
 // Shared-memory layout of k_trace (dynamic part), see trace_smem().
 struct TraceSmem {
   size_t y_bytes;  // one Y buffer

@@ -41,6 +41,12 @@ using namespace ptx;
 constexpr int TC_THREADS = 128;
 constexpr int TC_M = 128;
 constexpr int TC_MAX_DIM = 112;  // largest sector of the small-block kernel (A, D <= 128 columns)
+constexpr int TC_META_BYTES = 8192;  // staged string of one item: see k_trace_tc
+
+// Bytes of the staged string for max_ops operators and n_seg_max segments.
+__host__ __device__ constexpr size_t tc_meta_bytes(int max_ops, int n_seg_max) {
+  return size_t(2) * (n_seg_max + 1) * 8 + size_t(max_ops > 1 ? max_ops : 1) * (4 + 2 + 2) + 2;
+}
 
 // Block-wide (max, sum) of floats; all threads get the result.  red: 8 floats.
 __device__ __forceinline__ void block_max_sum_f(float& mx, float& sm, float* red) {
@@ -150,6 +156,7 @@ struct TcShared {
   int fail;
   float red[8];
   double redd[64];
+  double L;  // log scale of the current string (warp 0 writes)
 };
 
 }  // namespace
@@ -168,6 +175,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   stage[1] = stage[0] + P.stage_bytes;
   float* p_s = reinterpret_cast<float*>(stage[1] + P.stage_bytes);  // [128] column scales of the current step
   float* p0_s = p_s + TC_M;                // [128] wrap-around propagator of q0
+  // the item's string, staged once (TC_META_BYTES): log scale and applied
+  // log-norm sums at segment ends, operator codes, sectors, time steps
+  const int MO = max(cfg.max_ops, 1), NS = cfg.n_seg_max + 1;
+  double* segL = reinterpret_cast<double*>(p0_s + TC_M);  // [NS]
+  double* segP = segL + NS;                                // [NS]
+  float* dtf = reinterpret_cast<float*>(segP + NS);        // [MO] tau_{i+1} - tau_i
+  short* opsm = reinterpret_cast<short*>(dtf + MO);        // [MO]
+  short* path = opsm + MO;                                 // [MO + 1]
   __shared__ TcShared S;
 
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -257,21 +272,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       continue;
     }
 
+    // ---- the string once: operator codes and time steps (all threads),
+    // sectors (thread 0, integer walk), log scale and segment sums (warp 0,
+    // compensated, lanes over chunks of operators)
+    const double t_first = B.tau[a0], t_last = B.beta - B.tau[a0 + n - 1];
+    for (int i = tid; i < n; i += TC_THREADS) {
+      opsm[i] = short(B.op[a0 + i]);
+      if (i + 1 < n) dtf[i] = float(B.tau[a0 + i + 1] - B.tau[a0 + i]);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int q = q0;
+      path[0] = short(q0);
+      for (int i = 0; i < n; ++i) {
+        q = M.s[opsm[i] * ns + q];
+        path[i + 1] = short(q);
+      }
+    }
+    __syncthreads();
+    if (tid < 32) chain_log_scale(M, B, cfg, a0, n, q0, t_first, t_last, track, path, opsm, segL, segP, &S.L);
+    const double ub_const = track ? 0.5 * log(double(it.r)) + it.t_all : 0.0;  // sqrt(r), all log-norms
+
     // ---- operator 1 (elementwise): Z_1[j][m] = p0[j] F_1[m][j] p1[m]
     int qa = q0;
-    int alpha = B.op[a0];
-    int qb = M.s[alpha * ns + qa];
-    const double t_first = B.tau[a0], t_last = B.beta - B.tau[a0 + n - 1];
-    KSum L;  // thread 0 only (log scale relative to E_ref)
+    int alpha = opsm[0];
+    int qb = path[1];
     long long Eacc = 0;
-    double prefix = 0.0;
-    if (tid == 0) {
-      L.add(-t_first * (M.E_min[q0] - M.E_ref));
-      L.add(-t_last * (M.E_min[q0] - M.E_ref));
-      prefix = M.log_norm[alpha * ns + qa];
-    }
     {
-      const double dt = B.tau[a0 + 1] - B.tau[a0];
+      const float dt1 = dtf[0];
       const float* Eb = M.E_relf + M.E_off[qb];
       const float* E0f = M.E_relf + M.E_off[q0];
       const int db = M.dims[qb];
@@ -279,18 +307,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // FP32 exponentials: an absolute argument error of ~1e-7 x changes
         // e^{-x} by at most max(x e^{-x}) 1e-7 < 4e-8 relative to the largest
         // entry, below the resolution of the products.
-        p_s[j] = (j < db) ? __expf(-float(dt) * Eb[j]) : 0.0f;
+        p_s[j] = (j < db) ? __expf(-dt1 * Eb[j]) : 0.0f;
         p0_s[j] = (j < d0) ? __expf(-float(t_first) * E0f[j]) * __expf(-float(t_last) * E0f[j]) : 0.0f;
-      }
-      if (tid == 0) {
-        L.add(-dt * (M.E_min[qb] - M.E_ref));
-        prefix -= dt * (M.E_min[qb] - M.E_ref);
       }
     }
     // prefetch the block of operator 2 (the first tensor-core product)
     if (tid == 0 && n > 2) {
-      const int alpha2 = B.op[a0 + 1];
-      const int qn = M.s[alpha2 * ns + qb];
+      const int alpha2 = opsm[1];
+      const int qn = path[2];
       const int np = round_up(M.dims[qn], 16), kp = round_up(M.dims[qb], tc_kstep(PREC));
       const uint32_t bytes = uint32_t(SPLIT ? 2 : 1) * np * kp * EB;
       mbar_arrive_expect_tx(&S.bar_load[0], bytes);
@@ -330,8 +354,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int e = ilogbf(mx);
       if (track && applied % cfg.S == 0 && applied < n) {
         if (tid == 0) {
-          const double ub = 0.5 * log(double(it.r)) + 0.5 * log(double(fr)) + double(Eacc) * LN2 + L.val() +
-                            (it.t_all - prefix);
+          const double ub = ub_const + 0.5 * log(double(fr)) + double(Eacc) * LN2 + segL[applied / cfg.S] -
+                            segP[applied / cfg.S];
           segp[applied / cfg.S] = ub;
           if (cfg.lazy) {
             W.live[slot] = fmin(W.live[slot], ub);
@@ -360,11 +384,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if (S.abort_flag) { aborted = true; break; }
         }
       }
-      alpha = B.op[a0 + i];
+      alpha = opsm[i];
       const int idx_a = alpha * ns + qa;
-      qb = M.s[idx_a];
+      qb = path[i + 1];
       const float scale = ldexpf(1.0f, -e);
-      if (tid == 0) prefix += M.log_norm[idx_a];
       Eacc += e;
 
       if (i == n - 1) {  // final operator: diagonal of F_n Y = sum_{j,k} F_n[j][k] Z[j][k]
@@ -388,8 +411,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           W.res_val[2 * slot] = vr;
           W.res_val[2 * slot + 1] = vi;
           const bool zero_v = (vr == 0.0);
-          W.res_log[slot] = zero_v ? -INFINITY : L.val() + double(Eacc) * LN2;
-          if (track) segp[it.n_seg] = zero_v ? -INFINITY : log(fabs(vr)) + L.val() + double(Eacc) * LN2;
+          W.res_log[slot] = zero_v ? -INFINITY : S.L + double(Eacc) * LN2;
+          if (track) segp[it.n_seg] = zero_v ? -INFINITY : log(fabs(vr)) + S.L + double(Eacc) * LN2;
         }
         applied = n;
         break;
@@ -401,8 +424,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (tid == 0) {
         // prefetch the next block into the other stage (its last reader has completed)
         if (i + 1 < n - 1) {
-          const int alpha_n = B.op[a0 + i + 1];
-          const int qn = M.s[alpha_n * ns + qb];
+          const int alpha_n = opsm[i + 1];
+          const int qn = path[i + 2];
           const int np2 = round_up(M.dims[qn], 16), kp2 = round_up(db, tc_kstep(PREC));
           const uint32_t bytes = uint32_t(SPLIT ? 2 : 1) * np2 * kp2 * EB;
           const int st2 = cur_stage ^ 1;
@@ -426,14 +449,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       // column scales of this step (overlaps the MMA)
       {
-        const double dt = B.tau[a0 + i + 1] - B.tau[a0 + i];
         const float* Eb = M.E_relf + M.E_off[qb];
-        const float dtf = float(dt);
-        for (int j = tid; j < TC_M; j += TC_THREADS) p_s[j] = (j < db) ? __expf(-dtf * Eb[j]) * scale : 0.0f;
-        if (tid == 0) {
-          L.add(-dt * (M.E_min[qb] - M.E_ref));
-          prefix -= dt * (M.E_min[qb] - M.E_ref);
-        }
+        const float dti = dtf[i];
+        for (int j = tid; j < TC_M; j += TC_THREADS) p_s[j] = (j < db) ? __expf(-dti * Eb[j]) * scale : 0.0f;
       }
       __syncthreads();
       bool ok = (S.fail == 0) && mbar_wait(&S.bar_mma, ph_mma, P.timeout_ns);
@@ -446,18 +464,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       // epilogue: Z_next[row][j] = D[row][j] * p_s[j]
       mx = 0.f;
       fr = 0.f;
-      for (int c0 = 0; c0 < np; c0 += 16) {
-        uint32_t v[16];
-        float x[16];
-        tmem_ld16(tD + lane_off + c0, v);
+      for (int g0 = 0; g0 < np; g0 += 64) {  // four tensor-memory loads in flight, one wait
+        uint32_t v[4][16];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (g0 + 16 * u < np) tmem_ld16(tD + lane_off + g0 + 16 * u, v[u]);
         tmem_wait_ld();
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
-          x[t] = __uint_as_float(v[t]) * p_s[c0 + t];
-          mx = fmaxf(mx, fabsf(x[t]));
-          fr += x[t] * x[t];
+        for (int u = 0; u < 4; ++u) {
+          if (g0 + 16 * u >= np) break;
+          const int c0 = g0 + 16 * u;
+          float x[16];
+#pragma unroll
+          for (int t = 0; t < 16; ++t) {
+            x[t] = __uint_as_float(v[u][t]) * p_s[c0 + t];
+            mx = fmaxf(mx, fabsf(x[t]));
+            fr += x[t] * x[t];
+          }
+          store_a16<PREC>(tAh, tAl, c0, x);
         }
-        store_a16<PREC>(tAh, tAl, c0, x);
       }
       tmem_wait_st();
       tc_fence_before();
@@ -677,7 +702,7 @@ static cudaError_t tc_attr(size_t smem) {
 
 int prepare_eval_tc(const DevModel& M, int prec, int stage_bytes, int num_sms, LaunchCfg* lc) {
   lc->threads = TC_THREADS;
-  lc->smem = size_t(2) * stage_bytes + 2 * TC_M * 4;
+  lc->smem = size_t(2) * stage_bytes + 2 * TC_M * 4 + TC_META_BYTES;
   // At most 512 / tmem_cols CTAs may share an SM (each holds its TMEM for the
   // whole kernel): request enough shared memory to enforce that.
   lc->smem = std::max(lc->smem, size_t(prec == CTQ_TF32X3 ? 116 * 1024 : 76 * 1024));
@@ -712,6 +737,7 @@ int launch_eval_tc(const DevModel& M, const LaunchCfg& lc, const TcParams& P, co
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (B.n_chains == 0) return CTQ_OK;
   if (lc.per_sm < 1) return CTQ_ERR_UNSUPPORTED;
+  if (tc_meta_bytes(cfg.max_ops, cfg.n_seg_max) > size_t(TC_META_BYTES)) return CTQ_ERR_UNSUPPORTED;
   auto mark = [&](int i) {
     if (events) cudaEventRecord(static_cast<cudaEvent_t>(events[i]), st);
   };
