@@ -343,6 +343,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "tf32x3", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--chains", type=int, default=0, help="evaluate only the first N chains of the workload")
+    ap.add_argument("--no-autotune", action="store_true", help="library-default launch configuration")
+    ap.add_argument("--autotune-cache", default=None, help="JSON cache of tuned launch configurations")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -367,7 +369,13 @@ def main():
     imp = ctq.build_impurity(params, device=local)
     db = ctq.DeviceBatch(batch, device=dev)
     prec = PRECISIONS[args.precision]
-    ev = ctq.TraceEvaluator(imp, batch.n_chains, db.max_ops, precision=prec, device=dev)
+    tuning = {}
+    if not args.no_autotune:  # launch configuration picked by the package's autotuner, before any timing
+        from paper_2010_08482_gb300 import autotune
+        big = autotune.engine(imp, prec) == "big"
+        tdb = ctq.DeviceBatch(batch.subset(range(min(batch.n_chains, 4))), device=dev) if big else db
+        tuning = autotune.tune(imp, tdb, prec, cache_path=args.autotune_cache, reps=1 if big else 3)
+    ev = ctq.TraceEvaluator(imp, batch.n_chains, db.max_ops, precision=prec, device=dev, tune=tuning)
     flops, n_items = algorithmic_flops(imp, batch)
     launches = ctq.launches_per_eval(imp)
     stream = torch.cuda.current_stream()
@@ -458,6 +466,7 @@ def main():
                    "n_chains": batch.n_chains,
                    "surviving_strings": n_items, "precision": args.precision,
                    "l2": "flushed (256 MiB write) between steps",
+                   "launch_tuning": tuning or "library default",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "tflops": flops / (ms * 1e-3) / 1e12,
         "algorithmic_flops_per_step": flops,

@@ -193,6 +193,17 @@ typedef struct {
  *   recorded on `stream` before the first kernel and after each kernel, so a
  *   caller can time every kernel of the evaluation on its launching stream.
  * debug_flags: 0, or CTQ_DEBUG_STALL_WAIT (test of the timeout path).
+ * Launch tuning (0 everywhere = library defaults; the package's autotuner
+ * picks them per impurity, precision and batch shape):
+ *   threads_per_cta: FP64 kernel, 32 to 256 in steps of 32;
+ *   ctas_per_sm: upper bound on the resident CTAs per SM of the FP64 and
+ *     small-block trace kernels;
+ *   stages: large-block kernel pipeline stages, >= 2 and as many as fit in
+ *     shared memory (CTQ_ERR_UNSUPPORTED otherwise);
+ *   tile_order: large-block kernel tile order, 0 column-major (a B tile is
+ *     shared by consecutive CTAs), 1 row-major, 2 groups of 8 column tiles
+ *     row by row.
+ * Out-of-range values: CTQ_ERR_ARG.
  * When a bounded wait expires, every chain of the call gets
  * CTQ_CHAIN_ERR_TIMEOUT (log_abs NaN); the context stays usable.
  */
@@ -204,6 +215,10 @@ typedef struct {
   int64_t timeout_ns;
   void* const* timing_events;
   int32_t debug_flags;
+  int32_t threads_per_cta;
+  int32_t ctas_per_sm;
+  int32_t stages;
+  int32_t tile_order;
 } ctq_eval_opts;
 
 /*

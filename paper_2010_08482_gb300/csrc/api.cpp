@@ -433,6 +433,9 @@ int ctq_launches_per_eval(const ctq_impurity* imp, const ctq_eval_opts* opts) {
 int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_eval_opts* opts,
                     const ctq_result* result, void* workspace, size_t workspace_bytes, void* stream) {
   if (!imp || !batch || !opts || !result) return fail(CTQ_ERR_ARG, "null argument");
+  if (opts->threads_per_cta < 0 || opts->threads_per_cta > 256 || opts->threads_per_cta % 32 != 0 ||
+      opts->ctas_per_sm < 0 || opts->stages < 0 || opts->stages == 1 || opts->tile_order < 0 || opts->tile_order > 2)
+    return fail(CTQ_ERR_ARG, "launch tuning out of range");
   if (imp->device < 0) return fail(CTQ_ERR_ARG, "impurity has no device copy");
   if (batch->n_chains < 0) return fail(CTQ_ERR_ARG, "n_chains < 0");
   if (batch->n_chains == 0) return CTQ_OK;
@@ -478,6 +481,10 @@ int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_e
                                                : 1e-2;
   cfg.bounds = result->bounds;
   cfg.debug = opts->debug_flags;
+  cfg.threads = opts->threads_per_cta;
+  cfg.ctas_per_sm = opts->ctas_per_sm;
+  cfg.stages = opts->stages;
+  cfg.tile_order = opts->tile_order;
   int st;
   if (opts->precision == CTQ_FP64) {
     st = ctq::launch_eval_fp64(imp->dev, imp->launch, B, cfg, W, result, stream, opts->timing_events);

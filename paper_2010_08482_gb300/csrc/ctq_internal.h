@@ -94,6 +94,10 @@ struct EvalCfg {
   double margin;    // safety margin (log units) applied to bounds before rejecting
   double* bounds;   // result bounds [C x (n_seg_max + 1)] or nullptr
   int debug;        // ctq_eval_opts.debug_flags
+  int threads;      // launch tuning (ctq_eval_opts), 0 = default
+  int ctas_per_sm;
+  int stages;
+  int tile_order;
 };
 
 // A work item: one surviving (chain, q0) string.
@@ -154,6 +158,7 @@ struct BigParams {
   const int64_t* bt_off = nullptr;  // [n_alpha * n_sec] element offsets, -1 absent
   int prec = CTQ_TF32X3;          // CTQ_TF32, CTQ_TF32X3 or CTQ_BF16X3
   int nst = 3;                    // pipeline stages
+  int order = 0;                  // tile order (ctq_eval_opts.tile_order)
   uint64_t timeout_ns = 0;
   float* zbuf = nullptr;          // scratch: 2 x (hi, lo) Z buffers
   size_t zfloats = 0;             // floats of one Z plane

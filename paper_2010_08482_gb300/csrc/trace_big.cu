@@ -74,6 +74,26 @@ __host__ __device__ __forceinline__ size_t tiled_off(int r, int k, int rows_per_
          size_t((kk / EPC) * (rows_per_tile >> 3) + (rr >> 3)) * (8 * EPC) + (rr & 7) * EPC + (kk % EPC);
 }
 
+// Tile (row mt, column nt) of linear tile index t in a product of n_mt x n_nt
+// tiles: order 0 column-major (consecutive CTAs share a B tile), 1 row-major
+// (they share an A tile), 2 groups of 8 column tiles, row-major inside a group.
+__device__ __forceinline__ void tile_coords(int t, int n_mt, int n_nt, int order, int& mt, int& nt) {
+  if (order == 1) {
+    mt = t / n_nt;
+    nt = t - mt * n_nt;
+  } else if (order == 2) {
+    constexpr int G = 8;
+    const int g = t / (G * n_mt);
+    const int width = min(G, n_nt - g * G);
+    const int local = t - g * G * n_mt;
+    mt = local / width;
+    nt = g * G + (local - mt * width);
+  } else {
+    nt = t / n_mt;
+    mt = t - nt * n_mt;
+  }
+}
+
 // hi / lo split of x in the operand format of PREC.
 template <int PREC>
 __device__ __forceinline__ void split_store(float x, typename Elt<PREC>::T& hi, typename Elt<PREC>::T& lo) {
@@ -445,7 +465,8 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
       // Both then join the epilogue.
       volatile int* fail_v = &S.fail;
       auto produce = [&](uint32_t q, int tt, int kc) -> bool {
-        const int mt_ = tt % n_mt, nt_ = tt / n_mt;
+        int mt_, nt_;
+        tile_coords(tt, n_mt, n_nt, P.order, mt_, nt_);
         const int st = int(q % uint32_t(NST));
         if (q >= uint32_t(NST) && !mbar_wait(&S.empty[st], ((q / NST) - 1u) & 1u, P.timeout_ns)) return false;
         unsigned char* sb = stage0 + size_t(st) * stage_bytes;
@@ -462,7 +483,8 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
       };
       int pre = 0;  // (producer) chunks of the current tile already issued
       for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        const int mt = t % n_mt, nt = t / n_mt;  // column-major: B tiles reused across rows
+        int mt, nt;
+        tile_coords(t, n_mt, n_nt, P.order, mt, nt);
         const int ncols = min(BN, 2 * dpn - nt * BN);
         const uint32_t idesc = (PREC == CTQ_BF16X3) ? idesc_bf16(BM, ncols) : idesc_tf32(BM, ncols);
         if (tid == 32) {
@@ -763,8 +785,8 @@ size_t big_scratch_bytes(const HostModel& h, int max_ops, int grid) {
 
 static int big_stages(int prec) { return prec == CTQ_TF32 ? 6 : 3; }
 
-static size_t big_smem(int prec) {
-  return size_t(big_stages(prec)) * (prec == CTQ_TF32 ? 1 : 2) * (A_BYTES + B_BYTES) + 2 * PVEC * 4;
+static size_t big_smem(int prec, int nst) {
+  return size_t(nst) * (prec == CTQ_TF32 ? 1 : 2) * (A_BYTES + B_BYTES) + 2 * PVEC * 4;
 }
 
 template <int PREC>
@@ -772,13 +794,26 @@ static cudaError_t big_attr(size_t smem) {
   return cudaFuncSetAttribute(k_trace_big<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
 }
 
+// The kernel may be launched with up to lc->smem_optin bytes of dynamic shared
+// memory (more pipeline stages through the caller's launch tuning); lc->smem
+// is the default stage count's need.
 int prepare_eval_big(int prec, int num_sms, LaunchCfg* lc) {
   lc->threads = BG_THREADS;
   lc->num_sms = num_sms;
-  lc->smem = big_smem(prec);
-  const cudaError_t e = prec == CTQ_TF32     ? big_attr<CTQ_TF32>(lc->smem)
-                        : prec == CTQ_BF16X3 ? big_attr<CTQ_BF16X3>(lc->smem)
-                                             : big_attr<CTQ_TF32X3>(lc->smem);
+  lc->smem = big_smem(prec, big_stages(prec));
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return CTQ_ERR_CUDA;
+  cudaFuncAttributes fa;
+  cudaError_t e = prec == CTQ_TF32     ? cudaFuncGetAttributes(&fa, k_trace_big<CTQ_TF32>)
+                  : prec == CTQ_BF16X3 ? cudaFuncGetAttributes(&fa, k_trace_big<CTQ_BF16X3>)
+                                       : cudaFuncGetAttributes(&fa, k_trace_big<CTQ_TF32X3>);
+  if (e != cudaSuccess) return CTQ_ERR_CUDA;
+  lc->smem_optin = optin - int(fa.sharedSizeBytes);
+  e = prec == CTQ_TF32     ? big_attr<CTQ_TF32>(lc->smem_optin)
+      : prec == CTQ_BF16X3 ? big_attr<CTQ_BF16X3>(lc->smem_optin)
+                           : big_attr<CTQ_TF32X3>(lc->smem_optin);
   if (e != cudaSuccess) return CTQ_ERR_CUDA;
   lc->per_sm = 1;
   return CTQ_OK;
@@ -809,7 +844,10 @@ int launch_eval_big(const DevModel& M, const LaunchCfg& lc, BigParams P, const B
   P.part = reinterpret_cast<double*>(s);
   s += size_t(2 * grid) * 8;
   P.abort_flag = reinterpret_cast<int*>(s);
-  P.nst = big_stages(P.prec);
+  P.nst = cfg.stages > 0 ? cfg.stages : big_stages(P.prec);
+  P.order = cfg.tile_order;
+  const size_t smem = big_smem(P.prec, P.nst);
+  if (P.nst < 2 || P.nst > MAX_NST || smem > size_t(lc.smem_optin)) return CTQ_ERR_UNSUPPORTED;
   if (cudaMemsetAsync(W.counters, 0, 256, st) != cudaSuccess) return CTQ_ERR_CUDA;
   if (cudaMemsetAsync(P.bar, 0, 256, st) != cudaSuccess) return CTQ_ERR_CUDA;
   if (cudaMemsetAsync(P.zbuf, 0, 4 * P.zfloats * 4, st) != cudaSuccess) return CTQ_ERR_CUDA;
@@ -824,7 +862,7 @@ int launch_eval_big(const DevModel& M, const LaunchCfg& lc, BigParams P, const B
   void* fn = P.prec == CTQ_TF32     ? (void*)k_trace_big<CTQ_TF32>
              : P.prec == CTQ_BF16X3 ? (void*)k_trace_big<CTQ_BF16X3>
                                     : (void*)k_trace_big<CTQ_TF32X3>;
-  const cudaError_t e = cudaLaunchCooperativeKernel(fn, grid, BG_THREADS, args, lc.smem, st);
+  const cudaError_t e = cudaLaunchCooperativeKernel(fn, grid, BG_THREADS, args, smem, st);
   if (e != cudaSuccess) return CTQ_ERR_CUDA;
   mark(2);
   {

@@ -439,10 +439,13 @@ int launch_eval_fp64(const DevModel& M, const LaunchCfg& lc, const BatchView& B,
   const bool pre = use_pre(M.max_dim, cfg.max_ops);
   const size_t smem = trace_smem(M.max_dim, M.is_complex != 0, cfg.max_ops, cfg.n_seg_max, pre);
   if (smem + 1024 > size_t(lc.smem_optin)) return CTQ_ERR_UNSUPPORTED;
-  // resident CTAs per SM from shared memory, registers and the 32-CTA limit
+  // resident CTAs per SM from shared memory, registers and the 32-CTA
+  // limit, optionally capped by the caller's launch tuning
+  const int threads = cfg.threads > 0 ? cfg.threads : lc.threads;
   int per_sm = int((228 * 1024) / (smem + 1024));
-  per_sm = std::min(per_sm, 65536 / std::max(1, lc.regs * lc.threads));
-  per_sm = std::min(per_sm, std::min(32, 2048 / lc.threads));
+  per_sm = std::min(per_sm, 65536 / std::max(1, lc.regs * threads));
+  per_sm = std::min(per_sm, std::min(32, 2048 / threads));
+  if (cfg.ctas_per_sm > 0) per_sm = std::min(per_sm, cfg.ctas_per_sm);
   if (per_sm < 1) return CTQ_ERR_UNSUPPORTED;
   auto mark = [&](int i) {
     if (events) cudaEventRecord(static_cast<cudaEvent_t>(events[i]), st);
@@ -458,11 +461,11 @@ int launch_eval_fp64(const DevModel& M, const LaunchCfg& lc, const BatchView& B,
   long long grid = (long long)lc.num_sms * per_sm;
   if (grid > max_items) grid = max_items;
   if (M.is_complex) {
-    if (pre) k_trace<true, true><<<int(grid), lc.threads, smem, st>>>(M, B, cfg, W);
-    else k_trace<true, false><<<int(grid), lc.threads, smem, st>>>(M, B, cfg, W);
+    if (pre) k_trace<true, true><<<int(grid), threads, smem, st>>>(M, B, cfg, W);
+    else k_trace<true, false><<<int(grid), threads, smem, st>>>(M, B, cfg, W);
   } else {
-    if (pre) k_trace<false, true><<<int(grid), lc.threads, smem, st>>>(M, B, cfg, W);
-    else k_trace<false, false><<<int(grid), lc.threads, smem, st>>>(M, B, cfg, W);
+    if (pre) k_trace<false, true><<<int(grid), threads, smem, st>>>(M, B, cfg, W);
+    else k_trace<false, false><<<int(grid), threads, smem, st>>>(M, B, cfg, W);
   }
   if (cudaGetLastError() != cudaSuccess) return CTQ_ERR_CUDA;
   mark(2);

@@ -749,7 +749,8 @@ int launch_eval_tc(const DevModel& M, const LaunchCfg& lc, const TcParams& P, co
   }
   mark(1);
   long long max_items = (long long)B.n_chains * M.n_sec;
-  long long grid = (long long)lc.num_sms * lc.per_sm;
+  const int per_sm = cfg.ctas_per_sm > 0 ? std::min(lc.per_sm, cfg.ctas_per_sm) : lc.per_sm;
+  long long grid = (long long)lc.num_sms * per_sm;
   if (grid > max_items) grid = max_items;
   if (P.prec == CTQ_TF32)
     k_trace_tc<CTQ_TF32><<<int(grid), TC_THREADS, lc.smem, st>>>(M, B, cfg, W, P);

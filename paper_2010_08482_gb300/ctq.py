@@ -59,7 +59,8 @@ class BatchC(ctypes.Structure):
 
 class EvalOptsC(ctypes.Structure):
     _fields_ = [("precision", c_int), ("lazy", c_int), ("segment", c_int), ("max_ops", c_int),
-                ("timeout_ns", c_int64), ("timing_events", c_void_p), ("debug_flags", c_int32)]
+                ("timeout_ns", c_int64), ("timing_events", c_void_p), ("debug_flags", c_int32),
+                ("threads_per_cta", c_int32), ("ctas_per_sm", c_int32), ("stages", c_int32), ("tile_order", c_int32)]
 
 
 class ResultC(ctypes.Structure):
@@ -250,11 +251,20 @@ def load_impurity(n_flav: int, dims, N, energies, s_table, blocks, mu: float = 0
     return Impurity(h)
 
 
-def _opts(precision=FP64, lazy=False, segment=8, max_ops=0, timeout_ns=0, events=None, debug_flags=0) -> EvalOptsC:
+# Launch-tuning keys of ctq_eval_opts (0 = library default); see ctq.h.
+TUNE_KEYS = ("threads_per_cta", "ctas_per_sm", "stages", "tile_order")
+
+
+def _opts(precision=FP64, lazy=False, segment=8, max_ops=0, timeout_ns=0, events=None, debug_flags=0,
+          tune=None) -> EvalOptsC:
     o = EvalOptsC()
     o.precision, o.lazy, o.segment, o.max_ops, o.timeout_ns = precision, int(lazy), segment, max_ops, timeout_ns
     o.timing_events = events
     o.debug_flags = debug_flags
+    for k, v in (tune or {}).items():
+        if k not in TUNE_KEYS:
+            raise ValueError(f"unknown launch-tuning key {k!r}")
+        setattr(o, k, int(v))
     return o
 
 
@@ -270,15 +280,17 @@ def launches_per_eval(imp: Impurity, precision=FP64) -> int:
 
 def eval_traces(imp: Impurity, n_chains: int, beta: float, offsets, tau, op, log_threshold,
                 log_abs, phase, status, bounds, workspace, workspace_bytes: int, stream,
-                precision=FP64, lazy=False, segment=8, max_ops=0, timeout_ns=0, events=None, debug_flags=0):
+                precision=FP64, lazy=False, segment=8, max_ops=0, timeout_ns=0, events=None, debug_flags=0,
+                tune=None):
     """ctq_eval_traces with raw device pointers (ints) and a cudaStream_t (int);
-    events: optional address of an array of cudaEvent_t handles (see ctq.h)."""
+    events: optional address of an array of cudaEvent_t handles (see ctq.h);
+    tune: optional launch-tuning dict (TUNE_KEYS)."""
     b = BatchC()
     b.n_chains, b.beta = n_chains, beta
     b.offsets, b.tau, b.op, b.log_threshold = offsets, tau, op, log_threshold
     r = ResultC()
     r.log_abs, r.phase, r.status, r.bounds = log_abs, phase, status, bounds
-    o = _opts(precision, lazy, segment, max_ops, timeout_ns, events, debug_flags)
+    o = _opts(precision, lazy, segment, max_ops, timeout_ns, events, debug_flags, tune)
     _check(_lib.ctq_eval_traces(imp.handle, ctypes.byref(b), ctypes.byref(o), ctypes.byref(r),
                                 workspace, workspace_bytes, stream), "ctq_eval_traces")
 
@@ -330,12 +342,13 @@ class TraceEvaluator:
     the current torch stream (no allocation per call)."""
 
     def __init__(self, imp: Impurity, n_chains: int, max_ops: int, precision=FP64, segment=8,
-                 with_bounds=True, device="cuda"):
+                 with_bounds=True, device="cuda", tune=None):
         import torch
         self.imp = imp
         self.n_chains = n_chains
         self.max_ops = max_ops
         self.precision = precision
+        self.tune = dict(tune or {})  # launch tuning (TUNE_KEYS), e.g. from autotune.tune()
         self.segment = segment
         self.n_seg = (max_ops + segment - 1) // segment
         self.ws_bytes = workspace_size(imp, n_chains, precision, False, segment, max_ops)
@@ -359,7 +372,7 @@ class TraceEvaluator:
                     thr, self.log_abs.data_ptr(), self.phase.data_ptr(), self.status.data_ptr(),
                     self.bounds.data_ptr() if self.bounds is not None else None,
                     self.ws_ptr, self.ws_bytes, s.cuda_stream, self.precision, lazy, self.segment, self.max_ops,
-                    timeout_ns, events, debug_flags)
+                    timeout_ns, events, debug_flags, self.tune)
 
     def results(self, n_chains: Optional[int] = None):
         n = self.n_chains if n_chains is None else n_chains
