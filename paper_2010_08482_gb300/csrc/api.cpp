@@ -92,6 +92,18 @@ int upload_model(ctq_impurity* imp) {
   for (int q = 0; q < h.n_sec; ++q)
     for (int j = h.E_off[q]; j < h.E_off[q + 1]; ++j) e_rel[j] = h.E[j] - h.E_min[q];
   std::vector<float> e_relf(e_rel.begin(), e_rel.end());
+  std::vector<double> lev_E;
+  std::vector<int> lev_off(1, 0), lev_idx(h.E.size());
+  for (int q = 0; q < h.n_sec; ++q) {
+    const int base = int(lev_E.size());
+    for (int j = h.E_off[q]; j < h.E_off[q + 1]; ++j) {
+      int l = base;
+      while (l < int(lev_E.size()) && lev_E[l] != e_rel[j]) ++l;  // bitwise equal values only
+      if (l == int(lev_E.size())) lev_E.push_back(e_rel[j]);
+      lev_idx[j] = l - base;
+    }
+    lev_off.push_back(int(lev_E.size()));
+  }
   std::vector<double> blk;
   if (h.is_complex) {
     blk.resize(2 * h.blk_re.size());
@@ -109,7 +121,9 @@ int upload_model(ctq_impurity* imp) {
       (st = upload_vec(imp, e_rel, &d.E_rel)) || (st = upload_vec(imp, e_relf, &d.E_relf)) ||
       (st = upload_vec(imp, h.E_min, &d.E_min)) ||
       (st = upload_vec(imp, h.s, &d.s)) || (st = upload_vec(imp, h.blk_off, &d.blk_off)) ||
-      (st = upload_vec(imp, blk, &d.blk)) || (st = upload_vec(imp, lognorm, &d.log_norm))) {
+      (st = upload_vec(imp, blk, &d.blk)) || (st = upload_vec(imp, lognorm, &d.log_norm)) ||
+      (st = upload_vec(imp, lev_E, &d.lev_E)) || (st = upload_vec(imp, lev_off, &d.lev_off)) ||
+      (st = upload_vec(imp, lev_idx, &d.lev_idx))) {
     free_device(imp);
     return fail(st, "device upload failed");
   }

@@ -74,6 +74,11 @@ struct DevModel {
   const int64_t* blk_off;  // [n_alpha * n_sec]  element offsets, -1 absent
   const double* blk;    // real: re; complex: interleaved (re, im)
   const double* log_norm;  // [n_alpha * n_sec]  log ||F||_2 (-inf absent)
+  // distinct values of E_rel per sector (bitwise equal states share one
+  // propagator entry): level values, per-sector offsets, state -> level
+  const double* lev_E;     // [sum n_lev]
+  const int* lev_off;      // [n_sec + 1]
+  const int* lev_idx;      // [sum dims]  level of each state within its sector
 };
 
 struct BatchView {

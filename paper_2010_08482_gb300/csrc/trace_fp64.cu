@@ -100,7 +100,9 @@ __global__ void __launch_bounds__(256, 1) k_trace(DevModel M, BatchView B, EvalC
   double* red = p0 + D;                                          // [64] reductions
   double* segL = red + 64;                                       // [NS] log scale at segment ends
   double* segP = segL + NS;                                      // [NS] applied log-norm sums
-  double* pall = segP + NS;                                      // [MO * D] (PRE)
+  double* segF = segP + NS;                                      // [NS] ||Y||^2 at segment ends (deferred)
+  double* segE = segF + NS;                                      // [NS] exponent sums at segment ends
+  double* pall = segE + NS;                                      // [MO * D] (PRE)
   int* poff = reinterpret_cast<int*>(pall + (PRE ? size_t(MO) * D : 0));  // [MO + 1] (PRE)
   short* path = reinterpret_cast<short*>(poff + (PRE ? MO + 1 : 0));     // [MO + 1] sectors q_0..q_n
   short* opsm = path + (MO + 1);                                          // [MO] operator codes
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(256, 1) k_trace(DevModel M, BatchView B, EvalC
       for (int i = 0; i < n; ++i) {
         q = M.s[opsm[i] * ns + q];
         path[i + 1] = short(q);
-        if (PRE && i + 1 < n) poff[i + 1] = poff[i] + M.dims[q];
+        if (PRE && i + 1 < n) poff[i + 1] = poff[i] + (M.lev_off[q + 1] - M.lev_off[q]);
       }
     }
     __syncthreads();
@@ -195,7 +197,8 @@ __global__ void __launch_bounds__(256, 1) k_trace(DevModel M, BatchView B, EvalC
     __syncthreads();
     for (int j = tid; j < d0; j += nt) p0[j] = exp(-t_first * E0[j]) * exp(-t_last * E0[j]);
     if (PRE) {
-      // all propagators of the chain: flat index j -> (operator i, state m)
+      // all propagators of the chain, one per distinct level of each visited
+      // sector: flat index j -> (operator i, level l)
       const int total = poff[n - 1];
       for (int j = tid; j < total; j += nt) {
         int lo = 0, hi = n - 2;  // largest i with poff[i] <= j
@@ -205,7 +208,7 @@ __global__ void __launch_bounds__(256, 1) k_trace(DevModel M, BatchView B, EvalC
         }
         const int q = path[lo + 1];
         const double dt = B.tau[a0 + lo + 1] - B.tau[a0 + lo];
-        pall[j] = exp(-dt * M.E_rel[M.E_off[q] + (j - poff[lo])]);
+        pall[j] = exp(-dt * M.lev_E[M.lev_off[q] + (j - poff[lo])]);
       }
     }
 
@@ -219,7 +222,9 @@ __global__ void __launch_bounds__(256, 1) k_trace(DevModel M, BatchView B, EvalC
       const double* Eb = M.E_rel + M.E_off[qb];
       for (int m = tid; m < M.dims[qb]; m += nt) p[m] = exp(-dt * Eb[m]);
     } else {
-      p1 = pall;  // poff[0] = 0
+      __syncthreads();  // pall complete
+      const int* lv = M.lev_idx + M.E_off[qb];
+      for (int m = tid; m < M.dims[qb]; m += nt) p[m] = pall[lv[m]];  // poff[0] = 0
     }
     __syncthreads();
     T* Y = Ybuf0;
@@ -244,6 +249,7 @@ __global__ void __launch_bounds__(256, 1) k_trace(DevModel M, BatchView B, EvalC
     bool aborted = false;
     double fr = 0.0;     // ||Y||^2 of the stored product (segment steps only)
     bool have_fr = false;
+    int k_rec = 0;       // segments recorded for the deferred bounds
 
     // ---- operators 2 .. n: Y <- P F Y, the previous rescale folded into P
     for (int i = 1; i < n; ++i) {
@@ -255,14 +261,18 @@ __global__ void __launch_bounds__(256, 1) k_trace(DevModel M, BatchView B, EvalC
           for (int idx = tid; idx < dcur * d0; idx += nt) f += sq(Y[idx]);
           fr = block_sum(f, red);
         }
-        if (tid == 0) {
+        if (!cfg.lazy) {  // bounds output only: the logarithms are taken for all segments at the end
+          if (tid == 0) {
+            segF[applied / cfg.S] = fr;
+            segE[applied / cfg.S] = double(Eacc);
+          }
+          ++k_rec;
+        } else if (tid == 0) {
           const double ub = ub_const + 0.5 * log(fr) + double(Eacc) * LN2 +
                             segL[applied / cfg.S] + (it.t_all - segP[applied / cfg.S]);
           segp[applied / cfg.S] = ub;
-          if (cfg.lazy) {
-            W.live[slot] = fmin(W.live[slot], ub);
-            __threadfence();
-          }
+          W.live[slot] = fmin(W.live[slot], ub);
+          __threadfence();
         }
         if (cfg.lazy) {
           if (tid < 32) {
@@ -331,7 +341,8 @@ __global__ void __launch_bounds__(256, 1) k_trace(DevModel M, BatchView B, EvalC
       const int db = M.dims[qb];
       if (PRE) {
         const double* pi = pall + poff[i];
-        for (int m = tid; m < db; m += nt) p[m] = pi[m] * scale;
+        const int* lv = M.lev_idx + M.E_off[qb];
+        for (int m = tid; m < db; m += nt) p[m] = pi[lv[m]] * scale;
       } else {
         const double dt = B.tau[a0 + i + 1] - B.tau[a0 + i];
         const double* Eb = M.E_rel + M.E_off[qb];
@@ -364,6 +375,12 @@ __global__ void __launch_bounds__(256, 1) k_trace(DevModel M, BatchView B, EvalC
       qa = qb;
       ++applied;
     }
+    if (k_rec > 0) {  // deferred refined bounds, lanes over segments
+      __syncthreads();
+      for (int k = 1 + tid; k <= k_rec; k += nt)
+        segp[k] = ub_const + 0.5 * log(segF[k]) + segE[k] * LN2 + segL[k] + (it.t_all - segP[k]);
+      __syncthreads();
+    }
     if (dead && tid == 0) {
       W.res_val[2 * slot] = 0.0;
       W.res_val[2 * slot + 1] = 0.0;
@@ -390,7 +407,7 @@ static int trace_threads(int max_dim) {
 static size_t trace_smem(int max_dim, bool cplx, int max_ops, int n_seg_max, bool pre) {
   const size_t el = cplx ? 16 : 8;
   const size_t mo = size_t(std::max(max_ops, 1));
-  size_t b = 2 * size_t(max_dim) * max_dim * el + 2 * size_t(max_dim) * 8 + 64 * 8 + 2 * size_t(n_seg_max + 1) * 8;
+  size_t b = 2 * size_t(max_dim) * max_dim * el + 2 * size_t(max_dim) * 8 + 64 * 8 + 4 * size_t(n_seg_max + 1) * 8;
   if (pre) b += mo * max_dim * 8 + (mo + 1) * 4;
   b += (mo + 1) * 2 + mo * 2;
   return (b + 15) & ~size_t(15);
