@@ -105,7 +105,10 @@ __global__ void __launch_bounds__(128) k_plan(DevModel M, BatchView B, EvalCfg c
         W.items[slot] = it;  // staging copy in the (c, q0) slot
         W.lvl0[slot] = b;
         W.live[slot] = b;
-        if (b > lm) {
+        if (lm == -INFINITY) {  // first surviving string of this lane
+          ls = 1.0;
+          lm = b;
+        } else if (b > lm) {
           ls = ls * exp(lm - b) + 1.0;
           lm = b;
         } else {
@@ -114,7 +117,18 @@ __global__ void __launch_bounds__(128) k_plan(DevModel M, BatchView B, EvalCfg c
       }
     }
   }
-  const double logB = warp_logsumexp(lm, ls);  // relative to -beta E_ref
+  // relative to -beta E_ref; one lane with one surviving string needs no exp / log
+  const unsigned has = __ballot_sync(FULL, lm != -INFINITY);
+  double logB;
+  if (has == 0u) {
+    logB = -INFINITY;
+  } else if ((has & (has - 1u)) == 0u) {
+    const int src = __ffs(has) - 1;
+    const double l1 = __shfl_sync(FULL, lm, src), s1 = __shfl_sync(FULL, ls, src);
+    logB = (s1 == 1.0) ? l1 : l1 + log(s1);
+  } else {
+    logB = warp_logsumexp(lm, ls);
+  }
   const double shift = -B.beta * M.E_ref;
   if (cfg.bounds && lane == 0) cfg.bounds[size_t(c) * (cfg.n_seg_max + 1)] = logB + shift;
   bool reject = false;
@@ -169,14 +183,16 @@ __global__ void k_combine(DevModel M, BatchView B, EvalCfg cfg, Work W, ctq_resu
         if (s > 0 || (flag & FLAG_INVALID)) cfg.bounds[size_t(c) * nb + s] = NAN;
     return;
   }
-  // w = sum_q0 val * e^{log}, with a common max log (lanes over q0)
+  // w = sum_q0 val * e^{log} with a common scale lm = max_q0 (log + exponent
+  // of |val|): the dominant string's factor is the exact power of two
+  // 2^{-exponent}; only the others need an exponential (lanes over q0)
   double lm = -INFINITY;
   for (int q = lane; q < ns; q += 32) {
     const size_t slot = size_t(c) * ns + q;
     const double lg = W.res_log[slot];
     if (lg == -INFINITY) continue;
     const double a = fabs(W.res_val[2 * slot]) + fabs(W.res_val[2 * slot + 1]);
-    if (a > 0.0) lm = fmax(lm, lg + log(a));
+    if (a > 0.0) lm = fmax(lm, lg + double(ilogb(a)) * LN2);
   }
   lm = warp_max(lm);
   double sr = 0.0, si = 0.0;
@@ -185,16 +201,20 @@ __global__ void k_combine(DevModel M, BatchView B, EvalCfg cfg, Work W, ctq_resu
       const size_t slot = size_t(c) * ns + q;
       const double lg = W.res_log[slot];
       if (lg == -INFINITY) continue;
-      const double f = exp(lg - lm);
-      sr += W.res_val[2 * slot] * f;
-      si += W.res_val[2 * slot + 1] * f;
+      const double vr = W.res_val[2 * slot], vi = W.res_val[2 * slot + 1];
+      const double a = fabs(vr) + fabs(vi);
+      if (a == 0.0) continue;
+      const int ea = ilogb(a);
+      const double f = (lg + double(ea) * LN2 == lm) ? scalbn(1.0, -ea) : exp(lg - lm);
+      sr += vr * f;
+      si += vi * f;
     }
   }
   sr = warp_sum(sr);
   si = warp_sum(si);
   const double shift = -B.beta * M.E_ref;  // logs above are relative to e^{-beta E_ref}
   if (lane == 0) {
-    const double a = hypot(sr, si);
+    const double a = M.is_complex ? hypot(sr, si) : fabs(sr);
     int st = CTQ_CHAIN_OK;
     if (lm == -INFINITY || a == 0.0) {
       R.log_abs[c] = -INFINITY;
