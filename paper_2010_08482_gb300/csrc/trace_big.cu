@@ -9,18 +9,22 @@
 // with complex numbers in the real embedding
 //     [Re Z' | Im Z'] = [Re Z | Im Z] [[Re F, -Im F], [Im F, Re F]]^T,
 // so every product is a real GEMM C = A B^T with both operands K-major:
-//   A = Z_i in global memory as 128 x 32 tiles of K-major core matrices
-//       (8 rows x 16 bytes) so that one cp.async.bulk stages a tile,
-//   B = the embedded block, pre-formatted once per impurity as 256 x 32 tiles,
-// in TF32 or three-term split TF32 (hi*hi + hi*lo + lo*hi) with FP32
-// accumulation in tensor memory.  The epilogue applies the propagator
-// column scale e^{-dtau (E - E_min)} (times the power-of-two rescale of the
-// previous operator), reduces max|Z| and ||Z||_F over the grid, splits
-// hi/lo and writes Z_{i+1} tiles.  Tiles are visited column-major so that a
-// B tile is read from HBM once per product and reused from L2 by all row
-// tiles.  The first operator only scales F_1; the last one needs only the
-// diagonal of F_n Y (FP32 products, FP64 sum).  Log scale, exponents,
-// segment bounds and the trace stay in float64.
+//   A = Z_i in global memory as 128-row tiles of K-major core matrices
+//       (8 rows x 16 bytes), 128 bytes of K per staged chunk, so that one
+//       cp.async.bulk stages a chunk,
+//   B = the embedded block, pre-formatted once per impurity as 256-row tiles
+//       of the same form,
+// in TF32, three-term split TF32 (hi*hi + hi*lo + lo*hi) or three-term split
+// bf16, with FP32 accumulation in tensor memory (a 128 x 256 tile: two
+// accumulators fill the 512 columns, chunks alternate between them).  The
+// epilogue applies the propagator column scale e^{-dtau (E - E_min)} (times
+// the power-of-two rescale of the previous operator), reduces max|Z| and
+// ||Z||_F over the grid, splits hi/lo and writes Z_{i+1} tiles.  Tiles are
+// visited column-major by default so that a B tile is read from HBM once
+// per product and reused from L2 by all row tiles.  The first operator only
+// scales F_1; the last one needs only the diagonal of F_n Y (FP32 products,
+// FP64 sum).  Log scale, exponents, segment bounds and the trace stay in
+// float64.
 //
 // Every wait is bounded (mbarriers and the grid barrier) by the caller's
 // timeout: on expiry the kernel records CTQ_ERR_TIMEOUT in the workspace,
@@ -39,11 +43,14 @@ using namespace ptx;
 
 constexpr int BG_THREADS = 128;
 constexpr int BM = 128;       // rows of a C tile (rows of Z)
-constexpr int BN = 128;       // columns of a C tile (embedded output states)
+constexpr int BN = 256;       // columns of a C tile (embedded output states)
 constexpr int BK = 32;        // sector dimensions are padded to multiples of BK
 constexpr int ROWB = 128;     // bytes of one tile row in a staged K chunk
 constexpr uint32_t A_BYTES = BM * ROWB;  // one staged A tile (16 KB)
-constexpr uint32_t B_BYTES = BN * ROWB;  // one staged B tile (16 KB)
+constexpr uint32_t B_BYTES = BN * ROWB;  // one staged B tile (32 KB)
+// Descriptor strides of a staged tile: core matrices (8 rows x 16 bytes)
+// adjacent in K are rows/8 x 128 bytes apart, adjacent in M/N 128 bytes.
+constexpr uint32_t LBO_A = (BM / 8) * 128, LBO_B = (BN / 8) * 128;
 constexpr uint32_t BAR_TIMEOUT_FLAG = 1u;
 
 // Operand elements: TF32 and 3xTF32 stage float tiles (tf32-rounded), BF16X3
@@ -163,7 +170,7 @@ constexpr int MAX_NST = 12;
 // (chunk kc into accumulator kc % NACC) that the epilogue adds in FP32: each
 // accumulator then sums 1/NACC of the K' terms, which divides the
 // accumulation error of long products (K' up to ~6000) by about NACC.
-constexpr int NACC = 4;
+constexpr int NACC = 512 / BN;  // all 512 tensor-memory columns
 constexpr int PVEC = 3072;    // largest sector dimension of this path
 
 struct BigShared {
@@ -196,7 +203,9 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
   const uint32_t stage_bytes = (SPLIT ? 2u : 1u) * (A_BYTES + B_BYTES);
   unsigned char* stage0 = smem_raw;
   float* p_s = reinterpret_cast<float*>(stage0 + size_t(NST) * stage_bytes);  // [PVEC] column scales
-  float* q_s = p_s + PVEC;                            // [PVEC] wrap-around propagator of q0 (first product)
+  // [PVEC] wrap-around propagator of q0: only the first, elementwise product
+  // of a string reads it, when no copy or MMA uses the stages
+  float* q_s = reinterpret_cast<float*>(stage0);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int ns = M.n_sec;
   const int cplx = M.is_complex;
@@ -333,6 +342,9 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
           Zl[0][o_i] = li;
         }
       }
+      // q_s lives in the stages: order these generic accesses before the
+      // bulk copies that will refill them
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       ek = __reduce_max_sync(0xffffffffu, ek);
       double f2d = warp_sum(double(f2));
       if ((tid & 31) == 0) {
@@ -512,13 +524,13 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
             const uint32_t sbh = sa + A_BYTES, sal = sbh + B_BYTES, sbl = sal + A_BYTES;
             // one MMA covers 32 bytes of K (8 tf32 or 16 bf16): two core matrices
             for (int kk = 0; kk < ROWB / 32; ++kk) {
-              const uint64_t da = sdesc(sa + kk * 2 * 2048, 2048, 128);
-              const uint64_t dbh = sdesc(sbh + kk * 2 * 2048, 2048, 128);
+              const uint64_t da = sdesc(sa + kk * 2 * LBO_A, LBO_A, 128);
+              const uint64_t dbh = sdesc(sbh + kk * 2 * LBO_B, LBO_B, 128);
               const uint32_t tacc = tD + uint32_t(kc % NACC) * BN;
               mma_big<PREC>(tacc, da, dbh, idesc, (kc >= NACC || kk > 0) ? 1u : 0u);
               if (SPLIT) {
-                mma_big<PREC>(tacc, da, sdesc(sbl + kk * 2 * 2048, 2048, 128), idesc, 1u);
-                mma_big<PREC>(tacc, sdesc(sal + kk * 2 * 2048, 2048, 128), dbh, idesc, 1u);
+                mma_big<PREC>(tacc, da, sdesc(sbl + kk * 2 * LBO_B, LBO_B, 128), idesc, 1u);
+                mma_big<PREC>(tacc, sdesc(sal + kk * 2 * LBO_A, LBO_A, 128), dbh, idesc, 1u);
               }
             }
             mma_commit(&S.empty[st]);
@@ -716,12 +728,12 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
       tc_fence_after();
       const uint32_t sa = smem_u32(smem_raw), sbh = sa + A_BYTES, sal = sbh + B_BYTES, sbl = sal + A_BYTES;
       for (int kk = 0; kk < ROWB / 32; ++kk) {
-        const uint64_t da = sdesc(sa + kk * 2 * 2048, 2048, 128);
-        const uint64_t dbh = sdesc(sbh + kk * 2 * 2048, 2048, 128);
+        const uint64_t da = sdesc(sa + kk * 2 * LBO_A, LBO_A, 128);
+        const uint64_t dbh = sdesc(sbh + kk * 2 * LBO_B, LBO_B, 128);
         mma_big<PREC>(tD, da, dbh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
         if (SPLIT) {
-          mma_big<PREC>(tD, da, sdesc(sbl + kk * 2 * 2048, 2048, 128), idesc, 1u);
-          mma_big<PREC>(tD, sdesc(sal + kk * 2 * 2048, 2048, 128), dbh, idesc, 1u);
+          mma_big<PREC>(tD, da, sdesc(sbl + kk * 2 * LBO_B, LBO_B, 128), idesc, 1u);
+          mma_big<PREC>(tD, sdesc(sal + kk * 2 * LBO_A, LBO_A, 128), dbh, idesc, 1u);
         }
       }
       mma_commit(&bar_done);
@@ -783,10 +795,11 @@ size_t big_scratch_bytes(const HostModel& h, int max_ops, int grid) {
   return 4 * zf * 4 + 256 + size_t(max_ops + 2) * (4 + 8) + size_t(2 * grid) * 8 + 1024;
 }
 
-static int big_stages(int prec) { return prec == CTQ_TF32 ? 6 : 3; }
+static int big_stages(int prec) { return prec == CTQ_TF32 ? 4 : 2; }
 
 static size_t big_smem(int prec, int nst) {
-  return size_t(nst) * (prec == CTQ_TF32 ? 1 : 2) * (A_BYTES + B_BYTES) + 2 * PVEC * 4;
+  const size_t stages = size_t(nst) * (prec == CTQ_TF32 ? 1 : 2) * (A_BYTES + B_BYTES);
+  return std::max(stages, size_t(PVEC) * 4) + PVEC * 4;  // the stages also hold q_s
 }
 
 template <int PREC>
