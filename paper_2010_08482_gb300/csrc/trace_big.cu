@@ -41,7 +41,7 @@ namespace {
 using namespace dev;
 using namespace ptx;
 
-constexpr int BG_THREADS = 128;
+constexpr int BG_THREADS = 320;  // warp 0: MMA issuer, warp 1: producer, warps 2-9: drain / epilogue
 constexpr int BM = 128;       // rows of a C tile (rows of Z)
 constexpr int BN = 256;       // columns of a C tile (embedded output states)
 constexpr int BK = 32;        // sector dimensions are padded to multiples of BK
@@ -166,17 +166,20 @@ __device__ __forceinline__ bool grid_sync(unsigned* count, volatile unsigned* ge
 }
 
 constexpr int MAX_NST = 12;
-// The K loop of a product is spread over NACC tensor-memory accumulators
-// (chunk kc into accumulator kc % NACC) that the epilogue adds in FP32: each
-// accumulator then sums 1/NACC of the K' terms, which divides the
-// accumulation error of long products (K' up to ~6000) by about NACC.
-constexpr int NACC = 512 / BN;  // all 512 tensor-memory columns
+// The K loop of a product is cut into groups of GRP chunks accumulated in
+// alternating tensor-memory banks and added into FP32 registers (round to
+// nearest) by the drain warps, so the tensor core's own FP32 accumulation
+// spans at most GRP chunks (128 or 256 K' terms) of a product whose K' reaches
+// ~6000.
+constexpr int NBANK = 512 / BN;  // accumulator banks filling the 512 tensor-memory columns
+constexpr int GRP = 4;            // K chunks accumulated in a bank before it is drained
 constexpr int PVEC = 3072;    // largest sector dimension of this path
 
 struct BigShared {
   uint64_t full[MAX_NST];
   uint64_t empty[MAX_NST];
-  uint64_t done;
+  uint64_t bank_full[2];  // MMAs of a group have completed in the bank
+  uint64_t bank_free[2];  // the drain warps have read the bank
   uint64_t never;  // never arrived on: CTQ_DEBUG_STALL_WAIT waits on it
   uint32_t issued;    // chunks issued by the producer (sequence numbers [0, issued))
   uint32_t consumed;  // chunks whose data the MMA issuer has waited for
@@ -215,21 +218,24 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
       mbar_init(&S.full[i], 1);
       mbar_init(&S.empty[i], 1);
     }
-    mbar_init(&S.done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&S.bank_full[b], 1);
+      mbar_init(&S.bank_free[b], 8);  // one arrival per drain warp
+    }
     mbar_init(&S.never, 1);
     S.fail = 0;
     S.issued = 0;
     S.consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) tmem_alloc(&S.tmem_base, NACC * BN);
+  if (warp == 0) tmem_alloc(&S.tmem_base, NBANK * BN);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tD = S.tmem_base;
-  const uint32_t lane_off = uint32_t(32 * warp) << 16;
+  const int lane = tid & 31;
   uint32_t seq_base = 0;  // sequence number of chunk 0 of the current tile (all threads)
-  uint32_t ph_done = 0;
+  uint32_t grp_base = 0;  // sequence number of the current tile's first accumulation group
   bool alive = true;
   if (cfg.debug & CTQ_DEBUG_STALL_WAIT) {
     // CTA 0 waits on an event that never happens; the others then time out
@@ -473,8 +479,12 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
       // producer) refills a stage as soon as the products reading it have
       // completed and, at the end of a tile, issues the first chunks of the
       // CTA's next tile of the same product; thread 0 (the MMA issuer) only
-      // waits for data, so the tensor core can have up to NST chunks queued.
-      // Both then join the epilogue.
+      // waits for data.  The K loop is cut into groups of GRP chunks with
+      // sequence numbers g (g = grp_base + kc / GRP); group g accumulates in
+      // tensor-memory bank g % 2, which the eight drain warps add into FP32
+      // registers (round to nearest) while the tensor core fills the other
+      // bank.  After a tile's last group the drain warps run the epilogue
+      // from registers and the issuer and producer go on with the next tile.
       volatile int* fail_v = &S.fail;
       auto produce = [&](uint32_t q, int tt, int kc) -> bool {
         int mt_, nt_;
@@ -493,12 +503,12 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
         S.issued = q + 1;
         return true;
       };
+      const int ngrp = (nkc + GRP - 1) / GRP;
       int pre = 0;  // (producer) chunks of the current tile already issued
       for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         int mt, nt;
         tile_coords(t, n_mt, n_nt, P.order, mt, nt);
         const int ncols = min(BN, 2 * dpn - nt * BN);
-        const uint32_t idesc = (PREC == CTQ_BF16X3) ? idesc_bf16(BM, ncols) : idesc_tf32(BM, ncols);
         if (tid == 32) {
           bool okp = true;
           for (int kc = pre; kc < nkc && okp && !*fail_v; ++kc) okp = produce(seq_base + kc, t, kc);
@@ -511,9 +521,17 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
           }
           if (!okp) *fail_v = 1;
         } else if (tid == 0) {
+          const uint32_t idesc = (PREC == CTQ_BF16X3) ? idesc_bf16(BM, ncols) : idesc_tf32(BM, ncols);
           for (int kc = 0; kc < nkc; ++kc) {
             const uint32_t q = seq_base + kc;
+            const uint32_t g = grp_base + uint32_t(kc / GRP);
             const int st = int(q % uint32_t(NST));
+            const uint32_t bank = g & 1u;
+            if (kc % GRP == 0 && g >= 2u &&
+                (*fail_v || !mbar_wait(&S.bank_free[bank], ((g >> 1) - 1u) & 1u, P.timeout_ns))) {
+              *fail_v = 1;
+              break;
+            }
             if (*fail_v || !mbar_wait(&S.full[st], (q / NST) & 1u, P.timeout_ns)) {
               *fail_v = 1;
               break;
@@ -522,73 +540,90 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
             tc_fence_after();
             const uint32_t sa = smem_u32(stage0 + size_t(st) * stage_bytes);
             const uint32_t sbh = sa + A_BYTES, sal = sbh + B_BYTES, sbl = sal + A_BYTES;
+            const uint32_t tacc = tD + bank * uint32_t(BN);
             // one MMA covers 32 bytes of K (8 tf32 or 16 bf16): two core matrices
             for (int kk = 0; kk < ROWB / 32; ++kk) {
               const uint64_t da = sdesc(sa + kk * 2 * LBO_A, LBO_A, 128);
               const uint64_t dbh = sdesc(sbh + kk * 2 * LBO_B, LBO_B, 128);
-              const uint32_t tacc = tD + uint32_t(kc % NACC) * BN;
-              mma_big<PREC>(tacc, da, dbh, idesc, (kc >= NACC || kk > 0) ? 1u : 0u);
+              mma_big<PREC>(tacc, da, dbh, idesc, (kc % GRP != 0 || kk > 0) ? 1u : 0u);
               if (SPLIT) {
                 mma_big<PREC>(tacc, da, sdesc(sbl + kk * 2 * LBO_B, LBO_B, 128), idesc, 1u);
                 mma_big<PREC>(tacc, sdesc(sal + kk * 2 * LBO_A, LBO_A, 128), dbh, idesc, 1u);
               }
             }
             mma_commit(&S.empty[st]);
+            if (kc % GRP == GRP - 1 || kc == nkc - 1) mma_commit(&S.bank_full[bank]);
           }
-          mma_commit(&S.done);
+        } else if (warp >= 2) {
+          // drain warps: lane quarter warp % 4, column half (warp - 2) / 4
+          const int half = (warp - 2) >> 2;
+          const uint32_t tl = uint32_t(32 * (warp & 3)) << 16;
+          float acc[128];
+#pragma unroll
+          for (int c = 0; c < 128; ++c) acc[c] = 0.f;
+          bool okd = true;
+          for (int gi = 0; gi < ngrp; ++gi) {
+            const uint32_t g = grp_base + uint32_t(gi);
+            const uint32_t bank = g & 1u;
+            if (*fail_v || !mbar_wait(&S.bank_full[bank], (g >> 1) & 1u, P.timeout_ns)) {
+              okd = false;
+              break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {  // 32 columns per tensor-memory wait
+              uint32_t v[2][16];
+#pragma unroll
+              for (int u = 0; u < 2; ++u)
+                tmem_ld16(tD + bank * uint32_t(BN) + tl + uint32_t(half * 128 + h * 32 + u * 16), v[u]);
+              tmem_wait_ld();
+#pragma unroll
+              for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int c = 0; c < 16; ++c) acc[h * 32 + u * 16 + c] += __uint_as_float(v[u][c]);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.bank_free[bank]);
+          }
+          if (!okd) *fail_v = 1;
+          // epilogue from registers: this thread's row, 128 columns
+          const int row = mt * BM + 32 * (warp & 3) + lane;
+#pragma unroll
+          for (int c0 = 0; c0 < 128; c0 += 16) {
+            const int cb = half * 128 + c0;  // column within the tile
+            if (!okd || cb >= ncols) break;
+            T hi[16], lo[16];
+#pragma unroll
+            for (int t2 = 0; t2 < 16; ++t2) {
+              const int col = nt * BN + cb + t2;  // embedded column
+              const int j = (col < dpn) ? col : col - dpn;
+              const float x = acc[c0 + t2] * p_s[j];
+              ek = max(ek, (__float_as_int(x) >> 23) & 0xff);
+              f2 += x * x;
+              split_store<PREC>(x, hi[t2], lo[t2]);
+            }
+            // 16 consecutive K elements of the next product: 16-byte stores
+            constexpr int PER16 = 16 / EB;
+#pragma unroll
+            for (int g = 0; g < 16 / PER16; ++g) {
+              const size_t o = tiled_off<EB>(row, nt * BN + cb + PER16 * g, BM, nkc_n);
+              *reinterpret_cast<uint4*>(Zh[nxt] + o) = pack16<PREC>(hi + PER16 * g);
+              if (SPLIT) *reinterpret_cast<uint4*>(Zl[nxt] + o) = pack16<PREC>(lo + PER16 * g);
+            }
+          }
         }
         seq_base += uint32_t(nkc);
-        __syncthreads();
-        const bool ok = (S.fail == 0) && mbar_wait(&S.done, ph_done, P.timeout_ns);
-        ph_done ^= 1u;
-        if (__syncthreads_or(!ok)) {
-          if (tid == 32)  // let issued copies that were never consumed land before leaving
-            for (uint32_t q = S.consumed; q < S.issued; ++q)
-              mbar_wait(&S.full[q % uint32_t(NST)], (q / NST) & 1u, P.timeout_ns);
-          alive = false;
-          break;
-        }
-        tc_fence_after();
-        // epilogue: thread = row of the tile
-        const int row = mt * BM + tid;
-        const int nacc = min(NACC, nkc);
-        for (int c0 = 0; c0 < ncols; c0 += 16) {
-          float acc[16];
-          {
-            uint32_t v[16];
-            tmem_ld16(tD + lane_off + c0, v);
-            tmem_wait_ld();
-#pragma unroll
-            for (int t2 = 0; t2 < 16; ++t2) acc[t2] = __uint_as_float(v[t2]);
-          }
-          for (int a = 1; a < nacc; ++a) {
-            uint32_t v[16];
-            tmem_ld16(tD + uint32_t(a * BN) + lane_off + c0, v);
-            tmem_wait_ld();
-#pragma unroll
-            for (int t2 = 0; t2 < 16; ++t2) acc[t2] += __uint_as_float(v[t2]);
-          }
-          T hi[16], lo[16];
-#pragma unroll
-          for (int t2 = 0; t2 < 16; ++t2) {
-            const int col = nt * BN + c0 + t2;  // embedded column
-            const int j = (col < dpn) ? col : col - dpn;
-            const float x = acc[t2] * p_s[j];
-            ek = max(ek, (__float_as_int(x) >> 23) & 0xff);
-            f2 += x * x;
-            split_store<PREC>(x, hi[t2], lo[t2]);
-          }
-          // 16 consecutive K elements of the next product: 16-byte stores
-          constexpr int PER16 = 16 / EB;
-#pragma unroll
-          for (int g = 0; g < 16 / PER16; ++g) {
-            const size_t o = tiled_off<EB>(row, nt * BN + c0 + PER16 * g, BM, nkc_n);
-            *reinterpret_cast<uint4*>(Zh[nxt] + o) = pack16<PREC>(hi + PER16 * g);
-            if (SPLIT) *reinterpret_cast<uint4*>(Zl[nxt] + o) = pack16<PREC>(lo + PER16 * g);
-          }
-        }
-        tc_fence_before();
-        __syncthreads();
+        grp_base += uint32_t(ngrp);
+      }
+      // the running product is read by bulk copies (async proxy) next
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      __syncthreads();
+      if (S.fail) {
+        if (tid == 32)  // let issued copies that were never consumed land before leaving
+          for (uint32_t q = S.consumed; q < S.issued; ++q)
+            mbar_wait(&S.full[q % uint32_t(NST)], (q / NST) & 1u, P.timeout_ns);
+        alive = false;
       }
       if (!alive) break;
       ek = __reduce_max_sync(0xffffffffu, ek);
@@ -621,7 +656,7 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tD, NACC * BN);
+    tmem_dealloc(tD, NBANK * BN);
   }
 }
 
@@ -667,8 +702,10 @@ __global__ void k_format_big(const double* blk, int cplx, int dn, int dk, typena
 // one 128 x N tile, A (128 x K) and B (N x K) split and tiled on the device
 // exactly like Z and the embedded blocks, staged chunk by chunk with bulk
 // copies and multiplied with the same descriptors and instruction kinds.
+constexpr int CHK_THREADS = 128;  // one thread per row of the tile
+
 template <int PREC>
-__global__ void __launch_bounds__(BG_THREADS, 1)
+__global__ void __launch_bounds__(CHK_THREADS, 1)
     k_big_gemm_check(const float* A, const float* Bm, typename Elt<PREC>::T* ws, float* D, int N, int K,
                      uint64_t timeout_ns, int* status) {
   using T = typename Elt<PREC>::T;
@@ -685,14 +722,14 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
   T* Al = Ah + size_t(nkc) * a_tile;
   T* Bh = Al + size_t(nkc) * a_tile;
   T* Bl = Bh + size_t(nkc) * b_tile;
-  for (int e = tid; e < 128 * K; e += BG_THREADS) {
+  for (int e = tid; e < 128 * K; e += CHK_THREADS) {
     const int r = e / K, k = e - r * K;
     T h, l;
     split_store<PREC>(A[e], h, l);
     Ah[tiled_off<EB>(r, k, BM, nkc)] = h;
     Al[tiled_off<EB>(r, k, BM, nkc)] = l;
   }
-  for (int e = tid; e < BN * K; e += BG_THREADS) {
+  for (int e = tid; e < BN * K; e += CHK_THREADS) {
     const int r = e / K, k = e - r * K;
     T h, l;
     split_store<PREC>(r < N ? Bm[size_t(r) * K + k] : 0.f, h, l);
@@ -918,13 +955,13 @@ extern "C" int ctq_big_gemm_check(int device, const float* A, const float* Bm, f
     const uint64_t tmo = 2000000000ull;
     if (precision == CTQ_BF16X3) {
       cudaFuncSetAttribute(k_big_gemm_check<CTQ_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-      k_big_gemm_check<CTQ_BF16X3><<<1, BG_THREADS, smem>>>(dA, dB, static_cast<uint16_t*>(ws), dD, N, K, tmo, dS);
+      k_big_gemm_check<CTQ_BF16X3><<<1, CHK_THREADS, smem>>>(dA, dB, static_cast<uint16_t*>(ws), dD, N, K, tmo, dS);
     } else if (precision == CTQ_TF32X3) {
       cudaFuncSetAttribute(k_big_gemm_check<CTQ_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-      k_big_gemm_check<CTQ_TF32X3><<<1, BG_THREADS, smem>>>(dA, dB, static_cast<float*>(ws), dD, N, K, tmo, dS);
+      k_big_gemm_check<CTQ_TF32X3><<<1, CHK_THREADS, smem>>>(dA, dB, static_cast<float*>(ws), dD, N, K, tmo, dS);
     } else {
       cudaFuncSetAttribute(k_big_gemm_check<CTQ_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-      k_big_gemm_check<CTQ_TF32><<<1, BG_THREADS, smem>>>(dA, dB, static_cast<float*>(ws), dD, N, K, tmo, dS);
+      k_big_gemm_check<CTQ_TF32><<<1, CHK_THREADS, smem>>>(dA, dB, static_cast<float*>(ws), dD, N, K, tmo, dS);
     }
     if (cudaDeviceSynchronize() != cudaSuccess) st = CTQ_ERR_CUDA;
     if (st == CTQ_OK) {
