@@ -41,7 +41,8 @@ namespace {
 using namespace dev;
 using namespace ptx;
 
-constexpr int BG_THREADS = 320;  // warp 0: MMA issuer, warp 1: producer, warps 2-9: drain / epilogue
+constexpr int N_DRAIN = 8;                       // drain / epilogue warps (N_DRAIN / 4 per lane quarter)
+constexpr int BG_THREADS = 32 * (2 + N_DRAIN);   // warp 0: MMA issuer, warp 1: producer
 constexpr int BM = 128;       // rows of a C tile (rows of Z)
 constexpr int BN = 256;       // columns of a C tile (embedded output states)
 constexpr int BK = 32;        // sector dimensions are padded to multiples of BK
@@ -168,7 +169,7 @@ __device__ __forceinline__ bool grid_sync(unsigned* count, volatile unsigned* ge
 constexpr int MAX_NST = 12;
 // The K loop of a product is cut into groups of GRP chunks accumulated in
 // alternating tensor-memory banks and added into FP32 registers (round to
-// nearest) by the drain warps, so the tensor core's own FP32 accumulation
+// nearest) by the N_DRAIN drain warps, so the tensor core's own FP32 accumulation
 // spans at most GRP chunks (128 or 256 K' terms) of a product whose K' reaches
 // ~6000.
 constexpr int NBANK = 512 / BN;  // accumulator banks filling the 512 tensor-memory columns
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&S.bank_full[b], 1);
-      mbar_init(&S.bank_free[b], 8);  // one arrival per drain warp
+      mbar_init(&S.bank_free[b], N_DRAIN);  // one arrival per drain warp
     }
     mbar_init(&S.never, 1);
     S.fail = 0;
@@ -481,7 +482,7 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
       // CTA's next tile of the same product; thread 0 (the MMA issuer) only
       // waits for data.  The K loop is cut into groups of GRP chunks with
       // sequence numbers g (g = grp_base + kc / GRP); group g accumulates in
-      // tensor-memory bank g % 2, which the eight drain warps add into FP32
+      // tensor-memory bank g % 2, which the N_DRAIN drain warps add into FP32
       // registers (round to nearest) while the tensor core fills the other
       // bank.  After a tile's last group the drain warps run the epilogue
       // from registers and the issuer and producer go on with the next tile.
@@ -555,12 +556,14 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
             if (kc % GRP == GRP - 1 || kc == nkc - 1) mma_commit(&S.bank_full[bank]);
           }
         } else if (warp >= 2) {
-          // drain warps: lane quarter warp % 4, column half (warp - 2) / 4
-          const int half = (warp - 2) >> 2;
+          // drain warps: lane quarter warp % 4, column slice (warp - 2) / 4 of
+          // COLS columns
+          constexpr int COLS = BN / (N_DRAIN / 4);
+          const int slice = (warp - 2) >> 2;
           const uint32_t tl = uint32_t(32 * (warp & 3)) << 16;
-          float acc[128];
+          float acc[COLS];
 #pragma unroll
-          for (int c = 0; c < 128; ++c) acc[c] = 0.f;
+          for (int c = 0; c < COLS; ++c) acc[c] = 0.f;
           bool okd = true;
           for (int gi = 0; gi < ngrp; ++gi) {
             const uint32_t g = grp_base + uint32_t(gi);
@@ -571,11 +574,11 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
             }
             tc_fence_after();
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {  // 32 columns per tensor-memory wait
+            for (int h = 0; h < COLS / 32; ++h) {  // 32 columns per tensor-memory wait
               uint32_t v[2][16];
 #pragma unroll
               for (int u = 0; u < 2; ++u)
-                tmem_ld16(tD + bank * uint32_t(BN) + tl + uint32_t(half * 128 + h * 32 + u * 16), v[u]);
+                tmem_ld16(tD + bank * uint32_t(BN) + tl + uint32_t(slice * COLS + h * 32 + u * 16), v[u]);
               tmem_wait_ld();
 #pragma unroll
               for (int u = 0; u < 2; ++u)
@@ -587,29 +590,30 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
             if (lane == 0) mbar_arrive(&S.bank_free[bank]);
           }
           if (!okd) *fail_v = 1;
-          // epilogue from registers: this thread's row, 128 columns
+          // epilogue from registers: this thread's row, COLS columns
           const int row = mt * BM + 32 * (warp & 3) + lane;
 #pragma unroll
-          for (int c0 = 0; c0 < 128; c0 += 16) {
-            const int cb = half * 128 + c0;  // column within the tile
+          for (int c0 = 0; c0 < COLS; c0 += 16) {
+            const int cb = slice * COLS + c0;  // column within the tile
             if (!okd || cb >= ncols) break;
-            T hi[16], lo[16];
-#pragma unroll
-            for (int t2 = 0; t2 < 16; ++t2) {
-              const int col = nt * BN + cb + t2;  // embedded column
-              const int j = (col < dpn) ? col : col - dpn;
-              const float x = acc[c0 + t2] * p_s[j];
-              ek = max(ek, (__float_as_int(x) >> 23) & 0xff);
-              f2 += x * x;
-              split_store<PREC>(x, hi[t2], lo[t2]);
-            }
-            // 16 consecutive K elements of the next product: 16-byte stores
+            // 16 consecutive K elements of the next product, written as
+            // 16-byte vectors of PER16 elements
             constexpr int PER16 = 16 / EB;
 #pragma unroll
             for (int g = 0; g < 16 / PER16; ++g) {
+              T hi[PER16], lo[PER16];
+#pragma unroll
+              for (int t2 = 0; t2 < PER16; ++t2) {
+                const int col = nt * BN + cb + PER16 * g + t2;  // embedded column
+                const int j = (col < dpn) ? col : col - dpn;
+                const float x = acc[c0 + PER16 * g + t2] * p_s[j];
+                ek = max(ek, (__float_as_int(x) >> 23) & 0xff);
+                f2 += x * x;
+                split_store<PREC>(x, hi[t2], lo[t2]);
+              }
               const size_t o = tiled_off<EB>(row, nt * BN + cb + PER16 * g, BM, nkc_n);
-              *reinterpret_cast<uint4*>(Zh[nxt] + o) = pack16<PREC>(hi + PER16 * g);
-              if (SPLIT) *reinterpret_cast<uint4*>(Zl[nxt] + o) = pack16<PREC>(lo + PER16 * g);
+              *reinterpret_cast<uint4*>(Zh[nxt] + o) = pack16<PREC>(hi);
+              if (SPLIT) *reinterpret_cast<uint4*>(Zl[nxt] + o) = pack16<PREC>(lo);
             }
           }
         }
