@@ -52,7 +52,7 @@ def candidates(imp: "ctq.Impurity", precision: int) -> List[Dict[str, int]]:
         if precision != ctq.TF32X3:  # 3xTF32 holds all tensor memory: one CTA per SM
             out.append({"ctas_per_sm": 1})
     else:
-        stages = (2, 3) if precision != ctq.TF32 else (3, 4, 5, 6)
+        stages = (2, 3) if precision != ctq.TF32 else (2, 3, 4)  # deeper pipelines are refused if they do not fit
         for st in stages:
             for order in (0, 1, 2):
                 out.append({"stages": st, "tile_order": order})

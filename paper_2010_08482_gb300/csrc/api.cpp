@@ -21,6 +21,9 @@ struct ctq_impurity {
   ctq::LaunchCfg launch_tc1{}, launch_tc2{}, launch_tc3{};
   // large-block tensor-core path (complex impurities or blocks > 112)
   bool big = false;
+  bool big64 = false;  // CTQ_FP64 on the float64 large-block kernel
+  ctq::Big64Params b64{};
+  ctq::LaunchCfg launch_b64{};
   ctq::BigParams big1{}, big2{}, big3{};  // CTQ_TF32, CTQ_BF16X3, CTQ_TF32X3
   ctq::LaunchCfg launch_big1{}, launch_big2{}, launch_big3{};
   std::vector<void*> allocs;
@@ -204,6 +207,37 @@ int upload_model(ctq_impurity* imp) {
       return fail(st, "cannot configure the large-block kernel");
     }
     imp->big = true;
+  }
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, imp->device) != cudaSuccess) {
+    free_device(imp);
+    return fail(CTQ_ERR_CUDA, "cannot query the device");
+  }
+  if (!ctq::fp64_shared_kernel_fits(d, optin) && h.max_dim <= 3072) {
+    // float64 large-block path: embedded, row-major float64 copies of the blocks
+    std::vector<int64_t> off(h.s.size(), -1);
+    size_t total = 0;
+    for (int a = 0; a < h.n_alpha(); ++a)
+      for (int q = 0; q < h.n_sec; ++q) {
+        const size_t i = size_t(a) * h.n_sec + q;
+        if (h.s[i] < 0) continue;
+        off[i] = int64_t(total);
+        total += ctq::big64_block_elems(h.dims[h.s[i]], h.dims[q]);
+      }
+    void* bt = nullptr;
+    if (cudaMalloc(&bt, std::max<size_t>(total, 1) * sizeof(double)) != cudaSuccess) {
+      free_device(imp);
+      return fail(CTQ_ERR_NOMEM, "cannot allocate the float64 large-block operands");
+    }
+    imp->allocs.push_back(bt);
+    if ((st = ctq::format_big64_blocks(h, d.blk, static_cast<double*>(bt), off)) != CTQ_OK ||
+        (st = upload_vec(imp, off, &imp->b64.bt_off)) != CTQ_OK ||
+        (st = ctq::prepare_eval_big64(imp->num_sms, &imp->launch_b64)) != CTQ_OK) {
+      free_device(imp);
+      return fail(st, "float64 large-block setup failed");
+    }
+    imp->b64.bt = static_cast<const double*>(bt);
+    imp->big64 = true;
   }
   return CTQ_OK;
 }
@@ -430,7 +464,9 @@ static int n_seg_of(const ctq_eval_opts* o) {
 }
 
 static size_t big_extra(const ctq_impurity* imp, const ctq_eval_opts* opts) {
-  if (!imp->big || opts->precision == CTQ_FP64) return 0;
+  if (opts->precision == CTQ_FP64)
+    return imp->big64 ? ctq::big64_scratch_bytes(imp->host, std::max(0, opts->max_ops), imp->num_sms) + 256 : 0;
+  if (!imp->big) return 0;
   return ctq::big_scratch_bytes(imp->host, std::max(0, opts->max_ops), imp->num_sms) + 256;
 }
 
@@ -500,7 +536,13 @@ int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_e
   cfg.stages = opts->stages;
   cfg.tile_order = opts->tile_order;
   int st;
-  if (opts->precision == CTQ_FP64) {
+  if (opts->precision == CTQ_FP64 && imp->big64) {
+    ctq::Big64Params P = imp->b64;
+    P.timeout_ns = opts->timeout_ns > 0 ? uint64_t(opts->timeout_ns) : uint64_t(2000000000ull);
+    char* scratch = static_cast<char*>(workspace) + ((base + 255) & ~size_t(255));
+    st = ctq::launch_eval_big64(imp->dev, imp->launch_b64, P, B, cfg, W, result, scratch, stream,
+                                opts->timing_events);
+  } else if (opts->precision == CTQ_FP64) {
     st = ctq::launch_eval_fp64(imp->dev, imp->launch, B, cfg, W, result, stream, opts->timing_events);
   } else if (imp->big) {
     ctq::BigParams P = pr == CTQ_TF32 ? imp->big1 : pr == CTQ_BF16X3 ? imp->big2 : imp->big3;

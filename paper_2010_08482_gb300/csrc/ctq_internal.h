@@ -174,6 +174,29 @@ struct BigParams {
   int* abort_flag = nullptr;
 };
 
+// Per-impurity parameters and scratch of the float64 large-block path (trace_big64.cu).
+struct Big64Params {
+  const double* bt = nullptr;       // embedded float64 blocks, row-major, per (alpha, q)
+  const int64_t* bt_off = nullptr;  // [n_alpha * n_sec] element offsets, -1 absent
+  uint64_t timeout_ns = 0;
+  double* zbuf = nullptr;           // scratch: two Z buffers
+  size_t zelems = 0;                // elements of one Z buffer
+  unsigned* bar = nullptr;          // grid barrier: count, generation
+  int* ekey = nullptr;              // [max_ops + 2] max exponent field per operator
+  double* fr = nullptr;             // [max_ops + 2] ||Z||^2 per operator
+  double* part = nullptr;           // [2 * grid] final-trace partial sums
+  int* abort_flag = nullptr;
+  int order = 0;                    // tile order (ctq_eval_opts.tile_order)
+};
+
+size_t big64_block_elems(int dn, int dk);
+int format_big64_blocks(const HostModel& h, const double* d_blk, double* out, const std::vector<int64_t>& off);
+size_t big64_scratch_bytes(const HostModel& h, int max_ops, int grid);
+int prepare_eval_big64(int num_sms, LaunchCfg* lc);
+int launch_eval_big64(const DevModel& M, const LaunchCfg& lc, Big64Params P, const BatchView& B, const EvalCfg& cfg,
+                      const Work& W, const ctq_result* R, void* scratch, void* stream, void* const* events);
+bool fp64_shared_kernel_fits(const DevModel& M, int optin);
+
 size_t big_block_elems(int dn, int dk);
 int format_big_blocks(const HostModel& h, const double* d_blk, void* out, const std::vector<int64_t>& off, int prec);
 size_t big_scratch_bytes(const HostModel& h, int max_ops, int grid);

@@ -34,12 +34,14 @@
 
 #include "device_common.cuh"
 #include "tc_ptx.cuh"
+#include "big_common.cuh"
 
 namespace ctq {
 namespace {
 
 using namespace dev;
 using namespace ptx;
+using namespace bigc;
 
 constexpr int N_DRAIN = 8;                       // drain / epilogue warps (N_DRAIN / 4 per lane quarter)
 constexpr int BG_THREADS = 32 * (2 + N_DRAIN);   // warp 0: MMA issuer, warp 1: producer
@@ -66,7 +68,6 @@ struct Elt<CTQ_BF16X3> {
   using T = uint16_t;
 };
 
-__device__ __forceinline__ int rup(int x, int m) { return (x + m - 1) / m * m; }
 
 // Offset (elements of EB bytes) of element (row r, column k) of a matrix
 // stored as tiles of `rows_per_tile` rows x 128 bytes of K, tile (rt, kc) at
@@ -82,25 +83,6 @@ __host__ __device__ __forceinline__ size_t tiled_off(int r, int k, int rows_per_
          size_t((kk / EPC) * (rows_per_tile >> 3) + (rr >> 3)) * (8 * EPC) + (rr & 7) * EPC + (kk % EPC);
 }
 
-// Tile (row mt, column nt) of linear tile index t in a product of n_mt x n_nt
-// tiles: order 0 column-major (consecutive CTAs share a B tile), 1 row-major
-// (they share an A tile), 2 groups of 8 column tiles, row-major inside a group.
-__device__ __forceinline__ void tile_coords(int t, int n_mt, int n_nt, int order, int& mt, int& nt) {
-  if (order == 1) {
-    mt = t / n_nt;
-    nt = t - mt * n_nt;
-  } else if (order == 2) {
-    constexpr int G = 8;
-    const int g = t / (G * n_mt);
-    const int width = min(G, n_nt - g * G);
-    const int local = t - g * G * n_mt;
-    mt = local / width;
-    nt = g * G + (local - mt * width);
-  } else {
-    nt = t / n_mt;
-    mt = t - nt * n_mt;
-  }
-}
 
 // hi / lo split of x in the operand format of PREC.
 template <int PREC>
@@ -139,32 +121,6 @@ __device__ __forceinline__ void mma_big(uint32_t d, uint64_t a, uint64_t b, uint
   else mma_tf32_ss(d, a, b, idesc, acc);
 }
 
-// Grid barrier with a bounded wait (sense reversal on a generation word).
-__device__ __forceinline__ bool grid_sync(unsigned* count, volatile unsigned* gen, uint64_t timeout_ns) {
-  __syncthreads();
-  __shared__ int ok_s;
-  if (threadIdx.x == 0) {
-    ok_s = 1;
-    const unsigned g = *gen;
-    __threadfence();
-    if (atomicAdd(count, 1u) == gridDim.x - 1) {
-      *count = 0;
-      __threadfence();
-      atomicAdd(const_cast<unsigned*>(gen), 1u);
-    } else {
-      const uint64_t t0 = globaltimer();
-      while (*gen == g) {
-        if (globaltimer() - t0 > timeout_ns) {
-          ok_s = 0;
-          break;
-        }
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return ok_s != 0;
-}
 
 constexpr int MAX_NST = 12;
 // The K loop of a product is cut into groups of GRP chunks accumulated in

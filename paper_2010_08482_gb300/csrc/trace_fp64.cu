@@ -428,6 +428,12 @@ static int set_attr(int optin) {
              : CTQ_ERR_CUDA;
 }
 
+// Whether the shared-memory FP64 kernel can hold two blocks of the largest
+// sector (shortest strings); otherwise the float64 large-block kernel runs.
+bool fp64_shared_kernel_fits(const DevModel& M, int optin) {
+  return trace_smem(M.max_dim, M.is_complex != 0, 1, 1, false) + 2048 <= size_t(optin);
+}
+
 int prepare_eval_fp64(const DevModel& M, int num_sms, LaunchCfg* lc) {
   lc->threads = trace_threads(M.max_dim);
   lc->num_sms = num_sms;

@@ -50,8 +50,16 @@ def test_big_engine_candidates_agree_with_default():
     db = ctq.DeviceBatch(w.random_batch(np.random.default_rng(5), 10, p.beta, 6, 6, 12, gen="g2"))
     for prec in (ctq.TF32X3, ctq.BF16X3):
         ref = _run(imp, db, prec, {})
+        ran = 0
         for cand in autotune.candidates(imp, prec)[1:]:
-            _same(_run(imp, db, prec, cand), ref, 0.0)
+            try:
+                res = _run(imp, db, prec, cand)
+            except ctq.CtqError as exc:  # more stages than fit in shared memory: refused, as the tuner expects
+                assert "unsupported" in str(exc)
+                continue
+            _same(res, ref, 0.0)
+            ran += 1
+        assert ran >= 2
 
 
 def test_tune_picks_a_candidate_and_caches_it(tmp_path):

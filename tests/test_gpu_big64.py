@@ -1,0 +1,113 @@
+"""Float64 large-block engine (k_trace_big64: persistent cooperative kernel,
+SIMT float64 tiles, complex blocks in the real embedding): parity with the
+FP64 oracle at the FP64 bar on models whose blocks are too large for the
+shared-memory FP64 kernel (a complex d shell with SOC and complex crystal
+field, N in [1, 3], blocks up to 120; a real d shell with sectors by N, N in
+[4, 6], blocks up to 252), bounds that bracket |w|, and the f shell against
+the stored oracle values (tests/golden/f7_oracle.json)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import parity  # noqa: E402
+from oracle import atom  # noqa: E402
+from oracle import trace as OT  # noqa: E402
+from paper_2010_08482_gb300 import ctq  # noqa: E402
+from paper_2010_08482_gb300 import workloads as w  # noqa: E402
+from test_gpu_big import complex_d_model, real_d_window_model  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def run(imp, batch, S=8, thr=None, lazy=False):
+    db = ctq.DeviceBatch(batch, log_threshold=thr)
+    ev = ctq.TraceEvaluator(imp, batch.n_chains, max(1, db.max_ops), precision=ctq.FP64, segment=S)
+    ev(db, lazy=lazy)
+    torch.cuda.synchronize()
+    return ev.results(batch.n_chains)
+
+
+@pytest.fixture(scope="module")
+def small_models():
+    return {"dc": atom.Model(complex_d_model()), "dn": atom.Model(real_d_window_model())}
+
+
+@pytest.mark.parametrize("name", ["dc", "dn"])
+def test_big64_parity_at_fp64_bar(name, small_models):
+    m = small_models[name]
+    assert max(m.dims) > 112  # the shared-memory FP64 kernel cannot hold these blocks
+    rng = np.random.default_rng(51)
+    b = w.random_batch(rng, m.n_flav, m.beta, 12, 1, 14, gen="g2")
+    imp = parity.load_oracle_model(ctq, m)
+    res = run(imp, b)
+    ref = parity.oracle_chain_results(m, b, range(b.n_chains))
+    worst, n_ok = 0.0, 0
+    for c in range(b.n_chains):
+        r = ref[c]
+        err, kind = parity.chain_error(res["log_abs"][c], res["phase"][c], r)
+        assert err <= parity.fp64_tolerance(r), (c, err, kind, r.get("noise"))
+        worst = max(worst, err)
+        if r["log_abs"] == -math.inf:
+            assert res["status"][c] == ctq.CHAIN_ZERO
+        else:
+            assert res["status"][c] == ctq.CHAIN_OK
+            n_ok += 1
+    assert n_ok >= 6
+    print(f"{name} FP64 large-block: worst rel err {worst:.3e} over {n_ok} chains")
+
+
+def test_big64_bounds_and_lazy_decisions(small_models):
+    m = small_models["dn"]
+    rng = np.random.default_rng(53)
+    b = w.random_batch(rng, m.n_flav, m.beta, 8, 6, 12, gen="g2")
+    imp = parity.load_oracle_model(ctq, m)
+    ref = parity.oracle_chain_results(m, b, range(b.n_chains), noise=False)
+    res = run(imp, b, S=4)
+    for c in range(b.n_chains):
+        tau, ops = b.chain(c)
+        B, ub = OT.chain_bounds(m, tau, ops, b.beta, 4)
+        got = res["bounds"][c]
+        if B == -math.inf:
+            continue
+        assert got[0] == pytest.approx(B, abs=1e-9 + 1e-12 * abs(B))
+        fin = got[np.isfinite(got)]
+        if ref[c]["log_abs"] != -math.inf:
+            assert np.all(fin >= ref[c]["log_abs"] - 1e-9)
+    # thresholds that force a level-0 reject or an accept
+    thr = np.array([(ref[c]["log_abs"] - math.log(2.0)) if (c % 2 == 0 and ref[c]["log_abs"] != -math.inf)
+                    else 1e300 for c in range(b.n_chains)])
+    res = run(imp, b, thr=thr, lazy=True)
+    for c in range(b.n_chains):
+        if thr[c] == 1e300:
+            assert res["status"][c] in (ctq.CHAIN_REJECTED_EARLY, ctq.CHAIN_ZERO)
+        else:
+            assert res["status"][c] == ctq.CHAIN_ACCEPTED
+
+
+def test_f7_fp64_against_stored_oracle():
+    """Library-built f shell (device eigensolver) in float64 on the GPU against
+    the oracle's stored values: the bar is set by the two independent
+    eigensolvers (their ground-state energies agree to 1e-9), times beta."""
+    path = os.path.join(HERE, "golden", "f7_oracle.json")
+    if not os.path.exists(path):
+        pytest.skip("tests/golden/f7_oracle.json not generated")
+    with open(path) as f:
+        g = json.load(f)
+    imp = ctq.build_impurity(w.model_f7(), device=0)
+    n = 2
+    b = w.batch_f7().subset(range(n))
+    res = run(imp, b)
+    tol = 2.0 * b.beta * 1e-9 + 1e-12
+    for c in range(n):
+        ref = g["chains"][c]
+        err = abs(complex(*res["phase"][c]) * math.exp(res["log_abs"][c] - ref["log_abs"]) - complex(*ref["phase"]))
+        print(f"f7 FP64 chain {c}: rel err {err:.3e}")
+        assert err <= tol, (c, err)
+        assert res["status"][c] == ctq.CHAIN_OK
