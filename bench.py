@@ -372,9 +372,11 @@ def main():
     tuning = {}
     if not args.no_autotune:  # launch configuration picked by the package's autotuner, before any timing
         from paper_2010_08482_gb300 import autotune
-        big = autotune.engine(imp, prec) == "big"
-        tdb = ctq.DeviceBatch(batch.subset(range(min(batch.n_chains, 4))), device=dev) if big else db
-        tuning = autotune.tune(imp, tdb, prec, cache_path=args.autotune_cache, reps=1 if big else 3)
+        eng = autotune.engine(imp, prec)
+        if eng != "fp64big":  # the float64 large-block kernel is FP64-pipe bound: nothing worth seconds of tuning
+            big = eng == "big"
+            tdb = ctq.DeviceBatch(batch.subset(range(min(batch.n_chains, 4))), device=dev) if big else db
+            tuning = autotune.tune(imp, tdb, prec, cache_path=args.autotune_cache, reps=1 if big else 3)
     ev = ctq.TraceEvaluator(imp, batch.n_chains, db.max_ops, precision=prec, device=dev, tune=tuning)
     flops, n_items = algorithmic_flops(imp, batch)
     launches = ctq.launches_per_eval(imp)

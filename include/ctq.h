@@ -282,6 +282,20 @@ int ctq_eval_traces_static(const ctq_impurity* imp, const ctq_batch* batch, cons
  */
 int ctq_launches_per_eval(const ctq_impurity* imp, const ctq_eval_opts* opts);
 
+/*
+ * Which trace kernel ctq_eval_traces runs for this impurity and precision:
+ * CTQ_KERNEL_FP64_SHARED (float64, blocks in shared memory),
+ * CTQ_KERNEL_FP64_LARGE (float64, persistent large-block kernel),
+ * CTQ_KERNEL_TC_SMALL (tensor cores, running product in tensor memory),
+ * CTQ_KERNEL_TC_LARGE (tensor cores, persistent large-block kernel), or a
+ * negative CTQ_ERR_* code when the combination is not built.  Host only.
+ */
+#define CTQ_KERNEL_FP64_SHARED 0
+#define CTQ_KERNEL_FP64_LARGE 1
+#define CTQ_KERNEL_TC_SMALL 2
+#define CTQ_KERNEL_TC_LARGE 3
+int ctq_trace_kernel(const ctq_impurity* imp, int precision);
+
 void ctq_free_impurity(ctq_impurity* imp);
 
 /*

@@ -27,12 +27,16 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "ctq_autotune.js
 
 
 def engine(imp: "ctq.Impurity", precision: int) -> str:
-    """Which trace kernel a (impurity, precision) pair runs on."""
-    if precision == ctq.FP64:
-        return "fp64"
-    if imp.is_complex or imp.max_dim > 112:
-        return "big"
-    return "tc"
+    """Which trace kernel a (impurity, precision) pair runs on (the
+    library's own choice when the impurity has a device copy)."""
+    try:
+        k = ctq.trace_kernel(imp, precision)
+        return {ctq.KERNEL_FP64_SHARED: "fp64", ctq.KERNEL_FP64_LARGE: "fp64big",
+                ctq.KERNEL_TC_SMALL: "tc", ctq.KERNEL_TC_LARGE: "big"}[k]
+    except ctq.CtqError:  # host-only impurity: the same rule from the sector sizes
+        if precision == ctq.FP64:
+            return "fp64"
+        return "big" if (imp.is_complex or imp.max_dim > 112) else "tc"
 
 
 def candidates(imp: "ctq.Impurity", precision: int) -> List[Dict[str, int]]:
@@ -48,6 +52,9 @@ def candidates(imp: "ctq.Impurity", precision: int) -> List[Dict[str, int]]:
                 if threads * max(cap, 1) > 2048:
                     continue
                 out.append({"threads_per_cta": threads, "ctas_per_sm": cap})
+    elif eng == "fp64big":
+        for order in (1, 2):
+            out.append({"tile_order": order})
     elif eng == "tc":
         if precision != ctq.TF32X3:  # 3xTF32 holds all tensor memory: one CTA per SM
             out.append({"ctas_per_sm": 1})

@@ -480,6 +480,18 @@ int ctq_launches_per_eval(const ctq_impurity* imp, const ctq_eval_opts* opts) {
   return 3;  // plan, trace, combine
 }
 
+int ctq_trace_kernel(const ctq_impurity* imp, int precision) {
+  if (!imp) return CTQ_ERR_ARG;
+  if (imp->device < 0) return CTQ_ERR_ARG;
+  if (precision == CTQ_FP64) return imp->big64 ? CTQ_KERNEL_FP64_LARGE : CTQ_KERNEL_FP64_SHARED;
+  if (precision != CTQ_TF32 && precision != CTQ_TF32X3 && precision != CTQ_BF16X3) return CTQ_ERR_UNSUPPORTED;
+  if (imp->big) return CTQ_KERNEL_TC_LARGE;
+  const ctq::LaunchCfg& lc = precision == CTQ_TF32     ? imp->launch_tc1
+                             : precision == CTQ_BF16X3 ? imp->launch_tc2
+                                                       : imp->launch_tc3;
+  return lc.per_sm >= 1 ? CTQ_KERNEL_TC_SMALL : CTQ_ERR_UNSUPPORTED;
+}
+
 int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_eval_opts* opts,
                     const ctq_result* result, void* workspace, size_t workspace_bytes, void* stream) {
   if (!imp || !batch || !opts || !result) return fail(CTQ_ERR_ARG, "null argument");

@@ -88,6 +88,7 @@ def _load():
         "ctq_probe_fma_rate": (c_int, [c_int, c_int, c_int, POINTER(c_double)]),
         "ctq_tc_gemm_check": (c_int, [c_int, P, P, P, c_int, c_int, c_int]),
         "ctq_big_gemm_check": (c_int, [c_int, P, P, P, c_int, c_int, c_int]),
+        "ctq_trace_kernel": (c_int, [P, c_int]),
         "ctq_eval_traces_static": (c_int, [P, POINTER(BatchC), POINTER(EvalOptsC), POINTER(ResultC), P]),
     }
     for name, (res, args) in sig.items():
@@ -101,7 +102,8 @@ _lib = _load()
 EXPORTED = ("ctq_build_impurity", "ctq_load_impurity", "ctq_impurity_info", "ctq_get_sectors",
             "ctq_get_energies", "ctq_get_block", "ctq_workspace_size", "ctq_eval_traces",
             "ctq_launches_per_eval", "ctq_free_impurity", "ctq_strerror", "ctq_last_error_message",
-            "ctq_probe_fma_rate", "ctq_tc_gemm_check", "ctq_big_gemm_check", "ctq_eval_traces_static")
+            "ctq_probe_fma_rate", "ctq_tc_gemm_check", "ctq_big_gemm_check", "ctq_eval_traces_static",
+            "ctq_trace_kernel")
 
 # Size of the library-owned scratch used by eval_traces_static (ctq.h).
 STATIC_SCRATCH_BYTES = 32 << 20
@@ -271,6 +273,17 @@ def _opts(precision=FP64, lazy=False, segment=8, max_ops=0, timeout_ns=0, events
 def workspace_size(imp: Impurity, n_chains: int, precision=FP64, lazy=False, segment=8, max_ops=0) -> int:
     o = _opts(precision, lazy, segment, max_ops)
     return int(_lib.ctq_workspace_size(imp.handle, n_chains, ctypes.byref(o)))
+
+
+# ctq_trace_kernel results
+KERNEL_FP64_SHARED, KERNEL_FP64_LARGE, KERNEL_TC_SMALL, KERNEL_TC_LARGE = 0, 1, 2, 3
+
+
+def trace_kernel(imp: Impurity, precision: int) -> int:
+    """Which trace kernel evaluates this impurity at this precision (KERNEL_*)."""
+    k = int(_lib.ctq_trace_kernel(imp.handle, precision))
+    _check(min(k, 0), "ctq_trace_kernel")
+    return k
 
 
 def launches_per_eval(imp: Impurity, precision=FP64) -> int:
