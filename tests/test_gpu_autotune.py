@@ -34,6 +34,7 @@ def _same(a, b, rtol):
 def test_every_candidate_agrees_with_default(name, precision, n, tol):
     p, mk = w.WORKLOADS[name]
     imp = ctq.build_impurity(p(), device=0)
+    assert ctq.trace_kernel(imp, precision) == (ctq.KERNEL_FP64_SHARED if precision == ctq.FP64 else ctq.KERNEL_TC_SMALL)
     db = ctq.DeviceBatch(mk().subset(range(n)))
     ref = _run(imp, db, precision, {})
     cands = autotune.candidates(imp, precision)

@@ -46,6 +46,8 @@ def test_big64_parity_at_fp64_bar(name, small_models):
     rng = np.random.default_rng(51)
     b = w.random_batch(rng, m.n_flav, m.beta, 12, 1, 14, gen="g2")
     imp = parity.load_oracle_model(ctq, m)
+    assert ctq.trace_kernel(imp, ctq.FP64) == ctq.KERNEL_FP64_LARGE
+    assert ctq.trace_kernel(imp, ctq.BF16X3) == ctq.KERNEL_TC_LARGE
     res = run(imp, b)
     ref = parity.oracle_chain_results(m, b, range(b.n_chains))
     worst, n_ok = 0.0, 0
