@@ -18,6 +18,10 @@ reader can check each step against the paper by eye:
   the full-Fock-space brute-force trace with matrix exponentials, the
   lazy-trace norm bounds (Sec. 3.3.1, last paragraphs), the Metropolis
   decision (Eqs. MHratio, decide), and the atomic Green function.
+* ``oracle.observables`` -- the reduced-density-matrix estimator of one
+  configuration (Eq. ImpurityDensityMatrix: the projector |v><u| inserted at
+  every time, integrated analytically over each propagation interval), and
+  its brute-force counterpart by quadrature over the full Fock space.
 
 It shares no code with the GPU path (``paper_2010_08482_gb300``) and imports
 nothing from it.  Every function is pinned by a ``-m "not gpu"`` test against
