@@ -42,16 +42,17 @@ from .trace import walk
 
 
 def kernel_matrix(Ea: np.ndarray, Eb: np.ndarray, D: float) -> np.ndarray:
-    """K(Ea[u], Eb[v], D) for all u, v (energies relative to E_gs)."""
+    """K(Ea[u], Eb[v], D) for all u, v (energies relative to E_gs), written
+    as e^{-D min(a, b)} (1 - e^{-D |a - b|}) / |a - b| (the same closed form,
+    without the cancellation of the difference quotient for nearly equal
+    energies), D e^{-D a} for a == b."""
     a = np.asarray(Ea, dtype=np.float64)[:, None]
     b = np.asarray(Eb, dtype=np.float64)[None, :]
-    ea, eb = np.exp(-D * a), np.exp(-D * b)
-    diff = a - b
+    lo = np.minimum(a, b)
+    gap = np.abs(a - b)
     with np.errstate(divide="ignore", invalid="ignore"):
-        K = (eb - ea) / diff
-    same = diff == 0.0
-    K = np.where(same, D * ea * np.ones_like(eb), K)
-    return K
+        frac = np.where(gap > 0.0, -np.expm1(-D * gap) / gap, D)
+    return np.exp(-D * lo) * frac
 
 
 def rho_layout(model):

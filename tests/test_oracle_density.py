@@ -117,3 +117,12 @@ def test_kernel_matrix_closed_form():
         for v in range(3):
             ref = 0.5 * 2.5 * np.sum(wq * np.exp(-s * Ea[u] - (2.5 - s) * Ea[v]))
             assert abs(K[u, v] - ref) < 1e-13
+
+
+def test_kernel_matrix_nearly_degenerate_levels():
+    """Levels that differ by rounding (1e-15) give the degenerate limit
+    D e^{-D a} to full precision (no cancellation in the difference quotient)."""
+    a = 0.7
+    K = OB.kernel_matrix(np.array([a, a + 3.5e-15]), np.array([a, a + 3.5e-15]), 3.0)
+    ref = 3.0 * math.exp(-3.0 * a)
+    assert np.all(np.abs(K - ref) <= 1e-13 * ref)
