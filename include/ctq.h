@@ -296,6 +296,32 @@ int ctq_launches_per_eval(const ctq_impurity* imp, const ctq_eval_opts* opts);
 #define CTQ_KERNEL_TC_LARGE 3
 int ctq_trace_kernel(const ctq_impurity* imp, int precision);
 
+/*
+ * Reduced-density-matrix estimator (Sec. 2.3, Eq. ImpurityDensityMatrix):
+ * for every chain C,
+ *   rho^C_{uv} = beta^{-1} int_0^beta w_loc(C, |v><u|(tau)) / w_loc(C) dtau
+ * with u, v eigenstates of the same sector, the tau integral taken in closed
+ * form over every propagation interval.  float64, impurities whose blocks
+ * fit the shared-memory FP64 kernel (CTQ_ERR_UNSUPPORTED otherwise).
+ *
+ * ctq_density_size: doubles of one chain's estimator: the sector blocks
+ *   d_q x d_q, row-major (u row, v column), in sector order; complex
+ *   impurities store (re, im) pairs.
+ * ctq_density_workspace_size: workspace bytes for n_chains chains (the trace
+ *   evaluation's workspace plus per-CTA storage of the forward products).
+ * ctq_eval_density_matrices: evaluates the traces exactly as ctq_eval_traces
+ *   with CTQ_FP64 (result: log|w|, phase, status; bounds nullable) and then
+ *   writes rho (device, caller-owned, n_chains x ctq_density_size doubles).
+ *   Chains with w = 0, rejected or invalid chains get an all-zero estimator.
+ *   opts->precision must be CTQ_FP64 and opts->lazy 0.  Asynchronous on
+ *   `stream`.  Errors: as ctq_eval_traces.
+ */
+size_t ctq_density_size(const ctq_impurity* imp);
+size_t ctq_density_workspace_size(const ctq_impurity* imp, int n_chains, const ctq_eval_opts* opts);
+int ctq_eval_density_matrices(const ctq_impurity* imp, const ctq_batch* batch, const ctq_eval_opts* opts,
+                              const ctq_result* result, double* rho, void* workspace, size_t workspace_bytes,
+                              void* stream);
+
 void ctq_free_impurity(ctq_impurity* imp);
 
 /*

@@ -16,6 +16,8 @@ struct ctq_impurity {
   int num_sms = 0;
   ctq::DevModel dev{};
   ctq::LaunchCfg launch{};
+  const int64_t* rho_off = nullptr;  // density-matrix sector offsets (device)
+  int optin = 0;                     // opt-in shared memory per block
   // tensor-core path (real impurities with blocks <= 112): TF32 and 3xTF32
   ctq::TcParams tc1{}, tc2{}, tc3{};  // CTQ_TF32, CTQ_BF16X3, CTQ_TF32X3
   ctq::LaunchCfg launch_tc1{}, launch_tc2{}, launch_tc3{};
@@ -127,6 +129,23 @@ int upload_model(ctq_impurity* imp) {
       (st = upload_vec(imp, blk, &d.blk)) || (st = upload_vec(imp, lognorm, &d.log_norm)) ||
       (st = upload_vec(imp, lev_E, &d.lev_E)) || (st = upload_vec(imp, lev_off, &d.lev_off)) ||
       (st = upload_vec(imp, lev_idx, &d.lev_idx))) {
+    free_device(imp);
+    return fail(st, "device upload failed");
+  }
+  {
+    std::vector<int64_t> roff(h.n_sec);
+    int64_t acc = 0;
+    for (int q = 0; q < h.n_sec; ++q) {
+      roff[q] = acc;
+      acc += int64_t(h.dims[q]) * h.dims[q];
+    }
+    st = upload_vec(imp, roff, &imp->rho_off);
+  }
+  if (st == CTQ_OK &&
+      cudaDeviceGetAttribute(&imp->optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, imp->device) != cudaSuccess)
+    st = CTQ_ERR_CUDA;
+  if (st == CTQ_OK) st = ctq::prepare_rho(imp->optin);
+  if (st != CTQ_OK) {
     free_device(imp);
     return fail(st, "device upload failed");
   }
@@ -478,6 +497,55 @@ size_t ctq_workspace_size(const ctq_impurity* imp, int n_chains, const ctq_eval_
 int ctq_launches_per_eval(const ctq_impurity* imp, const ctq_eval_opts* opts) {
   if (!imp || !opts) return 0;
   return 3;  // plan, trace, combine
+}
+
+size_t ctq_density_size(const ctq_impurity* imp) {
+  if (!imp) return 0;
+  return ctq::rho_elems(imp->host) * (imp->host.is_complex ? 2 : 1);
+}
+
+size_t ctq_density_workspace_size(const ctq_impurity* imp, int n_chains, const ctq_eval_opts* opts) {
+  if (!imp || !opts || n_chains < 0) return 0;
+  const size_t base = ctq::workspace_layout(n_chains, imp->host.n_sec, n_seg_of(opts), nullptr, nullptr);
+  const int grid = ctq::rho_grid(imp->dev, imp->num_sms, std::max(0, opts->max_ops));
+  return ((base + 255) & ~size_t(255)) + ctq::rho_scratch_bytes(imp->host, std::max(0, opts->max_ops), grid);
+}
+
+int ctq_eval_density_matrices(const ctq_impurity* imp, const ctq_batch* batch, const ctq_eval_opts* opts,
+                              const ctq_result* result, double* rho, void* workspace, size_t workspace_bytes,
+                              void* stream) {
+  if (!imp || !batch || !opts || !result || !rho) return fail(CTQ_ERR_ARG, "null argument");
+  if (opts->precision != CTQ_FP64 || opts->lazy) return fail(CTQ_ERR_ARG, "the estimator runs in CTQ_FP64 without lazy rejects");
+  if (imp->device < 0) return fail(CTQ_ERR_ARG, "impurity has no device copy");
+  if (imp->big64) return fail(CTQ_ERR_UNSUPPORTED, "blocks too large for the density-matrix kernel");
+  if (batch->n_chains <= 0) return batch->n_chains == 0 ? CTQ_OK : fail(CTQ_ERR_ARG, "n_chains < 0");
+  const size_t need = ctq_density_workspace_size(imp, batch->n_chains, opts);
+  if (workspace_bytes < need) return fail(CTQ_ERR_WORKSPACE, "workspace smaller than ctq_density_workspace_size()");
+  const int n_seg = n_seg_of(opts);
+  const size_t base = ctq::workspace_layout(batch->n_chains, imp->host.n_sec, n_seg, nullptr, nullptr);
+  int st = ctq_eval_traces(imp, batch, opts, result, workspace, base, stream);
+  if (st != CTQ_OK) return st;
+  DeviceGuard g(imp->device);
+  if (!g.ok()) return fail(CTQ_ERR_CUDA, "cudaSetDevice failed");
+  ctq::Work W;
+  ctq::workspace_layout(batch->n_chains, imp->host.n_sec, n_seg, workspace, &W);
+  ctq::BatchView B{batch->n_chains, batch->beta, batch->offsets, batch->tau, batch->op, batch->log_threshold};
+  ctq::EvalCfg cfg;
+  cfg.lazy = 0;
+  cfg.has_thr = 0;
+  cfg.S = opts->segment;
+  cfg.n_seg_max = n_seg;
+  cfg.max_ops = opts->max_ops;
+  ctq::RhoParams P;
+  P.rho = rho;
+  P.rho_elems = ctq_density_size(imp);
+  P.rho_off = imp->rho_off;
+  P.scratch = static_cast<char*>(workspace) + ((base + 255) & ~size_t(255));
+  P.scratch_elems = size_t(std::max(opts->max_ops, 1) + 1) * imp->host.max_dim * imp->host.max_dim;
+  st = ctq::launch_rho(imp->dev, imp->num_sms, imp->optin, B, cfg, W, *result, P,
+                       P.rho_elems * size_t(batch->n_chains), stream);
+  if (st != CTQ_OK) return fail(st, st == CTQ_ERR_CUDA ? cudaGetErrorString(cudaGetLastError()) : "launch failed");
+  return CTQ_OK;
 }
 
 int ctq_trace_kernel(const ctq_impurity* imp, int precision) {

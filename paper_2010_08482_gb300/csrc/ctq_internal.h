@@ -189,6 +189,21 @@ struct Big64Params {
   int order = 0;                    // tile order (ctq_eval_opts.tile_order)
 };
 
+// Density-matrix estimator (density.cu).
+struct RhoParams {
+  double* rho = nullptr;            // [C x rho_elems] per-chain estimator, sector blocks
+  size_t rho_elems = 0;             // doubles per chain (complex: two per element)
+  const int64_t* rho_off = nullptr; // [n_sec] element offset of each sector block (sum of d^2 before it)
+  void* scratch = nullptr;          // per-CTA storage of the forward products
+  size_t scratch_elems = 0;         // elements (real or complex) per CTA
+};
+size_t rho_elems(const HostModel& h);
+size_t rho_scratch_bytes(const HostModel& h, int max_ops, int grid);
+int rho_grid(const DevModel& M, int num_sms, int max_ops);
+int prepare_rho(int optin);
+int launch_rho(const DevModel& M, int num_sms, int optin, const BatchView& B, const EvalCfg& cfg, const Work& W,
+               const ctq_result& R, RhoParams P, size_t rho_total_doubles, void* stream);
+
 size_t big64_block_elems(int dn, int dk);
 int format_big64_blocks(const HostModel& h, const double* d_blk, double* out, const std::vector<int64_t>& off);
 size_t big64_scratch_bytes(const HostModel& h, int max_ops, int grid);

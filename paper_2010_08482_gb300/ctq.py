@@ -89,6 +89,10 @@ def _load():
         "ctq_tc_gemm_check": (c_int, [c_int, P, P, P, c_int, c_int, c_int]),
         "ctq_big_gemm_check": (c_int, [c_int, P, P, P, c_int, c_int, c_int]),
         "ctq_trace_kernel": (c_int, [P, c_int]),
+        "ctq_density_size": (c_size_t, [P]),
+        "ctq_density_workspace_size": (c_size_t, [P, c_int, POINTER(EvalOptsC)]),
+        "ctq_eval_density_matrices": (c_int, [P, POINTER(BatchC), POINTER(EvalOptsC), POINTER(ResultC), P, P,
+                                              c_size_t, P]),
         "ctq_eval_traces_static": (c_int, [P, POINTER(BatchC), POINTER(EvalOptsC), POINTER(ResultC), P]),
     }
     for name, (res, args) in sig.items():
@@ -103,7 +107,7 @@ EXPORTED = ("ctq_build_impurity", "ctq_load_impurity", "ctq_impurity_info", "ctq
             "ctq_get_energies", "ctq_get_block", "ctq_workspace_size", "ctq_eval_traces",
             "ctq_launches_per_eval", "ctq_free_impurity", "ctq_strerror", "ctq_last_error_message",
             "ctq_probe_fma_rate", "ctq_tc_gemm_check", "ctq_big_gemm_check", "ctq_eval_traces_static",
-            "ctq_trace_kernel")
+            "ctq_trace_kernel", "ctq_density_size", "ctq_density_workspace_size", "ctq_eval_density_matrices")
 
 # Size of the library-owned scratch used by eval_traces_static (ctq.h).
 STATIC_SCRATCH_BYTES = 32 << 20
@@ -404,3 +408,53 @@ def log_value(log_abs: float, phase) -> complex:
     if log_abs == -math.inf:
         return 0j
     return complex(phase[0], phase[1]) * math.exp(log_abs)
+
+
+class DensityEvaluator:
+    """The reduced-density-matrix estimator of every chain (ctq.h,
+    ctq_eval_density_matrices): pre-allocated workspace, traces and per-chain
+    estimators; evaluates on the current torch stream."""
+
+    def __init__(self, imp: Impurity, n_chains: int, max_ops: int, device="cuda"):
+        import torch
+        self.imp = imp
+        self.n_chains = n_chains
+        self.max_ops = max_ops
+        self.size = int(_lib.ctq_density_size(imp.handle))
+        o = _opts(FP64, False, 8, max_ops)
+        self.ws_bytes = int(_lib.ctq_density_workspace_size(imp.handle, n_chains, ctypes.byref(o)))
+        self._ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=device)
+        self.ws_ptr = (self._ws.data_ptr() + 255) // 256 * 256
+        self.log_abs = torch.empty(n_chains, dtype=torch.float64, device=device)
+        self.phase = torch.empty(2 * n_chains, dtype=torch.float64, device=device)
+        self.status = torch.empty(n_chains, dtype=torch.int32, device=device)
+        self.rho = torch.empty(n_chains * self.size, dtype=torch.float64, device=device)
+
+    def __call__(self, db: "DeviceBatch", stream=None):
+        import torch
+        if db.n_chains > self.n_chains or db.max_ops > self.max_ops:
+            raise ValueError("batch larger than the evaluator was sized for")
+        s = torch.cuda.current_stream() if stream is None else stream
+        b = BatchC()
+        b.n_chains, b.beta = db.n_chains, db.beta
+        b.offsets, b.tau, b.op, b.log_threshold = db.offsets.data_ptr(), db.tau.data_ptr(), db.op.data_ptr(), None
+        r = ResultC()
+        r.log_abs, r.phase, r.status, r.bounds = (self.log_abs.data_ptr(), self.phase.data_ptr(),
+                                                  self.status.data_ptr(), None)
+        o = _opts(FP64, False, 8, self.max_ops)
+        _check(_lib.ctq_eval_density_matrices(self.imp.handle, ctypes.byref(b), ctypes.byref(o), ctypes.byref(r),
+                                              self.rho.data_ptr(), self.ws_ptr, self.ws_bytes, s.cuda_stream),
+               "ctq_eval_density_matrices")
+
+    def blocks(self, chain: int):
+        """The estimator of one chain as {sector q: d_q x d_q matrix}."""
+        dims = self.imp.sectors()[0]
+        flat = self.rho[chain * self.size:(chain + 1) * self.size].cpu().numpy()
+        if self.imp.is_complex:
+            flat = flat[0::2] + 1j * flat[1::2]
+        out, o = {}, 0
+        for q, d in enumerate(dims):
+            d = int(d)
+            out[q] = flat[o:o + d * d].reshape(d, d)
+            o += d * d
+        return out
