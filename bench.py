@@ -98,6 +98,88 @@ def algorithmic_flops(imp, batch):
     return total * (4.0 if imp.is_complex else 1.0), n_items
 
 
+def density_flops(imp, batch):
+    """Real FP64-equivalent flops of the density-matrix estimator over the
+    surviving strings (complex x4): the forward products A_i (the first
+    operator only scales), the backward products B_i (the last only scales)
+    and the interval products A_i B_i for 1 <= i <= n-1 (G_0 = B_0, G_n = A_n)."""
+    dims, _, _, s = imp.sectors()
+    total = 0.0
+    for c in range(batch.n_chains):
+        a, b = batch.offsets[c], batch.offsets[c + 1]
+        ops = batch.op[a:b]
+        n = len(ops)
+        for q0 in range(len(dims)):
+            path, q = [q0], q0
+            for al in ops:
+                q = int(s[al, q])
+                if q < 0:
+                    break
+                path.append(q)
+            if q < 0 or q != q0:
+                continue
+            d0 = float(dims[q0])
+            d = [float(dims[x]) for x in path]
+            if n == 0:
+                continue
+            total += d[1] * d0 + sum(2.0 * d[i] * d[i - 1] * d0 for i in range(2, n + 1))
+            total += d0 * d[n - 1] + sum(2.0 * d0 * d[i + 1] * d[i] for i in range(0, n - 1))
+            total += sum(2.0 * d[i] * d[i] * d0 for i in range(1, n))
+    return total * (4.0 if imp.is_complex else 1.0)
+
+
+def run_density(args, world, rank, local):
+    """The reduced-density-matrix estimator (ctq_eval_density_matrices) on a
+    workload: trace evaluation plus the estimator of every chain, float64."""
+    import torch
+    from paper_2010_08482_gb300 import ctq
+    from paper_2010_08482_gb300 import workloads as w
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mf, bf = w.WORKLOADS[args.workload]
+    batch = bf(rank=rank)
+    if args.chains:
+        batch = batch.subset(range(min(args.chains, batch.n_chains)))
+    imp = ctq.build_impurity(mf(), device=local)
+    db = ctq.DeviceBatch(batch, device=dev)
+    ev = ctq.DensityEvaluator(imp, batch.n_chains, db.max_ops, device=dev)
+    flops = density_flops(imp, batch) + algorithmic_flops(imp, batch)[0]
+    fp64_peak = ctq.probe_fma_rate(local, 0)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        ev(db)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ev(db)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clocks.stop()
+    mean = statistics.mean(ms)
+    achieved = flops / (mean * 1e-3) / 1e12
+    line = {"metric": "density-matrix estimator evals/s (trace + rho per chain), FP64, 1xGB300",
+            "value": batch.n_chains / (mean * 1e-3), "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": mean, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT[args.workload], "n_chains": batch.n_chains,
+                       "estimator": "reduced density matrix (Eq. ImpurityDensityMatrix)",
+                       "l2": "flushed (256 MiB write) between steps"},
+            "tflops": achieved, "algorithmic_flops_per_step": flops,
+            "roofline": {"kernel": "k_trace<fp64> + k_rho", "bound": "alu", "achieved": achieved,
+                         "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": achieved / (fp64_peak / 1e12),
+                         "peak_source": "measured FP64 FMA rate (ctq_probe_fma_rate, this run)", "traffic": None},
+            "gpu_launches": args.steps * 4, "clocks": clocks.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples during the timed region."""
 
@@ -344,6 +426,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--chains", type=int, default=0, help="evaluate only the first N chains of the workload")
     ap.add_argument("--no-autotune", action="store_true", help="library-default launch configuration")
+    ap.add_argument("--estimator", default="trace", choices=["trace", "rho"],
+                    help="trace: local traces (default); rho: traces plus the reduced-density-matrix estimator")
     ap.add_argument("--autotune-cache", default=None, help="JSON cache of tuned launch configurations")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -354,6 +438,9 @@ def main():
 
     if args.workload == "mixed":
         run_mixed(args, world, rank, local)
+        return
+    if args.estimator == "rho":
+        run_density(args, world, rank, local)
         return
     import torch
     from paper_2010_08482_gb300 import ctq

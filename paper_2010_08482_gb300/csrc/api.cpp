@@ -507,7 +507,7 @@ size_t ctq_density_size(const ctq_impurity* imp) {
 size_t ctq_density_workspace_size(const ctq_impurity* imp, int n_chains, const ctq_eval_opts* opts) {
   if (!imp || !opts || n_chains < 0) return 0;
   const size_t base = ctq::workspace_layout(n_chains, imp->host.n_sec, n_seg_of(opts), nullptr, nullptr);
-  const int grid = ctq::rho_grid(imp->dev, imp->num_sms, std::max(0, opts->max_ops));
+  const int grid = ctq::rho_grid(imp->dev, imp->num_sms, std::max(0, opts->max_ops), ctq_density_size(imp));
   return ((base + 255) & ~size_t(255)) + ctq::rho_scratch_bytes(imp->host, std::max(0, opts->max_ops), grid);
 }
 

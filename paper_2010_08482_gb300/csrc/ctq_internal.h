@@ -196,10 +196,11 @@ struct RhoParams {
   const int64_t* rho_off = nullptr; // [n_sec] element offset of each sector block (sum of d^2 before it)
   void* scratch = nullptr;          // per-CTA storage of the forward products
   size_t scratch_elems = 0;         // elements (real or complex) per CTA
+  int local_acc = 0;                // estimator summed in shared memory per string
 };
 size_t rho_elems(const HostModel& h);
 size_t rho_scratch_bytes(const HostModel& h, int max_ops, int grid);
-int rho_grid(const DevModel& M, int num_sms, int max_ops);
+int rho_grid(const DevModel& M, int num_sms, int max_ops, size_t rho_doubles);
 int prepare_rho(int optin);
 int launch_rho(const DevModel& M, int num_sms, int optin, const BatchView& B, const EvalCfg& cfg, const Work& W,
                const ctq_result& R, RhoParams P, size_t rho_total_doubles, void* stream);

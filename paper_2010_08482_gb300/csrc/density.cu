@@ -87,11 +87,15 @@ __device__ int block_rescale(T* X, int count, int* redi, bool* dead) {
 }
 
 // The interval integral without its e^{-D E_min(q)} factor: energies a, b
-// are relative to the sector's lowest level.
-__device__ __forceinline__ double kernel_rel(double a, double b, double D) {
+// are relative to the sector's lowest level, ea = e^{-D a}, eb = e^{-D b}.
+// Well separated levels use the difference quotient of the exponentials
+// (relative error below 3 u once D |a - b| > 1/2); close levels the form
+// e^{-D min(a, b)} (1 - e^{-D |a - b|}) / |a - b| with expm1.
+__device__ __forceinline__ double kernel_rel(double a, double b, double ea, double eb, double D) {
   const double gap = fabs(a - b);
-  const double frac = gap > 0.0 ? -expm1(-D * gap) / gap : D;
-  return exp(-D * fmin(a, b)) * frac;
+  if (gap == 0.0) return D * ea;
+  if (D * gap > 0.5) return (a > b) ? (eb - ea) / gap : (ea - eb) / gap;
+  return ((a < b) ? ea : eb) * (-expm1(-D * gap) / gap);
 }
 
 template <bool CPLX>
@@ -105,6 +109,10 @@ __global__ void __launch_bounds__(256) k_rho(DevModel M, BatchView B, EvalCfg cf
   short* path = reinterpret_cast<short*>(Xn + size_t(D) * D);  // [MO + 1]
   short* opsm = path + (MO + 1);                               // [MO], then one short of padding
   int* eA = reinterpret_cast<int*>(opsm + MO + 1);             // [MO + 1] exponents of the stored A_i
+  double* ex = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(eA + MO + 1) + 7) & ~uintptr_t(7));  // [D]
+  // small estimators: the string's contributions are summed in shared memory
+  // and added to the chain's estimator once
+  double* acc_s = P.local_acc ? ex + D : nullptr;  // [rho_elems]
   __shared__ int redi[32];
   __shared__ int s_item;
   __shared__ double s_L;
@@ -134,6 +142,11 @@ __global__ void __launch_bounds__(256) k_rho(DevModel M, BatchView B, EvalCfg cf
     const double logw_rel = lw + B.beta * M.E_ref;
     const double phr = R.phase[2 * c], phi = CPLX ? R.phase[2 * c + 1] : 0.0;
     double* out = P.rho + size_t(c) * P.rho_elems;
+    double* dst = acc_s ? acc_s : out;
+    if (acc_s) {
+      for (size_t i = tid; i < P.rho_elems; i += nt) acc_s[i] = 0.0;
+      __syncthreads();
+    }
 
     // ---- the string: operator codes, sectors, total log scale
     for (int i = tid; i < n; i += nt) opsm[i] = short(B.op[a0 + i]);
@@ -162,10 +175,13 @@ __global__ void __launch_bounds__(256) k_rho(DevModel M, BatchView B, EvalCfg cf
       const int d = M.dims[q];
       const double* Eq = M.E_rel + M.E_off[q];
       const double f = exp(base + double(e) * LN2) / B.beta;
-      double* blk = out + (CPLX ? 2 : 1) * P.rho_off[q];
+      double* blk = dst + (CPLX ? 2 : 1) * P.rho_off[q];
+      __syncthreads();
+      for (int u = tid; u < d; u += nt) ex[u] = exp(-Dlen * Eq[u]);
+      __syncthreads();
       for (int idx = tid; idx < d * d; idx += nt) {
         const int u = idx / d, v = idx - u * d;
-        const double k = kernel_rel(Eq[u], Eq[v], Dlen) * f;
+        const double k = kernel_rel(Eq[u], Eq[v], ex[u], ex[v], Dlen) * f;
         if constexpr (CPLX) {
           // (g / w) with w = |w| (phr + i phi): multiply by conj(phase)
           const double gr = Gm[idx].x, gi = Gm[idx].y;
@@ -184,6 +200,11 @@ __global__ void __launch_bounds__(256) k_rho(DevModel M, BatchView B, EvalCfg cf
       }
       __syncthreads();
       accumulate(X, q0, B.beta, 0);
+      if (acc_s) {
+        __syncthreads();
+        for (size_t i = tid; i < P.rho_elems; i += nt)
+          if (acc_s[i] != 0.0) atomicAdd(out + i, acc_s[i]);
+      }
       continue;
     }
 
@@ -193,10 +214,9 @@ __global__ void __launch_bounds__(256) k_rho(DevModel M, BatchView B, EvalCfg cf
     bool dead = false;
     {
       const double* E0 = M.E_rel + M.E_off[q0];
-      for (int idx = tid; idx < d0 * d0; idx += nt) {
-        const int r = idx / d0, j = idx - r * d0;
-        X[idx] = (r == j) ? num_scale(num_one(T()), exp(-t_first * E0[j])) : num_zero(T());
-      }
+      for (int idx = tid; idx < d0 * d0; idx += nt) X[idx] = num_zero(T());
+      __syncthreads();
+      for (int j = tid; j < d0; j += nt) X[j * d0 + j] = num_scale(num_one(T()), exp(-t_first * E0[j]));
     }
     __syncthreads();
     int eacc = 0;
@@ -223,10 +243,9 @@ __global__ void __launch_bounds__(256) k_rho(DevModel M, BatchView B, EvalCfg cf
       if (i < n) {
         const double dt = B.tau[a0 + i] - B.tau[a0 + i - 1];
         const double* Eb = M.E_rel + M.E_off[qb];
-        for (int idx = tid; idx < db * d0; idx += nt) {
-          const int m = idx / d0;
-          X[idx] = num_scale(Xn[idx], exp(-dt * Eb[m]));
-        }
+        for (int m = tid; m < db; m += nt) ex[m] = exp(-dt * Eb[m]);
+        __syncthreads();
+        for (int idx = tid; idx < db * d0; idx += nt) X[idx] = num_scale(Xn[idx], ex[idx / d0]);
       }
       __syncthreads();
       da = db;
@@ -239,10 +258,9 @@ __global__ void __launch_bounds__(256) k_rho(DevModel M, BatchView B, EvalCfg cf
     // ---- backward: Y = P_{beta - tau_n}(q0), then B_i = Y F_{i+1}, G_i = A_i B_i
     {
       const double* E0 = M.E_rel + M.E_off[q0];
-      for (int idx = tid; idx < d0 * d0; idx += nt) {
-        const int r = idx / d0, j = idx - r * d0;
-        X[idx] = (r == j) ? num_scale(num_one(T()), exp(-t_last * E0[j])) : num_zero(T());
-      }
+      for (int idx = tid; idx < d0 * d0; idx += nt) X[idx] = num_zero(T());
+      __syncthreads();
+      for (int j = tid; j < d0; j += nt) X[j * d0 + j] = num_scale(num_one(T()), exp(-t_last * E0[j]));
     }
     __syncthreads();
     int ebacc = 0;
@@ -282,23 +300,31 @@ __global__ void __launch_bounds__(256) k_rho(DevModel M, BatchView B, EvalCfg cf
       // Y = B_i P_{Delta} for the next (earlier) operator
       if (i > 0) {
         const double* Eq = M.E_rel + M.E_off[qa];
-        for (int idx = tid; idx < d0 * dq; idx += nt) {
-          const int m = idx % dq;
-          X[idx] = num_scale(Xn[idx], exp(-Dlen * Eq[m]));
-        }
+        for (int m = tid; m < dq; m += nt) ex[m] = exp(-Dlen * Eq[m]);
+        __syncthreads();
+        for (int idx = tid; idx < d0 * dq; idx += nt) X[idx] = num_scale(Xn[idx], ex[idx % dq]);
       }
       __syncthreads();
       dy = dq;
+    }
+    if (acc_s) {  // add this string's contributions to the chain's estimator
+      __syncthreads();
+      for (size_t i = tid; i < P.rho_elems; i += nt)
+        if (acc_s[i] != 0.0) atomicAdd(out + i, acc_s[i]);
     }
   }
 }
 
 }  // namespace
 
-static size_t rho_smem(int max_dim, bool cplx, int max_ops) {
+constexpr size_t RHO_LOCAL_MAX = 16384;  // bytes of an estimator summed in shared memory
+
+static size_t rho_smem(int max_dim, bool cplx, int max_ops, size_t rho_doubles) {
   const size_t el = cplx ? 16 : 8;
   const size_t mo = size_t(std::max(max_ops, 1));
-  size_t b = 2 * size_t(max_dim) * max_dim * el + (2 * mo + 2) * 2 + (mo + 1) * 4 + 16;
+  // products, path + operator codes + padding, exponents, then (8-byte aligned) e^{-D E}
+  size_t b = 2 * size_t(max_dim) * max_dim * el + (2 * mo + 2) * 2 + (mo + 1) * 4 + 8 + size_t(max_dim) * 8 + 16;
+  if (rho_doubles * 8 <= RHO_LOCAL_MAX) b += rho_doubles * 8;
   return (b + 15) & ~size_t(15);
 }
 
@@ -313,8 +339,8 @@ size_t rho_scratch_bytes(const HostModel& h, int max_ops, int grid) {
   return size_t(grid) * size_t(std::max(max_ops, 1) + 1) * h.max_dim * h.max_dim * el + 256;
 }
 
-int rho_grid(const DevModel& M, int num_sms, int max_ops) {
-  const size_t smem = rho_smem(M.max_dim, M.is_complex != 0, max_ops);
+int rho_grid(const DevModel& M, int num_sms, int max_ops, size_t rho_doubles) {
+  const size_t smem = rho_smem(M.max_dim, M.is_complex != 0, max_ops, rho_doubles);
   const int per_sm = std::max(1, std::min(16, int((200 * 1024) / (smem + 1024))));
   return num_sms * per_sm;
 }
@@ -332,10 +358,11 @@ int prepare_rho(int optin) {
 int launch_rho(const DevModel& M, int num_sms, int optin, const BatchView& B, const EvalCfg& cfg, const Work& W,
                const ctq_result& R, RhoParams P, size_t rho_total_doubles, void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const size_t smem = rho_smem(M.max_dim, M.is_complex != 0, cfg.max_ops);
+  P.local_acc = P.rho_elems * 8 <= RHO_LOCAL_MAX ? 1 : 0;
+  const size_t smem = rho_smem(M.max_dim, M.is_complex != 0, cfg.max_ops, P.rho_elems);
   if (smem + 1024 > size_t(optin)) return CTQ_ERR_UNSUPPORTED;
   const int threads = M.max_dim <= 12 ? 32 : (M.max_dim <= 32 ? 128 : 256);
-  const int grid = rho_grid(M, num_sms, cfg.max_ops);
+  const int grid = rho_grid(M, num_sms, cfg.max_ops, P.rho_elems);
   if (cudaMemsetAsync(P.rho, 0, rho_total_doubles * sizeof(double), st) != cudaSuccess) return CTQ_ERR_CUDA;
   // the item counter of this pass (the trace pass used counters[1])
   if (cudaMemsetAsync(W.counters + 3, 0, sizeof(int), st) != cudaSuccess) return CTQ_ERR_CUDA;
