@@ -37,8 +37,6 @@ struct Num<true> {
   using T = double2;
 };
 
-__device__ __forceinline__ double num_abs2(double v) { return v * v; }
-__device__ __forceinline__ double num_abs2(double2 v) { return v.x * v.x + v.y * v.y; }
 __device__ __forceinline__ int num_key(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
 __device__ __forceinline__ int num_key(double2 v) { return max(num_key(v.x), num_key(v.y)); }
 __device__ __forceinline__ double num_zero(double) { return 0.0; }

@@ -16,10 +16,15 @@
 //              exponents) stays in float64, relative to e^{-beta E_gs} (the
 //              propagation times sum to beta) and summed with compensation,
 //              so that log|w| ~ 10^3 loses no accuracy before the final
-//              -beta E_gs is added.  Every `segment` operators the refined bound
+//              -beta E_gs is added (one warp, lanes over chunks of
+//              operators).  Every `segment` operators the refined bound
 //                ub = sqrt(r) ||Y||_F prod_{rest} ||F||_2 e^{-dtau E_min}
 //              is recorded and, with lazy evaluation, the chain's live bound
-//              sum is compared with its threshold (stop early if below).
+//              sum is compared with its threshold (stop early if below);
+//              without lazy evaluation the logarithms of all segments are
+//              taken at the end, lanes over segments.  For short strings the
+//              propagators of the whole string are computed in one dense
+//              pass, once per distinct energy level of each visited sector.
 #include <algorithm>
 
 #include "device_common.cuh"
@@ -76,12 +81,6 @@ __device__ __forceinline__ int block_max_int(int v, int* redi) {
   for (int i = 1; i < nw; ++i) v = max(v, redi[i]);
   return v;
 }
-
-// Shared-memory layout of k_trace (dynamic part), see trace_smem().
-struct TraceSmem {
-  size_t y_bytes;  // one Y buffer
-  size_t pall;     // float64 propagators of the whole chain (PRE only)
-};
 
 // PRE: every propagator value of the chain is computed in one dense pass at
 // the start of an item (lanes over all (operator, state) pairs), which keeps
