@@ -353,8 +353,6 @@ def run_mixed(args, world, rank, local):
         idx = np.nonzero(batch.model == mi)[0]
         if idx.size == 0:
             continue
-        if prec == ctq.FP64 and p.name == "f7":
-            continue  # f-shell chains take seconds each in float64: not part of the mixed FP64 run
         sub = batch.subset(idx)
         sub.beta = p.beta  # the mixed batch draws each chain's times in [0, beta) of its own model
         thr = np.where(coin[idx] == 1, np.inf, -np.inf)
