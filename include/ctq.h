@@ -200,9 +200,11 @@ typedef struct {
  *     small-block trace kernels;
  *   stages: large-block kernel pipeline stages, >= 2 and as many as fit in
  *     shared memory (CTQ_ERR_UNSUPPORTED otherwise);
- *   tile_order: large-block kernel tile order, 0 column-major (a B tile is
- *     shared by consecutive CTAs), 1 row-major, 2 groups of 8 column tiles
- *     row by row.
+ *   tile_order: large-block kernel tile order, 0 the library default
+ *     (row-major for the tensor-core kernel, whose products overlap row tile
+ *     by row tile; column-major for the float64 one), 1 column-major (a B
+ *     tile is shared by consecutive CTAs), 2 row-major, 3 groups of 8 column
+ *     tiles row by row.
  * Out-of-range values: CTQ_ERR_ARG.
  * When a bounded wait expires, every chain of the call gets
  * CTQ_CHAIN_ERR_TIMEOUT (log_abs NaN); the context stays usable.

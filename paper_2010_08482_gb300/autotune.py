@@ -53,7 +53,7 @@ def candidates(imp: "ctq.Impurity", precision: int) -> List[Dict[str, int]]:
                     continue
                 out.append({"threads_per_cta": threads, "ctas_per_sm": cap})
     elif eng == "fp64big":
-        for order in (1, 2):
+        for order in (2, 3):  # row-major, groups of 8 column tiles (the default is column-major)
             out.append({"tile_order": order})
     elif eng == "tc":
         if precision != ctq.TF32X3:  # 3xTF32 holds all tensor memory: one CTA per SM
@@ -61,7 +61,7 @@ def candidates(imp: "ctq.Impurity", precision: int) -> List[Dict[str, int]]:
     else:
         stages = (2, 3) if precision != ctq.TF32 else (2, 3, 4)  # deeper pipelines are refused if they do not fit
         for st in stages:
-            for order in (0, 1, 2):
+            for order in (0, 1, 3):  # default (row-major), column-major, groups of 8 column tiles
                 out.append({"stages": st, "tile_order": order})
     # drop duplicates of the default, keep order
     seen, uniq = set(), []

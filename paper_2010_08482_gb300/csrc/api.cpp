@@ -564,7 +564,7 @@ int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_e
                     const ctq_result* result, void* workspace, size_t workspace_bytes, void* stream) {
   if (!imp || !batch || !opts || !result) return fail(CTQ_ERR_ARG, "null argument");
   if (opts->threads_per_cta < 0 || opts->threads_per_cta > 256 || opts->threads_per_cta % 32 != 0 ||
-      opts->ctas_per_sm < 0 || opts->stages < 0 || opts->stages == 1 || opts->tile_order < 0 || opts->tile_order > 2)
+      opts->ctas_per_sm < 0 || opts->stages < 0 || opts->stages == 1 || opts->tile_order < 0 || opts->tile_order > 3)
     return fail(CTQ_ERR_ARG, "launch tuning out of range");
   if (imp->device < 0) return fail(CTQ_ERR_ARG, "impurity has no device copy");
   if (batch->n_chains < 0) return fail(CTQ_ERR_ARG, "n_chains < 0");

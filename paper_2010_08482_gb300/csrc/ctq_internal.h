@@ -168,10 +168,7 @@ struct BigParams {
   float* zbuf = nullptr;          // scratch: 2 x (hi, lo) Z buffers
   size_t zfloats = 0;             // floats of one Z plane
   unsigned* bar = nullptr;        // grid barrier: count, generation
-  int* ekey = nullptr;            // [max_ops + 2] max exponent field per operator
-  double* fr = nullptr;           // [max_ops + 2] ||Z||^2 per operator
-  double* part = nullptr;         // [2 * grid] final-trace partial sums
-  int* abort_flag = nullptr;
+  unsigned char* state = nullptr; // two copies of the per-string row-tile state of the product schedule
 };
 
 // Per-impurity parameters and scratch of the float64 large-block path (trace_big64.cu).

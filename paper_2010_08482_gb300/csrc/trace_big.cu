@@ -130,26 +130,99 @@ constexpr int MAX_NST = 12;
 // ~6000.
 constexpr int NBANK = 512 / BN;  // accumulator banks filling the 512 tensor-memory columns
 constexpr int GRP = 4;            // K chunks accumulated in a bank before it is drained
-constexpr int PVEC = 3072;    // largest sector dimension of this path
+constexpr int PVEC = 3072;        // largest sector dimension of this path
+constexpr int RT_MAX = PVEC / BM; // row tiles of the largest running product
+constexpr int DR = 4;             // tile descriptors the producer may announce ahead
+
+// One tile of the product schedule: stage s (Z_{s+1} = Z_s F_{s+1}^T P_{s+1}),
+// row tile mt, column tile nt; s < 0 ends the products of the string.
+struct Unit {
+  int s, mt, nt, skip;
+};
 
 struct BigShared {
   uint64_t full[MAX_NST];
   uint64_t empty[MAX_NST];
-  uint64_t bank_full[2];  // MMAs of a group have completed in the bank
-  uint64_t bank_free[2];  // the drain warps have read the bank
+  uint64_t bank_full[2];   // MMAs of a group have completed in the bank
+  uint64_t bank_free[2];   // the drain warps have read the bank
+  uint64_t unit_full[DR];  // the producer has announced the tile in slot i
+  uint64_t unit_empty[DR]; // the MMA issuer and the drain warps have read it
   uint64_t never;  // never arrived on: CTQ_DEBUG_STALL_WAIT waits on it
+  Unit unit[DR];
   uint32_t issued;    // chunks issued by the producer (sequence numbers [0, issued))
   uint32_t consumed;  // chunks whose data the MMA issuer has waited for
   uint32_t tmem_base;
   int fail;
-  float red[8];
   double redd[64];
 };
+
+// Per-string state of the product schedule in global memory, two copies that
+// alternate between consecutive strings.  Entry s * RT_MAX + r belongs to row
+// tile r of the stored product Z_s:
+//   ekey   max float exponent field over the row tile,
+//   cnt    reports of drain warps (N_DRAIN per column tile) for the row tile,
+//   ready  the row tile is complete (set once, by the tile that completes it),
+//   ecum   sum over t <= s of the power-of-two exponents e_r(t) taken out of
+//          row tile r (every row tile carries its own rescale),
+//   fr     squared Frobenius norm of the stored row tile;
+// rows[s]: row tiles of Z_s complete; part[2 r]: partial trace of row tile r
+// (re, im); abort[0]: the string was rejected early.
+struct RowState {
+  int *ekey, *cnt, *ready, *ecum, *rows, *abort;
+  double *fr, *part;
+};
+
+__host__ __device__ __forceinline__ size_t row_state_int_bytes(int max_ops) {
+  return ((4 * size_t(max_ops + 2) * RT_MAX + size_t(max_ops + 2) + 2) * 4 + 15) / 16 * 16;
+}
+__host__ __device__ __forceinline__ size_t row_state_bytes(int max_ops) {
+  return (row_state_int_bytes(max_ops) + 8 * (size_t(max_ops + 2) * RT_MAX + 2 * RT_MAX) + 255) / 256 * 256;
+}
+__device__ __forceinline__ RowState row_state(unsigned char* base, int max_ops) {
+  const size_t ne = size_t(max_ops + 2) * RT_MAX;
+  int* ip = reinterpret_cast<int*>(base);
+  RowState R;
+  R.ekey = ip;
+  R.cnt = ip + ne;
+  R.ready = ip + 2 * ne;
+  R.ecum = ip + 3 * ne;
+  R.rows = ip + 4 * ne;
+  R.abort = R.rows + (max_ops + 2);
+  R.fr = reinterpret_cast<double*>(base + row_state_int_bytes(max_ops));
+  R.part = R.fr + ne;
+  return R;
+}
+
+// Shared-memory tables of the current string, after the stages: tau, log
+// scale and bound prefix (float64), operator, sector path and first tile of
+// every product stage (int), max_ops + 1 entries each.
+__host__ __device__ __forceinline__ size_t big_table_bytes(int max_ops) {
+  return size_t(max_ops + 1) * (3 * 8 + 3 * 4);
+}
+
+// Warp-uniform bounded wait: every lane waits, the warp goes on only if all
+// lanes saw the phase complete and nobody has failed.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, uint64_t limit, volatile int* fail) {
+  const bool ok = !*fail && mbar_wait(bar, parity, limit);
+  return __all_sync(0xffffffffu, ok) != 0;
+}
 
 }  // namespace
 
 namespace {
 
+// Products are scheduled tile by tile: all tiles of all product stages of a
+// string form one sequence (stage by stage, tile order P.order inside a
+// stage) dealt round-robin to the persistent CTAs.  A tile of stage s only
+// needs row tile mt of Z_s (a row of Z is one initial state: rows never mix),
+// so instead of a grid barrier per operator the producer waits for that row
+// tile's ready flag, and a CTA whose share of stage s runs out goes on with
+// stage s + 1 while others finish stage s.  Each row tile is rescaled by its
+// own power of two; the lazy bound of a checkpoint is computed by the tile
+// that completes the stage, and a rejected string's remaining tiles are
+// skipped.  Deadlock freedom: every tile depends only on tiles earlier in the
+// sequence, each CTA takes its tiles in sequence order, and all CTAs are
+// co-resident, so the earliest unfinished tile can always run.
 template <int PREC>
 __global__ void __launch_bounds__(BG_THREADS, 1)
     k_trace_big(DevModel M, BatchView B, EvalCfg cfg, Work W, BigParams P) {
@@ -162,11 +235,17 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
   const int NST = P.nst;
   const uint32_t stage_bytes = (SPLIT ? 2u : 1u) * (A_BYTES + B_BYTES);
   unsigned char* stage0 = smem_raw;
-  float* p_s = reinterpret_cast<float*>(stage0 + size_t(NST) * stage_bytes);  // [PVEC] column scales
-  // [PVEC] wrap-around propagator of q0: only the first, elementwise product
-  // of a string reads it, when no copy or MMA uses the stages
-  float* q_s = reinterpret_cast<float*>(stage0);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  // [PVEC] column propagator of the first, elementwise product: lives in the
+  // stages, which no copy or MMA uses at that time
+  float* p_s = reinterpret_cast<float*>(stage0);
+  const int TBL = cfg.max_ops + 1;
+  double* tau_s = reinterpret_cast<double*>(stage0 + size_t(NST) * stage_bytes);
+  double* L_s = tau_s + TBL;    // log scale after k propagators (compensated sum)
+  double* pre_s = L_s + TBL;    // bound prefix after k propagators
+  int* op_s = reinterpret_cast<int*>(pre_s + TBL);
+  int* path_s = op_s + TBL;     // sector after k operators
+  int* ustart_s = path_s + TBL; // first tile of product stage s; [n - 1] = all tiles
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ns = M.n_sec;
   const int cplx = M.is_complex;
 
@@ -179,6 +258,10 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
       mbar_init(&S.bank_full[b], 1);
       mbar_init(&S.bank_free[b], N_DRAIN);  // one arrival per drain warp
     }
+    for (int i = 0; i < DR; ++i) {
+      mbar_init(&S.unit_full[i], 1);
+      mbar_init(&S.unit_empty[i], 1 + N_DRAIN);  // the issuer and every drain warp
+    }
     mbar_init(&S.never, 1);
     S.fail = 0;
     S.issued = 0;
@@ -190,9 +273,11 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tD = S.tmem_base;
-  const int lane = tid & 31;
-  uint32_t seq_base = 0;  // sequence number of chunk 0 of the current tile (all threads)
+  volatile int* fail_v = &S.fail;
+  // per-role running counters (every role advances its own copy identically)
+  uint32_t seq_base = 0;  // sequence number of chunk 0 of the current tile
   uint32_t grp_base = 0;  // sequence number of the current tile's first accumulation group
+  uint32_t ucount = 0;    // tile descriptors passed through the ring
   bool alive = true;
   if (cfg.debug & CTQ_DEBUG_STALL_WAIT) {
     // CTA 0 waits on an event that never happens; the others then time out
@@ -207,6 +292,20 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
   T* zb = reinterpret_cast<T*>(P.zbuf);
   T* Zh[2] = {zb, zb + 2 * P.zfloats};
   T* Zl[2] = {zb + P.zfloats, zb + 3 * P.zfloats};
+  const size_t sbytes = row_state_bytes(cfg.max_ops);
+  // Row-tile stride (in K chunks) of every stored product: the widest Z.
+  // Row tile r of Z_{s+1} is written while other row tiles of Z_{s-1}, in
+  // the same buffer, may still be read; with one stride for all widths the
+  // row tiles of different products never share memory.
+  const int nkz = 2 * rup(M.max_dim, BK) / BKE;
+  const long long gthreads = (long long)gridDim.x * BG_THREADS;
+  const long long gtid = (long long)blockIdx.x * BG_THREADS + tid;
+  if (alive) {
+    int* z = reinterpret_cast<int*>(P.state);
+    for (long long i = gtid; i < (long long)(sbytes / 4); i += gthreads) z[i] = 0;
+    if (!grid_sync(P.bar, P.bar + 1, P.timeout_ns)) alive = false;
+  }
+  int par = 0;  // state copy of the current string
 
   for (int it_idx = 0; it_idx < n_items && alive; ++it_idx) {
     const Item it = items[it_idx];
@@ -219,13 +318,6 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
     const double* E0 = M.E_rel + M.E_off[q0];
     const bool track = cfg.lazy || cfg.bounds != nullptr;
     double* segp = W.seg + slot * size_t(cfg.n_seg_max + 1);
-    if (blockIdx.x == 0 && tid <= n) {
-      for (int i = tid; i <= n; i += BG_THREADS) {
-        P.ekey[i] = 0;
-        P.fr[i] = 0.0;
-      }
-    }
-    if (!grid_sync(P.bar, P.bar + 1, P.timeout_ns)) { alive = false; break; }
 
     if (n < 2) {  // tiny strings: one CTA does it in float64
       if (blockIdx.x == 0) {
@@ -257,44 +349,124 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
       continue;
     }
 
+    const RowState RS = row_state(P.state + size_t(par) * sbytes, cfg.max_ops);
+    unsigned char* next_state = P.state + size_t(par ^ 1) * sbytes;
+    par ^= 1;
+    const int R = dp0 / BM;
+
+    // ---- tables of the string (every CTA keeps its own copy)
+    for (int k = tid; k < n; k += BG_THREADS) {
+      op_s[k] = B.op[a0 + k];
+      tau_s[k] = B.tau[a0 + k];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const double er0 = M.E_min[q0] - M.E_ref;
+      KSum L;
+      L.add(-tau_s[0] * er0);
+      L.add(-(B.beta - tau_s[n - 1]) * er0);
+      double pre = M.log_norm[op_s[0] * ns + q0];
+      int q = q0;
+      path_s[0] = q0;
+      for (int k = 1; k < n; ++k) {
+        q = M.s[op_s[k - 1] * ns + q];
+        path_s[k] = q;
+        const double dt = tau_s[k] - tau_s[k - 1];
+        const double er = M.E_min[q] - M.E_ref;
+        L.add(-dt * er);
+        pre -= dt * er;
+        L_s[k] = L.val();
+        pre_s[k] = pre;
+        pre += M.log_norm[op_s[k] * ns + q];
+      }
+      path_s[n] = M.s[op_s[n - 1] * ns + q];
+      int u = 0;
+      for (int s = 1; s <= n - 2; ++s) {
+        ustart_s[s] = u;
+        u += R * ((2 * rup(M.dims[path_s[s + 1]], BK) + BN - 1) / BN);
+      }
+      ustart_s[n - 1] = u;
+    }
+    __syncthreads();
+
+    // Lazy bound after a applied operators (one thread): the stored Z_a row
+    // tiles carry the exponents ecum[a - 1][r].
+    auto bound = [&](int a) {
+      int emx = INT_MIN;
+      for (int r = 0; r < R; ++r)
+        if (__ldcg(&RS.fr[a * RT_MAX + r]) > 0.0) emx = max(emx, __ldcg(&RS.ecum[(a - 1) * RT_MAX + r]));
+      double sfr = 0.0;
+      if (emx != INT_MIN)
+        for (int r = 0; r < R; ++r) {
+          const double f = __ldcg(&RS.fr[a * RT_MAX + r]);
+          if (f > 0.0) sfr += ldexp(f, 2 * (__ldcg(&RS.ecum[(a - 1) * RT_MAX + r]) - emx));
+        }
+      const double ub = (sfr > 0.0) ? 0.5 * log(double(it.r)) + 0.5 * log(sfr) + double(emx) * LN2 + L_s[a] +
+                                          (it.t_all - pre_s[a])
+                                    : -INFINITY;
+      segp[a / cfg.S] = ub;
+      if (cfg.lazy) {
+        W.live[slot] = fmin(W.live[slot], ub);
+        double lm = -INFINITY, lsum = 0.0;
+        for (int q = 0; q < ns; ++q) {
+          const double v = W.live[size_t(c) * ns + q];
+          if (v > lm) { lsum = lsum * exp(lm - v) + 1.0; lm = v; }
+          else if (v != -INFINITY) lsum += exp(v - lm);
+        }
+        const double lub = (lm == -INFINITY) ? lm : lm + log(lsum);
+        int flag = W.chain_flag[c];
+        if (!(flag & FLAG_REJECTED) && lub + cfg.margin < B.log_threshold[c] + B.beta * M.E_ref) {
+          flag |= FLAG_REJECTED;
+          W.chain_flag[c] = flag;
+        }
+        if (flag & FLAG_REJECTED) atomicExch(RS.abort, 1);
+        __threadfence();
+      }
+    };
+
     // ---- operator 1 (elementwise): Z_1[j][m] = p0[j] F_1[m][j] p1[m]
-    const double t_first = B.tau[a0], t_last = B.beta - B.tau[a0 + n - 1];
-    int qa = q0;
-    int alpha = B.op[a0];
-    int qb = M.s[alpha * ns + qa];
-    KSum L;
-    long long Eacc = 0;
-    double prefix = M.log_norm[alpha * ns + qa];
-    L.add(-t_first * (M.E_min[q0] - M.E_ref));
-    L.add(-t_last * (M.E_min[q0] - M.E_ref));
     {
-      const double dt = B.tau[a0 + 1] - B.tau[a0];
-      L.add(-dt * (M.E_min[qb] - M.E_ref));
-      prefix -= dt * (M.E_min[qb] - M.E_ref);
+      const int qb = path_s[1];
       const int d1 = M.dims[qb];
       const int dpk = rup(d1, BK);
-      const int nkc = 2 * dpk / BKE;
+      const double dt = tau_s[1] - tau_s[0];
+      const double t_first = tau_s[0], t_last = B.beta - tau_s[n - 1];
       const double* Eb = M.E_rel + M.E_off[qb];
-      for (int j = tid; j < d0; j += BG_THREADS)
-        q_s[j] = expf(float(-t_first * E0[j])) * expf(float(-t_last * E0[j]));
       for (int m = tid; m < d1; m += BG_THREADS) p_s[m] = expf(float(-dt * Eb[m]));
       __syncthreads();
-      const int64_t off = M.blk_off[alpha * ns + qa];
-      int ek = 0;
+      const int64_t off = M.blk_off[op_s[0] * ns + q0];
+      int cur_r = -1, ek = 0;
       float f2 = 0.f;
+      // the 32 lanes of a warp always share a row (dpk is a multiple of 32),
+      // so row-tile partials are flushed warp by warp
+      auto flush = [&]() {
+        const int ekw = __reduce_max_sync(0xffffffffu, ek);
+        const double fw = warp_sum(double(f2));
+        if (lane == 0 && cur_r >= 0) {
+          atomicMax(&RS.ekey[RT_MAX + cur_r], ekw);
+          atomicAdd(&RS.fr[RT_MAX + cur_r], fw);
+        }
+        ek = 0;
+        f2 = 0.f;
+      };
       const long long total = (long long)dp0 * dpk;
-      for (long long e = (long long)blockIdx.x * BG_THREADS + tid; e < total; e += (long long)gridDim.x * BG_THREADS) {
+      for (long long e = gtid; e < total; e += gthreads) {
         const int j = int(e / dpk), m = int(e - (long long)j * dpk);
+        const int r = j / BM;
+        if (r != cur_r) {
+          flush();
+          cur_r = r;
+        }
         float xr = 0.f, xi = 0.f;
         if (j < d0 && m < d1) {
-          const float pj = q_s[j] * p_s[m];
+          const float pj = expf(float(-t_first * E0[j])) * expf(float(-t_last * E0[j])) * p_s[m];
           const int64_t fe = off + int64_t(m) * d0 + j;
           xr = float(cplx ? M.blk[2 * fe] : M.blk[fe]) * pj;
           xi = cplx ? float(M.blk[2 * fe + 1]) * pj : 0.f;
         }
         ek = max(ek, max((__float_as_int(xr) >> 23) & 0xff, (__float_as_int(xi) >> 23) & 0xff));
         f2 += xr * xr + xi * xi;
-        const size_t o_r = tiled_off<EB>(j, m, BM, nkc), o_i = tiled_off<EB>(j, dpk + m, BM, nkc);
+        const size_t o_r = tiled_off<EB>(j, m, BM, nkz), o_i = tiled_off<EB>(j, dpk + m, BM, nkz);
         T hr, lr, hi_, li;
         split_store<PREC>(xr, hr, lr);
         split_store<PREC>(xi, hi_, li);
@@ -305,192 +477,130 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
           Zl[0][o_i] = li;
         }
       }
-      // q_s lives in the stages: order these generic accesses before the
-      // bulk copies that will refill them
+      flush();
+      // p_s lives in the stages and Z_1 is read by bulk copies (async proxy)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      ek = __reduce_max_sync(0xffffffffu, ek);
-      double f2d = warp_sum(double(f2));
-      if ((tid & 31) == 0) {
-        atomicMax(&P.ekey[1], ek);
-        atomicAdd(&P.fr[1], f2d);
-      }
+      asm volatile("fence.proxy.async.global;" ::: "memory");
     }
     if (!grid_sync(P.bar, P.bar + 1, P.timeout_ns)) { alive = false; break; }
-    int cur = 0;
-    int dcur = M.dims[qb];
-    qa = qb;
-    int applied = 1;
-    bool dead = false, aborted = false;
+    if (blockIdx.x == 0 && tid == 64 && track && cfg.S == 1) bound(1);
 
-    for (int i = 1; i < n; ++i) {
-      const int ekey = *((volatile int*)&P.ekey[applied]);
-      if (ekey == 0) { dead = true; break; }
-      const int e = ekey - 127;  // floor(log2 max|Z|) of the stored product (float exponent)
-      if (track && applied % cfg.S == 0 && applied < n) {
-        const double frv = *((volatile double*)&P.fr[applied]);
-        const double ub = 0.5 * log(double(it.r)) + 0.5 * log(frv) + double(Eacc) * LN2 + L.val() +
-                          (it.t_all - prefix);
-        if (blockIdx.x == 0 && tid == 0) {
-          segp[applied / cfg.S] = ub;
-          if (cfg.lazy) {
-            W.live[slot] = fmin(W.live[slot], ub);
-            double lm = -INFINITY, lsum = 0.0;
-            for (int q = 0; q < ns; ++q) {
-              const double v = W.live[size_t(c) * ns + q];
-              if (v > lm) { lsum = lsum * exp(lm - v) + 1.0; lm = v; }
-              else if (v != -INFINITY) lsum += exp(v - lm);
+    // ---- products Z_{s+1} = Z_s F_{s+1}^T P_{s+1}, s = 1 .. n - 2
+    if (n >= 3) {
+      const int total = ustart_s[n - 1];
+      const size_t b_tile = B_BYTES / EB, a_tile = A_BYTES / EB;  // elements per staged tile
+      if (tid == 32) {
+        // producer and scheduler: announces each tile, waits for its input
+        // row tile, then streams its chunks through the stages
+        int s = 1;
+        for (int u = blockIdx.x;; u += gridDim.x) {
+          Unit d{-1, 0, 0, 0};
+          if (u < total && !*fail_v) {
+            while (ustart_s[s + 1] <= u) ++s;
+            const int n_nt = (2 * rup(M.dims[path_s[s + 1]], BK) + BN - 1) / BN;
+            tile_coords(u - ustart_s[s], R, n_nt, P.order, d.mt, d.nt);
+            d.s = s;
+            const volatile int* ab = RS.abort;
+            d.skip = *ab;
+            if (!d.skip && s >= 2) {
+              const volatile int* rdy = RS.ready + s * RT_MAX + d.mt;
+              bool ok = true;
+              if (*rdy == 0) {
+                const uint64_t t0 = globaltimer();
+                while (*rdy == 0 && *ab == 0) {
+                  if (globaltimer() - t0 > P.timeout_ns) {
+                    ok = false;
+                    break;
+                  }
+                }
+              }
+              if (!ok) {
+                *fail_v = 1;
+                d.s = -1;
+              } else if (*ab) {
+                d.skip = 1;
+              } else {
+                __threadfence();
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+              }
             }
-            const double lub = (lm == -INFINITY) ? lm : lm + log(lsum);
-            int flag = W.chain_flag[c];
-            if (!(flag & FLAG_REJECTED) && lub + cfg.margin < B.log_threshold[c] + B.beta * M.E_ref) {
-              flag |= FLAG_REJECTED;
-              W.chain_flag[c] = flag;
-            }
-            *P.abort_flag = (flag & FLAG_REJECTED) ? 1 : 0;
-            __threadfence();
           }
-        }
-        if (cfg.lazy) {
-          if (!grid_sync(P.bar, P.bar + 1, P.timeout_ns)) { alive = false; break; }
-          if (*((volatile int*)P.abort_flag)) { aborted = true; break; }
-        }
-      }
-      alpha = B.op[a0 + i];
-      const int idx_a = alpha * ns + qa;
-      qb = M.s[idx_a];
-      const float scale = ldexpf(1.0f, -e);
-      prefix += M.log_norm[idx_a];
-      Eacc += e;
-
-      if (i == n - 1) {  // final operator: sum_{j,k} F_n[j][k] Z[j][k]
-        const int64_t off = M.blk_off[idx_a];
-        const int dpk = rup(dcur, BK), nkc = 2 * dpk / BKE;
-        double vr = 0.0, vi = 0.0;
-        const long long total = (long long)d0 * dcur;
-        for (long long e2 = (long long)blockIdx.x * BG_THREADS + tid; e2 < total;
-             e2 += (long long)gridDim.x * BG_THREADS) {
-          const int j = int(e2 / dcur), k = int(e2 - (long long)j * dcur);
-          const size_t o_r = tiled_off<EB>(j, k, BM, nkc), o_i = tiled_off<EB>(j, dpk + k, BM, nkc);
-          float zr = elt_val<PREC>(Zh[cur][o_r]), zi = elt_val<PREC>(Zh[cur][o_i]);
-          if (SPLIT) {
-            zr += elt_val<PREC>(Zl[cur][o_r]);
-            zi += elt_val<PREC>(Zl[cur][o_i]);
+          const uint32_t us = ucount % DR;
+          if (ucount >= DR && !mbar_wait(&S.unit_empty[us], ((ucount / DR) - 1u) & 1u, P.timeout_ns)) {
+            *fail_v = 1;
+            break;
           }
-          const int64_t fe = off + int64_t(j) * dcur + k;
-          const float fr_ = float(cplx ? M.blk[2 * fe] : M.blk[fe]);
-          const float fi_ = cplx ? float(M.blk[2 * fe + 1]) : 0.f;
-          vr += double(fr_ * zr - fi_ * zi);
-          vi += double(fr_ * zi + fi_ * zr);
-        }
-        double dm = 0.0;
-        block_max_sum(dm, vr, S.redd);
-        dm = 0.0;
-        block_max_sum(dm, vi, S.redd);
-        if (tid == 0) {
-          P.part[2 * blockIdx.x] = vr;
-          P.part[2 * blockIdx.x + 1] = vi;
-        }
-        if (!grid_sync(P.bar, P.bar + 1, P.timeout_ns)) { alive = false; break; }
-        if (blockIdx.x == 0 && tid == 0) {
-          double sr = 0.0, si = 0.0;
-          for (int b = 0; b < int(gridDim.x); ++b) {
-            sr += P.part[2 * b];
-            si += P.part[2 * b + 1];
-          }
-          sr *= double(scale);
-          si *= double(scale);
-          const bool zero_v = (sr == 0.0 && si == 0.0);
-          W.res_val[2 * slot] = sr;
-          W.res_val[2 * slot + 1] = si;
-          W.res_log[slot] = zero_v ? -INFINITY : L.val() + double(Eacc) * LN2;
-          if (track) segp[it.n_seg] = zero_v ? -INFINITY : log(sqrt(sr * sr + si * si)) + L.val() + double(Eacc) * LN2;
-        }
-        applied = n;
-        break;
-      }
-
-      // ---- tensor-core product: Z_next = Z F^T, columns scaled by p * 2^-e
-      const int db = M.dims[qb];
-      const int dpk = rup(dcur, BK), nkc = 2 * dpk / BKE;   // K chunks of this product
-      const int dpn = rup(db, BK), nkc_n = 2 * dpn / BKE;   // K chunks of the next one
-      {
-        const double dt = B.tau[a0 + i + 1] - B.tau[a0 + i];
-        const double* Eb = M.E_rel + M.E_off[qb];
-        for (int j = tid; j < dpn; j += BG_THREADS) p_s[j] = (j < db) ? expf(float(-dt * Eb[j])) * scale : 0.f;
-        __syncthreads();
-        L.add(-dt * (M.E_min[qb] - M.E_ref));
-        prefix -= dt * (M.E_min[qb] - M.E_ref);
-      }
-      __syncthreads();
-      const T* Bt = reinterpret_cast<const T*>(P.bt) + P.bt_off[idx_a];
-      const size_t b_tile = B_BYTES / EB, a_tile = A_BYTES / EB;      // elements per staged tile
-      const size_t b_plane = size_t(rup(2 * dpn, BN) / BN) * nkc * b_tile;  // elements of one B plane
-      const int n_mt = dp0 / BM, n_nt = (2 * dpn + BN - 1) / BN;
-      const int n_tiles = n_mt * n_nt;
-      const int nxt = cur ^ 1;
-      int ek = 0;
-      float f2 = 0.f;
-      // Warp-specialised pipeline.  Chunks carry a per-CTA sequence number q
-      // (q = seq_base + kc within a tile), live in stage q % NST and complete
-      // phase q / NST of that stage's full / empty barriers.  Thread 32 (the
-      // producer) refills a stage as soon as the products reading it have
-      // completed and, at the end of a tile, issues the first chunks of the
-      // CTA's next tile of the same product; thread 0 (the MMA issuer) only
-      // waits for data.  The K loop is cut into groups of GRP chunks with
-      // sequence numbers g (g = grp_base + kc / GRP); group g accumulates in
-      // tensor-memory bank g % 2, which the N_DRAIN drain warps add into FP32
-      // registers (round to nearest) while the tensor core fills the other
-      // bank.  After a tile's last group the drain warps run the epilogue
-      // from registers and the issuer and producer go on with the next tile.
-      volatile int* fail_v = &S.fail;
-      auto produce = [&](uint32_t q, int tt, int kc) -> bool {
-        int mt_, nt_;
-        tile_coords(tt, n_mt, n_nt, P.order, mt_, nt_);
-        const int st = int(q % uint32_t(NST));
-        if (q >= uint32_t(NST) && !mbar_wait(&S.empty[st], ((q / NST) - 1u) & 1u, P.timeout_ns)) return false;
-        unsigned char* sb = stage0 + size_t(st) * stage_bytes;
-        const size_t ao = (size_t(mt_) * nkc + kc) * a_tile, bo = (size_t(nt_) * nkc + kc) * b_tile;
-        mbar_arrive_expect_tx(&S.full[st], stage_bytes);
-        bulk_g2s(sb, Zh[cur] + ao, A_BYTES, &S.full[st]);
-        bulk_g2s(sb + A_BYTES, Bt + bo, B_BYTES, &S.full[st]);
-        if (SPLIT) {
-          bulk_g2s(sb + A_BYTES + B_BYTES, Zl[cur] + ao, A_BYTES, &S.full[st]);
-          bulk_g2s(sb + 2 * A_BYTES + B_BYTES, Bt + b_plane + bo, B_BYTES, &S.full[st]);
-        }
-        S.issued = q + 1;
-        return true;
-      };
-      const int ngrp = (nkc + GRP - 1) / GRP;
-      int pre = 0;  // (producer) chunks of the current tile already issued
-      for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        int mt, nt;
-        tile_coords(t, n_mt, n_nt, P.order, mt, nt);
-        const int ncols = min(BN, 2 * dpn - nt * BN);
-        if (tid == 32) {
+          S.unit[us] = d;
+          mbar_arrive(&S.unit_full[us]);
+          ++ucount;
+          if (d.s < 0) break;
+          if (d.skip) continue;
+          const int qa = path_s[d.s], qb = path_s[d.s + 1];
+          const int dpk = rup(M.dims[qa], BK), nkc = 2 * dpk / BKE;
+          const int dpn = rup(M.dims[qb], BK);
+          const T* Bt = reinterpret_cast<const T*>(P.bt) + P.bt_off[op_s[d.s] * ns + qa];
+          const size_t b_plane = size_t(rup(2 * dpn, BN) / BN) * nkc * b_tile;
+          const T* Ah = Zh[(d.s - 1) & 1];
+          const T* Al = Zl[(d.s - 1) & 1];
           bool okp = true;
-          for (int kc = pre; kc < nkc && okp && !*fail_v; ++kc) okp = produce(seq_base + kc, t, kc);
-          pre = 0;
-          const int tn = t + int(gridDim.x);
-          if (okp && tn < n_tiles) {
-            const int np = min(NST, nkc);
-            for (int j = 0; j < np && okp && !*fail_v; ++j) okp = produce(seq_base + nkc + j, tn, j);
-            pre = np;
-          }
-          if (!okp) *fail_v = 1;
-        } else if (tid == 0) {
-          const uint32_t idesc = (PREC == CTQ_BF16X3) ? idesc_bf16(BM, ncols) : idesc_tf32(BM, ncols);
           for (int kc = 0; kc < nkc; ++kc) {
-            const uint32_t q = seq_base + kc;
+            const uint32_t q = seq_base + uint32_t(kc);
+            const int st = int(q % uint32_t(NST));
+            if (*fail_v || (q >= uint32_t(NST) && !mbar_wait(&S.empty[st], ((q / NST) - 1u) & 1u, P.timeout_ns))) {
+              okp = false;
+              break;
+            }
+            unsigned char* sb = stage0 + size_t(st) * stage_bytes;
+            const size_t ao = (size_t(d.mt) * nkz + kc) * a_tile, bo = (size_t(d.nt) * nkc + kc) * b_tile;
+            mbar_arrive_expect_tx(&S.full[st], stage_bytes);
+            bulk_g2s(sb, Ah + ao, A_BYTES, &S.full[st]);
+            bulk_g2s(sb + A_BYTES, Bt + bo, B_BYTES, &S.full[st]);
+            if (SPLIT) {
+              bulk_g2s(sb + A_BYTES + B_BYTES, Al + ao, A_BYTES, &S.full[st]);
+              bulk_g2s(sb + 2 * A_BYTES + B_BYTES, Bt + b_plane + bo, B_BYTES, &S.full[st]);
+            }
+            S.issued = q + 1;
+          }
+          seq_base += uint32_t(nkc);
+          if (!okp) {
+            *fail_v = 1;
+            break;
+          }
+        }
+      } else if (tid == 0) {
+        // MMA issuer: only waits for data.  Chunks carry a per-CTA sequence
+        // number q (stage q % NST, phase q / NST); groups of GRP chunks carry
+        // g and accumulate in tensor-memory bank g % 2, which the drain warps
+        // add into FP32 registers while the tensor core fills the other bank.
+        for (;;) {
+          const uint32_t us = ucount % DR;
+          if (*fail_v || !mbar_wait(&S.unit_full[us], (ucount / DR) & 1u, P.timeout_ns)) {
+            *fail_v = 1;
+            break;
+          }
+          const Unit d = S.unit[us];
+          mbar_arrive(&S.unit_empty[us]);
+          ++ucount;
+          if (d.s < 0) break;
+          if (d.skip) continue;
+          const int dpk = rup(M.dims[path_s[d.s]], BK), nkc = 2 * dpk / BKE;
+          const int dpn = rup(M.dims[path_s[d.s + 1]], BK);
+          const int ncols = min(BN, 2 * dpn - d.nt * BN);
+          const int ngrp = (nkc + GRP - 1) / GRP;
+          const uint32_t idesc = (PREC == CTQ_BF16X3) ? idesc_bf16(BM, ncols) : idesc_tf32(BM, ncols);
+          bool ok = true;
+          for (int kc = 0; kc < nkc; ++kc) {
+            const uint32_t q = seq_base + uint32_t(kc);
             const uint32_t g = grp_base + uint32_t(kc / GRP);
             const int st = int(q % uint32_t(NST));
             const uint32_t bank = g & 1u;
             if (kc % GRP == 0 && g >= 2u &&
                 (*fail_v || !mbar_wait(&S.bank_free[bank], ((g >> 1) - 1u) & 1u, P.timeout_ns))) {
-              *fail_v = 1;
+              ok = false;
               break;
             }
             if (*fail_v || !mbar_wait(&S.full[st], (q / NST) & 1u, P.timeout_ns)) {
-              *fail_v = 1;
+              ok = false;
               break;
             }
             S.consumed = q + 1;
@@ -511,20 +621,60 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
             mma_commit(&S.empty[st]);
             if (kc % GRP == GRP - 1 || kc == nkc - 1) mma_commit(&S.bank_full[bank]);
           }
-        } else if (warp >= 2) {
-          // drain warps: lane quarter warp % 4, column slice (warp - 2) / 4 of
-          // COLS columns
-          constexpr int COLS = BN / (N_DRAIN / 4);
-          const int slice = (warp - 2) >> 2;
-          const uint32_t tl = uint32_t(32 * (warp & 3)) << 16;
+          seq_base += uint32_t(nkc);
+          grp_base += uint32_t(ngrp);
+          if (!ok) {
+            *fail_v = 1;
+            break;
+          }
+        }
+      } else if (warp >= 2) {
+        // drain warps: lane quarter warp % 4, column slice (warp - 2) / 4 of
+        // COLS columns; they also run the epilogue and publish finished row tiles
+        constexpr int COLS = BN / (N_DRAIN / 4);
+        const int slice = (warp - 2) >> 2;
+        const uint32_t tl = uint32_t(32 * (warp & 3)) << 16;
+        for (;;) {
+          const uint32_t us = ucount % DR;
+          if (!warp_wait(&S.unit_full[us], (ucount / DR) & 1u, P.timeout_ns, fail_v)) {
+            *fail_v = 1;
+            break;
+          }
+          const Unit d = S.unit[us];
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&S.unit_empty[us]);
+          ++ucount;
+          if (d.s < 0) break;
+          if (d.skip) continue;
+          const int qb = path_s[d.s + 1];
+          const int dpk = rup(M.dims[path_s[d.s]], BK), nkc = 2 * dpk / BKE;
+          const int db = M.dims[qb];
+          const int dpn = rup(db, BK);
+          const int ncols = min(BN, 2 * dpn - d.nt * BN);
+          const int ngrp = (nkc + GRP - 1) / GRP;
+          // column scale e^{-dt (E - E_min)} 2^{-e_r(s)}: lane l holds columns
+          // l, l + 32, ... of this warp's slice
+          const int ek_in = __ldcg(&RS.ekey[d.s * RT_MAX + d.mt]);
+          const float scale = ek_in ? ldexpf(1.0f, -(ek_in - 127)) : 1.0f;
+          float preg[COLS / 32];
+          {
+            const double dt = tau_s[d.s + 1] - tau_s[d.s];
+            const double* Eb = M.E_rel + M.E_off[qb];
+#pragma unroll
+            for (int i = 0; i < COLS / 32; ++i) {
+              const int col = d.nt * BN + slice * COLS + 32 * i + lane;
+              const int j = (col < dpn) ? col : col - dpn;
+              preg[i] = (j < db) ? expf(float(-dt * Eb[j])) * scale : 0.f;
+            }
+          }
           float acc[COLS];
 #pragma unroll
-          for (int c = 0; c < COLS; ++c) acc[c] = 0.f;
+          for (int cc = 0; cc < COLS; ++cc) acc[cc] = 0.f;
           bool okd = true;
           for (int gi = 0; gi < ngrp; ++gi) {
             const uint32_t g = grp_base + uint32_t(gi);
             const uint32_t bank = g & 1u;
-            if (*fail_v || !mbar_wait(&S.bank_full[bank], (g >> 1) & 1u, P.timeout_ns)) {
+            if (!warp_wait(&S.bank_full[bank], (g >> 1) & 1u, P.timeout_ns, fail_v)) {
               okd = false;
               break;
             }
@@ -539,19 +689,27 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
 #pragma unroll
               for (int u = 0; u < 2; ++u)
 #pragma unroll
-                for (int c = 0; c < 16; ++c) acc[h * 32 + u * 16 + c] += __uint_as_float(v[u][c]);
+                for (int cc = 0; cc < 16; ++cc) acc[h * 32 + u * 16 + cc] += __uint_as_float(v[u][cc]);
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&S.bank_free[bank]);
           }
-          if (!okd) *fail_v = 1;
-          // epilogue from registers: this thread's row, COLS columns
-          const int row = mt * BM + 32 * (warp & 3) + lane;
+          grp_base += uint32_t(ngrp);
+          if (!okd) {
+            *fail_v = 1;
+            break;
+          }
+          // epilogue from registers: this thread's row, COLS columns of Z_{s+1}
+          T* Oh = Zh[d.s & 1];
+          T* Ol = Zl[d.s & 1];
+          const int row = d.mt * BM + 32 * (warp & 3) + lane;
+          int ek = 0;
+          float f2 = 0.f;
 #pragma unroll
           for (int c0 = 0; c0 < COLS; c0 += 16) {
             const int cb = slice * COLS + c0;  // column within the tile
-            if (!okd || cb >= ncols) break;
+            if (cb >= ncols) break;
             // 16 consecutive K elements of the next product, written as
             // 16-byte vectors of PER16 elements
             constexpr int PER16 = 16 / EB;
@@ -560,56 +718,130 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
               T hi[PER16], lo[PER16];
 #pragma unroll
               for (int t2 = 0; t2 < PER16; ++t2) {
-                const int col = nt * BN + cb + PER16 * g + t2;  // embedded column
-                const int j = (col < dpn) ? col : col - dpn;
-                const float x = acc[c0 + PER16 * g + t2] * p_s[j];
+                const int cc = c0 + PER16 * g + t2;
+                const float x = acc[cc] * __shfl_sync(0xffffffffu, preg[cc >> 5], cc & 31);
                 ek = max(ek, (__float_as_int(x) >> 23) & 0xff);
                 f2 += x * x;
                 split_store<PREC>(x, hi[t2], lo[t2]);
               }
-              const size_t o = tiled_off<EB>(row, nt * BN + cb + PER16 * g, BM, nkc_n);
-              *reinterpret_cast<uint4*>(Zh[nxt] + o) = pack16<PREC>(hi);
-              if (SPLIT) *reinterpret_cast<uint4*>(Zl[nxt] + o) = pack16<PREC>(lo);
+              const size_t o = tiled_off<EB>(row, d.nt * BN + cb + PER16 * g, BM, nkz);
+              *reinterpret_cast<uint4*>(Oh + o) = pack16<PREC>(hi);
+              if (SPLIT) *reinterpret_cast<uint4*>(Ol + o) = pack16<PREC>(lo);
             }
           }
+          ek = __reduce_max_sync(0xffffffffu, ek);
+          const double f2d = warp_sum(double(f2));
+          // the stored tile is read by bulk copies (async proxy) of other CTAs next
+          asm volatile("fence.proxy.async.global;" ::: "memory");
+          __threadfence();
+          __syncwarp();
+          if (lane == 0) {
+            // every drain warp of every column tile reports once; the report
+            // that completes a row tile marks it ready, the one that completes
+            // the stage takes the checkpoint bound
+            atomicMax(&RS.ekey[(d.s + 1) * RT_MAX + d.mt], ek);
+            atomicAdd(&RS.fr[(d.s + 1) * RT_MAX + d.mt], f2d);
+            __threadfence();
+            const int n_nt = (2 * dpn + BN - 1) / BN;
+            if (atomicAdd(&RS.cnt[(d.s + 1) * RT_MAX + d.mt], 1) == n_nt * N_DRAIN - 1) {
+              __threadfence();
+              RS.ecum[d.s * RT_MAX + d.mt] = __ldcg(&RS.ecum[(d.s - 1) * RT_MAX + d.mt]) + (ek_in ? ek_in - 127 : 0);
+              __threadfence();
+              *((volatile int*)&RS.ready[(d.s + 1) * RT_MAX + d.mt]) = 1;
+              if (atomicAdd(&RS.rows[d.s + 1], 1) == R - 1) {
+                __threadfence();
+                const int a = d.s + 1;
+                if (track && a % cfg.S == 0 && a < n) bound(a);
+              }
+            }
+          }
+          __syncwarp();
         }
-        seq_base += uint32_t(nkc);
-        grp_base += uint32_t(ngrp);
       }
-      // the running product is read by bulk copies (async proxy) next
-      asm volatile("fence.proxy.async.global;" ::: "memory");
-      __syncthreads();
-      if (S.fail) {
-        if (tid == 32)  // let issued copies that were never consumed land before leaving
-          for (uint32_t q = S.consumed; q < S.issued; ++q)
-            mbar_wait(&S.full[q % uint32_t(NST)], (q / NST) & 1u, P.timeout_ns);
-        alive = false;
-      }
-      if (!alive) break;
-      ek = __reduce_max_sync(0xffffffffu, ek);
-      const double f2d = warp_sum(double(f2));
-      if ((tid & 31) == 0) {
-        atomicMax(&P.ekey[applied + 1], ek);
-        atomicAdd(&P.fr[applied + 1], f2d);
-      }
-      if (!grid_sync(P.bar, P.bar + 1, P.timeout_ns)) { alive = false; break; }
-      cur = nxt;
-      dcur = db;
-      qa = qb;
-      ++applied;
     }
+    __syncthreads();
+    if (S.fail) {
+      if (tid == 32)  // let issued copies that were never consumed land before leaving
+        for (uint32_t q = S.consumed; q < S.issued; ++q)
+          mbar_wait(&S.full[q % uint32_t(NST)], (q / NST) & 1u, P.timeout_ns);
+      alive = false;
+    }
+    if (!alive) break;
+    if (!grid_sync(P.bar, P.bar + 1, P.timeout_ns)) { alive = false; break; }
+
+    // ---- final operator: partial traces sum_{j in r, k} F_n[j][k] Z_{n-1}[j][k]
+    const bool aborted = *((volatile int*)RS.abort) != 0;
+    if (!aborted) {
+      const int ql = path_s[n - 1];
+      const int dl = M.dims[ql];
+      const int dpk = rup(dl, BK);
+      const int64_t off = M.blk_off[op_s[n - 1] * ns + ql];
+      const T* Ah = Zh[(n - 2) & 1];
+      const T* Al = Zl[(n - 2) & 1];
+      int cur_r = -1;
+      double vr = 0.0, vi = 0.0;
+      auto flush = [&]() {
+        const double wr = warp_sum(vr), wi = warp_sum(vi);
+        if (lane == 0 && cur_r >= 0) {
+          atomicAdd(&RS.part[2 * cur_r], wr);
+          atomicAdd(&RS.part[2 * cur_r + 1], wi);
+        }
+        vr = 0.0;
+        vi = 0.0;
+      };
+      const long long total = (long long)dp0 * dpk;
+      for (long long e = gtid; e < total; e += gthreads) {
+        const int j = int(e / dpk), k = int(e - (long long)j * dpk);
+        const int r = j / BM;
+        if (r != cur_r) {
+          flush();
+          cur_r = r;
+        }
+        if (j < d0 && k < dl) {
+          const size_t o_r = tiled_off<EB>(j, k, BM, nkz), o_i = tiled_off<EB>(j, dpk + k, BM, nkz);
+          float zr = elt_val<PREC>(Ah[o_r]), zi = elt_val<PREC>(Ah[o_i]);
+          if (SPLIT) {
+            zr += elt_val<PREC>(Al[o_r]);
+            zi += elt_val<PREC>(Al[o_i]);
+          }
+          const int64_t fe = off + int64_t(j) * dl + k;
+          const float fr_ = float(cplx ? M.blk[2 * fe] : M.blk[fe]);
+          const float fi_ = cplx ? float(M.blk[2 * fe + 1]) : 0.f;
+          vr += double(fr_ * zr - fi_ * zi);
+          vi += double(fr_ * zi + fi_ * zr);
+        }
+      }
+      flush();
+    }
+    {  // the next string's state (its previous user finished before this string began)
+      int* z = reinterpret_cast<int*>(next_state);
+      for (long long i = gtid; i < (long long)(sbytes / 4); i += gthreads) z[i] = 0;
+    }
+    if (!grid_sync(P.bar, P.bar + 1, P.timeout_ns)) { alive = false; break; }
     if (blockIdx.x == 0 && tid == 0) {
-      if (dead) {
-        W.res_val[2 * slot] = 0.0;
-        W.res_val[2 * slot + 1] = 0.0;
-        W.res_log[slot] = -INFINITY;
-        if (track)
-          for (int s2 = (applied + cfg.S - 1) / cfg.S; s2 <= it.n_seg; ++s2)
-            if (s2 > 0) segp[s2] = -INFINITY;
+      if (aborted) {
+        W.res_log[slot] = NAN;
+      } else {
+        // row tile r of Z_{n-1} carries 2^{-ecum[n-2][r]}
+        int emx = INT_MIN;
+        for (int r = 0; r < R; ++r)
+          if (__ldcg(&RS.part[2 * r]) != 0.0 || __ldcg(&RS.part[2 * r + 1]) != 0.0)
+            emx = max(emx, __ldcg(&RS.ecum[(n - 2) * RT_MAX + r]));
+        double sr = 0.0, si = 0.0;
+        if (emx != INT_MIN)
+          for (int r = 0; r < R; ++r) {
+            const int sh = __ldcg(&RS.ecum[(n - 2) * RT_MAX + r]) - emx;
+            sr += ldexp(__ldcg(&RS.part[2 * r]), sh);
+            si += ldexp(__ldcg(&RS.part[2 * r + 1]), sh);
+          }
+        const bool zero_v = (sr == 0.0 && si == 0.0);
+        const double lg = L_s[n - 1] + double(emx) * LN2;
+        W.res_val[2 * slot] = sr;
+        W.res_val[2 * slot + 1] = si;
+        W.res_log[slot] = zero_v ? -INFINITY : lg;
+        if (track) segp[it.n_seg] = zero_v ? -INFINITY : log(sqrt(sr * sr + si * si)) + lg;
       }
-      if (aborted) W.res_log[slot] = NAN;
     }
-    if (!grid_sync(P.bar, P.bar + 1, P.timeout_ns)) alive = false;
   }
   if (!alive && tid == 0) atomicOr(&W.counters[2], int(BAR_TIMEOUT_FLAG));
   tc_fence_before();
@@ -787,16 +1019,17 @@ int format_big_blocks(const HostModel& h, const double* d_blk, void* out, const 
 }
 
 size_t big_scratch_bytes(const HostModel& h, int max_ops, int grid) {
+  (void)grid;
   int dmax = h.max_dim;
   const size_t zf = size_t((dmax + BM - 1) / BM * BM) * size_t(2 * ((dmax + BK - 1) / BK * BK));
-  return 4 * zf * 4 + 256 + size_t(max_ops + 2) * (4 + 8) + size_t(2 * grid) * 8 + 1024;
+  return 4 * zf * 4 + 256 + 2 * row_state_bytes(max_ops) + 1024;
 }
 
 static int big_stages(int prec) { return prec == CTQ_TF32 ? 4 : 2; }
 
-static size_t big_smem(int prec, int nst) {
+static size_t big_smem(int prec, int nst, int max_ops) {
   const size_t stages = size_t(nst) * (prec == CTQ_TF32 ? 1 : 2) * (A_BYTES + B_BYTES);
-  return std::max(stages, size_t(PVEC) * 4) + PVEC * 4;  // the stages also hold q_s
+  return std::max(stages, size_t(PVEC) * 4) + big_table_bytes(max_ops);  // the stages also hold p_s
 }
 
 template <int PREC>
@@ -810,7 +1043,7 @@ static cudaError_t big_attr(size_t smem) {
 int prepare_eval_big(int prec, int num_sms, LaunchCfg* lc) {
   lc->threads = BG_THREADS;
   lc->num_sms = num_sms;
-  lc->smem = big_smem(prec, big_stages(prec));
+  lc->smem = big_smem(prec, big_stages(prec), 256);
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
@@ -846,17 +1079,11 @@ int launch_eval_big(const DevModel& M, const LaunchCfg& lc, BigParams P, const B
   s += 4 * P.zfloats * 4;
   P.bar = reinterpret_cast<unsigned*>(s);
   s += 256;
-  P.ekey = reinterpret_cast<int*>(s);
-  s += size_t(cfg.max_ops + 2) * 4;
-  s = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(s) + 7) & ~uintptr_t(7));
-  P.fr = reinterpret_cast<double*>(s);
-  s += size_t(cfg.max_ops + 2) * 8;
-  P.part = reinterpret_cast<double*>(s);
-  s += size_t(2 * grid) * 8;
-  P.abort_flag = reinterpret_cast<int*>(s);
+  s = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(s) + 255) & ~uintptr_t(255));
+  P.state = reinterpret_cast<unsigned char*>(s);
   P.nst = cfg.stages > 0 ? cfg.stages : big_stages(P.prec);
-  P.order = cfg.tile_order;
-  const size_t smem = big_smem(P.prec, P.nst);
+  P.order = cfg.tile_order == 0 ? 1 : cfg.tile_order - 1;  // tile_coords codes; row-major by default
+  const size_t smem = big_smem(P.prec, P.nst, cfg.max_ops);
   if (P.nst < 2 || P.nst > MAX_NST || smem > size_t(lc.smem_optin)) return CTQ_ERR_UNSUPPORTED;
   if (cudaMemsetAsync(W.counters, 0, 256, st) != cudaSuccess) return CTQ_ERR_CUDA;
   if (cudaMemsetAsync(P.bar, 0, 256, st) != cudaSuccess) return CTQ_ERR_CUDA;

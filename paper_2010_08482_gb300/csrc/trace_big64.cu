@@ -451,7 +451,7 @@ int launch_eval_big64(const DevModel& M, const LaunchCfg& lc, Big64Params P, con
   P.part = reinterpret_cast<double*>(s);
   s += size_t(2 * grid) * 8;
   P.abort_flag = reinterpret_cast<int*>(s);
-  P.order = cfg.tile_order;
+  P.order = cfg.tile_order == 0 ? 0 : cfg.tile_order - 1;  // tile_coords codes; column-major by default
   if (cudaMemsetAsync(W.counters, 0, 256, st) != cudaSuccess) return CTQ_ERR_CUDA;
   if (cudaMemsetAsync(P.bar, 0, 256, st) != cudaSuccess) return CTQ_ERR_CUDA;
   mark(0);

@@ -62,7 +62,7 @@ def test_tuning_keys_marshalled():
 
 
 @pytest.mark.parametrize("bad", [{"threads_per_cta": 48}, {"threads_per_cta": 512}, {"stages": 1},
-                                 {"tile_order": 3}, {"ctas_per_sm": -1}])
+                                 {"tile_order": 4}, {"ctas_per_sm": -1}])
 def test_out_of_range_tuning_rejected_before_any_launch(imps, bad):
     """The tuning fields are validated on the host before anything else of
     the call (a host-only impurity would otherwise fail for lack of a device
