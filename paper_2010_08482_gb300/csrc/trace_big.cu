@@ -3,8 +3,8 @@
 //
 // One (chain, q0) item is evaluated at a time by the whole GPU: a persistent
 // cooperative kernel (one CTA per SM) walks the items of the work list and,
-// for each, the operators of its string; a bounded grid barrier separates
-// the operators.  The chain runs transposed, Z_i = Y_i^T (d0 x d_i),
+// for each, the operators of its string.  The chain runs transposed,
+// Z_i = Y_i^T (d0 x d_i),
 //     Z_{i+1} = Z_i F_{i+1}^T P_{i+1},
 // with complex numbers in the real embedding
 //     [Re Z' | Im Z'] = [Re Z | Im Z] [[Re F, -Im F], [Im F, Re F]]^T,
@@ -18,17 +18,18 @@
 // bf16, with FP32 accumulation in tensor memory (a 128 x 256 tile: two
 // accumulators fill the 512 columns, chunks alternate between them).  The
 // epilogue applies the propagator column scale e^{-dtau (E - E_min)} (times
-// the power-of-two rescale of the previous operator), reduces max|Z| and
-// ||Z||_F over the grid, splits hi/lo and writes Z_{i+1} tiles.  Tiles are
-// visited column-major by default so that a B tile is read from HBM once
-// per product and reused from L2 by all row tiles.  The first operator only
-// scales F_1; the last one needs only the diagonal of F_n Y (FP32 products,
-// FP64 sum).  Log scale, exponents, segment bounds and the trace stay in
-// float64.
+// the power-of-two rescale of the previous operator, one per 128-row tile),
+// reduces max|Z| and ||Z||_F per row tile, splits hi/lo and writes Z_{i+1}
+// tiles.  A row of Z belongs to one initial state and rows never mix, so the
+// products of a string are scheduled tile by tile with row-tile
+// dependencies instead of a grid barrier per operator (see k_trace_big).
+// The first operator only scales F_1; the last one needs only the diagonal
+// of F_n Y (FP32 products, FP64 sum).  Log scale, exponents, segment bounds
+// and the trace stay in float64.
 //
-// Every wait is bounded (mbarriers and the grid barrier) by the caller's
-// timeout: on expiry the kernel records CTQ_ERR_TIMEOUT in the workspace,
-// stops, frees its tensor memory and returns.
+// Every wait is bounded (mbarriers, row-tile flags and the grid barrier) by
+// the caller's timeout: on expiry the kernel records CTQ_ERR_TIMEOUT in the
+// workspace, stops, frees its tensor memory and returns.
 #include <algorithm>
 #include <cstring>
 
