@@ -35,7 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # --precision names and their ctq precision codes (ctq.FP64 = 0, TF32 = 1, BF16X3 = 2, TF32X3 = 3).
-PRECISIONS = {"fp64": 0, "tf32": 1, "bf16x3": 2, "tf32x3": 3}
+PRECISIONS = {"fp64": 0, "tf32": 1, "bf16x3": 2, "tf32x3": 3, "f32x2": 4}
 METRIC = "local-trace evals/s and TFLOP/s vs peak, FP64 vs mixed at stated error, 1×GB300"
 WORKLOAD_TEXT = {
     "t2g": "3-orbital t2g Kanamori (6 spin-orbitals, Fock dim 64, 16 (N_dn,N_up) sectors, blocks<=9), "
@@ -426,7 +426,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="t2g", choices=sorted(WORKLOAD_TEXT))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "tf32x3", "bf16x3"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "tf32x3", "bf16x3", "f32x2"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--chains", type=int, default=0, help="evaluate only the first N chains of the workload")
     ap.add_argument("--no-autotune", action="store_true", help="library-default launch configuration")
@@ -538,6 +538,7 @@ def main():
     trace_ms = statistics.mean(kern_ms[1])
     value = world * batch.n_chains / (ms * 1e-3)
     fp64_peak = ctq.probe_fma_rate(local, 0)
+    fp32_rate = ctq.probe_fma_rate(local, 1) if args.precision == "f32x2" else None
     achieved_tf = flops / (trace_ms * 1e-3) / 1e12
     big = imp.is_complex or imp.max_dim > 112
     # ncu DRAM counters are committed for the shared-memory FP64 kernel only
@@ -555,7 +556,8 @@ def main():
         "vs_baseline": None,
         "dtype": {"fp64": "f64", "tf32": "tf32 (fp32 accumulate, f64 log scale)",
                   "tf32x3": "3xtf32 (fp32 accumulate, f64 log scale)",
-                  "bf16x3": "3xbf16 (fp32 accumulate, f64 log scale)"}[args.precision],
+                  "bf16x3": "3xbf16 (fp32 accumulate, f64 log scale)",
+                  "f32x2": "two-float f32 pairs (~48-bit products, f64 propagators and log scale)"}[args.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT[args.workload] + (f" (first {batch.n_chains} chains)" if args.chains else ""),
                    "n_chains": batch.n_chains,
@@ -566,7 +568,7 @@ def main():
         "tflops": flops / (ms * 1e-3) / 1e12,
         "algorithmic_flops_per_step": flops,
         "kernel_ms": {"plan": statistics.mean(kern_ms[0]), "trace": trace_ms, "combine": statistics.mean(kern_ms[2])},
-        "roofline": roofline(args.precision, achieved_tf, fp64_peak, traffic, big=big),
+        "roofline": roofline(args.precision, achieved_tf, fp64_peak, traffic, big=big, fp32_rate=fp32_rate),
         "e2e": {"value": world * batch.n_chains / (e2e * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * launches,
@@ -586,11 +588,25 @@ def main():
         dist.destroy_process_group()
 
 
-def roofline(precision, achieved_tf, fp64_peak, traffic, big=False):
+# FP32 instructions per two-float multiply-add of the product loop
+# (trace_fp64.cu): df_fma is one FMUL, three FFMA and eight FADD / FSUB, and
+# the accumulator is renormalised (three FADD / FSUB) every four terms.
+F32X2_INSTR_PER_FMA = 12.75
+
+
+def roofline(precision, achieved_tf, fp64_peak, traffic, big=False, fp32_rate=None):
     """Roofline of the dominant kernel: the FP64 pipe for the FP64 path
-    (measured FMA rate), the tensor pipe of the operand type for the mixed
-    paths: measured bf16 dense peak for bf16 operands, x 1/2 (the nominal
-    TF32:BF16 ratio) for tf32 operands."""
+    (measured FMA rate), the FP32 pipe for the two-float path (measured FP32
+    FMA rate / 12.75 instructions per two-float multiply-add, in
+    FP64-equivalent flops), the tensor pipe of the operand type for the mixed paths: measured
+    bf16 dense peak for bf16 operands, x 1/2 (the nominal TF32:BF16 ratio)
+    for tf32 operands."""
+    if precision == "f32x2":
+        peak = fp32_rate / F32X2_INSTR_PER_FMA / 1e12
+        return {"kernel": "k_trace<f32x2>", "bound": "alu", "achieved": achieved_tf, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved_tf / peak,
+                "peak_source": "measured FP32 FMA rate (ctq_probe_fma_rate, this run) / 12.75 FP32 "
+                               "instructions per two-float multiply-add", "traffic": traffic}
     if precision == "fp64":
         return {"kernel": "k_trace_big64<fp64>" if big else "k_trace<fp64>", "bound": "alu", "achieved": achieved_tf, "peak": fp64_peak / 1e12,
                 "unit": "TFLOP/s", "frac": achieved_tf / (fp64_peak / 1e12),

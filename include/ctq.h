@@ -73,6 +73,8 @@ extern "C" {
 #define CTQ_TF32 1   /* tensor-core TF32 products, FP32 accumulation             */
 #define CTQ_BF16X3 2 /* three-term bf16 split products, FP32 accumulation        */
 #define CTQ_TF32X3 3 /* three-term tf32 split products, FP32 accumulation        */
+#define CTQ_F32X2 4  /* two-float (hi + lo float32, ~48-bit) products on the FP32
+                        pipe; propagators, log scale and final sum in float64   */
 
 /*
  * Local-Hamiltonian parameters (Eq. ImpurityHamiltonian, Sec. 2.1):
@@ -184,6 +186,8 @@ typedef struct {
  *   small-block kernel, any other impurity with blocks <= 3072 states the
  *   large-block kernel (complex blocks in their real embedding).  CTQ_BF16X3
  *   (bf16 hi / lo operands, hi*hi + hi*lo + lo*hi) runs on both kernels.
+ *   CTQ_F32X2 runs the float64 shared-memory kernel with two-float block
+ *   products (impurities whose two largest blocks fit in shared memory).
  *   Other combinations: CTQ_ERR_UNSUPPORTED.
  * lazy: 1 = stop a chain as soon as its upper bound falls below its threshold
  *   (needs log_threshold).  segment: operators per bound refinement (>= 1).
@@ -195,7 +199,7 @@ typedef struct {
  * debug_flags: 0, or CTQ_DEBUG_STALL_WAIT (test of the timeout path).
  * Launch tuning (0 everywhere = library defaults; the package's autotuner
  * picks them per impurity, precision and batch shape):
- *   threads_per_cta: FP64 kernel, 32 to 256 in steps of 32;
+ *   threads_per_cta: FP64 and two-float kernel, 32 to 512 in steps of 32;
  *   ctas_per_sm: upper bound on the resident CTAs per SM of the FP64 and
  *     small-block trace kernels;
  *   stages: large-block kernel pipeline stages, >= 2 and as many as fit in

@@ -45,7 +45,7 @@ def candidates(imp: "ctq.Impurity", precision: int) -> List[Dict[str, int]]:
     eng = engine(imp, precision)
     out: List[Dict[str, int]] = [{}]
     if eng == "fp64":
-        for threads in (32, 64, 128, 256):
+        for threads in (32, 64, 128, 256, 512):
             if threads < 32 * ((imp.max_dim + 31) // 32):
                 continue  # fewer threads than rows of the largest block
             for cap in (0, 8, 4):

@@ -153,6 +153,19 @@ int upload_model(ctq_impurity* imp) {
     free_device(imp);
     return fail(st, "cannot configure the trace kernel");
   }
+  if (ctq::fp64_shared_kernel_fits(d, imp->optin)) {
+    // two-float copy of the blocks for CTQ_F32X2: hi = fl(x), lo = fl(x - hi)
+    std::vector<float> bx(2 * blk.size());
+    for (size_t i = 0; i < blk.size(); ++i) {
+      const float hi = float(blk[i]);
+      bx[2 * i] = hi;
+      bx[2 * i + 1] = float(blk[i] - double(hi));
+    }
+    if ((st = upload_vec(imp, bx, &d.blk_x2)) != CTQ_OK) {
+      free_device(imp);
+      return fail(st, "device upload failed");
+    }
+  }
   if (!h.is_complex && h.max_dim <= 112) {
     std::vector<unsigned char> tcb, tcb16;
     std::vector<int64_t> tco, tco16;
@@ -483,6 +496,7 @@ static int n_seg_of(const ctq_eval_opts* o) {
 }
 
 static size_t big_extra(const ctq_impurity* imp, const ctq_eval_opts* opts) {
+  if (opts->precision == CTQ_F32X2) return 0;
   if (opts->precision == CTQ_FP64)
     return imp->big64 ? ctq::big64_scratch_bytes(imp->host, std::max(0, opts->max_ops), imp->num_sms) + 256 : 0;
   if (!imp->big) return 0;
@@ -552,6 +566,7 @@ int ctq_trace_kernel(const ctq_impurity* imp, int precision) {
   if (!imp) return CTQ_ERR_ARG;
   if (imp->device < 0) return CTQ_ERR_ARG;
   if (precision == CTQ_FP64) return imp->big64 ? CTQ_KERNEL_FP64_LARGE : CTQ_KERNEL_FP64_SHARED;
+  if (precision == CTQ_F32X2) return imp->dev.blk_x2 ? CTQ_KERNEL_FP64_SHARED : CTQ_ERR_UNSUPPORTED;
   if (precision != CTQ_TF32 && precision != CTQ_TF32X3 && precision != CTQ_BF16X3) return CTQ_ERR_UNSUPPORTED;
   if (imp->big) return CTQ_KERNEL_TC_LARGE;
   const ctq::LaunchCfg& lc = precision == CTQ_TF32     ? imp->launch_tc1
@@ -563,7 +578,7 @@ int ctq_trace_kernel(const ctq_impurity* imp, int precision) {
 int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_eval_opts* opts,
                     const ctq_result* result, void* workspace, size_t workspace_bytes, void* stream) {
   if (!imp || !batch || !opts || !result) return fail(CTQ_ERR_ARG, "null argument");
-  if (opts->threads_per_cta < 0 || opts->threads_per_cta > 256 || opts->threads_per_cta % 32 != 0 ||
+  if (opts->threads_per_cta < 0 || opts->threads_per_cta > 512 || opts->threads_per_cta % 32 != 0 ||
       opts->ctas_per_sm < 0 || opts->stages < 0 || opts->stages == 1 || opts->tile_order < 0 || opts->tile_order > 3)
     return fail(CTQ_ERR_ARG, "launch tuning out of range");
   if (imp->device < 0) return fail(CTQ_ERR_ARG, "impurity has no device copy");
@@ -575,12 +590,14 @@ int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_e
   if (opts->segment < 1 || opts->max_ops < 0) return fail(CTQ_ERR_ARG, "segment < 1 or max_ops < 0");
   if (opts->lazy && !batch->log_threshold) return fail(CTQ_ERR_ARG, "lazy evaluation needs thresholds");
   if (opts->precision != CTQ_FP64 && opts->precision != CTQ_TF32 && opts->precision != CTQ_TF32X3 &&
-      opts->precision != CTQ_BF16X3)
+      opts->precision != CTQ_BF16X3 && opts->precision != CTQ_F32X2)
     return fail(CTQ_ERR_UNSUPPORTED, "unknown precision");
   const int pr = opts->precision;
+  if (pr == CTQ_F32X2 && !imp->dev.blk_x2)
+    return fail(CTQ_ERR_UNSUPPORTED, "CTQ_F32X2 needs the shared-memory trace kernel (two blocks of the largest sector in shared memory)");
   const ctq::TcParams& tcp = pr == CTQ_TF32 ? imp->tc1 : pr == CTQ_BF16X3 ? imp->tc2 : imp->tc3;
   const ctq::LaunchCfg& tcl = pr == CTQ_TF32 ? imp->launch_tc1 : pr == CTQ_BF16X3 ? imp->launch_tc2 : imp->launch_tc3;
-  if (pr != CTQ_FP64 && !imp->big && tcl.per_sm < 1)
+  if (pr != CTQ_FP64 && pr != CTQ_F32X2 && !imp->big && tcl.per_sm < 1)
     return fail(CTQ_ERR_UNSUPPORTED, "no tensor-core path for this impurity");
   if (!workspace) return fail(CTQ_ERR_ARG, "null workspace");
   if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return fail(CTQ_ERR_ARG, "workspace not 256-byte aligned");
@@ -605,7 +622,10 @@ int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_e
   // Bounds are norms (no cancellation), so their relative error is about
   // n u for n products: TF32 (u = 2^-11, n <= 400) and 3xTF32 (u ~ 2^-22).
   // BF16X3 keeps 16 significant bits (u ~ 2^-16).
+  // CTQ_F32X2 takes the bound's norm from the high float words (relative
+  // error ~ 2^-24 per element).
   cfg.margin = opts->precision == CTQ_FP64     ? 1e-9
+               : opts->precision == CTQ_F32X2  ? 1e-5
                : opts->precision == CTQ_TF32   ? 0.5
                : opts->precision == CTQ_BF16X3 ? 5e-2
                                                : 1e-2;
@@ -622,8 +642,9 @@ int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_e
     char* scratch = static_cast<char*>(workspace) + ((base + 255) & ~size_t(255));
     st = ctq::launch_eval_big64(imp->dev, imp->launch_b64, P, B, cfg, W, result, scratch, stream,
                                 opts->timing_events);
-  } else if (opts->precision == CTQ_FP64) {
-    st = ctq::launch_eval_fp64(imp->dev, imp->launch, B, cfg, W, result, stream, opts->timing_events);
+  } else if (opts->precision == CTQ_FP64 || opts->precision == CTQ_F32X2) {
+    st = ctq::launch_eval_fp64(imp->dev, imp->launch, B, cfg, W, result, stream, opts->timing_events,
+                               opts->precision == CTQ_F32X2);
   } else if (imp->big) {
     ctq::BigParams P = pr == CTQ_TF32 ? imp->big1 : pr == CTQ_BF16X3 ? imp->big2 : imp->big3;
     const ctq::LaunchCfg& lc = pr == CTQ_TF32 ? imp->launch_big1 : pr == CTQ_BF16X3 ? imp->launch_big2 : imp->launch_big3;

@@ -73,6 +73,7 @@ struct DevModel {
   const int* s;         // [n_alpha * n_sec]
   const int64_t* blk_off;  // [n_alpha * n_sec]  element offsets, -1 absent
   const double* blk;    // real: re; complex: interleaved (re, im)
+  const float* blk_x2;  // two-float copy of blk (hi, lo per real number; CTQ_F32X2), nullptr if absent
   const double* log_norm;  // [n_alpha * n_sec]  log ||F||_2 (-inf absent)
   // distinct values of E_rel per sector (bitwise equal states share one
   // propagator entry): level values, per-sector offsets, state -> level
@@ -225,6 +226,6 @@ int launch_eval_tc(const DevModel& M, const LaunchCfg& lc, const TcParams& P, co
                    const EvalCfg& cfg, const Work& W, const ctq_result* R, void* stream, void* const* events);
 int prepare_eval_fp64(const DevModel& M, int num_sms, LaunchCfg* lc);
 int launch_eval_fp64(const DevModel& M, const LaunchCfg& lc, const BatchView& B, const EvalCfg& cfg,
-                     const Work& W, const ctq_result* R, void* stream, void* const* events);
+                     const Work& W, const ctq_result* R, void* stream, void* const* events, bool x2 = false);
 
 }  // namespace ctq

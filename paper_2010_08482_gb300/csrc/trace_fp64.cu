@@ -36,15 +36,38 @@ using namespace dev;
 
 // ----------------------------------------------------------------------- trace
 
-template <bool CPLX>
+// Two-float numbers (CTQ_F32X2): x = hi + lo with two float32 words, about
+// 48 significant bits, multiplied and added on the FP32 pipe with the
+// error-free transformations of Dekker (the product's rounding error as
+// fmaf(a, b, -a b)) and Knuth (TwoSum).  The complex form keeps (re, im).
+struct DF {
+  float hi, lo;
+};
+struct __align__(16) CDF {
+  DF re, im;
+};
+
+template <bool CPLX, bool X2>
 struct Scalar;
 template <>
-struct Scalar<false> {
+struct Scalar<false, false> {
   using T = double;
+  using PT = double;  // propagator entry
 };
 template <>
-struct Scalar<true> {
+struct Scalar<true, false> {
   using T = double2;
+  using PT = double;
+};
+template <>
+struct Scalar<false, true> {
+  using T = DF;
+  using PT = DF;
+};
+template <>
+struct Scalar<true, true> {
+  using T = CDF;
+  using PT = DF;
 };
 
 __device__ __forceinline__ double sq(double v) { return v * v; }
@@ -69,6 +92,101 @@ __device__ __forceinline__ void zero(double2& v) { v = make_double2(0.0, 0.0); }
 __device__ __forceinline__ int exp_key(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
 __device__ __forceinline__ int exp_key(double2 v) { return max(exp_key(v.x), exp_key(v.y)); }
 
+// ---- two-float arithmetic (no contraction: every step is an explicit
+// round-to-nearest intrinsic)
+__device__ __forceinline__ DF df_split(double x) {
+  const float h = __double2float_rn(x);
+  return DF{h, __double2float_rn(x - double(h))};
+}
+__device__ __forceinline__ double df_val(DF a) { return double(a.hi) + double(a.lo); }
+__device__ __forceinline__ double2 df_val(CDF a) { return make_double2(df_val(a.re), df_val(a.im)); }
+__device__ __forceinline__ double df_val(double a) { return a; }
+__device__ __forceinline__ double2 df_val(double2 a) { return a; }
+// acc += f y: the product's and the sum's rounding errors are gathered in
+// acc.lo, which df_finish folds back (renormalisation) once per output.
+__device__ __forceinline__ void df_fma(DF& acc, float fh, float fl, DF y) {
+  const float p = __fmul_rn(fh, y.hi);
+  float e = __fmaf_rn(fh, y.hi, -p);
+  e = __fmaf_rn(fh, y.lo, e);
+  e = __fmaf_rn(fl, y.hi, e);
+  const float s = __fadd_rn(acc.hi, p);
+  const float bp = __fsub_rn(s, acc.hi);
+  const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+  acc.hi = s;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, e));
+}
+constexpr int X2_RENORM = 4;  // two-float terms between renormalisations
+__device__ __forceinline__ void fma_acc(DF& acc, DF f, DF y) { df_fma(acc, f.hi, f.lo, y); }
+__device__ __forceinline__ void fma_acc(CDF& acc, CDF f, CDF y) {
+  df_fma(acc.re, f.re.hi, f.re.lo, y.re);
+  df_fma(acc.re, -f.im.hi, -f.im.lo, y.im);
+  df_fma(acc.im, f.re.hi, f.re.lo, y.im);
+  df_fma(acc.im, f.im.hi, f.im.lo, y.re);
+}
+__device__ __forceinline__ void df_norm(DF& a) {
+  const float s = __fadd_rn(a.hi, a.lo);
+  a.lo = __fsub_rn(a.lo, __fsub_rn(s, a.hi));
+  a.hi = s;
+}
+__device__ __forceinline__ void finish(DF& a) { df_norm(a); }
+// a += b for normalised two-float numbers (TwoSum of the high words, low
+// words added to its error, renormalised)
+__device__ __forceinline__ void add_into(DF& a, DF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bp = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bp)), __fsub_rn(b.hi, bp));
+  a.hi = s;
+  a.lo = __fadd_rn(err, __fadd_rn(a.lo, b.lo));
+  df_norm(a);
+}
+__device__ __forceinline__ void add_into(CDF& a, CDF b) {
+  add_into(a.re, b.re);
+  add_into(a.im, b.im);
+}
+__device__ __forceinline__ void finish(CDF& a) {
+  df_norm(a.re);
+  df_norm(a.im);
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const float s = __fadd_rn(p, e);
+  return DF{s, __fsub_rn(e, __fsub_rn(s, p))};
+}
+__device__ __forceinline__ DF operator*(DF a, DF b) { return df_mul(a, b); }
+__device__ __forceinline__ CDF operator*(DF a, CDF b) { return CDF{df_mul(a, b.re), df_mul(a, b.im)}; }
+__device__ __forceinline__ DF operator*(double a, DF b) { return df_mul(df_split(a), b); }
+__device__ __forceinline__ CDF operator*(double a, CDF b) { return df_split(a) * b; }
+__device__ __forceinline__ void zero(DF& v) { v = DF{0.f, 0.f}; }
+__device__ __forceinline__ void zero(CDF& v) { v = CDF{DF{0.f, 0.f}, DF{0.f, 0.f}}; }
+// exponent key on the float64 scale (bias 1023), so that the rescale logic
+// is shared: 0 for a zero or subnormal high word
+__device__ __forceinline__ int exp_key(DF v) {
+  const int f = (__float_as_int(v.hi) >> 23) & 0xff;
+  return f ? f + (1023 - 127) : 0;
+}
+__device__ __forceinline__ int exp_key(CDF v) { return max(exp_key(v.re), exp_key(v.im)); }
+__device__ __forceinline__ double sq(DF v) { return double(__fmul_rn(v.hi, v.hi)); }
+__device__ __forceinline__ double sq(CDF v) { return double(__fmaf_rn(v.re.hi, v.re.hi, __fmul_rn(v.im.hi, v.im.hi))); }
+
+// block element i: float64 blocks, or their two-float copy
+__device__ __forceinline__ double load_el(const DevModel& M, int64_t i, double) { return __ldg(M.blk + i); }
+__device__ __forceinline__ double2 load_el(const DevModel& M, int64_t i, double2) {
+  return __ldg(reinterpret_cast<const double2*>(M.blk) + i);
+}
+__device__ __forceinline__ DF load_el(const DevModel& M, int64_t i, DF) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(M.blk_x2) + i);
+  return DF{v.x, v.y};
+}
+__device__ __forceinline__ CDF load_el(const DevModel& M, int64_t i, CDF) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(M.blk_x2) + i);
+  return CDF{DF{v.x, v.y}, DF{v.z, v.w}};
+}
+__device__ __forceinline__ double to_prop(double x, double) { return x; }
+__device__ __forceinline__ DF to_prop(double x, DF) { return df_split(x); }
+
 // Block-wide max of an int; every thread gets the result.  redi: 32 ints.
 __device__ __forceinline__ int block_max_int(int v, int* redi) {
   v = __reduce_max_sync(0xffffffffu, v);
@@ -85,9 +203,13 @@ __device__ __forceinline__ int block_max_int(int v, int* redi) {
 // PRE: every propagator value of the chain is computed in one dense pass at
 // the start of an item (lanes over all (operator, state) pairs), which keeps
 // the FP64 pipe busy with full warps; used when max_ops * max_dim fits.
-template <bool CPLX, bool PRE>
-__global__ void __launch_bounds__(256, 1) k_trace(DevModel M, BatchView B, EvalCfg cfg, Work W) {
-  using T = typename Scalar<CPLX>::T;
+// X2: two-float products (CTQ_F32X2); propagators, log scale and the
+// final diagonal stay in float64.
+template <bool CPLX, bool PRE, bool X2>
+__global__ void __launch_bounds__(512, 1) k_trace(DevModel M, BatchView B, EvalCfg cfg, Work W) {
+  using T = typename Scalar<CPLX, X2>::T;
+  using T64 = typename Scalar<CPLX, false>::T;
+  using PT = typename Scalar<CPLX, X2>::PT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int D = M.max_dim;
   const int MO = max(cfg.max_ops, 1);
@@ -95,6 +217,7 @@ __global__ void __launch_bounds__(256, 1) k_trace(DevModel M, BatchView B, EvalC
   T* Ybuf0 = reinterpret_cast<T*>(smem_raw);
   T* Ybuf1 = Ybuf0 + size_t(D) * D;
   double* p = reinterpret_cast<double*>(Ybuf1 + size_t(D) * D);  // [D] propagator of the current step
+  PT* pp = reinterpret_cast<PT*>(p);  // the same, in the product's format (8 bytes either way)
   double* p0 = p + D;                                            // [D] wrap-around propagator (columns)
   double* red = p0 + D;                                          // [64] reductions
   double* segL = red + 64;                                       // [NS] log scale at segment ends
@@ -151,7 +274,7 @@ __global__ void __launch_bounds__(256, 1) k_trace(DevModel M, BatchView B, EvalC
       double vr = 0.0, vi = 0.0, mx = 0.0;
       for (int j = tid; j < d0; j += nt) {
         const double pj = exp(-t1 * E0[j]) * exp(-t2 * E0[j]);
-        const T f = load_blk(M.blk, off + int64_t(j) * d0 + j, T());
+        const T64 f = load_blk(M.blk, off + int64_t(j) * d0 + j, T64());
         if constexpr (CPLX) {
           vr += f.x * pj;
           vi += f.y * pj;
@@ -235,7 +358,7 @@ __global__ void __launch_bounds__(256, 1) k_trace(DevModel M, BatchView B, EvalC
       const int tot = dcur * d0;
       for (int idx = tid; idx < tot; idx += nt) {
         const int m = idx / d0, j = idx - m * d0;
-        const T v = (p1[m] * p0[j]) * load_blk(M.blk, off + idx, T());
+        const T v = (p1[m] * p0[j]) * load_el(M, off + idx, T());
         Y[idx] = v;
         ekey = max(ekey, exp_key(v));
       }
@@ -307,8 +430,8 @@ __global__ void __launch_bounds__(256, 1) k_trace(DevModel M, BatchView B, EvalC
         const int tot = d0 * dcur;
         for (int idx = tid; idx < tot; idx += nt) {
           const int j = idx / dcur, k = idx - j * dcur;
-          const T f = load_blk(M.blk, off + idx, T());
-          const T y = Y[k * d0 + j];
+          const T64 f = load_blk(M.blk, off + idx, T64());
+          const T64 y = df_val(Y[k * d0 + j]);
           if constexpr (CPLX) {
             vr += f.x * y.x - f.y * y.y;
             vi += f.x * y.y + f.y * y.x;
@@ -341,11 +464,11 @@ __global__ void __launch_bounds__(256, 1) k_trace(DevModel M, BatchView B, EvalC
       if (PRE) {
         const double* pi = pall + poff[i];
         const int* lv = M.lev_idx + M.E_off[qb];
-        for (int m = tid; m < db; m += nt) p[m] = pi[lv[m]] * scale;
+        for (int m = tid; m < db; m += nt) pp[m] = to_prop(pi[lv[m]] * scale, PT());
       } else {
         const double dt = B.tau[a0 + i + 1] - B.tau[a0 + i];
         const double* Eb = M.E_rel + M.E_off[qb];
-        for (int m = tid; m < db; m += nt) p[m] = exp(-dt * Eb[m]) * scale;
+        for (int m = tid; m < db; m += nt) pp[m] = to_prop(exp(-dt * Eb[m]) * scale, PT());
       }
       __syncthreads();
       // Yn[m][j] = p[m] * sum_k F[m][k] Y[k][j]
@@ -358,8 +481,30 @@ __global__ void __launch_bounds__(256, 1) k_trace(DevModel M, BatchView B, EvalC
         T acc;
         zero(acc);
         const int64_t frow = off + int64_t(m) * dcur;
-        for (int k = 0; k < dcur; ++k) fma_acc(acc, load_blk(M.blk, frow + k, T()), Y[k * d0 + j]);
-        const T v = p[m] * acc;
+        if constexpr (X2) {
+          // two independent accumulators (even and odd terms: the FP32 add
+          // chains of one output overlap), each renormalised every
+          // X2_RENORM terms so that its low word holds a few ulps of the
+          // high word and rounds at ~2^-48 of the sum per term
+          T acc2;
+          zero(acc2);
+          int k = 0;
+          for (; k + 2 * X2_RENORM <= dcur; k += 2 * X2_RENORM) {
+#pragma unroll
+            for (int u = 0; u < 2 * X2_RENORM; u += 2) {
+              fma_acc(acc, load_el(M, frow + k + u, T()), Y[(k + u) * d0 + j]);
+              fma_acc(acc2, load_el(M, frow + k + u + 1, T()), Y[(k + u + 1) * d0 + j]);
+            }
+            finish(acc);
+            finish(acc2);
+          }
+          for (; k < dcur; ++k) fma_acc(acc, load_el(M, frow + k, T()), Y[k * d0 + j]);
+          finish(acc);
+          add_into(acc, acc2);
+        } else {
+          for (int k = 0; k < dcur; ++k) fma_acc(acc, load_el(M, frow + k, T()), Y[k * d0 + j]);
+        }
+        const T v = pp[m] * acc;
         Yn[idx] = v;
         ekey = max(ekey, exp_key(v));
         if (seg_next) f2 += sq(v);
@@ -417,12 +562,14 @@ static bool use_pre(int max_dim, int max_ops) { return size_t(std::max(max_ops, 
 
 // Raise the dynamic shared-memory cap to the opt-in maximum minus the
 // kernel's static shared memory.
-template <bool CPLX, bool PRE>
-static int set_attr(int optin) {
+template <bool CPLX, bool PRE, bool X2>
+static int set_attr(int optin, int* regs) {
   cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, k_trace<CPLX, PRE>) != cudaSuccess) return CTQ_ERR_CUDA;
+  if (cudaFuncGetAttributes(&fa, k_trace<CPLX, PRE, X2>) != cudaSuccess) return CTQ_ERR_CUDA;
+  *regs = std::max(*regs, fa.numRegs);
   const int cap = optin - int(fa.sharedSizeBytes);
-  return cudaFuncSetAttribute(k_trace<CPLX, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) == cudaSuccess
+  return cudaFuncSetAttribute(k_trace<CPLX, PRE, X2>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) ==
+                 cudaSuccess
              ? CTQ_OK
              : CTQ_ERR_CUDA;
 }
@@ -444,26 +591,30 @@ int prepare_eval_fp64(const DevModel& M, int num_sms, LaunchCfg* lc) {
     return CTQ_ERR_CUDA;
   lc->smem_optin = optin;
   if ((st = prepare_plan(optin)) != CTQ_OK) return st;
-  if ((st = set_attr<false, false>(optin)) || (st = set_attr<false, true>(optin)) ||
-      (st = set_attr<true, false>(optin)) || (st = set_attr<true, true>(optin)))
+  int regs = 0;  // the largest of all variants sizes the resident CTAs
+  if ((st = set_attr<false, false, false>(optin, &regs)) || (st = set_attr<false, true, false>(optin, &regs)) ||
+      (st = set_attr<true, false, false>(optin, &regs)) || (st = set_attr<true, true, false>(optin, &regs)) ||
+      (st = set_attr<false, false, true>(optin, &regs)) || (st = set_attr<false, true, true>(optin, &regs)) ||
+      (st = set_attr<true, false, true>(optin, &regs)) || (st = set_attr<true, true, true>(optin, &regs)))
     return st;
-  cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, k_trace<true, true>) != cudaSuccess) return CTQ_ERR_CUDA;
-  lc->regs = fa.numRegs;
+  lc->regs = regs;
   return CTQ_OK;
 }
 
 int launch_eval_fp64(const DevModel& M, const LaunchCfg& lc, const BatchView& B, const EvalCfg& cfg,
-                     const Work& W, const ctq_result* R, void* stream, void* const* events) {
+                     const Work& W, const ctq_result* R, void* stream, void* const* events, bool x2) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (B.n_chains == 0) return CTQ_OK;
+  if (x2 && M.blk_x2 == nullptr) return CTQ_ERR_UNSUPPORTED;
   if (lc.per_sm < 1) return CTQ_ERR_UNSUPPORTED;
   const bool pre = use_pre(M.max_dim, cfg.max_ops);
   const size_t smem = trace_smem(M.max_dim, M.is_complex != 0, cfg.max_ops, cfg.n_seg_max, pre);
   if (smem + 1024 > size_t(lc.smem_optin)) return CTQ_ERR_UNSUPPORTED;
   // resident CTAs per SM from shared memory, registers and the 32-CTA
   // limit, optionally capped by the caller's launch tuning
-  const int threads = cfg.threads > 0 ? cfg.threads : lc.threads;
+  // the two-float products are FP32 add chains: blocks above 32 states get
+  // 16 warps per CTA to hide their latency (float64 needs no more than 8)
+  const int threads = cfg.threads > 0 ? cfg.threads : (x2 && lc.threads == 256 ? 512 : lc.threads);
   int per_sm = int((228 * 1024) / (smem + 1024));
   per_sm = std::min(per_sm, 65536 / std::max(1, lc.regs * threads));
   per_sm = std::min(per_sm, std::min(32, 2048 / threads));
@@ -482,12 +633,19 @@ int launch_eval_fp64(const DevModel& M, const LaunchCfg& lc, const BatchView& B,
   long long max_items = (long long)B.n_chains * M.n_sec;
   long long grid = (long long)lc.num_sms * per_sm;
   if (grid > max_items) grid = max_items;
-  if (M.is_complex) {
-    if (pre) k_trace<true, true><<<int(grid), threads, smem, st>>>(M, B, cfg, W);
-    else k_trace<true, false><<<int(grid), threads, smem, st>>>(M, B, cfg, W);
+  const dim3 g{unsigned(grid)}, b{unsigned(threads)};
+  if (x2 && M.is_complex) {
+    if (pre) k_trace<true, true, true><<<g, b, smem, st>>>(M, B, cfg, W);
+    else k_trace<true, false, true><<<g, b, smem, st>>>(M, B, cfg, W);
+  } else if (x2) {
+    if (pre) k_trace<false, true, true><<<g, b, smem, st>>>(M, B, cfg, W);
+    else k_trace<false, false, true><<<g, b, smem, st>>>(M, B, cfg, W);
+  } else if (M.is_complex) {
+    if (pre) k_trace<true, true, false><<<g, b, smem, st>>>(M, B, cfg, W);
+    else k_trace<true, false, false><<<g, b, smem, st>>>(M, B, cfg, W);
   } else {
-    if (pre) k_trace<false, true><<<int(grid), threads, smem, st>>>(M, B, cfg, W);
-    else k_trace<false, false><<<int(grid), threads, smem, st>>>(M, B, cfg, W);
+    if (pre) k_trace<false, true, false><<<g, b, smem, st>>>(M, B, cfg, W);
+    else k_trace<false, false, false><<<g, b, smem, st>>>(M, B, cfg, W);
   }
   if (cudaGetLastError() != cudaSuccess) return CTQ_ERR_CUDA;
   mark(2);

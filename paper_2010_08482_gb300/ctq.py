@@ -29,7 +29,7 @@ DEBUG_STALL_WAIT = 1
 KANAMORI, SLATER = 0, 1
 MU_GIVEN, MU_PH_SYMMETRIC = 0, 1
 SECTORS_N_SZ, SECTORS_N = 0, 1
-FP64, TF32, BF16X3, TF32X3 = 0, 1, 2, 3
+FP64, TF32, BF16X3, TF32X3, F32X2 = 0, 1, 2, 3, 4
 
 
 class CtqError(RuntimeError):

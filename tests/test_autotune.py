@@ -30,7 +30,7 @@ def test_candidates_start_with_default_and_are_unique(imps):
         for x in c:
             assert set(x) <= set(ctq.TUNE_KEYS)
             if "threads_per_cta" in x:
-                assert x["threads_per_cta"] % 32 == 0 and 32 <= x["threads_per_cta"] <= 256
+                assert x["threads_per_cta"] % 32 == 0 and 32 <= x["threads_per_cta"] <= 512
     assert autotune.candidates(imps["t2g"], ctq.TF32X3) == [{}]  # one CTA per SM, nothing to choose
     assert {"ctas_per_sm": 1} in autotune.candidates(imps["t2g"], ctq.BF16X3)
 
@@ -61,7 +61,7 @@ def test_tuning_keys_marshalled():
         ctq._opts(ctq.FP64, tune={"warps": 2})
 
 
-@pytest.mark.parametrize("bad", [{"threads_per_cta": 48}, {"threads_per_cta": 512}, {"stages": 1},
+@pytest.mark.parametrize("bad", [{"threads_per_cta": 48}, {"threads_per_cta": 544}, {"stages": 1},
                                  {"tile_order": 4}, {"ctas_per_sm": -1}])
 def test_out_of_range_tuning_rejected_before_any_launch(imps, bad):
     """The tuning fields are validated on the host before anything else of
