@@ -119,10 +119,13 @@ int upload_model(ctq_impurity* imp) {
   } else {
     blk = h.blk_re;
   }
+  std::vector<double> log_dim(h.dims.size());
+  for (size_t q = 0; q < log_dim.size(); ++q) log_dim[q] = std::log(double(h.dims[q]));
   std::vector<double> lognorm(h.opnorm.size());
   for (size_t i = 0; i < lognorm.size(); ++i) lognorm[i] = h.opnorm[i] > 0 ? std::log(h.opnorm[i]) : -INFINITY;
   int st = CTQ_OK;
-  if ((st = upload_vec(imp, h.dims, &d.dims)) || (st = upload_vec(imp, h.E_off, &d.E_off)) ||
+  if ((st = upload_vec(imp, h.dims, &d.dims)) || (st = upload_vec(imp, log_dim, &d.log_dim)) ||
+      (st = upload_vec(imp, h.E_off, &d.E_off)) ||
       (st = upload_vec(imp, e_rel, &d.E_rel)) || (st = upload_vec(imp, e_relf, &d.E_relf)) ||
       (st = upload_vec(imp, h.E_min, &d.E_min)) ||
       (st = upload_vec(imp, h.s, &d.s)) || (st = upload_vec(imp, h.blk_off, &d.blk_off)) ||

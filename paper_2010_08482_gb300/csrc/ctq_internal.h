@@ -66,6 +66,7 @@ struct DevModel {
   int n_flav, n_alpha, n_sec, max_dim, is_complex;
   double E_ref;         // reference energy (E_gs); logs are kept relative to -beta E_ref
   const int* dims;      // [n_sec]
+  const double* log_dim;  // [n_sec]  log(dims[q]) (rank factor of the bounds, no device logarithm)
   const int* E_off;     // [n_sec + 1]
   const double* E_rel;  // [sum dims]  E_q,j - E_min(q)  (>= 0)
   const float* E_relf;  // [sum dims]  the same in float32 (mixed-precision propagators)

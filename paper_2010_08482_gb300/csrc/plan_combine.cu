@@ -60,12 +60,13 @@ __global__ void __launch_bounds__(128) k_plan(DevModel M, BatchView B, EvalCfg c
   for (int base = 0; base < ns; base += 32) {
     const int q0 = base + lane;
     bool alive = q0 < ns;
-    int q = q0, r = alive ? M.dims[q0] : 0;
+    int q = q0, r = alive ? M.dims[q0] : 0, qr = q0;  // qr: a sector of the smallest dimension r
     if (alive) {
       for (int i = 0; i < n; ++i) {
         q = M.s[B.op[a0 + i] * ns + q];
         if (q < 0) { alive = false; break; }
-        r = min(r, M.dims[q]);
+        const int dq = M.dims[q];
+        if (dq < r) { r = dq; qr = q; }
         mine[i] = static_cast<unsigned char>(q);
       }
       alive = alive && (q == q0);
@@ -93,8 +94,8 @@ __global__ void __launch_bounds__(128) k_plan(DevModel M, BatchView B, EvalCfg c
       acc = warp_sum(acc);
       const int rs = __shfl_sync(FULL, r, src);
       if (lane == src) {
-        const double b = (n == 0) ? (log(double(M.dims[qs])) - B.beta * (M.E_min[qs] - M.E_ref))
-                                  : (log(double(rs)) - t_wrap * (M.E_min[qs] - M.E_ref) + acc);
+        const double b = (n == 0) ? (M.log_dim[qs] - B.beta * (M.E_min[qs] - M.E_ref))
+                                  : (M.log_dim[qr] - t_wrap * (M.E_min[qs] - M.E_ref) + acc);
         const size_t slot = size_t(c) * ns + qs;
         Item it;
         it.c = c;
@@ -153,6 +154,18 @@ __global__ void __launch_bounds__(128) k_plan(DevModel M, BatchView B, EvalCfg c
 
 // ----------------------------------------------------------------------- combine
 
+// GB300 runs float64 at 1/64 of the float32 rate, so the per-chain
+// bookkeeping below avoids float64 work that integer operations can do:
+// -inf tests on the bit pattern, exponents from the exponent field.
+__device__ __forceinline__ bool is_neg_inf(double x) {
+  return __double_as_longlong(x) == static_cast<long long>(0xFFF0000000000000ull);
+}
+// floor(log2 a) for a > 0 (ilogb for subnormal a)
+__device__ __forceinline__ int exp_of(double a) {
+  const int f = int((__double_as_longlong(a) >> 52) & 0x7ff);
+  return f ? f - 1023 : ilogb(a);
+}
+
 __global__ void k_combine(DevModel M, BatchView B, EvalCfg cfg, Work W, ctq_result R) {
   const int lane = threadIdx.x & 31;
   const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -190,9 +203,9 @@ __global__ void k_combine(DevModel M, BatchView B, EvalCfg cfg, Work W, ctq_resu
   for (int q = lane; q < ns; q += 32) {
     const size_t slot = size_t(c) * ns + q;
     const double lg = W.res_log[slot];
-    if (lg == -INFINITY) continue;
+    if (is_neg_inf(lg)) continue;
     const double a = fabs(W.res_val[2 * slot]) + fabs(W.res_val[2 * slot + 1]);
-    if (a > 0.0) lm = fmax(lm, lg + double(ilogb(a)) * LN2);
+    if (a > 0.0) lm = fmax(lm, lg + double(exp_of(a)) * LN2);
   }
   lm = warp_max(lm);
   double sr = 0.0, si = 0.0;
@@ -200,11 +213,11 @@ __global__ void k_combine(DevModel M, BatchView B, EvalCfg cfg, Work W, ctq_resu
     for (int q = lane; q < ns; q += 32) {
       const size_t slot = size_t(c) * ns + q;
       const double lg = W.res_log[slot];
-      if (lg == -INFINITY) continue;
+      if (is_neg_inf(lg)) continue;
       const double vr = W.res_val[2 * slot], vi = W.res_val[2 * slot + 1];
       const double a = fabs(vr) + fabs(vi);
       if (a == 0.0) continue;
-      const int ea = ilogb(a);
+      const int ea = exp_of(a);
       const double f = (lg + double(ea) * LN2 == lm) ? scalbn(1.0, -ea) : exp(lg - lm);
       sr += vr * f;
       si += vi * f;
@@ -224,8 +237,13 @@ __global__ void k_combine(DevModel M, BatchView B, EvalCfg cfg, Work W, ctq_resu
     } else {
       const double la = (lm + log(a)) + shift;
       R.log_abs[c] = la;
-      R.phase[2 * c] = sr / a;
-      R.phase[2 * c + 1] = si / a;
+      if (M.is_complex) {
+        R.phase[2 * c] = sr / a;
+        R.phase[2 * c + 1] = si / a;
+      } else {  // the sign, without a float64 division
+        R.phase[2 * c] = copysign(1.0, sr);
+        R.phase[2 * c + 1] = 0.0;
+      }
       if (cfg.has_thr) st = (la >= B.log_threshold[c]) ? CTQ_CHAIN_ACCEPTED : CTQ_CHAIN_REJECTED;
     }
     R.status[c] = st;
@@ -240,9 +258,9 @@ __global__ void k_combine(DevModel M, BatchView B, EvalCfg cfg, Work W, ctq_resu
       int cnt = 0;
       for (int q = 0; q < ns; ++q) {
         const size_t slot = size_t(c) * ns + q;
-        if (W.lvl0[slot] == -INFINITY) continue;
+        if (is_neg_inf(W.lvl0[slot])) continue;
         const double v = W.seg[slot * size_t(nb) + ss];
-        if (v == -INFINITY) continue;
+        if (is_neg_inf(v)) continue;
         ++cnt;
         if (v > m2) { s2 = (cnt == 1) ? 1.0 : s2 * exp(m2 - v) + 1.0; m2 = v; }
         else s2 += exp(v - m2);
