@@ -114,12 +114,21 @@ struct Item {
   int r;         // min over the string of the sector dimension (rank bound)
   int n_seg;     // ceil(n / S)
   double t_all;  // sum of log ||F_i||_2 and -dtau (E_min - E_ref) over the string (plan kernel)
+  float cost;    // work estimate: d0 sum_i d_i d_{i+1} + PLAN_OP_COST n (orders the work list)
 };
+
+// Work-list ordering: strings are pulled in decreasing order of their cost
+// estimate, in ORDER_CLASSES classes of 1/8 octave (counting sort).
+constexpr int ORDER_CLASSES = 512;
+constexpr int ORDER_HIST = 64;         // first counter of the class histogram
+constexpr size_t COUNTER_BYTES = 4096;  // counters region, cleared before every evaluation
 
 // Views of the caller's workspace.
 struct Work {
-  int* counters;   // [0] n_items, [1] next item, [2] device error bits
-  Item* items;     // [C * n_sec]
+  int* counters;   // [0] n_items, [1] next item, [2] device error bits, [3] estimator next item,
+                   // [4] plan CTAs done, [ORDER_HIST + k] strings of cost class k
+  Item* items;     // [2 C n_sec] staging slots per (c, q0), then the compacted list
+  int* order;      // [C * n_sec] list position -> compacted item, most expensive first
   double* res_val; // [C * n_sec * 2]  scaled trace value (re, im)
   // All logs below are relative: the true value carries an extra e^{-beta E_ref}.
   double* res_log; // [C * n_sec]      log scale of res_val (-inf: zero)

@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(256) k_rho(DevModel M, BatchView B, EvalCfg cf
     __syncthreads();
     const int it_idx = s_item;
     if (it_idx >= n_items) break;
-    const Item it = items[it_idx];
+    const Item it = items[W.order[it_idx]];
     const int c = it.c, q0 = it.q0;
     const int a0 = B.offsets[c];
     const int n = B.offsets[c + 1] - a0;

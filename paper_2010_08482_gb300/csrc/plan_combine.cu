@@ -25,7 +25,18 @@ using namespace dev;
 // only and keep the visited sectors in shared memory (one byte per operator,
 // PLAN_MAX_OPS per lane), so that the float64 sums of a surviving string are
 // then taken by the whole warp with lanes over operators.
-__global__ void __launch_bounds__(128) k_plan(DevModel M, BatchView B, EvalCfg cfg, Work W) {
+// Work of one operator besides its block product (rescale, propagators,
+// reductions), in multiply-adds, for the ordering of the work list.
+constexpr float PLAN_OP_COST = 200.f;
+
+// Cost class of a string, 0 = most expensive: 1/8-octave steps of the float
+// cost (its exponent and top three mantissa bits) from 2^7 upward.
+__device__ __forceinline__ int order_class(float cost) {
+  const int key = (__float_as_int(fmaxf(cost, 1.f)) >> 20) - ((127 + 7) << 3);
+  return ORDER_CLASSES - 1 - min(ORDER_CLASSES - 1, max(0, key));
+}
+
+__device__ void plan_chain(const DevModel& M, const BatchView& B, const EvalCfg& cfg, const Work& W) {
   extern __shared__ unsigned char plan_paths[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -61,12 +72,16 @@ __global__ void __launch_bounds__(128) k_plan(DevModel M, BatchView B, EvalCfg c
     const int q0 = base + lane;
     bool alive = q0 < ns;
     int q = q0, r = alive ? M.dims[q0] : 0, qr = q0;  // qr: a sector of the smallest dimension r
+    float cw = 0.f;  // sum over the block products of d_i d_{i+1}
     if (alive) {
+      int dprev = r;
       for (int i = 0; i < n; ++i) {
         q = M.s[B.op[a0 + i] * ns + q];
         if (q < 0) { alive = false; break; }
         const int dq = M.dims[q];
         if (dq < r) { r = dq; qr = q; }
+        if (i >= 1 && i <= n - 2) cw += float(dprev) * float(dq);
+        dprev = dq;
         mine[i] = static_cast<unsigned char>(q);
       }
       alive = alive && (q == q0);
@@ -93,6 +108,7 @@ __global__ void __launch_bounds__(128) k_plan(DevModel M, BatchView B, EvalCfg c
       }
       acc = warp_sum(acc);
       const int rs = __shfl_sync(FULL, r, src);
+      const float cws = __shfl_sync(FULL, cw, src);
       if (lane == src) {
         const double b = (n == 0) ? (M.log_dim[qs] - B.beta * (M.E_min[qs] - M.E_ref))
                                   : (M.log_dim[qr] - t_wrap * (M.E_min[qs] - M.E_ref) + acc);
@@ -103,6 +119,7 @@ __global__ void __launch_bounds__(128) k_plan(DevModel M, BatchView B, EvalCfg c
         it.r = rs;
         it.n_seg = (n + cfg.S - 1) / cfg.S;
         it.t_all = acc;
+        it.cost = float(M.dims[qs]) * cws + PLAN_OP_COST * float(n);
         W.items[slot] = it;  // staging copy in the (c, q0) slot
         W.lvl0[slot] = b;
         W.live[slot] = b;
@@ -147,9 +164,77 @@ __global__ void __launch_bounds__(128) k_plan(DevModel M, BatchView B, EvalCfg c
     first = __shfl_sync(FULL, first, 0);
     if (alive) {
       const int pos = first + __popc(mask & ((1u << lane) - 1u));
-      W.items[size_t(B.n_chains) * ns + pos] = W.items[size_t(c) * ns + q0];
+      const Item it = W.items[size_t(c) * ns + q0];
+      W.items[size_t(B.n_chains) * ns + pos] = it;
+      atomicAdd(&W.counters[ORDER_HIST + order_class(it.cost)], 1);
     }
   }
+}
+
+// Orders the compacted work list by decreasing cost estimate (counting sort
+// over the class histogram the plan CTAs built; one CTA of 128 threads): the
+// persistent trace kernels pull strings through W.order, so the longest start
+// first and the short ones fill the tail.
+constexpr int PLAN_THREADS = 128;
+static_assert(ORDER_CLASSES == 4 * PLAN_THREADS, "four classes per thread in the prefix sum");
+
+__device__ void order_items(const Work& W, size_t cs) {
+  __shared__ int off_s[ORDER_CLASSES];
+  __shared__ int part_s[PLAN_THREADS];
+  const int tid = threadIdx.x;
+  const int n = *((volatile int*)&W.counters[0]);
+  int loc[4], sum = 0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    loc[u] = __ldcg(&W.counters[ORDER_HIST + 4 * tid + u]);
+    sum += loc[u];
+  }
+  part_s[tid] = sum;
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+    for (int t = 0; t < PLAN_THREADS; ++t) {
+      const int v = part_s[t];
+      part_s[t] = acc;
+      acc += v;
+    }
+  }
+  __syncthreads();
+  int acc = part_s[tid];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    off_s[4 * tid + u] = acc;
+    acc += loc[u];
+  }
+  __syncthreads();
+  const Item* list = W.items + cs;
+  for (int i0 = tid; i0 < n; i0 += 4 * PLAN_THREADS) {  // four independent loads in flight
+    float cst[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * PLAN_THREADS;
+      cst[u] = (i < n) ? __ldcg(&list[i].cost) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * PLAN_THREADS;
+      if (i < n) W.order[atomicAdd(&off_s[order_class(cst[u])], 1)] = i;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(PLAN_THREADS) k_plan(DevModel M, BatchView B, EvalCfg cfg, Work W) {
+  plan_chain(M, B, cfg, W);
+  // the last CTA to finish orders the work list (no wait: it is simply the
+  // one whose arrival completes the count)
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(&W.counters[4], 1) == int(gridDim.x) - 1) ? 1 : 0;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  order_items(W, size_t(B.n_chains) * M.n_sec);
 }
 
 // ----------------------------------------------------------------------- combine
@@ -283,10 +368,10 @@ int prepare_plan(int optin) {
 // k_plan keeps one byte per operator per lane (4 warps of 32 lanes per CTA).
 int launch_plan(const DevModel& M, const BatchView& B, const EvalCfg& cfg, const Work& W, cudaStream_t st) {
   if (M.n_sec > 255) return CTQ_ERR_UNSUPPORTED;
-  const size_t smem = size_t(128) * size_t(cfg.max_ops > 0 ? cfg.max_ops : 1);
+  const size_t smem = size_t(PLAN_THREADS) * size_t(cfg.max_ops > 0 ? cfg.max_ops : 1);
   if (smem > 200 * 1024) return CTQ_ERR_UNSUPPORTED;  // max_ops <= 1600
   const int grid = (B.n_chains + 3) / 4;
-  k_plan<<<grid, 128, smem, st>>>(M, B, cfg, W);
+  k_plan<<<grid, PLAN_THREADS, smem, st>>>(M, B, cfg, W);
   return cudaGetLastError() == cudaSuccess ? CTQ_OK : CTQ_ERR_CUDA;
 }
 
@@ -307,7 +392,7 @@ size_t workspace_layout(int n_chains, int n_sec, int n_seg_max, void* base, Work
     off += align(bytes);
     return p;
   };
-  char* counters = take(256);
+  char* counters = take(COUNTER_BYTES);
   char* items = take(2 * cs * sizeof(Item));  // staging slots + compacted list
   char* res_val = take(2 * cs * sizeof(double));
   char* res_log = take(cs * sizeof(double));
@@ -315,6 +400,7 @@ size_t workspace_layout(int n_chains, int n_sec, int n_seg_max, void* base, Work
   char* lvl0 = take(cs * sizeof(double));
   char* seg = take(cs * size_t(n_seg_max + 1) * sizeof(double));
   char* flags = take(size_t(n_chains) * sizeof(int));
+  char* order = take(cs * sizeof(int));
   if (w) {
     w->counters = reinterpret_cast<int*>(counters);
     w->items = reinterpret_cast<Item*>(items);
@@ -324,6 +410,7 @@ size_t workspace_layout(int n_chains, int n_sec, int n_seg_max, void* base, Work
     w->lvl0 = reinterpret_cast<double*>(lvl0);
     w->seg = reinterpret_cast<double*>(seg);
     w->chain_flag = reinterpret_cast<int*>(flags);
+    w->order = reinterpret_cast<int*>(order);
   }
   return off;
 }

@@ -151,6 +151,18 @@ __device__ __forceinline__ uint32_t bf16_bits(float x) {
   return (u + 0x7fffu + ((u >> 16) & 1u)) >> 16;
 }
 __device__ __forceinline__ float bf16_val(uint32_t b) { return __uint_as_float(b << 16); }
+// Two floats to packed bf16 (round to nearest even, the same as bf16_bits
+// for finite values), a in the low half: one cvt for two elements.
+__device__ __forceinline__ uint32_t bf16x2_rn(float a, float b) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+  return r;
+}
+// hi = bf16(x), lo = bf16(x - hi) for a pair, each packed as bf16x2.
+__device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  hi = bf16x2_rn(a, b);
+  lo = bf16x2_rn(a - __uint_as_float(hi << 16), b - __uint_as_float(hi & 0xffff0000u));
+}
 
 
 // D[tmem] (+)= A[smem desc] * B[smem desc]

@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
   int par = 0;  // state copy of the current string
 
   for (int it_idx = 0; it_idx < n_items && alive; ++it_idx) {
-    const Item it = items[it_idx];
+    const Item it = items[W.order[it_idx]];
     const int c = it.c, q0 = it.q0;
     const size_t slot = size_t(c) * ns + q0;
     const int a0 = B.offsets[c];
@@ -716,18 +716,35 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
             constexpr int PER16 = 16 / EB;
 #pragma unroll
             for (int g = 0; g < 16 / PER16; ++g) {
-              T hi[PER16], lo[PER16];
-#pragma unroll
-              for (int t2 = 0; t2 < PER16; ++t2) {
-                const int cc = c0 + PER16 * g + t2;
-                const float x = acc[cc] * __shfl_sync(0xffffffffu, preg[cc >> 5], cc & 31);
-                ek = max(ek, (__float_as_int(x) >> 23) & 0xff);
-                f2 += x * x;
-                split_store<PREC>(x, hi[t2], lo[t2]);
-              }
               const size_t o = tiled_off<EB>(row, d.nt * BN + cb + PER16 * g, BM, nkz);
-              *reinterpret_cast<uint4*>(Oh + o) = pack16<PREC>(hi);
-              if (SPLIT) *reinterpret_cast<uint4*>(Ol + o) = pack16<PREC>(lo);
+              if constexpr (PREC == CTQ_BF16X3) {  // pairs through one packed conversion
+                float xs[PER16];
+#pragma unroll
+                for (int t2 = 0; t2 < PER16; ++t2) {
+                  const int cc = c0 + PER16 * g + t2;
+                  const float x = acc[cc] * __shfl_sync(0xffffffffu, preg[cc >> 5], cc & 31);
+                  ek = max(ek, (__float_as_int(x) >> 23) & 0xff);
+                  f2 += x * x;
+                  xs[t2] = x;
+                }
+                uint32_t hv[4], lv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) split_bf16x2(xs[2 * u], xs[2 * u + 1], hv[u], lv[u]);
+                *reinterpret_cast<uint4*>(Oh + o) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                *reinterpret_cast<uint4*>(Ol + o) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+              } else {
+                T hi[PER16], lo[PER16];
+#pragma unroll
+                for (int t2 = 0; t2 < PER16; ++t2) {
+                  const int cc = c0 + PER16 * g + t2;
+                  const float x = acc[cc] * __shfl_sync(0xffffffffu, preg[cc >> 5], cc & 31);
+                  ek = max(ek, (__float_as_int(x) >> 23) & 0xff);
+                  f2 += x * x;
+                  split_store<PREC>(x, hi[t2], lo[t2]);
+                }
+                *reinterpret_cast<uint4*>(Oh + o) = pack16<PREC>(hi);
+                if (SPLIT) *reinterpret_cast<uint4*>(Ol + o) = pack16<PREC>(lo);
+              }
             }
           }
           ek = __reduce_max_sync(0xffffffffu, ek);
@@ -1086,7 +1103,7 @@ int launch_eval_big(const DevModel& M, const LaunchCfg& lc, BigParams P, const B
   P.order = cfg.tile_order == 0 ? 1 : cfg.tile_order - 1;  // tile_coords codes; row-major by default
   const size_t smem = big_smem(P.prec, P.nst, cfg.max_ops);
   if (P.nst < 2 || P.nst > MAX_NST || smem > size_t(lc.smem_optin)) return CTQ_ERR_UNSUPPORTED;
-  if (cudaMemsetAsync(W.counters, 0, 256, st) != cudaSuccess) return CTQ_ERR_CUDA;
+  if (cudaMemsetAsync(W.counters, 0, COUNTER_BYTES, st) != cudaSuccess) return CTQ_ERR_CUDA;
   if (cudaMemsetAsync(P.bar, 0, 256, st) != cudaSuccess) return CTQ_ERR_CUDA;
   if (cudaMemsetAsync(P.zbuf, 0, 4 * P.zfloats * 4, st) != cudaSuccess) return CTQ_ERR_CUDA;
   mark(0);

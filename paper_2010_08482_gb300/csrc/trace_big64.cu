@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(B64_THREADS, 1)
   double* Z[2] = {P.zbuf, P.zbuf + P.zelems};
 
   for (int it_idx = 0; it_idx < n_items && alive; ++it_idx) {
-    const Item it = items[it_idx];
+    const Item it = items[W.order[it_idx]];
     const int c = it.c, q0 = it.q0;
     const size_t slot = size_t(c) * ns + q0;
     const int a0 = B.offsets[c];
@@ -452,7 +452,7 @@ int launch_eval_big64(const DevModel& M, const LaunchCfg& lc, Big64Params P, con
   s += size_t(2 * grid) * 8;
   P.abort_flag = reinterpret_cast<int*>(s);
   P.order = cfg.tile_order == 0 ? 0 : cfg.tile_order - 1;  // tile_coords codes; column-major by default
-  if (cudaMemsetAsync(W.counters, 0, 256, st) != cudaSuccess) return CTQ_ERR_CUDA;
+  if (cudaMemsetAsync(W.counters, 0, COUNTER_BYTES, st) != cudaSuccess) return CTQ_ERR_CUDA;
   if (cudaMemsetAsync(P.bar, 0, 256, st) != cudaSuccess) return CTQ_ERR_CUDA;
   mark(0);
   {

@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(512, 1) k_trace(DevModel M, BatchView B, EvalC
     __syncthreads();
     const int it_idx = s_item;
     if (it_idx >= n_items) break;
-    const Item it = items[it_idx];
+    const Item it = items[W.order[it_idx]];
     const int c = it.c, q0 = it.q0;
     const size_t slot = size_t(c) * ns + q0;
     const int a0 = B.offsets[c];
@@ -623,7 +623,7 @@ int launch_eval_fp64(const DevModel& M, const LaunchCfg& lc, const BatchView& B,
   auto mark = [&](int i) {
     if (events) cudaEventRecord(static_cast<cudaEvent_t>(events[i]), st);
   };
-  if (cudaMemsetAsync(W.counters, 0, 256, st) != cudaSuccess) return CTQ_ERR_CUDA;
+  if (cudaMemsetAsync(W.counters, 0, COUNTER_BYTES, st) != cudaSuccess) return CTQ_ERR_CUDA;
   mark(0);
   {
     const int ps = launch_plan(M, B, cfg, W, st);

@@ -77,12 +77,7 @@ __device__ __forceinline__ void store_a16(uint32_t tAh, uint32_t tAl, int c0, co
   if constexpr (PREC == CTQ_BF16X3) {
     uint32_t hi[8], lo[8];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      const uint32_t h0 = bf16_bits(x[2 * t]), h1 = bf16_bits(x[2 * t + 1]);
-      const uint32_t l0 = bf16_bits(x[2 * t] - bf16_val(h0)), l1 = bf16_bits(x[2 * t + 1] - bf16_val(h1));
-      hi[t] = h0 | (h1 << 16);
-      lo[t] = l0 | (l1 << 16);
-    }
+    for (int t = 0; t < 8; ++t) split_bf16x2(x[2 * t], x[2 * t + 1], hi[t], lo[t]);
     tmem_st8(tAh + uint32_t(c0 / 2), hi);
     tmem_st8(tAl + uint32_t(c0 / 2), lo);
   } else {
@@ -230,7 +225,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     const int it_idx = S.item;
     if (it_idx >= n_items || S.fail) break;
-    const Item it = items[it_idx];
+    const Item it = items[W.order[it_idx]];
     const int c = it.c, q0 = it.q0;
     const size_t slot = size_t(c) * ns + q0;
     const int a0 = B.offsets[c];
@@ -741,7 +736,7 @@ int launch_eval_tc(const DevModel& M, const LaunchCfg& lc, const TcParams& P, co
   auto mark = [&](int i) {
     if (events) cudaEventRecord(static_cast<cudaEvent_t>(events[i]), st);
   };
-  if (cudaMemsetAsync(W.counters, 0, 256, st) != cudaSuccess) return CTQ_ERR_CUDA;
+  if (cudaMemsetAsync(W.counters, 0, COUNTER_BYTES, st) != cudaSuccess) return CTQ_ERR_CUDA;
   mark(0);
   {
     const int ps = launch_plan(M, B, cfg, W, st);
