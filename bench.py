@@ -603,7 +603,8 @@ def roofline(precision, achieved_tf, fp64_peak, traffic, big=False, fp32_rate=No
     for tf32 operands."""
     if precision == "f32x2":
         peak = fp32_rate / F32X2_INSTR_PER_FMA / 1e12
-        return {"kernel": "k_trace<f32x2>", "bound": "alu", "achieved": achieved_tf, "peak": peak,
+        return {"kernel": "k_trace_big64<f32x2>" if big else "k_trace<f32x2>", "bound": "alu",
+                "achieved": achieved_tf, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved_tf / peak,
                 "peak_source": "measured FP32 FMA rate (ctq_probe_fma_rate, this run) / 12.75 FP32 "
                                "instructions per two-float multiply-add", "traffic": traffic}

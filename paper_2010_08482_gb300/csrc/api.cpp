@@ -259,19 +259,28 @@ int upload_model(ctq_impurity* imp) {
         off[i] = int64_t(total);
         total += ctq::big64_block_elems(h.dims[h.s[i]], h.dims[q]);
       }
+    // and the same as two-float pairs (CTQ_F32X2), 8 bytes per element too
     void* bt = nullptr;
+    void* bx = nullptr;
     if (cudaMalloc(&bt, std::max<size_t>(total, 1) * sizeof(double)) != cudaSuccess) {
       free_device(imp);
       return fail(CTQ_ERR_NOMEM, "cannot allocate the float64 large-block operands");
     }
     imp->allocs.push_back(bt);
-    if ((st = ctq::format_big64_blocks(h, d.blk, static_cast<double*>(bt), off)) != CTQ_OK ||
+    if (cudaMalloc(&bx, std::max<size_t>(total, 1) * 2 * sizeof(float)) != cudaSuccess) {
+      free_device(imp);
+      return fail(CTQ_ERR_NOMEM, "cannot allocate the two-float large-block operands");
+    }
+    imp->allocs.push_back(bx);
+    if ((st = ctq::format_big64_blocks(h, d.blk, bt, off, false)) != CTQ_OK ||
+        (st = ctq::format_big64_blocks(h, d.blk, bx, off, true)) != CTQ_OK ||
         (st = upload_vec(imp, off, &imp->b64.bt_off)) != CTQ_OK ||
         (st = ctq::prepare_eval_big64(imp->num_sms, &imp->launch_b64)) != CTQ_OK) {
       free_device(imp);
       return fail(st, "float64 large-block setup failed");
     }
     imp->b64.bt = static_cast<const double*>(bt);
+    imp->b64.bt_x2 = static_cast<const float*>(bx);
     imp->big64 = true;
   }
   return CTQ_OK;
@@ -499,8 +508,7 @@ static int n_seg_of(const ctq_eval_opts* o) {
 }
 
 static size_t big_extra(const ctq_impurity* imp, const ctq_eval_opts* opts) {
-  if (opts->precision == CTQ_F32X2) return 0;
-  if (opts->precision == CTQ_FP64)
+  if (opts->precision == CTQ_FP64 || opts->precision == CTQ_F32X2)
     return imp->big64 ? ctq::big64_scratch_bytes(imp->host, std::max(0, opts->max_ops), imp->num_sms) + 256 : 0;
   if (!imp->big) return 0;
   return ctq::big_scratch_bytes(imp->host, std::max(0, opts->max_ops), imp->num_sms) + 256;
@@ -569,7 +577,8 @@ int ctq_trace_kernel(const ctq_impurity* imp, int precision) {
   if (!imp) return CTQ_ERR_ARG;
   if (imp->device < 0) return CTQ_ERR_ARG;
   if (precision == CTQ_FP64) return imp->big64 ? CTQ_KERNEL_FP64_LARGE : CTQ_KERNEL_FP64_SHARED;
-  if (precision == CTQ_F32X2) return imp->dev.blk_x2 ? CTQ_KERNEL_FP64_SHARED : CTQ_ERR_UNSUPPORTED;
+  if (precision == CTQ_F32X2)
+    return imp->big64 ? CTQ_KERNEL_FP64_LARGE : imp->dev.blk_x2 ? CTQ_KERNEL_FP64_SHARED : CTQ_ERR_UNSUPPORTED;
   if (precision != CTQ_TF32 && precision != CTQ_TF32X3 && precision != CTQ_BF16X3) return CTQ_ERR_UNSUPPORTED;
   if (imp->big) return CTQ_KERNEL_TC_LARGE;
   const ctq::LaunchCfg& lc = precision == CTQ_TF32     ? imp->launch_tc1
@@ -596,8 +605,8 @@ int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_e
       opts->precision != CTQ_BF16X3 && opts->precision != CTQ_F32X2)
     return fail(CTQ_ERR_UNSUPPORTED, "unknown precision");
   const int pr = opts->precision;
-  if (pr == CTQ_F32X2 && !imp->dev.blk_x2)
-    return fail(CTQ_ERR_UNSUPPORTED, "CTQ_F32X2 needs the shared-memory trace kernel (two blocks of the largest sector in shared memory)");
+  if (pr == CTQ_F32X2 && !imp->dev.blk_x2 && !imp->big64)
+    return fail(CTQ_ERR_UNSUPPORTED, "CTQ_F32X2: no float64 kernel serves this impurity");
   const ctq::TcParams& tcp = pr == CTQ_TF32 ? imp->tc1 : pr == CTQ_BF16X3 ? imp->tc2 : imp->tc3;
   const ctq::LaunchCfg& tcl = pr == CTQ_TF32 ? imp->launch_tc1 : pr == CTQ_BF16X3 ? imp->launch_tc2 : imp->launch_tc3;
   if (pr != CTQ_FP64 && pr != CTQ_F32X2 && !imp->big && tcl.per_sm < 1)
@@ -639,12 +648,12 @@ int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_e
   cfg.stages = opts->stages;
   cfg.tile_order = opts->tile_order;
   int st;
-  if (opts->precision == CTQ_FP64 && imp->big64) {
+  if ((opts->precision == CTQ_FP64 || opts->precision == CTQ_F32X2) && imp->big64) {
     ctq::Big64Params P = imp->b64;
     P.timeout_ns = opts->timeout_ns > 0 ? uint64_t(opts->timeout_ns) : uint64_t(2000000000ull);
     char* scratch = static_cast<char*>(workspace) + ((base + 255) & ~size_t(255));
     st = ctq::launch_eval_big64(imp->dev, imp->launch_b64, P, B, cfg, W, result, scratch, stream,
-                                opts->timing_events);
+                                opts->timing_events, opts->precision == CTQ_F32X2);
   } else if (opts->precision == CTQ_FP64 || opts->precision == CTQ_F32X2) {
     st = ctq::launch_eval_fp64(imp->dev, imp->launch, B, cfg, W, result, stream, opts->timing_events,
                                opts->precision == CTQ_F32X2);

@@ -185,6 +185,7 @@ struct BigParams {
 // Per-impurity parameters and scratch of the float64 large-block path (trace_big64.cu).
 struct Big64Params {
   const double* bt = nullptr;       // embedded float64 blocks, row-major, per (alpha, q)
+  const float* bt_x2 = nullptr;     // the same as two-float pairs (CTQ_F32X2), same element offsets
   const int64_t* bt_off = nullptr;  // [n_alpha * n_sec] element offsets, -1 absent
   uint64_t timeout_ns = 0;
   double* zbuf = nullptr;           // scratch: two Z buffers
@@ -214,11 +215,12 @@ int launch_rho(const DevModel& M, int num_sms, int optin, const BatchView& B, co
                const ctq_result& R, RhoParams P, size_t rho_total_doubles, void* stream);
 
 size_t big64_block_elems(int dn, int dk);
-int format_big64_blocks(const HostModel& h, const double* d_blk, double* out, const std::vector<int64_t>& off);
+int format_big64_blocks(const HostModel& h, const double* d_blk, void* out, const std::vector<int64_t>& off, bool x2);
 size_t big64_scratch_bytes(const HostModel& h, int max_ops, int grid);
 int prepare_eval_big64(int num_sms, LaunchCfg* lc);
 int launch_eval_big64(const DevModel& M, const LaunchCfg& lc, Big64Params P, const BatchView& B, const EvalCfg& cfg,
-                      const Work& W, const ctq_result* R, void* scratch, void* stream, void* const* events);
+                      const Work& W, const ctq_result* R, void* scratch, void* stream, void* const* events,
+                      bool x2 = false);
 bool fp64_shared_kernel_fits(const DevModel& M, int optin);
 
 size_t big_block_elems(int dn, int dk);

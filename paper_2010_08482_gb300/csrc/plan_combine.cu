@@ -208,15 +208,16 @@ __device__ void order_items(const Work& W, size_t cs) {
   }
   __syncthreads();
   const Item* list = W.items + cs;
-  for (int i0 = tid; i0 < n; i0 += 4 * PLAN_THREADS) {  // four independent loads in flight
-    float cst[4];
+  constexpr int U = 8;  // independent loads in flight per thread
+  for (int i0 = tid; i0 < n; i0 += U * PLAN_THREADS) {
+    float cst[U];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int i = i0 + u * PLAN_THREADS;
       cst[u] = (i < n) ? __ldcg(&list[i].cost) : 0.f;
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int i = i0 + u * PLAN_THREADS;
       if (i < n) W.order[atomicAdd(&off_s[order_class(cst[u])], 1)] = i;
     }

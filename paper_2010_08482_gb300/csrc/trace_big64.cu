@@ -25,12 +25,14 @@
 
 #include "big_common.cuh"
 #include "device_common.cuh"
+#include "two_float.cuh"
 
 namespace ctq {
 namespace {
 
 using namespace dev;
 using namespace bigc;
+using namespace tf2;
 
 constexpr int B64_THREADS = 256;
 constexpr int TM = 128, TN = 128, TK = 16;  // C tile and K chunk (float64 elements)
@@ -48,9 +50,32 @@ struct Big64Shared {
 
 __device__ __forceinline__ int exp_key64(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
 
-template <bool CPLX>
+// Operand element of the product: float64, or (X2, CTQ_F32X2) a two-float
+// pair of the same 8 bytes.  Staging copies bytes; only the arithmetic
+// differs.
+template <bool X2>
+struct Op64;
+template <>
+struct Op64<false> {
+  using E = double;
+  static __device__ __forceinline__ E make(double x) { return x; }
+  static __device__ __forceinline__ double val(E x) { return x; }
+};
+template <>
+struct Op64<true> {
+  using E = DF;
+  static __device__ __forceinline__ E make(double x) { return df_split(x); }
+  static __device__ __forceinline__ double val(E x) { return df_val(x); }
+};
+
+// X2: the products in two-float arithmetic on the FP32 pipe (accumulators
+// renormalised every X2_RENORM K terms); propagators, log scale, bounds and
+// the final trace in float64.
+template <bool CPLX, bool X2>
 __global__ void __launch_bounds__(B64_THREADS, 1)
     k_trace_big64(DevModel M, BatchView B, EvalCfg cfg, Work W, Big64Params P) {
+  using E = typename Op64<X2>::E;
+  static_assert(sizeof(E) == 8, "operand elements are 8 bytes in both forms");
   extern __shared__ __align__(16) double dsm[];
   double* p_s = dsm;           // [PVEC64] column scales of the current product
   double* q_s = dsm + PVEC64;  // [PVEC64] wrap-around propagator of q0
@@ -76,7 +101,7 @@ __global__ void __launch_bounds__(B64_THREADS, 1)
 
   const int n_items = W.counters[0];
   const Item* items = W.items + size_t(B.n_chains) * ns;
-  double* Z[2] = {P.zbuf, P.zbuf + P.zelems};
+  E* Z[2] = {reinterpret_cast<E*>(P.zbuf), reinterpret_cast<E*>(P.zbuf) + P.zelems};
 
   for (int it_idx = 0; it_idx < n_items && alive; ++it_idx) {
     const Item it = items[W.order[it_idx]];
@@ -162,8 +187,8 @@ __global__ void __launch_bounds__(B64_THREADS, 1)
         }
         ek = max(ek, max(exp_key64(xr), exp_key64(xi)));
         f2 += xr * xr + xi * xi;
-        Z[0][size_t(j) * K2 + m] = xr;
-        Z[0][size_t(j) * K2 + dpk + m] = xi;
+        Z[0][size_t(j) * K2 + m] = Op64<X2>::make(xr);
+        Z[0][size_t(j) * K2 + dpk + m] = Op64<X2>::make(xi);
       }
       ek = __reduce_max_sync(0xffffffffu, ek);
       const double f2d = warp_sum(f2);
@@ -227,7 +252,8 @@ __global__ void __launch_bounds__(B64_THREADS, 1)
         for (long long e2 = (long long)blockIdx.x * B64_THREADS + tid; e2 < total;
              e2 += (long long)gridDim.x * B64_THREADS) {
           const int j = int(e2 / dcur), k = int(e2 - (long long)j * dcur);
-          const double zr = Z[cur][size_t(j) * K2 + k], zi = Z[cur][size_t(j) * K2 + dpk + k];
+          const double zr = Op64<X2>::val(Z[cur][size_t(j) * K2 + k]);
+          const double zi = Op64<X2>::val(Z[cur][size_t(j) * K2 + dpk + k]);
           const int64_t fe = off + int64_t(j) * dcur + k;
           const double fr_ = CPLX ? M.blk[2 * fe] : M.blk[fe];
           const double fi_ = CPLX ? M.blk[2 * fe + 1] : 0.0;
@@ -272,9 +298,10 @@ __global__ void __launch_bounds__(B64_THREADS, 1)
         prefix -= dt * (M.E_min[qb] - M.E_ref);
       }
       __syncthreads();
-      const double* Bt = P.bt + P.bt_off[idx_a];  // rup(N2, TN) x K2, row-major
-      const double* A = Z[cur];
-      double* C = Z[cur ^ 1];
+      // rup(N2, TN) x K2, row-major
+      const E* Bt = (X2 ? reinterpret_cast<const E*>(P.bt_x2) : reinterpret_cast<const E*>(P.bt)) + P.bt_off[idx_a];
+      const E* A = Z[cur];
+      E* C = Z[cur ^ 1];
       const int n_mt = dp0 / TM, n_nt = rup(N2, TN) / TN;
       const int n_tiles = n_mt * n_nt;
       int ek = 0;
@@ -282,16 +309,17 @@ __global__ void __launch_bounds__(B64_THREADS, 1)
       for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         int mt, nt;
         tile_coords(t, n_mt, n_nt, P.order, mt, nt);
-        double acc[8][8];
+        E acc[8][8];
 #pragma unroll
         for (int a = 0; a < 8; ++a)
 #pragma unroll
-          for (int b = 0; b < 8; ++b) acc[a][b] = 0.0;
-        const double* Ab = A + size_t(mt) * TM * K2;
-        const double* Bb = Bt + size_t(nt) * TN * K2;
+          for (int b = 0; b < 8; ++b) acc[a][b] = Op64<X2>::make(0.0);
+        const E* Ab = A + size_t(mt) * TM * K2;
+        const E* Bb = Bt + size_t(nt) * TN * K2;
         const int lr = tid >> 1, lk = (tid & 1) * 8;  // this thread's staging row and K half
         for (int k0 = 0; k0 < K2; k0 += TK) {
           {
+            // 16-byte copies of the operand bytes (two elements of either form)
             const double2* sa = reinterpret_cast<const double2*>(Ab + size_t(lr) * K2 + k0 + lk);
             const double2* sb = reinterpret_cast<const double2*>(Bb + size_t(lr) * K2 + k0 + lk);
 #pragma unroll
@@ -306,15 +334,30 @@ __global__ void __launch_bounds__(B64_THREADS, 1)
           __syncthreads();
 #pragma unroll
           for (int k = 0; k < TK; ++k) {
-            double av[8], bv[8];
+            E av[8], bv[8];
+            const E* as = reinterpret_cast<const E*>(&S.As[k][0]);
+            const E* bs = reinterpret_cast<const E*>(&S.Bs[k][0]);
 #pragma unroll
-            for (int a = 0; a < 8; ++a) av[a] = S.As[k][ty + 16 * a];
+            for (int a = 0; a < 8; ++a) av[a] = as[ty + 16 * a];
 #pragma unroll
-            for (int b = 0; b < 8; ++b) bv[b] = S.Bs[k][tx + 16 * b];
+            for (int b = 0; b < 8; ++b) bv[b] = bs[tx + 16 * b];
+            if constexpr (X2) {
 #pragma unroll
-            for (int a = 0; a < 8; ++a)
+              for (int a = 0; a < 8; ++a)
 #pragma unroll
-              for (int b = 0; b < 8; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+                for (int b = 0; b < 8; ++b) fma_acc(acc[a][b], av[a], bv[b]);
+              if (k % X2_RENORM == X2_RENORM - 1) {
+#pragma unroll
+                for (int a = 0; a < 8; ++a)
+#pragma unroll
+                  for (int b = 0; b < 8; ++b) finish(acc[a][b]);
+              }
+            } else {
+#pragma unroll
+              for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+            }
           }
           __syncthreads();
         }
@@ -327,10 +370,17 @@ __global__ void __launch_bounds__(B64_THREADS, 1)
 #pragma unroll
           for (int a = 0; a < 8; ++a) {
             const int row = mt * TM + ty + 16 * a;
-            const double x = acc[a][b] * ps;
-            ek = max(ek, exp_key64(x));
-            f2 = fma(x, x, f2);
-            C[size_t(row) * N2 + col] = x;
+            if constexpr (X2) {
+              const DF x = df_split(ps) * acc[a][b];
+              ek = max(ek, exp_key(x));
+              f2 += sq(x);
+              C[size_t(row) * N2 + col] = x;
+            } else {
+              const double x = acc[a][b] * ps;
+              ek = max(ek, exp_key64(x));
+              f2 = fma(x, x, f2);
+              C[size_t(row) * N2 + col] = x;
+            }
           }
         }
       }
@@ -366,7 +416,8 @@ __global__ void __launch_bounds__(B64_THREADS, 1)
 // k < 2 dpk) with
 //   n < dpn:  [Re F[n][k],  -Im F[n][k - dpk]]
 //   n >= dpn: [Im F[n - dpn][k], Re F[n - dpn][k - dpk]].
-__global__ void k_format_big64(const double* blk, int cplx, int dn, int dk, double* out) {
+template <typename OUT>
+__global__ void k_format_big64(const double* blk, int cplx, int dn, int dk, OUT* out) {
   const int dpn = rup(dn, PAD64), dpk = rup(dk, PAD64);
   const int N2 = rup(2 * dpn, TN), K2 = 2 * dpk;
   const long long total = (long long)N2 * K2;
@@ -382,7 +433,12 @@ __global__ void k_format_big64(const double* blk, int cplx, int dn, int dk, doub
       if (n < dpn) v = (k < dpk) ? re : -im;
       else v = (k < dpk) ? im : re;
     }
-    out[e] = v;
+    if constexpr (sizeof(OUT) == 8 && alignof(OUT) == 4) {  // two-float pair
+      const float hi = __double2float_rn(v);
+      out[e] = OUT{hi, __double2float_rn(v - double(hi))};
+    } else {
+      out[e] = v;
+    }
   }
 }
 
@@ -393,7 +449,8 @@ size_t big64_block_elems(int dn, int dk) {
   return size_t((2 * dpn + TN - 1) / TN * TN) * size_t(2 * dpk);
 }
 
-int format_big64_blocks(const HostModel& h, const double* d_blk, double* out, const std::vector<int64_t>& off) {
+// x2: the two-float copy (float hi, lo per element) for CTQ_F32X2.
+int format_big64_blocks(const HostModel& h, const double* d_blk, void* out, const std::vector<int64_t>& off, bool x2) {
   const int na = h.n_alpha();
   for (int a = 0; a < na; ++a)
     for (int q = 0; q < h.n_sec; ++q) {
@@ -401,7 +458,11 @@ int format_big64_blocks(const HostModel& h, const double* d_blk, double* out, co
       const int qp = h.s[i];
       if (qp < 0) continue;
       const double* src = d_blk + (h.is_complex ? 2 : 1) * h.blk_off[i];
-      k_format_big64<<<1024, 256>>>(src, h.is_complex, h.dims[qp], h.dims[q], out + off[i]);
+      if (x2)
+        k_format_big64<DF><<<1024, 256>>>(src, h.is_complex, h.dims[qp], h.dims[q], static_cast<DF*>(out) + off[i]);
+      else
+        k_format_big64<double><<<1024, 256>>>(src, h.is_complex, h.dims[qp], h.dims[q],
+                                              static_cast<double*>(out) + off[i]);
       if (cudaGetLastError() != cudaSuccess) return CTQ_ERR_CUDA;
     }
   return cudaDeviceSynchronize() == cudaSuccess ? CTQ_OK : CTQ_ERR_CUDA;
@@ -419,20 +480,21 @@ int prepare_eval_big64(int num_sms, LaunchCfg* lc) {
   lc->threads = B64_THREADS;
   lc->num_sms = num_sms;
   lc->smem = 2 * PVEC64 * sizeof(double);
-  if (cudaFuncSetAttribute(k_trace_big64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lc->smem)) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k_trace_big64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lc->smem)) !=
-          cudaSuccess)
+  const int sm = int(lc->smem);
+  if (cudaFuncSetAttribute(k_trace_big64<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess ||
+      cudaFuncSetAttribute(k_trace_big64<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess ||
+      cudaFuncSetAttribute(k_trace_big64<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess ||
+      cudaFuncSetAttribute(k_trace_big64<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess)
     return CTQ_ERR_CUDA;
   lc->per_sm = 1;
   return CTQ_OK;
 }
 
 int launch_eval_big64(const DevModel& M, const LaunchCfg& lc, Big64Params P, const BatchView& B, const EvalCfg& cfg,
-                      const Work& W, const ctq_result* R, void* scratch, void* stream, void* const* events) {
+                      const Work& W, const ctq_result* R, void* scratch, void* stream, void* const* events, bool x2) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (B.n_chains == 0) return CTQ_OK;
-  if (M.max_dim > PVEC64) return CTQ_ERR_UNSUPPORTED;
+  if (M.max_dim > PVEC64 || (x2 && P.bt_x2 == nullptr)) return CTQ_ERR_UNSUPPORTED;
   auto mark = [&](int i) {
     if (events) cudaEventRecord(static_cast<cudaEvent_t>(events[i]), st);
   };
@@ -462,7 +524,8 @@ int launch_eval_big64(const DevModel& M, const LaunchCfg& lc, Big64Params P, con
   mark(1);
   void* args[] = {const_cast<DevModel*>(&M), const_cast<BatchView*>(&B), const_cast<EvalCfg*>(&cfg),
                   const_cast<Work*>(&W), &P};
-  void* fn = M.is_complex ? (void*)k_trace_big64<true> : (void*)k_trace_big64<false>;
+  void* fn = x2 ? (M.is_complex ? (void*)k_trace_big64<true, true> : (void*)k_trace_big64<false, true>)
+               : (M.is_complex ? (void*)k_trace_big64<true, false> : (void*)k_trace_big64<false, false>);
   if (cudaLaunchCooperativeKernel(fn, grid, B64_THREADS, args, lc.smem, st) != cudaSuccess) return CTQ_ERR_CUDA;
   mark(2);
   {

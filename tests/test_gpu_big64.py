@@ -113,3 +113,59 @@ def test_f7_fp64_against_stored_oracle():
         print(f"f7 FP64 chain {c}: rel err {err:.3e}")
         assert err <= tol, (c, err)
         assert res["status"][c] == ctq.CHAIN_OK
+
+
+def run_x2(imp, batch, S=8):
+    db = ctq.DeviceBatch(batch)
+    ev = ctq.TraceEvaluator(imp, batch.n_chains, max(1, db.max_ops), precision=ctq.F32X2, segment=S)
+    ev(db)
+    torch.cuda.synchronize()
+    return ev.results(batch.n_chains)
+
+
+@pytest.mark.parametrize("name", ["dc", "dn"])
+def test_big64_two_float_parity(name, small_models):
+    """CTQ_F32X2 on the large-block kernel (two-float tiles on the FP32 pipe):
+    the two-float bar of tests/test_gpu_x2.py (1e-10 relative, or 32 x the
+    FP64 allowance of a chain that cancels internally)."""
+    m = small_models[name]
+    rng = np.random.default_rng(51)
+    b = w.random_batch(rng, m.n_flav, m.beta, 12, 1, 14, gen="g2")
+    imp = parity.load_oracle_model(ctq, m)
+    assert ctq.trace_kernel(imp, ctq.F32X2) == ctq.KERNEL_FP64_LARGE
+    res = run_x2(imp, b)
+    ref = parity.oracle_chain_results(m, b, range(b.n_chains))
+    worst = 0.0
+    for c in range(b.n_chains):
+        r = ref[c]
+        err, kind = parity.chain_error(res["log_abs"][c], res["phase"][c], r)
+        assert err <= max(1e-10, 32.0 * parity.fp64_tolerance(r)), (c, err, kind, r.get("noise"))
+        worst = max(worst, err)
+        if r["log_abs"] == -math.inf:
+            assert res["status"][c] == ctq.CHAIN_ZERO
+        else:
+            assert res["status"][c] == ctq.CHAIN_OK
+    print(f"{name} two-float large-block: worst rel err {worst:.3e}")
+
+
+def test_f7_two_float_against_stored_oracle():
+    """The library-built f shell in two-float arithmetic against the stored
+    oracle values: the eigensolver bar of the FP64 test plus the two-float
+    bar."""
+    path = os.path.join(HERE, "golden", "f7_oracle.json")
+    if not os.path.exists(path):
+        pytest.skip("tests/golden/f7_oracle.json not generated")
+    with open(path) as f:
+        g = json.load(f)
+    imp = ctq.build_impurity(w.model_f7(), device=0)
+    assert ctq.trace_kernel(imp, ctq.F32X2) == ctq.KERNEL_FP64_LARGE
+    n = 2
+    b = w.batch_f7().subset(range(n))
+    res = run_x2(imp, b)
+    tol = 2.0 * b.beta * 1e-9 + 1e-10
+    for c in range(n):
+        ref = g["chains"][c]
+        err = abs(complex(*res["phase"][c]) * math.exp(res["log_abs"][c] - ref["log_abs"]) - complex(*ref["phase"]))
+        print(f"f7 two-float chain {c}: rel err {err:.3e}")
+        assert err <= tol, (c, err)
+        assert res["status"][c] == ctq.CHAIN_OK
