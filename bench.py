@@ -246,10 +246,10 @@ def profile_traffic(kernel: str, workload: str, src_hash: str):
 
 
 def source_hash() -> str:
-    """Hash of the dominant kernel's code (trace_fp64.cu and the device
-    helpers it includes)."""
+    """Hash of the dominant kernel's code (trace_fp64.cu and the headers it
+    includes)."""
     h = hashlib.sha256()
-    for fn in ("trace_fp64.cu", "device_common.cuh"):
+    for fn in ("trace_fp64.cu", "device_common.cuh", "two_float.cuh", "ctq_internal.h"):
         with open(os.path.join(ROOT, "paper_2010_08482_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()

@@ -75,6 +75,11 @@ template <bool CPLX, bool X2>
 __global__ void __launch_bounds__(B64_THREADS, 1)
     k_trace_big64(DevModel M, BatchView B, EvalCfg cfg, Work W, Big64Params P) {
   using E = typename Op64<X2>::E;
+  // C tiles of TM x TNV: the two-float accumulators take two registers each,
+  // so that variant keeps an 8 x 4 tile per thread on 128 x 64 C tiles
+  constexpr int TNV = X2 ? TN / 2 : TN;
+  constexpr int CB = TNV / 16;                // columns of the register tile (rows: 8)
+  constexpr int EPB = TNV * TK / B64_THREADS;  // staged B elements per thread
   static_assert(sizeof(E) == 8, "operand elements are 8 bytes in both forms");
   extern __shared__ __align__(16) double dsm[];
   double* p_s = dsm;           // [PVEC64] column scales of the current product
@@ -302,69 +307,74 @@ __global__ void __launch_bounds__(B64_THREADS, 1)
       const E* Bt = (X2 ? reinterpret_cast<const E*>(P.bt_x2) : reinterpret_cast<const E*>(P.bt)) + P.bt_off[idx_a];
       const E* A = Z[cur];
       E* C = Z[cur ^ 1];
-      const int n_mt = dp0 / TM, n_nt = rup(N2, TN) / TN;
+      const int n_mt = dp0 / TM, n_nt = rup(N2, TN) / TNV;
       const int n_tiles = n_mt * n_nt;
       int ek = 0;
       double f2 = 0.0;
       for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         int mt, nt;
         tile_coords(t, n_mt, n_nt, P.order, mt, nt);
-        E acc[8][8];
+        E acc[8][CB];
 #pragma unroll
         for (int a = 0; a < 8; ++a)
 #pragma unroll
-          for (int b = 0; b < 8; ++b) acc[a][b] = Op64<X2>::make(0.0);
+          for (int b = 0; b < CB; ++b) acc[a][b] = Op64<X2>::make(0.0);
         const E* Ab = A + size_t(mt) * TM * K2;
-        const E* Bb = Bt + size_t(nt) * TN * K2;
-        const int lr = tid >> 1, lk = (tid & 1) * 8;  // this thread's staging row and K half
+        const E* Bb = Bt + size_t(nt) * TNV * K2;
+        const int lr = tid >> 1, lk = (tid & 1) * 8;  // this thread's staging row and K half of A
+        const int lrb = tid / (TK / EPB), lkb = (tid % (TK / EPB)) * EPB;  // and of B
         for (int k0 = 0; k0 < K2; k0 += TK) {
           {
             // 16-byte copies of the operand bytes (two elements of either form)
             const double2* sa = reinterpret_cast<const double2*>(Ab + size_t(lr) * K2 + k0 + lk);
-            const double2* sb = reinterpret_cast<const double2*>(Bb + size_t(lr) * K2 + k0 + lk);
+            const double2* sb = reinterpret_cast<const double2*>(Bb + size_t(lrb) * K2 + k0 + lkb);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              const double2 va = __ldg(sa + u), vb = __ldg(sb + u);
+              const double2 va = __ldg(sa + u);
               S.As[lk + 2 * u][lr] = va.x;
               S.As[lk + 2 * u + 1][lr] = va.y;
-              S.Bs[lk + 2 * u][lr] = vb.x;
-              S.Bs[lk + 2 * u + 1][lr] = vb.y;
+            }
+#pragma unroll
+            for (int u = 0; u < EPB / 2; ++u) {
+              const double2 vb = __ldg(sb + u);
+              S.Bs[lkb + 2 * u][lrb] = vb.x;
+              S.Bs[lkb + 2 * u + 1][lrb] = vb.y;
             }
           }
           __syncthreads();
 #pragma unroll
           for (int k = 0; k < TK; ++k) {
-            E av[8], bv[8];
+            E av[8], bv[CB];
             const E* as = reinterpret_cast<const E*>(&S.As[k][0]);
             const E* bs = reinterpret_cast<const E*>(&S.Bs[k][0]);
 #pragma unroll
             for (int a = 0; a < 8; ++a) av[a] = as[ty + 16 * a];
 #pragma unroll
-            for (int b = 0; b < 8; ++b) bv[b] = bs[tx + 16 * b];
+            for (int b = 0; b < CB; ++b) bv[b] = bs[tx + 16 * b];
             if constexpr (X2) {
 #pragma unroll
               for (int a = 0; a < 8; ++a)
 #pragma unroll
-                for (int b = 0; b < 8; ++b) fma_acc(acc[a][b], av[a], bv[b]);
+                for (int b = 0; b < CB; ++b) fma_acc(acc[a][b], av[a], bv[b]);
               if (k % X2_RENORM == X2_RENORM - 1) {
 #pragma unroll
                 for (int a = 0; a < 8; ++a)
 #pragma unroll
-                  for (int b = 0; b < 8; ++b) finish(acc[a][b]);
+                  for (int b = 0; b < CB; ++b) finish(acc[a][b]);
               }
             } else {
 #pragma unroll
               for (int a = 0; a < 8; ++a)
 #pragma unroll
-                for (int b = 0; b < 8; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+                for (int b = 0; b < CB; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
             }
           }
           __syncthreads();
         }
-        // epilogue: rows mt*TM + ty + 16a, columns nt*TN + tx + 16b
+        // epilogue: rows mt*TM + ty + 16a, columns nt*TNV + tx + 16b
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
-          const int col = nt * TN + tx + 16 * b;  // embedded column
+        for (int b = 0; b < CB; ++b) {
+          const int col = nt * TNV + tx + 16 * b;  // embedded column
           if (col >= N2) continue;
           const double ps = p_s[(col < dpn) ? col : col - dpn];
 #pragma unroll
