@@ -186,8 +186,8 @@ typedef struct {
  *   small-block kernel, any other impurity with blocks <= 3072 states the
  *   large-block kernel (complex blocks in their real embedding).  CTQ_BF16X3
  *   (bf16 hi / lo operands, hi*hi + hi*lo + lo*hi) runs on both kernels.
- *   CTQ_F32X2 runs the float64 shared-memory kernel with two-float block
- *   products (impurities whose two largest blocks fit in shared memory).
+ *   CTQ_F32X2 runs the float64 kernel of the impurity (shared-memory or
+ *   large-block) with two-float block products.
  *   Other combinations: CTQ_ERR_UNSUPPORTED.
  * lazy: 1 = stop a chain as soon as its upper bound falls below its threshold
  *   (needs log_threshold).  segment: operators per bound refinement (>= 1).
