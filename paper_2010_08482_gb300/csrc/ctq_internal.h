@@ -114,6 +114,7 @@ struct Item {
   int r;         // min over the string of the sector dimension (rank bound)
   int n_seg;     // ceil(n / S)
   double t_all;  // sum of log ||F_i||_2 and -dtau (E_min - E_ref) over the string (plan kernel)
+  double log_r;  // log r, from the host table of log(dims)
   float cost;    // work estimate: d0 sum_i d_i d_{i+1} + PLAN_OP_COST n (orders the work list)
 };
 

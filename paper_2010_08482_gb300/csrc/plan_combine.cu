@@ -117,6 +117,7 @@ __device__ void plan_chain(const DevModel& M, const BatchView& B, const EvalCfg&
         it.c = c;
         it.q0 = qs;
         it.r = rs;
+        it.log_r = M.log_dim[qr];
         it.n_seg = (n + cfg.S - 1) / cfg.S;
         it.t_all = acc;
         it.cost = float(M.dims[qs]) * cws + PLAN_OP_COST * float(n);
@@ -175,25 +176,24 @@ __device__ void plan_chain(const DevModel& M, const BatchView& B, const EvalCfg&
 // over the class histogram the plan CTAs built; one CTA of 128 threads): the
 // persistent trace kernels pull strings through W.order, so the longest start
 // first and the short ones fill the tail.
-constexpr int PLAN_THREADS = 128;
-static_assert(ORDER_CLASSES == 4 * PLAN_THREADS, "four classes per thread in the prefix sum");
+// CTA size of k_plan: 512 threads (16 chains) while the per-lane sector
+// buffers fit, 128 for the longest strings.
+constexpr int PLAN_THREADS_MAX = 512, PLAN_THREADS_MIN = 128;
+static_assert(ORDER_CLASSES % PLAN_THREADS_MIN == 0 && ORDER_CLASSES % PLAN_THREADS_MAX == 0, "classes per thread");
 
 __device__ void order_items(const Work& W, size_t cs) {
   __shared__ int off_s[ORDER_CLASSES];
-  __shared__ int part_s[PLAN_THREADS];
-  const int tid = threadIdx.x;
+  __shared__ int part_s[PLAN_THREADS_MAX];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int cpt = ORDER_CLASSES / nt;  // classes per thread in the prefix sum
   const int n = *((volatile int*)&W.counters[0]);
-  int loc[4], sum = 0;
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    loc[u] = __ldcg(&W.counters[ORDER_HIST + 4 * tid + u]);
-    sum += loc[u];
-  }
+  int sum = 0;
+  for (int u = 0; u < cpt; ++u) sum += __ldcg(&W.counters[ORDER_HIST + cpt * tid + u]);
   part_s[tid] = sum;
   __syncthreads();
   if (tid == 0) {
     int acc = 0;
-    for (int t = 0; t < PLAN_THREADS; ++t) {
+    for (int t = 0; t < nt; ++t) {
       const int v = part_s[t];
       part_s[t] = acc;
       acc += v;
@@ -201,30 +201,29 @@ __device__ void order_items(const Work& W, size_t cs) {
   }
   __syncthreads();
   int acc = part_s[tid];
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    off_s[4 * tid + u] = acc;
-    acc += loc[u];
+  for (int u = 0; u < cpt; ++u) {
+    off_s[cpt * tid + u] = acc;
+    acc += __ldcg(&W.counters[ORDER_HIST + cpt * tid + u]);
   }
   __syncthreads();
   const Item* list = W.items + cs;
   constexpr int U = 8;  // independent loads in flight per thread
-  for (int i0 = tid; i0 < n; i0 += U * PLAN_THREADS) {
+  for (int i0 = tid; i0 < n; i0 += U * nt) {
     float cst[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int i = i0 + u * PLAN_THREADS;
+      const int i = i0 + u * nt;
       cst[u] = (i < n) ? __ldcg(&list[i].cost) : 0.f;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int i = i0 + u * PLAN_THREADS;
+      const int i = i0 + u * nt;
       if (i < n) W.order[atomicAdd(&off_s[order_class(cst[u])], 1)] = i;
     }
   }
 }
 
-__global__ void __launch_bounds__(PLAN_THREADS) k_plan(DevModel M, BatchView B, EvalCfg cfg, Work W) {
+__global__ void __launch_bounds__(PLAN_THREADS_MAX) k_plan(DevModel M, BatchView B, EvalCfg cfg, Work W) {
   plan_chain(M, B, cfg, W);
   // the last CTA to finish orders the work list (no wait: it is simply the
   // one whose arrival completes the count)
@@ -366,13 +365,17 @@ int prepare_plan(int optin) {
              : CTQ_ERR_CUDA;
 }
 
-// k_plan keeps one byte per operator per lane (4 warps of 32 lanes per CTA).
+// k_plan keeps one byte per operator per lane (16 or 4 warps of 32 lanes per CTA).
 int launch_plan(const DevModel& M, const BatchView& B, const EvalCfg& cfg, const Work& W, cudaStream_t st) {
   if (M.n_sec > 255) return CTQ_ERR_UNSUPPORTED;
-  const size_t smem = size_t(PLAN_THREADS) * size_t(cfg.max_ops > 0 ? cfg.max_ops : 1);
+  const size_t mo = size_t(cfg.max_ops > 0 ? cfg.max_ops : 1);
+  // one byte per operator per lane: the largest CTA whose buffers fit 200 KB
+  const int threads = (size_t(PLAN_THREADS_MAX) * mo <= 200 * 1024) ? PLAN_THREADS_MAX : PLAN_THREADS_MIN;
+  const size_t smem = size_t(threads) * mo;
   if (smem > 200 * 1024) return CTQ_ERR_UNSUPPORTED;  // max_ops <= 1600
-  const int grid = (B.n_chains + 3) / 4;
-  k_plan<<<grid, PLAN_THREADS, smem, st>>>(M, B, cfg, W);
+  const int warps = threads / 32;
+  const int grid = (B.n_chains + warps - 1) / warps;
+  k_plan<<<grid, threads, smem, st>>>(M, B, cfg, W);
   return cudaGetLastError() == cudaSuccess ? CTQ_OK : CTQ_ERR_CUDA;
 }
 

@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(BG_THREADS, 1)
           const double f = __ldcg(&RS.fr[a * RT_MAX + r]);
           if (f > 0.0) sfr += ldexp(f, 2 * (__ldcg(&RS.ecum[(a - 1) * RT_MAX + r]) - emx));
         }
-      const double ub = (sfr > 0.0) ? 0.5 * log(double(it.r)) + 0.5 * log(sfr) + double(emx) * LN2 + L_s[a] +
+      const double ub = (sfr > 0.0) ? 0.5 * it.log_r + 0.5 * log(sfr) + double(emx) * LN2 + L_s[a] +
                                           (it.t_all - pre_s[a])
                                     : -INFINITY;
       segp[a / cfg.S] = ub;

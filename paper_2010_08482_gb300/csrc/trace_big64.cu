@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(B64_THREADS, 1)
       const int e = min(ekey - 1023, 1022);  // floor(log2 max|Z|) of the stored product
       if (track && applied % cfg.S == 0 && applied < n) {
         const double frv = *((volatile double*)&P.fr[applied]);
-        const double ub = 0.5 * log(double(it.r)) + 0.5 * log(frv) + double(Eacc) * LN2 + L.val() +
+        const double ub = 0.5 * it.log_r + 0.5 * log(frv) + double(Eacc) * LN2 + L.val() +
                           (it.t_all - prefix);
         if (blockIdx.x == 0 && tid == 0) {
           segp[applied / cfg.S] = ub;

@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(512, 1) k_trace(DevModel M, BatchView B, EvalC
     const double* E0 = M.E_rel + M.E_off[q0];
     const bool track = cfg.lazy || cfg.bounds != nullptr;
     double* segp = W.seg + slot * size_t(cfg.n_seg_max + 1);
-    const double ub_const = (track && n > 1) ? 0.5 * log(double(it.r)) : 0.0;  // sqrt(r) of the refined bound
+    const double ub_const = (track && n > 1) ? 0.5 * it.log_r : 0.0;  // sqrt(r) of the refined bound
 
     if (n == 0) {  // empty sequence: Tr e^{-beta H(q0)}
       double sm = 0.0, mx = 0.0;

@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     __syncthreads();
     if (tid < 32) chain_log_scale(M, B, cfg, a0, n, q0, t_first, t_last, track, path, opsm, segL, segP, &S.L);
-    const double ub_const = track ? 0.5 * log(double(it.r)) + it.t_all : 0.0;  // sqrt(r), all log-norms
+    const double ub_const = track ? 0.5 * it.log_r + it.t_all : 0.0;  // sqrt(r), all log-norms
 
     // ---- operator 1 (elementwise): Z_1[j][m] = p0[j] F_1[m][j] p1[m]
     int qa = q0;
