@@ -121,13 +121,12 @@ struct Item {
 // Work-list ordering: strings are pulled in decreasing order of their cost
 // estimate, in ORDER_CLASSES classes of 1/8 octave (counting sort).
 constexpr int ORDER_CLASSES = 512;
-constexpr int ORDER_HIST = 64;         // first counter of the class histogram
-constexpr size_t COUNTER_BYTES = 4096;  // counters region, cleared before every evaluation
+constexpr size_t COUNTER_BYTES = 256;  // counters region, cleared before every evaluation
 
 // Views of the caller's workspace.
 struct Work {
   int* counters;   // [0] n_items, [1] next item, [2] device error bits, [3] estimator next item,
-                   // [4] plan CTAs done, [ORDER_HIST + k] strings of cost class k
+                   // [4] plan CTAs done
   Item* items;     // [2 C n_sec] staging slots per (c, q0), then the compacted list
   int* order;      // [C * n_sec] list position -> compacted item, most expensive first
   double* res_val; // [C * n_sec * 2]  scaled trace value (re, im)

@@ -165,17 +165,17 @@ __device__ void plan_chain(const DevModel& M, const BatchView& B, const EvalCfg&
     first = __shfl_sync(FULL, first, 0);
     if (alive) {
       const int pos = first + __popc(mask & ((1u << lane) - 1u));
-      const Item it = W.items[size_t(c) * ns + q0];
-      W.items[size_t(B.n_chains) * ns + pos] = it;
-      atomicAdd(&W.counters[ORDER_HIST + order_class(it.cost)], 1);
+      W.items[size_t(B.n_chains) * ns + pos] = W.items[size_t(c) * ns + q0];
     }
   }
 }
 
-// Orders the compacted work list by decreasing cost estimate (counting sort
-// over the class histogram the plan CTAs built; one CTA of 128 threads): the
-// persistent trace kernels pull strings through W.order, so the longest start
-// first and the short ones fill the tail.
+// Orders the compacted work list by decreasing cost estimate (a counting
+// sort over the cost classes, done by one CTA: histogram in shared memory,
+// prefix, scatter of the list positions): the persistent trace kernels pull
+// strings through W.order, so the longest start first and the short ones fill
+// the tail.  (Histogram atomics in global memory from every plan CTA cost more
+// than this pass: the classes of one workload crowd into a few counters.)
 // CTA size of k_plan: 512 threads (16 chains) while the per-lane sector
 // buffers fit, 128 for the longest strings.
 constexpr int PLAN_THREADS_MAX = 512, PLAN_THREADS_MIN = 128;
@@ -183,32 +183,49 @@ static_assert(ORDER_CLASSES % PLAN_THREADS_MIN == 0 && ORDER_CLASSES % PLAN_THRE
 
 __device__ void order_items(const Work& W, size_t cs) {
   __shared__ int off_s[ORDER_CLASSES];
-  __shared__ int part_s[PLAN_THREADS_MAX];
-  const int tid = threadIdx.x, nt = blockDim.x;
+  __shared__ int warp_s[PLAN_THREADS_MAX / 32];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
   const int cpt = ORDER_CLASSES / nt;  // classes per thread in the prefix sum
   const int n = *((volatile int*)&W.counters[0]);
-  int sum = 0;
-  for (int u = 0; u < cpt; ++u) sum += __ldcg(&W.counters[ORDER_HIST + cpt * tid + u]);
-  part_s[tid] = sum;
-  __syncthreads();
-  if (tid == 0) {
-    int acc = 0;
-    for (int t = 0; t < nt; ++t) {
-      const int v = part_s[t];
-      part_s[t] = acc;
-      acc += v;
-    }
-  }
-  __syncthreads();
-  int acc = part_s[tid];
-  for (int u = 0; u < cpt; ++u) {
-    off_s[cpt * tid + u] = acc;
-    acc += __ldcg(&W.counters[ORDER_HIST + cpt * tid + u]);
-  }
-  __syncthreads();
   const Item* list = W.items + cs;
   constexpr int U = 8;  // independent loads in flight per thread
-  for (int i0 = tid; i0 < n; i0 += U * nt) {
+  for (int k = tid; k < ORDER_CLASSES; k += nt) off_s[k] = 0;
+  __syncthreads();
+  for (int i0 = tid; i0 < n; i0 += U * nt) {  // histogram of the classes
+    float cst[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * nt;
+      cst[u] = (i < n) ? __ldcg(&list[i].cost) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (i0 + u * nt < n) atomicAdd(&off_s[order_class(cst[u])], 1);
+  }
+  __syncthreads();
+  int loc[ORDER_CLASSES / PLAN_THREADS_MIN];
+  int sum = 0;
+  for (int u = 0; u < cpt; ++u) {
+    loc[u] = off_s[cpt * tid + u];
+    sum += loc[u];
+  }
+  // exclusive prefix over the threads: a warp scan, then the warp totals
+  int inc = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(FULL, inc, o);
+    if (lane >= o) inc += v;
+  }
+  if (lane == 31) warp_s[wid] = inc;
+  __syncthreads();
+  int base = 0;
+  for (int w = 0; w < wid; ++w) base += warp_s[w];
+  int acc = base + inc - sum;
+  for (int u = 0; u < cpt; ++u) {
+    off_s[cpt * tid + u] = acc;
+    acc += loc[u];
+  }
+  __syncthreads();
+  for (int i0 = tid; i0 < n; i0 += U * nt) {  // scatter of the list positions
     float cst[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
