@@ -243,14 +243,18 @@ __device__ void order_items(const Work& W, size_t cs) {
 __global__ void __launch_bounds__(PLAN_THREADS_MAX) k_plan(DevModel M, BatchView B, EvalCfg cfg, Work W) {
   plan_chain(M, B, cfg, W);
   // the last CTA to finish orders the work list (no wait: it is simply the
-  // one whose arrival completes the count)
+  // one whose arrival completes the count).  One thread per CTA fences: the
+  // barrier orders the CTA's writes before its fence, which is cumulative,
+  // and the last CTA's fence orders every CTA's writes before its reads.
   __shared__ int s_last;
-  __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(&W.counters[4], 1) == int(gridDim.x) - 1) ? 1 : 0;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = (atomicAdd(&W.counters[4], 1) == int(gridDim.x) - 1) ? 1 : 0;
+    if (s_last) __threadfence();
+  }
   __syncthreads();
   if (!s_last) return;
-  __threadfence();
   order_items(W, size_t(B.n_chains) * M.n_sec);
 }
 
