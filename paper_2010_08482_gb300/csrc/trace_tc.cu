@@ -45,7 +45,7 @@ constexpr int TC_META_BYTES = 8192;  // staged string of one item: see k_trace_t
 
 // Bytes of the staged string for max_ops operators and n_seg_max segments.
 __host__ __device__ constexpr size_t tc_meta_bytes(int max_ops, int n_seg_max) {
-  return size_t(2) * (n_seg_max + 1) * 8 + size_t(max_ops > 1 ? max_ops : 1) * (4 + 2 + 2) + 2;
+  return size_t(4) * (n_seg_max + 1) * 8 + size_t(max_ops > 1 ? max_ops : 1) * (4 + 2 + 2) + 2;
 }
 
 // Block-wide (max, sum) of floats; all threads get the result.  red: 8 floats.
@@ -175,7 +175,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int MO = max(cfg.max_ops, 1), NS = cfg.n_seg_max + 1;
   double* segL = reinterpret_cast<double*>(p0_s + TC_M);  // [NS]
   double* segP = segL + NS;                                // [NS]
-  float* dtf = reinterpret_cast<float*>(segP + NS);        // [MO] tau_{i+1} - tau_i
+  double* segF = segP + NS;                                // [NS] ||Z||^2 at segment ends (deferred bounds)
+  double* segE = segF + NS;                                // [NS] exponent sums at segment ends
+  float* dtf = reinterpret_cast<float*>(segE + NS);        // [MO] tau_{i+1} - tau_i
   short* opsm = reinterpret_cast<short*>(dtf + MO);        // [MO]
   short* path = opsm + MO;                                 // [MO + 1]
   __shared__ TcShared S;
@@ -341,6 +343,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     block_max_sum_f(mx, fr, S.red);
     qa = qb;
     int applied = 1;
+    int k_rec = 0;  // segments recorded for the deferred bounds
     bool dead = false, aborted = false;
     int cur_stage = 0;
 
@@ -348,14 +351,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (mx == 0.f) { dead = true; break; }
       const int e = ilogbf(mx);
       if (track && applied % cfg.S == 0 && applied < n) {
-        if (tid == 0) {
+        if (!cfg.lazy) {  // bounds output only: the logarithms are taken for all segments at the end
+          if (tid == 0) {
+            segF[applied / cfg.S] = double(fr);
+            segE[applied / cfg.S] = double(Eacc);
+          }
+          k_rec = applied / cfg.S;
+        } else if (tid == 0) {
           const double ub = ub_const + 0.5 * log(double(fr)) + double(Eacc) * LN2 + segL[applied / cfg.S] -
                             segP[applied / cfg.S];
           segp[applied / cfg.S] = ub;
-          if (cfg.lazy) {
-            W.live[slot] = fmin(W.live[slot], ub);
-            __threadfence();
-          }
+          W.live[slot] = fmin(W.live[slot], ub);
+          __threadfence();
         }
         if (cfg.lazy) {
           if (tid < 32) {
@@ -486,6 +493,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       dcur = db;
       qa = qb;
       ++applied;
+    }
+    if (k_rec > 0) {  // deferred bounds, lanes over segments
+      __syncthreads();
+      for (int k = 1 + tid; k <= k_rec; k += TC_THREADS)
+        segp[k] = ub_const + 0.5 * log(segF[k]) + segE[k] * LN2 + segL[k] - segP[k];
     }
     // drain prefetches that this item no longer needs
     if (tid == 0) {

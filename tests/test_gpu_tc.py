@@ -19,6 +19,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 import parity  # noqa: E402
+from oracle import trace as OT  # noqa: E402
 from paper_2010_08482_gb300 import ctq  # noqa: E402
 from paper_2010_08482_gb300 import workloads as w  # noqa: E402
 
@@ -105,3 +106,35 @@ def test_mixed_lazy_decisions_never_contradict_exact(models):
             assert la < thr[c]
         elif res["status"][c] == ctq.CHAIN_ACCEPTED:
             assert la >= thr[c]
+
+
+@pytest.mark.parametrize("precision", [ctq.TF32X3, ctq.BF16X3])
+def test_small_block_bounds_match_oracle(precision, models):
+    """Segment bounds of the small-block tensor kernel (taken after the
+    string, lanes over segments) against the oracle's refined bounds: equal
+    up to the products' rounding (the Frobenius norms come from FP32 sums),
+    and never below log|w| by more than the early-reject margin."""
+    m = models("d5")
+    sub = w.batch_d5().subset(range(24))
+    imp = parity.load_oracle_model(ctq, m)
+    S = 8
+    res = run(imp, sub, precision, S=S)
+    margin = 5e-2 if precision == ctq.BF16X3 else 1e-2
+    n_cmp = 0
+    for c in range(sub.n_chains):
+        tau, ops = sub.chain(c)
+        B, ub = OT.chain_bounds(m, tau, ops, sub.beta, S)
+        got = res["bounds"][c]
+        if B == -math.inf:
+            continue
+        r = OT.trace_chain(m, tau, ops, beta=sub.beta)
+        for s in range(1, len(got)):
+            exp = ub[min(s, len(ub) - 1)]
+            if exp == -math.inf or not np.isfinite(got[s]):
+                continue
+            assert abs(got[s] - exp) <= margin, (c, s, got[s], exp)
+            n_cmp += 1
+        fin = got[np.isfinite(got)]
+        if r["log_abs"] != -math.inf:
+            assert np.all(fin >= r["log_abs"] - margin)
+    assert n_cmp > 20
