@@ -8,7 +8,7 @@ and the full window's particle-hole chemical potential, with two chains of
 80 operators whose particle number alternates between 4 and 5, and
 evaluates them a few times:
 
-    python -m paper_2010_08482_gb300.profile_case bf16x3
+    python -m paper_2010_08482_gb300.profile_case bf16x3     # or tf32x3, tf32, fp64, f32x2
 """
 import sys
 
@@ -25,7 +25,8 @@ MU_F7 = 18.37060157531069
 def main(argv=None):
     import torch
     argv = sys.argv[1:] if argv is None else argv
-    prec = {"bf16x3": ctq.BF16X3, "tf32x3": ctq.TF32X3, "tf32": ctq.TF32}[argv[0] if argv else "bf16x3"]
+    prec = {"bf16x3": ctq.BF16X3, "tf32x3": ctq.TF32X3, "tf32": ctq.TF32, "fp64": ctq.FP64,
+            "f32x2": ctq.F32X2}[argv[0] if argv else "bf16x3"]
     reps = int(argv[1]) if len(argv) > 1 else 4
     p = w.model_f7()
     p.n_min, p.n_max, p.mu = 4, 5, MU_F7
