@@ -720,7 +720,7 @@ int prepare_eval_tc(const DevModel& M, int prec, int stage_bytes, int num_sms, L
                   : prec == CTQ_BF16X3 ? tc_attr<CTQ_BF16X3>(lc->smem)
                                        : tc_attr<CTQ_TF32X3>(lc->smem);
   if (e != cudaSuccess) return CTQ_ERR_CUDA;
-  // resident CTAs per SM: shared memory (with the driver's 1 KB per CTA),
+  // resident CTAs per SM: shared memory (with the 1 KB per CTA the CUDA runtime reserves),
   // registers, and tensor memory (512 or 256 of the SM's 512 columns)
   cudaFuncAttributes fa;
   e = prec == CTQ_TF32     ? cudaFuncGetAttributes(&fa, k_trace_tc<CTQ_TF32>)
