@@ -253,3 +253,70 @@ def test_left_and_right_association_agree(models):
             assert l["log_abs"] == -math.inf
             continue
         assert rel_log(l, r) < 1e-12
+
+
+# ---------------------------------------------------------------- signed log-space sum
+
+def la_or0(la):
+    return 0.0 if la == -math.inf else la
+
+
+def test_logsumexp_signed_exact():
+    """The combine over starting sectors (Sec. 3.3.1: w is the sum of the
+    per-sector traces, each held as a value and a log scale) against exact
+    rational arithmetic: scales are whole multiples of log 2, so every term
+    is a dyadic rational and the sum is exact.  Covers cancellation down to
+    a few ulps of the largest term, zero values, -inf scales, an exactly
+    cancelling sum and complex phases."""
+    from fractions import Fraction
+    LN2 = math.log(2.0)
+    rng = np.random.default_rng(11)
+    n_rel = 0
+    for case in range(300):
+        k = int(rng.integers(1, 7))
+        cplx = case % 3 == 2
+        terms, exact_re, exact_im = [], Fraction(0), Fraction(0)
+        for _ in range(k):
+            e = int(rng.integers(-900, 900)) if case % 5 else int(rng.integers(-3, 3))
+            re = float(rng.integers(-2 ** 20, 2 ** 20)) / 2 ** 10
+            im = float(rng.integers(-2 ** 20, 2 ** 20)) / 2 ** 10 if cplx else 0.0
+            if rng.random() < 0.1:
+                re, im = 0.0, 0.0
+            v = complex(re, im) if cplx else re
+            terms.append((v, e * LN2))
+            exact_re += Fraction(re) * Fraction(2) ** e
+            exact_im += Fraction(im) * Fraction(2) ** e
+        if case % 7 == 0 and terms:  # an opposite copy of the first term: partial cancellation
+            v0, l0 = terms[0]
+            terms.append((-v0, l0))
+            exact_re -= Fraction(v0.real if cplx else v0) * Fraction(2) ** round(l0 / LN2)
+            exact_im -= Fraction(v0.imag if cplx else 0.0) * Fraction(2) ** round(l0 / LN2)
+        terms.append((1.5, -math.inf))  # a dead sector contributes nothing
+        la, ph = T.logsumexp_signed(terms)
+        if exact_re == 0 and exact_im == 0:
+            assert la == -math.inf and ph == 0.0
+            continue
+        live = [(v, l) for v, l in terms if v != 0 and l != -math.inf]
+        # the largest term as a power of two 2^E (E = its scale in units of
+        # log 2 plus the binary exponent of its value)
+        E = max(round(l / LN2) + math.frexp(abs(v))[1] for v, l in live)
+        # absolute pin: |w - w_exact| <= a few ulps of the largest term per term
+        r_ex = complex(float(exact_re / Fraction(2) ** E), float(exact_im / Fraction(2) ** E))
+        r = 0.0 if la == -math.inf else complex(ph) * math.exp(la - E * LN2)
+        # (the second term: rounding of log|w| and of E log 2 in this check)
+        tol_abs = 4 * len(live) * 2.0 ** -52 + 4 * abs(r_ex) * math.ulp(max(abs(la_or0(la)), abs(E * LN2)))
+        assert abs(r - r_ex) <= tol_abs, (case, r, r_ex)
+        # relative pin where the sum keeps most of its bits
+        big = max(abs(exact_re), abs(exact_im))
+        sh = big.numerator.bit_length() - big.denominator.bit_length()
+        sre, sim = float(exact_re / Fraction(2) ** sh), float(exact_im / Fraction(2) ** sh)
+        la_ex = sh * LN2 + math.log(abs(complex(sre, sim)))
+        if E * LN2 - la_ex < 20.0:  # the sum keeps all but ~29 of its bits
+            rel_tol = 4 * len(live) * 2.0 ** -52 * math.exp(E * LN2 - la_ex)
+            assert abs(la - la_ex) <= rel_tol + 8 * math.ulp(abs(la_ex)), (case, la, la_ex)
+            ph_ex = complex(sre, sim) / abs(complex(sre, sim))
+            assert abs(complex(ph) - ph_ex) <= 2 * rel_tol + 1e-15, (case, ph, ph_ex)
+            n_rel += 1
+    assert n_rel > 200
+    assert T.logsumexp_signed([]) == (-math.inf, 0.0)
+    assert T.logsumexp_signed([(0.0, 3.0), (2.0, -math.inf)]) == (-math.inf, 0.0)
