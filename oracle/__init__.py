@@ -22,6 +22,11 @@ reader can check each step against the paper by eye:
   configuration (Eq. ImpurityDensityMatrix: the projector |v><u| inserted at
   every time, integrated analytically over each propagation interval), and
   its brute-force counterpart by quadrature over the full Fock space.
+* ``oracle.improved`` -- the static part of the improved estimator for the
+  self-energy (Eq. PImprovedEstimatorStatic): the Bulla operators [c_f, U]
+  from the interaction terms alone, in the occupation basis and then the
+  eigenbasis, and the ratio of the trace with one annihilator replaced to
+  the plain trace.
 
 It shares no code with the GPU path (``paper_2010_08482_gb300``) and imports
 nothing from it.  Every function is pinned by a ``-m "not gpu"`` test against

@@ -264,32 +264,45 @@ def soc_complex(l: int, xi: float) -> np.ndarray:
 # ---------------------------------------------------------------------------
 
 
-def hamiltonian_terms(p, mu: float):
-    """All terms of H_loc for a parameter set (see paper_2010_08482_gb300
-    workloads.ModelParams for the fields), at chemical potential mu."""
+def one_body_matrix(p, mu: float) -> np.ndarray:
+    """The one-body part t_ij - mu delta_ij of H_loc (Eq. ImpurityHamiltonian)
+    as an n_f x n_f complex matrix in the flavour basis: spin-orbit coupling
+    (slater shells) and the crystal field, with -mu on the diagonal."""
     n_orb = p.n_orb
     n_f = 2 * n_orb
     t = np.zeros((n_f, n_f), dtype=np.complex128)
     t -= mu * np.eye(n_f)
+    if p.interaction == "slater" and p.soc_xi != 0.0:
+        T = real_harmonics_T(p.l)
+        TT = np.zeros((n_f, n_f), dtype=np.complex128)
+        TT[:n_orb, :n_orb] = T
+        TT[n_orb:, n_orb:] = T
+        t += to_real_basis_one_body(soc_complex(p.l, p.soc_xi), TT)
+    if p.cf is not None:
+        t += np.asarray(p.cf, dtype=np.complex128)
+    return t
+
+
+def interaction_terms(p):
+    """The interaction part U of H_loc (the two-body terms of Eq.
+    ImpurityHamiltonian) for a parameter set."""
     if p.interaction == "kanamori":
-        inter = kanamori_terms(n_orb, p.U, p.J)
         if p.soc_xi != 0.0:
             raise ValueError("SOC needs a slater shell")
-    elif p.interaction == "slater":
+        return kanamori_terms(p.n_orb, p.U, p.J)
+    if p.interaction == "slater":
         F = slater_F(p.l, p.U, p.J)
         T = real_harmonics_T(p.l)
         Vr = to_real_basis_tensor(slater_orbital_tensor(p.l, F), T)
-        inter = orbital_tensor_terms(n_orb, Vr)
-        if p.soc_xi != 0.0:
-            TT = np.zeros((n_f, n_f), dtype=np.complex128)
-            TT[:n_orb, :n_orb] = T
-            TT[n_orb:, n_orb:] = T
-            t += to_real_basis_one_body(soc_complex(p.l, p.soc_xi), TT)
-    else:
-        raise ValueError(p.interaction)
-    if p.cf is not None:
-        t += np.asarray(p.cf, dtype=np.complex128)
-    return one_body_terms(t) + inter
+        return orbital_tensor_terms(p.n_orb, Vr)
+    raise ValueError(p.interaction)
+
+
+def hamiltonian_terms(p, mu: float):
+    """All terms of H_loc for a parameter set (see paper_2010_08482_gb300
+    workloads.ModelParams for the fields), at chemical potential mu."""
+    inter = interaction_terms(p)
+    return one_body_terms(one_body_matrix(p, mu)) + inter
 
 
 def sector_states(p):
@@ -405,31 +418,43 @@ class Model:
     def _build_blocks(self):
         all_states = np.concatenate(self.states)
         order = np.argsort(all_states)
-        sorted_states = all_states[order]
-        sec_of = np.concatenate([np.full(d, q) for q, d in enumerate(self.dims)])[order]
-        pos_of = np.concatenate([np.arange(d) for d in self.dims])[order]
+        self._sorted_states = all_states[order]
+        self._sec_of = np.concatenate([np.full(d, q) for q, d in enumerate(self.dims)])[order]
+        self._pos_of = np.concatenate([np.arange(d) for d in self.dims])[order]
         n_alpha = 2 * self.n_flav
         self.s = np.full((n_alpha, self.n_sec), -1, dtype=np.int64)
         self.F = {}
         for alpha in range(n_alpha):
-            f, dag = alpha // 2, alpha % 2
-            for q, st in enumerate(self.states):
-                ok, sign, new = apply_op(st, f, dag)
-                cols = np.nonzero(ok)[0]
-                idx = np.minimum(np.searchsorted(sorted_states, new[cols]), len(sorted_states) - 1)
-                inside = sorted_states[idx] == new[cols]  # else: leaves the N window
-                cols, idx = cols[inside], idx[inside]
-                if cols.size == 0:
+            for q in range(self.n_sec):
+                got = self.occupation_op(alpha, q)
+                if got is None:
                     continue
-                targets = np.unique(sec_of[idx])
-                if targets.size != 1:
-                    raise RuntimeError("operator does not map a sector onto a unique sector")
-                qp = int(targets[0])
-                C = np.zeros((self.dims[qp], self.dims[q]))
-                C[pos_of[idx], cols] = sign[cols]
+                qp, C = got
                 Fb = self.V[qp].conj().T @ (C @ self.V[q])
                 self.s[alpha, q] = qp
                 self.F[(alpha, q)] = Fb if self.is_complex else Fb.real
+
+    def occupation_op(self, alpha: int, q: int):
+        """Operator alpha = 2 f + dag restricted to sector q in the occupation
+        basis: (target sector q', C) with C[m, n] = <m(q')|c_f or c+_f|n(q)>
+        (Jordan-Wigner signs), or None if it maps q to zero (or out of the N
+        window)."""
+        f, dag = alpha // 2, alpha % 2
+        st = self.states[q]
+        ok, sign, new = apply_op(st, f, dag)
+        cols = np.nonzero(ok)[0]
+        idx = np.minimum(np.searchsorted(self._sorted_states, new[cols]), len(self._sorted_states) - 1)
+        inside = self._sorted_states[idx] == new[cols]  # else: leaves the N window
+        cols, idx = cols[inside], idx[inside]
+        if cols.size == 0:
+            return None
+        targets = np.unique(self._sec_of[idx])
+        if targets.size != 1:
+            raise RuntimeError("operator does not map a sector onto a unique sector")
+        qp = int(targets[0])
+        C = np.zeros((self.dims[qp], self.dims[q]))
+        C[self._pos_of[idx], cols] = sign[cols]
+        return qp, C
 
     def opnorm(self, alpha: int, q: int) -> float:
         """Spectral norm ||F_alpha(q)||_2 (numpy SVD)."""
