@@ -67,6 +67,8 @@ def algorithmic_flops(imp, batch):
     + 2 d_{q0} d_{q_{n-1}} (the first operator only scales; the last needs only
     a diagonal).  Host accounting from the library's sector table."""
     dims, _, _, s = imp.sectors()
+    if imp.n_alpha > s.shape[0]:  # Bulla operators 2 n_flav + f map sectors as c_f (code 2 f)
+        s = s[[a if a < s.shape[0] else 2 * (a - s.shape[0]) for a in range(imp.n_alpha)]]
     C = batch.n_chains
     lens = np.diff(batch.offsets)
     nmax = int(lens.max()) if C else 0
@@ -176,6 +178,71 @@ def run_density(args, world, rank, local):
                          "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": achieved / (fp64_peak / 1e12),
                          "peak_source": "measured FP64 FMA rate (ctq_probe_fma_rate, this run)", "traffic": None},
             "gpu_launches": args.steps * 4, "clocks": clocks.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_improved(args, world, rank, local):
+    """The static improved estimator for the self-energy (Eq.
+    PImprovedEstimatorStatic) on a workload: every chain and, for each of its
+    annihilators, the chain with that operator replaced by its Bulla operator
+    [c_f, U] (ctq_eval_traces on both batches), then h^st = w^U / w
+    (ctq_static_ratios).  The replaced sequences are built on the host once,
+    before timing (they are the caller's input)."""
+    import torch
+    from paper_2010_08482_gb300 import ctq
+    from paper_2010_08482_gb300 import workloads as w
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mf, bf = w.WORKLOADS[args.workload]
+    batch = bf(rank=rank)
+    if args.chains:
+        batch = batch.subset(range(min(args.chains, batch.n_chains)))
+    imp = ctq.build_impurity(mf(), device=local)
+    imp.add_bulla_operators()
+    bu, chain, _ = w.bulla_sequences(batch, imp.n_flav)
+    db, dbu = ctq.DeviceBatch(batch, device=dev), ctq.DeviceBatch(bu, device=dev)
+    prec = PRECISIONS[args.precision]
+    ev = ctq.StaticImprovedEvaluator(imp, batch.n_chains, bu.n_chains, max(db.max_ops, 1), precision=prec,
+                                     device=dev)
+    ch = torch.as_tensor(chain, device=dev)
+    flops = algorithmic_flops(imp, batch)[0] + algorithmic_flops(imp, bu)[0]
+    fp64_peak = ctq.probe_fma_rate(local, 0)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        ev(db, dbu, ch)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ev(db, dbu, ch)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clocks.stop()
+    mean = statistics.mean(ms)
+    achieved = flops / (mean * 1e-3) / 1e12
+    launches = 2 * ctq.launches_per_eval(imp, prec) + 1
+    line = {"metric": "static improved-estimator ratios h^st per second (Eq. PImprovedEstimatorStatic), 1xGB300",
+            "value": bu.n_chains / (mean * 1e-3), "unit": "ratios/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": mean, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else args.precision,
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT[args.workload], "n_chains": batch.n_chains,
+                       "replaced_sequences": bu.n_chains, "precision": args.precision,
+                       "estimator": "static improved estimator, Bulla operators [c_f, U]",
+                       "l2": "flushed (256 MiB write) between steps"},
+            "tflops": achieved, "algorithmic_flops_per_step": flops,
+            "roofline": {"kernel": "k_trace<fp64>" if args.precision == "fp64" else f"trace kernels<{args.precision}>",
+                         "bound": "alu", "achieved": achieved, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+                         "frac": achieved / (fp64_peak / 1e12),
+                         "peak_source": "measured FP64 FMA rate (ctq_probe_fma_rate, this run)", "traffic": None},
+            "gpu_launches": args.steps * launches, "clocks": clocks.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -430,8 +497,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--chains", type=int, default=0, help="evaluate only the first N chains of the workload")
     ap.add_argument("--no-autotune", action="store_true", help="library-default launch configuration")
-    ap.add_argument("--estimator", default="trace", choices=["trace", "rho"],
-                    help="trace: local traces (default); rho: traces plus the reduced-density-matrix estimator")
+    ap.add_argument("--estimator", default="trace", choices=["trace", "rho", "hst"],
+                    help="trace: local traces (default); rho: traces plus the reduced-density-matrix estimator; "
+                         "hst: the static improved-estimator ratio of every annihilator")
     ap.add_argument("--autotune-cache", default=None, help="JSON cache of tuned launch configurations")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -445,6 +513,9 @@ def main():
         return
     if args.estimator == "rho":
         run_density(args, world, rank, local)
+        return
+    if args.estimator == "hst":
+        run_improved(args, world, rank, local)
         return
     import torch
     from paper_2010_08482_gb300 import ctq

@@ -22,7 +22,8 @@
  *     device; "host" pointers are ordinary CPU memory.
  *   - operator code alpha = 2*f + dag (dag = 1: c^dagger), flavour f in the
  *     paper's order: all spin-down orbitals, then all spin-up (App. A,
- *     Eqs. enumProduct / enumCoupled).
+ *     Eqs. enumProduct / enumCoupled).  After ctq_add_bulla_operators the
+ *     codes 2*n_flav + f name the Bulla operators [c_f, U].
  */
 #ifndef CTQ_H
 #define CTQ_H
@@ -114,6 +115,8 @@ typedef struct {
   double mu;       /* chemical potential used                               */
   double E_gs;     /* ground-state energy (mu included)                     */
   int64_t n_block_elems; /* total elements over all nonzero blocks          */
+  int n_alpha;     /* operator codes: 2 n_flav, or 3 n_flav with the Bulla
+                      operators (ctq_add_bulla_operators)                    */
 } ctq_info;
 
 /*
@@ -142,11 +145,36 @@ int ctq_load_impurity(int n_flav, int n_sec, const int* dims, const int* N, cons
                       const int* s_table, const double* blocks_re, const double* blocks_im,
                       const double* opnorm, double mu, int device, ctq_impurity** out);
 
+/*
+ * Add the Bulla operators B_f = [c_f, U] of the improved estimator for the
+ * self-energy (Sec. 2.4, Eq. ImprCorrFunc and Eq. PImprovedEstimatorStatic:
+ * the static ratio h^st replaces one annihilator c_f(tau) of a configuration
+ * by [c_f, U](tau), U the interaction part of H_loc) as operator codes
+ * 2 n_flav + f, f = 0 .. n_flav - 1.  Their blocks are formed on the host in
+ * the impurity's eigenbasis from the identity
+ *   <m|[c_f, U]|n> = <m|c_f|n> (E_n - E_m) - sum_j h_fj <m|c_j|n>,
+ * with h = t - mu the one-body part of H_loc (Eq. ImpurityHamiltonian):
+ * h_re / h_im (host, n_flav x n_flav row-major, flavour basis; h_im nullable)
+ * or, when both are NULL, the matrix ctq_build_impurity used (an impurity
+ * from ctq_load_impurity then fails with CTQ_ERR_ARG).  B_f maps each sector
+ * where c_f does, so its sector map equals that of c_f; a one-body term that
+ * links sectors differently is CTQ_ERR_UNSUPPORTED.  Block norms for the
+ * lazy bounds: power iteration up to 400 x 400, the Frobenius norm above.
+ * Every device copy of the impurity is then rebuilt (blocks and
+ * precision-specific operand formats; ~1.5x the block memory), so no
+ * evaluation on this impurity may be in flight.  Once per impurity (a second
+ * call is CTQ_ERR_ARG).  Errors: CTQ_ERR_ARG, CTQ_ERR_UNSUPPORTED,
+ * CTQ_ERR_NOMEM, CTQ_ERR_CUDA; after a device error the impurity has no
+ * device copy and must be freed.
+ */
+int ctq_add_bulla_operators(ctq_impurity* imp, const double* h_re, const double* h_im);
+
 int ctq_impurity_info(const ctq_impurity* imp, ctq_info* out);
 
 /*
  * Copy sector data to host arrays (each nullable): dims[n_sec], N[n_sec],
- * E_min[n_sec], s_table[(2 n_flav) x n_sec].
+ * E_min[n_sec], s_table[(2 n_flav) x n_sec] (the c / c+ codes; a Bulla
+ * operator 2 n_flav + f maps sectors as c_f, code 2 f, does).
  */
 int ctq_get_sectors(const ctq_impurity* imp, int* dims, int* N, double* E_min, int* s_table);
 
@@ -165,7 +193,7 @@ int ctq_get_block(const ctq_impurity* imp, int alpha, int q, double* re, double*
  *   offsets[n_chains + 1] int32, nondecreasing; chain c owns entries
  *     offsets[c] .. offsets[c+1]-1 of tau and op,
  *   tau   float64, strictly increasing within a chain, in [0, beta),
- *   op    int32 alpha codes in [0, 2 n_flav),
+ *   op    int32 alpha codes in [0, n_alpha) (ctq_info.n_alpha),
  *   log_threshold[n_chains] float64 (nullable): Metropolis threshold
  *     T = log r + log|w_old| - log(other ratios), the random number r drawn
  *     first (App. B, Eq. decide); accept iff log|w| >= T.
@@ -282,6 +310,24 @@ int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_e
 #define CTQ_STATIC_SCRATCH_BYTES (32u << 20)
 int ctq_eval_traces_static(const ctq_impurity* imp, const ctq_batch* batch, const ctq_eval_opts* opts,
                            const ctq_result* result, void* stream);
+
+/*
+ * Static part of the improved estimator for the self-energy (Sec. 2.4,
+ * Eq. PImprovedEstimatorStatic): h^st_i = w^U_i / w_loc(C_{chain[i]}) from
+ * the results of two ctq_eval_traces calls, one on the configurations
+ * (n_chains entries of log_abs / phase) and one on m sequences, each a
+ * configuration with one annihilator c_f replaced by its Bulla operator
+ * (code 2 n_flav + f; log_abs_u / phase_u).  All device pointers, on the
+ * current device: chain[m] int32, the configuration of each sequence;
+ * h[2 m] float64 out, (re, im) pairs.  An entry is NaN when its
+ * configuration has w = 0, was rejected or failed (log_abs -inf or NaN), its
+ * sequence failed, or chain[i] is outside [0, n_chains); w^U = 0 gives 0.
+ * One kernel, asynchronous on `stream` (cudaStream_t), graph-capturable.
+ * Errors: CTQ_ERR_ARG (m < 0, n_chains < 0, a NULL pointer with m > 0),
+ * CTQ_ERR_CUDA.
+ */
+int ctq_static_ratios(int m, const int32_t* chain, int n_chains, const double* log_abs, const double* phase,
+                      const double* log_abs_u, const double* phase_u, double* h, void* stream);
 
 /*
  * Number of kernels one ctq_eval_traces call enqueues (for launch accounting).

@@ -453,6 +453,104 @@ int ctq_load_impurity(int n_flav, int n_sec, const int* dims, const int* N, cons
   }
 }
 
+int ctq_add_bulla_operators(ctq_impurity* imp, const double* h_re, const double* h_im) {
+  if (!imp) return fail(CTQ_ERR_ARG, "null impurity");
+  ctq::HostModel& h = imp->host;
+  if (h.n_extra != 0) return fail(CTQ_ERR_ARG, "the Bulla operators are already present");
+  const int nf = h.n_flav, ns = h.n_sec;
+  try {
+    std::vector<ctq::cplx> t(size_t(nf) * nf);
+    if (h_re || h_im) {
+      for (size_t i = 0; i < t.size(); ++i) t[i] = ctq::cplx(h_re ? h_re[i] : 0.0, h_im ? h_im[i] : 0.0);
+    } else if (h.h1.size() == t.size()) {
+      t = h.h1;
+    } else {
+      return fail(CTQ_ERR_ARG, "a loaded impurity needs the one-body matrix h_re / h_im");
+    }
+    for (const auto& x : t)
+      if (!std::isfinite(x.real()) || !std::isfinite(x.imag())) return fail(CTQ_ERR_ARG, "non-finite one-body term");
+    if (!h.is_complex)
+      for (const auto& x : t)
+        if (x.imag() != 0.0) return fail(CTQ_ERR_ARG, "complex one-body term on a real impurity");
+    // B_f(q) = F_f(q) o (E_q,n - E_q',m) - sum_j h_fj F_j(q) in the eigenbasis:
+    // <m|[c_f, H]|n> = <m|c_f|n> (E_n - E_m) and [c_f, H - U] = sum_j h_fj c_j.
+    std::vector<int> s_new(size_t(nf) * ns, -1);
+    std::vector<int64_t> off_new(size_t(nf) * ns, -1);
+    std::vector<double> norm_new(size_t(nf) * ns, 0.0);
+    std::vector<double> re_new, im_new;
+    int64_t total = int64_t(h.blk_re.size());
+    for (int f = 0; f < nf; ++f)
+      for (int q = 0; q < ns; ++q) {
+        const int qp = h.s[size_t(2 * f) * ns + q];
+        for (int j = 0; j < nf; ++j) {
+          const int qj = h.s[size_t(2 * j) * ns + q];
+          if (t[size_t(f) * nf + j] != 0.0 && qj >= 0 && qj != qp)
+            return fail(CTQ_ERR_UNSUPPORTED, "the one-body term connects sectors that c_f does not");
+        }
+        if (qp < 0) continue;
+        const int r = h.dims[qp], c = h.dims[q];
+        const size_t n = size_t(r) * c;
+        std::vector<double> br(n, 0.0), bi(n, 0.0);
+        const int64_t o = h.blk_off[size_t(2 * f) * ns + q];
+        const double* Eq = &h.E[h.E_off[q]];
+        const double* Ep = &h.E[h.E_off[qp]];
+        for (int m = 0; m < r; ++m)
+          for (int k = 0; k < c; ++k) {
+            const double de = Eq[k] - Ep[m];
+            br[size_t(m) * c + k] = h.blk_re[o + size_t(m) * c + k] * de;
+            if (h.is_complex) bi[size_t(m) * c + k] = h.blk_im[o + size_t(m) * c + k] * de;
+          }
+        for (int j = 0; j < nf; ++j) {
+          const ctq::cplx tj = t[size_t(f) * nf + j];
+          if (tj == 0.0 || h.s[size_t(2 * j) * ns + q] < 0) continue;
+          const int64_t oj = h.blk_off[size_t(2 * j) * ns + q];
+          for (size_t i = 0; i < n; ++i) {
+            const double fr = h.blk_re[oj + i], fi = h.is_complex ? h.blk_im[oj + i] : 0.0;
+            br[i] -= tj.real() * fr - tj.imag() * fi;
+            bi[i] -= tj.real() * fi + tj.imag() * fr;
+          }
+        }
+        const size_t idx = size_t(f) * ns + q;
+        s_new[idx] = qp;
+        off_new[idx] = total;
+        // spectral norm by power iteration; above 400 x 400 the Frobenius
+        // norm (an upper bound, so the lazy bounds stay valid)
+        if (n <= 160000) {
+          norm_new[idx] = spectral_norm(r, c, br.data(), h.is_complex ? bi.data() : nullptr);
+        } else {
+          double fro = 0.0;
+          for (size_t i = 0; i < n; ++i) fro += br[i] * br[i] + bi[i] * bi[i];
+          norm_new[idx] = std::sqrt(fro) * (1.0 + 1e-12);
+        }
+        re_new.insert(re_new.end(), br.begin(), br.end());
+        if (h.is_complex) im_new.insert(im_new.end(), bi.begin(), bi.end());
+        total += int64_t(n);
+      }
+    h.s.insert(h.s.end(), s_new.begin(), s_new.end());
+    h.blk_off.insert(h.blk_off.end(), off_new.begin(), off_new.end());
+    h.opnorm.insert(h.opnorm.end(), norm_new.begin(), norm_new.end());
+    h.blk_re.insert(h.blk_re.end(), re_new.begin(), re_new.end());
+    if (h.is_complex) h.blk_im.insert(h.blk_im.end(), im_new.begin(), im_new.end());
+    h.n_extra = nf;
+  } catch (const std::bad_alloc&) {
+    return fail(CTQ_ERR_NOMEM, "host allocation failed");
+  }
+  // every device copy (blocks, precision-specific operand formats, launch
+  // configurations) is rebuilt for the larger operator table
+  free_device(imp);
+  imp->dev = ctq::DevModel{};
+  imp->launch = ctq::LaunchCfg{};
+  imp->rho_off = nullptr;
+  imp->tc1 = imp->tc2 = imp->tc3 = ctq::TcParams{};
+  imp->launch_tc1 = imp->launch_tc2 = imp->launch_tc3 = ctq::LaunchCfg{};
+  imp->big = imp->big64 = false;
+  imp->b64 = ctq::Big64Params{};
+  imp->launch_b64 = ctq::LaunchCfg{};
+  imp->big1 = imp->big2 = imp->big3 = ctq::BigParams{};
+  imp->launch_big1 = imp->launch_big2 = imp->launch_big3 = ctq::LaunchCfg{};
+  return upload_model(imp);
+}
+
 int ctq_impurity_info(const ctq_impurity* imp, ctq_info* out) {
   if (!imp || !out) return fail(CTQ_ERR_ARG, "null argument");
   const ctq::HostModel& h = imp->host;
@@ -463,6 +561,7 @@ int ctq_impurity_info(const ctq_impurity* imp, ctq_info* out) {
   out->mu = h.mu;
   out->E_gs = h.E_gs;
   out->n_block_elems = int64_t(h.blk_re.size());
+  out->n_alpha = h.n_alpha();
   return CTQ_OK;
 }
 
@@ -472,7 +571,7 @@ int ctq_get_sectors(const ctq_impurity* imp, int* dims, int* N, double* E_min, i
   if (dims) std::copy(h.dims.begin(), h.dims.end(), dims);
   if (N) std::copy(h.N.begin(), h.N.end(), N);
   if (E_min) std::copy(h.E_min.begin(), h.E_min.end(), E_min);
-  if (s_table) std::copy(h.s.begin(), h.s.end(), s_table);
+  if (s_table) std::copy(h.s.begin(), h.s.begin() + size_t(2 * h.n_flav) * h.n_sec, s_table);
   return CTQ_OK;
 }
 
@@ -670,6 +769,15 @@ int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_e
   }
   if (st != CTQ_OK) return fail(st, st == CTQ_ERR_CUDA ? cudaGetErrorString(cudaGetLastError()) : "launch failed");
   return CTQ_OK;
+}
+
+int ctq_static_ratios(int m, const int32_t* chain, int n_chains, const double* log_abs, const double* phase,
+                      const double* log_abs_u, const double* phase_u, double* h, void* stream) {
+  if (m < 0 || n_chains < 0) return fail(CTQ_ERR_ARG, "negative size");
+  if (m == 0) return CTQ_OK;
+  if (!chain || !log_abs || !phase || !log_abs_u || !phase_u || !h) return fail(CTQ_ERR_ARG, "null pointer");
+  const int st = ctq::launch_static_ratios(m, chain, n_chains, log_abs, phase, log_abs_u, phase_u, h, stream);
+  return st == CTQ_OK ? CTQ_OK : fail(st, "static-ratio kernel launch failed");
 }
 
 void ctq_free_impurity(ctq_impurity* imp) {

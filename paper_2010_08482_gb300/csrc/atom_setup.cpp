@@ -381,6 +381,8 @@ int build_host_model(const ctq_model_params* p, HostModel& m, std::string& err) 
     m.E_min[q] = m.E[m.E_off[q]];
     m.E_gs = std::min(m.E_gs, m.E_min[q]);
   }
+  m.h1 = t;  // one-body matrix t - mu (for the Bulla operators [c_f, U])
+  for (int i = 0; i < nf; ++i) m.h1[size_t(i) * nf + i] -= m.mu;
 
   // blocks F_alpha(q) = V_{q'}^H C_alpha V_q  (C: signed partial permutation)
   const int na = 2 * nf;

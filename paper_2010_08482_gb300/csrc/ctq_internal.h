@@ -18,8 +18,13 @@ using cplx = std::complex<double>;
 //   blk_off[alpha * n_sec + q]: element offset of block F_alpha(q)
 //     (d_{s(q)} x d_q, row-major) in blk_re / blk_im, or -1.
 //   opnorm: spectral norm of each block (0 for absent blocks).
+//   Operator codes: 2 f + dag for c_f / c+_f, then n_extra further codes
+//   (2 n_flav + f: the Bulla operator [c_f, U] once added).
+//   h1: the one-body matrix t - mu (n_flav x n_flav, flavour basis) of a
+//     model built from parameters; empty for a loaded model.
 struct HostModel {
   int n_flav = 0, n_sec = 0, max_dim = 0, is_complex = 0;
+  int n_extra = 0;
   double mu = 0.0, E_gs = 0.0;
   std::vector<int> dims, N, E_off;
   std::vector<double> E, E_min;
@@ -27,7 +32,8 @@ struct HostModel {
   std::vector<int64_t> blk_off;
   std::vector<double> blk_re, blk_im;
   std::vector<double> opnorm;
-  int n_alpha() const { return 2 * n_flav; }
+  std::vector<cplx> h1;
+  int n_alpha() const { return 2 * n_flav + n_extra; }
 };
 
 // Builds the model from physics parameters on the host (Fock space, H_loc,
@@ -213,6 +219,10 @@ int rho_grid(const DevModel& M, int num_sms, int max_ops, size_t rho_doubles);
 int prepare_rho(int optin);
 int launch_rho(const DevModel& M, int num_sms, int optin, const BatchView& B, const EvalCfg& cfg, const Work& W,
                const ctq_result& R, RhoParams P, size_t rho_total_doubles, void* stream);
+
+// Static improved-estimator ratios h^st = w^U / w (improved.cu).
+int launch_static_ratios(int m, const int* chain, int n_chains, const double* log_abs, const double* phase,
+                         const double* log_abs_u, const double* phase_u, double* h, void* stream);
 
 size_t big64_block_elems(int dn, int dk);
 int format_big64_blocks(const HostModel& h, const double* d_blk, void* out, const std::vector<int64_t>& off, bool x2);

@@ -49,7 +49,7 @@ class ModelParamsC(ctypes.Structure):
 
 class InfoC(ctypes.Structure):
     _fields_ = [("n_flav", c_int), ("n_sec", c_int), ("max_dim", c_int), ("is_complex", c_int),
-                ("mu", c_double), ("E_gs", c_double), ("n_block_elems", c_int64)]
+                ("mu", c_double), ("E_gs", c_double), ("n_block_elems", c_int64), ("n_alpha", c_int)]
 
 
 class BatchC(ctypes.Structure):
@@ -94,6 +94,8 @@ def _load():
         "ctq_eval_density_matrices": (c_int, [P, POINTER(BatchC), POINTER(EvalOptsC), POINTER(ResultC), P, P,
                                               c_size_t, P]),
         "ctq_eval_traces_static": (c_int, [P, POINTER(BatchC), POINTER(EvalOptsC), POINTER(ResultC), P]),
+        "ctq_add_bulla_operators": (c_int, [P, P, P]),
+        "ctq_static_ratios": (c_int, [c_int, P, c_int, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -107,7 +109,8 @@ EXPORTED = ("ctq_build_impurity", "ctq_load_impurity", "ctq_impurity_info", "ctq
             "ctq_get_energies", "ctq_get_block", "ctq_workspace_size", "ctq_eval_traces",
             "ctq_launches_per_eval", "ctq_free_impurity", "ctq_strerror", "ctq_last_error_message",
             "ctq_probe_fma_rate", "ctq_tc_gemm_check", "ctq_big_gemm_check", "ctq_eval_traces_static",
-            "ctq_trace_kernel", "ctq_density_size", "ctq_density_workspace_size", "ctq_eval_density_matrices")
+            "ctq_trace_kernel", "ctq_density_size", "ctq_density_workspace_size", "ctq_eval_density_matrices",
+            "ctq_add_bulla_operators", "ctq_static_ratios")
 
 # Size of the library-owned scratch used by eval_traces_static (ctq.h).
 STATIC_SCRATCH_BYTES = 32 << 20
@@ -171,6 +174,7 @@ class Impurity:
         self.mu = info.mu
         self.E_gs = info.E_gs
         self.n_block_elems = info.n_block_elems
+        self.n_alpha = info.n_alpha
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -192,9 +196,26 @@ class Impurity:
         _check(_lib.ctq_get_energies(self.handle, q, _ptr(E)), "ctq_get_energies")
         return E
 
+    def add_bulla_operators(self, h: Optional[np.ndarray] = None):
+        """ctq_add_bulla_operators: operator codes 2 n_flav + f become the
+        Bulla operators [c_f, U]; h: the one-body matrix t - mu (n_flav x
+        n_flav, flavour basis), or None for the one the library built."""
+        h_re = h_im = None
+        if h is not None:
+            h = np.asarray(h, dtype=np.complex128).reshape(self.n_flav, self.n_flav)
+            h_re = np.ascontiguousarray(h.real)
+            h_im = np.ascontiguousarray(h.imag) if np.any(h.imag != 0) else None
+        _check(_lib.ctq_add_bulla_operators(self.handle, _ptr(h_re), _ptr(h_im)), "ctq_add_bulla_operators")
+        info = InfoC()
+        _check(_lib.ctq_impurity_info(self.handle, ctypes.byref(info)), "ctq_impurity_info")
+        self.n_alpha = info.n_alpha
+        self.n_block_elems = info.n_block_elems
+
     def block(self, alpha: int, q: int) -> np.ndarray:
         dims, _, _, s = self.sectors()
-        qp = int(s[alpha, q])
+        # a Bulla operator 2 n_flav + f maps sectors as c_f (code 2 f)
+        row = alpha if alpha < 2 * self.n_flav else 2 * (alpha - 2 * self.n_flav)
+        qp = int(s[row, q])
         if qp < 0:
             raise CtqError(CTQ_ERR_ARG, "zero block")
         re = np.zeros((int(dims[qp]), int(dims[q])))
@@ -401,6 +422,55 @@ class TraceEvaluator:
         if self.bounds is not None:
             out["bounds"] = self.bounds[: n * (self.n_seg + 1)].cpu().numpy().reshape(n, self.n_seg + 1)
         return out
+
+
+def bulla_code(n_flav: int, f: int) -> int:
+    """Operator code of the Bulla operator [c_f, U] (after ctq_add_bulla_operators)."""
+    return 2 * n_flav + f
+
+
+def static_ratios(chain, n_chains: int, log_abs, phase, log_abs_u, phase_u, out, stream=None):
+    """ctq_static_ratios on device tensors: chain int32 [m] (configuration of
+    each replaced sequence), log_abs / phase of the configurations, log_abs_u /
+    phase_u of the replaced sequences, out float64 [2 m] (h^st as re, im)."""
+    import torch
+    m = int(chain.numel())
+    if out.numel() < 2 * m or log_abs_u.numel() < m or phase_u.numel() < 2 * m:
+        raise ValueError("ratio buffers smaller than the sequence count")
+    s = torch.cuda.current_stream() if stream is None else stream
+    _check(_lib.ctq_static_ratios(m, chain.data_ptr(), int(n_chains), log_abs.data_ptr(), phase.data_ptr(),
+                                  log_abs_u.data_ptr(), phase_u.data_ptr(), out.data_ptr(), s.cuda_stream),
+           "ctq_static_ratios")
+
+
+class StaticImprovedEvaluator:
+    """Static part of the improved estimator for the self-energy (Eq.
+    PImprovedEstimatorStatic) for every annihilator of every configuration:
+    evaluates the configurations and the replaced sequences
+    (workloads.bulla_sequences) with the library's trace kernels, then
+    h^st = w^U / w with ctq_static_ratios.  The impurity must hold the Bulla
+    operators (Impurity.add_bulla_operators)."""
+
+    def __init__(self, imp: Impurity, n_chains: int, n_seq: int, max_ops: int, precision=FP64, device="cuda",
+                 tune=None):
+        import torch
+        if imp.n_alpha < 3 * imp.n_flav:
+            raise ValueError("the impurity has no Bulla operators (Impurity.add_bulla_operators)")
+        self.base = TraceEvaluator(imp, n_chains, max_ops, precision=precision, with_bounds=False, device=device,
+                                   tune=tune)
+        self.repl = TraceEvaluator(imp, n_seq, max_ops, precision=precision, with_bounds=False, device=device,
+                                   tune=tune)
+        self.h = torch.empty(2 * max(n_seq, 1), dtype=torch.float64, device=device)
+
+    def __call__(self, db: "DeviceBatch", db_u: "DeviceBatch", chain, stream=None):
+        self.base(db, stream=stream)
+        self.repl(db_u, stream=stream)
+        static_ratios(chain, db.n_chains, self.base.log_abs, self.base.phase, self.repl.log_abs, self.repl.phase,
+                      self.h, stream)
+
+    def ratios(self, n_seq: int) -> np.ndarray:
+        v = self.h[: 2 * n_seq].cpu().numpy()
+        return v[0::2] + 1j * v[1::2]
 
 
 def log_value(log_abs: float, phase) -> complex:

@@ -252,6 +252,33 @@ def g2_chain(rng, n_flav: int, k: int, beta: float, width: int = 2):
     return tau, op
 
 
+def bulla_sequences(batch: Batch, n_flav: int):
+    """Input of the static improved estimator (Eq. PImprovedEstimatorStatic):
+    for every chain and each of its annihilators c_f (codes 2 f), the chain
+    with that one operator replaced by the Bulla operator [c_f, U] (code
+    2 n_flav + f), times unchanged.  Returns (Batch of the replaced sequences,
+    int32 chain index of each, int32 position of the replaced operator within
+    its chain), sequences ordered by chain, then position."""
+    op = np.asarray(batch.op, np.int64)
+    offs = np.asarray(batch.offsets, np.int64)
+    lens = np.diff(offs)
+    chain_of = np.repeat(np.arange(batch.n_chains), lens)
+    ann = np.nonzero((op < 2 * n_flav) & (op % 2 == 0))[0]
+    c_new = chain_of[ann]
+    pos = ann - offs[c_new]
+    ln = lens[c_new]
+    new_offs = np.zeros(len(ann) + 1, np.int64)
+    np.cumsum(ln, out=new_offs[1:])
+    # gather index of every entry of the replaced sequences
+    start = np.repeat(offs[c_new] - new_offs[:-1], ln)
+    gather = np.arange(int(new_offs[-1]), dtype=np.int64) + start
+    op_new = op[gather].astype(np.int32)
+    op_new[new_offs[:-1] + pos] = (2 * n_flav + op[ann] // 2).astype(np.int32)
+    out = Batch(beta=batch.beta, offsets=new_offs.astype(np.int32),
+                tau=np.asarray(batch.tau, np.float64)[gather], op=op_new)
+    return out, c_new.astype(np.int32), pos.astype(np.int32)
+
+
 def _pack(chains, beta, model=None) -> Batch:
     offs = [0]
     for t, _ in chains:

@@ -1,0 +1,223 @@
+"""GPU parity of the static improved estimator (Sec. 2.4, Eq.
+PImprovedEstimatorStatic) through the C ABI: the traces of the sequences
+with one annihilator replaced by its Bulla operator [c_f, U]
+(ctq_add_bulla_operators, ctq_eval_traces) and the ratios h^st = w^U / w
+(ctq_static_ratios), against oracle.improved.
+
+Bars: each replaced trace as any FP64 trace (relative 1e-12, or 8x the
+chain's own float64 rounding spread; two-float: the two-float bar); the
+ratio kernel against the same arithmetic on the host to 16 ulps (the
+device and host exponentials and complex products round differently); h^st
+against the oracle's ratio within the two traces' bars propagated through
+the quotient."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import parity  # noqa: E402
+from oracle import atom  # noqa: E402
+from oracle import improved as OI  # noqa: E402
+from paper_2010_08482_gb300 import ctq  # noqa: E402
+from paper_2010_08482_gb300 import workloads as w  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+X2_REL = 100.0 * parity.FP64_REL
+STATED_TC = {(ctq.TF32X3, "t2g"): 5e-4}  # 10x the mixed-precision bar of plain t2g traces
+
+
+def small_complex_model():
+    cf = w.crystal_field_complex(4, 0.3, 17)
+    return w.ModelParams("k2c", n_orb=2, l=0, interaction="kanamori", U=3.0, J=0.6, beta=4.0, mu=1.1,
+                         n0=2, cf=cf, sector_mode="n")
+
+
+def evaluate(imp, sub, n_flav, precision=ctq.FP64):
+    bu, chain, pos = w.bulla_sequences(sub, n_flav)
+    db, dbu = ctq.DeviceBatch(sub), ctq.DeviceBatch(bu)
+    ev = ctq.StaticImprovedEvaluator(imp, sub.n_chains, bu.n_chains, max(db.max_ops, 1), precision=precision)
+    ch = torch.as_tensor(chain, device="cuda")
+    ev(db, dbu, ch)
+    torch.cuda.synchronize()
+    return bu, chain, pos, ev
+
+
+def log_scale(ref, kind):
+    return parity.log_sum_abs_q0(ref) if kind == "sum_q0" else ref["log_abs"]
+
+
+def check(m, mb, sub, bu, chain, ev, bar, scale_floor=0.0):
+    """Replaced traces and ratios against the oracle; returns the worst errors.
+    scale_floor > 0 (two different eigenbases) also allows that much error
+    relative to the configuration's conditioning scale e^{log_cond} (the
+    float64 rounding of the two bases' blocks, which a near-cancelling trace
+    does not scale down)."""
+    n_seq = bu.n_chains
+    ru = ev.repl.results(n_seq)
+    rb = ev.base.results(sub.n_chains)
+    ref_u = parity.oracle_chain_results(mb, bu, range(n_seq))
+    ref_b = parity.oracle_chain_results(mb, sub, range(sub.n_chains))
+    h = ev.ratios(n_seq)
+    worst_u = worst_h = 0.0
+    for i in range(n_seq):
+        c = int(chain[i])
+        rw = ref_b[c]
+        if ref_u[i]["log_abs"] == -math.inf and ru["log_abs"][i] != -math.inf:
+            # exactly zero in the oracle (a symmetry of its eigenbasis):
+            # float64 rounding noise only, far below the configuration's scale
+            assert rw["log_cond"] != -math.inf and ru["log_abs"][i] < rw["log_cond"] - 20, (i, c)
+            eu, ku, tu = 0.0, "zero", 0.0
+        else:
+            eu, ku = parity.chain_error(ru["log_abs"][i], ru["phase"][i], ref_u[i])
+            tu = bar(ref_u[i])
+            if scale_floor > 0.0 and ref_u[i]["log_abs"] != -math.inf:
+                lc = max(ref_u[i]["log_cond"], rw["log_cond"])
+                tu = max(tu, scale_floor * math.exp(lc - log_scale(ref_u[i], ku)))
+            assert eu <= tu, (i, c, eu, ku)
+        worst_u = max(worst_u, eu)
+        # the ratio kernel: the same quotient taken on the host from the
+        # library's own two results
+        la, lu = rb["log_abs"][c], ru["log_abs"][i]
+        if not np.isfinite(la):
+            assert math.isnan(h[i].real) and math.isnan(h[i].imag)
+            continue
+        if lu == -math.inf:
+            assert h[i] == 0
+        else:
+            pu = complex(*ru["phase"][i])
+            pb = complex(*rb["phase"][c])
+            hh = math.exp(lu - la) * pu * pb.conjugate()
+            assert abs(h[i] - hh) <= 16 * 2.0 ** -52 * abs(hh) + 1e-300, (i, h[i], hh)
+        # against the oracle's ratio: bars of both traces through the quotient
+        if rw["log_abs"] == -math.inf:
+            continue
+        ew, kw = parity.chain_error(la, rb["phase"][c], rw)
+        tw = bar(rw)
+        if scale_floor > 0.0:
+            tw = max(tw, scale_floor * math.exp(rw["log_cond"] - log_scale(rw, kw)))
+        assert ew <= tw
+        if ref_u[i]["log_abs"] == -math.inf:
+            h_ref, su = 0j, math.exp(rw["log_cond"] - 20 - rw["log_abs"])
+            tu = 1.0
+        else:
+            h_ref = (complex(ref_u[i]["phase"]) / complex(rw["phase"])
+                     * math.exp(ref_u[i]["log_abs"] - rw["log_abs"]))
+            su = math.exp(log_scale(ref_u[i], ku) - rw["log_abs"])
+        sw = math.exp(log_scale(rw, kw) - rw["log_abs"])
+        tol = 2.0 * (tu * su + tw * sw * abs(h_ref)) + 1e-300
+        assert abs(h[i] - h_ref) <= tol, (i, c, h[i], h_ref, tol)
+        if h_ref != 0:
+            worst_h = max(worst_h, abs(h[i] - h_ref) / abs(h_ref))
+    return worst_u, worst_h
+
+
+@pytest.mark.parametrize("name,n", [("hubbard2", 32), ("t2g", 48), ("d5", 4)])
+def test_static_improved_fp64_on_oracle_eigenbasis(name, n, models):
+    m = models(name)
+    mb = OI.with_bulla(m)
+    sub = w.WORKLOADS[name][1]().subset(range(n))
+    imp = parity.load_oracle_model(ctq, m)
+    imp.add_bulla_operators(atom.one_body_matrix(m.params, m.mu))
+    assert imp.n_alpha == 3 * m.n_flav
+    bu, chain, pos, ev = evaluate(imp, sub, m.n_flav)
+    assert bu.n_chains > n
+    wu, wh = check(m, mb, sub, bu, chain, ev, parity.fp64_tolerance)
+    print(f"\n{name}: {bu.n_chains} replaced sequences, max rel err w^U {wu:.2e}, h^st {wh:.2e}")
+
+
+@pytest.mark.parametrize("name", ["hubbard2", "complex"])
+def test_static_improved_on_library_eigenbasis(name, models):
+    """The library's own eigenbasis and one-body matrix (ctq_build_impurity,
+    then ctq_add_bulla_operators with no matrix): traces and ratios are
+    basis-invariant, so they compare with the oracle directly."""
+    m = atom.Model(small_complex_model()) if name == "complex" else models(name)
+    mb = OI.with_bulla(m)
+    rng = np.random.default_rng(31)
+    sub = w.random_batch(rng, m.n_flav, m.beta, 24, 2, 10)
+    imp = ctq.build_impurity(m.params, device=0)
+    imp.add_bulla_operators()
+    bu, chain, pos, ev = evaluate(imp, sub, m.n_flav)
+
+    def bar(ref):  # two eigenbases: allow their float64 spread as well
+        return max(1e-11, parity.NOISE_FACTOR * ref.get("noise", 0.0))
+    wu, wh = check(m, mb, sub, bu, chain, ev, bar, scale_floor=1e-12)
+    print(f"\n{name} (library eigenbasis): max rel err w^U {wu:.2e}, h^st {wh:.2e}")
+
+
+def test_static_improved_two_float(models):
+    m = models("t2g")
+    mb = OI.with_bulla(m)
+    sub = w.WORKLOADS["t2g"][1]().subset(range(32))
+    imp = parity.load_oracle_model(ctq, m)
+    imp.add_bulla_operators(atom.one_body_matrix(m.params, m.mu))
+    bu, chain, pos, ev = evaluate(imp, sub, m.n_flav, precision=ctq.F32X2)
+
+    def bar(ref):
+        return max(X2_REL, 32.0 * parity.fp64_tolerance(ref))
+    wu, wh = check(m, mb, sub, bu, chain, ev, bar)
+    print(f"\nt2g F32X2: max rel err w^U {wu:.2e}, h^st {wh:.2e}")
+
+
+def test_static_improved_tensor_cores(models):
+    m = models("t2g")
+    mb = OI.with_bulla(m)
+    sub = w.WORKLOADS["t2g"][1]().subset(range(24))
+    imp = parity.load_oracle_model(ctq, m)
+    imp.add_bulla_operators(atom.one_body_matrix(m.params, m.mu))
+    assert ctq.trace_kernel(imp, ctq.TF32X3) == ctq.KERNEL_TC_SMALL
+    bu, chain, pos, ev = evaluate(imp, sub, m.n_flav, precision=ctq.TF32X3)
+
+    def bar(ref):
+        return STATED_TC[(ctq.TF32X3, "t2g")] * max(1.0, ref.get("noise", 0.0) / 1e-15)
+    wu, wh = check(m, mb, sub, bu, chain, ev, bar)
+    print(f"\nt2g TF32X3: max rel err w^U {wu:.2e}, h^st {wh:.2e}")
+
+
+def test_full_t2g_batch_sampled(models):
+    """Every annihilator of the full 4096-chain t2g batch in one evaluation
+    (the benchmark shape); sampled sequences against the oracle."""
+    m = models("t2g")
+    mb = OI.with_bulla(m)
+    b = w.WORKLOADS["t2g"][1]()
+    imp = parity.load_oracle_model(ctq, m)
+    imp.add_bulla_operators(atom.one_body_matrix(m.params, m.mu))
+    bu, chain, pos, ev = evaluate(imp, b, m.n_flav)
+    h = ev.ratios(bu.n_chains)
+    ru = ev.repl.results(bu.n_chains)
+    assert np.all(np.isin(ru["status"], [ctq.CHAIN_OK, ctq.CHAIN_ZERO]))
+    rng = np.random.default_rng(5)
+    sample = np.sort(rng.choice(bu.n_chains, size=48, replace=False))
+    for i in sample:
+        c = int(chain[i])
+        tau, ops = b.chain(c)
+        ratios = dict(OI.static_ratios(mb, tau, ops, beta=b.beta))
+        h_ref = ratios[int(pos[i])]
+        if math.isnan(h_ref.real):
+            assert math.isnan(h[i].real)
+            continue
+        assert abs(h[i] - h_ref) <= 1e-9 * max(1.0, abs(h_ref)), (i, h[i], h_ref)
+
+
+def test_ratio_kernel_edge_cases():
+    """Zero, failed and out-of-range configurations; w^U = 0; complex phases."""
+    dev = "cuda"
+    la = torch.tensor([0.5, -math.inf, math.nan, 700.0], dtype=torch.float64, device=dev)
+    ph = torch.tensor([1.0, 0.0, -1.0, 0.0, 0.0, 0.0, 0.6, 0.8], dtype=torch.float64, device=dev)
+    chain = torch.tensor([0, 1, 2, 4, -1, 0, 3, 0], dtype=torch.int32, device=dev)
+    lu = torch.tensor([1.25, 0.0, 0.0, 0.0, 0.0, -math.inf, 702.0, math.nan], dtype=torch.float64, device=dev)
+    pu = torch.tensor([0.0, 1.0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, -0.8, 0.6, 1, 0], dtype=torch.float64, device=dev)
+    out = torch.full((16,), 7.0, dtype=torch.float64, device=dev)
+    ctq.static_ratios(chain, 4, la, ph, lu, pu, out)
+    torch.cuda.synchronize()
+    h = out.cpu().numpy()
+    h = h[0::2] + 1j * h[1::2]
+    assert abs(h[0] - math.exp(0.75) * 1j) <= 8 * 2.0 ** -52 * math.exp(0.75)
+    for i in (1, 2, 3, 4, 7):  # w = 0, w failed, index out of range (twice), w^U failed
+        assert math.isnan(h[i].real) and math.isnan(h[i].imag), i
+    assert h[5] == 0
+    ref6 = math.exp(2.0) * complex(-0.8, 0.6) * complex(0.6, -0.8)
+    assert abs(h[6] - ref6) <= 16 * 2.0 ** -52 * abs(ref6)
+    ctq.static_ratios(chain[:0], 4, la, ph, lu, pu, out)  # m = 0 launches nothing

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 from oracle import atom
+from oracle import improved as OI
 from oracle import trace as OT
 from paper_2010_08482_gb300 import ctq
 from paper_2010_08482_gb300 import workloads as w
@@ -97,10 +98,15 @@ class _LibModel:
         self.E = [imp.energies(q) for q in range(self.n_sec)]
         self.E_min = np.asarray([e[0] for e in self.E])
         self.E_gs = float(self.E_min.min())
-        self.s = s.astype(np.int64)
+        nf = imp.n_flav
+        # Bulla operators 2 n_flav + f (when present) map sectors as c_f
+        rows = [a if a < 2 * nf else 2 * (a - 2 * nf) for a in range(imp.n_alpha)]
+        self.s = s.astype(np.int64)[rows]
+        self.n_flav = nf
         self.is_complex = imp.is_complex
         self.beta = beta
-        self.F = {(a, q): imp.block(a, q) for a in range(2 * imp.n_flav) for q in range(self.n_sec) if s[a, q] >= 0}
+        self.F = {(a, q): imp.block(a, q) for a in range(imp.n_alpha) for q in range(self.n_sec)
+                  if self.s[a, q] >= 0}
 
     def opnorm(self, a, q):
         return float(np.linalg.norm(self.F[(a, q)], 2))
@@ -144,3 +150,86 @@ def test_load_impurity_roundtrip(models):
     assert list(dims) == m.dims and np.array_equal(s, m.s)
     for (a, q), F in m.F.items():
         assert np.array_equal(imp.block(a, q), F)
+
+
+# ---------------------------------------------------------------- Bulla operators
+
+def small_complex_model():
+    cf = w.crystal_field_complex(4, 0.3, 17)
+    return w.ModelParams("k2c", n_orb=2, l=0, interaction="kanamori", U=3.0, J=0.6, beta=4.0, mu=1.1,
+                         n0=2, cf=cf, sector_mode="n")
+
+
+@pytest.mark.parametrize("name", ["hubbard2", "t2g", "d5"])
+def test_bulla_blocks_on_the_oracle_eigenbasis(name, models):
+    """ctq_add_bulla_operators on the oracle's eigenbasis and one-body matrix
+    against the oracle's Bulla blocks (formed from the interaction terms in
+    the occupation basis): element by element."""
+    import parity
+    m = models(name)
+    mb = OI.with_bulla(m)
+    imp = parity.load_oracle_model(ctq, m, device=-1)
+    imp.add_bulla_operators(atom.one_body_matrix(m.params, m.mu))
+    nf = m.n_flav
+    assert imp.n_alpha == 3 * nf
+    n = 0
+    for f in range(nf):
+        for q in range(m.n_sec):
+            code = OI.bulla_code(nf, f)
+            if mb.s[code, q] < 0:
+                with pytest.raises(ctq.CtqError):
+                    imp.block(code, q)
+                continue
+            ref = mb.F[(code, q)]
+            got = imp.block(code, q)
+            assert np.abs(got - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max()), (f, q)
+            n += 1
+    assert n > 0
+
+
+@pytest.mark.parametrize("name", ["hubbard2", "t2g", "complex"])
+def test_library_bulla_traces_match_oracle(name, models):
+    """Library-built impurity (its own eigenbasis and one-body matrix t - mu):
+    traces with one annihilator replaced by its Bulla operator, evaluated by
+    the oracle's trace routine on the library's blocks, equal the oracle's
+    (basis-invariant)."""
+    m = atom.Model(small_complex_model()) if name == "complex" else models(name)
+    imp = ctq.build_impurity(m.params, device=-1)
+    imp.add_bulla_operators()
+    lm = _LibModel(imp, m.beta)
+    mb = OI.with_bulla(m)
+    rng = np.random.default_rng(12)
+    b = w.random_batch(rng, m.n_flav, m.beta, 12, 2, 8)
+    n_cmp = 0
+    for c in range(b.n_chains):
+        tau, ops = b.chain(c)
+        base = OT.trace_chain(mb, tau, ops)
+        for pos in OI.annihilators(mb, ops)[:3]:
+            seq = OI.bulla_sequence(mb, ops, pos)
+            r1 = OT.trace_chain(mb, tau, seq)
+            r2 = OT.trace_chain(lm, tau, seq)
+            if r1["log_abs"] == -math.inf:
+                # exactly zero in the oracle's eigenbasis (a hidden symmetry):
+                # rounding noise only on the library's
+                assert r2["log_abs"] == -math.inf or r2["log_abs"] < base["log_cond"] - 20
+                continue
+            err = abs(complex(r2["phase"]) * math.exp(r2["log_abs"] - r1["log_abs"]) - complex(r1["phase"]))
+            tol = 1e-11 * math.exp(r1["log_cond"] - r1["log_abs"]) + 1e-12
+            assert err <= tol, (c, pos, err, tol)
+            n_cmp += 1
+    assert n_cmp >= 10
+
+
+def test_bulla_argument_errors(models):
+    import parity
+    m = models("hubbard2")
+    imp = parity.load_oracle_model(ctq, m, device=-1)
+    with pytest.raises(ctq.CtqError):  # a loaded impurity has no one-body matrix of its own
+        imp.add_bulla_operators()
+    h = atom.one_body_matrix(m.params, m.mu)
+    imp.add_bulla_operators(h)
+    with pytest.raises(ctq.CtqError):  # once per impurity
+        imp.add_bulla_operators(h)
+    with pytest.raises(ctq.CtqError):  # complex one-body term on a real impurity
+        imp2 = parity.load_oracle_model(ctq, m, device=-1)
+        imp2.add_bulla_operators(h + 0.1j * np.eye(m.n_flav))
