@@ -130,6 +130,36 @@ def density_flops(imp, batch):
     return total * (4.0 if imp.is_complex else 1.0)
 
 
+def one_pass_ratio_flops(imp, batch):
+    """Real FP64-equivalent flops of the one-pass static ratios over the
+    surviving strings (complex x4): the forward products A_i (the first
+    operator only scales), the backward products (the last only scales) and,
+    per annihilator, the product Y Q and its trace against P A."""
+    dims, _, _, s = imp.sectors()
+    nf2 = s.shape[0]
+    total = 0.0
+    for c in range(batch.n_chains):
+        a, b = batch.offsets[c], batch.offsets[c + 1]
+        ops = batch.op[a:b]
+        n = len(ops)
+        for q0 in range(len(dims)):
+            path, q = [q0], q0
+            for al in ops:
+                q = int(s[al, q])
+                if q < 0:
+                    break
+                path.append(q)
+            if q < 0 or q != q0 or n == 0:
+                continue
+            d0 = float(dims[q0])
+            d = [float(dims[x]) for x in path]
+            total += d[1] * d0 + sum(2.0 * d[i] * d[i - 1] * d0 for i in range(2, n + 1))
+            total += d0 * d[n - 1] + sum(2.0 * d0 * d[i + 1] * d[i] for i in range(0, n - 1))
+            total += sum(2.0 * d0 * d[i + 1] * d[i] + 2.0 * d0 * d[i] for i in range(n)
+                         if ops[i] < nf2 and ops[i] % 2 == 0)
+    return total * (4.0 if imp.is_complex else 1.0)
+
+
 def run_density(args, world, rank, local):
     """The reduced-density-matrix estimator (ctq_eval_density_matrices) on a
     workload: trace evaluation plus the estimator of every chain, float64."""
@@ -201,17 +231,35 @@ def run_improved(args, world, rank, local):
     imp = ctq.build_impurity(mf(), device=local)
     imp.add_bulla_operators()
     bu, chain, _ = w.bulla_sequences(batch, imp.n_flav)
-    db, dbu = ctq.DeviceBatch(batch, device=dev), ctq.DeviceBatch(bu, device=dev)
+    db = ctq.DeviceBatch(batch, device=dev)
     prec = PRECISIONS[args.precision]
-    ev = ctq.StaticImprovedEvaluator(imp, batch.n_chains, bu.n_chains, max(db.max_ops, 1), precision=prec,
-                                     device=dev)
-    ch = torch.as_tensor(chain, device=dev)
-    flops = algorithmic_flops(imp, batch)[0] + algorithmic_flops(imp, bu)[0]
+    one_pass = args.estimator == "hst"
+    if one_pass:
+        if args.precision != "fp64":
+            raise SystemExit("--estimator hst runs in fp64 (use hst-seq for the other precisions)")
+        fe = ctq.FusedStaticEvaluator(imp, batch.n_chains, max(db.max_ops, 1), db.n_ops, device=dev)
+        flops = algorithmic_flops(imp, batch)[0] + one_pass_ratio_flops(imp, batch)
+
+        def step():
+            fe(db)
+        launches = ctq.launches_per_eval(imp, prec) + 1
+        kernel = "k_trace<fp64> + k_rho<hst>"
+    else:
+        dbu = ctq.DeviceBatch(bu, device=dev)
+        ev = ctq.StaticImprovedEvaluator(imp, batch.n_chains, bu.n_chains, max(db.max_ops, 1), precision=prec,
+                                         device=dev)
+        ch = torch.as_tensor(chain, device=dev)
+        flops = algorithmic_flops(imp, batch)[0] + algorithmic_flops(imp, bu)[0]
+
+        def step():
+            ev(db, dbu, ch)
+        launches = 2 * ctq.launches_per_eval(imp, prec) + 1
+        kernel = "k_trace<fp64>" if args.precision == "fp64" else "trace kernels<" + args.precision + ">"
     fp64_peak = ctq.probe_fma_rate(local, 0)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
-        ev(db, dbu, ch)
+        step()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
@@ -220,14 +268,13 @@ def run_improved(args, world, rank, local):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ev(db, dbu, ch)
+        step()
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
     clocks.stop()
     mean = statistics.mean(ms)
     achieved = flops / (mean * 1e-3) / 1e12
-    launches = 2 * ctq.launches_per_eval(imp, prec) + 1
     line = {"metric": "static improved-estimator ratios h^st per second (Eq. PImprovedEstimatorStatic), 1xGB300",
             "value": bu.n_chains / (mean * 1e-3), "unit": "ratios/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean, "higher_is_better": True, "scaling": "weak",
@@ -235,11 +282,11 @@ def run_improved(args, world, rank, local):
             "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT[args.workload], "n_chains": batch.n_chains,
                        "replaced_sequences": bu.n_chains, "precision": args.precision,
-                       "estimator": "static improved estimator, Bulla operators [c_f, U]",
+                       "estimator": "static improved estimator, Bulla operators [c_f, U], "
+                                    + ("one pass (forward / backward products)" if one_pass else "replaced sequences"),
                        "l2": "flushed (256 MiB write) between steps"},
             "tflops": achieved, "algorithmic_flops_per_step": flops,
-            "roofline": {"kernel": "k_trace<fp64>" if args.precision == "fp64" else f"trace kernels<{args.precision}>",
-                         "bound": "alu", "achieved": achieved, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+            "roofline": {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
                          "frac": achieved / (fp64_peak / 1e12),
                          "peak_source": "measured FP64 FMA rate (ctq_probe_fma_rate, this run)", "traffic": None},
             "gpu_launches": args.steps * launches, "clocks": clocks.summary()}
@@ -497,9 +544,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--chains", type=int, default=0, help="evaluate only the first N chains of the workload")
     ap.add_argument("--no-autotune", action="store_true", help="library-default launch configuration")
-    ap.add_argument("--estimator", default="trace", choices=["trace", "rho", "hst"],
+    ap.add_argument("--estimator", default="trace", choices=["trace", "rho", "hst", "hst-seq"],
                     help="trace: local traces (default); rho: traces plus the reduced-density-matrix estimator; "
-                         "hst: the static improved-estimator ratio of every annihilator")
+                         "hst: the static improved-estimator ratio of every annihilator in one pass; "
+                         "hst-seq: the same from traces of the replaced sequences")
     ap.add_argument("--autotune-cache", default=None, help="JSON cache of tuned launch configurations")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -514,7 +562,7 @@ def main():
     if args.estimator == "rho":
         run_density(args, world, rank, local)
         return
-    if args.estimator == "hst":
+    if args.estimator in ("hst", "hst-seq"):
         run_improved(args, world, rank, local)
         return
     import torch

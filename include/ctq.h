@@ -330,6 +330,31 @@ int ctq_static_ratios(int m, const int32_t* chain, int n_chains, const double* l
                       const double* log_abs_u, const double* phase_u, double* h, void* stream);
 
 /*
+ * The same ratios for every annihilator of every configuration in one pass
+ * (Sec. 2.4, Eq. PImprovedEstimatorStatic), without replaced sequences: after
+ * the float64 trace evaluation of the batch (ctq_eval_traces, results in
+ * `result`), the forward products A_i and backward products Y_i of each
+ * surviving string (those of the density-matrix estimator) give
+ *   w^U_i = Tr[ Y_i Q_i P_{Delta_i} A_i ]
+ * for the annihilator at operator i replaced by Q_i = [c_f, U], one product
+ * per annihilator instead of a trace of a replaced sequence.  The impurity
+ * must hold the Bulla operators (ctq_add_bulla_operators).
+ * h: device float64 [2 n_ops], n_ops = offsets[n_chains] (the batch's total
+ * operator count): entry 2 k, 2 k + 1 is h^st (re, im) of the operator with
+ * global index k when it is an annihilator (code 2 f), 0 otherwise; every
+ * entry of a chain whose status is not CTQ_CHAIN_OK is 0.  Writes beyond
+ * n_ops are skipped.  CTQ_FP64 without lazy rejects, blocks that fit the
+ * shared-memory kernel (CTQ_ERR_UNSUPPORTED otherwise).  Workspace:
+ * ctq_static_ratio_workspace_size() bytes, 256-byte aligned.  Asynchronous on
+ * `stream`; enqueues the trace evaluation, one memset and the ratio kernel.
+ * Errors: CTQ_ERR_ARG, CTQ_ERR_WORKSPACE, CTQ_ERR_UNSUPPORTED, CTQ_ERR_CUDA.
+ */
+size_t ctq_static_ratio_workspace_size(const ctq_impurity* imp, int n_chains, const ctq_eval_opts* opts);
+int ctq_eval_static_ratios(const ctq_impurity* imp, const ctq_batch* batch, const ctq_eval_opts* opts,
+                           const ctq_result* result, double* h, int n_ops, void* workspace, size_t workspace_bytes,
+                           void* stream);
+
+/*
  * Number of kernels one ctq_eval_traces call enqueues (for launch accounting).
  */
 int ctq_launches_per_eval(const ctq_impurity* imp, const ctq_eval_opts* opts);

@@ -672,6 +672,50 @@ int ctq_eval_density_matrices(const ctq_impurity* imp, const ctq_batch* batch, c
   return CTQ_OK;
 }
 
+size_t ctq_static_ratio_workspace_size(const ctq_impurity* imp, int n_chains, const ctq_eval_opts* opts) {
+  if (!imp || !opts || n_chains < 0) return 0;
+  const size_t base = ctq::workspace_layout(n_chains, imp->host.n_sec, n_seg_of(opts), nullptr, nullptr);
+  const int grid = ctq::rho_grid(imp->dev, imp->num_sms, std::max(0, opts->max_ops), 0);
+  return ((base + 255) & ~size_t(255)) + ctq::rho_scratch_bytes(imp->host, std::max(0, opts->max_ops), grid);
+}
+
+int ctq_eval_static_ratios(const ctq_impurity* imp, const ctq_batch* batch, const ctq_eval_opts* opts,
+                           const ctq_result* result, double* h, int n_ops, void* workspace, size_t workspace_bytes,
+                           void* stream) {
+  if (!imp || !batch || !opts || !result || !h) return fail(CTQ_ERR_ARG, "null argument");
+  if (opts->precision != CTQ_FP64 || opts->lazy) return fail(CTQ_ERR_ARG, "the ratios run in CTQ_FP64 without lazy rejects");
+  if (imp->device < 0) return fail(CTQ_ERR_ARG, "impurity has no device copy");
+  if (imp->host.n_extra < imp->host.n_flav) return fail(CTQ_ERR_ARG, "no Bulla operators (ctq_add_bulla_operators)");
+  if (imp->big64) return fail(CTQ_ERR_UNSUPPORTED, "blocks too large for the static-ratio kernel");
+  if (n_ops < 0) return fail(CTQ_ERR_ARG, "n_ops < 0");
+  if (batch->n_chains <= 0) return batch->n_chains == 0 ? CTQ_OK : fail(CTQ_ERR_ARG, "n_chains < 0");
+  const size_t need = ctq_static_ratio_workspace_size(imp, batch->n_chains, opts);
+  if (workspace_bytes < need) return fail(CTQ_ERR_WORKSPACE, "workspace smaller than ctq_static_ratio_workspace_size()");
+  const int n_seg = n_seg_of(opts);
+  const size_t base = ctq::workspace_layout(batch->n_chains, imp->host.n_sec, n_seg, nullptr, nullptr);
+  int st = ctq_eval_traces(imp, batch, opts, result, workspace, base, stream);
+  if (st != CTQ_OK) return st;
+  DeviceGuard g(imp->device);
+  if (!g.ok()) return fail(CTQ_ERR_CUDA, "cudaSetDevice failed");
+  ctq::Work W;
+  ctq::workspace_layout(batch->n_chains, imp->host.n_sec, n_seg, workspace, &W);
+  ctq::BatchView B{batch->n_chains, batch->beta, batch->offsets, batch->tau, batch->op, batch->log_threshold};
+  ctq::EvalCfg cfg;
+  cfg.lazy = 0;
+  cfg.has_thr = 0;
+  cfg.S = opts->segment;
+  cfg.n_seg_max = n_seg;
+  cfg.max_ops = opts->max_ops;
+  ctq::RhoParams P;
+  P.rho = h;
+  P.h_len = size_t(n_ops);
+  P.scratch = static_cast<char*>(workspace) + ((base + 255) & ~size_t(255));
+  P.scratch_elems = size_t(std::max(opts->max_ops, 1) + 1) * imp->host.max_dim * imp->host.max_dim;
+  st = ctq::launch_rho(imp->dev, imp->num_sms, imp->optin, B, cfg, W, *result, P, 2 * size_t(n_ops), stream, true);
+  if (st != CTQ_OK) return fail(st, st == CTQ_ERR_CUDA ? cudaGetErrorString(cudaGetLastError()) : "launch failed");
+  return CTQ_OK;
+}
+
 int ctq_trace_kernel(const ctq_impurity* imp, int precision) {
   if (!imp) return CTQ_ERR_ARG;
   if (imp->device < 0) return CTQ_ERR_ARG;

@@ -212,13 +212,14 @@ struct RhoParams {
   void* scratch = nullptr;          // per-CTA storage of the forward products
   size_t scratch_elems = 0;         // elements (real or complex) per CTA
   int local_acc = 0;                // estimator summed in shared memory per string
+  size_t h_len = 0;                 // static ratios: operator slots of the output (pairs)
 };
 size_t rho_elems(const HostModel& h);
 size_t rho_scratch_bytes(const HostModel& h, int max_ops, int grid);
 int rho_grid(const DevModel& M, int num_sms, int max_ops, size_t rho_doubles);
 int prepare_rho(int optin);
 int launch_rho(const DevModel& M, int num_sms, int optin, const BatchView& B, const EvalCfg& cfg, const Work& W,
-               const ctq_result& R, RhoParams P, size_t rho_total_doubles, void* stream);
+               const ctq_result& R, RhoParams P, size_t rho_total_doubles, void* stream, bool hst = false);
 
 // Static improved-estimator ratios h^st = w^U / w (improved.cu).
 int launch_static_ratios(int m, const int* chain, int n_chains, const double* log_abs, const double* phase,

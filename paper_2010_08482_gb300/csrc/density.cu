@@ -17,6 +17,18 @@
 //           atomics; w_C from the trace evaluation that precedes it).
 // float64 throughout; blocks of both products live in shared memory (the
 // sizes of the shared-memory trace kernel).
+//
+//   HST     the same two passes give the static improved-estimator ratio
+//           (Sec. 2.4, Eq. PImprovedEstimatorStatic) of every annihilator
+//           c_f at operator i: with the annihilator replaced by its Bulla
+//           operator Q = [c_f, U] (operator code 2 n_f + f),
+//             w^U_i = Tr[ Y_i Q P_{Delta_i} A_i ],
+//           Y_i the backward product after operator i (its propagator
+//           included), A_i the stored forward product before it and
+//           P_{Delta_i} the propagator of the interval that ends at
+//           operator i (A_0 = 1, P = P_{tau_1}(q0) for the first operator).
+//           One extra product per annihilator instead of a full trace of a
+//           replaced sequence; h^st_i = sum_{q0} w^U_i / w_C.
 #include <algorithm>
 
 #include "device_common.cuh"
@@ -96,7 +108,7 @@ __device__ __forceinline__ double kernel_rel(double a, double b, double ea, doub
   return ((a < b) ? ea : eb) * (-expm1(-D * gap) / gap);
 }
 
-template <bool CPLX>
+template <bool CPLX, bool HST>
 __global__ void __launch_bounds__(256) k_rho(DevModel M, BatchView B, EvalCfg cfg, Work W, ctq_result R, RhoParams P) {
   using T = typename Num<CPLX>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -191,6 +203,7 @@ __global__ void __launch_bounds__(256) k_rho(DevModel M, BatchView B, EvalCfg cf
       }
     };
 
+    if (HST && n == 0) continue;  // no operator, no ratio
     if (n == 0) {  // one interval (0, beta) with G = identity
       for (int idx = tid; idx < d0 * d0; idx += nt) {
         const int u = idx / d0, v = idx - u * d0;
@@ -250,7 +263,7 @@ __global__ void __launch_bounds__(256) k_rho(DevModel M, BatchView B, EvalCfg cf
     }
     // interval n: (tau_n, beta) in q0, G = A_n, B_n = I
     aoff -= size_t(d0) * d0;  // A_n (d0 x d0) is the last stored product
-    accumulate(Ast + aoff, q0, t_last, eA[n]);
+    if (!HST) accumulate(Ast + aoff, q0, t_last, eA[n]);
     __syncthreads();
 
     // ---- backward: Y = P_{beta - tau_n}(q0), then B_i = Y F_{i+1}, G_i = A_i B_i
@@ -267,6 +280,12 @@ __global__ void __launch_bounds__(256) k_rho(DevModel M, BatchView B, EvalCfg cf
       const int qa = path[i];  // F_{i+1} maps qa -> path[i + 1]
       const int dq = M.dims[qa];
       const int64_t off = M.blk_off[opsm[i] * ns + qa];
+      const T* Ai = nullptr;  // A_i is d_{q_i} x d0 (i >= 1)
+      if (i >= 1) {
+        aoff -= size_t(dq) * d0;
+        Ai = Ast + aoff;
+      }
+      const double Dlen = (i == 0) ? t_first : (B.tau[a0 + i] - B.tau[a0 + i - 1]);
       // Xn = Y F  (d0 x dq), F is dy x dq
       for (int idx = tid; idx < d0 * dq; idx += nt) {
         const int j = idx / dq, m = idx - j * dq;
@@ -275,15 +294,53 @@ __global__ void __launch_bounds__(256) k_rho(DevModel M, BatchView B, EvalCfg cf
         Xn[idx] = acc;
       }
       __syncthreads();
+      if (HST && opsm[i] < 2 * M.n_flav && (opsm[i] & 1) == 0) {
+        // w^U_i / w_C = 2^{e} e^{base} sum_{j, m} (Y Q)_{jm} e^{-Dlen E_m} (A_i)_{mj}, Q dy x dq
+        const int64_t qoff = M.blk_off[(2 * M.n_flav + (opsm[i] >> 1)) * ns + qa];
+        const double* Eq = M.E_rel + M.E_off[qa];
+        for (int m = tid; m < dq; m += nt) ex[m] = exp(-Dlen * Eq[m]);
+        __syncthreads();
+        T part = num_zero(T());
+        if (qoff >= 0) {
+          for (int idx = tid; idx < d0 * dq; idx += nt) {
+            const int j = idx / dq, m = idx - j * dq;
+            if (i == 0 && m != j) continue;  // A_0 = 1
+            T yq = num_zero(T());
+            for (int k = 0; k < dy; ++k) num_fma(yq, X[j * dy + k], num_blk(M.blk, qoff + int64_t(k) * dq + m, T()));
+            const T z = (i == 0) ? num_scale(num_one(T()), ex[m]) : num_scale(Ai[m * d0 + j], ex[m]);
+            num_fma(part, yq, z);
+          }
+        }
+        const double f = exp(base + double(ebacc + (i >= 1 ? eA[i] : 0)) * LN2);
+        double pr, pi;
+        if constexpr (CPLX) {
+          pr = part.x;
+          pi = part.y;
+        } else {
+          pr = part;
+          pi = 0.0;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          pr += __shfl_down_sync(0xffffffffu, pr, o);
+          pi += __shfl_down_sync(0xffffffffu, pi, o);
+        }
+        if ((tid & 31) == 0 && (pr != 0.0 || pi != 0.0) && size_t(a0) + i < P.h_len) {
+          // (w^U / |w|) conj(phase)
+          double* hdst = P.rho + 2 * (size_t(a0) + i);
+          atomicAdd(hdst, f * (pr * phr + pi * phi));
+          atomicAdd(hdst + 1, f * (pi * phr - pr * phi));
+        }
+        __syncthreads();
+      }
       ebacc += block_rescale(Xn, d0 * dq, redi, &dead);
       if (dead) break;  // B_i = 0, and so are the products of every earlier interval
       // G_i = A_i B_i (dq x dq) into X (Y is no longer needed); A_0 = I
       T* G = X;
-      if (i == 0) {
+      if (HST) {
+        // no interval products: Y = B_i P_{Delta} below
+      } else if (i == 0) {
         for (int idx = tid; idx < dq * dq; idx += nt) G[idx] = Xn[idx];
       } else {
-        aoff -= size_t(dq) * d0;  // A_i is d_{q_i} x d0
-        const T* Ai = Ast + aoff;
         for (int idx = tid; idx < dq * dq; idx += nt) {
           const int u = idx / dq, v = idx - u * dq;
           T acc = num_zero(T());
@@ -292,8 +349,7 @@ __global__ void __launch_bounds__(256) k_rho(DevModel M, BatchView B, EvalCfg cf
         }
       }
       __syncthreads();
-      const double Dlen = (i == 0) ? t_first : (B.tau[a0 + i] - B.tau[a0 + i - 1]);
-      accumulate(G, qa, Dlen, ebacc + (i >= 1 ? eA[i] : 0));
+      if (!HST) accumulate(G, qa, Dlen, ebacc + (i >= 1 ? eA[i] : 0));
       __syncthreads();
       // Y = B_i P_{Delta} for the next (earlier) operator
       if (i > 0) {
@@ -345,18 +401,26 @@ int rho_grid(const DevModel& M, int num_sms, int max_ops, size_t rho_doubles) {
 
 int prepare_rho(int optin) {
   cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, k_rho<false>) != cudaSuccess) return CTQ_ERR_CUDA;
-  const int cap = optin - int(fa.sharedSizeBytes);
-  if (cudaFuncSetAttribute(k_rho<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess ||
-      cudaFuncSetAttribute(k_rho<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess)
+  int stat = 0;
+  for (const void* fn : {reinterpret_cast<const void*>(k_rho<false, false>), reinterpret_cast<const void*>(k_rho<true, false>),
+                         reinterpret_cast<const void*>(k_rho<false, true>), reinterpret_cast<const void*>(k_rho<true, true>)}) {
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return CTQ_ERR_CUDA;
+    stat = std::max(stat, int(fa.sharedSizeBytes));
+  }
+  const int cap = optin - stat;
+  if (cudaFuncSetAttribute(k_rho<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess ||
+      cudaFuncSetAttribute(k_rho<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess ||
+      cudaFuncSetAttribute(k_rho<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess ||
+      cudaFuncSetAttribute(k_rho<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess)
     return CTQ_ERR_CUDA;
   return CTQ_OK;
 }
 
 int launch_rho(const DevModel& M, int num_sms, int optin, const BatchView& B, const EvalCfg& cfg, const Work& W,
-               const ctq_result& R, RhoParams P, size_t rho_total_doubles, void* stream) {
+               const ctq_result& R, RhoParams P, size_t rho_total_doubles, void* stream, bool hst) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  P.local_acc = P.rho_elems * 8 <= RHO_LOCAL_MAX ? 1 : 0;
+  if (hst) P.rho_elems = 0;  // ratios go straight to the output, one pair per operator
+  P.local_acc = (!hst && P.rho_elems * 8 <= RHO_LOCAL_MAX) ? 1 : 0;
   const size_t smem = rho_smem(M.max_dim, M.is_complex != 0, cfg.max_ops, P.rho_elems);
   if (smem + 1024 > size_t(optin)) return CTQ_ERR_UNSUPPORTED;
   const int threads = M.max_dim <= 12 ? 32 : (M.max_dim <= 32 ? 128 : 256);
@@ -364,10 +428,16 @@ int launch_rho(const DevModel& M, int num_sms, int optin, const BatchView& B, co
   if (cudaMemsetAsync(P.rho, 0, rho_total_doubles * sizeof(double), st) != cudaSuccess) return CTQ_ERR_CUDA;
   // the item counter of this pass (the trace pass used counters[1])
   if (cudaMemsetAsync(W.counters + 3, 0, sizeof(int), st) != cudaSuccess) return CTQ_ERR_CUDA;
-  if (M.is_complex)
-    k_rho<true><<<grid, threads, smem, st>>>(M, B, cfg, W, R, P);
-  else
-    k_rho<false><<<grid, threads, smem, st>>>(M, B, cfg, W, R, P);
+  if (hst) {
+    if (M.is_complex)
+      k_rho<true, true><<<grid, threads, smem, st>>>(M, B, cfg, W, R, P);
+    else
+      k_rho<false, true><<<grid, threads, smem, st>>>(M, B, cfg, W, R, P);
+  } else if (M.is_complex) {
+    k_rho<true, false><<<grid, threads, smem, st>>>(M, B, cfg, W, R, P);
+  } else {
+    k_rho<false, false><<<grid, threads, smem, st>>>(M, B, cfg, W, R, P);
+  }
   return cudaGetLastError() == cudaSuccess ? CTQ_OK : CTQ_ERR_CUDA;
 }
 

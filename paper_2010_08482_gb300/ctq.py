@@ -96,6 +96,9 @@ def _load():
         "ctq_eval_traces_static": (c_int, [P, POINTER(BatchC), POINTER(EvalOptsC), POINTER(ResultC), P]),
         "ctq_add_bulla_operators": (c_int, [P, P, P]),
         "ctq_static_ratios": (c_int, [c_int, P, c_int, P, P, P, P, P, P]),
+        "ctq_static_ratio_workspace_size": (c_size_t, [P, c_int, POINTER(EvalOptsC)]),
+        "ctq_eval_static_ratios": (c_int, [P, POINTER(BatchC), POINTER(EvalOptsC), POINTER(ResultC), P, c_int, P,
+                                           c_size_t, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -110,7 +113,8 @@ EXPORTED = ("ctq_build_impurity", "ctq_load_impurity", "ctq_impurity_info", "ctq
             "ctq_launches_per_eval", "ctq_free_impurity", "ctq_strerror", "ctq_last_error_message",
             "ctq_probe_fma_rate", "ctq_tc_gemm_check", "ctq_big_gemm_check", "ctq_eval_traces_static",
             "ctq_trace_kernel", "ctq_density_size", "ctq_density_workspace_size", "ctq_eval_density_matrices",
-            "ctq_add_bulla_operators", "ctq_static_ratios")
+            "ctq_add_bulla_operators", "ctq_static_ratios", "ctq_static_ratio_workspace_size",
+            "ctq_eval_static_ratios")
 
 # Size of the library-owned scratch used by eval_traces_static (ctq.h).
 STATIC_SCRATCH_BYTES = 32 << 20
@@ -360,6 +364,7 @@ class DeviceBatch:
     def __init__(self, batch, device="cuda", log_threshold: Optional[np.ndarray] = None):
         import torch
         self.n_chains = batch.n_chains
+        self.n_ops = len(batch.tau)
         self.beta = float(batch.beta)
         self.max_ops = int(np.max(np.diff(batch.offsets))) if batch.n_chains else 0
         self.offsets = torch.as_tensor(np.asarray(batch.offsets, np.int32), device=device)
@@ -470,6 +475,49 @@ class StaticImprovedEvaluator:
 
     def ratios(self, n_seq: int) -> np.ndarray:
         v = self.h[: 2 * n_seq].cpu().numpy()
+        return v[0::2] + 1j * v[1::2]
+
+
+class FusedStaticEvaluator:
+    """ctq_eval_static_ratios: the static improved-estimator ratio of every
+    annihilator of every configuration in one pass over the configurations
+    (forward and backward products, one extra product per annihilator),
+    float64.  The impurity must hold the Bulla operators."""
+
+    def __init__(self, imp: Impurity, n_chains: int, max_ops: int, n_ops: int, device="cuda"):
+        import torch
+        if imp.n_alpha < 3 * imp.n_flav:
+            raise ValueError("the impurity has no Bulla operators (Impurity.add_bulla_operators)")
+        self.imp = imp
+        self.n_chains, self.max_ops, self.n_ops = n_chains, max_ops, n_ops
+        o = _opts(FP64, False, 8, max_ops)
+        self.ws_bytes = int(_lib.ctq_static_ratio_workspace_size(imp.handle, n_chains, ctypes.byref(o)))
+        self._ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=device)
+        self.ws_ptr = (self._ws.data_ptr() + 255) // 256 * 256
+        self.log_abs = torch.empty(n_chains, dtype=torch.float64, device=device)
+        self.phase = torch.empty(2 * n_chains, dtype=torch.float64, device=device)
+        self.status = torch.empty(n_chains, dtype=torch.int32, device=device)
+        self.h = torch.empty(2 * max(n_ops, 1), dtype=torch.float64, device=device)
+
+    def __call__(self, db: "DeviceBatch", stream=None):
+        import torch
+        if db.n_chains > self.n_chains or db.max_ops > self.max_ops or db.n_ops > self.n_ops:
+            raise ValueError("batch larger than the evaluator was sized for")
+        s = torch.cuda.current_stream() if stream is None else stream
+        b = BatchC()
+        b.n_chains, b.beta = db.n_chains, db.beta
+        b.offsets, b.tau, b.op, b.log_threshold = db.offsets.data_ptr(), db.tau.data_ptr(), db.op.data_ptr(), None
+        r = ResultC()
+        r.log_abs, r.phase, r.status, r.bounds = (self.log_abs.data_ptr(), self.phase.data_ptr(),
+                                                  self.status.data_ptr(), None)
+        o = _opts(FP64, False, 8, self.max_ops)
+        _check(_lib.ctq_eval_static_ratios(self.imp.handle, ctypes.byref(b), ctypes.byref(o), ctypes.byref(r),
+                                           self.h.data_ptr(), db.n_ops, self.ws_ptr, self.ws_bytes, s.cuda_stream),
+               "ctq_eval_static_ratios")
+
+    def ratios(self, n_ops: int) -> np.ndarray:
+        """h^st by global operator index (0 where the operator is not an annihilator)."""
+        v = self.h[: 2 * n_ops].cpu().numpy()
         return v[0::2] + 1j * v[1::2]
 
 

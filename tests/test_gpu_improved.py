@@ -221,3 +221,89 @@ def test_ratio_kernel_edge_cases():
     ref6 = math.exp(2.0) * complex(-0.8, 0.6) * complex(0.6, -0.8)
     assert abs(h[6] - ref6) <= 16 * 2.0 ** -52 * abs(ref6)
     ctq.static_ratios(chain[:0], 4, la, ph, lu, pu, out)  # m = 0 launches nothing
+
+
+# ---------------------------------------------------------------- one-pass ratios (ctq_eval_static_ratios)
+
+def kind_of(ref):
+    """The scale chain_error measures against: |w|, or sum_q0 |w_q0| when the
+    q0 terms cancel."""
+    return "sum_q0" if parity.log_sum_abs_q0(ref) - ref["log_abs"] > math.log(parity.CANCEL) else "abs"
+
+
+def fused(imp, sub):
+    db = ctq.DeviceBatch(sub)
+    fe = ctq.FusedStaticEvaluator(imp, sub.n_chains, max(db.max_ops, 1), db.n_ops)
+    fe(db)
+    torch.cuda.synchronize()
+    return fe.ratios(db.n_ops), fe.status.cpu().numpy()
+
+
+def check_fused(m, mb, sub, hf, status, bar, floor):
+    """One-pass ratios against the oracle's ratio of every annihilator; every
+    other entry exactly 0.  floor: error allowed relative to the replaced
+    trace's conditioning scale e^{log_cond} (the one-pass product associates
+    Y (Q (P A)) instead of the string order)."""
+    bu, chain, pos = w.bulla_sequences(sub, m.n_flav)
+    ref_u = parity.oracle_chain_results(mb, bu, range(bu.n_chains))
+    ref_b = parity.oracle_chain_results(mb, sub, range(sub.n_chains))
+    ann = np.zeros(len(sub.op), bool)
+    ann[np.asarray(sub.offsets[chain], np.int64) + pos] = True
+    assert np.all(hf[~ann] == 0)
+    worst = 0.0
+    for i in range(bu.n_chains):
+        c = int(chain[i])
+        k = int(sub.offsets[c]) + int(pos[i])
+        rw, ru = ref_b[c], ref_u[i]
+        if status[c] != ctq.CHAIN_OK:
+            assert hf[k] == 0 and rw["log_abs"] == -math.inf
+            continue
+        if rw["log_abs"] == -math.inf:  # exactly zero in the oracle: the ratio is undefined
+            continue
+        if ru["log_abs"] == -math.inf:
+            assert abs(hf[k]) <= 2 * floor * math.exp(rw["log_cond"] - rw["log_abs"]) + 1e-300, (i, hf[k])
+            continue
+        h_ref = complex(ru["phase"]) / complex(rw["phase"]) * math.exp(ru["log_abs"] - rw["log_abs"])
+        ls_u = log_scale(ru, kind_of(ru))
+        tu = max(bar(ru), floor * math.exp(max(ru["log_cond"], rw["log_cond"]) - ls_u))
+        su = math.exp(ls_u - rw["log_abs"])
+        tw = max(bar(rw), floor * math.exp(rw["log_cond"] - rw["log_abs"]))
+        sw = math.exp(log_scale(rw, kind_of(rw)) - rw["log_abs"])
+        tol = 2.0 * (tu * su + tw * sw * abs(h_ref)) + 1e-300
+        assert abs(hf[k] - h_ref) <= tol, (i, c, int(pos[i]), hf[k], h_ref, tol)
+        worst = max(worst, abs(hf[k] - h_ref) / abs(h_ref))
+    return worst
+
+
+@pytest.mark.parametrize("name,n", [("hubbard2", 32), ("t2g", 48), ("d5", 4)])
+def test_one_pass_ratios_on_oracle_eigenbasis(name, n, models):
+    m = models(name)
+    mb = OI.with_bulla(m)
+    sub = w.WORKLOADS[name][1]().subset(range(n))
+    imp = parity.load_oracle_model(ctq, m)
+    imp.add_bulla_operators(atom.one_body_matrix(m.params, m.mu))
+    hf, status = fused(imp, sub)
+    worst = check_fused(m, mb, sub, hf, status, parity.fp64_tolerance, 1e-13)
+    print(f"\n{name} one pass: max rel err h^st {worst:.2e}")
+
+
+def test_one_pass_ratios_complex_library_eigenbasis(models):
+    m = atom.Model(small_complex_model())
+    mb = OI.with_bulla(m)
+    rng = np.random.default_rng(31)
+    sub = w.random_batch(rng, m.n_flav, m.beta, 24, 2, 10)
+    imp = ctq.build_impurity(m.params, device=0)
+    imp.add_bulla_operators()
+    hf, status = fused(imp, sub)
+
+    def bar(ref):
+        return max(1e-11, parity.NOISE_FACTOR * ref.get("noise", 0.0))
+    worst = check_fused(m, mb, sub, hf, status, bar, 1e-12)
+    print(f"\ncomplex one pass (library eigenbasis): max rel err h^st {worst:.2e}")
+
+
+def test_one_pass_needs_bulla_operators(models):
+    m = models("hubbard2")
+    imp = parity.load_oracle_model(ctq, m)
+    with pytest.raises(ValueError):
+        ctq.FusedStaticEvaluator(imp, 4, 8, 32)
