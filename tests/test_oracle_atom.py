@@ -282,3 +282,25 @@ def test_symmetry_forbidden_string_is_exactly_zero(models):
     tau = [0.5, 1.0, 2.0, 3.0, 4.0, 5.0]
     r = OT.trace_chain(m, tau, [11, 10, 8, 4, 1, 9])
     assert r["log_abs"] == -math.inf
+
+
+@pytest.mark.parametrize("l,U,J", [(2, 8.0, 1.0), (2, 3.0, 0.4), (3, 4.5, 0.5), (3, 6.0, 0.9)])
+def test_slater_F_reproduces_average_U_and_J(l, U, J):
+    """slater_F pinned through the standard orbital averages of the Slater
+    interaction (App. A: F0 = U and J fix the Slater integrals), which any
+    reading of (U, J) -> F^k must satisfy:
+        U     = (2l+1)^-2        sum_{m,m'} U_{mm'},
+        U - J = [2l(2l+1)]^-1    sum_{m,m'} (U_{mm'} - J_{mm'}),
+    with U_{mm'} = <m m'|V|m m'> and J_{mm'} = <m m'|V|m' m>.  Averages over
+    all orbital pairs are invariant under a unitary change of orbital basis,
+    so the complex- and real-harmonic tensors must give the same U and J."""
+    V = atom.slater_orbital_tensor(l, atom.slater_F(l, U, J))
+    T = atom.real_harmonics_T(l)
+    n = 2 * l + 1
+    for tensor in (V, atom.to_real_basis_tensor(V, T)):
+        Umm = np.array([[tensor[a, b, a, b] for b in range(n)] for a in range(n)])
+        Jmm = np.array([[tensor[a, b, b, a] for b in range(n)] for a in range(n)])
+        U_avg = Umm.sum() / n ** 2
+        UJ_avg = (Umm - Jmm).sum() / (n * (n - 1))
+        assert abs(U_avg - U) < 1e-12
+        assert abs((U_avg - UJ_avg) - J) < 1e-12

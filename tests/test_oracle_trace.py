@@ -236,6 +236,60 @@ def test_level0_bound_is_tight_for_single_state():
     assert B == pytest.approx(r["log_abs"], abs=1e-12)
 
 
+def test_refined_bounds_are_tight_for_single_state():
+    """One state per sector: every block is 1 x 1 with |F| = ||F||_2 = 1,
+    r = 1 and each propagator is the scalar e^{-dtau E_min}, so every refined
+    bound sqrt(r) ||Y_j||_F prod_{i>j} ||F_i||_2 e^{-dtau E_min} equals |w_q0|
+    (a doubled or misplaced tail factor would break the equality)."""
+    m = atom.Model(w.model_atom1(3.0, 1.0, 5.0))
+    tau, ops = [0.3, 2.0, 3.5, 4.0, 4.2, 4.9], [1, 3, 0, 2, 1, 0]
+    r = T.trace_chain(m, tau, ops)
+    for S in (1, 2, 4):
+        for q0, (lw, _) in r["per_q0"].items():
+            ub = T.refined_bounds_q0(m, np.asarray(tau), np.asarray(ops), q0, m.beta, S)
+            assert len(ub) == -(-len(ops) // S) + 1
+            for u in ub:
+                assert u == pytest.approx(lw, abs=1e-12), (S, q0, ub, lw)
+
+
+class _TwoSectorModel:
+    """Hand-built model: sectors q0 and q1 of dimension 2, operator 0 maps
+    q0 -> q1 with block A, operator 1 maps q1 -> q0 with block B."""
+
+    def __init__(self, A, B, E0, E1):
+        self.n_sec = 2
+        self.dims = [2, 2]
+        self.s = np.array([[1, -1], [-1, 0]])
+        self.F = {(0, 0): np.asarray(A, float), (1, 1): np.asarray(B, float)}
+        self.E = [np.asarray(E0, float), np.asarray(E1, float)]
+        self.E_min = [min(E0), min(E1)]
+        self.E_gs = min(self.E_min)
+        self.is_complex = False
+
+    def opnorm(self, alpha, q):
+        return float(np.linalg.norm(self.F[(alpha, q)], 2))
+
+
+def test_refined_bounds_hand_built_two_by_two():
+    """Values worked out by hand.  A = [[1, 1], [1, 1]] / 2 (a projector:
+    ||A||_2 = ||A||_F = 1), B = I, energies 0 in q0 and 0.5 (twice) in q1,
+    tau = (1, 3), beta = 10, one operator per segment (S = 1), r = 2:
+      s = 0: sqrt(2) ||I||_F ||A||_2 e^{-2 * 0.5} ||B||_2 = 2 e^{-1}
+      s = 1: sqrt(2) ||e^{-1} A||_F ||B||_2 = sqrt(2) e^{-1}
+      s = 2: |Tr(B e^{-1} A)| = e^{-1}
+    and the level-0 bound r ||A||_2 ||B||_2 e^{-1} = 2 e^{-1}."""
+    m = _TwoSectorModel([[0.5, 0.5], [0.5, 0.5]], np.eye(2), [0.0, 0.0], [0.5, 0.5])
+    tau, ops = np.array([1.0, 3.0]), np.array([0, 1])
+    ub = T.refined_bounds_q0(m, tau, ops, 0, 10.0, 1)
+    exp = [math.log(2.0) - 1.0, 0.5 * math.log(2.0) - 1.0, -1.0]
+    assert ub == pytest.approx(exp, abs=1e-14)
+    assert T.level0_bound(m, tau, ops, 0, 10.0) == pytest.approx(math.log(2.0) - 1.0, abs=1e-14)
+    # the string starting in q1 dies at once (operator 0 annihilates q1)
+    assert T.refined_bounds_q0(m, tau, ops, 1, 10.0, 1) is None
+    r = T.trace_chain(m, tau, ops, beta=10.0)
+    assert r["log_abs"] == pytest.approx(-1.0, abs=1e-14)
+
+
 def test_decide_matches_threshold():
     assert T.decide(-1.0, -1.5) and not T.decide(-2.0, -1.5)
 
