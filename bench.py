@@ -1,18 +1,26 @@
 """Benchmark of the GB300 local-trace path (one JSON line on rank 0).
 
-One step = one ctq_eval_traces call over the whole batch: sector walk and
-level-0 bounds, the chain products with fused propagators, renormalisation,
-per-segment refined bounds, final traces and the per-chain combine.
+One step = one evaluation of the whole batch: sector walk and level-0
+bounds, the chain products with fused propagators, renormalisation,
+per-segment refined bounds and early rejects, final traces and the
+per-chain combine.
 
-Default workload: the 3-orbital t2g Kanamori impurity (U=5, J=0.7, beta=50,
-16 sectors by (N_dn, N_up), blocks <= 9), 4096 seeded chains with orders
-~ Poisson(40), FP64.  `value` is evaluations/s with inputs resident in HBM;
-L2 is flushed (a 256 MiB write) between timed steps, outside the timed
-kernels.  `e2e` repeats the measurement through the same C-ABI call with the
-batch copied from pinned host memory and the results copied back inside the
-timed region.  Multi-GPU (torchrun): every rank evaluates its own batch (no
-collective on the data path; weak scaling); timing is max over ranks.
+Default workload: the uneven mixed batch -- 2048 seeded chains drawn
+uniformly from the 3-orbital t2g, 5-orbital d-shell and 7-orbital f-shell
+impurities, orders uniform in 10..200, lazy bounds on with half the chains
+rejected early -- in three-term split bf16 (BF16X3) on the tensor cores,
+captured once as a CUDA graph and replayed per step.  `value` is
+evaluations/s with the inputs resident in HBM; `e2e` is the same steps
+timed from the host->device copy of the inputs (pinned host memory) to the
+device->host copy of the results; `fp64` times the plain float64 path and
+the mixed path on the same named subset of the batch (the like-for-like
+speedup); `roofline` is the dominant kernel (k_trace_big) timed with CUDA
+events captured inside the graph.  L2 is flushed (a 256 MiB write) between
+steps, outside the timed region.  Multi-GPU (torchrun): every rank
+evaluates its own batch (no collective on the data path; weak scaling);
+timing is max over ranks.
 
+--workload t2g|d5|f7|hubbard2|f45 times one impurity's batch instead, and
 --impl reference times the FP64 CPU oracle (the reference arm here) on a
 bounded sample of the same workload on the host cores.
 """
@@ -48,9 +56,15 @@ WORKLOAD_TEXT = {
     "f7": "7-orbital f-shell Slater-Condon with SOC 0.3 and complex CF sigma=0.05 (14 spin-orbitals, N in {4,5,6}, "
           "sectors 1001/2002/3003, complex), U=4.5, J=0.5, beta=40; 256 chains, order ~Poisson(80)",
 }
-CPU_SAMPLE = {"t2g": 4096, "hubbard2": 64, "d5": 24, "f7": 1}  # cpu_baseline leg: chains cycled for >= 10 s
-CPU_SAMPLE_REF = {"t2g": 64, "hubbard2": 64, "d5": 2, "f7": 1}  # per step of --impl reference
+WORKLOAD_TEXT["f45"] = ("f shell of the f7 model restricted to N in {4,5} (sectors 1001/2002, complex), mu where "
+                        "E_gs(4) = E_gs(5); 2 chains of 80 operators, width-1 particle-number walk (profiling case)")
+CPU_SAMPLE = {"t2g": 4096, "hubbard2": 64, "d5": 24, "f7": 1, "mixed": 4096}  # cpu_baseline: chains cycled >= 10 s
+CPU_SAMPLE_REF = {"t2g": 64, "hubbard2": 64, "d5": 2, "f7": 1, "mixed": 24}  # per step of --impl reference
 FLUSH_BYTES = 256 << 20
+DEFAULT_PRECISION = {"mixed": "bf16x3"}  # every other workload: fp64
+# Chains of the mixed batch on which the float64 path and the mixed path are
+# timed side by side (the first N of the batch).
+FP64_SUBSET = 8
 
 
 def load_peaks():
@@ -340,9 +354,27 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def profile_traffic(kernel: str, workload: str, src_hash: str):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+KERNEL_SOURCES = {
+    "small": ("trace_fp64.cu", "device_common.cuh", "two_float.cuh", "ctq_internal.h"),
+    "big": ("trace_big.cu", "big_common.cuh", "tc_ptx.cuh", "device_common.cuh", "ctq_internal.h"),
+}
+
+
+def source_hash(kind: str = "small") -> str:
+    """Hash of a dominant kernel's code: the shared-memory FP64 kernel
+    ("small") or the large-block tensor-core kernel ("big"), with the
+    headers it includes."""
+    h = hashlib.sha256()
+    for fn in KERNEL_SOURCES[kind]:
+        with open(os.path.join(ROOT, "paper_2010_08482_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def profile_traffic(kernel: str, workload: str, kind: str = "small"):
+    """DRAM bytes per launch from a committed ncu summary
+    (profiles/<kernel>_<workload>.md, lines "- key: value"), if it was taken
+    on the current kernel source (else None)."""
     p = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(p):
         return None
@@ -351,7 +383,7 @@ def profile_traffic(kernel: str, workload: str, src_hash: str):
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip().split()[0] if v.strip() else ""
-    if vals.get("source_sha256", "")[:16] != src_hash[:16]:
+    if vals.get("source_sha256", "")[:16] != source_hash(kind)[:16]:
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -359,40 +391,151 @@ def profile_traffic(kernel: str, workload: str, src_hash: str):
         return None
 
 
-def source_hash() -> str:
-    """Hash of the dominant kernel's code (trace_fp64.cu and the headers it
-    includes)."""
-    h = hashlib.sha256()
-    for fn in ("trace_fp64.cu", "device_common.cuh", "two_float.cuh", "ctq_internal.h"):
-        with open(os.path.join(ROOT, "paper_2010_08482_gb300", "csrc", fn), "rb") as f:
-            h.update(f.read())
-    return h.hexdigest()
+def host_cpu():
+    """(logical core count, CPU model name) of this host."""
+    n = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return n, model or "unknown"
 
 
-_ORACLE_CACHE = {}
+THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+               "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS")
 
 
-def cpu_oracle_rate(workload: str, n_chains: int, min_s: float = 0.0):
-    """The FP64 oracle, as it stands, on the first n_chains of the workload,
-    cycled through again until at least min_s seconds of CPU work (the
-    cpu_baseline leg asks for 10-30 s).  Returns (evals/s, evaluations, s)."""
+def oracle_subprocess(spec: dict, threads: int, timeout: float = 1200.0) -> dict:
+    """Runs oracle_worker(spec) in a child interpreter whose BLAS / OpenMP
+    thread counts are fixed to `threads` through its environment (set before
+    numpy loads) and which sees no GPU; returns the worker's JSON result."""
+    env = dict(os.environ)
+    for v in THREAD_VARS:
+        env[v] = str(threads)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", json.dumps(spec)],
+                         cwd=ROOT, env=env, capture_output=True, text=True, timeout=timeout)
+    if out.returncode != 0:
+        raise RuntimeError("oracle worker failed: " + out.stderr[-2000:])
+    for line in out.stdout.splitlines():
+        if line.startswith("ORACLE "):
+            return json.loads(line[len("ORACLE "):])
+    raise RuntimeError("oracle worker printed no result: " + out.stdout[-500:])
+
+
+MIXED_ORACLE_NOTE = ("the t2g and d5 chains of the mixed batch in batch order (the f-shell chains are left out: the "
+                     "oracle's f-shell model takes minutes to build and about a minute per chain), each decided "
+                     "as the method does: level-0 bound against the threshold, then the full trace")
+
+
+def oracle_worker(spec: dict) -> dict:
+    """The FP64 oracle, as it stands, on chains of a workload (runs in the
+    child process of oracle_subprocess).  spec: workload; then either
+    per_step + n_steps (per-step rates, the reference arm) or min_s + n_min
+    (one rate over at least n_min evaluations and min_s seconds, cycling
+    through the chains, and the first pass's results).  Chains with a
+    threshold are decided as the method does: the level-0 bound first, the
+    full trace only if the bound reaches the threshold."""
     from oracle import atom
     from oracle import trace as OT
     from paper_2010_08482_gb300 import workloads as w
-    if workload not in _ORACLE_CACHE:
-        mf, bf = w.WORKLOADS[workload]
-        _ORACLE_CACHE[workload] = (atom.Model(mf()), bf())
-    m, b = _ORACLE_CACHE[workload]
-    n = min(n_chains, b.n_chains)
-    t0 = time.perf_counter()
-    count = 0
+    name = spec["workload"]
+    if name == "mixed":
+        batch, coin = w.batch_mixed()
+        ps = {0: w.model_t2g(), 1: w.model_d5()}
+        ms = {mi: atom.Model(p) for mi, p in ps.items()}
+        chains = [c for c in range(batch.n_chains) if int(batch.model[c]) in ps]
+
+        def job(c):
+            mi = int(batch.model[c])
+            return ms[mi], ps[mi].beta, (math.inf if coin[c] else -math.inf)
+    else:
+        mf, bf = w.WORKLOADS[name]
+        batch = bf()
+        m = atom.Model(mf())
+        chains = list(range(batch.n_chains))
+
+        def job(c):
+            return m, batch.beta, None
+    if spec.get("first"):
+        chains = chains[: int(spec["first"])]
+
+    def one(c):
+        m, beta, T = job(c)
+        tau, ops = batch.chain(c)
+        if T is not None:
+            logs = [OT.level0_bound(m, tau, ops, q0, beta) for q0 in range(m.n_sec)]
+            logs = [x for x in logs if x != -math.inf]
+            if not logs:
+                return ["zero", -math.inf, 0.0, 0.0]
+            mx = max(logs)
+            if mx + math.log(sum(math.exp(x - mx) for x in logs)) < T:
+                return ["rejected_early", None, None, None]
+        r = OT.trace_chain(m, tau, ops, beta=beta)
+        ph = complex(r["phase"])
+        st = "ok" if T is None else ("accepted" if OT.decide(r["log_abs"], T) else "rejected")
+        return [st, r["log_abs"], ph.real, ph.imag]
+
+    out = {"chains_in_sample": len(chains), "blas_threads": {v: os.environ.get(v) for v in THREAD_VARS}}
+    if "per_step" in spec:
+        rates, pos = [], 0
+        for _ in range(int(spec["n_steps"])):
+            t0 = time.perf_counter()
+            for _ in range(int(spec["per_step"])):
+                one(chains[pos % len(chains)])
+                pos += 1
+            rates.append(int(spec["per_step"]) / (time.perf_counter() - t0))
+        out["step_rates"] = rates
+        return out
+    results = {}
+    count, t0 = 0, time.perf_counter()
+    n_min = int(spec.get("n_min", len(chains)))
     while True:
-        OT.trace_chain(m, *b.chain(count % n), beta=b.beta)
+        c = chains[count % len(chains)]
+        r = one(c)
+        if count < len(chains):
+            results[str(c)] = r
         count += 1
         dt = time.perf_counter() - t0
-        if count >= n and dt >= min_s:
+        if count >= min(n_min, len(chains)) and dt >= float(spec.get("min_s", 0.0)):
             break
-    return count / dt, count, dt
+    out.update({"rate": count / dt, "count": count, "seconds": dt, "results": results})
+    return out
+
+
+def cpu_baseline_leg(workload: str, n_first: int, min_s: float = 10.0, n_min: int = 0):
+    """The oracle on a bounded sample of the workload (at least min_s seconds
+    and n_min evaluations, default one pass over the first n_first chains),
+    once on one thread and once on every host core (BLAS / OpenMP threads
+    fixed per child process).  Returns (cpu_baseline dict, the one-thread
+    run's per-chain results)."""
+    ncpu, model = host_cpu()
+    spec = {"workload": workload, "first": n_first, "min_s": min_s, "n_min": n_min or n_first}
+    one = oracle_subprocess(spec, threads=1)
+    allc = oracle_subprocess(dict(spec, min_s=min_s), threads=ncpu)
+    what = MIXED_ORACLE_NOTE if workload == "mixed" else f"the first {one['chains_in_sample']} chains of the workload"
+    base = {"value": allc["rate"], "unit": "evals/s", "cores": ncpu, "kind": "oracle",
+            "sample": f"{allc['count']} chain evaluations ({allc['seconds']:.1f} s) cycling over {what}; NumPy FP64 "
+                      f"with BLAS / OpenMP threads = {ncpu} (all host cores)",
+            "one_thread": {"value": one["rate"], "cores": 1,
+                           "sample": f"{one['count']} evaluations ({one['seconds']:.1f} s) of the same chains, "
+                                     "BLAS / OpenMP threads = 1"},
+            "host": {"cpu_count": ncpu, "cpu_model": model}}
+    return base, one["results"]
 
 
 def dist_setup():
@@ -424,123 +567,378 @@ def max_over_ranks(world, x: float, device) -> float:
 
 
 def run_reference(args, world, rank):
+    """The reference arm: the FP64 oracle, as it stands, on the host cores
+    (BLAS / OpenMP threads = all cores), a bounded sample of the workload per
+    step; rank 0 only."""
     if rank != 0:
         return
-    per_step = CPU_SAMPLE_REF.get(args.workload, 8)
-    rates = []
-    for i in range(args.warmup + args.steps):
-        r, n, dt = cpu_oracle_rate(args.workload, per_step)
-        if i >= args.warmup:
-            rates.append(r)
+    workload = args.workload
+    per_step = CPU_SAMPLE_REF.get(workload, 8)
+    ncpu, model = host_cpu()
+    res = oracle_subprocess({"workload": workload, "per_step": per_step, "n_steps": args.warmup + args.steps},
+                            threads=ncpu)
+    rates = res["step_rates"][args.warmup:]
     value = statistics.mean(rates)
+    what = MIXED_ORACLE_NOTE if workload == "mixed" else f"the {res['chains_in_sample']} chains of the workload"
+    sample = (f"{per_step} chain evaluations per step cycling over {what}; NumPy FP64, BLAS / OpenMP threads = "
+              f"{ncpu} (all host cores of a {model})")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_step / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_TEXT[args.workload], "parallelism": "host cores, 1 process"},
-        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {per_step} chains of the workload per step, NumPy FP64, 1 thread"},
+        "config": {"workload": WORKLOAD_TEXT[workload], "parallelism": "host cores, 1 process"},
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": ncpu, "kind": "oracle", "sample": sample,
+                         "host": {"cpu_count": ncpu, "cpu_model": model}},
         "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
+class _Group:
+    """One impurity's share of the mixed batch: its chains, device batch,
+    evaluator, timing events (captured inside the graph) and pinned host
+    copies of its inputs and results."""
+
+
+def _err_stats(errs):
+    if not errs:
+        return None
+    e = np.asarray(errs)
+    return {"n": int(e.size), "max": float(e.max()), "p90": float(np.quantile(e, 0.9)), "median": float(np.median(e))}
+
+
+def _rel_err(la, ph, la_ref, ph_ref):
+    """|w - w_ref| / |w_ref| for values held as (log|w|, phase)."""
+    if la_ref == -math.inf:
+        return 0.0 if la == -math.inf else math.inf
+    if not np.isfinite(la):
+        return math.inf
+    return abs(complex(ph[0], ph[1]) * math.exp(la - la_ref) - complex(ph_ref[0], ph_ref[1]))
+
+
 def run_mixed(args, world, rank, local):
-    """The uneven mixed batch: chains of three impurities evaluated on one
-    stream (one ctq_eval_traces per impurity), lazy bounds on.  The coin of
-    each chain sets its threshold to +inf (every bound falls below it: level-0
-    reject) or -inf (never rejected: full trace, accepted), which reproduces
-    the intended 50 % early rejects without an oracle pass."""
+    """The uneven mixed batch (the default workload): chains of the t2g, d5
+    and f7 impurities, one ctq_eval_traces per impurity, lazy bounds on,
+    captured once as a CUDA graph and replayed per step.  The coin of each
+    chain sets its threshold to +inf (every bound falls below it: rejected
+    at level 0, before any product) or -inf (never rejected: full trace,
+    accepted), which gives the workload's 50 % early rejects with known
+    decisions."""
+    import ctypes
+
     import torch
+    from paper_2010_08482_gb300 import autotune
     from paper_2010_08482_gb300 import ctq
     from paper_2010_08482_gb300 import workloads as w
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    batch, coin = w.batch_mixed()
+    t_setup = time.perf_counter()
+    batch, coin = w.batch_mixed(rank=rank)
     if args.chains:
         keep = np.arange(min(args.chains, batch.n_chains))
         batch, coin = batch.subset(keep), coin[keep]
-    models = [w.model_t2g(), w.model_d5(), w.model_f7()]
+    params = [w.model_t2g(), w.model_d5(), w.model_f7()]
     prec = PRECISIONS[args.precision]
-    groups, flops = [], 0.0
-    for mi, p in enumerate(models):
+    stream = torch.cuda.current_stream()
+    groups = []
+    for mi, p in enumerate(params):
         idx = np.nonzero(batch.model == mi)[0]
         if idx.size == 0:
             continue
-        sub = batch.subset(idx)
-        sub.beta = p.beta  # the mixed batch draws each chain's times in [0, beta) of its own model
-        thr = np.where(coin[idx] == 1, np.inf, -np.inf)
-        imp = ctq.build_impurity(p, device=local)
-        db = ctq.DeviceBatch(sub, device=dev, log_threshold=thr)
-        ev = ctq.TraceEvaluator(imp, sub.n_chains, db.max_ops, precision=prec, device=dev)
-        f, _ = algorithmic_flops(imp, sub.subset(np.nonzero(coin[idx] == 0)[0]))
-        flops += f
-        groups.append((p.name, imp, db, ev, sub.n_chains))
-    n_chains = sum(g[4] for g in groups)
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g = _Group()
+        g.name, g.idx = p.name, idx
+        g.sub = batch.subset(idx)
+        g.sub.beta = p.beta  # the mixed batch draws each chain's times in [0, beta) of its own model
+        g.thr = np.where(coin[idx] == 1, np.inf, -np.inf)
+        g.imp = ctq.build_impurity(p, device=local)
+        g.db = ctq.DeviceBatch(g.sub, device=dev, log_threshold=g.thr)
+        g.tuning = {}
+        acc = np.nonzero(coin[idx] == 0)[0]
+        if not args.no_autotune and acc.size:
+            eng = autotune.engine(g.imp, prec)
+            if eng != "fp64big":  # the float64 large-block kernel is FP64-pipe bound: nothing to tune
+                piece = acc[:4] if eng == "big" else acc[:512]
+                tdb = ctq.DeviceBatch(g.sub.subset(piece), device=dev, log_threshold=np.full(piece.size, -np.inf))
+                g.tuning = autotune.tune(g.imp, tdb, prec, lazy=True, cache_path=args.autotune_cache,
+                                         reps=1 if eng == "big" else 3)
+        g.ev = ctq.TraceEvaluator(g.imp, g.sub.n_chains, g.db.max_ops, precision=prec, device=dev, tune=g.tuning)
+        g.flops, g.items = algorithmic_flops(g.imp, g.sub.subset(acc))
+        g.launches = ctq.launches_per_eval(g.imp, prec)
+        g.events = [torch.cuda.Event(enable_timing=True) for _ in range(g.launches + 1)]
+        for e in g.events:
+            e.record(stream)  # materialise the cudaEvent_t handles
+        g.ev_arr = (ctypes.c_void_p * len(g.events))(*[e.cuda_event for e in g.events])
+        g.ev_ptr = ctypes.cast(g.ev_arr, ctypes.c_void_p).value
+        n, n_ops = g.sub.n_chains, len(g.sub.tau)
+        g.h_off = torch.as_tensor(np.asarray(g.sub.offsets, np.int32)).pin_memory()
+        g.h_tau = torch.as_tensor(np.asarray(g.sub.tau, np.float64)).pin_memory()
+        g.h_op = torch.as_tensor(np.asarray(g.sub.op, np.int32)).pin_memory()
+        g.h_thr = torch.as_tensor(g.thr.astype(np.float64)).pin_memory()
+        g.h_la = torch.empty(n, dtype=torch.float64).pin_memory()
+        g.h_ph = torch.empty(2 * n, dtype=torch.float64).pin_memory()
+        g.h_st = torch.empty(n, dtype=torch.int32).pin_memory()
+        g.n_ops = n_ops
+        g.kern_ms = []
+        groups.append(g)
+    n_chains = sum(g.sub.n_chains for g in groups)
+    # The group with the most work runs on the main stream; the others are
+    # forked onto side streams and joined again, so that their small-block
+    # kernels run beside the large-block kernel (which keeps one CTA per SM
+    # and leaves room on each SM for small CTAs).
+    order = sorted(groups, key=lambda g: -g.flops)
+    side = [torch.cuda.Stream(device=dev) for _ in order[1:]]
 
     def step():
-        for _, _, db, ev, _ in groups:
-            ev(db, lazy=True)
+        cur = torch.cuda.current_stream()
+        if args.serial_groups:
+            for g in groups:
+                g.ev(g.db, lazy=True, events=g.ev_ptr)
+            return
+        fork = torch.cuda.Event()
+        fork.record(cur)
+        for sd in side:
+            sd.wait_event(fork)
+        order[0].ev(order[0].db, lazy=True, events=order[0].ev_ptr)
+        for g, sd in zip(order[1:], side):
+            with torch.cuda.stream(sd):
+                g.ev(g.db, lazy=True, events=g.ev_ptr)
+        for sd in side:
+            cur.wait_stream(sd)
 
-    for _ in range(args.warmup):
-        step()
+    step()  # eager first evaluation (also the library's first-call set-up)
     torch.cuda.synchronize()
-    # The whole mixed evaluation (every impurity's plan / trace / combine
-    # launches) is captured once as a CUDA graph and replayed per step.
-    graph, graph_note = None, "captured"
+    # The whole mixed evaluation (every impurity's memsets and plan / trace /
+    # combine launches, with the timing events as event-record nodes) is
+    # captured once as a CUDA graph and replayed per step.
+    graph, graph_note = None, "captured once, replayed per step"
     try:
         cap_stream = torch.cuda.Stream(device=dev)
         cap_stream.wait_stream(stream)
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=cap_stream):
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr, stream=cap_stream):
             step()
         torch.cuda.synchronize()
-        g.replay()
-        torch.cuda.synchronize()
-        graph = g
-    except Exception as exc:  # capture is refused: run the same launches eagerly
+        graph = gr
+    except Exception as exc:  # capture refused: the same launches eagerly
         torch.cuda.synchronize()
         graph_note = f"eager ({type(exc).__name__}: {str(exc)[:80]})"
     run = graph.replay if graph is not None else step
-    for _ in range(2):
+    for _ in range(max(args.warmup - 1, 0)):
         run()
     torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
+
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    e_start, e0, e1, e_end = (torch.cuda.Event(enable_timing=True) for _ in range(4))
     clocks = ClockSampler(local)
     clocks.start()
-    ms = []
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    step_ms, e2e_ms = [], []
     for _ in range(args.steps):
+        flush.zero_()
+        e_start.record(stream)
+        for g in groups:  # this step's inputs, host (pinned) -> device
+            g.db.offsets.copy_(g.h_off, non_blocking=True)
+            g.db.tau[: g.n_ops].copy_(g.h_tau, non_blocking=True)
+            g.db.op[: g.n_ops].copy_(g.h_op, non_blocking=True)
+            g.db.log_threshold.copy_(g.h_thr, non_blocking=True)
         e0.record(stream)
         run()
         e1.record(stream)
-        e1.synchronize()
-        ms.append(e0.elapsed_time(e1))
+        for g in groups:  # results, device -> host (pinned)
+            n = g.sub.n_chains
+            g.h_la.copy_(g.ev.log_abs[:n], non_blocking=True)
+            g.h_ph.copy_(g.ev.phase[: 2 * n], non_blocking=True)
+            g.h_st.copy_(g.ev.status[:n], non_blocking=True)
+        e_end.record(stream)
+        e_end.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        e2e_ms.append(e_start.elapsed_time(e_end))
+        for g in groups:
+            g.kern_ms.append([g.events[k].elapsed_time(g.events[k + 1]) for k in range(g.launches)])
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - t0
     clocks.stop()
-    status = {g[0]: np.bincount(g[3].results(g[4])["status"] + 1, minlength=6)[1:].tolist() for g in groups}
-    mean = statistics.mean(ms)
-    line = {"metric": METRIC, "value": n_chains / (mean * 1e-3), "unit": "evals/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": WORKLOAD_TEXT["mixed"], "n_chains": n_chains,
-                       "groups": {g[0]: g[4] for g in groups}, "precision": args.precision,
-                       "cuda_graph": graph_note},
-            "tflops": flops / (mean * 1e-3) / 1e12, "algorithmic_flops_per_step": flops,
-            "status_counts [ok, zero, rejected_early, accepted, rejected]": status,
-            "gpu_launches": args.steps * sum(ctq.launches_per_eval(g[1]) for g in groups),
-            "clocks": clocks.summary()}
+    h2d = sum(g.h_off.numel() * 4 + g.h_tau.numel() * 8 + g.h_op.numel() * 4 + g.h_thr.numel() * 8 for g in groups)
+    d2h = sum(g.h_la.numel() * 8 + g.h_ph.numel() * 8 + g.h_st.numel() * 4 for g in groups)
+
+    ms = max_over_ranks(world, statistics.mean(step_ms), dev)
+    e2e = max_over_ranks(world, statistics.mean(e2e_ms), dev)
+    flops = sum(g.flops for g in groups)
+    # decisions of the last step: coin 1 rejected at level 0, coin 0 accepted (or exactly zero)
+    status, decisions_ok = {}, True
+    for g in groups:
+        st = g.h_st.numpy()
+        status[g.name] = np.bincount(st + 1, minlength=6)[1:].tolist()
+        c1 = coin[g.idx] == 1
+        decisions_ok &= bool(np.all(st[c1] == ctq.CHAIN_REJECTED_EARLY))
+        decisions_ok &= bool(np.all(np.isin(st[~c1], [ctq.CHAIN_ACCEPTED, ctq.CHAIN_ZERO])))
+    # dominant kernel: the trace kernel of the group with the most step time
+    dom = max(groups, key=lambda g: statistics.mean(k[1] for k in g.kern_ms))
+    dom_ms = statistics.mean(k[1] for k in dom.kern_ms)
+    big = dom.imp.is_complex or dom.imp.max_dim > 112
+    achieved = dom.flops / (dom_ms * 1e-3) / 1e12
+    fp64_peak = ctq.probe_fma_rate(local, 0)
+    fp32_rate = ctq.probe_fma_rate(local, 1) if args.precision == "f32x2" else None
+    kname = kernel_name(args.precision, big)
+    # DRAM bytes per launch from a committed ncu summary of this kernel on the
+    # f shell (profiles/k_trace_big_<precision>_f7.md), if current
+    traffic = profile_traffic(f"k_trace_big_{args.precision}", "f7", "big") if big else None
+    roof = roofline(args.precision, achieved, fp64_peak, traffic, big=big, fp32_rate=fp32_rate, sustained=True)
+    roof["kernel"] = kname
+    group_span = {g.name: statistics.mean(sum(k) for k in g.kern_ms) for g in groups}
+    per_group = {g.name: {"chains": int(g.sub.n_chains), "evaluated": int(np.sum(coin[g.idx] == 0)),
+                          "surviving_strings": int(g.items), "algorithmic_flops": g.flops,
+                          "kernel_ms": {"plan": statistics.mean(k[0] for k in g.kern_ms),
+                                        "trace": statistics.mean(k[1] for k in g.kern_ms),
+                                        "combine": statistics.mean(k[2] for k in g.kern_ms)},
+                          "launch_tuning": g.tuning or "library default"} for g in groups}
+    line = {
+        "metric": METRIC, "value": world * n_chains / (ms * 1e-3), "unit": "evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_TEXT[args.precision], "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT["mixed"] + (f" (first {n_chains} chains)" if args.chains else ""),
+                   "n_chains": n_chains, "precision": args.precision, "groups": per_group,
+                   "thresholds": "coin 1: +inf (rejected on the level-0 bound), coin 0: -inf (full trace, "
+                                 "accepted)", "cuda_graph": graph_note,
+                   "groups_overlapped": (f"no (one stream)" if args.serial_groups else
+                                         f"{order[0].name} on the main stream, "
+                                         + ", ".join(g.name for g in order[1:]) + " forked onto side streams"),
+                   "sum_of_group_kernel_ms": sum(group_span.values()),
+                   "l2": "flushed (256 MiB write) between steps",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "tflops": flops / (ms * 1e-3) / 1e12, "algorithmic_flops_per_step": flops,
+        "roofline": roof,
+        "e2e": {"value": world * n_chains / (e2e * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h,
+                "timed": "the same steps, from the host->device copy of every group's offsets, times, operator "
+                         "codes and thresholds (pinned) to the device->host copy of log|w|, phase and status"},
+        "status_counts [ok, zero, rejected_early, accepted, rejected]": status,
+        "decisions_as_expected": decisions_ok,
+        "gpu_launches": args.steps * sum(g.launches for g in groups),
+        "clocks": clocks.summary(), "wall_s_timed_region": wall, "setup_s": setup_s,
+    }
+    if rank == 0 and world == 1 and not args.no_fp64_subset:
+        line["fp64"] = fp64_subset_leg(args, batch, coin, groups, dev, fp64_peak)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base, oracle_res = cpu_baseline_leg("mixed", CPU_SAMPLE["mixed"], min_s=10.0, n_min=1)
+        line["cpu_baseline"] = base
+        errs = {}
+        for g in groups:
+            e = []
+            la, ph = g.h_la.numpy(), g.h_ph.numpy().reshape(-1, 2)
+            for k, c in enumerate(g.idx):
+                r = oracle_res.get(str(int(c)))
+                if r is None or r[0] != "accepted":
+                    continue
+                e.append(_rel_err(la[k], ph[k], r[1], (r[2], r[3])))
+            if e:
+                errs[g.name] = _err_stats(e)
+        line["error_vs_oracle"] = dict(errs, note="relative error |w - w_oracle| / |w_oracle| of the accepted chains "
+                                                  "of the oracle's sample (t2g and d5; the f shell is compared with "
+                                                  "the float64 GPU path in fp64)")
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def fp64_subset_leg(args, batch, coin, groups, dev, fp64_peak):
+    """The plain float64 path and the mixed path on the same chains: the first
+    FP64_SUBSET chains of the mixed batch, one ctq_eval_traces per impurity
+    on one stream, eager; also the mixed path's error on them against the
+    float64 path."""
+    import torch
+    from paper_2010_08482_gb300 import ctq
+    stream = torch.cuda.current_stream()
+    n_sub = min(args.fp64_subset, batch.n_chains)
+    legs = []
+    for g in groups:
+        loc = np.nonzero(g.idx < n_sub)[0]
+        if loc.size == 0:
+            continue
+        sub = g.sub.subset(loc)
+        db = ctq.DeviceBatch(sub, device=dev, log_threshold=g.thr[loc])
+        acc = loc[coin[g.idx[loc]] == 0]
+        legs.append((g, loc, db, algorithmic_flops(g.imp, g.sub.subset(acc))[0]))
+
+    def timed(precision, reps):
+        evs = [ctq.TraceEvaluator(g.imp, db.n_chains, max(1, db.max_ops), precision=precision, device=dev,
+                                  tune=g.tuning if precision != ctq.FP64 else None) for g, _, db, _ in legs]
+
+        def once():
+            for ev, (_, _, db, _) in zip(evs, legs):
+                ev(db, lazy=True)
+        once()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            once()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        res = [ev.results(db.n_chains) for ev, (_, _, db, _) in zip(evs, legs)]
+        return statistics.mean(ms), res
+
+    prec = PRECISIONS[args.precision]
+    ms64, r64 = timed(ctq.FP64, 1)
+    msm, rm = timed(prec, 3)
+    errs = {}
+    for (g, loc, db, _), a, b in zip(legs, r64, rm):
+        e = [_rel_err(b["log_abs"][k], b["phase"][k], a["log_abs"][k], a["phase"][k])
+             for k in range(len(loc)) if a["status"][k] == ctq.CHAIN_ACCEPTED]
+        if e:
+            errs[g.name] = _err_stats(e)
+    flops = sum(f for *_, f in legs)
+    return {"subset": f"first {n_sub} chains of the mixed batch ("
+                      + ", ".join(f"{g.name}: {len(loc)} chains, {int(np.sum(coin[g.idx[loc]] == 0))} evaluated"
+                                  for g, loc, _, _ in legs) + "), same thresholds, eager launches",
+            "fp64_evals_per_s": n_sub / (ms64 * 1e-3), "fp64_ms": ms64,
+            "fp64_tflops": flops / (ms64 * 1e-3) / 1e12,
+            "fp64_frac_of_fp64_rate": flops / (ms64 * 1e-3) / fp64_peak,
+            "mixed_precision": args.precision, "mixed_evals_per_s": n_sub / (msm * 1e-3), "mixed_ms": msm,
+            "speedup_mixed_over_fp64": ms64 / msm,
+            "mixed_error_vs_fp64": dict(errs, note="relative error of the accepted chains against the float64 "
+                                                   "path (itself held to 1e-12 of the oracle by the tests, plus "
+                                                   "the eigensolver term for library-built impurities)")}
+
+
+def f45_impurity(ctq, w, device: int):
+    """The profiling case's impurity: the f shell with N in {4, 5}, mu at the
+    point where the N = 4 and N = 5 ground states are degenerate, computed
+    from a first build at mu = 0."""
+    p0 = w.model_f45(0.0)
+    imp0 = ctq.build_impurity(p0, device=device)
+    _, N, Emin, _ = imp0.sectors()
+    e4, e5 = float(Emin[N == 4].min()), float(Emin[N == 5].min())
+    del imp0
+    return ctq.build_impurity(w.model_f45(e5 - e4), device=device)
 
 
 def main():
+    if len(sys.argv) >= 3 and sys.argv[1] == "--oracle-worker":
+        print("ORACLE " + json.dumps(oracle_worker(json.loads(sys.argv[2]))), flush=True)
+        return
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="t2g", choices=sorted(WORKLOAD_TEXT))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "tf32x3", "bf16x3", "f32x2"])
+    ap.add_argument("--workload", default="mixed", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--precision", default=None, choices=["fp64", "tf32", "tf32x3", "bf16x3", "f32x2"],
+                    help="default: bf16x3 for the mixed batch, fp64 otherwise")
+    ap.add_argument("--fp64-subset", type=int, default=FP64_SUBSET,
+                    help="mixed batch: chains (the first N) timed in float64 and in the mixed precision")
+    ap.add_argument("--no-fp64-subset", action="store_true")
+    ap.add_argument("--serial-groups", action="store_true",
+                    help="mixed batch: evaluate the impurity groups one after another on one stream")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--chains", type=int, default=0, help="evaluate only the first N chains of the workload")
     ap.add_argument("--no-autotune", action="store_true", help="library-default launch configuration")
@@ -551,6 +949,8 @@ def main():
     ap.add_argument("--autotune-cache", default=None, help="JSON cache of tuned launch configurations")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.precision is None:
+        args.precision = DEFAULT_PRECISION.get(args.workload, "fp64")
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -571,12 +971,15 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    mf, bf = w.WORKLOADS[args.workload]
-    params = mf()
-    batch = bf(rank=rank)  # each rank evaluates its own independent batch (weak scaling)
+    if args.workload == "f45":
+        batch = w.batch_f45()
+        imp = f45_impurity(ctq, w, local)
+    else:
+        mf, bf = w.WORKLOADS[args.workload]
+        batch = bf(rank=rank)  # each rank evaluates its own independent batch (weak scaling)
+        imp = ctq.build_impurity(mf(), device=local)
     if args.chains:
         batch = batch.subset(range(min(args.chains, batch.n_chains)))
-    imp = ctq.build_impurity(params, device=local)
     db = ctq.DeviceBatch(batch, device=dev)
     prec = PRECISIONS[args.precision]
     tuning = {}
@@ -661,7 +1064,7 @@ def main():
     achieved_tf = flops / (trace_ms * 1e-3) / 1e12
     big = imp.is_complex or imp.max_dim > 112
     # ncu DRAM counters are committed for the shared-memory FP64 kernel only
-    traffic = profile_traffic("k_trace", args.workload, source_hash()) if (args.precision == "fp64" and not big) else None
+    traffic = profile_traffic("k_trace", args.workload) if (args.precision == "fp64" and not big) else None
     line = {
         "metric": METRIC,
         "value": value,
@@ -673,10 +1076,7 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {"fp64": "f64", "tf32": "tf32 (fp32 accumulate, f64 log scale)",
-                  "tf32x3": "3xtf32 (fp32 accumulate, f64 log scale)",
-                  "bf16x3": "3xbf16 (fp32 accumulate, f64 log scale)",
-                  "f32x2": "two-float f32 pairs (~48-bit products, f64 propagators and log scale)"}[args.precision],
+        "dtype": DTYPE_TEXT[args.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT[args.workload] + (f" (first {batch.n_chains} chains)" if args.chains else ""),
                    "n_chains": batch.n_chains,
@@ -694,12 +1094,9 @@ def main():
         "clocks": clocks.summary(),
         "wall_s_timed_region": wall,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in w.WORKLOADS:
         n_first = min(CPU_SAMPLE.get(args.workload, 64), batch.n_chains)
-        r, n, dt = cpu_oracle_rate(args.workload, n_first, min_s=10.0)
-        line["cpu_baseline"] = {"value": r, "unit": "evals/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{n} chain evaluations cycling over the first {n_first} chains of the "
-                                          f"same workload ({dt:.1f} s), NumPy FP64, 1 thread"}
+        line["cpu_baseline"], _ = cpu_baseline_leg(args.workload, n_first, min_s=10.0)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -712,34 +1109,50 @@ def main():
 # the accumulator is renormalised (three FADD / FSUB) every four terms.
 F32X2_INSTR_PER_FMA = 12.75
 
+DTYPE_TEXT = {"fp64": "f64", "tf32": "tf32 (fp32 accumulate, f64 log scale)",
+              "tf32x3": "3xtf32 (fp32 accumulate, f64 log scale)",
+              "bf16x3": "3xbf16 (fp32 accumulate, f64 log scale)",
+              "f32x2": "two-float f32 pairs (~48-bit products, f64 propagators and log scale)"}
 
-def roofline(precision, achieved_tf, fp64_peak, traffic, big=False, fp32_rate=None):
+
+def kernel_name(precision: str, big: bool) -> str:
+    if precision == "f32x2":
+        return "k_trace_big64<f32x2>" if big else "k_trace<f32x2>"
+    if precision == "fp64":
+        return "k_trace_big64<fp64>" if big else "k_trace<fp64>"
+    return f"k_trace_big<{precision}>" if big else f"k_trace_tc<{precision}>"
+
+
+def roofline(precision, achieved_tf, fp64_peak, traffic, big=False, fp32_rate=None, sustained=False):
     """Roofline of the dominant kernel: the FP64 pipe for the FP64 path
     (measured FMA rate), the FP32 pipe for the two-float path (measured FP32
     FMA rate / 12.75 instructions per two-float multiply-add, in
-    FP64-equivalent flops), the tensor pipe of the operand type for the mixed paths: measured
-    bf16 dense peak for bf16 operands, x 1/2 (the nominal TF32:BF16 ratio)
-    for tf32 operands."""
+    FP64-equivalent flops), the tensor pipe of the operand type for the mixed
+    paths: measured bf16 dense peak for bf16 operands, x 1/2 (the nominal
+    TF32:BF16 ratio) for tf32 operands; the sustained bf16 figure when the
+    kernel runs for seconds inside a long step, else the burst figure."""
+    kernel = kernel_name(precision, big)
     if precision == "f32x2":
         peak = fp32_rate / F32X2_INSTR_PER_FMA / 1e12
-        return {"kernel": "k_trace_big64<f32x2>" if big else "k_trace<f32x2>", "bound": "alu",
-                "achieved": achieved_tf, "peak": peak,
+        return {"kernel": kernel, "bound": "alu", "achieved": achieved_tf, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved_tf / peak,
                 "peak_source": "measured FP32 FMA rate (ctq_probe_fma_rate, this run) / 12.75 FP32 "
                                "instructions per two-float multiply-add", "traffic": traffic}
     if precision == "fp64":
-        return {"kernel": "k_trace_big64<fp64>" if big else "k_trace<fp64>", "bound": "alu", "achieved": achieved_tf, "peak": fp64_peak / 1e12,
+        return {"kernel": kernel, "bound": "alu", "achieved": achieved_tf, "peak": fp64_peak / 1e12,
                 "unit": "TFLOP/s", "frac": achieved_tf / (fp64_peak / 1e12),
                 "peak_source": "measured FP64 FMA rate (ctq_probe_fma_rate, this run)", "traffic": traffic}
     peaks, src = load_peaks()
     bf16 = precision == "bf16x3"
-    peak = peaks["bf16_tflops"] * (1.0 if bf16 else 0.5)
+    key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
+    peak = peaks[key] * (1.0 if bf16 else 0.5)
     passes = 1 if precision == "tf32" else 3
-    kernel = f"k_trace_big<{precision}>" if big else f"k_trace_tc<{precision}>"
+    which = "sustained" if sustained else "burst"
     return {"kernel": kernel, "bound": "tensor", "achieved": achieved_tf, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved_tf / peak, "hardware_passes": passes,
-            "peak_source": (f"{src} bf16 dense, MEASURED_PEAKS.json" if bf16 else
-                            f"{src} bf16 dense x 0.5 (nominal TF32:BF16 ratio), MEASURED_PEAKS.json"),
+            "tensor_pipe_frac_of_hardware_passes": passes * achieved_tf / peak,
+            "peak_source": (f"{src} bf16 dense, {which} (MEASURED_PEAKS.json {key})" if bf16 else
+                            f"{src} bf16 dense, {which}, x 0.5 (nominal TF32:BF16 ratio; MEASURED_PEAKS.json {key})"),
             "traffic": traffic}
 
 

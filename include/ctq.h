@@ -224,6 +224,8 @@ typedef struct {
  * timing_events (nullable): ctq_launches_per_eval() + 1 cudaEvent_t handles,
  *   recorded on `stream` before the first kernel and after each kernel, so a
  *   caller can time every kernel of the evaluation on its launching stream.
+ *   While `stream` is being captured into a CUDA graph they are captured as
+ *   event-record nodes (cudaEventRecordExternal), recorded on every replay.
  * debug_flags: 0, or CTQ_DEBUG_STALL_WAIT (test of the timeout path).
  * Launch tuning (0 everywhere = library defaults; the package's autotuner
  * picks them per impurity, precision and batch shape):
@@ -301,10 +303,14 @@ int ctq_eval_traces(const ctq_impurity* imp, const ctq_batch* batch, const ctq_e
  * Batches whose ctq_workspace_size() exceeds CTQ_STATIC_SCRATCH_BYTES are
  * rejected with CTQ_ERR_WORKSPACE (ctq_last_error_message() gives the sizes).
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls share the one array: calls whose work overlaps on the
- * GPU (other streams, other threads) race on it and must be serialised by the
- * caller.  Every call re-initialises the parts of the scratch it reads.
+ * device, with that device current) and keeps it for the rest of the process;
+ * make that first call before any stream capture.  A device reset
+ * (cudaDeviceReset, by the caller or by another runtime in the process)
+ * destroys the array together with the context, and the kept address then
+ * points nowhere: do not call this entry point on a device that has been
+ * reset since its first call there.  All calls share the one array: calls
+ * whose work overlaps on the GPU (other streams, other threads) race on it
+ * and must be serialised by the caller.  Every call re-initialises the parts of the scratch it reads.
  * Arguments, results and the other errors are those of ctq_eval_traces.
  */
 #define CTQ_STATIC_SCRATCH_BYTES (32u << 20)

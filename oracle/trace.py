@@ -149,9 +149,11 @@ def logsumexp_signed(terms):
 
 
 def trace_chain(model, tau, ops, beta: float | None = None):
-    """w for one chain.  Returns dict(log_abs, phase, per_q0, log_cond) where
-    per_q0 = {q0: (log|w_q0|, phase_q0)} over surviving q0 and log_cond is the
-    log of sum_q0 of the |F|-product traces.  The sum over q0 is taken in the
+    """w for one chain.  Returns dict(log_abs, phase, per_q0, log_cond, log_rel)
+    where per_q0 = {q0: (log|w_q0|, phase_q0)} over surviving q0, log_cond is
+    the log of sum_q0 of the |F|-product traces and log_rel is log|w| + beta
+    E_gs (the same value before the large shift is added, so that two
+    evaluations can be compared below the float64 resolution of log|w|).  The sum over q0 is taken in the
     E_gs-relative log convention of trace_q0; -beta E_gs is added last."""
     beta = model.beta if beta is None else beta
     tau = np.asarray(tau, dtype=np.float64)
@@ -174,7 +176,7 @@ def trace_chain(model, tau, ops, beta: float | None = None):
         lcond = m + math.log(sum(math.exp(c - m) for c in finite)) + shift
     else:
         lcond = -math.inf
-    return {"log_abs": la + shift, "phase": ph, "per_q0": per_q0, "log_cond": lcond}
+    return {"log_abs": la + shift, "phase": ph, "per_q0": per_q0, "log_cond": lcond, "log_rel": la}
 
 
 def trace_q0_left(model, tau, ops, q0: int, beta: float):
@@ -212,7 +214,7 @@ def trace_q0_left(model, tau, ops, q0: int, beta: float):
 
 def trace_chain_left(model, tau, ops, beta: float | None = None):
     """trace_chain with every q0 product multiplied left to right (see
-    trace_q0_left); returns dict(log_abs, phase)."""
+    trace_q0_left); returns dict(log_abs, phase, log_rel)."""
     beta = model.beta if beta is None else beta
     tau = np.asarray(tau, dtype=np.float64)
     ops = np.asarray(ops, dtype=np.int64)
@@ -222,7 +224,7 @@ def trace_chain_left(model, tau, ops, beta: float | None = None):
         if r is not None:
             terms.append(r)
     la, ph = logsumexp_signed(terms)
-    return {"log_abs": la - beta * model.E_gs, "phase": ph}
+    return {"log_abs": la - beta * model.E_gs, "phase": ph, "log_rel": la}
 
 
 def trace_batch(model, batch, chains=None):

@@ -335,6 +335,15 @@ int impurity_device(const ctq_impurity* imp, int* device) {
   *device = imp->device;
   return CTQ_OK;
 }
+void record_timing_event(void* event, void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t ev = static_cast<cudaEvent_t>(event);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+  else
+    cudaEventRecord(ev, st);
+}
 }  // namespace ctq
 
 extern "C" {

@@ -150,6 +150,10 @@ size_t workspace_layout(int n_chains, int n_sec, int n_seg_max, void* base, Work
 
 // Helpers for entry points defined outside api.cpp.
 void set_last_error(const std::string& msg);
+// Records a caller's timing event on `stream`; while the stream is being
+// captured into a CUDA graph the record becomes an event-record node of the
+// graph (so that every replay records it), otherwise a plain record.
+void record_timing_event(void* event, void* stream);
 int impurity_device(const ctq_impurity* imp, int* device);
 
 // Launch shape of the trace kernel, fixed per impurity when it is uploaded

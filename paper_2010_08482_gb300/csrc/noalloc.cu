@@ -25,7 +25,8 @@ void* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of g_static_scratch on `device` (which must be current).
 // In host code the symbol name is only a host-side stand-in, so the address
-// is looked up once per device and cached.
+// is looked up once per device and cached for the life of the process; a
+// device reset invalidates it (the header says so to the caller).
 int scratch_address(int device, void** out) {
   if (device < 0 || device >= kMaxDevices) return CTQ_ERR_ARG;
   std::lock_guard<std::mutex> lock(g_mutex);

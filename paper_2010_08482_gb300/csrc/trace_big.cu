@@ -1086,7 +1086,7 @@ int launch_eval_big(const DevModel& M, const LaunchCfg& lc, BigParams P, const B
   if (B.n_chains == 0) return CTQ_OK;
   if (M.max_dim > PVEC) return CTQ_ERR_UNSUPPORTED;
   auto mark = [&](int i) {
-    if (events) cudaEventRecord(static_cast<cudaEvent_t>(events[i]), st);
+    if (events) record_timing_event(events[i], st);
   };
   const int grid = lc.num_sms;
   // carve the scratch

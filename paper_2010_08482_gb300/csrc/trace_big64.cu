@@ -506,7 +506,7 @@ int launch_eval_big64(const DevModel& M, const LaunchCfg& lc, Big64Params P, con
   if (B.n_chains == 0) return CTQ_OK;
   if (M.max_dim > PVEC64 || (x2 && P.bt_x2 == nullptr)) return CTQ_ERR_UNSUPPORTED;
   auto mark = [&](int i) {
-    if (events) cudaEventRecord(static_cast<cudaEvent_t>(events[i]), st);
+    if (events) record_timing_event(events[i], st);
   };
   const int grid = lc.num_sms;
   char* s = static_cast<char*>(scratch);

@@ -536,7 +536,7 @@ int launch_eval_fp64(const DevModel& M, const LaunchCfg& lc, const BatchView& B,
   if (cfg.ctas_per_sm > 0) per_sm = std::min(per_sm, cfg.ctas_per_sm);
   if (per_sm < 1) return CTQ_ERR_UNSUPPORTED;
   auto mark = [&](int i) {
-    if (events) cudaEventRecord(static_cast<cudaEvent_t>(events[i]), st);
+    if (events) record_timing_event(events[i], st);
   };
   if (cudaMemsetAsync(W.counters, 0, COUNTER_BYTES, st) != cudaSuccess) return CTQ_ERR_CUDA;
   mark(0);

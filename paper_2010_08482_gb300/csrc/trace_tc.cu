@@ -746,7 +746,7 @@ int launch_eval_tc(const DevModel& M, const LaunchCfg& lc, const TcParams& P, co
   if (lc.per_sm < 1) return CTQ_ERR_UNSUPPORTED;
   if (tc_meta_bytes(cfg.max_ops, cfg.n_seg_max) > size_t(TC_META_BYTES)) return CTQ_ERR_UNSUPPORTED;
   auto mark = [&](int i) {
-    if (events) cudaEventRecord(static_cast<cudaEvent_t>(events[i]), st);
+    if (events) record_timing_event(events[i], st);
   };
   if (cudaMemsetAsync(W.counters, 0, COUNTER_BYTES, st) != cudaSuccess) return CTQ_ERR_CUDA;
   mark(0);

@@ -162,6 +162,23 @@ def model_f7() -> ModelParams:
                        sector_mode="n", n_min=4, n_max=6)
 
 
+def model_f45(mu: float) -> ModelParams:
+    """The f shell of model_f7 restricted to N in {4, 5} (blocks 1001 / 2002),
+    a smaller large-block case for profiler captures; mu is given (the
+    caller takes the particle-hole point of the full N in {4, 5, 6} window)."""
+    p = model_f7()
+    p.name, p.n_min, p.n_max, p.mu = "f45", 4, 5, float(mu)
+    return p
+
+
+def batch_f45(n_chains: int = 2, k: int = 40) -> Batch:
+    """Chains of 2k operators for model_f45: a width-1 particle-number walk
+    (alternating between N = 4 and 5), G2."""
+    rng = np.random.default_rng(7)
+    m = model_f7()
+    return _pack([g2_chain(rng, m.n_flav, k, m.beta, width=1) for _ in range(n_chains)], m.beta)
+
+
 def model_atom1(U: float = 3.0, mu: float = 1.0, beta: float = 5.0) -> ModelParams:
     """Single-orbital Hubbard atom (used for the atomic-limit G(tau) check)."""
     return ModelParams("atom1", n_orb=1, l=0, interaction="kanamori", U=U, J=0.0,
@@ -322,11 +339,12 @@ def batch_f7(n_chains: int = 256, rank: int = 0) -> Batch:
     return _pack(chains, m.beta)
 
 
-def batch_mixed(n_chains: int = 2048):
+def batch_mixed(n_chains: int = 2048, rank: int = 0):
     """2048 chains; model uniform over {t2g, d5, f7}; k ~ U{10..200}; G1 for the
     3- and 5-orbital chains, G2 for the f-shell chains.  Also returns a fair
-    coin per chain (1: the threshold is set to force an early reject)."""
-    rng = np.random.default_rng(SEED_BASE + 5)
+    coin per chain (1: the threshold is set to force an early reject).
+    rank: see batch_hubbard2."""
+    rng = np.random.default_rng(SEED_BASE + 5 + 1000 * rank)
     models = [model_t2g(), model_d5(), model_f7()]
     which = rng.integers(0, 3, size=n_chains)
     chains = []

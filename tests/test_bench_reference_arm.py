@@ -28,9 +28,10 @@ def test_reference_arm_json_line():
         assert k in d, k
     assert d["value"] > 0 and d["unit"] == "evals/s" and d["higher_is_better"] is True
     assert d["steps"] == 2 and d["warmup"] == 3 and d["n_gpus"] == 1
-    assert "workload" in d["config"] and "t2g" in d["config"]["workload"]
+    assert "workload" in d["config"] and "mixed" in d["config"]["workload"]
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] == os.cpu_count() and cb["value"] == d["value"] and cb["sample"]
+    assert cb["host"]["cpu_count"] == os.cpu_count() and cb["host"]["cpu_model"]
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
@@ -38,5 +39,20 @@ def test_reference_arm_json_line():
 
 def test_reference_arm_other_workload():
     d = run_ref("--workload", "hubbard2")
+    assert d["config"]["workload"].startswith("2-orbital")
     assert d["impl"] == "reference" and d["value"] > 0
     assert "2-orbital" in d["config"]["workload"] or "hubbard" in d["config"]["workload"].lower()
+
+
+def test_oracle_worker_thread_count_and_results():
+    """The cpu_baseline leg's child processes run with the BLAS / OpenMP
+    thread count fixed in their environment, and return the oracle's value
+    of every chain of the first pass (used for the error report)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    spec = {"workload": "hubbard2", "first": 8, "min_s": 0.0, "n_min": 8}
+    r = bench.oracle_subprocess(spec, threads=1)
+    assert r["count"] == 8 and len(r["results"]) == 8 and r["rate"] > 0
+    st, la, re, im = r["results"]["0"]
+    assert st == "ok" and abs(abs(complex(re, im)) - 1.0) < 1e-12
+    assert all(v == "1" for v in r["blas_threads"].values())

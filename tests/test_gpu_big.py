@@ -39,7 +39,7 @@ def real_d_window_model(beta=10.0):
 
 
 STATED = {("dc", ctq.TF32X3): 1e-4, ("dc", ctq.TF32): 5e-2, ("dn", ctq.TF32X3): 1e-4, ("dn", ctq.TF32): 5e-2,
-          ("f7", ctq.TF32X3): 1e-3, ("f7", ctq.TF32): 0.5,
+          ("f7", ctq.TF32X3): 1e-3, ("f7", ctq.TF32): 0.1,
           ("dc", ctq.BF16X3): 2e-3, ("dn", ctq.BF16X3): 2e-3, ("f7", ctq.BF16X3): 3e-3}
 
 

@@ -59,6 +59,7 @@ def test_edges(name, precision, kernel, oracle_models):
     res = run(imp, b, precision)
     ref = parity.oracle_chain_results(m, b, range(b.n_chains))
     n_live = 0
+    bars = parity.Bars(f"{name} precision={precision} unstructured strings")
     for c in range(b.n_chains):
         r = ref[c]
         if r["log_abs"] == -math.inf:
@@ -66,9 +67,10 @@ def test_edges(name, precision, kernel, oracle_models):
             continue
         n_live += 1
         err, kind = parity.chain_error(res["log_abs"][c], res["phase"][c], r)
-        tol = parity.fp64_tolerance(r) if TOL[precision] is None else TOL[precision] * max(1.0, r["noise"] / 1e-15)
+        tol = bars.fp64(c, r) if TOL[precision] is None else bars.mixed(c, r, TOL[precision])
         assert err <= tol, (c, err, kind)
         assert res["status"][c] == ctq.CHAIN_OK
+    bars.check()
     assert n_live >= 5 and np.sum(res["status"] == ctq.CHAIN_ZERO) > 40
     # malformed chains: unsorted, operator out of range, tau == beta, tau < 0
     tau = np.array([0.5, 0.2, 1.0, 2.0, 3.0, 4.0, 0.1, m.beta, -0.1, 0.3, 1.0, 2.0])

@@ -4,9 +4,10 @@ Bar (FP64 mode): |w_gpu - w_oracle| / |w_oracle| <= 1e-12 with the sign
 identical, on the oracle's own eigenbasis (ctq_load_impurity), so that only
 the GPU arithmetic is compared.  Chains whose q0 terms cancel by more than
 10x are measured against sum_q0 |w_q0|; chains whose trace cancels
-internally (e.g. exact zeros by symmetry computed as rounding noise) are
-held to 8x the oracle's own rounding spread, measured per chain by
-multiplying the same string in the opposite association order.  The
+internally are held to 8x the oracle's own rounding spread, measured per
+chain by multiplying the same string in the opposite association order,
+never above 1e-10, and at most 8 % of a test's chains (at least two) may be
+held to such a widened bar (parity.Bars prints them).  The
 impurity built by the library's own eigensolver (ctq_build_impurity) is compared at the tolerance its
 eigenvalue differences allow: |d log w| <= beta * max|dE| (the trace's
 sensitivity to energies) plus the 1e-12 arithmetic bar.
@@ -44,14 +45,16 @@ def full_batch(name):
     return _BATCHES[name]
 
 
-def assert_parity(res, ref, chains, tol=parity.FP64_REL, is_complex=False):
-    """Per chain: error <= max(tol, 8 x the oracle's own association spread)."""
+def assert_parity(res, ref, chains, tol=parity.FP64_REL, is_complex=False, label="fp64"):
+    """Per chain: error <= max(tol, min(1e-10, 8 x the oracle's own
+    association spread)); widened chains are counted (parity.Bars)."""
     worst = 0.0
+    bars = parity.Bars(label)
     for i, c in enumerate(chains):
         r = ref[int(c)]
         err, kind = parity.chain_error(res["log_abs"][i], res["phase"][i], r)
         worst = max(worst, err)
-        t = max(tol, parity.fp64_tolerance(r))
+        t = bars.fp64(c, r, base=tol)
         assert err <= t, (int(c), err, kind, r.get("noise"))
         if r["log_abs"] == -math.inf:
             assert res["status"][i] == ctq.CHAIN_ZERO
@@ -60,32 +63,21 @@ def assert_parity(res, ref, chains, tol=parity.FP64_REL, is_complex=False):
         if kind == "abs" and not is_complex and r.get("noise", 0.0) <= parity.FP64_REL:
             # well-conditioned chain: the sign must agree exactly
             assert res["phase"][i][0] == np.sign(np.real(r["phase"])) and res["phase"][i][1] == 0.0
+    bars.check()
+    print(f"{label}: worst error {worst:.3e} over {len(chains)} chains")
     return worst
 
 
-@pytest.mark.parametrize("name,n", [("hubbard2", 64), ("t2g", 512), ("d5", 48)])
-def test_fp64_parity_on_oracle_eigenbasis(name, n, models):
-    m = models(name)
-    sub = full_batch(name).subset(range(n))
-    imp = parity.load_oracle_model(ctq, m)
-    res = run(imp, sub)
-    ref = parity.oracle_chain_results(m, sub, range(n))
-    assert_parity(res, ref, range(n))
-
-
-@pytest.mark.parametrize("name,n_sample", [("t2g", 96), ("d5", 12)])
-def test_fp64_full_size_batch_sampled(name, n_sample, models):
-    """The whole batch in one launch (the benchmark shape); sampled chains
-    compared one by one with the oracle."""
+@pytest.mark.parametrize("name", ["hubbard2", "t2g", "d5"])
+def test_fp64_full_batch_on_oracle_eigenbasis(name, models):
+    """Every chain of the workload (64 / 4096 / 1024) in one launch, the
+    benchmark shape, compared one by one with the oracle."""
     m = models(name)
     b = full_batch(name)
     imp = parity.load_oracle_model(ctq, m)
     res = run(imp, b)
-    rng = np.random.default_rng(17)
-    sample = np.sort(rng.choice(b.n_chains, size=n_sample, replace=False))
-    ref = parity.oracle_chain_results(m, b, sample)
-    sub = {k: v[sample] for k, v in res.items() if k != "bounds"}
-    assert_parity(sub, ref, sample)
+    ref = parity.oracle_chain_results(m, b, range(b.n_chains))
+    assert_parity(res, ref, range(b.n_chains), label=f"{name} fp64 full batch")
     assert np.all(np.isin(res["status"], [ctq.CHAIN_OK, ctq.CHAIN_ZERO]))
 
 
@@ -98,7 +90,8 @@ def test_fp64_build_impurity_end_to_end(name, n, models):
     sub = full_batch(name).subset(range(n))
     res = run(imp, sub)
     ref = parity.oracle_chain_results(m, sub, range(n))
-    assert_parity(res, ref, range(n), tol=tol)
+    print(f"{name}: library vs oracle eigenvalues differ by {dE:.2e}; bar {tol:.2e}")
+    assert_parity(res, ref, range(n), tol=tol, label=f"{name} build_impurity")
 
 
 @pytest.mark.parametrize("name,n,S", [("hubbard2", 64, 3), ("t2g", 128, 8), ("d5", 16, 16)])
@@ -150,6 +143,7 @@ def test_lazy_decisions_equal_exact_decisions(name, n, models):
     res = run(imp, sub, thr=thr, lazy=True)
     st = res["status"]
     n_early_late = 0
+    bars = parity.Bars(f"{name} lazy accepts")
     for c in range(n):
         la = ref[c]["log_abs"]
         if la == -math.inf:
@@ -162,11 +156,12 @@ def test_lazy_decisions_equal_exact_decisions(name, n, models):
         elif st[c] == ctq.CHAIN_ACCEPTED:
             assert exact_accept
             err, _ = parity.chain_error(res["log_abs"][c], res["phase"][c], ref[c])
-            assert err <= parity.fp64_tolerance(ref[c])
+            assert err <= bars.fp64(c, ref[c])
         else:
             assert st[c] == ctq.CHAIN_REJECTED and not exact_accept
         if kind[c] == 0:
             assert st[c] == ctq.CHAIN_REJECTED_EARLY
+    bars.check()
     # without lazy evaluation the same thresholds give the same decisions
     res2 = run(imp, sub, thr=thr, lazy=False)
     for c in range(n):
@@ -191,7 +186,7 @@ def test_edge_cases(models):
     b = w.uniform_random_ops_batch(rng, m.n_flav, m.beta, 200, 0, 9)
     res = run(imp, b)
     ref = parity.oracle_chain_results(m, b, range(b.n_chains))
-    assert_parity(res, ref, range(b.n_chains))
+    assert_parity(res, ref, range(b.n_chains), label="unstructured strings")
     assert np.sum(res["status"] == ctq.CHAIN_ZERO) > 50
     # malformed chains
     tau = np.array([0.5, 0.2, 1.0, 2.0, 3.0, 4.0, 0.1, 50.0, -0.1, 0.3, 1.0, 2.0])

@@ -10,7 +10,9 @@ ratio kernel against the same arithmetic on the host to 16 ulps (the
 device and host exponentials and complex products round differently); h^st
 against the oracle's ratio within the two traces' bars propagated through
 the quotient."""
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -26,7 +28,7 @@ from paper_2010_08482_gb300 import workloads as w  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 X2_REL = 100.0 * parity.FP64_REL
-STATED_TC = {(ctq.TF32X3, "t2g"): 5e-4}  # 10x the mixed-precision bar of plain t2g traces
+STATED_TC = {(ctq.TF32X3, "t2g"): 1e-4}  # 5x the 3xTF32 bar of plain t2g traces (one operator replaced)
 
 
 def small_complex_model():
@@ -49,12 +51,48 @@ def log_scale(ref, kind):
     return parity.log_sum_abs_q0(ref) if kind == "sum_q0" else ref["log_abs"]
 
 
-def check(m, mb, sub, bu, chain, ev, bar, scale_floor=0.0):
+# The conditioning-scale allowance (floor x e^{log_cond - log scale}) never
+# exceeds this relative error, and the entries that pass only because of it
+# are counted.
+FLOOR_CAP = 1e-8
+
+
+class FloorCount:
+    """Entries whose error exceeds their arithmetic bar and pass only because
+    of the (capped) conditioning-scale allowance; check() prints the count and
+    asserts at most max(2, 8 %) of the entries seen."""
+
+    def __init__(self, label):
+        self.label, self.n, self.hits = label, 0, []
+
+    def bar(self, err, base, allowed, key):
+        """base: the arithmetic bar; allowed: the bar including the capped
+        conditioning allowance.  Returns max(base, allowed)."""
+        self.n += 1
+        allowed = max(base, allowed)
+        if err > base:
+            self.hits.append((key, err, base, allowed))
+        return allowed
+
+    def check(self):
+        lim = max(2, int(parity.WIDEN_FRAC * self.n))
+        for key, err, base, allowed in self.hits[:20]:
+            print(f"{self.label}: entry {key} err {err:.2e} above its arithmetic bar {base:.2e}, "
+                  f"within the conditioning allowance {allowed:.2e}")
+        print(f"{self.label}: {len(self.hits)} of {self.n} entries pass only on the conditioning allowance "
+              f"(allowed {lim})")
+        assert len(self.hits) <= lim, (self.label, len(self.hits), self.n)
+
+
+def check(m, mb, sub, bu, chain, ev, bar, scale_floor=0.0, label="h^st", floor_cap=FLOOR_CAP):
     """Replaced traces and ratios against the oracle; returns the worst errors.
-    scale_floor > 0 (two different eigenbases) also allows that much error
-    relative to the configuration's conditioning scale e^{log_cond} (the
-    float64 rounding of the two bases' blocks, which a near-cancelling trace
-    does not scale down)."""
+    bar(key, ref) gives a trace's arithmetic bar (a parity.Bars method, which
+    counts widened chains).  scale_floor > 0 (two different eigenbases) also
+    allows that much error relative to the configuration's conditioning scale
+    e^{log_cond} (the float64 rounding of the two bases' blocks, which a
+    near-cancelling trace does not scale down), at most floor_cap, with the
+    entries that need it counted (FloorCount)."""
+    floors = FloorCount(label)
     n_seq = bu.n_chains
     ru = ev.repl.results(n_seq)
     rb = ev.base.results(sub.n_chains)
@@ -72,10 +110,11 @@ def check(m, mb, sub, bu, chain, ev, bar, scale_floor=0.0):
             eu, ku, tu = 0.0, "zero", 0.0
         else:
             eu, ku = parity.chain_error(ru["log_abs"][i], ru["phase"][i], ref_u[i])
-            tu = bar(ref_u[i])
+            tu = bar(i, ref_u[i])
             if scale_floor > 0.0 and ref_u[i]["log_abs"] != -math.inf:
                 lc = max(ref_u[i]["log_cond"], rw["log_cond"])
-                tu = max(tu, scale_floor * math.exp(lc - log_scale(ref_u[i], ku)))
+                tu = floors.bar(eu, tu, min(floor_cap, scale_floor * math.exp(lc - log_scale(ref_u[i], ku))),
+                                ("w^U", i))
             assert eu <= tu, (i, c, eu, ku)
         worst_u = max(worst_u, eu)
         # the ratio kernel: the same quotient taken on the host from the
@@ -95,9 +134,10 @@ def check(m, mb, sub, bu, chain, ev, bar, scale_floor=0.0):
         if rw["log_abs"] == -math.inf:
             continue
         ew, kw = parity.chain_error(la, rb["phase"][c], rw)
-        tw = bar(rw)
+        tw = bar(c, rw)
         if scale_floor > 0.0:
-            tw = max(tw, scale_floor * math.exp(rw["log_cond"] - log_scale(rw, kw)))
+            tw = floors.bar(ew, tw, min(floor_cap, scale_floor * math.exp(rw["log_cond"] - log_scale(rw, kw))),
+                            ("w", i))
         assert ew <= tw
         if ref_u[i]["log_abs"] == -math.inf:
             h_ref, su = 0j, math.exp(rw["log_cond"] - 20 - rw["log_abs"])
@@ -111,6 +151,7 @@ def check(m, mb, sub, bu, chain, ev, bar, scale_floor=0.0):
         assert abs(h[i] - h_ref) <= tol, (i, c, h[i], h_ref, tol)
         if h_ref != 0:
             worst_h = max(worst_h, abs(h[i] - h_ref) / abs(h_ref))
+    floors.check()
     return worst_u, worst_h
 
 
@@ -124,7 +165,9 @@ def test_static_improved_fp64_on_oracle_eigenbasis(name, n, models):
     assert imp.n_alpha == 3 * m.n_flav
     bu, chain, pos, ev = evaluate(imp, sub, m.n_flav)
     assert bu.n_chains > n
-    wu, wh = check(m, mb, sub, bu, chain, ev, parity.fp64_tolerance)
+    bars = parity.Bars(f"{name} h^st fp64")
+    wu, wh = check(m, mb, sub, bu, chain, ev, bars.fp64, label=f"{name} h^st fp64")
+    bars.check()
     print(f"\n{name}: {bu.n_chains} replaced sequences, max rel err w^U {wu:.2e}, h^st {wh:.2e}")
 
 
@@ -141,9 +184,15 @@ def test_static_improved_on_library_eigenbasis(name, models):
     imp.add_bulla_operators()
     bu, chain, pos, ev = evaluate(imp, sub, m.n_flav)
 
-    def bar(ref):  # two eigenbases: allow their float64 spread as well
-        return max(1e-11, parity.NOISE_FACTOR * ref.get("noise", 0.0))
-    wu, wh = check(m, mb, sub, bu, chain, ev, bar, scale_floor=1e-12)
+    bars = parity.Bars(f"{name} h^st library eigenbasis")
+
+    def bar(key, ref):  # two eigenbases: 1e-11, or their float64 spread as well
+        return bars.fp64(key, ref, base=1e-11)
+    # two independent eigensolvers agree to ~1e-12 of the configuration's
+    # scale, so a replaced trace 1e4 times below that scale carries ~1e-8
+    wu, wh = check(m, mb, sub, bu, chain, ev, bar, scale_floor=1e-12, label=f"{name} h^st library eigenbasis",
+                   floor_cap=1e-7)
+    bars.check()
     print(f"\n{name} (library eigenbasis): max rel err w^U {wu:.2e}, h^st {wh:.2e}")
 
 
@@ -155,9 +204,12 @@ def test_static_improved_two_float(models):
     imp.add_bulla_operators(atom.one_body_matrix(m.params, m.mu))
     bu, chain, pos, ev = evaluate(imp, sub, m.n_flav, precision=ctq.F32X2)
 
-    def bar(ref):
-        return max(X2_REL, 32.0 * parity.fp64_tolerance(ref))
-    wu, wh = check(m, mb, sub, bu, chain, ev, bar)
+    bars = parity.Bars("t2g h^st F32X2")
+
+    def bar(key, ref):
+        return bars.fp64(key, ref, base=X2_REL / 32.0, scale=32.0)
+    wu, wh = check(m, mb, sub, bu, chain, ev, bar, label="t2g h^st F32X2")
+    bars.check()
     print(f"\nt2g F32X2: max rel err w^U {wu:.2e}, h^st {wh:.2e}")
 
 
@@ -170,9 +222,12 @@ def test_static_improved_tensor_cores(models):
     assert ctq.trace_kernel(imp, ctq.TF32X3) == ctq.KERNEL_TC_SMALL
     bu, chain, pos, ev = evaluate(imp, sub, m.n_flav, precision=ctq.TF32X3)
 
-    def bar(ref):
-        return STATED_TC[(ctq.TF32X3, "t2g")] * max(1.0, ref.get("noise", 0.0) / 1e-15)
-    wu, wh = check(m, mb, sub, bu, chain, ev, bar)
+    bars = parity.Bars("t2g h^st TF32X3")
+
+    def bar(key, ref):
+        return bars.mixed(key, ref, STATED_TC[(ctq.TF32X3, "t2g")])
+    wu, wh = check(m, mb, sub, bu, chain, ev, bar, label="t2g h^st TF32X3")
+    bars.check()
     print(f"\nt2g TF32X3: max rel err w^U {wu:.2e}, h^st {wh:.2e}")
 
 
@@ -239,19 +294,24 @@ def fused(imp, sub):
     return fe.ratios(db.n_ops), fe.status.cpu().numpy()
 
 
-def check_fused(m, mb, sub, hf, status, bar, floor):
+def check_fused(m, mb, sub, hf, status, bar, floor, label="one pass", chains=None):
     """One-pass ratios against the oracle's ratio of every annihilator; every
-    other entry exactly 0.  floor: error allowed relative to the replaced
-    trace's conditioning scale e^{log_cond} (the one-pass product associates
-    Y (Q (P A)) instead of the string order)."""
+    other entry exactly 0.  bar(key, ref): a trace's arithmetic bar (counted
+    by a parity.Bars).  floor: error allowed relative to the replaced trace's
+    conditioning scale e^{log_cond} (the one-pass product associates
+    Y (Q (P A)) instead of the string order), at most FLOOR_CAP relative,
+    with the entries that pass only on it counted (FloorCount).  chains:
+    the configurations to compare (default: all)."""
     bu, chain, pos = w.bulla_sequences(sub, m.n_flav)
-    ref_u = parity.oracle_chain_results(mb, bu, range(bu.n_chains))
-    ref_b = parity.oracle_chain_results(mb, sub, range(sub.n_chains))
+    keep = np.arange(bu.n_chains) if chains is None else np.nonzero(np.isin(chain, chains))[0]
+    floors = FloorCount(label)
+    ref_u = parity.oracle_chain_results(mb, bu, keep)
+    ref_b = parity.oracle_chain_results(mb, sub, np.unique(chain[keep]))
     ann = np.zeros(len(sub.op), bool)
     ann[np.asarray(sub.offsets[chain], np.int64) + pos] = True
     assert np.all(hf[~ann] == 0)
     worst = 0.0
-    for i in range(bu.n_chains):
+    for i in keep:
         c = int(chain[i])
         k = int(sub.offsets[c]) + int(pos[i])
         rw, ru = ref_b[c], ref_u[i]
@@ -265,13 +325,19 @@ def check_fused(m, mb, sub, hf, status, bar, floor):
             continue
         h_ref = complex(ru["phase"]) / complex(rw["phase"]) * math.exp(ru["log_abs"] - rw["log_abs"])
         ls_u = log_scale(ru, kind_of(ru))
-        tu = max(bar(ru), floor * math.exp(max(ru["log_cond"], rw["log_cond"]) - ls_u))
         su = math.exp(ls_u - rw["log_abs"])
-        tw = max(bar(rw), floor * math.exp(rw["log_cond"] - rw["log_abs"]))
         sw = math.exp(log_scale(rw, kind_of(rw)) - rw["log_abs"])
-        tol = 2.0 * (tu * su + tw * sw * abs(h_ref)) + 1e-300
-        assert abs(hf[k] - h_ref) <= tol, (i, c, int(pos[i]), hf[k], h_ref, tol)
+        # both traces' bars carried through the quotient: arithmetic bars, and
+        # the conditioning allowance (each term capped at FLOOR_CAP)
+        tu, tw = bar(i, ru), bar(c, rw)
+        fu = min(FLOOR_CAP, floor * math.exp(max(ru["log_cond"], rw["log_cond"]) - ls_u))
+        fw = min(FLOOR_CAP, floor * math.exp(rw["log_cond"] - rw["log_abs"]))
+        err = abs(hf[k] - h_ref)
+        tol_base = 2.0 * (tu * su + tw * sw * abs(h_ref)) + 1e-300
+        tol = floors.bar(err, tol_base, 2.0 * (max(tu, fu) * su + max(tw, fw) * sw * abs(h_ref)) + 1e-300, int(i))
+        assert err <= tol, (i, c, int(pos[i]), hf[k], h_ref, tol)
         worst = max(worst, abs(hf[k] - h_ref) / abs(h_ref))
+    floors.check()
     return worst
 
 
@@ -283,8 +349,57 @@ def test_one_pass_ratios_on_oracle_eigenbasis(name, n, models):
     imp = parity.load_oracle_model(ctq, m)
     imp.add_bulla_operators(atom.one_body_matrix(m.params, m.mu))
     hf, status = fused(imp, sub)
-    worst = check_fused(m, mb, sub, hf, status, parity.fp64_tolerance, 1e-13)
+    bars = parity.Bars(f"{name} one pass")
+    worst = check_fused(m, mb, sub, hf, status, bars.fp64, 1e-13, label=f"{name} one pass")
+    bars.check()
     print(f"\n{name} one pass: max rel err h^st {worst:.2e}")
+
+
+def test_one_pass_ratios_full_d5_batch_sampled(models):
+    """The whole 1024-chain d5 batch in one pass (the benchmark shape); a
+    seeded sample of 24 configurations (about 1,400 ratios) against the
+    oracle."""
+    m = models("d5")
+    mb = OI.with_bulla(m)
+    b = w.WORKLOADS["d5"][1]()
+    imp = parity.load_oracle_model(ctq, m)
+    imp.add_bulla_operators(atom.one_body_matrix(m.params, m.mu))
+    hf, status = fused(imp, b)
+    sample = np.sort(np.random.default_rng(23).choice(b.n_chains, size=24, replace=False))
+    bars = parity.Bars("d5 one pass, full batch")
+    worst = check_fused(m, mb, b, hf, status, bars.fp64, 1e-13, label="d5 one pass, full batch", chains=sample)
+    bars.check()
+    print(f"\nd5 one pass, full batch, 24 sampled configurations: max rel err h^st {worst:.2e}")
+
+
+def dead_backward_cases():
+    """t2g configurations whose backward product dies for one starting sector
+    (tests/golden/t2g_dead_backward.json)."""
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "t2g_dead_backward.json")) as f:
+        return [(c["tau"], c["op"]) for c in json.load(f)["chains"]]
+
+
+def test_one_pass_ratios_when_a_backward_product_dies(models):
+    """The one-pass kernel stops a string's backward pass when its product is
+    exactly zero; the ratios of the earlier annihilators must still equal the
+    oracle's (their other starting sectors carry them)."""
+    m = models("t2g")
+    mb = OI.with_bulla(m)
+    chains = [(np.asarray(t, np.float64), np.asarray(o, np.int32)) for t, o in dead_backward_cases()]
+    offs = np.cumsum([0] + [len(o) for _, o in chains]).astype(np.int32)
+    sub = w.Batch(beta=m.beta, offsets=offs, tau=np.concatenate([t for t, _ in chains]),
+                  op=np.concatenate([o for _, o in chains]))
+    imp = parity.load_oracle_model(ctq, m)
+    imp.add_bulla_operators(atom.one_body_matrix(m.params, m.mu))
+    hf, status = fused(imp, sub)
+    assert np.all(status == ctq.CHAIN_OK)
+    bars = parity.Bars("t2g one pass, dead backward products")
+    check_fused(m, mb, sub, hf, status, bars.fp64, 1e-13, label="t2g one pass, dead backward products")
+    bars.check()
+    for c, (tau, ops) in enumerate(chains):
+        for pos, h_ref in OI.static_ratios(mb, tau, ops, beta=m.beta):
+            got = hf[int(offs[c]) + pos]
+            assert abs(got - h_ref) <= 1e-10 * max(1.0, abs(h_ref)), (c, pos, got, h_ref)
 
 
 def test_one_pass_ratios_complex_library_eigenbasis(models):
@@ -296,9 +411,12 @@ def test_one_pass_ratios_complex_library_eigenbasis(models):
     imp.add_bulla_operators()
     hf, status = fused(imp, sub)
 
-    def bar(ref):
-        return max(1e-11, parity.NOISE_FACTOR * ref.get("noise", 0.0))
-    worst = check_fused(m, mb, sub, hf, status, bar, 1e-12)
+    bars = parity.Bars("complex one pass, library eigenbasis")
+
+    def bar(key, ref):
+        return bars.fp64(key, ref, base=1e-11)
+    worst = check_fused(m, mb, sub, hf, status, bar, 1e-12, label="complex one pass, library eigenbasis")
+    bars.check()
     print(f"\ncomplex one pass (library eigenbasis): max rel err h^st {worst:.2e}")
 
 

@@ -20,7 +20,9 @@ from paper_2010_08482_gb300 import workloads as w  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 MODELS = [w.model_t2g, w.model_d5, w.model_f7]
-TOL = {ctq.FP64: 1e-10, ctq.TF32X3: 4e-3}
+# stated 3xTF32 bars of the mixed batch's chains (orders up to 200, longer
+# than the t2g and d5 workloads' own chains); FP64 chains take the FP64 bar
+STATED_TF32X3 = {0: 2e-4, 1: 4e-3}
 
 
 def run_lazy(imp, batch, thr, precision):
@@ -41,7 +43,7 @@ def test_mixed_batch_decisions(mi, n, precision, models):
     sub.beta = p.beta
     m = models(p.name)
     thr = np.zeros(n)
-    ref = parity.oracle_chain_results(m, sub, range(n), noise=False)
+    ref = parity.oracle_chain_results(m, sub, range(n))
     for c in range(n):
         tau, ops = sub.chain(c)
         if coin[idx[c]] == 1:
@@ -51,6 +53,7 @@ def test_mixed_batch_decisions(mi, n, precision, models):
             thr[c] = ref[c]["log_abs"] - math.log(2.0) if ref[c]["log_abs"] != -math.inf else -1e300
     imp = parity.load_oracle_model(ctq, m)
     res = run_lazy(imp, sub, thr, precision)
+    bars = parity.Bars(f"mixed {p.name} precision={precision}")
     for c in range(n):
         if ref[c]["log_abs"] == -math.inf:
             continue
@@ -59,7 +62,10 @@ def test_mixed_batch_decisions(mi, n, precision, models):
         else:
             assert res["status"][c] == ctq.CHAIN_ACCEPTED, c
             err, _ = parity.chain_error(res["log_abs"][c], res["phase"][c], ref[c])
-            assert err <= TOL[precision], (c, err)
+            bar = bars.fp64(c, ref[c]) if precision == ctq.FP64 else bars.mixed(c, ref[c], STATED_TF32X3[mi])
+            print(f"  chain {int(idx[c])}: n_ops {len(sub.chain(c)[1])} err {err:.3e} bar {bar:.1e}")
+            assert err <= bar, (c, err)
+    bars.check()
 
 
 def test_mixed_batch_f_shell_decisions():

@@ -4,8 +4,9 @@ FP64 oracle.
 
 Mixed-precision bar: the paper gives no number, so the error against the
 FP64 oracle is stated per configuration (STATED below, relative error of w
-per chain; the measured distributions are printed and recorded in the design
-notes).  A chain of n products of d-dimensional blocks accumulates about
+per chain, enforced as stated on every chain whose float64 spread is at most
+half the FP64 bar; the measured distributions are printed and recorded in the
+design notes).  A chain of n products of d-dimensional blocks accumulates about
 n u kappa relative error (u = 2^-11 for TF32 operands, ~2^-22 for the
 three-term split with FP32 accumulation, ~2^-17 for bf16 hi / lo, kappa the
 chain's cancellation);
@@ -25,18 +26,15 @@ from paper_2010_08482_gb300 import workloads as w  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
+# Stated bars: about 3x the largest error measured on the well-conditioned
+# chains (float64 spread <= parity.WIDEN_AT); an ill-conditioned chain is held
+# to its bar times spread / WIDEN_AT, at most 10x (parity.Bars).  TF32 in one
+# pass does not resolve the d shell: its errors there are O(1).
 STATED = {
-    (ctq.TF32X3, "hubbard2"): 2e-5, (ctq.TF32X3, "t2g"): 5e-5, (ctq.TF32X3, "d5"): 4e-3,
-    (ctq.TF32, "hubbard2"): 2e-2, (ctq.TF32, "t2g"): 5e-2, (ctq.TF32, "d5"): 1.0,
-    (ctq.BF16X3, "hubbard2"): 1e-4, (ctq.BF16X3, "t2g"): 3e-4, (ctq.BF16X3, "d5"): 1e-1,
+    (ctq.TF32X3, "hubbard2"): 1e-5, (ctq.TF32X3, "t2g"): 2e-5, (ctq.TF32X3, "d5"): 1.5e-3,
+    (ctq.TF32, "hubbard2"): 1.5e-2, (ctq.TF32, "t2g"): 2.5e-2, (ctq.TF32, "d5"): 2.0,
+    (ctq.BF16X3, "hubbard2"): 7e-5, (ctq.BF16X3, "t2g"): 2e-4, (ctq.BF16X3, "d5"): 1.2e-2,
 }
-
-
-def mixed_tolerance(precision, name, ref):
-    """Stated bar, widened by the chain's own float64 conditioning when the
-    oracle's two association orders already disagree."""
-    cond = max(1.0, ref.get("noise", 0.0) / 1e-15)
-    return STATED[(precision, name)] * cond
 
 
 # Operand rounding bound of one product relative to max |A B^T| (TF32: 2^-11
@@ -75,19 +73,26 @@ def test_mixed_precision_parity(precision, name, n, models):
     imp = parity.load_oracle_model(ctq, m)
     res = run(imp, sub, precision)
     ref = parity.oracle_chain_results(m, sub, range(n))
-    errs = []
+    errs, well = [], []
+    bars = parity.Bars(f"{name} precision={precision}")
     for c in range(n):
         r = ref[c]
         if r["log_abs"] == -math.inf:
             continue
         err, kind = parity.chain_error(res["log_abs"][c], res["phase"][c], r)
         n_ops = int(sub.offsets[c + 1] - sub.offsets[c])
-        assert err <= mixed_tolerance(precision, name, r), (c, err, kind, n_ops)
+        bar = bars.mixed(c, r, STATED[(precision, name)])
+        print(f"  chain {c}: n_ops {n_ops} err {err:.3e} float64 spread {r.get('noise', 0.0):.1e} bar {bar:.1e}")
+        assert err <= bar, (c, err, kind, n_ops)
         errs.append(err)
-        if r.get("noise", 0.0) <= 1e-12 and kind == "abs":
+        if r.get("noise", 0.0) <= parity.WIDEN_AT:
+            well.append(err)
+        if r.get("noise", 0.0) <= parity.WIDEN_AT and kind == "abs":
             assert res["phase"][c][0] == np.sign(np.real(r["phase"]))
+    bars.check()
     print(f"{name} precision={precision}: n={len(errs)} max rel err {max(errs):.3e}, "
-          f"p90 {np.quantile(errs, 0.9):.3e}, median {np.median(errs):.3e}")
+          f"p90 {np.quantile(errs, 0.9):.3e}, median {np.median(errs):.3e}; well-conditioned chains: "
+          f"max {max(well):.3e}, median {np.median(well):.3e}")
 
 
 def test_mixed_lazy_decisions_never_contradict_exact(models):

@@ -143,3 +143,43 @@ def test_bulla_blocks_are_the_commutator_with_h_in_the_eigenbasis(name, models):
             err = np.abs(B - ref).max() / max(1.0, np.abs(ref).max())
             worst = max(worst, err)
     assert worst < 1e-11, worst
+
+
+def test_dead_backward_cases_have_the_stated_property(models):
+    """The fixture tests/golden/t2g_dead_backward.json: for some surviving
+    starting sector the product of the operators after position j (taken from
+    the end of the string) is exactly zero for a j with an annihilator before
+    it, the forward products up to the last operator are nonzero, and w != 0
+    (another starting sector carries it), so the ratios of those earlier
+    annihilators come from the other sectors."""
+    import json
+    import os
+    from oracle import trace as T
+    m = models("t2g")
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "t2g_dead_backward.json")
+    with open(path) as f:
+        cases = json.load(f)["chains"]
+    assert len(cases) >= 2
+    for case in cases:
+        tau, ops = np.asarray(case["tau"]), np.asarray(case["op"], np.int64)
+        n = len(ops)
+        assert T.trace_chain(m, tau, ops)["log_abs"] != -math.inf
+        surv = [q0 for q0 in range(m.n_sec) if T.walk(m, ops, q0) is not None]
+        hit = False
+        for q0 in surv:
+            path_q = T.walk(m, ops, q0)
+            A = np.eye(m.dims[q0])
+            fwd = []
+            for i in range(n - 1):
+                A = m.F[(int(ops[i]), path_q[i])] @ A
+                fwd.append(bool(np.any(A)))
+            Y = np.eye(m.dims[q0])
+            dead = None
+            for i in range(n - 1, -1, -1):
+                Y = Y @ m.F[(int(ops[i]), path_q[i])]
+                if not np.any(Y):
+                    dead = i
+                    break
+            if all(fwd) and dead is not None and any(ops[j] % 2 == 0 for j in range(dead)):
+                hit = True
+        assert hit
