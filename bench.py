@@ -681,29 +681,10 @@ def run_mixed(args, world, rank, local):
         g.kern_ms = []
         groups.append(g)
     n_chains = sum(g.sub.n_chains for g in groups)
-    # The group with the most work runs on the main stream; the others are
-    # forked onto side streams and joined again, so that their small-block
-    # kernels run beside the large-block kernel (which keeps one CTA per SM
-    # and leaves room on each SM for small CTAs).
-    order = sorted(groups, key=lambda g: -g.flops)
-    side = [torch.cuda.Stream(device=dev) for _ in order[1:]]
 
     def step():
-        cur = torch.cuda.current_stream()
-        if args.serial_groups:
-            for g in groups:
-                g.ev(g.db, lazy=True, events=g.ev_ptr)
-            return
-        fork = torch.cuda.Event()
-        fork.record(cur)
-        for sd in side:
-            sd.wait_event(fork)
-        order[0].ev(order[0].db, lazy=True, events=order[0].ev_ptr)
-        for g, sd in zip(order[1:], side):
-            with torch.cuda.stream(sd):
-                g.ev(g.db, lazy=True, events=g.ev_ptr)
-        for sd in side:
-            cur.wait_stream(sd)
+        for g in groups:
+            g.ev(g.db, lazy=True, events=g.ev_ptr)
 
     step()  # eager first evaluation (also the library's first-call set-up)
     torch.cuda.synchronize()
@@ -777,8 +758,8 @@ def run_mixed(args, world, rank, local):
         c1 = coin[g.idx] == 1
         decisions_ok &= bool(np.all(st[c1] == ctq.CHAIN_REJECTED_EARLY))
         decisions_ok &= bool(np.all(np.isin(st[~c1], [ctq.CHAIN_ACCEPTED, ctq.CHAIN_ZERO])))
-    # dominant kernel: the trace kernel of the group with the most step time
-    dom = max(groups, key=lambda g: statistics.mean(k[1] for k in g.kern_ms))
+    # dominant kernel: the trace kernel of the group with the most work
+    dom = max(groups, key=lambda g: g.flops)
     dom_ms = statistics.mean(k[1] for k in dom.kern_ms)
     big = dom.imp.is_complex or dom.imp.max_dim > 112
     achieved = dom.flops / (dom_ms * 1e-3) / 1e12
@@ -790,7 +771,6 @@ def run_mixed(args, world, rank, local):
     traffic = profile_traffic(f"k_trace_big_{args.precision}", "f7", "big") if big else None
     roof = roofline(args.precision, achieved, fp64_peak, traffic, big=big, fp32_rate=fp32_rate, sustained=True)
     roof["kernel"] = kname
-    group_span = {g.name: statistics.mean(sum(k) for k in g.kern_ms) for g in groups}
     per_group = {g.name: {"chains": int(g.sub.n_chains), "evaluated": int(np.sum(coin[g.idx] == 0)),
                           "surviving_strings": int(g.items), "algorithmic_flops": g.flops,
                           "kernel_ms": {"plan": statistics.mean(k[0] for k in g.kern_ms),
@@ -805,10 +785,7 @@ def run_mixed(args, world, rank, local):
                    "n_chains": n_chains, "precision": args.precision, "groups": per_group,
                    "thresholds": "coin 1: +inf (rejected on the level-0 bound), coin 0: -inf (full trace, "
                                  "accepted)", "cuda_graph": graph_note,
-                   "groups_overlapped": (f"no (one stream)" if args.serial_groups else
-                                         f"{order[0].name} on the main stream, "
-                                         + ", ".join(g.name for g in order[1:]) + " forked onto side streams"),
-                   "sum_of_group_kernel_ms": sum(group_span.values()),
+                   "group_order": "one after another on one stream (t2g, d5, f7)",
                    "l2": "flushed (256 MiB write) between steps",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "tflops": flops / (ms * 1e-3) / 1e12, "algorithmic_flops_per_step": flops,
@@ -937,8 +914,6 @@ def main():
     ap.add_argument("--fp64-subset", type=int, default=FP64_SUBSET,
                     help="mixed batch: chains (the first N) timed in float64 and in the mixed precision")
     ap.add_argument("--no-fp64-subset", action="store_true")
-    ap.add_argument("--serial-groups", action="store_true",
-                    help="mixed batch: evaluate the impurity groups one after another on one stream")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--chains", type=int, default=0, help="evaluate only the first N chains of the workload")
     ap.add_argument("--no-autotune", action="store_true", help="library-default launch configuration")

@@ -227,6 +227,71 @@ def trace_chain_left(model, tau, ops, beta: float | None = None):
     return {"log_abs": la - beta * model.E_gs, "phase": ph, "log_rel": la}
 
 
+def trace_q0_split(model, tau, ops, q0: int, beta: float):
+    """The same trace as trace_q0 in a third association order: the first
+    half of the string multiplied right to left into A (the propagator
+    after operator m included), the second half left to right into B
+    (starting from the wrap-around propagator P_{beta - tau_n}), then
+    Tr(B A).  Returns (value, log_rel).  With the left-to-right order it
+    gives a second measure of the chain's float64 rounding spread."""
+    path = walk(model, ops, q0)
+    if path is None:
+        return None
+    n = len(ops)
+    if n < 2:
+        return trace_q0(model, tau, ops, q0, beta)[:2]
+    E, Emin, Egs = model.E, model.E_min, model.E_gs
+    m = n // 2
+
+    def prop(q, dt):
+        return np.exp(-dt * (E[q] - Emin[q])), -dt * (Emin[q] - Egs)
+
+    # A = P_{tau_{m+1} - tau_m}(q_m) F_m ... F_1 P_{tau_1}(q0)   (operators 0 .. m-1)
+    p, l0 = prop(q0, tau[0])
+    A = np.diag(p).astype(model_dtype(model))
+    logs = [l0]
+    e_sum = 0
+    for i in range(m):
+        A = model.F[(int(ops[i]), path[i])] @ A
+        p, l = prop(path[i + 1], tau[i + 1] - tau[i])
+        A = p[:, None] * A
+        logs.append(l)
+        A, e = _rescale_exp(A)
+        if A is None:
+            return 0.0, -math.inf
+        e_sum += e
+    # B = P_{beta - tau_n}(q0) F_n P ... P F_{m+1}   (operators n-1 .. m)
+    p, l = prop(q0, beta - tau[n - 1])
+    Bm = np.diag(p).astype(model_dtype(model))
+    logs.append(l)
+    for i in range(n - 1, m - 1, -1):
+        Bm = Bm @ model.F[(int(ops[i]), path[i])]
+        if i > m:
+            p, l = prop(path[i], tau[i] - tau[i - 1])
+            Bm = Bm * p[None, :]
+            logs.append(l)
+        Bm, e = _rescale_exp(Bm)
+        if Bm is None:
+            return 0.0, -math.inf
+        e_sum += e
+    return np.trace(Bm @ A), math.fsum(logs) + e_sum * LN2
+
+
+def trace_chain_split(model, tau, ops, beta: float | None = None):
+    """trace_chain with every q0 product in the split association of
+    trace_q0_split; returns dict(log_abs, phase, log_rel)."""
+    beta = model.beta if beta is None else beta
+    tau = np.asarray(tau, dtype=np.float64)
+    ops = np.asarray(ops, dtype=np.int64)
+    terms = []
+    for q0 in range(model.n_sec):
+        r = trace_q0_split(model, tau, ops, q0, beta)
+        if r is not None:
+            terms.append(r)
+    la, ph = logsumexp_signed(terms)
+    return {"log_abs": la - beta * model.E_gs, "phase": ph, "log_rel": la}
+
+
 def trace_batch(model, batch, chains=None):
     """trace_chain over a workloads.Batch (optionally a subset of chain ids)."""
     idx = range(batch.n_chains) if chains is None else chains

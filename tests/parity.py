@@ -85,15 +85,18 @@ class Bars:
 
 def oracle_chain_results(model, batch, chains, noise=True):
     """Oracle trace per chain; with noise=True each result also carries
-    'noise': the relative spread between multiplying the strings right-to-left
-    and left-to-right (the chain's own float64 rounding spread)."""
+    'noise': the largest relative spread between multiplying the strings
+    right-to-left and either left-to-right or split in the middle (the
+    chain's own float64 rounding spread, measured in two ways so that one
+    accidental agreement does not hide it)."""
     out = {}
     for c in chains:
         tau, ops = batch.chain(int(c))
         r = OT.trace_chain(model, tau, ops, beta=batch.beta)
         if noise:
             l = OT.trace_chain_left(model, tau, ops, beta=batch.beta)
-            r["noise"] = rel_spread(l, r)
+            sp = OT.trace_chain_split(model, tau, ops, beta=batch.beta)
+            r["noise"] = max(rel_spread(l, r), rel_spread(sp, r))
         out[int(c)] = r
     return out
 

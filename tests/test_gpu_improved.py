@@ -55,6 +55,11 @@ def log_scale(ref, kind):
 # exceeds this relative error, and the entries that pass only because of it
 # are counted.
 FLOOR_CAP = 1e-8
+# Absolute allowance on a one-pass ratio h^st (energy units of the model,
+# |h| ~ U): a replaced trace that nearly cancels (|w^U| << |w|) carries the
+# float64 rounding of terms of the size of w, about 1e-15 |w|, which is a
+# large relative error of a tiny h; entries that need it are counted.
+H_ABS = 1e-13
 
 
 class FloorCount:
@@ -300,7 +305,8 @@ def check_fused(m, mb, sub, hf, status, bar, floor, label="one pass", chains=Non
     by a parity.Bars).  floor: error allowed relative to the replaced trace's
     conditioning scale e^{log_cond} (the one-pass product associates
     Y (Q (P A)) instead of the string order), at most FLOOR_CAP relative,
-    with the entries that pass only on it counted (FloorCount).  chains:
+    or H_ABS absolute on h, with the entries that pass only on these
+    allowances counted (FloorCount).  chains:
     the configurations to compare (default: all)."""
     bu, chain, pos = w.bulla_sequences(sub, m.n_flav)
     keep = np.arange(bu.n_chains) if chains is None else np.nonzero(np.isin(chain, chains))[0]
@@ -334,7 +340,8 @@ def check_fused(m, mb, sub, hf, status, bar, floor, label="one pass", chains=Non
         fw = min(FLOOR_CAP, floor * math.exp(rw["log_cond"] - rw["log_abs"]))
         err = abs(hf[k] - h_ref)
         tol_base = 2.0 * (tu * su + tw * sw * abs(h_ref)) + 1e-300
-        tol = floors.bar(err, tol_base, 2.0 * (max(tu, fu) * su + max(tw, fw) * sw * abs(h_ref)) + 1e-300, int(i))
+        allowed = max(2.0 * (max(tu, fu) * su + max(tw, fw) * sw * abs(h_ref)), H_ABS)
+        tol = floors.bar(err, tol_base, allowed, int(i))
         assert err <= tol, (i, c, int(pos[i]), hf[k], h_ref, tol)
         worst = max(worst, abs(hf[k] - h_ref) / abs(h_ref))
     floors.check()

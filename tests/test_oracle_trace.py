@@ -374,3 +374,20 @@ def test_logsumexp_signed_exact():
     assert n_rel > 200
     assert T.logsumexp_signed([]) == (-math.inf, 0.0)
     assert T.logsumexp_signed([(0.0, 3.0), (2.0, -math.inf)]) == (-math.inf, 0.0)
+
+
+@pytest.mark.parametrize("name", ["hubbard2", "t2g"])
+def test_split_association_agrees(name, models):
+    """The split association (first half right to left, second half left
+    to right, then the trace of their product) gives the same trace as the
+    plain right-to-left product to float64 rounding."""
+    m = models(name)
+    b = (w.batch_hubbard2() if name == "hubbard2" else w.batch_t2g(64))
+    for c in range(b.n_chains):
+        tau, ops = b.chain(c)
+        r = T.trace_chain(m, tau, ops)
+        s = T.trace_chain_split(m, tau, ops)
+        if r["log_abs"] == -math.inf:
+            assert s["log_abs"] == -math.inf
+            continue
+        assert rel_log(s, r) < 1e-12, c
