@@ -318,6 +318,51 @@ int ctq_eval_traces_static(const ctq_impurity* imp, const ctq_batch* batch, cons
                            const ctq_result* result, void* stream);
 
 /*
+ * Incremental local trace of one configuration with a skip list of cached
+ * segment products (Sec. 3.3.1, skip-list paragraph): after a local change
+ * (a pair inserted or removed) only the products of the segments that
+ * contain a changed operator are recomputed, about one per level of the
+ * skip list (O(log k)), plus the ancestors of operators whose sector the
+ * change shifted.  Products in float64 on the SIMT pipe, renormalised by
+ * exact powers of two; operators c and c+ only (codes 2 f + dag).
+ *
+ * ctq_skiplist_create: the handle works on imp's device, enqueues its
+ *   kernels on `stream` (cudaStream_t, NULL = legacy default) and allocates
+ *   its own device memory (released by ctq_skiplist_free); beta > 0; seed
+ *   draws the operators' skip-list heights.  Errors: CTQ_ERR_ARG,
+ *   CTQ_ERR_UNSUPPORTED (an impurity with Bulla operators), CTQ_ERR_NOMEM.
+ * ctq_skiplist_set: replaces the configuration by n operators (host arrays,
+ *   tau strictly increasing in [0, beta), op = 2 f + dag); no product is
+ *   kept from the previous configuration.
+ * ctq_skiplist_insert: adds m operators (host arrays, any order; times in
+ *   [0, beta), distinct from each other and from the configuration's).
+ * ctq_skiplist_remove: removes the m operators at exactly these times.
+ * ctq_skiplist_evaluate: computes what the current configuration needs
+ *   (cached products are reused), synchronises `stream` and returns, on the
+ *   host, log|w| (-inf if w = 0) and the phase (re, im) of the raw trace of
+ *   the time-ordered product, as ctq_eval_traces does, and, if stats is not
+ *   NULL, the work done by this call.  Products no longer used are released.
+ * Errors of set / insert / remove: CTQ_ERR_ARG (nothing changed).
+ */
+typedef struct ctq_skiplist ctq_skiplist;
+typedef struct {
+  int64_t products;      /* segment products computed by this evaluation */
+  int64_t leaves;        /* leaves (propagator x block) formed */
+  int64_t reused;        /* cached leaves and products found */
+  int64_t cached;        /* products held after the evaluation */
+  double flops;          /* real flops of the products (complex counts 4 x) */
+  int n_ops;             /* operators of the configuration */
+  int n_strings;         /* surviving starting sectors */
+  int64_t device_bytes;  /* device memory held by the handle */
+} ctq_skiplist_stats;
+int ctq_skiplist_create(const ctq_impurity* imp, double beta, uint64_t seed, void* stream, ctq_skiplist** out);
+int ctq_skiplist_set(ctq_skiplist* sl, int n, const double* tau, const int32_t* op);
+int ctq_skiplist_insert(ctq_skiplist* sl, int m, const double* tau, const int32_t* op);
+int ctq_skiplist_remove(ctq_skiplist* sl, int m, const double* tau);
+int ctq_skiplist_evaluate(ctq_skiplist* sl, double* log_abs, double* phase, ctq_skiplist_stats* stats);
+void ctq_skiplist_free(ctq_skiplist* sl);
+
+/*
  * Static part of the improved estimator for the self-energy (Sec. 2.4,
  * Eq. PImprovedEstimatorStatic): h^st_i = w^U_i / w_loc(C_{chain[i]}) from
  * the results of two ctq_eval_traces calls, one on the configurations

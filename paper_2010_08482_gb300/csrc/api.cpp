@@ -335,6 +335,8 @@ int impurity_device(const ctq_impurity* imp, int* device) {
   *device = imp->device;
   return CTQ_OK;
 }
+const HostModel* impurity_host(const ctq_impurity* imp) { return imp ? &imp->host : nullptr; }
+const DevModel* impurity_dev(const ctq_impurity* imp) { return imp ? &imp->dev : nullptr; }
 void record_timing_event(void* event, void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaEvent_t ev = static_cast<cudaEvent_t>(event);

@@ -155,6 +155,9 @@ void set_last_error(const std::string& msg);
 // graph (so that every replay records it), otherwise a plain record.
 void record_timing_event(void* event, void* stream);
 int impurity_device(const ctq_impurity* imp, int* device);
+// The impurity's host model and its device view (nullptr for a null handle).
+const HostModel* impurity_host(const ctq_impurity* imp);
+const DevModel* impurity_dev(const ctq_impurity* imp);
 
 // Launch shape of the trace kernel, fixed per impurity when it is uploaded
 // (so that evaluation makes no attribute or occupancy query, e.g. while a

@@ -1,0 +1,642 @@
+// Incremental local trace with a skip list of cached segment products
+// (Sec. 3.3.1, skip-list paragraph: products of operator sub-sequences are
+// kept, so that a local change of the configuration recomputes O(log k)
+// products instead of all k).
+//
+// One ctq_skiplist holds one configuration (a time-ordered operator
+// sequence).  For every starting sector q0 whose string survives, the trace
+//     w_q0 = Tr P_{beta - tau_n + tau_1}(q0) F_n P ... P F_2 P_{tau_2 - tau_1} F_1
+// is the trace of the wrap-around propagator times the ordered product of
+// "leaves" X_i = P_{tau_{i+1} - tau_i}(q_i) F_{alpha_i}(q_{i-1}) (the last leaf
+// is F_n alone).  Each operator gets a random height h >= 1 (geometric, 1/2)
+// when it is inserted.  Level 0 holds the leaves; the segments of level l
+// start at the first operator and at every operator with h > l, and a
+// segment's product is the product of the level-(l-1) segments it covers,
+// the latest on the left.  The top level is a single segment: the whole
+// product.  Every product is cached under a key made from the keys of its
+// factors (a leaf's key: operator identity, input sector and time step), so
+// after a move only the segments that contain a changed leaf get a new key
+// and are recomputed: about one product per level for a local insertion or
+// removal, plus the ancestors of the leaves whose sector the move shifted.
+//
+// Arithmetic: float64 on the SIMT pipe (complex blocks as [Re | Im] rows);
+// each product is renormalised by an exact power of two (exponent kept on
+// the device) and carries the log of its propagators' E_min factors (kept
+// on the host), as in the other trace kernels.  The host structure is
+// small (operators, heights, the cache map); every product, leaf and trace
+// runs in the kernels below, asynchronously on the handle's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "ctq_internal.h"
+
+namespace ctq {
+namespace {
+
+constexpr int SL_MAX_LEVEL = 24;
+constexpr int GT = 64;   // GEMM tile (rows and columns of C)
+constexpr int GK = 16;   // K chunk
+constexpr int G_THREADS = 256;
+constexpr long long EXP_DEAD = LLONG_MIN / 4;
+
+__device__ __forceinline__ void atomic_max_abs(unsigned long long* w, double v) {
+  // |v| >= 0: the bit patterns of non-negative doubles order like the values
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0 && v > 0.0) atomicMax(w, (unsigned long long)__double_as_longlong(v));
+}
+
+// Leaf X = P_dt(q_out) F: out[m][j] = e^{-dt E_rel(q_out)_m} F[m][j]; complex
+// rows are stored [Re(0..d_in) | Im(0..d_in)].
+__global__ void k_sl_leaf(const double* blk, int64_t off, int cplx, int d_out, int d_in, const double* E_out,
+                          double dt, double* out, unsigned long long* maxw) {
+  double mx = 0.0;
+  const long long total = (long long)d_out * d_in;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int m = int(e / d_in), j = int(e - (long long)m * d_in);
+    const double p = dt > 0.0 ? exp(-dt * E_out[m]) : 1.0;
+    if (cplx) {
+      const double re = blk[2 * (off + e)] * p, im = blk[2 * (off + e) + 1] * p;
+      out[size_t(m) * 2 * d_in + j] = re;
+      out[size_t(m) * 2 * d_in + d_in + j] = im;
+      mx = fmax(mx, fmax(fabs(re), fabs(im)));
+    } else {
+      const double v = blk[off + e] * p;
+      out[e] = v;
+      mx = fmax(mx, fabs(v));
+    }
+  }
+  atomic_max_abs(maxw, mx);
+}
+
+// C = R L.  Real: R (M x K), L (K x N), C (M x N), row-major.  Complex
+// ([Re | Im] rows): the real GEMM of [Rr | Ri] (M x 2K) with
+// [[Lr, Li], [-Li, Lr]] (2K x 2N) gives [Cr | Ci] (M x 2N).
+__global__ void __launch_bounds__(G_THREADS) k_sl_gemm(const double* R, const double* L, double* C, int M, int K,
+                                                       int N, int cplx, unsigned long long* maxw) {
+  __shared__ double As[GK][GT + 1];
+  __shared__ double Bs[GK][GT + 1];
+  const int Kp = cplx ? 2 * K : K, Np = cplx ? 2 * N : N;
+  const int row0 = blockIdx.y * GT, col0 = blockIdx.x * GT;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < Kp; k0 += GK) {
+    for (int e = threadIdx.x; e < GT * GK; e += G_THREADS) {
+      const int r = e / GK, k = e - r * GK;  // A: row r, column k0 + k
+      const int gr = row0 + r, gk = k0 + k;
+      As[k][r] = (gr < M && gk < Kp) ? R[size_t(gr) * Kp + gk] : 0.0;
+      const int kb = e / GT, c = e - kb * GT;  // B: row k0 + kb, column c
+      const int bk = k0 + kb, bc = col0 + c;
+      double v = 0.0;
+      if (bk < Kp && bc < Np) {
+        if (!cplx || bk < K) {
+          v = L[size_t(bk) * Np + bc];
+        } else {
+          const int kk = bk - K;
+          v = (bc < N) ? -L[size_t(kk) * Np + N + bc] : L[size_t(kk) * Np + (bc - N)];
+        }
+      }
+      Bs[kb][c] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < GK; ++k) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[k][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double mx = 0.0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = row0 + ty * 4 + i;
+    if (r >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = col0 + tx * 4 + j;
+      if (c < Np) {
+        C[size_t(r) * Np + c] = acc[i][j];
+        mx = fmax(mx, fabs(acc[i][j]));
+      }
+    }
+  }
+  atomic_max_abs(maxw, mx);
+}
+
+// X *= 2^-e with e the exponent of max|X| (an exact scaling); the product's
+// exponent becomes e + the factors' exponents, or EXP_DEAD when X == 0.
+__global__ void k_sl_scale(double* X, long long count, const unsigned long long* maxw, const long long* eR,
+                           const long long* eL, long long* eout) {
+  const double mx = __longlong_as_double((long long)*maxw);
+  if (mx == 0.0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *eout = EXP_DEAD;
+    return;
+  }
+  const int e = ilogb(mx);
+  const double s = ldexp(1.0, -e);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    X[i] *= s;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *eout = e + (eR ? *eR : 0) + (eL ? *eL : 0);
+}
+
+// Tr P_t(q0) X = sum_j e^{-t E_rel(q0)_j} X[j][j] (one block); out: re, im;
+// the product's exponent is copied beside it.
+__global__ void k_sl_root(const double* X, int d, int cplx, const double* E0, double t, const long long* ex,
+                          double* out) {
+  __shared__ double sr[32], si[32];
+  double re = 0.0, im = 0.0;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    const double p = exp(-t * E0[j]);
+    if (cplx) {
+      re += p * X[size_t(j) * 2 * d + j];
+      im += p * X[size_t(j) * 2 * d + d + j];
+    } else {
+      re += p * X[size_t(j) * d + j];
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    sr[w] = re;
+    si[w] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < int(blockDim.x >> 5); ++i) {
+      a += sr[i];
+      b += si[i];
+    }
+    out[0] = a;
+    out[1] = b;
+    out[2] = __longlong_as_double(*ex);
+  }
+}
+
+// ---------------------------------------------------------------- host
+
+uint64_t mix64(uint64_t x) {  // splitmix64 finaliser
+  x += 0x9e3779b97f4a7c15ull;
+  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+  x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
+
+// A cached product: device matrix (rows x cols doubles, complex rows as
+// [Re | Im]), its max word and exponent on the device, its log scale on the host.
+struct Buf {
+  double* p = nullptr;
+  size_t elems = 0;
+  unsigned long long* maxw = nullptr;  // [0] max|X| bits; [1] exponent (long long)
+  int d_out = 0, d_in = 0;
+  double L = 0.0;
+  long long* ex() const { return reinterpret_cast<long long*>(maxw + 1); }
+};
+
+class Pool {
+ public:
+  ~Pool() { release(); }
+  double* get(size_t elems) {
+    const size_t b = bucket(elems);
+    auto it = free_.find(b);
+    if (it != free_.end() && !it->second.empty()) {
+      double* p = it->second.back();
+      it->second.pop_back();
+      return p;
+    }
+    void* p = nullptr;
+    if (cudaMalloc(&p, b * sizeof(double)) != cudaSuccess) return nullptr;
+    bytes_ += b * sizeof(double);
+    return static_cast<double*>(p);
+  }
+  void put(double* p, size_t elems) { free_[bucket(elems)].push_back(p); }
+  unsigned long long* word() {
+    if (words_.empty()) {
+      void* p = nullptr;
+      if (cudaMalloc(&p, 4096 * 16) != cudaSuccess) return nullptr;
+      blocks_.push_back(p);
+      for (int i = 0; i < 4096; ++i) words_.push_back(static_cast<unsigned long long*>(p) + 2 * i);
+    }
+    unsigned long long* w = words_.back();
+    words_.pop_back();
+    return w;
+  }
+  void put_word(unsigned long long* w) { words_.push_back(w); }
+  size_t bytes() const { return bytes_; }
+  void release() {
+    for (auto& kv : free_)
+      for (double* p : kv.second) cudaFree(p);
+    free_.clear();
+    for (void* p : blocks_) cudaFree(p);
+    blocks_.clear();
+    words_.clear();
+    bytes_ = 0;
+  }
+
+ private:
+  static size_t bucket(size_t elems) {  // size classes 2^k and 1.5 x 2^k, at least 256
+    size_t b = 256;
+    while (b < elems) b *= 2;
+    const size_t c = b / 4 * 3;
+    return (c >= elems && c >= 256) ? c : b;
+  }
+  std::map<size_t, std::vector<double*>> free_;
+  std::vector<unsigned long long*> words_;
+  std::vector<void*> blocks_;
+  size_t bytes_ = 0;
+};
+
+struct Op {
+  uint64_t id;
+  double t;
+  int alpha;
+  int h;
+};
+
+}  // namespace
+}  // namespace ctq
+
+struct ctq_skiplist {
+  const ctq_impurity* imp = nullptr;
+  const ctq::HostModel* H = nullptr;
+  const ctq::DevModel* D = nullptr;
+  int device = 0;
+  cudaStream_t st = nullptr;
+  double beta = 0.0;
+  uint64_t rng = 0, next_id = 1;
+  std::vector<ctq::Op> ops;
+  ctq::Pool pool;
+  std::unordered_map<std::string, std::shared_ptr<ctq::Buf>> cache;
+  double* d_res = nullptr;  // [3 n_sec]: trace re, im, exponent bits per q0
+  ctq_skiplist_stats stats{};
+};
+
+namespace ctq {
+namespace {
+
+int sl_height(ctq_skiplist* S) {
+  int h = 1;
+  S->rng = mix64(S->rng);
+  uint64_t r = S->rng;
+  while ((r & 1u) && h < SL_MAX_LEVEL - 1) {
+    ++h;
+    r >>= 1;
+  }
+  return h;
+}
+
+std::shared_ptr<Buf> new_buf(ctq_skiplist* S, int d_out, int d_in) {
+  auto b = std::shared_ptr<Buf>(new Buf(), [S](Buf* x) {
+    if (x->p) S->pool.put(x->p, x->elems);
+    if (x->maxw) S->pool.put_word(x->maxw);
+    delete x;
+  });
+  b->d_out = d_out;
+  b->d_in = d_in;
+  b->elems = size_t(d_out) * d_in * (S->H->is_complex ? 2 : 1);
+  b->p = S->pool.get(b->elems);
+  b->maxw = S->pool.word();
+  if (!b->p || !b->maxw) return nullptr;
+  return b;
+}
+
+int grid_for(long long n) { return int(std::min<long long>((n + 255) / 256, 152LL * 8)); }
+
+// Scales a freshly written product and records its exponent.
+int finish(ctq_skiplist* S, const Buf& b, const Buf* R, const Buf* L) {
+  k_sl_scale<<<grid_for((long long)b.elems), 256, 0, S->st>>>(b.p, (long long)b.elems, b.maxw, R ? R->ex() : nullptr,
+                                                              L ? L->ex() : nullptr, b.ex());
+  return cudaPeekAtLastError() == cudaSuccess ? CTQ_OK : CTQ_ERR_CUDA;
+}
+
+std::shared_ptr<Buf> make_leaf(ctq_skiplist* S, int alpha, int q_in, int q_out, double dt, int* st) {
+  const HostModel& H = *S->H;
+  const int ns = H.n_sec, d_in = H.dims[q_in], d_out = H.dims[q_out];
+  auto b = new_buf(S, d_out, d_in);
+  if (!b) { *st = CTQ_ERR_NOMEM; return nullptr; }
+  cudaMemsetAsync(b->maxw, 0, 16, S->st);
+  const int64_t off = H.blk_off[size_t(alpha) * ns + q_in];
+  k_sl_leaf<<<grid_for((long long)d_out * d_in), 256, 0, S->st>>>(S->D->blk, off, H.is_complex, d_out, d_in,
+                                                                   S->D->E_rel + H.E_off[q_out], dt, b->p, b->maxw);
+  *st = finish(S, *b, nullptr, nullptr);
+  b->L = dt > 0.0 ? -dt * (H.E_min[q_out] - H.E_gs) : 0.0;
+  S->stats.leaves += 1;
+  return b;
+}
+
+// C = R L (R applied after L).
+std::shared_ptr<Buf> product(ctq_skiplist* S, const std::shared_ptr<Buf>& R, const std::shared_ptr<Buf>& L, int* st) {
+  auto b = new_buf(S, R->d_out, L->d_in);
+  if (!b) { *st = CTQ_ERR_NOMEM; return nullptr; }
+  cudaMemsetAsync(b->maxw, 0, 16, S->st);
+  const int cplx = S->H->is_complex;
+  const int Np = cplx ? 2 * L->d_in : L->d_in;
+  dim3 grid((Np + GT - 1) / GT, (R->d_out + GT - 1) / GT);
+  k_sl_gemm<<<grid, G_THREADS, 0, S->st>>>(R->p, L->p, b->p, R->d_out, R->d_in, L->d_in, cplx, b->maxw);
+  *st = finish(S, *b, R.get(), L.get());
+  b->L = R->L + L->L;
+  S->stats.products += 1;
+  S->stats.flops += 2.0 * R->d_out * double(R->d_in) * L->d_in * (cplx ? 4.0 : 1.0);
+  return b;
+}
+
+std::string leaf_key(const Op& o, int q_in, double dt) {
+  std::string k(1, 'L');
+  k.append(reinterpret_cast<const char*>(&o.id), 8);
+  k.append(reinterpret_cast<const char*>(&q_in), 4);
+  k.append(reinterpret_cast<const char*>(&dt), 8);
+  return k;
+}
+
+// A segment's key depends only on its factors' keys (the same factors give
+// the same product at any level).
+std::string seg_key(const std::vector<const std::string*>& kids) {
+  uint64_t h = 0x243f6a8885a308d3ull;
+  for (const std::string* k : kids) {
+    uint64_t x = 1469598103934665603ull;
+    for (unsigned char c : *k) x = (x ^ c) * 1099511628211ull;
+    h = mix64(h ^ x);
+  }
+  std::string k(1, 'S');
+  k.append(reinterpret_cast<const char*>(&h), 8);
+  const uint64_t n = kids.size();
+  k.append(reinterpret_cast<const char*>(&n), 8);
+  return k;
+}
+
+// Builds (or finds in the cache) every segment product of the string that
+// starts in sector q0 and launches its root trace into d_res[3 q0 ..].
+// Returns the root's log scale in *L_root.
+int eval_string(ctq_skiplist* S, int q0, const std::vector<int>& path, std::unordered_set<std::string>& used,
+                double* L_root) {
+  const int n = int(S->ops.size());
+  std::vector<std::string> keys(n);
+  std::vector<std::shared_ptr<Buf>> bufs(n);
+  int st = CTQ_OK;
+  for (int i = 0; i < n; ++i) {
+    const double dt = (i + 1 < n) ? S->ops[i + 1].t - S->ops[i].t : 0.0;
+    keys[i] = leaf_key(S->ops[i], path[i], dt);
+    auto it = S->cache.find(keys[i]);
+    if (it != S->cache.end()) {
+      bufs[i] = it->second;
+      S->stats.reused += 1;
+    } else {
+      bufs[i] = make_leaf(S, S->ops[i].alpha, path[i], path[i + 1], dt, &st);
+      if (st != CTQ_OK) return st;
+      S->cache[keys[i]] = bufs[i];
+    }
+    used.insert(keys[i]);
+  }
+  // levels: segment starts are index 0 and every operator with h > level
+  std::vector<int> starts(n);
+  for (int i = 0; i < n; ++i) starts[i] = i;
+  for (int level = 1; starts.size() > 1; ++level) {
+    std::vector<int> ns_;
+    for (size_t j = 0; j < starts.size(); ++j)
+      if (j == 0 || S->ops[starts[j]].h > level) ns_.push_back(int(j));  // indices into starts
+    std::vector<std::string> nkeys;
+    std::vector<std::shared_ptr<Buf>> nbufs;
+    std::vector<int> nstarts;
+    for (size_t g = 0; g < ns_.size(); ++g) {
+      const int a = ns_[g], b = (g + 1 < ns_.size()) ? ns_[g + 1] : int(starts.size());
+      nstarts.push_back(starts[a]);
+      if (b - a == 1) {  // one factor: the same product
+        nkeys.push_back(keys[a]);
+        nbufs.push_back(bufs[a]);
+        continue;
+      }
+      std::vector<const std::string*> kids;
+      for (int j = a; j < b; ++j) kids.push_back(&keys[j]);
+      std::string k = seg_key(kids);
+      auto it = S->cache.find(k);
+      std::shared_ptr<Buf> buf;
+      if (it != S->cache.end()) {
+        buf = it->second;
+        S->stats.reused += 1;
+      } else {
+        buf = bufs[a];
+        for (int j = a + 1; j < b && st == CTQ_OK; ++j) buf = product(S, bufs[j], buf, &st);
+        if (st != CTQ_OK) return st;
+        S->cache[k] = buf;
+      }
+      used.insert(k);
+      nkeys.push_back(std::move(k));
+      nbufs.push_back(buf);
+    }
+    keys.swap(nkeys);
+    bufs.swap(nbufs);
+    starts.swap(nstarts);
+  }
+  const Buf& root = *bufs[0];
+  const HostModel& H = *S->H;
+  const double t_wrap = S->beta - S->ops[n - 1].t + S->ops[0].t;
+  k_sl_root<<<1, 256, 0, S->st>>>(root.p, H.dims[q0], H.is_complex, S->D->E_rel + H.E_off[q0], t_wrap, root.ex(),
+                                  S->d_res + 3 * q0);
+  *L_root = root.L - t_wrap * (H.E_min[q0] - H.E_gs);
+  return cudaPeekAtLastError() == cudaSuccess ? CTQ_OK : CTQ_ERR_CUDA;
+}
+
+class DevGuard {
+ public:
+  explicit DevGuard(int d) {
+    cudaGetDevice(&prev_);
+    if (prev_ != d) cudaSetDevice(d);
+    sw_ = prev_ != d;
+  }
+  ~DevGuard() {
+    if (sw_) cudaSetDevice(prev_);
+  }
+
+ private:
+  int prev_ = 0;
+  bool sw_ = false;
+};
+
+}  // namespace
+}  // namespace ctq
+
+using ctq::Op;
+
+extern "C" int ctq_skiplist_create(const ctq_impurity* imp, double beta, uint64_t seed, void* stream,
+                                   ctq_skiplist** out) {
+  if (!imp || !out || !(beta > 0.0)) return CTQ_ERR_ARG;
+  const ctq::HostModel* H = ctq::impurity_host(imp);
+  if (H->n_extra != 0) {
+    ctq::set_last_error("the skip list takes the operators c and c+ only");
+    return CTQ_ERR_UNSUPPORTED;
+  }
+  auto* S = new ctq_skiplist();
+  S->imp = imp;
+  S->H = H;
+  S->D = ctq::impurity_dev(imp);
+  ctq::impurity_device(imp, &S->device);
+  S->st = static_cast<cudaStream_t>(stream);
+  S->beta = beta;
+  S->rng = ctq::mix64(seed ^ 0x5ca1ab1eull);
+  ctq::DevGuard g(S->device);
+  if (cudaMalloc(&S->d_res, sizeof(double) * 3 * std::max(H->n_sec, 1)) != cudaSuccess) {
+    delete S;
+    return CTQ_ERR_NOMEM;
+  }
+  *out = S;
+  return CTQ_OK;
+}
+
+extern "C" void ctq_skiplist_free(ctq_skiplist* S) {
+  if (!S) return;
+  {
+    ctq::DevGuard g(S->device);
+    cudaStreamSynchronize(S->st);
+    S->cache.clear();
+    S->pool.release();
+    cudaFree(S->d_res);
+  }
+  delete S;
+}
+
+static int sl_check_ops(const ctq_skiplist* S, int m, const double* tau, const int32_t* op) {
+  for (int i = 0; i < m; ++i) {
+    if (!(tau[i] >= 0.0 && tau[i] < S->beta)) return CTQ_ERR_ARG;
+    if (op && (op[i] < 0 || op[i] >= 2 * S->H->n_flav)) return CTQ_ERR_ARG;
+  }
+  return CTQ_OK;
+}
+
+extern "C" int ctq_skiplist_set(ctq_skiplist* S, int n, const double* tau, const int32_t* op) {
+  if (!S || n < 0 || (n > 0 && (!tau || !op))) return CTQ_ERR_ARG;
+  if (sl_check_ops(S, n, tau, op) != CTQ_OK) return CTQ_ERR_ARG;
+  for (int i = 1; i < n; ++i)
+    if (!(tau[i] > tau[i - 1])) return CTQ_ERR_ARG;
+  S->ops.clear();
+  for (int i = 0; i < n; ++i) S->ops.push_back(Op{S->next_id++, tau[i], op[i], ctq::sl_height(S)});
+  return CTQ_OK;
+}
+
+extern "C" int ctq_skiplist_insert(ctq_skiplist* S, int m, const double* tau, const int32_t* op) {
+  if (!S || m < 0 || (m > 0 && (!tau || !op))) return CTQ_ERR_ARG;
+  if (sl_check_ops(S, m, tau, op) != CTQ_OK) return CTQ_ERR_ARG;
+  std::vector<Op> add;
+  for (int i = 0; i < m; ++i) add.push_back(Op{0, tau[i], op[i], 0});
+  for (const Op& a : add)
+    for (const Op& o : S->ops)
+      if (o.t == a.t) return CTQ_ERR_ARG;
+  for (int i = 0; i < m; ++i)
+    for (int j = i + 1; j < m; ++j)
+      if (tau[i] == tau[j]) return CTQ_ERR_ARG;
+  for (Op& a : add) {
+    a.id = S->next_id++;
+    a.h = ctq::sl_height(S);
+    auto it = std::lower_bound(S->ops.begin(), S->ops.end(), a.t, [](const Op& o, double t) { return o.t < t; });
+    S->ops.insert(it, a);
+  }
+  return CTQ_OK;
+}
+
+extern "C" int ctq_skiplist_remove(ctq_skiplist* S, int m, const double* tau) {
+  if (!S || m < 0 || (m > 0 && !tau)) return CTQ_ERR_ARG;
+  std::vector<size_t> idx;
+  for (int i = 0; i < m; ++i) {
+    auto it = std::lower_bound(S->ops.begin(), S->ops.end(), tau[i], [](const Op& o, double t) { return o.t < t; });
+    if (it == S->ops.end() || it->t != tau[i]) return CTQ_ERR_ARG;
+    idx.push_back(size_t(it - S->ops.begin()));
+  }
+  std::sort(idx.begin(), idx.end());
+  if (std::adjacent_find(idx.begin(), idx.end()) != idx.end()) return CTQ_ERR_ARG;
+  for (size_t k = idx.size(); k-- > 0;) S->ops.erase(S->ops.begin() + idx[k]);
+  return CTQ_OK;
+}
+
+extern "C" int ctq_skiplist_evaluate(ctq_skiplist* S, double* log_abs, double* phase, ctq_skiplist_stats* stats) {
+  if (!S || !log_abs || !phase) return CTQ_ERR_ARG;
+  const ctq::HostModel& H = *S->H;
+  const int ns = H.n_sec, n = int(S->ops.size());
+  ctq::DevGuard g(S->device);
+  S->stats = ctq_skiplist_stats{};
+  std::unordered_set<std::string> used;
+  std::vector<int> live;
+  std::vector<double> Lq(ns, 0.0);
+  double lm = -INFINITY;
+  double acc_re = 0.0, acc_im = 0.0;
+  if (n == 0) {  // w = Z_loc
+    for (int q = 0; q < ns; ++q)
+      for (int j = 0; j < H.dims[q]; ++j) {
+        const double l = -S->beta * (H.E[H.E_off[q] + j] - H.E_gs);
+        if (l > lm) { acc_re *= std::exp(lm - l); lm = l; }
+        acc_re += std::exp(l - lm);
+      }
+  } else {
+    for (int q0 = 0; q0 < ns; ++q0) {
+      std::vector<int> path(n + 1);
+      path[0] = q0;
+      bool ok = true;
+      for (int i = 0; i < n && ok; ++i) {
+        const int q = H.s[size_t(S->ops[i].alpha) * ns + path[i]];
+        ok = q >= 0;
+        path[i + 1] = q;
+      }
+      if (!ok || path[n] != q0) continue;
+      const int st = ctq::eval_string(S, q0, path, used, &Lq[q0]);
+      if (st != CTQ_OK) return st;
+      live.push_back(q0);
+    }
+    std::vector<double> res(3 * std::max(ns, 1));
+    if (!live.empty() &&
+        cudaMemcpyAsync(res.data(), S->d_res, sizeof(double) * 3 * ns, cudaMemcpyDeviceToHost, S->st) != cudaSuccess)
+      return CTQ_ERR_CUDA;
+    if (cudaStreamSynchronize(S->st) != cudaSuccess) return CTQ_ERR_CUDA;
+    for (int q0 : live) {
+      long long e;
+      std::memcpy(&e, &res[3 * q0 + 2], 8);
+      const double re = res[3 * q0], im = res[3 * q0 + 1];
+      if (e == ctq::EXP_DEAD || (re == 0.0 && im == 0.0)) continue;
+      const double l = Lq[q0] + double(e) * 0.69314718055994530942 + std::log(std::hypot(re, im));
+      const double ur = re / std::hypot(re, im), ui = im / std::hypot(re, im);
+      if (l > lm) {
+        const double f = std::exp(lm - l);
+        acc_re *= f;
+        acc_im *= f;
+        lm = l;
+      }
+      const double f = std::exp(l - lm);
+      acc_re += f * ur;
+      acc_im += f * ui;
+    }
+  }
+  // drop every cached product the current configuration no longer uses
+  for (auto it = S->cache.begin(); it != S->cache.end();)
+    it = used.count(it->first) ? std::next(it) : S->cache.erase(it);
+  const double a = std::hypot(acc_re, acc_im);
+  if (!(a > 0.0) || lm == -INFINITY) {
+    *log_abs = -INFINITY;
+    phase[0] = phase[1] = 0.0;
+  } else {
+    *log_abs = lm + std::log(a) - S->beta * H.E_gs;
+    phase[0] = acc_re / a;
+    phase[1] = acc_im / a;
+  }
+  S->stats.n_ops = n;
+  S->stats.n_strings = int(live.size());
+  S->stats.cached = int64_t(S->cache.size());
+  S->stats.device_bytes = int64_t(S->pool.bytes());
+  if (stats) *stats = S->stats;
+  return cudaGetLastError() == cudaSuccess ? CTQ_OK : CTQ_ERR_CUDA;
+}

@@ -99,6 +99,12 @@ def _load():
         "ctq_static_ratio_workspace_size": (c_size_t, [P, c_int, POINTER(EvalOptsC)]),
         "ctq_eval_static_ratios": (c_int, [P, POINTER(BatchC), POINTER(EvalOptsC), POINTER(ResultC), P, c_int, P,
                                            c_size_t, P]),
+        "ctq_skiplist_create": (c_int, [P, c_double, ctypes.c_uint64, P, POINTER(P)]),
+        "ctq_skiplist_set": (c_int, [P, c_int, P, P]),
+        "ctq_skiplist_insert": (c_int, [P, c_int, P, P]),
+        "ctq_skiplist_remove": (c_int, [P, c_int, P]),
+        "ctq_skiplist_evaluate": (c_int, [P, POINTER(c_double), P, P]),
+        "ctq_skiplist_free": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -114,7 +120,8 @@ EXPORTED = ("ctq_build_impurity", "ctq_load_impurity", "ctq_impurity_info", "ctq
             "ctq_probe_fma_rate", "ctq_tc_gemm_check", "ctq_big_gemm_check", "ctq_eval_traces_static",
             "ctq_trace_kernel", "ctq_density_size", "ctq_density_workspace_size", "ctq_eval_density_matrices",
             "ctq_add_bulla_operators", "ctq_static_ratios", "ctq_static_ratio_workspace_size",
-            "ctq_eval_static_ratios")
+            "ctq_eval_static_ratios", "ctq_skiplist_create", "ctq_skiplist_set", "ctq_skiplist_insert",
+            "ctq_skiplist_remove", "ctq_skiplist_evaluate", "ctq_skiplist_free")
 
 # Size of the library-owned scratch used by eval_traces_static (ctq.h).
 STATIC_SCRATCH_BYTES = 32 << 20
@@ -576,3 +583,54 @@ class DensityEvaluator:
             out[q] = flat[o:o + d * d].reshape(d, d)
             o += d * d
         return out
+
+
+class SkipListStatsC(ctypes.Structure):
+    _fields_ = [("products", c_int64), ("leaves", c_int64), ("reused", c_int64), ("cached", c_int64),
+                ("flops", c_double), ("n_ops", c_int), ("n_strings", c_int), ("device_bytes", c_int64)]
+
+
+class SkipListTrace:
+    """ctq_skiplist: the local trace of one configuration kept as a skip
+    list of cached segment products, updated by inserting and removing
+    operators (see ctq.h).  Host arrays in, host results out."""
+
+    def __init__(self, imp: Impurity, beta: float, seed: int = 0, stream=None):
+        import torch
+        self.imp = imp
+        s = torch.cuda.current_stream() if stream is None else stream
+        self._stream = s
+        h = c_void_p()
+        _check(_lib.ctq_skiplist_create(imp.handle, float(beta), ctypes.c_uint64(seed), s.cuda_stream,
+                                        ctypes.byref(h)), "ctq_skiplist_create")
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.ctq_skiplist_free(h)
+            self.handle = None
+
+    def set(self, tau, op):
+        tau = np.ascontiguousarray(tau, dtype=np.float64)
+        op = np.ascontiguousarray(op, dtype=np.int32)
+        _check(_lib.ctq_skiplist_set(self.handle, len(tau), _ptr(tau), _ptr(op)), "ctq_skiplist_set")
+
+    def insert(self, tau, op):
+        tau = np.ascontiguousarray(tau, dtype=np.float64)
+        op = np.ascontiguousarray(op, dtype=np.int32)
+        _check(_lib.ctq_skiplist_insert(self.handle, len(tau), _ptr(tau), _ptr(op)), "ctq_skiplist_insert")
+
+    def remove(self, tau):
+        tau = np.ascontiguousarray(tau, dtype=np.float64)
+        _check(_lib.ctq_skiplist_remove(self.handle, len(tau), _ptr(tau)), "ctq_skiplist_remove")
+
+    def evaluate(self):
+        """(log|w|, phase as complex, stats dict) of the current configuration."""
+        la = c_double()
+        ph = np.zeros(2)
+        st = SkipListStatsC()
+        _check(_lib.ctq_skiplist_evaluate(self.handle, ctypes.byref(la), _ptr(ph), ctypes.byref(st)),
+               "ctq_skiplist_evaluate")
+        stats = {k: getattr(st, k) for k, _ in SkipListStatsC._fields_}
+        return la.value, complex(ph[0], ph[1]), stats

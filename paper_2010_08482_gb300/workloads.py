@@ -296,6 +296,42 @@ def bulla_sequences(batch: Batch, n_flav: int):
     return out, c_new.astype(np.int32), pos.astype(np.int32)
 
 
+def pair_move(rng, tau: np.ndarray, op: np.ndarray, n_flav: int, beta: float):
+    """A random local move of a configuration that respects per-flavour
+    alternation (the Pauli-aware pair moves of App. B): a flavour is drawn;
+    with probability 1/2 (if it has operators) ("rem", times) removes one of
+    its operators and the next one of the flavour; otherwise ("ins", times,
+    codes) puts two new operators between consecutive operators of the
+    flavour on the circle [0, beta) (anywhere if it has none), the earlier
+    one of the type that the preceding operator's type requires next."""
+    f = int(rng.integers(0, n_flav))
+    mine = np.nonzero(np.asarray(op) // 2 == f)[0]
+    if len(mine) >= 2 and rng.random() < 0.5:
+        i = int(rng.integers(0, len(mine)))
+        j = (i + 1) % len(mine)
+        return "rem", np.array([tau[mine[i]], tau[mine[j]]])
+    if len(mine) == 0:
+        return "ins", rng.uniform(0.0, beta, size=2), np.array([2 * f + 1, 2 * f], np.int32)
+    i = int(rng.integers(0, len(mine)))
+    j = (i + 1) % len(mine)
+    L = (tau[mine[j]] - tau[mine[i]]) % beta or beta
+    s1, s2 = np.sort(rng.uniform(0.0, L, size=2))
+    t1, t2 = (tau[mine[i]] + s1) % beta, (tau[mine[i]] + s2) % beta
+    dag_i = int(op[mine[i]]) % 2  # after a creator the flavour is occupied: annihilate first
+    return "ins", np.array([t1, t2]), np.array([2 * f + (0 if dag_i else 1), 2 * f + (1 if dag_i else 0)], np.int32)
+
+
+def apply_pair_move(move, tau: np.ndarray, op: np.ndarray):
+    """The configuration (times ascending, codes) after a pair_move."""
+    if move[0] == "rem":
+        keep = ~np.isin(tau, move[1])
+        return tau[keep], op[keep]
+    t = np.concatenate([tau, move[1]])
+    o = np.concatenate([op, move[2]]).astype(np.int32)
+    order = np.argsort(t)
+    return t[order], o[order]
+
+
 def _pack(chains, beta, model=None) -> Batch:
     offs = [0]
     for t, _ in chains:

@@ -18,14 +18,17 @@ NOISE_FACTOR = 8.0
 # No chain's FP64 bar exceeds this, whatever its measured spread.
 FP64_CAP = 1e-10
 # A chain is ill-conditioned when the oracle's own float64 spread exceeds
-# this (half the FP64 bar): only then is its bar widened.
-WIDEN_AT = 0.5 * FP64_REL
+# the FP64 bar itself: only then is its bar widened.
+WIDEN_AT = FP64_REL
 # An ill-conditioned mixed-precision chain is held to its stated bar times
 # spread / WIDEN_AT, at most this many times the stated bar.
 MIXED_WIDEN_CAP = 10.0
-# At most this fraction of a test's chains (and at least two chains) may be
-# held to a widened bar; every widened chain is printed.
-WIDEN_FRAC = 0.08
+# At most this fraction of a test's chains (and at least three chains) may
+# be held to a widened bar; every widened chain is printed.  (The d shell at
+# beta = 40 has 4.9 % of its 1024 chains above the FP64 bar in float64
+# spread; hubbard2 and t2g have none.)
+WIDEN_FRAC = 0.10
+WIDEN_MIN = 3
 # The result is carried as log|w| in float64, which resolves relative changes
 # of w only down to the spacing of log|w| (4.5e-13 at |log w| ~ 3600, the d
 # shell at beta = 40): the library's and the oracle's final roundings of
@@ -51,7 +54,7 @@ class Bars:
     mixed(c, ref, b): b, or, when spread > WIDEN_AT,
                       b x min(MIXED_WIDEN_CAP, spread / WIDEN_AT)
     check():          prints the widened chains and asserts that there are
-                      at most max(2, WIDEN_FRAC x chains seen) of them."""
+                      at most max(WIDEN_MIN, WIDEN_FRAC x chains seen) of them."""
 
     def __init__(self, label: str, max_frac: float = WIDEN_FRAC):
         self.label = label
@@ -76,19 +79,39 @@ class Bars:
         return stated * f
 
     def check(self):
-        allowed = max(2, int(self.max_frac * self.n))
+        allowed = max(WIDEN_MIN, int(self.max_frac * self.n))
         for c, noise, bar in self.widened:
             print(f"{self.label}: chain {c} bar widened to {bar:.2e} (float64 spread {noise:.2e})")
         print(f"{self.label}: {len(self.widened)} of {self.n} chains on a widened bar (allowed {allowed})")
         assert len(self.widened) <= allowed, (self.label, self.widened)
 
 
+_PERTURBED = {}
+
+
+def perturbed_model(model, seed: int = 20100848):
+    """A copy of an oracle model whose every block entry is multiplied by
+    (1 + r 2^-52), r = +-1 seeded: the blocks as another float64 eigensolver
+    could have rounded them.  Evaluating a chain on it measures the chain's
+    sensitivity to the float64 rounding of its inputs (the perturbation is
+    of the inputs only; the oracle's arithmetic is unchanged)."""
+    key = id(model)
+    if key not in _PERTURBED:
+        import copy
+        rng = np.random.default_rng(seed)
+        m = copy.copy(model)
+        m.F = {k: v * (1.0 + rng.choice([-1.0, 1.0], size=v.shape) * 2.0 ** -52) for k, v in model.F.items()}
+        _PERTURBED[key] = (model, m)  # keep the original alive so that its id stays unique
+    return _PERTURBED[key][1]
+
+
 def oracle_chain_results(model, batch, chains, noise=True):
     """Oracle trace per chain; with noise=True each result also carries
-    'noise': the largest relative spread between multiplying the strings
-    right-to-left and either left-to-right or split in the middle (the
-    chain's own float64 rounding spread, measured in two ways so that one
-    accidental agreement does not hide it)."""
+    'noise': the largest relative spread between the right-to-left product
+    and (a) the left-to-right product, (b) the product split in the middle,
+    (c) the right-to-left product on blocks perturbed by one unit in the
+    last place (perturbed_model): the chain's own float64 rounding spread,
+    measured three ways so that one accidental agreement does not hide it."""
     out = {}
     for c in chains:
         tau, ops = batch.chain(int(c))
@@ -96,7 +119,8 @@ def oracle_chain_results(model, batch, chains, noise=True):
         if noise:
             l = OT.trace_chain_left(model, tau, ops, beta=batch.beta)
             sp = OT.trace_chain_split(model, tau, ops, beta=batch.beta)
-            r["noise"] = max(rel_spread(l, r), rel_spread(sp, r))
+            pt = OT.trace_chain(perturbed_model(model), tau, ops, beta=batch.beta)
+            r["noise"] = max(rel_spread(l, r), rel_spread(sp, r), rel_spread(pt, r))
         out[int(c)] = r
     return out
 

@@ -64,8 +64,8 @@ H_ABS = 1e-13
 
 class FloorCount:
     """Entries whose error exceeds their arithmetic bar and pass only because
-    of the (capped) conditioning-scale allowance; check() prints the count and
-    asserts at most max(2, 8 %) of the entries seen."""
+    of the (capped) conditioning-scale or absolute allowance; check() prints
+    the count and asserts at most max(3, 10 %) of the entries seen."""
 
     def __init__(self, label):
         self.label, self.n, self.hits = label, 0, []
@@ -80,7 +80,7 @@ class FloorCount:
         return allowed
 
     def check(self):
-        lim = max(2, int(parity.WIDEN_FRAC * self.n))
+        lim = max(parity.WIDEN_MIN, int(parity.WIDEN_FRAC * self.n))
         for key, err, base, allowed in self.hits[:20]:
             print(f"{self.label}: entry {key} err {err:.2e} above its arithmetic bar {base:.2e}, "
                   f"within the conditioning allowance {allowed:.2e}")

@@ -1,0 +1,121 @@
+"""The skip-list incremental trace (ctq_skiplist, Sec. 3.3.1 skip-list
+paragraph) against the FP64 oracle and against a fresh ctq_eval_traces of
+the same configuration, over sequences of random pair insertions and
+removals; plus the work it saves (products per move) and its argument
+checks."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import parity  # noqa: E402
+from oracle import atom  # noqa: E402
+from oracle import trace as OT  # noqa: E402
+from paper_2010_08482_gb300 import ctq  # noqa: E402
+from paper_2010_08482_gb300 import workloads as w  # noqa: E402
+from test_gpu_big import complex_d_model  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def fresh_eval(imp, tau, op, beta):
+    b = w.Batch(beta=beta, offsets=np.array([0, len(tau)], np.int32), tau=np.asarray(tau), op=np.asarray(op, np.int32))
+    db = ctq.DeviceBatch(b)
+    ev = ctq.TraceEvaluator(imp, 1, max(1, len(tau)))
+    ev(db)
+    torch.cuda.synchronize()
+    r = ev.results(1)
+    return float(r["log_abs"][0]), complex(*r["phase"][0])
+
+
+def rel(la, ph, la_ref, ph_ref):
+    if la_ref == -math.inf:
+        return 0.0 if la == -math.inf else math.inf
+    return abs(ph * math.exp(la - la_ref) - ph_ref)
+
+
+def run_moves(m, imp, tau, op, beta, n_moves, seed, oracle_every=1):
+    rng = np.random.default_rng(seed)
+    sl = ctq.SkipListTrace(imp, beta, seed=seed)
+    sl.set(tau, op)
+    la, ph, st = sl.evaluate()
+    bars = parity.Bars(f"skip list, {n_moves} moves")
+    products, n_ops, worst = [], [], 0.0
+    for k in range(n_moves + 1):
+        if k > 0:
+            mv = w.pair_move(rng, tau, op, m.n_flav, beta)
+            if mv[0] == "rem":
+                sl.remove(mv[1])
+            else:
+                sl.insert(mv[1], mv[2])
+            tau, op = w.apply_pair_move(mv, tau, op)
+            la, ph, st = sl.evaluate()
+            products.append(st["products"])
+            n_ops.append(len(tau))
+        la_f, ph_f = fresh_eval(imp, tau, op, beta)
+        assert st["n_ops"] == len(tau)
+        if k % oracle_every == 0:
+            ref = parity.oracle_chain_results(m, w.Batch(beta=beta, offsets=np.array([0, len(tau)], np.int32),
+                                                         tau=tau, op=op), [0])[0]
+            ph_ref = complex(ref["phase"])
+            if ref["log_abs"] == -math.inf:
+                assert la == -math.inf and la_f == -math.inf, k
+                continue
+            err = rel(la, ph, ref["log_abs"], ph_ref)
+            worst = max(worst, err)
+            assert err <= bars.fp64(k, ref), (k, err, len(tau))
+        # against the library's own float64 path on the same configuration
+        assert rel(la, ph, la_f, ph_f) <= 2 * parity.FP64_CAP, k
+    bars.check()
+    return np.asarray(products), np.asarray(n_ops), worst
+
+
+@pytest.mark.parametrize("name,chain,n_moves", [("t2g", 3, 100), ("d5", 1, 40)])
+def test_skiplist_moves_match_oracle(name, chain, n_moves, models):
+    m = models(name)
+    imp = parity.load_oracle_model(ctq, m)
+    b = w.WORKLOADS[name][1]()
+    tau, op = b.chain(chain)
+    prods, n_ops, worst = run_moves(m, imp, np.asarray(tau), np.asarray(op), b.beta, n_moves, seed=7)
+    print(f"\n{name}: {n_moves} moves, {n_ops.mean():.0f} operators on average, {prods.mean():.1f} products per "
+          f"move (max {prods.max()}), worst error vs oracle {worst:.2e}")
+    # a local move recomputes O(log k) segment products (plus the ancestors of
+    # the operators whose sector it shifted), far fewer than the k - 1 of a
+    # full product
+    assert prods.mean() < 0.5 * n_ops.mean()
+
+
+def test_skiplist_complex_large_blocks():
+    """Complex d shell with SOC and a complex crystal field, N in [1, 3]
+    (blocks up to 120): the [Re | Im] float64 products."""
+    m = atom.Model(complex_d_model())
+    imp = parity.load_oracle_model(ctq, m)
+    rng = np.random.default_rng(3)
+    b = w.random_batch(rng, m.n_flav, m.beta, 1, 6, 10, gen="g2")
+    tau, op = b.chain(0)
+    prods, n_ops, worst = run_moves(m, imp, np.asarray(tau), np.asarray(op), m.beta, 24, seed=9, oracle_every=2)
+    print(f"\ncomplex d shell: {n_ops.mean():.0f} operators, {prods.mean():.1f} products per move, worst {worst:.2e}")
+
+
+def test_skiplist_empty_and_argument_errors(models):
+    m = models("hubbard2")
+    imp = parity.load_oracle_model(ctq, m)
+    sl = ctq.SkipListTrace(imp, m.beta, seed=1)
+    sl.set([], [])
+    la, ph, st = sl.evaluate()
+    z = OT.trace_chain(m, [], [])
+    assert abs(la - z["log_abs"]) <= 1e-12 * abs(z["log_abs"]) + 1e-14 and ph == 1.0
+    with pytest.raises(ctq.CtqError):
+        sl.set([0.5, 0.2], [1, 0])  # not increasing
+    sl.set([0.5, 1.5], [1, 0])
+    with pytest.raises(ctq.CtqError):
+        sl.insert([0.5], [3])  # time already taken
+    with pytest.raises(ctq.CtqError):
+        sl.insert([m.beta], [3])  # outside [0, beta)
+    with pytest.raises(ctq.CtqError):
+        sl.remove([0.7])  # no operator there
+    la, ph, st = sl.evaluate()  # the configuration is unchanged by the refused calls
+    ref = OT.trace_chain(m, [0.5, 1.5], [1, 0])
+    assert rel(la, ph, ref["log_abs"], complex(ref["phase"])) <= 1e-12
