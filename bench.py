@@ -326,6 +326,25 @@ def run_skiplist(args, world, rank, local):
     rng = np.random.default_rng(2010084820 + rank)
     sl = ctq.SkipListTrace(imp, batch.beta, seed=11)
     stream = torch.cuda.current_stream()
+    s_tab = imp.sectors()[3]
+
+    def n_live(o):
+        """Starting sectors whose string survives (integer walk on the sector table)."""
+        q = np.arange(s_tab.shape[1])
+        for a in o:
+            q = np.where(q >= 0, s_tab[int(a), np.maximum(q, 0)], -1)
+        return int(np.sum(q == np.arange(s_tab.shape[1])))
+
+    def move(t, o):
+        """A pair move whose configuration keeps a surviving string (a move
+        that kills every string has weight 0 and would be rejected anyway;
+        the N-truncated f shell rejects most moves this way)."""
+        for _ in range(10000):
+            mv = w.pair_move(rng, t, o, imp.n_flav, batch.beta)
+            t2, o2 = w.apply_pair_move(mv, t, o)
+            if n_live(o2) > 0:
+                return mv, t2, o2
+        raise RuntimeError("no surviving pair move found")
 
     def fresh(t, o):
         b = w.Batch(beta=batch.beta, offsets=np.array([0, len(t)], np.int32), tau=t, op=o)
@@ -349,24 +368,23 @@ def run_skiplist(args, world, rank, local):
     fresh_first = fresh(tau, op)
     diffs = [abs(ph * math.exp(la - fresh_first[1]) - fresh_first[2])] if np.isfinite(fresh_first[1]) else []
     for _ in range(args.warmup):
-        mv = w.pair_move(rng, tau, op, imp.n_flav, batch.beta)
+        mv, tau, op = move(tau, op)
         (sl.remove(mv[1]) if mv[0] == "rem" else sl.insert(mv[1], mv[2]))
-        tau, op = w.apply_pair_move(mv, tau, op)
         sl.evaluate()
     clocks = ClockSampler(local)
     clocks.start()
-    secs, prods, flops, n_ops = [], [], [], []
+    secs, prods, flops, n_ops, full = [], [], [], [], []
     for _ in range(args.steps):
-        mv = w.pair_move(rng, tau, op, imp.n_flav, batch.beta)
+        mv, tau, op = move(tau, op)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         (sl.remove(mv[1]) if mv[0] == "rem" else sl.insert(mv[1], mv[2]))
         la, ph, st = sl.evaluate()  # synchronises the stream
         secs.append(time.perf_counter() - t1)
-        tau, op = w.apply_pair_move(mv, tau, op)
         prods.append(st["products"])
         flops.append(st["flops"])
         n_ops.append(len(tau))
+        full.append((len(tau) - 1) * st["n_strings"])  # a full evaluation's products
     clocks.stop()
     fresh_last = fresh(tau, op)
     if np.isfinite(fresh_last[1]):
@@ -381,8 +399,10 @@ def run_skiplist(args, world, rank, local):
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT[args.workload] + " (first chain, random pair moves)",
                        "moves": "workloads.pair_move: insert or remove a pair between consecutive operators of "
-                                "one flavour (Pauli-aware)", "mean_operators": statistics.mean(n_ops)},
-            "products_per_move": statistics.mean(prods), "full_products": statistics.mean(n_ops) - 1,
+                                "one flavour (Pauli-aware), redrawn until some string survives",
+                       "mean_operators": statistics.mean(n_ops)},
+            "products_per_move": statistics.mean(prods),
+            "full_products": statistics.mean(full),  # (operators - 1) x surviving strings
             "build": {"seconds": build_s, "products": build_products},
             "fresh_eval_s": fresh_s, "speedup_vs_fresh_eval": fresh_s / per_move,
             "max_rel_diff_vs_fresh": max(diffs) if diffs else None,
@@ -744,10 +764,10 @@ def run_mixed(args, world, rank, local):
         if not args.no_autotune and acc.size:
             eng = autotune.engine(g.imp, prec)
             if eng != "fp64big":  # the float64 large-block kernel is FP64-pipe bound: nothing to tune
-                piece = acc[:4] if eng == "big" else acc[:512]
+                piece = acc[:8] if eng == "big" else acc[:512]
                 tdb = ctq.DeviceBatch(g.sub.subset(piece), device=dev, log_threshold=np.full(piece.size, -np.inf))
                 g.tuning = autotune.tune(g.imp, tdb, prec, lazy=True, cache_path=args.autotune_cache,
-                                         reps=1 if eng == "big" else 3)
+                                         reps=2 if eng == "big" else 3)
         g.ev = ctq.TraceEvaluator(g.imp, g.sub.n_chains, g.db.max_ops, precision=prec, device=dev, tune=g.tuning)
         g.flops, g.items = algorithmic_flops(g.imp, g.sub.subset(acc))
         g.launches = ctq.launches_per_eval(g.imp, prec)

@@ -9,6 +9,7 @@
 #include <cublas_v2.h>
 #include <cusolverDn.h>
 
+#include <cstdlib>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -33,10 +34,18 @@ struct DeviceLA {
   decltype(&cublasDgemm_v2) dgemm = nullptr;
 };
 
-void* open_lib(const char* const* names) {
-  for (int i = 0; names[i]; ++i) {
-    void* h = dlopen(names[i], RTLD_NOW | RTLD_GLOBAL);
+// The first of the names (or of $env, if set) that loads; on failure
+// *why lists every name tried with the loader's message.
+void* open_lib(const char* env, const char* const* names, std::string* why) {
+  std::vector<const char*> tries;
+  const char* over = std::getenv(env);
+  if (over && *over) tries.push_back(over);
+  for (int i = 0; names[i]; ++i) tries.push_back(names[i]);
+  for (const char* n : tries) {
+    void* h = dlopen(n, RTLD_NOW | RTLD_GLOBAL);
     if (h) return h;
+    const char* e = dlerror();
+    *why += std::string(" [") + n + ": " + (e ? e : "not found") + "]";
   }
   return nullptr;
 }
@@ -49,10 +58,15 @@ DeviceLA& la() {
                               "/usr/local/cuda/lib64/libcusolver.so", nullptr};
     const char* bl_names[] = {"libcublas.so.13", "libcublas.so", "/usr/local/cuda/lib64/libcublas.so.13",
                               "/usr/local/cuda/lib64/libcublas.so", nullptr};
-    void* hs = open_lib(sv_names);
-    void* hb = open_lib(bl_names);
+    std::string why_s, why_b;
+    void* hs = open_lib("CTQ_CUSOLVER_LIB", sv_names, &why_s);
+    void* hb = open_lib("CTQ_CUBLAS_LIB", bl_names, &why_b);
     if (!hs || !hb) {
-      L.err = "cannot load cuSOLVER / cuBLAS for large sectors";
+      // sectors above kJacobiMaxDim are diagonalised with cuSOLVER (set-up only);
+      // CTQ_CUSOLVER_LIB / CTQ_CUBLAS_LIB name the libraries when they are elsewhere
+      L.err = "cannot load " + std::string(!hs ? "cuSOLVER" : "cuBLAS") +
+              " (needed to diagonalise sectors larger than 160 states; set CTQ_CUSOLVER_LIB / CTQ_CUBLAS_LIB"
+              " to the library paths):" + (!hs ? why_s : why_b);
       return;
     }
 #define LOAD(h, field, sym) L.field = reinterpret_cast<decltype(L.field)>(dlsym(h, #sym))

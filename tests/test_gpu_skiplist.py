@@ -36,6 +36,18 @@ def rel(la, ph, la_ref, ph_ref):
     return abs(ph * math.exp(la - la_ref) - ph_ref)
 
 
+def live_move(rng, m, tau, op, beta):
+    """A pair move whose configuration keeps a surviving string in the
+    oracle's sector table (a move that kills every string has weight 0; in
+    an N-truncated model most moves do)."""
+    for _ in range(10000):
+        mv = w.pair_move(rng, tau, op, m.n_flav, beta)
+        t2, o2 = w.apply_pair_move(mv, tau, op)
+        if any(OT.walk(m, o2, q0) is not None for q0 in range(m.n_sec)):
+            return mv, t2, o2
+    raise RuntimeError("no surviving pair move")
+
+
 def run_moves(m, imp, tau, op, beta, n_moves, seed, oracle_every=1):
     rng = np.random.default_rng(seed)
     sl = ctq.SkipListTrace(imp, beta, seed=seed)
@@ -45,12 +57,11 @@ def run_moves(m, imp, tau, op, beta, n_moves, seed, oracle_every=1):
     products, n_ops, worst = [], [], 0.0
     for k in range(n_moves + 1):
         if k > 0:
-            mv = w.pair_move(rng, tau, op, m.n_flav, beta)
+            mv, tau, op = live_move(rng, m, tau, op, beta)
             if mv[0] == "rem":
                 sl.remove(mv[1])
             else:
                 sl.insert(mv[1], mv[2])
-            tau, op = w.apply_pair_move(mv, tau, op)
             la, ph, st = sl.evaluate()
             products.append(st["products"])
             n_ops.append(len(tau))
@@ -97,6 +108,7 @@ def test_skiplist_complex_large_blocks():
     tau, op = b.chain(0)
     prods, n_ops, worst = run_moves(m, imp, np.asarray(tau), np.asarray(op), m.beta, 24, seed=9, oracle_every=2)
     print(f"\ncomplex d shell: {n_ops.mean():.0f} operators, {prods.mean():.1f} products per move, worst {worst:.2e}")
+    assert prods.mean() > 0  # the moves keep a surviving string, so every move recomputes something
 
 
 def test_skiplist_empty_and_argument_errors(models):
