@@ -373,7 +373,7 @@ def run_skiplist(args, world, rank, local):
         sl.evaluate()
     clocks = ClockSampler(local)
     clocks.start()
-    secs, prods, flops, n_ops, full = [], [], [], [], []
+    secs, prods, flops, n_ops, full, launches, rounds = [], [], [], [], [], [], []
     for _ in range(args.steps):
         mv, tau, op = move(tau, op)
         torch.cuda.synchronize()
@@ -385,6 +385,8 @@ def run_skiplist(args, world, rank, local):
         flops.append(st["flops"])
         n_ops.append(len(tau))
         full.append((len(tau) - 1) * st["n_strings"])  # a full evaluation's products
+        launches.append(st["launches"])
+        rounds.append(st["rounds"])
     clocks.stop()
     fresh_last = fresh(tau, op)
     if np.isfinite(fresh_last[1]):
@@ -410,7 +412,8 @@ def run_skiplist(args, world, rank, local):
                          "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": achieved / (fp64_peak / 1e12),
                          "peak_source": "measured FP64 FMA rate (ctq_probe_fma_rate, this run); achieved counts "
                                         "the products' flops over the whole move time", "traffic": None},
-            "gpu_launches": None, "clocks": clocks.summary()}
+            "launches_per_move": statistics.mean(launches), "rounds_per_move": statistics.mean(rounds),
+            "gpu_launches": int(sum(launches)), "clocks": clocks.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -1182,6 +1185,10 @@ def main():
         "clocks": clocks.summary(),
         "wall_s_timed_region": wall,
     }
+    if args.precision == "fp64":
+        # the float64 pipe two ways: DFMA (the roofline's peak) and the warp-level MMA
+        line["fp64_rates_tflops"] = {"dfma": fp64_peak / 1e12,
+                                     "mma_sync_m8n8k4": ctq.probe_fma_rate(local, 2, 4000) / 1e12}
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in w.WORKLOADS:
         n_first = min(CPU_SAMPLE.get(args.workload, 64), batch.n_chains)
         line["cpu_baseline"], _ = cpu_baseline_leg(args.workload, n_first, min_s=10.0)

@@ -324,7 +324,11 @@ int ctq_eval_traces_static(const ctq_impurity* imp, const ctq_batch* batch, cons
  * contain a changed operator are recomputed, about one per level of the
  * skip list (O(log k)), plus the ancestors of operators whose sector the
  * change shifted.  Products in float64 on the SIMT pipe, renormalised by
- * exact powers of two; operators c and c+ only (codes 2 f + dag).
+ * exact powers of two; operators c and c+ only (codes 2 f + dag).  An
+ * evaluation launches one kernel per dependency round of its new products
+ * (all strings and segments together), plus one for the new leaves, one
+ * clearing their bookkeeping words and one for the root traces, after a
+ * single host-to-device copy of its task tables.
  *
  * ctq_skiplist_create: the handle works on imp's device, enqueues its
  *   kernels on `stream` (cudaStream_t, NULL = legacy default) and allocates
@@ -354,6 +358,8 @@ typedef struct {
   int n_ops;             /* operators of the configuration */
   int n_strings;         /* surviving starting sectors */
   int64_t device_bytes;  /* device memory held by the handle */
+  int64_t launches;      /* kernels this evaluation launched */
+  int rounds;            /* dependency rounds of its products */
 } ctq_skiplist_stats;
 int ctq_skiplist_create(const ctq_impurity* imp, double beta, uint64_t seed, void* stream, ctq_skiplist** out);
 int ctq_skiplist_set(ctq_skiplist* sl, int n, const double* tau, const int32_t* op);
@@ -454,13 +460,26 @@ void ctq_free_impurity(ctq_impurity* imp);
 
 /*
  * Measures the sustained fused-multiply-add rate of one arithmetic pipe on
- * `device` (kind 0: float64, 1: float32), 8 independent FMA chains per thread,
- * 8 CTAs of 256 threads per SM.  *flops_per_s receives 2 x FMAs / second.
- * Allocates and frees a small device buffer; synchronises the device.
- * No counterpart in the paper: it states the arithmetic roofline of the
- * small-block trace.  Errors: CTQ_ERR_ARG, CTQ_ERR_NOMEM, CTQ_ERR_CUDA.
+ * `device` (kind 0: float64 FMA, 1: float32 FMA, 8 independent chains per
+ * thread; kind 2: the float64 warp-level MMA mma.sync.m8n8k4.f64, 8
+ * independent accumulators per warp, 256 multiply-adds per instruction),
+ * 8 CTAs of 256 threads per SM.  *flops_per_s receives 2 x multiply-adds /
+ * second.  Allocates and frees a small device buffer; synchronises the
+ * device.  No counterpart in the paper: it states the arithmetic roofline of
+ * the small-block trace.  Errors: CTQ_ERR_ARG, CTQ_ERR_NOMEM, CTQ_ERR_CUDA.
  */
 int ctq_probe_fma_rate(int device, int kind, int iters, double* flops_per_s);
+
+/*
+ * Accuracy hook of the propagators' exponential: for the n host values x[i]
+ * (the propagator arguments -dtau (E - E_min) <= 0), computes on `device`
+ * y_table[i] = the table-driven e^x the float64 trace kernel uses (Tang's
+ * method, 64 entries) and y_lib[i] = the CUDA library's exp(x[i]), both
+ * written to host arrays of n doubles owned by the caller.  Allocates and
+ * frees device buffers and synchronises.  No counterpart in the paper.
+ * Errors: CTQ_ERR_ARG, CTQ_ERR_NOMEM, CTQ_ERR_CUDA.
+ */
+int ctq_probe_exp(int device, int n, const double* x, double* y_table, double* y_lib);
 
 /*
  * Diagnostic of the small-block kernel's tensor-core operand conventions

@@ -93,16 +93,27 @@ __device__ __forceinline__ void two_sum_acc(double& h, double& l, double x) {
 // sector q_j contributes -dtau_j (E_min(q_j) - E_ref) to the log of the
 // product).  The chunk sums are compensated and combined by a compensated
 // inclusive scan over lanes, so the total keeps the accuracy of a
-// compensated sequential sum.  With tracking, the chunks are the segments of
-// S operators and the scan also yields the log scale segL and the applied
-// log-norm prefix segP at every segment end.
+// compensated sequential sum.  With tracking, every segment end (a multiple
+// of S operators) is a chunk end and the scan also yields the log scale segL
+// and the applied log-norm prefix segP there.
 __device__ __forceinline__ void chain_log_scale(const DevModel& M, const BatchView& B, const EvalCfg& cfg, int a0, int n, int q0,
                                 double t_first, double t_last, bool track, const short* path, const short* opsm,
                                 double* segL, double* segP, double* out_L) {
   const int lane = threadIdx.x & 31;
   const int ns = M.n_sec;
   const double emr0 = M.E_min[q0] - M.E_ref;
-  const int CH = track ? cfg.S : max(1, (n + 30) / 32);  // chunk length over j = 1 .. n-1
+  // chunk length over j = 1 .. n-1: with tracking the smallest divisor of S
+  // that covers the string in one pass of 32 lanes (segment ends stay chunk
+  // ends), else S; without tracking ceil((n - 1) / 32)
+  int CH = max(1, (n + 30) / 32);
+  if (track) {
+    CH = cfg.S;
+    for (int d = 1; d < cfg.S; ++d)
+      if (cfg.S % d == 0 && 32 * d >= n - 1) {
+        CH = d;
+        break;
+      }
+  }
   const int nch = (n - 1 + CH - 1) / CH;
   double ch = -t_first * emr0, cl = 0.0, cp = 0.0;  // running carry (compensated) and log-norm prefix
   two_sum_acc(ch, cl, -t_last * emr0);
@@ -129,9 +140,9 @@ __device__ __forceinline__ void chain_log_scale(const DevModel& M, const BatchVi
     double H = ch, Lo = cl + l;
     two_sum_acc(H, Lo, h);
     const double P = cp + ps;
-    if (track && t < nch && (t + 1) * CH < n) {
-      segL[t + 1] = H + Lo;
-      segP[t + 1] = P;
+    if (track && t < nch && (t + 1) * CH < n && ((t + 1) * CH) % cfg.S == 0) {
+      segL[(t + 1) * CH / cfg.S] = H + Lo;
+      segP[(t + 1) * CH / cfg.S] = P;
     }
     ch = __shfl_sync(FULL, H, 31);
     cl = __shfl_sync(FULL, Lo, 31);

@@ -19,12 +19,21 @@
 // and are recomputed: about one product per level for a local insertion or
 // removal, plus the ancestors of the leaves whose sector the move shifted.
 //
-// Arithmetic: float64 on the SIMT pipe (complex blocks as [Re | Im] rows);
-// each product is renormalised by an exact power of two (exponent kept on
-// the device) and carries the log of its propagators' E_min factors (kept
-// on the host), as in the other trace kernels.  The host structure is
-// small (operators, heights, the cache map); every product, leaf and trace
-// runs in the kernels below, asynchronously on the handle's stream.
+// Arithmetic: float64 on the SIMT pipe (complex blocks as [Re | Im] rows).
+// A stored product is raw: its true value is the stored matrix times
+// 2^{E} (E kept on the device beside the matrix's max |entry|), and every
+// consumer scales its factors by the exact power of two that brings their
+// max |entry| into [1, 2) as it loads them, so the products are the
+// renormalised products of the other trace kernels, value for value.  The
+// log of the propagators' E_min factors is kept on the host.
+//
+// Launches: an evaluation first plans every product it needs on the host
+// (the cache decides what is new), orders the new products in rounds (a
+// product's round is one more than its factors'), and then launches one
+// grouped kernel per round over all strings and segments (CTAs find their
+// product by a binary search on tile offsets), after one kernel for the
+// new leaves and one clearing the new products' max words; one kernel takes
+// every string's root trace.  The task tables go to the device in one copy.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,10 +53,50 @@ namespace ctq {
 namespace {
 
 constexpr int SL_MAX_LEVEL = 24;
-constexpr int GT = 64;   // GEMM tile (rows and columns of C)
-constexpr int GK = 16;   // K chunk
-constexpr int G_THREADS = 256;
+constexpr int GK = 16;            // K chunk of the product tiles
+constexpr int LEAF_CHUNK = 1024;  // elements of a leaf per CTA (256 threads)
 constexpr long long EXP_DEAD = LLONG_MIN / 4;
+
+// A leaf X = P_dt(q_out) F (raw, exponent 0).
+struct SlLeaf {
+  const double* E_out;
+  double* out;
+  unsigned long long* w;
+  int64_t off;
+  double dt;
+  int d_out, d_in, cplx, tile0;
+};
+// A product C = (R 2^-r)(L 2^-l), r and l the exponents of max|R|, max|L|.
+struct SlProd {
+  const double* R;
+  const double* L;
+  double* C;
+  const unsigned long long* wR;
+  const unsigned long long* wL;
+  unsigned long long* wC;
+  int M, K, N, cplx, tile0, tiles_x;
+};
+// A root: Tr P_t(q0) X, written with X's exponent to out[0..2].
+struct SlRoot {
+  const double* X;
+  const unsigned long long* w;
+  const double* E0;
+  double* out;
+  double t;
+  int d, cplx;
+};
+
+// Index of the task whose tile range holds CTA b (tile0 ascending, first 0).
+template <typename T>
+__device__ __forceinline__ int find_task(const T* t, int n, int b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (t[mid].tile0 <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
 
 __device__ __forceinline__ void atomic_max_abs(unsigned long long* w, double v) {
   // |v| >= 0: the bit patterns of non-negative doubles order like the values
@@ -55,57 +104,88 @@ __device__ __forceinline__ void atomic_max_abs(unsigned long long* w, double v) 
   if ((threadIdx.x & 31) == 0 && v > 0.0) atomicMax(w, (unsigned long long)__double_as_longlong(v));
 }
 
-// Leaf X = P_dt(q_out) F: out[m][j] = e^{-dt E_rel(q_out)_m} F[m][j]; complex
-// rows are stored [Re(0..d_in) | Im(0..d_in)].
-__global__ void k_sl_leaf(const double* blk, int64_t off, int cplx, int d_out, int d_in, const double* E_out,
-                          double dt, double* out, unsigned long long* maxw) {
+// 2^-e for the max word m (0 for an all-zero matrix) and e itself.
+__device__ __forceinline__ double norm_of(const unsigned long long* w, int* e) {
+  const double m = __longlong_as_double((long long)w[0]);
+  if (!(m > 0.0)) {
+    *e = 0;
+    return 0.0;
+  }
+  *e = ilogb(m);
+  return ldexp(1.0, -*e);
+}
+
+__global__ void k_sl_zero(unsigned long long* const* w, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    w[i][0] = 0ull;
+    w[i][1] = 0ull;
+  }
+}
+
+// Leaves: out[m][j] = e^{-dt E_rel(q_out)_m} F[m][j]; complex rows are
+// stored [Re(0..d_in) | Im(0..d_in)].
+__global__ void k_sl_leaves(const double* blk, const SlLeaf* tasks, int n) {
+  const SlLeaf T = tasks[find_task(tasks, n, blockIdx.x)];
+  const long long total = (long long)T.d_out * T.d_in;
+  const long long e0 = (long long)(blockIdx.x - T.tile0) * LEAF_CHUNK;
+  const long long e1 = e0 + LEAF_CHUNK < total ? e0 + LEAF_CHUNK : total;
   double mx = 0.0;
-  const long long total = (long long)d_out * d_in;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-    const int m = int(e / d_in), j = int(e - (long long)m * d_in);
-    const double p = dt > 0.0 ? exp(-dt * E_out[m]) : 1.0;
-    if (cplx) {
-      const double re = blk[2 * (off + e)] * p, im = blk[2 * (off + e) + 1] * p;
-      out[size_t(m) * 2 * d_in + j] = re;
-      out[size_t(m) * 2 * d_in + d_in + j] = im;
+  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const int m = int(e / T.d_in), j = int(e - (long long)m * T.d_in);
+    const double p = T.dt > 0.0 ? exp(-T.dt * T.E_out[m]) : 1.0;
+    if (T.cplx) {
+      const double re = blk[2 * (T.off + e)] * p, im = blk[2 * (T.off + e) + 1] * p;
+      T.out[size_t(m) * 2 * T.d_in + j] = re;
+      T.out[size_t(m) * 2 * T.d_in + T.d_in + j] = im;
       mx = fmax(mx, fmax(fabs(re), fabs(im)));
     } else {
-      const double v = blk[off + e] * p;
-      out[e] = v;
+      const double v = blk[T.off + e] * p;
+      T.out[e] = v;
       mx = fmax(mx, fabs(v));
     }
   }
-  atomic_max_abs(maxw, mx);
+  atomic_max_abs(T.w, mx);
 }
 
-// C = R L.  Real: R (M x K), L (K x N), C (M x N), row-major.  Complex
-// ([Re | Im] rows): the real GEMM of [Rr | Ri] (M x 2K) with
-// [[Lr, Li], [-Li, Lr]] (2K x 2N) gives [Cr | Ci] (M x 2N).
-__global__ void __launch_bounds__(G_THREADS) k_sl_gemm(const double* R, const double* L, double* C, int M, int K,
-                                                       int N, int cplx, unsigned long long* maxw) {
-  __shared__ double As[GK][GT + 1];
-  __shared__ double Bs[GK][GT + 1];
-  const int Kp = cplx ? 2 * K : K, Np = cplx ? 2 * N : N;
-  const int row0 = blockIdx.y * GT, col0 = blockIdx.x * GT;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+// Products, TILE x TILE outputs per CTA, 4 x 4 per thread.  Real: R (M x K),
+// L (K x N), C (M x N), row-major.  Complex ([Re | Im] rows): the real GEMM
+// of [Rr | Ri] (M x 2K) with [[Lr, Li], [-Li, Lr]] (2K x 2N) gives
+// [Cr | Ci] (M x 2N).
+template <int TILE>
+__global__ void __launch_bounds__((TILE / 4) * (TILE / 4)) k_sl_gemm(const SlProd* tasks, int n) {
+  constexpr int NT = (TILE / 4) * (TILE / 4), TPR = TILE / 4;
+  __shared__ double As[GK][TILE + 1];
+  __shared__ double Bs[GK][TILE + 1];
+  const SlProd P = tasks[find_task(tasks, n, blockIdx.x)];
+  const int local = blockIdx.x - P.tile0;
+  const int row0 = (local / P.tiles_x) * TILE, col0 = (local % P.tiles_x) * TILE;
+  int er, el;
+  const double sR = norm_of(P.wR, &er), sL = norm_of(P.wL, &el);
+  if (local == 0 && threadIdx.x == 0) {
+    const long long eR = reinterpret_cast<const long long*>(P.wR)[1], eL = reinterpret_cast<const long long*>(P.wL)[1];
+    reinterpret_cast<long long*>(P.wC)[1] = (sR > 0.0 && sL > 0.0) ? eR + er + eL + el : EXP_DEAD;
+  }
+  const int M = P.M, K = P.K, N = P.N;
+  const int Kp = P.cplx ? 2 * K : K, Np = P.cplx ? 2 * N : N;
+  const int tx = threadIdx.x % TPR, ty = threadIdx.x / TPR;
   double acc[4][4] = {};
   for (int k0 = 0; k0 < Kp; k0 += GK) {
-    for (int e = threadIdx.x; e < GT * GK; e += G_THREADS) {
+    for (int e = threadIdx.x; e < TILE * GK; e += NT) {
       const int r = e / GK, k = e - r * GK;  // A: row r, column k0 + k
       const int gr = row0 + r, gk = k0 + k;
-      As[k][r] = (gr < M && gk < Kp) ? R[size_t(gr) * Kp + gk] : 0.0;
-      const int kb = e / GT, c = e - kb * GT;  // B: row k0 + kb, column c
+      As[k][r] = (gr < M && gk < Kp) ? P.R[size_t(gr) * Kp + gk] * sR : 0.0;
+      const int kb = e / TILE, c = e - kb * TILE;  // B: row k0 + kb, column c
       const int bk = k0 + kb, bc = col0 + c;
       double v = 0.0;
       if (bk < Kp && bc < Np) {
-        if (!cplx || bk < K) {
-          v = L[size_t(bk) * Np + bc];
+        if (!P.cplx || bk < K) {
+          v = P.L[size_t(bk) * Np + bc];
         } else {
           const int kk = bk - K;
-          v = (bc < N) ? -L[size_t(kk) * Np + N + bc] : L[size_t(kk) * Np + (bc - N)];
+          v = (bc < N) ? -P.L[size_t(kk) * Np + N + bc] : P.L[size_t(kk) * Np + (bc - N)];
         }
       }
-      Bs[kb][c] = v;
+      Bs[kb][c] = v * sL;
     }
     __syncthreads();
 #pragma unroll
@@ -131,43 +211,27 @@ __global__ void __launch_bounds__(G_THREADS) k_sl_gemm(const double* R, const do
     for (int j = 0; j < 4; ++j) {
       const int c = col0 + tx * 4 + j;
       if (c < Np) {
-        C[size_t(r) * Np + c] = acc[i][j];
+        P.C[size_t(r) * Np + c] = acc[i][j];
         mx = fmax(mx, fabs(acc[i][j]));
       }
     }
   }
-  atomic_max_abs(maxw, mx);
+  atomic_max_abs(P.wC, mx);
 }
 
-// X *= 2^-e with e the exponent of max|X| (an exact scaling); the product's
-// exponent becomes e + the factors' exponents, or EXP_DEAD when X == 0.
-__global__ void k_sl_scale(double* X, long long count, const unsigned long long* maxw, const long long* eR,
-                           const long long* eL, long long* eout) {
-  const double mx = __longlong_as_double((long long)*maxw);
-  if (mx == 0.0) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *eout = EXP_DEAD;
-    return;
-  }
-  const int e = ilogb(mx);
-  const double s = ldexp(1.0, -e);
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
-    X[i] *= s;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *eout = e + (eR ? *eR : 0) + (eL ? *eL : 0);
-}
-
-// Tr P_t(q0) X = sum_j e^{-t E_rel(q0)_j} X[j][j] (one block); out: re, im;
-// the product's exponent is copied beside it.
-__global__ void k_sl_root(const double* X, int d, int cplx, const double* E0, double t, const long long* ex,
-                          double* out) {
+// Roots, one CTA each: out = (Re, Im) of sum_j e^{-t E_rel(q0)_j} X[j][j]
+// and X's exponent bits (EXP_DEAD for a zero product).
+__global__ void k_sl_roots(const SlRoot* tasks) {
+  const SlRoot T = tasks[blockIdx.x];
   __shared__ double sr[32], si[32];
   double re = 0.0, im = 0.0;
-  for (int j = threadIdx.x; j < d; j += blockDim.x) {
-    const double p = exp(-t * E0[j]);
-    if (cplx) {
-      re += p * X[size_t(j) * 2 * d + j];
-      im += p * X[size_t(j) * 2 * d + d + j];
+  for (int j = threadIdx.x; j < T.d; j += blockDim.x) {
+    const double p = exp(-T.t * T.E0[j]);
+    if (T.cplx) {
+      re += p * T.X[size_t(j) * 2 * T.d + j];
+      im += p * T.X[size_t(j) * 2 * T.d + T.d + j];
     } else {
-      re += p * X[size_t(j) * d + j];
+      re += p * T.X[size_t(j) * T.d + j];
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -186,9 +250,11 @@ __global__ void k_sl_root(const double* X, int d, int cplx, const double* E0, do
       a += sr[i];
       b += si[i];
     }
-    out[0] = a;
-    out[1] = b;
-    out[2] = __longlong_as_double(*ex);
+    const bool dead = !(__longlong_as_double((long long)T.w[0]) > 0.0);
+    const long long e = dead ? EXP_DEAD : reinterpret_cast<const long long*>(T.w)[1];
+    T.out[0] = dead ? 0.0 : a;
+    T.out[1] = dead ? 0.0 : b;
+    T.out[2] = __longlong_as_double(e);
   }
 }
 
@@ -209,7 +275,8 @@ struct Buf {
   unsigned long long* maxw = nullptr;  // [0] max|X| bits; [1] exponent (long long)
   int d_out = 0, d_in = 0;
   double L = 0.0;
-  long long* ex() const { return reinterpret_cast<long long*>(maxw + 1); }
+  uint64_t epoch = 0;  // the evaluation that planned it
+  int round = 0;       // its launch round in that evaluation (leaves 0)
 };
 
 class Pool {
@@ -288,6 +355,11 @@ struct ctq_skiplist {
   std::unordered_map<std::string, std::shared_ptr<ctq::Buf>> cache;
   double* d_res = nullptr;  // [3 n_sec]: trace re, im, exponent bits per q0
   ctq_skiplist_stats stats{};
+  uint64_t epoch = 0;
+  int num_sms = 1;
+  unsigned char* h_tab = nullptr;  // task tables: pinned host staging and device copy
+  unsigned char* d_tab = nullptr;
+  size_t tab_cap = 0;
 };
 
 namespace ctq {
@@ -304,7 +376,16 @@ int sl_height(ctq_skiplist* S) {
   return h;
 }
 
-std::shared_ptr<Buf> new_buf(ctq_skiplist* S, int d_out, int d_in) {
+// The work one evaluation launches, planned on the host.
+struct Plan {
+  std::vector<unsigned long long*> zero;        // max / exponent words of the new leaves and products
+  std::vector<SlLeaf> leaves;
+  std::vector<std::vector<SlProd>> rounds;      // rounds[r - 1]: products of round r
+  std::vector<SlRoot> roots;
+  std::vector<std::shared_ptr<Buf>> keep;       // new buffers, alive until their kernels are enqueued
+};
+
+std::shared_ptr<Buf> new_buf(ctq_skiplist* S, Plan& P, int d_out, int d_in, int round) {
   auto b = std::shared_ptr<Buf>(new Buf(), [S](Buf* x) {
     if (x->p) S->pool.put(x->p, x->elems);
     if (x->maxw) S->pool.put_word(x->maxw);
@@ -316,43 +397,55 @@ std::shared_ptr<Buf> new_buf(ctq_skiplist* S, int d_out, int d_in) {
   b->p = S->pool.get(b->elems);
   b->maxw = S->pool.word();
   if (!b->p || !b->maxw) return nullptr;
+  b->epoch = S->epoch;
+  b->round = round;
+  P.zero.push_back(b->maxw);
+  P.keep.push_back(b);
   return b;
 }
 
-int grid_for(long long n) { return int(std::min<long long>((n + 255) / 256, 152LL * 8)); }
+int round_of(const ctq_skiplist* S, const Buf& b) { return b.epoch == S->epoch ? b.round : 0; }
 
-// Scales a freshly written product and records its exponent.
-int finish(ctq_skiplist* S, const Buf& b, const Buf* R, const Buf* L) {
-  k_sl_scale<<<grid_for((long long)b.elems), 256, 0, S->st>>>(b.p, (long long)b.elems, b.maxw, R ? R->ex() : nullptr,
-                                                              L ? L->ex() : nullptr, b.ex());
-  return cudaPeekAtLastError() == cudaSuccess ? CTQ_OK : CTQ_ERR_CUDA;
-}
-
-std::shared_ptr<Buf> make_leaf(ctq_skiplist* S, int alpha, int q_in, int q_out, double dt, int* st) {
+std::shared_ptr<Buf> make_leaf(ctq_skiplist* S, Plan& P, int alpha, int q_in, int q_out, double dt, int* st) {
   const HostModel& H = *S->H;
   const int ns = H.n_sec, d_in = H.dims[q_in], d_out = H.dims[q_out];
-  auto b = new_buf(S, d_out, d_in);
+  auto b = new_buf(S, P, d_out, d_in, 0);
   if (!b) { *st = CTQ_ERR_NOMEM; return nullptr; }
-  cudaMemsetAsync(b->maxw, 0, 16, S->st);
-  const int64_t off = H.blk_off[size_t(alpha) * ns + q_in];
-  k_sl_leaf<<<grid_for((long long)d_out * d_in), 256, 0, S->st>>>(S->D->blk, off, H.is_complex, d_out, d_in,
-                                                                   S->D->E_rel + H.E_off[q_out], dt, b->p, b->maxw);
-  *st = finish(S, *b, nullptr, nullptr);
+  SlLeaf t{};
+  t.E_out = S->D->E_rel + H.E_off[q_out];
+  t.out = b->p;
+  t.w = b->maxw;
+  t.off = H.blk_off[size_t(alpha) * ns + q_in];
+  t.dt = dt;
+  t.d_out = d_out;
+  t.d_in = d_in;
+  t.cplx = H.is_complex;
+  P.leaves.push_back(t);
   b->L = dt > 0.0 ? -dt * (H.E_min[q_out] - H.E_gs) : 0.0;
   S->stats.leaves += 1;
   return b;
 }
 
-// C = R L (R applied after L).
-std::shared_ptr<Buf> product(ctq_skiplist* S, const std::shared_ptr<Buf>& R, const std::shared_ptr<Buf>& L, int* st) {
-  auto b = new_buf(S, R->d_out, L->d_in);
+// C = R L (R applied after L), in the round after its factors'.
+std::shared_ptr<Buf> product(ctq_skiplist* S, Plan& P, const std::shared_ptr<Buf>& R, const std::shared_ptr<Buf>& L,
+                             int* st) {
+  const int round = std::max(round_of(S, *R), round_of(S, *L)) + 1;
+  auto b = new_buf(S, P, R->d_out, L->d_in, round);
   if (!b) { *st = CTQ_ERR_NOMEM; return nullptr; }
-  cudaMemsetAsync(b->maxw, 0, 16, S->st);
   const int cplx = S->H->is_complex;
-  const int Np = cplx ? 2 * L->d_in : L->d_in;
-  dim3 grid((Np + GT - 1) / GT, (R->d_out + GT - 1) / GT);
-  k_sl_gemm<<<grid, G_THREADS, 0, S->st>>>(R->p, L->p, b->p, R->d_out, R->d_in, L->d_in, cplx, b->maxw);
-  *st = finish(S, *b, R.get(), L.get());
+  SlProd t{};
+  t.R = R->p;
+  t.L = L->p;
+  t.C = b->p;
+  t.wR = R->maxw;
+  t.wL = L->maxw;
+  t.wC = b->maxw;
+  t.M = R->d_out;
+  t.K = R->d_in;
+  t.N = L->d_in;
+  t.cplx = cplx;
+  if (int(P.rounds.size()) < round) P.rounds.resize(round);
+  P.rounds[round - 1].push_back(t);
   b->L = R->L + L->L;
   S->stats.products += 1;
   S->stats.flops += 2.0 * R->d_out * double(R->d_in) * L->d_in * (cplx ? 4.0 : 1.0);
@@ -383,11 +476,11 @@ std::string seg_key(const std::vector<const std::string*>& kids) {
   return k;
 }
 
-// Builds (or finds in the cache) every segment product of the string that
-// starts in sector q0 and launches its root trace into d_res[3 q0 ..].
-// Returns the root's log scale in *L_root.
-int eval_string(ctq_skiplist* S, int q0, const std::vector<int>& path, std::unordered_set<std::string>& used,
-                double* L_root) {
+// Plans (or finds in the cache) every segment product of the string that
+// starts in sector q0 and its root trace into d_res[3 q0 ..].  Returns the
+// root's log scale in *L_root.
+int plan_string(ctq_skiplist* S, Plan& P, int q0, const std::vector<int>& path,
+                std::unordered_set<std::string>& used, double* L_root) {
   const int n = int(S->ops.size());
   std::vector<std::string> keys(n);
   std::vector<std::shared_ptr<Buf>> bufs(n);
@@ -400,7 +493,7 @@ int eval_string(ctq_skiplist* S, int q0, const std::vector<int>& path, std::unor
       bufs[i] = it->second;
       S->stats.reused += 1;
     } else {
-      bufs[i] = make_leaf(S, S->ops[i].alpha, path[i], path[i + 1], dt, &st);
+      bufs[i] = make_leaf(S, P, S->ops[i].alpha, path[i], path[i + 1], dt, &st);
       if (st != CTQ_OK) return st;
       S->cache[keys[i]] = bufs[i];
     }
@@ -434,7 +527,7 @@ int eval_string(ctq_skiplist* S, int q0, const std::vector<int>& path, std::unor
         S->stats.reused += 1;
       } else {
         buf = bufs[a];
-        for (int j = a + 1; j < b && st == CTQ_OK; ++j) buf = product(S, bufs[j], buf, &st);
+        for (int j = a + 1; j < b && st == CTQ_OK; ++j) buf = product(S, P, bufs[j], buf, &st);
         if (st != CTQ_OK) return st;
         S->cache[k] = buf;
       }
@@ -449,9 +542,106 @@ int eval_string(ctq_skiplist* S, int q0, const std::vector<int>& path, std::unor
   const Buf& root = *bufs[0];
   const HostModel& H = *S->H;
   const double t_wrap = S->beta - S->ops[n - 1].t + S->ops[0].t;
-  k_sl_root<<<1, 256, 0, S->st>>>(root.p, H.dims[q0], H.is_complex, S->D->E_rel + H.E_off[q0], t_wrap, root.ex(),
-                                  S->d_res + 3 * q0);
+  SlRoot r{};
+  r.X = root.p;
+  r.w = root.maxw;
+  r.E0 = S->D->E_rel + H.E_off[q0];
+  r.out = S->d_res + 3 * q0;
+  r.t = t_wrap;
+  r.d = H.dims[q0];
+  r.cplx = H.is_complex;
+  P.roots.push_back(r);
   *L_root = root.L - t_wrap * (H.E_min[q0] - H.E_gs);
+  return CTQ_OK;
+}
+
+size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// Copies the planned tables to the device (one copy) and enqueues the
+// zeroing, leaf, per-round product and root kernels.
+int launch_plan(ctq_skiplist* S, Plan& P) {
+  // tile offsets: leaves in chunks, products in tiles (32 x 32 when a round
+  // would not fill two CTAs per SM with 64 x 64 tiles)
+  int leaf_tiles = 0;
+  for (SlLeaf& t : P.leaves) {
+    t.tile0 = leaf_tiles;
+    leaf_tiles += int((int64_t(t.d_out) * t.d_in + LEAF_CHUNK - 1) / LEAF_CHUNK);
+  }
+  std::vector<int> tile(P.rounds.size()), n_tiles(P.rounds.size());
+  for (size_t r = 0; r < P.rounds.size(); ++r) {
+    long long t64 = 0;
+    for (const SlProd& t : P.rounds[r]) {
+      const int np = t.cplx ? 2 * t.N : t.N;
+      t64 += (long long)((t.M + 63) / 64) * ((np + 63) / 64);
+    }
+    tile[r] = t64 < 2LL * S->num_sms ? 32 : 64;
+    int acc = 0;
+    for (SlProd& t : P.rounds[r]) {
+      const int np = t.cplx ? 2 * t.N : t.N;
+      t.tile0 = acc;
+      t.tiles_x = (np + tile[r] - 1) / tile[r];
+      acc += t.tiles_x * ((t.M + tile[r] - 1) / tile[r]);
+    }
+    n_tiles[r] = acc;
+  }
+  // one host staging buffer: zero list, leaves, rounds, roots
+  size_t off = 0;
+  const size_t o_zero = off;
+  off = align16(off + P.zero.size() * sizeof(unsigned long long*));
+  const size_t o_leaf = off;
+  off = align16(off + P.leaves.size() * sizeof(SlLeaf));
+  std::vector<size_t> o_round(P.rounds.size());
+  for (size_t r = 0; r < P.rounds.size(); ++r) {
+    o_round[r] = off;
+    off = align16(off + P.rounds[r].size() * sizeof(SlProd));
+  }
+  const size_t o_root = off;
+  off = align16(off + P.roots.size() * sizeof(SlRoot));
+  if (off == 0) return CTQ_OK;
+  if (off > S->tab_cap) {
+    // the previous evaluation synchronised the stream: the old tables are idle
+    if (S->h_tab) cudaFreeHost(S->h_tab);
+    if (S->d_tab) cudaFree(S->d_tab);
+    S->h_tab = nullptr;
+    S->d_tab = nullptr;
+    S->tab_cap = 0;
+    const size_t cap = std::max<size_t>(off * 2, 64 * 1024);
+    if (cudaMallocHost(&S->h_tab, cap) != cudaSuccess) return CTQ_ERR_NOMEM;
+    if (cudaMalloc(&S->d_tab, cap) != cudaSuccess) return CTQ_ERR_NOMEM;
+    S->tab_cap = cap;
+  }
+  std::memcpy(S->h_tab + o_zero, P.zero.data(), P.zero.size() * sizeof(unsigned long long*));
+  std::memcpy(S->h_tab + o_leaf, P.leaves.data(), P.leaves.size() * sizeof(SlLeaf));
+  for (size_t r = 0; r < P.rounds.size(); ++r)
+    std::memcpy(S->h_tab + o_round[r], P.rounds[r].data(), P.rounds[r].size() * sizeof(SlProd));
+  std::memcpy(S->h_tab + o_root, P.roots.data(), P.roots.size() * sizeof(SlRoot));
+  if (cudaMemcpyAsync(S->d_tab, S->h_tab, off, cudaMemcpyHostToDevice, S->st) != cudaSuccess) return CTQ_ERR_CUDA;
+  int launches = 0;
+  if (!P.zero.empty()) {
+    const int n = int(P.zero.size());
+    k_sl_zero<<<std::min((n + 255) / 256, 1024), 256, 0, S->st>>>(
+        reinterpret_cast<unsigned long long* const*>(S->d_tab + o_zero), n);
+    ++launches;
+  }
+  if (!P.leaves.empty()) {
+    k_sl_leaves<<<leaf_tiles, 256, 0, S->st>>>(S->D->blk, reinterpret_cast<const SlLeaf*>(S->d_tab + o_leaf),
+                                                int(P.leaves.size()));
+    ++launches;
+  }
+  for (size_t r = 0; r < P.rounds.size(); ++r) {
+    if (P.rounds[r].empty()) continue;
+    const SlProd* t = reinterpret_cast<const SlProd*>(S->d_tab + o_round[r]);
+    const int n = int(P.rounds[r].size());
+    if (tile[r] == 32) k_sl_gemm<32><<<n_tiles[r], 64, 0, S->st>>>(t, n);
+    else k_sl_gemm<64><<<n_tiles[r], 256, 0, S->st>>>(t, n);
+    ++launches;
+  }
+  if (!P.roots.empty()) {
+    k_sl_roots<<<int(P.roots.size()), 256, 0, S->st>>>(reinterpret_cast<const SlRoot*>(S->d_tab + o_root));
+    ++launches;
+  }
+  S->stats.launches += launches;
+  S->stats.rounds = int(P.rounds.size());
   return cudaPeekAtLastError() == cudaSuccess ? CTQ_OK : CTQ_ERR_CUDA;
 }
 
@@ -493,6 +683,8 @@ extern "C" int ctq_skiplist_create(const ctq_impurity* imp, double beta, uint64_
   S->beta = beta;
   S->rng = ctq::mix64(seed ^ 0x5ca1ab1eull);
   ctq::DevGuard g(S->device);
+  cudaDeviceGetAttribute(&S->num_sms, cudaDevAttrMultiProcessorCount, S->device);
+  S->num_sms = std::max(S->num_sms, 1);
   if (cudaMalloc(&S->d_res, sizeof(double) * 3 * std::max(H->n_sec, 1)) != cudaSuccess) {
     delete S;
     return CTQ_ERR_NOMEM;
@@ -509,6 +701,8 @@ extern "C" void ctq_skiplist_free(ctq_skiplist* S) {
     S->cache.clear();
     S->pool.release();
     cudaFree(S->d_res);
+    if (S->h_tab) cudaFreeHost(S->h_tab);
+    if (S->d_tab) cudaFree(S->d_tab);
   }
   delete S;
 }
@@ -571,6 +765,8 @@ extern "C" int ctq_skiplist_evaluate(ctq_skiplist* S, double* log_abs, double* p
   const int ns = H.n_sec, n = int(S->ops.size());
   ctq::DevGuard g(S->device);
   S->stats = ctq_skiplist_stats{};
+  S->epoch += 1;
+  ctq::Plan plan;
   std::unordered_set<std::string> used;
   std::vector<int> live;
   std::vector<double> Lq(ns, 0.0);
@@ -594,9 +790,19 @@ extern "C" int ctq_skiplist_evaluate(ctq_skiplist* S, double* log_abs, double* p
         path[i + 1] = q;
       }
       if (!ok || path[n] != q0) continue;
-      const int st = ctq::eval_string(S, q0, path, used, &Lq[q0]);
-      if (st != CTQ_OK) return st;
+      const int st = ctq::plan_string(S, plan, q0, path, used, &Lq[q0]);
+      if (st != CTQ_OK) {  // no cached product may outlive a plan that never ran
+        S->cache.clear();
+        return st;
+      }
       live.push_back(q0);
+    }
+    const int st = ctq::launch_plan(S, plan);
+    plan.keep.clear();  // the buffers' kernels are enqueued: later reuse is ordered after them
+    if (st != CTQ_OK) {
+      cudaStreamSynchronize(S->st);
+      S->cache.clear();
+      return st;
     }
     std::vector<double> res(3 * std::max(ns, 1));
     if (!live.empty() &&

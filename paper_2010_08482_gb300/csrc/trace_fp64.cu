@@ -24,10 +24,13 @@
 //              without lazy evaluation the logarithms of all segments are
 //              taken at the end, lanes over segments.  For short strings the
 //              propagators of the whole string are computed in one dense
-//              pass, once per distinct energy level of each visited sector.
+//              pass, once per distinct energy level of each visited sector,
+//              by the table-driven exponential of exp_tang.cuh, and the
+//              power-of-two rescale enters them by an exponent add.
 #include <algorithm>
 
 #include "device_common.cuh"
+#include "exp_tang.cuh"
 #include "two_float.cuh"
 
 namespace ctq {
@@ -232,7 +235,7 @@ __global__ void __launch_bounds__(512, 1) k_trace(DevModel M, BatchView B, EvalC
     __syncthreads();
     if (tid < 32) chain_log_scale(M, B, cfg, a0, n, q0, t_first, t_last, track, path, opsm, segL, segP, &s_L);
     __syncthreads();
-    for (int j = tid; j < d0; j += nt) p0[j] = exp(-t_first * E0[j]) * exp(-t_last * E0[j]);
+    for (int j = tid; j < d0; j += nt) p0[j] = exp_nonpos(-t_first * E0[j]) * exp_nonpos(-t_last * E0[j]);
     if (PRE) {
       // all propagators of the chain, one per distinct level of each visited
       // sector: flat index j -> (operator i, level l)
@@ -245,7 +248,7 @@ __global__ void __launch_bounds__(512, 1) k_trace(DevModel M, BatchView B, EvalC
         }
         const int q = path[lo + 1];
         const double dt = B.tau[a0 + lo + 1] - B.tau[a0 + lo];
-        pall[j] = exp(-dt * M.lev_E[M.lev_off[q] + (j - poff[lo])]);
+        pall[j] = exp_nonpos(-dt * M.lev_E[M.lev_off[q] + (j - poff[lo])]);
       }
     }
 
@@ -257,7 +260,7 @@ __global__ void __launch_bounds__(512, 1) k_trace(DevModel M, BatchView B, EvalC
     if (!PRE) {
       const double dt = B.tau[a0 + 1] - B.tau[a0];
       const double* Eb = M.E_rel + M.E_off[qb];
-      for (int m = tid; m < M.dims[qb]; m += nt) p[m] = exp(-dt * Eb[m]);
+      for (int m = tid; m < M.dims[qb]; m += nt) p[m] = exp_nonpos(-dt * Eb[m]);
     } else {
       __syncthreads();  // pall complete
       const int* lv = M.lev_idx + M.E_off[qb];
@@ -379,11 +382,11 @@ __global__ void __launch_bounds__(512, 1) k_trace(DevModel M, BatchView B, EvalC
       if (PRE) {
         const double* pi = pall + poff[i];
         const int* lv = M.lev_idx + M.E_off[qb];
-        for (int m = tid; m < db; m += nt) pp[m] = to_prop(pi[lv[m]] * scale, PT());
+        for (int m = tid; m < db; m += nt) pp[m] = to_prop(scale_pow2(pi[lv[m]], -e), PT());
       } else {
         const double dt = B.tau[a0 + i + 1] - B.tau[a0 + i];
         const double* Eb = M.E_rel + M.E_off[qb];
-        for (int m = tid; m < db; m += nt) pp[m] = to_prop(exp(-dt * Eb[m]) * scale, PT());
+        for (int m = tid; m < db; m += nt) pp[m] = to_prop(scale_pow2(exp_nonpos(-dt * Eb[m]), -e), PT());
       }
       __syncthreads();
       // Yn[m][j] = p[m] * sum_k F[m][k] Y[k][j]

@@ -86,6 +86,7 @@ def _load():
         "ctq_strerror": (c_char_p, [c_int]),
         "ctq_last_error_message": (c_char_p, []),
         "ctq_probe_fma_rate": (c_int, [c_int, c_int, c_int, POINTER(c_double)]),
+        "ctq_probe_exp": (c_int, [c_int, c_int, P, P, P]),
         "ctq_tc_gemm_check": (c_int, [c_int, P, P, P, c_int, c_int, c_int]),
         "ctq_big_gemm_check": (c_int, [c_int, P, P, P, c_int, c_int, c_int]),
         "ctq_trace_kernel": (c_int, [P, c_int]),
@@ -117,7 +118,7 @@ _lib = _load()
 EXPORTED = ("ctq_build_impurity", "ctq_load_impurity", "ctq_impurity_info", "ctq_get_sectors",
             "ctq_get_energies", "ctq_get_block", "ctq_workspace_size", "ctq_eval_traces",
             "ctq_launches_per_eval", "ctq_free_impurity", "ctq_strerror", "ctq_last_error_message",
-            "ctq_probe_fma_rate", "ctq_tc_gemm_check", "ctq_big_gemm_check", "ctq_eval_traces_static",
+            "ctq_probe_fma_rate", "ctq_probe_exp", "ctq_tc_gemm_check", "ctq_big_gemm_check", "ctq_eval_traces_static",
             "ctq_trace_kernel", "ctq_density_size", "ctq_density_workspace_size", "ctq_eval_density_matrices",
             "ctq_add_bulla_operators", "ctq_static_ratios", "ctq_static_ratio_workspace_size",
             "ctq_eval_static_ratios", "ctq_skiplist_create", "ctq_skiplist_set", "ctq_skiplist_insert",
@@ -148,10 +149,20 @@ def big_gemm_check(A: np.ndarray, Bm: np.ndarray, precision: int = TF32X3, devic
 
 
 def probe_fma_rate(device: int = 0, kind: int = 0, iters: int = 20000) -> float:
-    """Measured FMA throughput (flop/s) of the FP64 (kind 0) or FP32 (kind 1) pipe."""
+    """Measured multiply-add throughput (flop/s): FP64 FMA (kind 0), FP32 FMA
+    (kind 1) or the FP64 warp-level MMA mma.sync.m8n8k4 (kind 2)."""
     out = c_double()
     _check(_lib.ctq_probe_fma_rate(device, kind, iters, ctypes.byref(out)), "ctq_probe_fma_rate")
     return out.value
+
+
+def probe_exp(x, device: int = 0):
+    """(table exponential of the float64 trace kernel, CUDA exp) of the host
+    values x <= 0, both computed on the device."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    yt, yl = np.empty_like(x), np.empty_like(x)
+    _check(_lib.ctq_probe_exp(device, x.size, _ptr(x), _ptr(yt), _ptr(yl)), "ctq_probe_exp")
+    return yt, yl
 
 
 def lib_path() -> str:
@@ -587,7 +598,8 @@ class DensityEvaluator:
 
 class SkipListStatsC(ctypes.Structure):
     _fields_ = [("products", c_int64), ("leaves", c_int64), ("reused", c_int64), ("cached", c_int64),
-                ("flops", c_double), ("n_ops", c_int), ("n_strings", c_int), ("device_bytes", c_int64)]
+                ("flops", c_double), ("n_ops", c_int), ("n_strings", c_int), ("device_bytes", c_int64),
+                ("launches", c_int64), ("rounds", c_int)]
 
 
 class SkipListTrace:

@@ -65,6 +65,9 @@ def run_moves(m, imp, tau, op, beta, n_moves, seed, oracle_every=1):
             la, ph, st = sl.evaluate()
             products.append(st["products"])
             n_ops.append(len(tau))
+            # one grouped launch per dependency round, plus leaves, bookkeeping words and roots
+            assert st["launches"] <= st["rounds"] + 3, st
+            assert st["products"] == 0 or st["rounds"] >= 1
         la_f, ph_f = fresh_eval(imp, tau, op, beta)
         assert st["n_ops"] == len(tau)
         if k % oracle_every == 0:
