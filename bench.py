@@ -324,7 +324,9 @@ def run_skiplist(args, world, rank, local):
     imp = ctq.build_impurity(mf(), device=local)
     tau, op = (np.asarray(x) for x in batch.chain(0))
     rng = np.random.default_rng(2010084820 + rank)
-    sl = ctq.SkipListTrace(imp, batch.beta, seed=11)
+    if args.precision not in ("fp64", "bf16x3"):
+        raise SystemExit("--estimator skiplist runs its products in fp64 or bf16x3")
+    sl = ctq.SkipListTrace(imp, batch.beta, seed=11, precision=PRECISIONS[args.precision])
     stream = torch.cuda.current_stream()
     s_tab = imp.sectors()[3]
 
@@ -349,7 +351,7 @@ def run_skiplist(args, world, rank, local):
     def fresh(t, o):
         b = w.Batch(beta=batch.beta, offsets=np.array([0, len(t)], np.int32), tau=t, op=o)
         db = ctq.DeviceBatch(b, device=dev)
-        ev = ctq.TraceEvaluator(imp, 1, max(1, len(t)), device=dev)
+        ev = ctq.TraceEvaluator(imp, 1, max(1, len(t)), device=dev, precision=PRECISIONS[args.precision])
         ev(db)  # warm (first-call set-up)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -395,10 +397,18 @@ def run_skiplist(args, world, rank, local):
     fresh_s = 0.5 * (fresh_first[0] + fresh_last[0])
     fp64_peak = ctq.probe_fma_rate(local, 0)
     achieved = sum(flops) / sum(secs) / 1e12
-    line = {"metric": "skip-list incremental local trace: seconds per pair move, FP64, 1xGB300",
+    if args.precision == "fp64":
+        sl_roofline = {"kernel": "k_sl_gemm (float64 SIMT)", "bound": "alu", "achieved": achieved,
+                       "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": achieved / (fp64_peak / 1e12),
+                       "peak_source": "measured FP64 FMA rate (ctq_probe_fma_rate, this run); achieved counts "
+                                      "the products' flops over the whole move time", "traffic": None}
+    else:
+        sl_roofline = dict(roofline("bf16x3", achieved, fp64_peak, None), kernel="k_sl_tc (tcgen05 BF16X3)",
+                           note="achieved counts the products' algorithmic flops over the whole move time")
+    line = {"metric": f"skip-list incremental local trace: seconds per pair move, {args.precision.upper()}, 1xGB300",
             "value": per_move, "unit": "s/move", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * per_move, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
+            "dtype": "f64" if args.precision == "fp64" else DTYPE_TEXT[args.precision], "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT[args.workload] + " (first chain, random pair moves)",
                        "moves": "workloads.pair_move: insert or remove a pair between consecutive operators of "
                                 "one flavour (Pauli-aware), redrawn until some string survives",
@@ -406,12 +416,10 @@ def run_skiplist(args, world, rank, local):
             "products_per_move": statistics.mean(prods),
             "full_products": statistics.mean(full),  # (operators - 1) x surviving strings
             "build": {"seconds": build_s, "products": build_products},
-            "fresh_eval_s": fresh_s, "speedup_vs_fresh_eval": fresh_s / per_move,
+            "fresh_eval_s": fresh_s, "fresh_eval": f"ctq_eval_traces, {args.precision}, the same configuration",
+            "speedup_vs_fresh_eval": fresh_s / per_move,
             "max_rel_diff_vs_fresh": max(diffs) if diffs else None,
-            "roofline": {"kernel": "k_sl_gemm (float64 SIMT)", "bound": "alu", "achieved": achieved,
-                         "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": achieved / (fp64_peak / 1e12),
-                         "peak_source": "measured FP64 FMA rate (ctq_probe_fma_rate, this run); achieved counts "
-                                        "the products' flops over the whole move time", "traffic": None},
+            "roofline": sl_roofline,
             "launches_per_move": statistics.mean(launches), "rounds_per_move": statistics.mean(rounds),
             "gpu_launches": int(sum(launches)), "clocks": clocks.summary()}
     if rank == 0:
@@ -465,7 +473,7 @@ class ClockSampler:
 
 
 KERNEL_SOURCES = {
-    "small": ("trace_fp64.cu", "device_common.cuh", "two_float.cuh"),
+    "small": ("trace_fp64.cu", "device_common.cuh", "two_float.cuh", "exp_tang.cuh"),
     "big": ("trace_big.cu", "big_common.cuh", "tc_ptx.cuh", "device_common.cuh"),
 }
 

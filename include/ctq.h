@@ -346,6 +346,14 @@ int ctq_eval_traces_static(const ctq_impurity* imp, const ctq_batch* batch, cons
  *   host, log|w| (-inf if w = 0) and the phase (re, im) of the raw trace of
  *   the time-ordered product, as ctq_eval_traces does, and, if stats is not
  *   NULL, the work done by this call.  Products no longer used are released.
+ *   CTQ_ERR_TIMEOUT: a tensor-core product gave up one of its bounded waits
+ *   (20 s); no product of that call is kept.
+ * ctq_skiplist_set_precision: CTQ_FP64 (default: float64 SIMT products) or
+ *   CTQ_BF16X3 (products on the tensor cores: each factor scaled to max
+ *   |entry| in [1, 2), split into bf16 hi / lo, hi hi + hi lo + lo hi with
+ *   FP32 accumulation, stored in float64; leaves, exponents and the root
+ *   traces stay float64).  Changing it releases every cached product.
+ *   Errors: CTQ_ERR_ARG, CTQ_ERR_UNSUPPORTED (another precision), CTQ_ERR_NOMEM.
  * Errors of set / insert / remove: CTQ_ERR_ARG (nothing changed).
  */
 typedef struct ctq_skiplist ctq_skiplist;
@@ -366,6 +374,7 @@ int ctq_skiplist_set(ctq_skiplist* sl, int n, const double* tau, const int32_t* 
 int ctq_skiplist_insert(ctq_skiplist* sl, int m, const double* tau, const int32_t* op);
 int ctq_skiplist_remove(ctq_skiplist* sl, int m, const double* tau);
 int ctq_skiplist_evaluate(ctq_skiplist* sl, double* log_abs, double* phase, ctq_skiplist_stats* stats);
+int ctq_skiplist_set_precision(ctq_skiplist* sl, int precision);
 void ctq_skiplist_free(ctq_skiplist* sl);
 
 /*

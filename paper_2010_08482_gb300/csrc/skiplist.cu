@@ -42,15 +42,16 @@
 #include <cstring>
 #include <map>
 #include <memory>
-#include <string>
 #include <unordered_map>
-#include <unordered_set>
 #include <vector>
 
 #include "ctq_internal.h"
+#include "tc_ptx.cuh"
 
 namespace ctq {
 namespace {
+
+using namespace ptx;
 
 constexpr int SL_MAX_LEVEL = 24;
 constexpr int GK = 16;            // K chunk of the product tiles
@@ -147,13 +148,13 @@ __global__ void k_sl_leaves(const double* blk, const SlLeaf* tasks, int n) {
   atomic_max_abs(T.w, mx);
 }
 
-// Products, TILE x TILE outputs per CTA, 4 x 4 per thread.  Real: R (M x K),
+// Products, TILE x TILE outputs per CTA, RR x RR per thread.  Real: R (M x K),
 // L (K x N), C (M x N), row-major.  Complex ([Re | Im] rows): the real GEMM
 // of [Rr | Ri] (M x 2K) with [[Lr, Li], [-Li, Lr]] (2K x 2N) gives
 // [Cr | Ci] (M x 2N).
-template <int TILE>
-__global__ void __launch_bounds__((TILE / 4) * (TILE / 4)) k_sl_gemm(const SlProd* tasks, int n) {
-  constexpr int NT = (TILE / 4) * (TILE / 4), TPR = TILE / 4;
+template <int TILE, int RR>
+__global__ void __launch_bounds__((TILE / RR) * (TILE / RR)) k_sl_gemm(const SlProd* tasks, int n) {
+  constexpr int NT = (TILE / RR) * (TILE / RR), TPR = TILE / RR;
   __shared__ double As[GK][TILE + 1];
   __shared__ double Bs[GK][TILE + 1];
   const SlProd P = tasks[find_task(tasks, n, blockIdx.x)];
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__((TILE / 4) * (TILE / 4)) k_sl_gemm(const SlPro
   const int M = P.M, K = P.K, N = P.N;
   const int Kp = P.cplx ? 2 * K : K, Np = P.cplx ? 2 * N : N;
   const int tx = threadIdx.x % TPR, ty = threadIdx.x / TPR;
-  double acc[4][4] = {};
+  double acc[RR][RR] = {};
   for (int k0 = 0; k0 < Kp; k0 += GK) {
     for (int e = threadIdx.x; e < TILE * GK; e += NT) {
       const int r = e / GK, k = e - r * GK;  // A: row r, column k0 + k
@@ -190,26 +191,26 @@ __global__ void __launch_bounds__((TILE / 4) * (TILE / 4)) k_sl_gemm(const SlPro
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < GK; ++k) {
-      double a[4], b[4];
+      double a[RR], b[RR];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[k][ty * 4 + i];
+      for (int i = 0; i < RR; ++i) a[i] = As[k][ty * RR + i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx * 4 + j];
+      for (int j = 0; j < RR; ++j) b[j] = Bs[k][tx * RR + j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < RR; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < RR; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
   double mx = 0.0;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int r = row0 + ty * 4 + i;
+  for (int i = 0; i < RR; ++i) {
+    const int r = row0 + ty * RR + i;
     if (r >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = col0 + tx * 4 + j;
+    for (int j = 0; j < RR; ++j) {
+      const int c = col0 + tx * RR + j;
       if (c < Np) {
         P.C[size_t(r) * Np + c] = acc[i][j];
         mx = fmax(mx, fabs(acc[i][j]));
@@ -258,6 +259,203 @@ __global__ void k_sl_roots(const SlRoot* tasks) {
   }
 }
 
+// ------------------------------------------------ tensor-core products
+// CTQ_BF16X3 products: each factor is scaled by its power of two, split
+// into bf16 hi / lo planes and laid out as K-major tiles of 8 x 16-byte core
+// matrices (k_sl_fmt); then C = A B^T runs on 128 x 256 tiles (k_sl_tc):
+// A = the left factor R as stored (M x K', complex rows [Re | Im]), B = the
+// rows of the real embedding of the right factor transposed (N' x K'),
+// chunks of 64 K elements staged by bulk copies through two 96 KB stages,
+// three MMAs per 16 K (hi hi + hi lo + lo hi) into one FP32 accumulator of
+// 256 tensor-memory columns, drained to the float64 product with its max.
+constexpr int TBM = 128, TBN = 256, TKE = 64;                      // tile rows, columns, K per chunk
+constexpr uint32_t TA_BYTES = TBM * 128, TB_BYTES = TBN * 128;     // one plane of a staged chunk
+constexpr uint32_t TSTAGE = 2 * (TA_BYTES + TB_BYTES);             // hi and lo planes of A and B
+constexpr int TC_SL_THREADS = 128;                                 // one thread per accumulator row
+constexpr int FMT_CHUNK = 2048;                                    // operand elements per format CTA
+constexpr uint64_t SL_TC_TIMEOUT_NS = 20000000000ull;              // bound of every wait (20 s)
+
+// Element (r, k) of an operand stored as tiles of rpt rows x 64 K elements:
+// tile (r / rpt, k / 64) at ((r / rpt) nkc + k / 64) rpt 64, core matrix
+// (k % 64 / 8, r % rpt / 8) at (k % 64 / 8 * rpt / 8 + r % rpt / 8) 64,
+// element (r % 8) 8 + k % 8.
+__device__ __forceinline__ size_t tc_off(int r, int k, int rpt, int nkc) {
+  const int rt = r / rpt, rr = r - rt * rpt, kc = k >> 6, kk = k & 63;
+  return (size_t(rt) * nkc + kc) * size_t(rpt) * TKE + size_t((kk >> 3) * (rpt >> 3) + (rr >> 3)) * 64 +
+         (rr & 7) * 8 + (kk & 7);
+}
+
+// One operand to format.  mode 0: A = the stored rows of R (rows x kp);
+// mode 1: B[n][k] = L_emb[k][n], L_emb the real embedding of L (K x N
+// complex: [[Lr, Li], [-Li, Lr]], stored rows [Lr | Li]).
+struct SlFmt {
+  const double* src;
+  const unsigned long long* w;
+  uint16_t* hi;
+  uint16_t* lo;
+  int rows, kp, rows_pad, kp_pad, mode, K, N, cplx, rpt, tile0;
+};
+// One product on the tensor cores: tiled operands, output and records.
+struct SlTc {
+  const uint16_t* Ah;
+  const uint16_t* Al;
+  const uint16_t* Bh;
+  const uint16_t* Bl;
+  double* C;
+  const unsigned long long* wR;
+  const unsigned long long* wL;
+  unsigned long long* wC;
+  int M, Np, nkc, tiles_n, tile0;
+};
+
+__global__ void k_sl_fmt(const SlFmt* tasks, int n) {
+  const SlFmt T = tasks[find_task(tasks, n, blockIdx.x)];
+  int e_unused;
+  const double sc = norm_of(T.w, &e_unused);
+  const long long total = (long long)T.rows_pad * T.kp_pad;
+  const long long e0 = (long long)(blockIdx.x - T.tile0) * FMT_CHUNK;
+  const long long e1 = e0 + FMT_CHUNK < total ? e0 + FMT_CHUNK : total;
+  const int nkc = T.kp_pad / TKE;
+  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    int r, k;
+    double v = 0.0;
+    if (T.mode == 0) {  // consecutive threads: consecutive k of a row of R
+      r = int(e / T.kp_pad);
+      k = int(e - (long long)r * T.kp_pad);
+      if (r < T.rows && k < T.kp) v = T.src[size_t(r) * T.kp + k];
+    } else {  // consecutive threads: consecutive n of a row of L
+      k = int(e / T.rows_pad);
+      r = int(e - (long long)k * T.rows_pad);
+      if (r < T.rows && k < T.kp) {
+        const int Np = T.cplx ? 2 * T.N : T.N;
+        if (!T.cplx || k < T.K) {
+          v = T.src[size_t(k) * Np + r];
+        } else {
+          const int kk = k - T.K;
+          v = (r < T.N) ? -T.src[size_t(kk) * Np + T.N + r] : T.src[size_t(kk) * Np + (r - T.N)];
+        }
+      }
+    }
+    const float x = float(v * sc);
+    const uint32_t h = bf16_bits(x);
+    const size_t o = tc_off(r, k, T.rpt, nkc);
+    T.hi[o] = uint16_t(h);
+    T.lo[o] = uint16_t(bf16_bits(x - bf16_val(h)));
+  }
+}
+
+__global__ void __launch_bounds__(TC_SL_THREADS, 1)
+    k_sl_tc(const SlTc* tasks, int n, uint64_t timeout_ns, int* status) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ uint64_t full[2], empty[2], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int fail;
+  const SlTc T = tasks[find_task(tasks, n, blockIdx.x)];
+  const int local = blockIdx.x - T.tile0;
+  const int mt = local / T.tiles_n, nt = local - mt * T.tiles_n;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(&done, 1);
+    fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, TBN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tD = tmem_base;
+  int er, el;
+  const double sR = norm_of(T.wR, &er), sL = norm_of(T.wL, &el);
+  if (local == 0 && tid == 0) {
+    const long long eR = reinterpret_cast<const long long*>(T.wR)[1], eL = reinterpret_cast<const long long*>(T.wL)[1];
+    reinterpret_cast<long long*>(T.wC)[1] = (sR > 0.0 && sL > 0.0) ? eR + er + eL + el : EXP_DEAD;
+  }
+  if (tid == 0) {
+    const int nkc = T.nkc;
+    const size_t a_tile = size_t(TBM) * TKE, b_tile = size_t(TBN) * TKE;  // elements of one chunk
+    auto issue = [&](int kc) {
+      unsigned char* base = sm + (kc & 1) * TSTAGE;
+      const size_t ao = (size_t(mt) * nkc + kc) * a_tile, bo = (size_t(nt) * nkc + kc) * b_tile;
+      mbar_arrive_expect_tx(&full[kc & 1], TSTAGE);
+      bulk_g2s(base, T.Ah + ao, TA_BYTES, &full[kc & 1]);
+      bulk_g2s(base + TA_BYTES, T.Bh + bo, TB_BYTES, &full[kc & 1]);
+      bulk_g2s(base + TA_BYTES + TB_BYTES, T.Al + ao, TA_BYTES, &full[kc & 1]);
+      bulk_g2s(base + 2 * TA_BYTES + TB_BYTES, T.Bl + bo, TB_BYTES, &full[kc & 1]);
+    };
+    constexpr uint32_t LBO_A = (TBM / 8) * 128, LBO_B = (TBN / 8) * 128;
+    const uint32_t idesc = idesc_bf16(TBM, TBN);
+    issue(0);
+    if (nkc > 1) issue(1);
+    int issued = nkc > 1 ? 2 : 1, kc = 0;
+    bool ok = true;
+    for (; kc < nkc; ++kc) {
+      const int st = kc & 1;
+      ok = mbar_wait(&full[st], uint32_t((kc >> 1) & 1), timeout_ns);
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t sa = smem_u32(sm + st * TSTAGE), sbh = sa + TA_BYTES, sal = sbh + TB_BYTES, sbl = sal + TA_BYTES;
+      for (int kk = 0; kk < TKE / 16; ++kk) {  // 16 K elements (32 bytes) per MMA
+        const uint64_t dah = sdesc(sa + kk * 2 * LBO_A, LBO_A, 128), dbh = sdesc(sbh + kk * 2 * LBO_B, LBO_B, 128);
+        mma_bf16_ss(tD, dah, dbh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+        mma_bf16_ss(tD, dah, sdesc(sbl + kk * 2 * LBO_B, LBO_B, 128), idesc, 1u);
+        mma_bf16_ss(tD, sdesc(sal + kk * 2 * LBO_A, LBO_A, 128), dbh, idesc, 1u);
+      }
+      mma_commit(&empty[st]);
+      if (kc >= 1 && kc + 1 < nkc) {  // chunk kc - 1's stage takes chunk kc + 1 once its MMAs are done
+        ok = mbar_wait(&empty[st ^ 1], uint32_t(((kc - 1) >> 1) & 1), timeout_ns);
+        if (!ok) break;
+        issue(kc + 1);
+        issued = kc + 2;
+      }
+    }
+    if (ok) {
+      mma_commit(&done);
+    } else {
+      fail = 1;
+      atomicExch(status, CTQ_ERR_TIMEOUT);
+      // copies still in flight land in this CTA's shared memory: wait for them (bounded)
+      for (int j = kc; j < issued; ++j) mbar_wait(&full[j & 1], uint32_t((j >> 1) & 1), timeout_ns);
+    }
+  }
+  __syncthreads();
+  const bool ok = !fail && mbar_wait(&done, 0, timeout_ns);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) atomicExch(status, CTQ_ERR_TIMEOUT);
+  } else {
+    tc_fence_after();
+    const int r = mt * TBM + tid;  // accumulator row = lane of this thread's warp quarter
+    const uint32_t lane_off = uint32_t(32 * warp) << 16;
+    double mx = 0.0;
+    for (int c0 = 0; c0 < TBN; c0 += 16) {
+      uint32_t v[16];
+      tmem_ld16(tD + lane_off + uint32_t(c0), v);
+      tmem_wait_ld();
+      const int cb = nt * TBN + c0;
+      if (r < T.M) {
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          if (cb + t < T.Np) {
+            const double x = double(__uint_as_float(v[t]));
+            T.C[size_t(r) * T.Np + cb + t] = x;
+            mx = fmax(mx, fabs(x));
+          }
+        }
+      }
+    }
+    atomic_max_abs(T.wC, mx);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tD, TBN);
+  }
+}
+
 // ---------------------------------------------------------------- host
 
 uint64_t mix64(uint64_t x) {  // splitmix64 finaliser
@@ -266,6 +464,16 @@ uint64_t mix64(uint64_t x) {  // splitmix64 finaliser
   x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
   return x ^ (x >> 31);
 }
+
+// 128-bit cache key of a leaf or a segment product (two independent
+// 64-bit hashes; a collision needs both to agree).
+struct Key {
+  uint64_t a, b;
+  bool operator==(const Key& o) const { return a == o.a && b == o.b; }
+};
+struct KeyHash {
+  size_t operator()(const Key& k) const { return size_t(k.a ^ (k.b * 0x9e3779b97f4a7c15ull)); }
+};
 
 // A cached product: device matrix (rows x cols doubles, complex rows as
 // [Re | Im]), its max word and exponent on the device, its log scale on the host.
@@ -277,6 +485,7 @@ struct Buf {
   double L = 0.0;
   uint64_t epoch = 0;  // the evaluation that planned it
   int round = 0;       // its launch round in that evaluation (leaves 0)
+  uint64_t used = 0;   // the last evaluation whose configuration needed it
 };
 
 class Pool {
@@ -352,7 +561,7 @@ struct ctq_skiplist {
   uint64_t rng = 0, next_id = 1;
   std::vector<ctq::Op> ops;
   ctq::Pool pool;
-  std::unordered_map<std::string, std::shared_ptr<ctq::Buf>> cache;
+  std::unordered_map<ctq::Key, std::shared_ptr<ctq::Buf>, ctq::KeyHash> cache;
   double* d_res = nullptr;  // [3 n_sec]: trace re, im, exponent bits per q0
   ctq_skiplist_stats stats{};
   uint64_t epoch = 0;
@@ -360,6 +569,10 @@ struct ctq_skiplist {
   unsigned char* h_tab = nullptr;  // task tables: pinned host staging and device copy
   unsigned char* d_tab = nullptr;
   size_t tab_cap = 0;
+  int prec = CTQ_FP64;             // products: CTQ_FP64 (SIMT) or CTQ_BF16X3 (tensor cores)
+  unsigned char* d_fmt = nullptr;  // tiled bf16 operands of one round (CTQ_BF16X3)
+  size_t fmt_cap = 0;
+  int* d_status = nullptr;         // CTQ_ERR_TIMEOUT from a tensor-core product
 };
 
 namespace ctq {
@@ -452,37 +665,30 @@ std::shared_ptr<Buf> product(ctq_skiplist* S, Plan& P, const std::shared_ptr<Buf
   return b;
 }
 
-std::string leaf_key(const Op& o, int q_in, double dt) {
-  std::string k(1, 'L');
-  k.append(reinterpret_cast<const char*>(&o.id), 8);
-  k.append(reinterpret_cast<const char*>(&q_in), 4);
-  k.append(reinterpret_cast<const char*>(&dt), 8);
-  return k;
+Key leaf_key(const Op& o, int q_in, double dt) {
+  uint64_t t;
+  std::memcpy(&t, &dt, 8);
+  return Key{mix64(o.id * 0x100000001b3ull + uint64_t(q_in)), mix64(t ^ mix64(o.id ^ 0x5bd1e995ull)) | 1ull};
 }
 
 // A segment's key depends only on its factors' keys (the same factors give
-// the same product at any level).
-std::string seg_key(const std::vector<const std::string*>& kids) {
-  uint64_t h = 0x243f6a8885a308d3ull;
-  for (const std::string* k : kids) {
-    uint64_t x = 1469598103934665603ull;
-    for (unsigned char c : *k) x = (x ^ c) * 1099511628211ull;
-    h = mix64(h ^ x);
+// the same product at any level); leaf keys have the low bit of b set,
+// segment keys clear.
+Key seg_key(const Key* kids, int n) {
+  uint64_t h1 = 0x243f6a8885a308d3ull, h2 = 0x13198a2e03707344ull ^ uint64_t(n);
+  for (int i = 0; i < n; ++i) {
+    h1 = mix64(h1 ^ kids[i].a) + kids[i].b;
+    h2 = mix64(h2 + kids[i].b) ^ (kids[i].a * 0xff51afd7ed558ccdull);
   }
-  std::string k(1, 'S');
-  k.append(reinterpret_cast<const char*>(&h), 8);
-  const uint64_t n = kids.size();
-  k.append(reinterpret_cast<const char*>(&n), 8);
-  return k;
+  return Key{mix64(h1), mix64(h2) & ~1ull};
 }
 
 // Plans (or finds in the cache) every segment product of the string that
 // starts in sector q0 and its root trace into d_res[3 q0 ..].  Returns the
 // root's log scale in *L_root.
-int plan_string(ctq_skiplist* S, Plan& P, int q0, const std::vector<int>& path,
-                std::unordered_set<std::string>& used, double* L_root) {
+int plan_string(ctq_skiplist* S, Plan& P, int q0, const std::vector<int>& path, double* L_root) {
   const int n = int(S->ops.size());
-  std::vector<std::string> keys(n);
+  std::vector<Key> keys(n);
   std::vector<std::shared_ptr<Buf>> bufs(n);
   int st = CTQ_OK;
   for (int i = 0; i < n; ++i) {
@@ -497,7 +703,7 @@ int plan_string(ctq_skiplist* S, Plan& P, int q0, const std::vector<int>& path,
       if (st != CTQ_OK) return st;
       S->cache[keys[i]] = bufs[i];
     }
-    used.insert(keys[i]);
+    bufs[i]->used = S->epoch;
   }
   // levels: segment starts are index 0 and every operator with h > level
   std::vector<int> starts(n);
@@ -506,7 +712,7 @@ int plan_string(ctq_skiplist* S, Plan& P, int q0, const std::vector<int>& path,
     std::vector<int> ns_;
     for (size_t j = 0; j < starts.size(); ++j)
       if (j == 0 || S->ops[starts[j]].h > level) ns_.push_back(int(j));  // indices into starts
-    std::vector<std::string> nkeys;
+    std::vector<Key> nkeys;
     std::vector<std::shared_ptr<Buf>> nbufs;
     std::vector<int> nstarts;
     for (size_t g = 0; g < ns_.size(); ++g) {
@@ -517,9 +723,7 @@ int plan_string(ctq_skiplist* S, Plan& P, int q0, const std::vector<int>& path,
         nbufs.push_back(bufs[a]);
         continue;
       }
-      std::vector<const std::string*> kids;
-      for (int j = a; j < b; ++j) kids.push_back(&keys[j]);
-      std::string k = seg_key(kids);
+      const Key k = seg_key(&keys[a], b - a);
       auto it = S->cache.find(k);
       std::shared_ptr<Buf> buf;
       if (it != S->cache.end()) {
@@ -531,8 +735,8 @@ int plan_string(ctq_skiplist* S, Plan& P, int q0, const std::vector<int>& path,
         if (st != CTQ_OK) return st;
         S->cache[k] = buf;
       }
-      used.insert(k);
-      nkeys.push_back(std::move(k));
+      buf->used = S->epoch;
+      nkeys.push_back(k);
       nbufs.push_back(buf);
     }
     keys.swap(nkeys);
@@ -560,21 +764,60 @@ size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 // Copies the planned tables to the device (one copy) and enqueues the
 // zeroing, leaf, per-round product and root kernels.
 int launch_plan(ctq_skiplist* S, Plan& P) {
-  // tile offsets: leaves in chunks, products in tiles (32 x 32 when a round
-  // would not fill two CTAs per SM with 64 x 64 tiles)
+  // tile offsets: leaves in chunks, products in tiles (the largest of
+  // 64 x 64, 32 x 32 and 16 x 16 that gives the round a CTA per SM)
   int leaf_tiles = 0;
   for (SlLeaf& t : P.leaves) {
     t.tile0 = leaf_tiles;
     leaf_tiles += int((int64_t(t.d_out) * t.d_in + LEAF_CHUNK - 1) / LEAF_CHUNK);
   }
   std::vector<int> tile(P.rounds.size()), n_tiles(P.rounds.size());
-  for (size_t r = 0; r < P.rounds.size(); ++r) {
-    long long t64 = 0;
+  const bool tc = S->prec == CTQ_BF16X3;
+  // tensor-core rounds: two operands to format and the 128 x 256 tiles of
+  // every product, operands in the round's workspace (reused by the next round)
+  std::vector<std::vector<SlFmt>> fmts(tc ? P.rounds.size() : 0);
+  std::vector<std::vector<SlTc>> tcs(tc ? P.rounds.size() : 0);
+  std::vector<int> fmt_tiles(tc ? P.rounds.size() : 0);
+  size_t fmt_need = 0;
+  for (size_t r = 0; tc && r < P.rounds.size(); ++r) {
+    size_t wo = 0;  // bytes into the workspace
+    int ft = 0, tt = 0;
     for (const SlProd& t : P.rounds[r]) {
-      const int np = t.cplx ? 2 * t.N : t.N;
-      t64 += (long long)((t.M + 63) / 64) * ((np + 63) / 64);
+      const int Kp = t.cplx ? 2 * t.K : t.K, Np = t.cplx ? 2 * t.N : t.N;
+      const int Kpad = (Kp + TKE - 1) / TKE * TKE, Mpad = (t.M + TBM - 1) / TBM * TBM,
+                Npad = (Np + TBN - 1) / TBN * TBN;
+      // byte offsets into the workspace, made pointers once it is allocated
+      auto at = [](size_t bytes) { return reinterpret_cast<uint16_t*>(static_cast<uintptr_t>(bytes)); };
+      const size_t a_el = size_t(Mpad) * Kpad, b_el = size_t(Npad) * Kpad;
+      SlFmt fa{t.R, t.wR, at(wo), at(wo + 2 * a_el), t.M, Kp, Mpad, Kpad, 0, t.K, t.N, t.cplx, TBM, ft};
+      ft += int((int64_t(a_el) + FMT_CHUNK - 1) / FMT_CHUNK);
+      SlFmt fb{t.L, t.wL, at(wo + 4 * a_el), at(wo + 4 * a_el + 2 * b_el), Np, Kp, Npad, Kpad, 1, t.K, t.N, t.cplx,
+               TBN, ft};
+      ft += int((int64_t(b_el) + FMT_CHUNK - 1) / FMT_CHUNK);
+      SlTc g{fa.hi, fa.lo, fb.hi, fb.lo, t.C, t.wR, t.wL, t.wC, t.M, Np, Kpad / TKE, Npad / TBN, tt};
+      tt += (Mpad / TBM) * (Npad / TBN);
+      wo += 2 * (2 * a_el + 2 * b_el);
+      fmts[r].push_back(fa);
+      fmts[r].push_back(fb);
+      tcs[r].push_back(g);
     }
-    tile[r] = t64 < 2LL * S->num_sms ? 32 : 64;
+    fmt_tiles[r] = ft;
+    n_tiles[r] = tt;
+    fmt_need = std::max(fmt_need, wo);
+  }
+  for (size_t r = 0; !tc && r < P.rounds.size(); ++r) {
+    tile[r] = 16;
+    for (int T : {64, 32}) {
+      long long nt = 0;
+      for (const SlProd& t : P.rounds[r]) {
+        const int np = t.cplx ? 2 * t.N : t.N;
+        nt += (long long)((t.M + T - 1) / T) * ((np + T - 1) / T);
+      }
+      if (nt >= S->num_sms) {
+        tile[r] = T;
+        break;
+      }
+    }
     int acc = 0;
     for (SlProd& t : P.rounds[r]) {
       const int np = t.cplx ? 2 * t.N : t.N;
@@ -590,10 +833,17 @@ int launch_plan(ctq_skiplist* S, Plan& P) {
   off = align16(off + P.zero.size() * sizeof(unsigned long long*));
   const size_t o_leaf = off;
   off = align16(off + P.leaves.size() * sizeof(SlLeaf));
-  std::vector<size_t> o_round(P.rounds.size());
+  std::vector<size_t> o_round(P.rounds.size()), o_fmt(P.rounds.size());
   for (size_t r = 0; r < P.rounds.size(); ++r) {
-    o_round[r] = off;
-    off = align16(off + P.rounds[r].size() * sizeof(SlProd));
+    if (tc) {
+      o_fmt[r] = off;
+      off = align16(off + fmts[r].size() * sizeof(SlFmt));
+      o_round[r] = off;
+      off = align16(off + tcs[r].size() * sizeof(SlTc));
+    } else {
+      o_round[r] = off;
+      off = align16(off + P.rounds[r].size() * sizeof(SlProd));
+    }
   }
   const size_t o_root = off;
   off = align16(off + P.roots.size() * sizeof(SlRoot));
@@ -610,10 +860,41 @@ int launch_plan(ctq_skiplist* S, Plan& P) {
     if (cudaMalloc(&S->d_tab, cap) != cudaSuccess) return CTQ_ERR_NOMEM;
     S->tab_cap = cap;
   }
+  if (tc && fmt_need > S->fmt_cap) {  // the stream is idle here (the previous evaluation synchronised)
+    if (S->d_fmt) cudaFree(S->d_fmt);
+    S->d_fmt = nullptr;
+    S->fmt_cap = 0;
+    if (cudaMalloc(&S->d_fmt, fmt_need) != cudaSuccess) return CTQ_ERR_NOMEM;
+    S->fmt_cap = fmt_need;
+  }
+  if (tc) {  // the operand offsets become pointers into the workspace
+    const uintptr_t shift = reinterpret_cast<uintptr_t>(S->d_fmt);
+    auto rebase = [shift](const uint16_t* p) {
+      return reinterpret_cast<uint16_t*>(reinterpret_cast<uintptr_t>(p) + shift);
+    };
+    for (size_t r = 0; r < P.rounds.size(); ++r) {
+      for (SlFmt& f : fmts[r]) {
+        f.hi = rebase(f.hi);
+        f.lo = rebase(f.lo);
+      }
+      for (SlTc& g : tcs[r]) {
+        g.Ah = rebase(g.Ah);
+        g.Al = rebase(g.Al);
+        g.Bh = rebase(g.Bh);
+        g.Bl = rebase(g.Bl);
+      }
+    }
+  }
   std::memcpy(S->h_tab + o_zero, P.zero.data(), P.zero.size() * sizeof(unsigned long long*));
   std::memcpy(S->h_tab + o_leaf, P.leaves.data(), P.leaves.size() * sizeof(SlLeaf));
-  for (size_t r = 0; r < P.rounds.size(); ++r)
-    std::memcpy(S->h_tab + o_round[r], P.rounds[r].data(), P.rounds[r].size() * sizeof(SlProd));
+  for (size_t r = 0; r < P.rounds.size(); ++r) {
+    if (tc) {
+      std::memcpy(S->h_tab + o_fmt[r], fmts[r].data(), fmts[r].size() * sizeof(SlFmt));
+      std::memcpy(S->h_tab + o_round[r], tcs[r].data(), tcs[r].size() * sizeof(SlTc));
+    } else {
+      std::memcpy(S->h_tab + o_round[r], P.rounds[r].data(), P.rounds[r].size() * sizeof(SlProd));
+    }
+  }
   std::memcpy(S->h_tab + o_root, P.roots.data(), P.roots.size() * sizeof(SlRoot));
   if (cudaMemcpyAsync(S->d_tab, S->h_tab, off, cudaMemcpyHostToDevice, S->st) != cudaSuccess) return CTQ_ERR_CUDA;
   int launches = 0;
@@ -628,12 +909,21 @@ int launch_plan(ctq_skiplist* S, Plan& P) {
                                                 int(P.leaves.size()));
     ++launches;
   }
-  for (size_t r = 0; r < P.rounds.size(); ++r) {
+  for (size_t r = 0; tc && r < P.rounds.size(); ++r) {
+    if (P.rounds[r].empty()) continue;
+    k_sl_fmt<<<fmt_tiles[r], 256, 0, S->st>>>(reinterpret_cast<const SlFmt*>(S->d_tab + o_fmt[r]),
+                                              int(fmts[r].size()));
+    k_sl_tc<<<n_tiles[r], TC_SL_THREADS, TSTAGE * 2, S->st>>>(
+        reinterpret_cast<const SlTc*>(S->d_tab + o_round[r]), int(tcs[r].size()), SL_TC_TIMEOUT_NS, S->d_status);
+    launches += 2;
+  }
+  for (size_t r = 0; !tc && r < P.rounds.size(); ++r) {
     if (P.rounds[r].empty()) continue;
     const SlProd* t = reinterpret_cast<const SlProd*>(S->d_tab + o_round[r]);
     const int n = int(P.rounds[r].size());
-    if (tile[r] == 32) k_sl_gemm<32><<<n_tiles[r], 64, 0, S->st>>>(t, n);
-    else k_sl_gemm<64><<<n_tiles[r], 256, 0, S->st>>>(t, n);
+    if (tile[r] == 16) k_sl_gemm<16, 2><<<n_tiles[r], 64, 0, S->st>>>(t, n);
+    else if (tile[r] == 32) k_sl_gemm<32, 4><<<n_tiles[r], 64, 0, S->st>>>(t, n);
+    else k_sl_gemm<64, 4><<<n_tiles[r], 256, 0, S->st>>>(t, n);
     ++launches;
   }
   if (!P.roots.empty()) {
@@ -693,6 +983,26 @@ extern "C" int ctq_skiplist_create(const ctq_impurity* imp, double beta, uint64_
   return CTQ_OK;
 }
 
+extern "C" int ctq_skiplist_set_precision(ctq_skiplist* S, int precision) {
+  if (!S) return CTQ_ERR_ARG;
+  if (precision != CTQ_FP64 && precision != CTQ_BF16X3) {
+    ctq::set_last_error("the skip list's products run in CTQ_FP64 or CTQ_BF16X3");
+    return CTQ_ERR_UNSUPPORTED;
+  }
+  if (precision == S->prec) return CTQ_OK;
+  ctq::DevGuard g(S->device);
+  if (precision == CTQ_BF16X3) {
+    if (!S->d_status && cudaMalloc(&S->d_status, sizeof(int)) != cudaSuccess) return CTQ_ERR_NOMEM;
+    if (cudaFuncSetAttribute(ctq::k_sl_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(2 * ctq::TSTAGE)) !=
+        cudaSuccess)
+      return CTQ_ERR_CUDA;
+  }
+  cudaStreamSynchronize(S->st);
+  S->cache.clear();  // products of the other precision are not reused
+  S->prec = precision;
+  return CTQ_OK;
+}
+
 extern "C" void ctq_skiplist_free(ctq_skiplist* S) {
   if (!S) return;
   {
@@ -703,6 +1013,8 @@ extern "C" void ctq_skiplist_free(ctq_skiplist* S) {
     cudaFree(S->d_res);
     if (S->h_tab) cudaFreeHost(S->h_tab);
     if (S->d_tab) cudaFree(S->d_tab);
+    if (S->d_fmt) cudaFree(S->d_fmt);
+    if (S->d_status) cudaFree(S->d_status);
   }
   delete S;
 }
@@ -767,7 +1079,6 @@ extern "C" int ctq_skiplist_evaluate(ctq_skiplist* S, double* log_abs, double* p
   S->stats = ctq_skiplist_stats{};
   S->epoch += 1;
   ctq::Plan plan;
-  std::unordered_set<std::string> used;
   std::vector<int> live;
   std::vector<double> Lq(ns, 0.0);
   double lm = -INFINITY;
@@ -790,13 +1101,15 @@ extern "C" int ctq_skiplist_evaluate(ctq_skiplist* S, double* log_abs, double* p
         path[i + 1] = q;
       }
       if (!ok || path[n] != q0) continue;
-      const int st = ctq::plan_string(S, plan, q0, path, used, &Lq[q0]);
+      const int st = ctq::plan_string(S, plan, q0, path, &Lq[q0]);
       if (st != CTQ_OK) {  // no cached product may outlive a plan that never ran
         S->cache.clear();
         return st;
       }
       live.push_back(q0);
     }
+    const bool tc = S->prec == CTQ_BF16X3;
+    if (tc && cudaMemsetAsync(S->d_status, 0, sizeof(int), S->st) != cudaSuccess) return CTQ_ERR_CUDA;
     const int st = ctq::launch_plan(S, plan);
     plan.keep.clear();  // the buffers' kernels are enqueued: later reuse is ordered after them
     if (st != CTQ_OK) {
@@ -805,10 +1118,17 @@ extern "C" int ctq_skiplist_evaluate(ctq_skiplist* S, double* log_abs, double* p
       return st;
     }
     std::vector<double> res(3 * std::max(ns, 1));
+    int tc_status = 0;
     if (!live.empty() &&
         cudaMemcpyAsync(res.data(), S->d_res, sizeof(double) * 3 * ns, cudaMemcpyDeviceToHost, S->st) != cudaSuccess)
       return CTQ_ERR_CUDA;
+    if (tc && cudaMemcpyAsync(&tc_status, S->d_status, sizeof(int), cudaMemcpyDeviceToHost, S->st) != cudaSuccess)
+      return CTQ_ERR_CUDA;
     if (cudaStreamSynchronize(S->st) != cudaSuccess) return CTQ_ERR_CUDA;
+    if (tc_status != 0) {  // a product gave up waiting: none of this evaluation's products is kept
+      S->cache.clear();
+      return CTQ_ERR_TIMEOUT;
+    }
     for (int q0 : live) {
       long long e;
       std::memcpy(&e, &res[3 * q0 + 2], 8);
@@ -829,7 +1149,7 @@ extern "C" int ctq_skiplist_evaluate(ctq_skiplist* S, double* log_abs, double* p
   }
   // drop every cached product the current configuration no longer uses
   for (auto it = S->cache.begin(); it != S->cache.end();)
-    it = used.count(it->first) ? std::next(it) : S->cache.erase(it);
+    it = it->second->used == S->epoch ? std::next(it) : S->cache.erase(it);
   const double a = std::hypot(acc_re, acc_im);
   if (!(a > 0.0) || lm == -INFINITY) {
     *log_abs = -INFINITY;

@@ -105,6 +105,7 @@ def _load():
         "ctq_skiplist_insert": (c_int, [P, c_int, P, P]),
         "ctq_skiplist_remove": (c_int, [P, c_int, P]),
         "ctq_skiplist_evaluate": (c_int, [P, POINTER(c_double), P, P]),
+        "ctq_skiplist_set_precision": (c_int, [P, c_int]),
         "ctq_skiplist_free": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -122,7 +123,7 @@ EXPORTED = ("ctq_build_impurity", "ctq_load_impurity", "ctq_impurity_info", "ctq
             "ctq_trace_kernel", "ctq_density_size", "ctq_density_workspace_size", "ctq_eval_density_matrices",
             "ctq_add_bulla_operators", "ctq_static_ratios", "ctq_static_ratio_workspace_size",
             "ctq_eval_static_ratios", "ctq_skiplist_create", "ctq_skiplist_set", "ctq_skiplist_insert",
-            "ctq_skiplist_remove", "ctq_skiplist_evaluate", "ctq_skiplist_free")
+            "ctq_skiplist_remove", "ctq_skiplist_evaluate", "ctq_skiplist_set_precision", "ctq_skiplist_free")
 
 # Size of the library-owned scratch used by eval_traces_static (ctq.h).
 STATIC_SCRATCH_BYTES = 32 << 20
@@ -607,7 +608,7 @@ class SkipListTrace:
     list of cached segment products, updated by inserting and removing
     operators (see ctq.h).  Host arrays in, host results out."""
 
-    def __init__(self, imp: Impurity, beta: float, seed: int = 0, stream=None):
+    def __init__(self, imp: Impurity, beta: float, seed: int = 0, stream=None, precision=FP64):
         import torch
         self.imp = imp
         s = torch.cuda.current_stream() if stream is None else stream
@@ -616,6 +617,12 @@ class SkipListTrace:
         _check(_lib.ctq_skiplist_create(imp.handle, float(beta), ctypes.c_uint64(seed), s.cuda_stream,
                                         ctypes.byref(h)), "ctq_skiplist_create")
         self.handle = h
+        if precision != FP64:
+            self.set_precision(precision)
+
+    def set_precision(self, precision):
+        """FP64 (float64 SIMT products) or BF16X3 (tensor-core products)."""
+        _check(_lib.ctq_skiplist_set_precision(self.handle, precision), "ctq_skiplist_set_precision")
 
     def __del__(self):
         h = getattr(self, "handle", None)

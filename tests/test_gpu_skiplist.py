@@ -48,12 +48,18 @@ def live_move(rng, m, tau, op, beta):
     raise RuntimeError("no surviving pair move")
 
 
-def run_moves(m, imp, tau, op, beta, n_moves, seed, oracle_every=1):
+# Stated relative errors of the tensor-core (BF16X3) skip list against the
+# oracle: the small-block BF16X3 kernel's stated bars (a cached product is
+# one bf16 hi / lo product with FP32 accumulation, like a step of that kernel).
+STATED_BF16X3 = {"t2g": 2e-4, "d5": 1.2e-2}
+
+
+def run_moves(m, imp, tau, op, beta, n_moves, seed, oracle_every=1, precision=ctq.FP64, stated=None):
     rng = np.random.default_rng(seed)
-    sl = ctq.SkipListTrace(imp, beta, seed=seed)
+    sl = ctq.SkipListTrace(imp, beta, seed=seed, precision=precision)
     sl.set(tau, op)
     la, ph, st = sl.evaluate()
-    bars = parity.Bars(f"skip list, {n_moves} moves")
+    bars = parity.Bars(f"skip list ({'FP64' if precision == ctq.FP64 else 'BF16X3'}), {n_moves} moves")
     products, n_ops, worst = [], [], 0.0
     for k in range(n_moves + 1):
         if k > 0:
@@ -79,9 +85,10 @@ def run_moves(m, imp, tau, op, beta, n_moves, seed, oracle_every=1):
                 continue
             err = rel(la, ph, ref["log_abs"], ph_ref)
             worst = max(worst, err)
-            assert err <= bars.fp64(k, ref), (k, err, len(tau))
+            bar = bars.fp64(k, ref) if precision == ctq.FP64 else bars.mixed(k, ref, stated)
+            assert err <= bar, (k, err, bar, len(tau))
         # against the library's own float64 path on the same configuration
-        assert rel(la, ph, la_f, ph_f) <= 2 * parity.FP64_CAP, k
+        assert rel(la, ph, la_f, ph_f) <= (2 * parity.FP64_CAP if precision == ctq.FP64 else 10 * stated), k
     bars.check()
     return np.asarray(products), np.asarray(n_ops), worst
 
@@ -99,6 +106,42 @@ def test_skiplist_moves_match_oracle(name, chain, n_moves, models):
     # the operators whose sector it shifted), far fewer than the k - 1 of a
     # full product
     assert prods.mean() < 0.5 * n_ops.mean()
+
+
+@pytest.mark.parametrize("name,chain,n_moves", [("t2g", 3, 40), ("d5", 1, 16)])
+def test_skiplist_tensor_cores_match_oracle(name, chain, n_moves, models):
+    """The same moves with the products on the tensor cores (CTQ_BF16X3):
+    every configuration against the oracle at the stated BF16X3 bar."""
+    m = models(name)
+    imp = parity.load_oracle_model(ctq, m)
+    b = w.WORKLOADS[name][1]()
+    tau, op = b.chain(chain)
+    prods, n_ops, worst = run_moves(m, imp, np.asarray(tau), np.asarray(op), b.beta, n_moves, seed=7,
+                                    precision=ctq.BF16X3, stated=STATED_BF16X3[name])
+    print(f"\n{name} BF16X3: {n_moves} moves, {prods.mean():.1f} products per move, worst error vs oracle "
+          f"{worst:.2e} (stated {STATED_BF16X3[name]:.0e})")
+    assert prods.mean() < 0.5 * n_ops.mean()
+
+
+def test_skiplist_precision_switch(models):
+    """Switching precision releases the cached products; both give the
+    configuration's trace; an unsupported precision is refused."""
+    m = models("t2g")
+    imp = parity.load_oracle_model(ctq, m)
+    b = w.WORKLOADS["t2g"][1]()
+    tau, op = (np.asarray(x) for x in b.chain(3))
+    sl = ctq.SkipListTrace(imp, b.beta, seed=3)
+    sl.set(tau, op)
+    la64, ph64, st = sl.evaluate()
+    assert st["cached"] > 0
+    sl.set_precision(ctq.BF16X3)
+    la, ph, st = sl.evaluate()
+    assert st["reused"] == 0 and st["products"] > 0  # nothing kept from the float64 products
+    assert rel(la, ph, la64, ph64) <= STATED_BF16X3["t2g"]
+    with pytest.raises(ctq.CtqError):
+        sl.set_precision(ctq.TF32)
+    la2, ph2, _ = sl.evaluate()  # the refused call changed nothing
+    assert rel(la2, ph2, la, ph) <= 1e-12
 
 
 def test_skiplist_complex_large_blocks():
