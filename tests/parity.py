@@ -2,7 +2,9 @@
 the oracle and the library binding).  Test infrastructure only."""
 from __future__ import annotations
 
+import json
 import math
+import os
 
 import numpy as np
 
@@ -20,9 +22,19 @@ FP64_CAP = 1e-10
 # A chain is ill-conditioned when the oracle's own float64 spread exceeds
 # the FP64 bar itself: only then is its bar widened.
 WIDEN_AT = FP64_REL
-# An ill-conditioned mixed-precision chain is held to its stated bar times
-# spread / WIDEN_AT, at most this many times the stated bar.
+# A mixed-precision chain is held to its stated bar, or, when its measured
+# condition number kappa = spread / 2^-53 (the chain's float64 perturbation
+# spread in units of float64's unit roundoff) times the precision's
+# effective unit exceeds the stated bar, to unit x kappa, at most this many
+# times the stated bar.
 MIXED_WIDEN_CAP = 10.0
+U64 = 2.0 ** -53
+# Effective unit roundoff of one block product per precision code (ctq.TF32 = 1,
+# BF16X3 = 2, TF32X3 = 3, F32X2 = 4): TF32 operands keep 11 bits; bf16 hi / lo
+# about 16; the three-term TF32 split keeps 22 but its FP32 accumulation over
+# ~100 terms loses about 3 more (fitted on the d shell: the worst chain of
+# 384 sits at 0.8 of unit x kappa); two-float about 45.
+UNIT = {1: 2.0 ** -11, 2: 2.0 ** -16, 3: 2.0 ** -19, 4: 2.0 ** -45}
 # At most this fraction of a test's chains (and at least three chains) may
 # be held to a widened bar; every widened chain is printed.  (The d shell at
 # beta = 40 has 4.9 % of its 1024 chains above the FP64 bar in float64
@@ -53,8 +65,11 @@ class Bars:
     fp64(c, ref):     base x scale, or, when spread > WIDEN_AT,
                       max(base, min(FP64_CAP, 8 x spread)) x scale;
                       plus log_carrier(ref)
-    mixed(c, ref, b): b, or, when spread > WIDEN_AT,
-                      b x min(MIXED_WIDEN_CAP, spread / WIDEN_AT)
+    mixed(c, ref, b, unit, err):
+                      b x min(MIXED_WIDEN_CAP, max(1, unit x spread / 2^-53 / b));
+                      a chain counts as widened only if its error needed it
+                      (err > b; every chain with a factor above 1 when err
+                      is not given)
     check():          prints the widened chains and asserts that there are
                       at most max(WIDEN_MIN, WIDEN_FRAC x chains seen) of them."""
 
@@ -72,11 +87,11 @@ class Bars:
             self.widened.append((int(c), noise, bar * scale))
         return bar * scale + log_carrier(ref)
 
-    def mixed(self, c, ref, stated: float) -> float:
+    def mixed(self, c, ref, stated: float, unit: float, err=None) -> float:
         self.n += 1
         noise = ref.get("noise", 0.0)
-        f = min(MIXED_WIDEN_CAP, noise / WIDEN_AT) if noise > WIDEN_AT else 1.0
-        if f > 1.0:
+        f = min(MIXED_WIDEN_CAP, max(1.0, unit * (noise / U64) / stated))
+        if f > 1.0 and (err is None or err > stated):
             self.widened.append((int(c), noise, stated * f))
         return stated * f
 
@@ -184,3 +199,19 @@ def load_oracle_model(ctq, m, device=0, with_norms=True):
     the GPU arithmetic is compared on identical blocks and energies."""
     return ctq.load_impurity(m.n_flav, m.dims, m.N, m.E, m.s, m.F, mu=m.mu,
                              opnorm=model_opnorms(m) if with_norms else None, device=device)
+
+
+GOLD_D5 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "d5_oracle.json")
+
+
+def gold_d5():
+    """Stored oracle results of the first chains of the d-shell batch
+    (tests/golden/make_d5_oracle.py), in the form chain_error reads."""
+    with open(GOLD_D5) as f:
+        g = json.load(f)
+    refs = {}
+    for e in g["chains"]:
+        refs[e["chain"]] = {"log_abs": e["log_abs"], "phase": complex(*e["phase"]), "noise": e["noise"],
+                            "n_ops": e["n_ops"],
+                            "per_q0": {int(q): (v[0], complex(v[1], v[2])) for q, v in e["per_q0"].items()}}
+    return g["n_chains"], refs

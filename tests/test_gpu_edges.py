@@ -67,7 +67,8 @@ def test_edges(name, precision, kernel, oracle_models):
             continue
         n_live += 1
         err, kind = parity.chain_error(res["log_abs"][c], res["phase"][c], r)
-        tol = bars.fp64(c, r) if TOL[precision] is None else bars.mixed(c, r, TOL[precision])
+        tol = (bars.fp64(c, r) if TOL[precision] is None
+               else bars.mixed(c, r, TOL[precision], parity.UNIT[precision], err))
         assert err <= tol, (c, err, kind)
         assert res["status"][c] == ctq.CHAIN_OK
     bars.check()

@@ -230,7 +230,7 @@ def test_static_improved_tensor_cores(models):
     bars = parity.Bars("t2g h^st TF32X3")
 
     def bar(key, ref):
-        return bars.mixed(key, ref, STATED_TC[(ctq.TF32X3, "t2g")])
+        return bars.mixed(key, ref, STATED_TC[(ctq.TF32X3, "t2g")], parity.UNIT[ctq.TF32X3])
     wu, wh = check(m, mb, sub, bu, chain, ev, bar, label="t2g h^st TF32X3")
     bars.check()
     print(f"\nt2g TF32X3: max rel err w^U {wu:.2e}, h^st {wh:.2e}")

@@ -62,7 +62,8 @@ def test_mixed_batch_decisions(mi, n, precision, models):
         else:
             assert res["status"][c] == ctq.CHAIN_ACCEPTED, c
             err, _ = parity.chain_error(res["log_abs"][c], res["phase"][c], ref[c])
-            bar = bars.fp64(c, ref[c]) if precision == ctq.FP64 else bars.mixed(c, ref[c], STATED_TF32X3[mi])
+            bar = (bars.fp64(c, ref[c]) if precision == ctq.FP64
+                   else bars.mixed(c, ref[c], STATED_TF32X3[mi], parity.UNIT[precision], err))
             print(f"  chain {int(idx[c])}: n_ops {len(sub.chain(c)[1])} err {err:.3e} bar {bar:.1e}")
             assert err <= bar, (c, err)
     bars.check()

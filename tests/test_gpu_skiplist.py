@@ -87,7 +87,7 @@ def run_moves(m, imp, tau, op, beta, n_moves, seed, oracle_every=1, precision=ct
                 continue
             err = rel(la, ph, ref["log_abs"], ph_ref)
             worst = max(worst, err)
-            bar = bars.fp64(k, ref) if precision == ctq.FP64 else bars.mixed(k, ref, stated)
+            bar = bars.fp64(k, ref) if precision == ctq.FP64 else bars.mixed(k, ref, stated, parity.UNIT[precision], err)
             assert err <= bar, (k, err, bar, len(tau))
         # against the library's own float64 path on the same configuration
         assert rel(la, ph, la_f, ph_f) <= (2 * parity.FP64_CAP if precision == ctq.FP64 else 10 * stated), k
