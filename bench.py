@@ -1023,8 +1023,9 @@ def main():
         return
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 6 for the mixed batch, about a minute of timed work; 20 otherwise)")
+    ap.add_argument("--warmup", type=int, default=None, help="untimed warm-up steps (default: 3 mixed, 5 otherwise)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mixed", choices=sorted(WORKLOAD_TEXT))
     ap.add_argument("--precision", default=None, choices=["fp64", "tf32", "tf32x3", "bf16x3", "f32x2"],
@@ -1042,6 +1043,11 @@ def main():
                          "skiplist: incremental traces of one configuration under random pair moves")
     ap.add_argument("--autotune-cache", default=None, help="JSON cache of tuned launch configurations")
     args = ap.parse_args()
+    long_steps = args.workload == "mixed" and args.estimator == "trace"
+    if args.steps is None:
+        args.steps = 6 if long_steps else 20
+    if args.warmup is None:
+        args.warmup = 3 if long_steps else 5
     args.warmup = max(args.warmup, 3)
     if args.precision is None:
         args.precision = DEFAULT_PRECISION.get(args.workload, "fp64")

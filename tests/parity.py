@@ -79,7 +79,7 @@ class Bars:
         self.n = 0
         self.widened = []
 
-    def fp64(self, c, ref, base: float = FP64_REL, scale: float = 1.0) -> float:
+    def fp64(self, c, ref, base: float = FP64_REL, scale: float = 1.0, err=None) -> float:
         self.n += 1
         noise = ref.get("noise", 0.0)
         bar = max(base, min(FP64_CAP, NOISE_FACTOR * noise)) if noise > WIDEN_AT else base

@@ -91,8 +91,9 @@ class FloorCount:
 
 def check(m, mb, sub, bu, chain, ev, bar, scale_floor=0.0, label="h^st", floor_cap=FLOOR_CAP):
     """Replaced traces and ratios against the oracle; returns the worst errors.
-    bar(key, ref) gives a trace's arithmetic bar (a parity.Bars method, which
-    counts widened chains).  scale_floor > 0 (two different eigenbases) also
+    bar(key, ref, err) gives a trace's arithmetic bar (a parity.Bars method,
+    which counts widened chains; err lets a mixed bar count only the chains
+    that needed the widening).  scale_floor > 0 (two different eigenbases) also
     allows that much error relative to the configuration's conditioning scale
     e^{log_cond} (the float64 rounding of the two bases' blocks, which a
     near-cancelling trace does not scale down), at most floor_cap, with the
@@ -115,7 +116,7 @@ def check(m, mb, sub, bu, chain, ev, bar, scale_floor=0.0, label="h^st", floor_c
             eu, ku, tu = 0.0, "zero", 0.0
         else:
             eu, ku = parity.chain_error(ru["log_abs"][i], ru["phase"][i], ref_u[i])
-            tu = bar(i, ref_u[i])
+            tu = bar(i, ref_u[i], eu)
             if scale_floor > 0.0 and ref_u[i]["log_abs"] != -math.inf:
                 lc = max(ref_u[i]["log_cond"], rw["log_cond"])
                 tu = floors.bar(eu, tu, min(floor_cap, scale_floor * math.exp(lc - log_scale(ref_u[i], ku))),
@@ -139,7 +140,7 @@ def check(m, mb, sub, bu, chain, ev, bar, scale_floor=0.0, label="h^st", floor_c
         if rw["log_abs"] == -math.inf:
             continue
         ew, kw = parity.chain_error(la, rb["phase"][c], rw)
-        tw = bar(c, rw)
+        tw = bar(c, rw, ew)
         if scale_floor > 0.0:
             tw = floors.bar(ew, tw, min(floor_cap, scale_floor * math.exp(rw["log_cond"] - log_scale(rw, kw))),
                             ("w", i))
@@ -191,7 +192,7 @@ def test_static_improved_on_library_eigenbasis(name, models):
 
     bars = parity.Bars(f"{name} h^st library eigenbasis")
 
-    def bar(key, ref):  # two eigenbases: 1e-11, or their float64 spread as well
+    def bar(key, ref, err=None):  # two eigenbases: 1e-11, or their float64 spread as well
         return bars.fp64(key, ref, base=1e-11)
     # two independent eigensolvers agree to ~1e-12 of the configuration's
     # scale, so a replaced trace 1e4 times below that scale carries ~1e-8
@@ -211,7 +212,7 @@ def test_static_improved_two_float(models):
 
     bars = parity.Bars("t2g h^st F32X2")
 
-    def bar(key, ref):
+    def bar(key, ref, err=None):
         return bars.fp64(key, ref, base=X2_REL / 32.0, scale=32.0)
     wu, wh = check(m, mb, sub, bu, chain, ev, bar, label="t2g h^st F32X2")
     bars.check()
@@ -229,8 +230,8 @@ def test_static_improved_tensor_cores(models):
 
     bars = parity.Bars("t2g h^st TF32X3")
 
-    def bar(key, ref):
-        return bars.mixed(key, ref, STATED_TC[(ctq.TF32X3, "t2g")], parity.UNIT[ctq.TF32X3])
+    def bar(key, ref, err=None):
+        return bars.mixed(key, ref, STATED_TC[(ctq.TF32X3, "t2g")], parity.UNIT[ctq.TF32X3], err)
     wu, wh = check(m, mb, sub, bu, chain, ev, bar, label="t2g h^st TF32X3")
     bars.check()
     print(f"\nt2g TF32X3: max rel err w^U {wu:.2e}, h^st {wh:.2e}")
