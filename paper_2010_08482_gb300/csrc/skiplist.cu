@@ -265,22 +265,24 @@ __global__ void k_sl_roots(const SlRoot* tasks) {
 // matrices (k_sl_fmt); then C = A B^T runs on 128 x 256 tiles (k_sl_tc):
 // A = the left factor R as stored (M x K', complex rows [Re | Im]), B = the
 // rows of the real embedding of the right factor transposed (N' x K'),
-// chunks of 64 K elements staged by bulk copies through two 96 KB stages,
+// chunks of 32 K elements staged by bulk copies through four 48 KB stages,
 // three MMAs per 16 K (hi hi + hi lo + lo hi) into one FP32 accumulator of
 // 256 tensor-memory columns, drained to the float64 product with its max.
-constexpr int TBM = 128, TBN = 256, TKE = 64;                      // tile rows, columns, K per chunk
-constexpr uint32_t TA_BYTES = TBM * 128, TB_BYTES = TBN * 128;     // one plane of a staged chunk
+constexpr int TBM = 128, TBN = 256, TKE = 32;                      // tile rows, columns, K per chunk
+constexpr uint32_t TA_BYTES = TBM * TKE * 2, TB_BYTES = TBN * TKE * 2;  // one bf16 plane of a staged chunk
 constexpr uint32_t TSTAGE = 2 * (TA_BYTES + TB_BYTES);             // hi and lo planes of A and B
+constexpr int NSTG = 4;                                            // stages in flight (192 KB)
+constexpr int SL_GW = 8;                                           // column tiles per scheduling group
 constexpr int TC_SL_THREADS = 128;                                 // one thread per accumulator row
 constexpr int FMT_CHUNK = 2048;                                    // operand elements per format CTA
 constexpr uint64_t SL_TC_TIMEOUT_NS = 20000000000ull;              // bound of every wait (20 s)
 
-// Element (r, k) of an operand stored as tiles of rpt rows x 64 K elements:
-// tile (r / rpt, k / 64) at ((r / rpt) nkc + k / 64) rpt 64, core matrix
-// (k % 64 / 8, r % rpt / 8) at (k % 64 / 8 * rpt / 8 + r % rpt / 8) 64,
+// Element (r, k) of an operand stored as tiles of rpt rows x TKE K elements:
+// tile (r / rpt, k / TKE) at ((r / rpt) nkc + k / TKE) rpt TKE, core matrix
+// (k % TKE / 8, r % rpt / 8) at (k % TKE / 8 * rpt / 8 + r % rpt / 8) 64,
 // element (r % 8) 8 + k % 8.
 __device__ __forceinline__ size_t tc_off(int r, int k, int rpt, int nkc) {
-  const int rt = r / rpt, rr = r - rt * rpt, kc = k >> 6, kk = k & 63;
+  const int rt = r / rpt, rr = r - rt * rpt, kc = k / TKE, kk = k % TKE;
   return (size_t(rt) * nkc + kc) * size_t(rpt) * TKE + size_t((kk >> 3) * (rpt >> 3) + (rr >> 3)) * 64 +
          (rr & 7) * 8 + (kk & 7);
 }
@@ -305,57 +307,79 @@ struct SlTc {
   const unsigned long long* wR;
   const unsigned long long* wL;
   unsigned long long* wC;
-  int M, Np, nkc, tiles_n, tile0;
+  int M, Np, nkc, tiles_n, tiles_m, tile0;
 };
 
+// One thread per 8 consecutive K elements of one operand row (a 16-byte
+// core-matrix row of each plane, stored as one vector): A rows read as 64
+// contiguous bytes, L read row by row with consecutive threads on
+// consecutive columns.
 __global__ void k_sl_fmt(const SlFmt* tasks, int n) {
   const SlFmt T = tasks[find_task(tasks, n, blockIdx.x)];
   int e_unused;
   const double sc = norm_of(T.w, &e_unused);
-  const long long total = (long long)T.rows_pad * T.kp_pad;
-  const long long e0 = (long long)(blockIdx.x - T.tile0) * FMT_CHUNK;
-  const long long e1 = e0 + FMT_CHUNK < total ? e0 + FMT_CHUNK : total;
+  const int kg_n = T.kp_pad / 8;
+  const long long total = (long long)T.rows_pad * kg_n;  // groups of 8 elements
+  const long long g0 = (long long)(blockIdx.x - T.tile0) * (FMT_CHUNK / 8);
+  const long long g1 = g0 + FMT_CHUNK / 8 < total ? g0 + FMT_CHUNK / 8 : total;
   const int nkc = T.kp_pad / TKE;
-  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    int r, k;
-    double v = 0.0;
-    if (T.mode == 0) {  // consecutive threads: consecutive k of a row of R
-      r = int(e / T.kp_pad);
-      k = int(e - (long long)r * T.kp_pad);
-      if (r < T.rows && k < T.kp) v = T.src[size_t(r) * T.kp + k];
-    } else {  // consecutive threads: consecutive n of a row of L
-      k = int(e / T.rows_pad);
-      r = int(e - (long long)k * T.rows_pad);
-      if (r < T.rows && k < T.kp) {
-        const int Np = T.cplx ? 2 * T.N : T.N;
-        if (!T.cplx || k < T.K) {
-          v = T.src[size_t(k) * Np + r];
-        } else {
-          const int kk = k - T.K;
-          v = (r < T.N) ? -T.src[size_t(kk) * Np + T.N + r] : T.src[size_t(kk) * Np + (r - T.N)];
-        }
-      }
+  const int Np = T.cplx ? 2 * T.N : T.N;
+  for (long long g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+    int r, k0;
+    if (T.mode == 0) {
+      r = int(g / kg_n);
+      k0 = 8 * int(g - (long long)r * kg_n);
+    } else {
+      const int kg = int(g / T.rows_pad);
+      r = int(g - (long long)kg * T.rows_pad);
+      k0 = 8 * kg;
     }
-    const float x = float(v * sc);
-    const uint32_t h = bf16_bits(x);
-    const size_t o = tc_off(r, k, T.rpt, nkc);
-    T.hi[o] = uint16_t(h);
-    T.lo[o] = uint16_t(bf16_bits(x - bf16_val(h)));
+    uint32_t hw[4], lw[4];
+#pragma unroll
+    for (int t = 0; t < 8; t += 2) {
+      float x[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int k = k0 + t + u;
+        double v = 0.0;
+        if (r < T.rows && k < T.kp) {
+          if (T.mode == 0) {
+            v = T.src[size_t(r) * T.kp + k];
+          } else if (!T.cplx || k < T.K) {
+            v = T.src[size_t(k) * Np + r];
+          } else {
+            const int kk = k - T.K;
+            v = (r < T.N) ? -T.src[size_t(kk) * Np + T.N + r] : T.src[size_t(kk) * Np + (r - T.N)];
+          }
+        }
+        x[u] = float(v * sc);
+      }
+      const uint32_t h0 = bf16_bits(x[0]), h1 = bf16_bits(x[1]);
+      hw[t / 2] = h0 | (h1 << 16);
+      lw[t / 2] = bf16_bits(x[0] - bf16_val(h0)) | (bf16_bits(x[1] - bf16_val(h1)) << 16);
+    }
+    const size_t o = tc_off(r, k0, T.rpt, nkc);  // 8 consecutive elements, 16-byte aligned
+    *reinterpret_cast<uint4*>(T.hi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *reinterpret_cast<uint4*>(T.lo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
   }
 }
 
 __global__ void __launch_bounds__(TC_SL_THREADS, 1)
     k_sl_tc(const SlTc* tasks, int n, uint64_t timeout_ns, int* status) {
   extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ uint64_t full[2], empty[2], done;
+  __shared__ uint64_t full[NSTG], empty[NSTG], done;
   __shared__ uint32_t tmem_base;
   __shared__ int fail;
   const SlTc T = tasks[find_task(tasks, n, blockIdx.x)];
   const int local = blockIdx.x - T.tile0;
-  const int mt = local / T.tiles_n, nt = local - mt * T.tiles_n;
+  // tiles in groups of SL_GW column tiles, row tiles fastest within a group:
+  // the CTAs resident together share a few block columns and row panels in L2
+  const int grp = local / (SL_GW * T.tiles_m), n0 = grp * SL_GW;
+  const int gw = min(SL_GW, T.tiles_n - n0), in = local - grp * SL_GW * T.tiles_m;
+  const int mt = in / gw, nt = n0 + (in - mt * gw);
   const int tid = threadIdx.x, warp = tid >> 5;
   if (tid == 0) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < NSTG; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
     }
@@ -378,23 +402,23 @@ __global__ void __launch_bounds__(TC_SL_THREADS, 1)
     const int nkc = T.nkc;
     const size_t a_tile = size_t(TBM) * TKE, b_tile = size_t(TBN) * TKE;  // elements of one chunk
     auto issue = [&](int kc) {
-      unsigned char* base = sm + (kc & 1) * TSTAGE;
+      const int st = kc % NSTG;
+      unsigned char* base = sm + st * TSTAGE;
       const size_t ao = (size_t(mt) * nkc + kc) * a_tile, bo = (size_t(nt) * nkc + kc) * b_tile;
-      mbar_arrive_expect_tx(&full[kc & 1], TSTAGE);
-      bulk_g2s(base, T.Ah + ao, TA_BYTES, &full[kc & 1]);
-      bulk_g2s(base + TA_BYTES, T.Bh + bo, TB_BYTES, &full[kc & 1]);
-      bulk_g2s(base + TA_BYTES + TB_BYTES, T.Al + ao, TA_BYTES, &full[kc & 1]);
-      bulk_g2s(base + 2 * TA_BYTES + TB_BYTES, T.Bl + bo, TB_BYTES, &full[kc & 1]);
+      mbar_arrive_expect_tx(&full[st], TSTAGE);
+      bulk_g2s(base, T.Ah + ao, TA_BYTES, &full[st]);
+      bulk_g2s(base + TA_BYTES, T.Bh + bo, TB_BYTES, &full[st]);
+      bulk_g2s(base + TA_BYTES + TB_BYTES, T.Al + ao, TA_BYTES, &full[st]);
+      bulk_g2s(base + 2 * TA_BYTES + TB_BYTES, T.Bl + bo, TB_BYTES, &full[st]);
     };
     constexpr uint32_t LBO_A = (TBM / 8) * 128, LBO_B = (TBN / 8) * 128;
     const uint32_t idesc = idesc_bf16(TBM, TBN);
-    issue(0);
-    if (nkc > 1) issue(1);
-    int issued = nkc > 1 ? 2 : 1, kc = 0;
+    int issued = 0, kc = 0;
+    for (; issued < nkc && issued < NSTG; ++issued) issue(issued);
     bool ok = true;
     for (; kc < nkc; ++kc) {
-      const int st = kc & 1;
-      ok = mbar_wait(&full[st], uint32_t((kc >> 1) & 1), timeout_ns);
+      const int st = kc % NSTG;
+      ok = mbar_wait(&full[st], uint32_t((kc / NSTG) & 1), timeout_ns);
       if (!ok) break;
       tc_fence_after();
       const uint32_t sa = smem_u32(sm + st * TSTAGE), sbh = sa + TA_BYTES, sal = sbh + TB_BYTES, sbl = sal + TA_BYTES;
@@ -405,11 +429,11 @@ __global__ void __launch_bounds__(TC_SL_THREADS, 1)
         mma_bf16_ss(tD, sdesc(sal + kk * 2 * LBO_A, LBO_A, 128), dbh, idesc, 1u);
       }
       mma_commit(&empty[st]);
-      if (kc >= 1 && kc + 1 < nkc) {  // chunk kc - 1's stage takes chunk kc + 1 once its MMAs are done
-        ok = mbar_wait(&empty[st ^ 1], uint32_t(((kc - 1) >> 1) & 1), timeout_ns);
+      if (kc >= 1 && kc + NSTG - 1 < nkc) {  // chunk kc - 1's stage takes chunk kc + NSTG - 1 once its MMAs are done
+        ok = mbar_wait(&empty[(kc - 1) % NSTG], uint32_t(((kc - 1) / NSTG) & 1), timeout_ns);
         if (!ok) break;
-        issue(kc + 1);
-        issued = kc + 2;
+        issue(kc + NSTG - 1);
+        issued = kc + NSTG;
       }
     }
     if (ok) {
@@ -418,7 +442,7 @@ __global__ void __launch_bounds__(TC_SL_THREADS, 1)
       fail = 1;
       atomicExch(status, CTQ_ERR_TIMEOUT);
       // copies still in flight land in this CTA's shared memory: wait for them (bounded)
-      for (int j = kc; j < issued; ++j) mbar_wait(&full[j & 1], uint32_t((j >> 1) & 1), timeout_ns);
+      for (int j = kc; j < issued; ++j) mbar_wait(&full[j % NSTG], uint32_t((j / NSTG) & 1), timeout_ns);
     }
   }
   __syncthreads();
@@ -794,7 +818,7 @@ int launch_plan(ctq_skiplist* S, Plan& P) {
       SlFmt fb{t.L, t.wL, at(wo + 4 * a_el), at(wo + 4 * a_el + 2 * b_el), Np, Kp, Npad, Kpad, 1, t.K, t.N, t.cplx,
                TBN, ft};
       ft += int((int64_t(b_el) + FMT_CHUNK - 1) / FMT_CHUNK);
-      SlTc g{fa.hi, fa.lo, fb.hi, fb.lo, t.C, t.wR, t.wL, t.wC, t.M, Np, Kpad / TKE, Npad / TBN, tt};
+      SlTc g{fa.hi, fa.lo, fb.hi, fb.lo, t.C, t.wR, t.wL, t.wC, t.M, Np, Kpad / TKE, Npad / TBN, Mpad / TBM, tt};
       tt += (Mpad / TBM) * (Npad / TBN);
       wo += 2 * (2 * a_el + 2 * b_el);
       fmts[r].push_back(fa);
@@ -913,7 +937,7 @@ int launch_plan(ctq_skiplist* S, Plan& P) {
     if (P.rounds[r].empty()) continue;
     k_sl_fmt<<<fmt_tiles[r], 256, 0, S->st>>>(reinterpret_cast<const SlFmt*>(S->d_tab + o_fmt[r]),
                                               int(fmts[r].size()));
-    k_sl_tc<<<n_tiles[r], TC_SL_THREADS, TSTAGE * 2, S->st>>>(
+    k_sl_tc<<<n_tiles[r], TC_SL_THREADS, TSTAGE * NSTG, S->st>>>(
         reinterpret_cast<const SlTc*>(S->d_tab + o_round[r]), int(tcs[r].size()), SL_TC_TIMEOUT_NS, S->d_status);
     launches += 2;
   }
@@ -993,7 +1017,7 @@ extern "C" int ctq_skiplist_set_precision(ctq_skiplist* S, int precision) {
   ctq::DevGuard g(S->device);
   if (precision == CTQ_BF16X3) {
     if (!S->d_status && cudaMalloc(&S->d_status, sizeof(int)) != cudaSuccess) return CTQ_ERR_NOMEM;
-    if (cudaFuncSetAttribute(ctq::k_sl_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(2 * ctq::TSTAGE)) !=
+    if (cudaFuncSetAttribute(ctq::k_sl_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ctq::NSTG * ctq::TSTAGE)) !=
         cudaSuccess)
       return CTQ_ERR_CUDA;
   }
