@@ -126,14 +126,18 @@ __global__ void k_sl_zero(unsigned long long* const* w, int n) {
 // Leaves: out[m][j] = e^{-dt E_rel(q_out)_m} F[m][j]; complex rows are
 // stored [Re(0..d_in) | Im(0..d_in)].
 __global__ void k_sl_leaves(const double* blk, const SlLeaf* tasks, int n) {
+  __shared__ double p_s[LEAF_CHUNK];  // the propagator of the chunk's rows, one exponential per row
   const SlLeaf T = tasks[find_task(tasks, n, blockIdx.x)];
   const long long total = (long long)T.d_out * T.d_in;
   const long long e0 = (long long)(blockIdx.x - T.tile0) * LEAF_CHUNK;
   const long long e1 = e0 + LEAF_CHUNK < total ? e0 + LEAF_CHUNK : total;
+  const int m0 = int(e0 / T.d_in), nrow = int((e1 - 1) / T.d_in) - m0 + 1;  // nrow <= LEAF_CHUNK
+  for (int i = threadIdx.x; i < nrow; i += blockDim.x) p_s[i] = T.dt > 0.0 ? exp(-T.dt * T.E_out[m0 + i]) : 1.0;
+  __syncthreads();
   double mx = 0.0;
   for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int m = int(e / T.d_in), j = int(e - (long long)m * T.d_in);
-    const double p = T.dt > 0.0 ? exp(-T.dt * T.E_out[m]) : 1.0;
+    const double p = p_s[m - m0];
     if (T.cplx) {
       const double re = blk[2 * (T.off + e)] * p, im = blk[2 * (T.off + e) + 1] * p;
       T.out[size_t(m) * 2 * T.d_in + j] = re;
