@@ -146,16 +146,24 @@ def test_skiplist_precision_switch(models):
     assert rel(la2, ph2, la, ph) <= 1e-12
 
 
-def test_skiplist_complex_large_blocks():
+# Stated BF16X3 error of the large-block d shells (the large-block kernels' stated bar).
+STATED_BF16X3_LARGE_D = 2e-3
+
+
+@pytest.mark.parametrize("precision", [ctq.FP64, ctq.BF16X3])
+def test_skiplist_complex_large_blocks(precision):
     """Complex d shell with SOC and a complex crystal field, N in [1, 3]
-    (blocks up to 120): the [Re | Im] float64 products."""
+    (blocks up to 120): the [Re | Im] products in float64, and on the tensor
+    cores through the real embedding of the right factor."""
     m = atom.Model(complex_d_model())
     imp = parity.load_oracle_model(ctq, m)
     rng = np.random.default_rng(3)
     b = w.random_batch(rng, m.n_flav, m.beta, 1, 6, 10, gen="g2")
     tau, op = b.chain(0)
-    prods, n_ops, worst = run_moves(m, imp, np.asarray(tau), np.asarray(op), m.beta, 24, seed=9, oracle_every=2)
-    print(f"\ncomplex d shell: {n_ops.mean():.0f} operators, {prods.mean():.1f} products per move, worst {worst:.2e}")
+    prods, n_ops, worst = run_moves(m, imp, np.asarray(tau), np.asarray(op), m.beta, 24, seed=9, oracle_every=2,
+                                    precision=precision, stated=STATED_BF16X3_LARGE_D)
+    print(f"\ncomplex d shell ({'FP64' if precision == ctq.FP64 else 'BF16X3'}): {n_ops.mean():.0f} operators, "
+          f"{prods.mean():.1f} products per move, worst {worst:.2e}")
     assert prods.mean() > 0  # the moves keep a surviving string, so every move recomputes something
 
 
