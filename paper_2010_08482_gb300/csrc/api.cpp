@@ -109,6 +109,8 @@ int upload_model(ctq_impurity* imp) {
     }
     lev_off.push_back(int(lev_E.size()));
   }
+  d.max_lev = 1;
+  for (int q = 0; q < h.n_sec; ++q) d.max_lev = std::max(d.max_lev, lev_off[q + 1] - lev_off[q]);
   std::vector<double> blk;
   if (h.is_complex) {
     blk.resize(2 * h.blk_re.size());

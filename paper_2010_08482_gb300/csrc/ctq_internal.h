@@ -87,6 +87,7 @@ struct DevModel {
   const double* lev_E;     // [sum n_lev]
   const int* lev_off;      // [n_sec + 1]
   const int* lev_idx;      // [sum dims]  level of each state within its sector
+  int max_lev;             // largest number of levels of one sector
 };
 
 struct BatchView {
@@ -168,6 +169,7 @@ struct LaunchCfg {
   int per_sm = 0;   // resident CTAs per SM (0: shape not supported)
   int num_sms = 0;
   int regs = 0;     // registers per thread of the kernel
+  int regs_small = 0;  // registers per thread of the 32-thread variant (small blocks), if any
   int smem_optin = 0;  // opt-in shared memory per block of the device
 };
 

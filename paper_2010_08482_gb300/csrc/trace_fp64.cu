@@ -122,9 +122,12 @@ __device__ __forceinline__ int block_max_int(int v, int* redi) {
 // the start of an item (lanes over all (operator, state) pairs), which keeps
 // the FP64 pipe busy with full warps; used when max_ops * max_dim fits.
 // X2: two-float products (CTQ_F32X2); propagators, log scale and the
-// final diagonal stay in float64.
-template <bool CPLX, bool PRE, bool X2>
-__global__ void __launch_bounds__(512, 1) k_trace(DevModel M, BatchView B, EvalCfg cfg, Work W) {
+// final diagonal stay in float64.  SMALL: a one-warp build held to 64
+// registers so that 32 CTAs fit an SM (used for the two-float products of
+// blocks of at most 12 states, whose FP32 add chains are latency bound).
+template <bool CPLX, bool PRE, bool X2, bool SMALL>
+__global__ void __launch_bounds__(SMALL ? 32 : 512, SMALL ? 32 : 1)
+    k_trace(DevModel M, BatchView B, EvalCfg cfg, Work W) {
   using T = typename Scalar<CPLX, X2>::T;
   using T64 = typename Scalar<CPLX, false>::T;
   using PT = typename Scalar<CPLX, X2>::PT;
@@ -142,8 +145,8 @@ __global__ void __launch_bounds__(512, 1) k_trace(DevModel M, BatchView B, EvalC
   double* segP = segL + NS;                                      // [NS] applied log-norm sums
   double* segF = segP + NS;                                      // [NS] ||Y||^2 at segment ends (deferred)
   double* segE = segF + NS;                                      // [NS] exponent sums at segment ends
-  double* pall = segE + NS;                                      // [MO * D] (PRE)
-  int* poff = reinterpret_cast<int*>(pall + (PRE ? size_t(MO) * D : 0));  // [MO + 1] (PRE)
+  double* pall = segE + NS;                                      // [MO * max_lev] (PRE)
+  int* poff = reinterpret_cast<int*>(pall + (PRE ? size_t(MO) * M.max_lev : 0));  // [MO + 1] (PRE)
   short* path = reinterpret_cast<short*>(poff + (PRE ? MO + 1 : 0));     // [MO + 1] sectors q_0..q_n
   short* opsm = path + (MO + 1);                                          // [MO] operator codes
   __shared__ int s_item;
@@ -464,32 +467,61 @@ static int trace_threads(int max_dim) {
 }
 
 // Dynamic shared memory of k_trace: two Y buffers, p, p0, reductions, the
-// segment bookkeeping, and (PRE) the chain's propagators and offsets, then
-// the path and operator codes.
-static size_t trace_smem(int max_dim, bool cplx, int max_ops, int n_seg_max, bool pre) {
+// segment bookkeeping, and (PRE) the chain's propagators (one per distinct
+// level of each visited sector) and offsets, then the path and operator codes.
+static size_t trace_smem(int max_dim, bool cplx, int max_ops, int n_seg_max, bool pre, int max_lev = 0) {
   const size_t el = cplx ? 16 : 8;
   const size_t mo = size_t(std::max(max_ops, 1));
   size_t b = 2 * size_t(max_dim) * max_dim * el + 2 * size_t(max_dim) * 8 + 64 * 8 + 4 * size_t(n_seg_max + 1) * 8;
-  if (pre) b += mo * max_dim * 8 + (mo + 1) * 4;
+  if (pre) b += mo * size_t(max_lev) * 8 + (mo + 1) * 4;
   b += (mo + 1) * 2 + mo * 2;
   return (b + 15) & ~size_t(15);
 }
 
 // Whole-chain propagator precompute when it fits comfortably.
-static bool use_pre(int max_dim, int max_ops) { return size_t(std::max(max_ops, 1)) * max_dim * 8 <= 48 * 1024; }
+static bool use_pre(int max_lev, int max_ops) { return size_t(std::max(max_ops, 1)) * max_lev * 8 <= 48 * 1024; }
 
 // Raise the dynamic shared-memory cap to the opt-in maximum minus the
 // kernel's static shared memory.
-template <bool CPLX, bool PRE, bool X2>
+template <bool CPLX, bool PRE, bool X2, bool SMALL>
 static int set_attr(int optin, int* regs) {
   cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, k_trace<CPLX, PRE, X2>) != cudaSuccess) return CTQ_ERR_CUDA;
+  if (cudaFuncGetAttributes(&fa, k_trace<CPLX, PRE, X2, SMALL>) != cudaSuccess) return CTQ_ERR_CUDA;
   *regs = std::max(*regs, fa.numRegs);
   const int cap = optin - int(fa.sharedSizeBytes);
-  return cudaFuncSetAttribute(k_trace<CPLX, PRE, X2>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) ==
+  return cudaFuncSetAttribute(k_trace<CPLX, PRE, X2, SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) ==
                  cudaSuccess
              ? CTQ_OK
              : CTQ_ERR_CUDA;
+}
+
+template <bool SMALL>
+static int set_attrs(int optin, int* regs) {
+  int st;
+  if ((st = set_attr<false, false, false, SMALL>(optin, regs)) || (st = set_attr<false, true, false, SMALL>(optin, regs)) ||
+      (st = set_attr<true, false, false, SMALL>(optin, regs)) || (st = set_attr<true, true, false, SMALL>(optin, regs)) ||
+      (st = set_attr<false, false, true, SMALL>(optin, regs)) || (st = set_attr<false, true, true, SMALL>(optin, regs)) ||
+      (st = set_attr<true, false, true, SMALL>(optin, regs)) || (st = set_attr<true, true, true, SMALL>(optin, regs)))
+    return st;
+  return CTQ_OK;
+}
+
+template <bool SMALL>
+static void launch_trace(bool x2, bool cplx, bool pre, dim3 g, dim3 b, size_t smem, cudaStream_t st, const DevModel& M,
+                         const BatchView& B, const EvalCfg& cfg, const Work& W) {
+  if (x2 && cplx) {
+    if (pre) k_trace<true, true, true, SMALL><<<g, b, smem, st>>>(M, B, cfg, W);
+    else k_trace<true, false, true, SMALL><<<g, b, smem, st>>>(M, B, cfg, W);
+  } else if (x2) {
+    if (pre) k_trace<false, true, true, SMALL><<<g, b, smem, st>>>(M, B, cfg, W);
+    else k_trace<false, false, true, SMALL><<<g, b, smem, st>>>(M, B, cfg, W);
+  } else if (cplx) {
+    if (pre) k_trace<true, true, false, SMALL><<<g, b, smem, st>>>(M, B, cfg, W);
+    else k_trace<true, false, false, SMALL><<<g, b, smem, st>>>(M, B, cfg, W);
+  } else {
+    if (pre) k_trace<false, true, false, SMALL><<<g, b, smem, st>>>(M, B, cfg, W);
+    else k_trace<false, false, false, SMALL><<<g, b, smem, st>>>(M, B, cfg, W);
+  }
 }
 
 // Whether the shared-memory FP64 kernel can hold two blocks of the largest
@@ -509,13 +541,10 @@ int prepare_eval_fp64(const DevModel& M, int num_sms, LaunchCfg* lc) {
     return CTQ_ERR_CUDA;
   lc->smem_optin = optin;
   if ((st = prepare_plan(optin)) != CTQ_OK) return st;
-  int regs = 0;  // the largest of all variants sizes the resident CTAs
-  if ((st = set_attr<false, false, false>(optin, &regs)) || (st = set_attr<false, true, false>(optin, &regs)) ||
-      (st = set_attr<true, false, false>(optin, &regs)) || (st = set_attr<true, true, false>(optin, &regs)) ||
-      (st = set_attr<false, false, true>(optin, &regs)) || (st = set_attr<false, true, true>(optin, &regs)) ||
-      (st = set_attr<true, false, true>(optin, &regs)) || (st = set_attr<true, true, true>(optin, &regs)))
-    return st;
+  int regs = 0, regs_small = 0;  // the largest of the variants sizes the resident CTAs
+  if ((st = set_attrs<false>(optin, &regs)) || (st = set_attrs<true>(optin, &regs_small))) return st;
   lc->regs = regs;
+  lc->regs_small = regs_small;
   return CTQ_OK;
 }
 
@@ -525,16 +554,21 @@ int launch_eval_fp64(const DevModel& M, const LaunchCfg& lc, const BatchView& B,
   if (B.n_chains == 0) return CTQ_OK;
   if (x2 && M.blk_x2 == nullptr) return CTQ_ERR_UNSUPPORTED;
   if (lc.per_sm < 1) return CTQ_ERR_UNSUPPORTED;
-  const bool pre = use_pre(M.max_dim, cfg.max_ops);
-  const size_t smem = trace_smem(M.max_dim, M.is_complex != 0, cfg.max_ops, cfg.n_seg_max, pre);
+  const bool pre = use_pre(M.max_lev, cfg.max_ops);
+  const size_t smem = trace_smem(M.max_dim, M.is_complex != 0, cfg.max_ops, cfg.n_seg_max, pre, M.max_lev);
   if (smem + 1024 > size_t(lc.smem_optin)) return CTQ_ERR_UNSUPPORTED;
   // resident CTAs per SM from shared memory, registers and the 32-CTA
   // limit, optionally capped by the caller's launch tuning
   // the two-float products are FP32 add chains: blocks above 32 states get
   // 16 warps per CTA to hide their latency (float64 needs no more than 8)
   const int threads = cfg.threads > 0 ? cfg.threads : (x2 && lc.threads == 256 ? 512 : lc.threads);
+  // the one-warp two-float variant at 64 registers (32 CTAs per SM: its FP32
+  // add chains need the latency hiding; measured on t2g, 4 % faster); the
+  // float64 products are FP64-pipe bound, and the register cap only added
+  // instructions there (3 % slower), so they keep the 512-thread build
+  const bool small = threads == 32 && x2;
   int per_sm = int((228 * 1024) / (smem + 1024));
-  per_sm = std::min(per_sm, 65536 / std::max(1, lc.regs * threads));
+  per_sm = std::min(per_sm, 65536 / std::max(1, (small ? lc.regs_small : lc.regs) * threads));
   per_sm = std::min(per_sm, std::min(32, 2048 / threads));
   if (cfg.ctas_per_sm > 0) per_sm = std::min(per_sm, cfg.ctas_per_sm);
   if (per_sm < 1) return CTQ_ERR_UNSUPPORTED;
@@ -552,19 +586,8 @@ int launch_eval_fp64(const DevModel& M, const LaunchCfg& lc, const BatchView& B,
   long long grid = (long long)lc.num_sms * per_sm;
   if (grid > max_items) grid = max_items;
   const dim3 g{unsigned(grid)}, b{unsigned(threads)};
-  if (x2 && M.is_complex) {
-    if (pre) k_trace<true, true, true><<<g, b, smem, st>>>(M, B, cfg, W);
-    else k_trace<true, false, true><<<g, b, smem, st>>>(M, B, cfg, W);
-  } else if (x2) {
-    if (pre) k_trace<false, true, true><<<g, b, smem, st>>>(M, B, cfg, W);
-    else k_trace<false, false, true><<<g, b, smem, st>>>(M, B, cfg, W);
-  } else if (M.is_complex) {
-    if (pre) k_trace<true, true, false><<<g, b, smem, st>>>(M, B, cfg, W);
-    else k_trace<true, false, false><<<g, b, smem, st>>>(M, B, cfg, W);
-  } else {
-    if (pre) k_trace<false, true, false><<<g, b, smem, st>>>(M, B, cfg, W);
-    else k_trace<false, false, false><<<g, b, smem, st>>>(M, B, cfg, W);
-  }
+  if (small) launch_trace<true>(x2, M.is_complex != 0, pre, g, b, smem, st, M, B, cfg, W);
+  else launch_trace<false>(x2, M.is_complex != 0, pre, g, b, smem, st, M, B, cfg, W);
   if (cudaGetLastError() != cudaSuccess) return CTQ_ERR_CUDA;
   mark(2);
   {
