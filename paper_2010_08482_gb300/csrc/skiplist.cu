@@ -270,14 +270,19 @@ __global__ void k_sl_roots(const SlRoot* tasks) {
 // A = the left factor R as stored (M x K', complex rows [Re | Im]), B = the
 // rows of the real embedding of the right factor transposed (N' x K'),
 // chunks of 32 K elements staged by bulk copies through four 48 KB stages,
-// three MMAs per 16 K (hi hi + hi lo + lo hi) into one FP32 accumulator of
-// 256 tensor-memory columns, drained to the float64 product with its max.
+// three MMAs per 16 K (hi hi + hi lo + lo hi) into two alternating FP32
+// accumulators of 256 tensor-memory columns; every 8 chunks (256 K terms)
+// sixteen drain warps fold the full one into FP32 registers while the tensor
+// core fills the other (the tensor core's own accumulation never spans more
+// than 256 terms), and write the float64 product with its max at the end.
 constexpr int TBM = 128, TBN = 256, TKE = 32;                      // tile rows, columns, K per chunk
 constexpr uint32_t TA_BYTES = TBM * TKE * 2, TB_BYTES = TBN * TKE * 2;  // one bf16 plane of a staged chunk
 constexpr uint32_t TSTAGE = 2 * (TA_BYTES + TB_BYTES);             // hi and lo planes of A and B
 constexpr int NSTG = 4;                                            // stages in flight (192 KB)
 constexpr int SL_GW = 8;                                           // column tiles per scheduling group
-constexpr int TC_SL_THREADS = 128;                                 // one thread per accumulator row
+constexpr int SL_DRAIN = 16;                                       // drain warps (four per tensor-memory lane quarter)
+constexpr int TC_SL_THREADS = 32 * (1 + SL_DRAIN);                 // warp 0: copies and MMAs
+constexpr int SL_GRP = 8;                                          // chunks (256 K terms) per accumulator group
 constexpr int FMT_CHUNK = 2048;                                    // operand elements per format CTA
 constexpr uint64_t SL_TC_TIMEOUT_NS = 20000000000ull;              // bound of every wait (20 s)
 
@@ -371,7 +376,7 @@ __global__ void k_sl_fmt(const SlFmt* tasks, int n) {
 __global__ void __launch_bounds__(TC_SL_THREADS, 1)
     k_sl_tc(const SlTc* tasks, int n, uint64_t timeout_ns, int* status) {
   extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ uint64_t full[NSTG], empty[NSTG], done;
+  __shared__ uint64_t full[NSTG], empty[NSTG], bank_full[2], bank_free[2];
   __shared__ uint32_t tmem_base;
   __shared__ int fail;
   const SlTc T = tasks[find_task(tasks, n, blockIdx.x)];
@@ -381,29 +386,36 @@ __global__ void __launch_bounds__(TC_SL_THREADS, 1)
   const int grp = local / (SL_GW * T.tiles_m), n0 = grp * SL_GW;
   const int gw = min(SL_GW, T.tiles_n - n0), in = local - grp * SL_GW * T.tiles_m;
   const int mt = in / gw, nt = n0 + (in - mt * gw);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int i = 0; i < NSTG; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
     }
-    mbar_init(&done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&bank_full[b], 1);
+      mbar_init(&bank_free[b], SL_DRAIN);  // one arrival per drain warp
+    }
     fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) tmem_alloc(&tmem_base, TBN);
+  if (warp == 0) tmem_alloc(&tmem_base, 2 * TBN);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tD = tmem_base;
+  volatile int* fail_v = &fail;
   int er, el;
   const double sR = norm_of(T.wR, &er), sL = norm_of(T.wL, &el);
   if (local == 0 && tid == 0) {
     const long long eR = reinterpret_cast<const long long*>(T.wR)[1], eL = reinterpret_cast<const long long*>(T.wL)[1];
     reinterpret_cast<long long*>(T.wC)[1] = (sR > 0.0 && sL > 0.0) ? eR + er + eL + el : EXP_DEAD;
   }
+  const int nkc = T.nkc, ngrp = (nkc + SL_GRP - 1) / SL_GRP;
   if (tid == 0) {
-    const int nkc = T.nkc;
+    // copies and MMAs: chunks through the stages; group g of SL_GRP chunks
+    // accumulates in bank g % 2, which the drain warps fold into registers
+    // while the tensor core fills the other bank
     const size_t a_tile = size_t(TBM) * TKE, b_tile = size_t(TBN) * TKE;  // elements of one chunk
     auto issue = [&](int kc) {
       const int st = kc % NSTG;
@@ -421,66 +433,98 @@ __global__ void __launch_bounds__(TC_SL_THREADS, 1)
     for (; issued < nkc && issued < NSTG; ++issued) issue(issued);
     bool ok = true;
     for (; kc < nkc; ++kc) {
-      const int st = kc % NSTG;
-      ok = mbar_wait(&full[st], uint32_t((kc / NSTG) & 1), timeout_ns);
-      if (!ok) break;
+      const int st = kc % NSTG, g = kc / SL_GRP;
+      const uint32_t bank = uint32_t(g & 1);
+      if (kc % SL_GRP == 0 && g >= 2 && !mbar_wait(&bank_free[bank], uint32_t(((g >> 1) - 1) & 1), timeout_ns)) {
+        ok = false;
+        break;
+      }
+      if (!mbar_wait(&full[st], uint32_t((kc / NSTG) & 1), timeout_ns)) {
+        ok = false;
+        break;
+      }
       tc_fence_after();
       const uint32_t sa = smem_u32(sm + st * TSTAGE), sbh = sa + TA_BYTES, sal = sbh + TB_BYTES, sbl = sal + TA_BYTES;
+      const uint32_t tacc = tD + bank * uint32_t(TBN);
       for (int kk = 0; kk < TKE / 16; ++kk) {  // 16 K elements (32 bytes) per MMA
         const uint64_t dah = sdesc(sa + kk * 2 * LBO_A, LBO_A, 128), dbh = sdesc(sbh + kk * 2 * LBO_B, LBO_B, 128);
-        mma_bf16_ss(tD, dah, dbh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-        mma_bf16_ss(tD, dah, sdesc(sbl + kk * 2 * LBO_B, LBO_B, 128), idesc, 1u);
-        mma_bf16_ss(tD, sdesc(sal + kk * 2 * LBO_A, LBO_A, 128), dbh, idesc, 1u);
+        mma_bf16_ss(tacc, dah, dbh, idesc, (kc % SL_GRP != 0 || kk > 0) ? 1u : 0u);
+        mma_bf16_ss(tacc, dah, sdesc(sbl + kk * 2 * LBO_B, LBO_B, 128), idesc, 1u);
+        mma_bf16_ss(tacc, sdesc(sal + kk * 2 * LBO_A, LBO_A, 128), dbh, idesc, 1u);
       }
       mma_commit(&empty[st]);
+      if (kc % SL_GRP == SL_GRP - 1 || kc == nkc - 1) mma_commit(&bank_full[bank]);
       if (kc >= 1 && kc + NSTG - 1 < nkc) {  // chunk kc - 1's stage takes chunk kc + NSTG - 1 once its MMAs are done
-        ok = mbar_wait(&empty[(kc - 1) % NSTG], uint32_t(((kc - 1) / NSTG) & 1), timeout_ns);
-        if (!ok) break;
+        if (!mbar_wait(&empty[(kc - 1) % NSTG], uint32_t(((kc - 1) / NSTG) & 1), timeout_ns)) {
+          ok = false;
+          break;
+        }
         issue(kc + NSTG - 1);
         issued = kc + NSTG;
       }
     }
-    if (ok) {
-      mma_commit(&done);
-    } else {
-      fail = 1;
+    if (!ok) {
+      *fail_v = 1;
       atomicExch(status, CTQ_ERR_TIMEOUT);
       // copies still in flight land in this CTA's shared memory: wait for them (bounded)
       for (int j = kc; j < issued; ++j) mbar_wait(&full[j % NSTG], uint32_t((j / NSTG) & 1), timeout_ns);
     }
-  }
-  __syncthreads();
-  const bool ok = !fail && mbar_wait(&done, 0, timeout_ns);
-  if (__syncthreads_or(!ok)) {
-    if (tid == 0) atomicExch(status, CTQ_ERR_TIMEOUT);
-  } else {
-    tc_fence_after();
-    const int r = mt * TBM + tid;  // accumulator row = lane of this thread's warp quarter
-    const uint32_t lane_off = uint32_t(32 * warp) << 16;
-    double mx = 0.0;
-    for (int c0 = 0; c0 < TBN; c0 += 16) {
-      uint32_t v[16];
-      tmem_ld16(tD + lane_off + uint32_t(c0), v);
-      tmem_wait_ld();
-      const int cb = nt * TBN + c0;
+  } else if (warp >= 1) {
+    // drain warps: lane quarter warp % 4, column slice (warp - 1) / 4 of
+    // COLS columns; every group of the accumulator is added into FP32
+    // registers (round to nearest)
+    constexpr int COLS = TBN / (SL_DRAIN / 4);
+    const int half = (warp - 1) >> 2;
+    const uint32_t tl = uint32_t(32 * (warp & 3)) << 16;
+    float acc[COLS];
+#pragma unroll
+    for (int c = 0; c < COLS; ++c) acc[c] = 0.f;
+    bool okd = true;
+    for (int g = 0; g < ngrp; ++g) {
+      const uint32_t bank = uint32_t(g & 1);
+      const bool ok = !*fail_v && mbar_wait(&bank_full[bank], uint32_t((g >> 1) & 1), timeout_ns);
+      if (!__all_sync(0xffffffffu, ok)) {
+        okd = false;
+        break;
+      }
+      tc_fence_after();
+#pragma unroll
+      for (int h = 0; h < COLS / 16; ++h) {  // 16 columns per tensor-memory wait
+        uint32_t v[16];
+        tmem_ld16(tD + bank * uint32_t(TBN) + tl + uint32_t(half * COLS + h * 16), v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[h * 16 + c] += __uint_as_float(v[c]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bank_free[bank]);
+    }
+    if (!okd) {
+      if (lane == 0) atomicExch(status, CTQ_ERR_TIMEOUT);
+      *fail_v = 1;
+    } else {
+      const int r = mt * TBM + 32 * (warp & 3) + lane;  // this thread's accumulator row
+      double mx = 0.0;
       if (r < T.M) {
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
-          if (cb + t < T.Np) {
-            const double x = double(__uint_as_float(v[t]));
-            T.C[size_t(r) * T.Np + cb + t] = x;
+        for (int c = 0; c < COLS; ++c) {
+          const int col = nt * TBN + half * COLS + c;
+          if (col < T.Np) {
+            const double x = double(acc[c]);
+            T.C[size_t(r) * T.Np + col] = x;
             mx = fmax(mx, fabs(x));
           }
         }
       }
+      atomic_max_abs(T.wC, mx);
     }
-    atomic_max_abs(T.wC, mx);
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tD, TBN);
+    tmem_dealloc(tD, 2 * TBN);
   }
 }
 

@@ -16,6 +16,7 @@ from oracle import trace as OT  # noqa: E402
 from paper_2010_08482_gb300 import ctq  # noqa: E402
 from paper_2010_08482_gb300 import workloads as w  # noqa: E402
 from test_gpu_big import complex_d_model  # noqa: E402
+from test_gpu_big64 import f7_bar  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -144,6 +145,41 @@ def test_skiplist_precision_switch(models):
         sl.set_precision(ctq.TF32)
     la2, ph2, _ = sl.evaluate()  # the refused call changed nothing
     assert rel(la2, ph2, la, ph) <= 1e-12
+
+
+# Stated BF16X3 error of the f shell (the large-block tensor kernel's stated bar).
+STATED_BF16X3_F7 = 3e-3
+
+
+def test_skiplist_f_shell_against_stored_oracle():
+    """The library-built f shell (N in {4, 5, 6}, blocks up to 3003 complex):
+    the skip list's evaluation of the first two configurations of the f7
+    batch, float64 and tensor-core products, against the oracle's stored
+    values, at the FP64 bar or the stated BF16X3 bar plus 2 beta max|dE| for
+    the measured difference of the two eigensolvers' energies."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "f7_oracle.json")
+    with open(path) as f:
+        g = json.load(f)
+    imp = ctq.build_impurity(w.model_f7(), device=0)
+    b = w.batch_f7()
+    dE, e_bar = f7_bar(imp, g, b.beta)
+    bars = parity.Bars("f7 skip list stored oracle")
+    for precision in (ctq.FP64, ctq.BF16X3):
+        sl = ctq.SkipListTrace(imp, b.beta, seed=5, precision=precision)
+        for c in range(2):
+            ref = g["chains"][c]
+            tau, op = b.chain(c)
+            sl.set(tau, op)
+            la, ph, st = sl.evaluate()
+            assert st["n_strings"] == len(ref["q0"]) and st["products"] > 0
+            err = rel(la, ph, ref["log_abs"], complex(*ref["phase"]))
+            tol = (bars.fp64(c, ref) if precision == ctq.FP64 else STATED_BF16X3_F7) + e_bar
+            print(f"\nf7 skip list precision={precision} chain {c}: rel err {err:.3e}, bar {tol:.3e}")
+            assert err <= tol, (precision, c, err)
+        del sl
+    bars.check()
 
 
 # Stated BF16X3 error of the large-block d shells (the large-block kernels' stated bar).
