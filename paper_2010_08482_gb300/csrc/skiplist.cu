@@ -320,9 +320,10 @@ struct SlTc {
 };
 
 // One thread per 8 consecutive K elements of one operand row (a 16-byte
-// core-matrix row of each plane, stored as one vector): A rows read as 64
-// contiguous bytes, L read row by row with consecutive threads on
-// consecutive columns.
+// core-matrix row of each plane, stored as one vector); consecutive threads
+// take consecutive operand rows, so a warp writes 512 contiguous bytes per
+// plane (A rows are read as 64-byte segments, L row by row with consecutive
+// threads on consecutive columns).
 __global__ void k_sl_fmt(const SlFmt* tasks, int n) {
   const SlFmt T = tasks[find_task(tasks, n, blockIdx.x)];
   int e_unused;
@@ -334,15 +335,8 @@ __global__ void k_sl_fmt(const SlFmt* tasks, int n) {
   const int nkc = T.kp_pad / TKE;
   const int Np = T.cplx ? 2 * T.N : T.N;
   for (long long g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
-    int r, k0;
-    if (T.mode == 0) {
-      r = int(g / kg_n);
-      k0 = 8 * int(g - (long long)r * kg_n);
-    } else {
-      const int kg = int(g / T.rows_pad);
-      r = int(g - (long long)kg * T.rows_pad);
-      k0 = 8 * kg;
-    }
+    const int kg = int(g / T.rows_pad);
+    const int r = int(g - (long long)kg * T.rows_pad), k0 = 8 * kg;
     uint32_t hw[4], lw[4];
 #pragma unroll
     for (int t = 0; t < 8; t += 2) {
