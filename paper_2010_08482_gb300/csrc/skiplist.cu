@@ -19,8 +19,9 @@
 // and are recomputed: about one product per level for a local insertion or
 // removal, plus the ancestors of the leaves whose sector the move shifted.
 //
-// Arithmetic: float64 on the SIMT pipe (complex blocks as [Re | Im] rows).
-// A stored product is raw: its true value is the stored matrix times
+// Arithmetic: float64 on the SIMT pipe (complex blocks as [Re | Im] rows),
+// or, with CTQ_BF16X3, the products on the tensor cores (below; leaves,
+// exponents and root traces stay float64).  A stored product is raw: its true value is the stored matrix times
 // 2^{E} (E kept on the device beside the matrix's max |entry|), and every
 // consumer scales its factors by the exact power of two that brings their
 // max |entry| into [1, 2) as it loads them, so the products are the
@@ -30,7 +31,8 @@
 // Launches: an evaluation first plans every product it needs on the host
 // (the cache decides what is new), orders the new products in rounds (a
 // product's round is one more than its factors'), and then launches one
-// grouped kernel per round over all strings and segments (CTAs find their
+// grouped kernel per round over all strings and segments (two on the
+// tensor cores: the factors' formatting and the products; CTAs find their
 // product by a binary search on tile offsets), after one kernel for the
 // new leaves and one clearing the new products' max words; one kernel takes
 // every string's root trace.  The task tables go to the device in one copy.
