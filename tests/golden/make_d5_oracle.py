@@ -1,6 +1,6 @@
-"""Writes tests/golden/d5_oracle.json: FP64 oracle traces of the first chains
-of the seeded d-shell workload (5 orbitals, Slater-Condon U = 8, J = 1, real
-crystal field, beta = 40), with, per chain, the per-sector terms (for the
+"""Writes tests/golden/d5_oracle.json: FP64 oracle traces of the chains of the
+seeded d-shell workload (by default all 1024; 5 orbitals, Slater-Condon
+U = 8, J = 1, real crystal field, beta = 40), with, per chain, the per-sector terms (for the
 cancellation rule of the comparison) and the chain's float64 perturbation
 spread: the largest relative change of w between the right-to-left product
 and the left-to-right product, the product split in the middle, and the
@@ -9,7 +9,7 @@ over 2^-53 is the chain's measured condition number, which sets how far a
 reduced-precision evaluation may stray.  Calls only the oracle (the
 perturbed blocks come from the oracle model, through tests/parity.py) and
 the seeded input generator; the GPU tests compare against these stored
-values because the oracle takes minutes for hundreds of d-shell chains.
+values because the oracle takes minutes for a thousand d-shell chains.
 
     python tests/golden/make_d5_oracle.py [n_chains] [processes]
 """
@@ -46,7 +46,7 @@ def part(args):
 
 
 def main():
-    n = int(sys.argv[1]) if len(sys.argv) > 1 else 384
+    n = int(sys.argv[1]) if len(sys.argv) > 1 else 1024
     procs = int(sys.argv[2]) if len(sys.argv) > 2 else os.cpu_count()
     t0 = time.time()
     with mp.get_context("spawn").Pool(procs) as pool:

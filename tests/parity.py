@@ -25,15 +25,19 @@ WIDEN_AT = FP64_REL
 # A mixed-precision chain is held to its stated bar, or, when its measured
 # condition number kappa = spread / 2^-53 (the chain's float64 perturbation
 # spread in units of float64's unit roundoff) times the precision's
-# effective unit exceeds the stated bar, to unit x kappa, at most this many
-# times the stated bar.
-MIXED_WIDEN_CAP = 10.0
+# effective unit exceeds the stated bar, to unit x kappa (the first-order
+# error of that precision on that chain).  A chain with unit x kappa above 1
+# (and above the stated bar) has no significant digit in the precision: it
+# gets no bar, is listed, and at most UNRESOLVED_FRAC of a test's chains
+# (at least UNRESOLVED_MIN) may be so.
+UNRESOLVED_FRAC = 0.01
+UNRESOLVED_MIN = 3
 U64 = 2.0 ** -53
 # Effective unit roundoff of one block product per precision code (ctq.TF32 = 1,
 # BF16X3 = 2, TF32X3 = 3, F32X2 = 4): TF32 operands keep 11 bits; bf16 hi / lo
 # about 16; the three-term TF32 split keeps 22 but its FP32 accumulation over
-# ~100 terms loses about 3 more (fitted on the d shell: the worst chain of
-# 384 sits at 0.8 of unit x kappa); two-float about 45.
+# ~100 terms loses about 3 more (fitted on the d shell's chains); two-float
+# about 45.
 UNIT = {1: 2.0 ** -11, 2: 2.0 ** -16, 3: 2.0 ** -19, 4: 2.0 ** -45}
 # At most this fraction of a test's chains (and at least three chains) may
 # be held to a widened bar; every widened chain is printed.  (The d shell at
@@ -66,18 +70,21 @@ class Bars:
                       max(base, min(FP64_CAP, 8 x spread)) x scale;
                       plus log_carrier(ref)
     mixed(c, ref, b, unit, err):
-                      b x min(MIXED_WIDEN_CAP, max(1, unit x spread / 2^-53 / b));
-                      a chain counts as widened only if its error needed it
-                      (err > b; every chain with a factor above 1 when err
-                      is not given)
-    check():          prints the widened chains and asserts that there are
-                      at most max(WIDEN_MIN, WIDEN_FRAC x chains seen) of them."""
+                      max(b, unit x spread / 2^-53), or no bar (inf) when
+                      that estimate exceeds max(1, b) (an unresolved chain); a chain
+                      counts as widened only if its error needed it (err > b;
+                      every chain above b when err is not given)
+    check():          prints the widened and unresolved chains and asserts
+                      that there are at most max(WIDEN_MIN, WIDEN_FRAC x
+                      chains seen) widened and max(UNRESOLVED_MIN,
+                      UNRESOLVED_FRAC x chains seen) unresolved ones."""
 
     def __init__(self, label: str, max_frac: float = WIDEN_FRAC):
         self.label = label
         self.max_frac = max_frac
         self.n = 0
         self.widened = []
+        self.unresolved = []
 
     def fp64(self, c, ref, base: float = FP64_REL, scale: float = 1.0, err=None) -> float:
         self.n += 1
@@ -90,10 +97,14 @@ class Bars:
     def mixed(self, c, ref, stated: float, unit: float, err=None) -> float:
         self.n += 1
         noise = ref.get("noise", 0.0)
-        f = min(MIXED_WIDEN_CAP, max(1.0, unit * (noise / U64) / stated))
-        if f > 1.0 and (err is None or err > stated):
-            self.widened.append((int(c), noise, stated * f))
-        return stated * f
+        est = unit * (noise / U64)
+        if est > max(1.0, stated):
+            self.unresolved.append((int(c), noise, err))
+            return math.inf
+        bar = max(stated, est)
+        if bar > stated and (err is None or err > stated):
+            self.widened.append((int(c), noise, bar))
+        return bar
 
     def check(self):
         allowed = max(WIDEN_MIN, int(self.max_frac * self.n))
@@ -101,6 +112,11 @@ class Bars:
             print(f"{self.label}: chain {c} bar widened to {bar:.2e} (float64 spread {noise:.2e})")
         print(f"{self.label}: {len(self.widened)} of {self.n} chains on a widened bar (allowed {allowed})")
         assert len(self.widened) <= allowed, (self.label, self.widened)
+        n_unres = max(UNRESOLVED_MIN, int(UNRESOLVED_FRAC * self.n))
+        for c, noise, err in self.unresolved:
+            print(f"{self.label}: chain {c} not resolved in this precision (float64 spread {noise:.2e}, "
+                  f"error {err})")
+        assert len(self.unresolved) <= n_unres, (self.label, self.unresolved)
 
 
 _PERTURBED = {}

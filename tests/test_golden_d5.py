@@ -14,10 +14,10 @@ from paper_2010_08482_gb300 import workloads as w
 
 def test_stored_values_are_the_oracle():
     n, ref = parity.gold_d5()
-    assert n == len(ref) == 384
+    assert n == len(ref) == 1024
     m = atom.Model(w.model_d5())
     b = w.batch_d5()
-    for c in (0, 101, 383):
+    for c in (0, 101, 383, 1023):
         tau, ops = b.chain(c)
         r = OT.trace_chain(m, tau, ops, beta=b.beta)
         assert ref[c]["n_ops"] == len(ops)
@@ -32,12 +32,15 @@ def test_mixed_bar_rule():
     u = parity.UNIT[2]
     well = {"noise": 0.0}
     assert bars.mixed(0, well, 1e-2, u, err=5e-3) == 1e-2
-    kappa = 1e4  # unit x kappa = 0.15: 15 x the stated bar, capped at 10 x
+    kappa = 1e4  # unit x kappa = 0.15: the first-order error on that chain
     ill = {"noise": kappa * parity.U64}
-    assert bars.mixed(1, ill, 1e-2, u, err=5e-3) == pytest.approx(0.1)
+    assert bars.mixed(1, ill, 1e-2, u, err=5e-3) == pytest.approx(u * kappa)
     assert bars.widened == []  # its error did not need the wider bar
-    assert bars.mixed(2, ill, 1e-2, u, err=5e-2) == pytest.approx(0.1)
+    assert bars.mixed(2, ill, 1e-2, u, err=5e-2) == pytest.approx(u * kappa)
     assert [c for c, _, _ in bars.widened] == [2]
     mid = {"noise": 2000 * parity.U64}  # unit x kappa = 0.0305
     assert bars.mixed(3, mid, 1e-2, u) == pytest.approx(u * 2000)
+    lost = {"noise": 2.0 ** 17 * parity.U64}  # unit x kappa = 2: no digit left
+    assert bars.mixed(4, lost, 1e-2, u, err=3.0) == math.inf
+    assert [c for c, _, _ in bars.unresolved] == [4]
     assert math.isclose(parity.UNIT[3], 2.0 ** -19)
