@@ -323,12 +323,14 @@ int ctq_eval_traces_static(const ctq_impurity* imp, const ctq_batch* batch, cons
  * (a pair inserted or removed) only the products of the segments that
  * contain a changed operator are recomputed, about one per level of the
  * skip list (O(log k)), plus the ancestors of operators whose sector the
- * change shifted.  Products in float64 on the SIMT pipe, renormalised by
- * exact powers of two; operators c and c+ only (codes 2 f + dag).  An
- * evaluation launches one kernel per dependency round of its new products
- * (all strings and segments together), plus one for the new leaves, one
- * clearing their bookkeeping words and one for the root traces, after a
- * single host-to-device copy of its task tables.
+ * change shifted.  Products in float64 on the SIMT pipe (or on the tensor
+ * cores, ctq_skiplist_set_precision), renormalised by exact powers of two;
+ * operators c and c+ only (codes 2 f + dag).  An evaluation launches one
+ * kernel per dependency round of its new products (two on the tensor cores:
+ * the factors' formatting and the products; all strings and segments
+ * together), plus one for the new leaves, one clearing their bookkeeping
+ * words and one for the root traces, after a single host-to-device copy of
+ * its task tables.
  *
  * ctq_skiplist_create: the handle works on imp's device, enqueues its
  *   kernels on `stream` (cudaStream_t, NULL = legacy default) and allocates
@@ -351,8 +353,11 @@ int ctq_eval_traces_static(const ctq_impurity* imp, const ctq_batch* batch, cons
  * ctq_skiplist_set_precision: CTQ_FP64 (default: float64 SIMT products) or
  *   CTQ_BF16X3 (products on the tensor cores: each factor scaled to max
  *   |entry| in [1, 2), split into bf16 hi / lo, hi hi + hi lo + lo hi with
- *   FP32 accumulation, stored in float64; leaves, exponents and the root
- *   traces stay float64).  Changing it releases every cached product.
+ *   FP32 accumulation folded into registers every 256 K terms, stored in
+ *   float64; leaves, exponents and the root traces stay float64; products
+ *   are computed on 128 x 256 tiles, so small blocks are mostly padding and
+ *   the float64 products are the faster choice for them).  Changing it
+ *   releases every cached product.
  *   Errors: CTQ_ERR_ARG, CTQ_ERR_UNSUPPORTED (another precision), CTQ_ERR_NOMEM.
  * Errors of set / insert / remove: CTQ_ERR_ARG (nothing changed).
  */
